@@ -1,0 +1,409 @@
+"""Benchmark: blind deblurring throughput of coprime blurred pairs at 1080p.
+
+Workload (rgb_1080p): batches of 60 frame pairs, 1920x1080 RGB float32 latents
+(20-blob generator), kernels 15x15 and 17x17 (Gaussian + random-walk motion
+mixture, unit sum), full-convolution blur plus N(0, 1e-3^2) noise; the mixed
+precision path.  One step = blind kernel estimation and dual-kernel
+deconvolution of one batch of 60 pairs, one cbp_deblur_pair call.  Inputs are
+synthesised on the device before timing (3.0 GB per batch, larger than L2, so
+no flush is needed between steps).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Multi-GPU: one process per GPU (torchrun); each rank deblurs its own batch
+(weak scaling, no data-path collective -- frame pairs are independent);
+the host-side barrier and max-over-ranks timing use gloo.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "deblurred frame-pairs/s at 1080p (plain vs mixed/learned, kernel rel-err≤1e-3); p99 ms"
+UNIT = "frame-pairs/s"
+WORKLOAD = "rgb_1080p"
+H, W, C, T1, T2, SIGMA, EPS = 1080, 1920, 3, 15, 17, 1e-3, 1e-4
+H1, W1, H2, W2 = H + T1 - 1, W + T1 - 1, H + T2 - 1, W + T2 - 1
+PH, PW = 1120, 1944          # smallest 7-smooth sizes >= 1096, 1936
+PW2 = PW // 2 + 1
+
+
+def config(pairs):
+    return {"workload": f"{WORKLOAD}: {pairs} pairs/step, 1920x1080x3 f32, kernels 15x15 + 17x17 "
+                        f"(Gaussian+motion mixture), noise sigma 1e-3, mixed path, eps 1e-4",
+            "pairs_per_step": pairs, "fft_grid": [PH, PW],
+            "l2": "inputs 3.0 GB per step > L2; no flush between steps"}
+
+
+# ----------------------------------------------------------- roofline data --
+def algorithmic_bytes(stage: str, n: int) -> float | None:
+    """Bytes a stage must move per launch in the three-pass design (f32 frames,
+    complex64 spectra), for n pairs."""
+    fr = n * C * (H1 * W1 + H2 * W2) * 4
+    spec = n * C * (H1 + H2) * PW2 * 8
+    khat = n * 2 * PH * PW2 * 8
+    ihat = n * C * H * PW2 * 8
+    lat = n * C * H * W * 4
+    return {
+        "eval": fr,                                # two kernels, each reads one direction
+        "row_fft": fr + spec,
+        "col_deconv": spec + khat + ihat,
+        "row_ifft": ihat + lat,
+    }.get(stage)
+
+
+STAGE_LAUNCHES = {"eval": 2}
+STAGE_FILES = {"eval": "cbp_eval.cu", "sample_solve": "cbp_solve.cu", "scale_solve": "cbp_solve.cu",
+               "kernel_spectra": "cbp_fft.cu", "row_fft": "cbp_fft.cu", "col_deconv": "cbp_fft.cu",
+               "row_ifft": "cbp_fft.cu"}
+
+
+def source_hash(stage: str) -> str:
+    f = ROOT / "paper_1203_4874_gb300" / "csrc" / STAGE_FILES[stage]
+    return hashlib.sha256(f.read_bytes()).hexdigest()[:16]
+
+
+def measured_traffic(stage: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel's
+    source has not changed since it was captured."""
+    p = ROOT / "profiles" / "traffic.json"
+    if not p.exists():
+        return None
+    rec = json.loads(p.read_text()).get(stage)
+    if not rec or rec.get("source_sha256_16") != source_hash(stage):
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------ clocks --
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)], stdout=self.out, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.out.flush()
+        rows = [l.split(",") for l in Path(self.out.name).read_text().splitlines() if l.strip()]
+        os.unlink(self.out.name)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------- inputs ---
+def make_inputs(ctx, n: int, seed0: int, device):
+    """Kernels and blob parameters drawn on the host (cbp_synth), latents and
+    blurred frames synthesised on the device by the library's forward model."""
+    import numpy as np
+    import torch
+    from cbp_synth.generators import _rng, blob_params, draw_kernel_pair
+    from paper_1203_4874_gb300 import cbp
+
+    k1s, k2s, blobs = [], [], []
+    for f in range(n):
+        rng = _rng(seed0 + f)
+        blobs.append(np.stack([blob_params(rng, H, W) for _ in range(C)]))
+        a, b = draw_kernel_pair(rng, T1, T2, max(T1, T2), "mixture")
+        k1s.append(a)
+        k2s.append(b)
+    k1 = torch.from_numpy(np.stack(k1s)).to(device)
+    k2 = torch.from_numpy(np.stack(k2s)).to(device)
+    bl = torch.from_numpy(np.stack(blobs)).to(device)
+    lat = cbp.cbp_synth_latent(ctx, bl, n, C, H, W, torch.float32, 0.05, seed0)
+    b1 = cbp.cbp_forward_blur(ctx, lat, k1, SIGMA, seed0 * 2 + 1)
+    b2 = cbp.cbp_forward_blur(ctx, lat, k2, SIGMA, seed0 * 2 + 2)
+    torch.cuda.synchronize()
+    del lat
+    return b1, b2, k1, k2
+
+
+# ------------------------------------------------------- CPU oracle sample --
+def cpu_worker(pairs: int):
+    """Time the FP64 oracle on `pairs` pairs of the workload (host cores)."""
+    import numpy as np
+    import scipy.signal
+    import oracle
+    from cbp_synth import make_pair_inputs
+
+    total = 0.0
+    for f in range(pairs):
+        inp = make_pair_inputs(WORKLOAD, f)
+        b1 = np.stack([scipy.signal.fftconvolve(ch, inp.k1) for ch in inp.latent]) + inp.noise1
+        b2 = np.stack([scipy.signal.fftconvolve(ch, inp.k2) for ch in inp.latent]) + inp.noise2
+        b1 = b1.astype(np.float32).astype(np.float64)
+        b2 = b2.astype(np.float32).astype(np.float64)
+        t0 = time.perf_counter()
+        oracle.deblur_pair(b1, b2, T1, T2, eps=EPS)
+        total += time.perf_counter() - t0
+    print(json.dumps({"pairs": pairs, "seconds": total}))
+
+
+def cpu_baseline(pairs: int):
+    cores = os.cpu_count() or 1
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = str(cores)
+    r = subprocess.run([sys.executable, str(Path(__file__).resolve()), "--cpu-worker", str(pairs)],
+                       capture_output=True, text=True, env=env, timeout=1800)
+    line = [l for l in r.stdout.splitlines() if l.startswith("{")]
+    if r.returncode != 0 or not line:
+        return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle",
+                "sample": "failed: " + (r.stderr.strip().splitlines() or ["?"])[-1]}
+    d = json.loads(line[-1])
+    return {"value": d["pairs"] / d["seconds"], "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{d['pairs']} pairs (frames 0..{d['pairs'] - 1}) of {WORKLOAD}, FP64 numpy "
+                      f"oracle, estimation + deconvolution, BLAS threads = {cores}"}
+
+
+def reference_arm(args):
+    """The oracle on the host cores: each step deblurs one pair of the workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
+        os.environ.setdefault(k, str(cores))
+    import numpy as np
+    import scipy.signal
+    import oracle
+    from cbp_synth import make_pair_inputs
+
+    inputs = []
+    for f in range(args.steps + args.warmup):
+        inp = make_pair_inputs(WORKLOAD, f % 60)
+        b1 = np.stack([scipy.signal.fftconvolve(ch, inp.k1) for ch in inp.latent]) + inp.noise1
+        b2 = np.stack([scipy.signal.fftconvolve(ch, inp.k2) for ch in inp.latent]) + inp.noise2
+        inputs.append((b1.astype(np.float32).astype(np.float64), b2.astype(np.float32).astype(np.float64)))
+    for i in range(args.warmup):
+        oracle.deblur_pair(*inputs[i], T1, T2, eps=EPS)
+    times = []
+    for i in range(args.warmup, args.warmup + args.steps):
+        t0 = time.perf_counter()
+        oracle.deblur_pair(*inputs[i], T1, T2, eps=EPS)
+        times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps / total
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config(1),
+        "p50_ms": 1e3 * statistics.median(times), "p99_ms": 1e3 * max(times),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"1 pair per step of {WORKLOAD}, FP64 numpy oracle"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+# ------------------------------------------------------------------ main ----
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="cbp", choices=["cbp", "reference"])
+    ap.add_argument("--pairs", type=int, default=60)
+    ap.add_argument("--cpu-pairs", type=int, default=6)
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-worker", type=int, default=0)
+    args = ap.parse_args()
+    if args.cpu_worker:
+        cpu_worker(args.cpu_worker)
+        return
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+    from paper_1203_4874_gb300 import build, cbp
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("gloo")
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    ctx = cbp.cbp_create(local, 0)
+    n = args.pairs
+    b1, b2, _, _ = make_inputs(ctx, n, 1203000 + rank * n, dev)
+    prm = cbp.params(T1, T2, path="mixed", eps=EPS)
+    lat = torch.empty((n, C, H, W), dtype=torch.float32, device=dev)
+    k1 = torch.empty((n, T1, T1), dtype=torch.float32, device=dev)
+    k2 = torch.empty((n, T2, T2), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step(p=prm):
+        cbp.cbp_deblur_pair(ctx, b1, b2, p, k1=k1, k2=k2, latent=lat, diag=False, stream=stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    # ---- timed region (device-resident inputs) ----
+    clocks = ClockSampler(local)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    cbp.cbp_stage_times(ctx)
+    cbp.cbp_profile(ctx, True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev[0].record(stream)
+    for i in range(args.steps):
+        step()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    cbp.cbp_profile(ctx, False)
+    stages = cbp.cbp_stage_times(ctx)
+    per_step = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    elapsed_ms = ev[0].elapsed_time(ev[-1])
+    if world > 1:
+        t = torch.tensor([elapsed_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    value = world * n * args.steps / (elapsed_ms / 1e3)
+    mixed_k1, mixed_k2 = k1.clone(), k2.clone()
+
+    # ---- plain FP64 path on the same batch (comparison) ----
+    prm64 = cbp.params(T1, T2, path="fp64", eps=EPS)
+    step(prm64)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.fp64_steps):
+        step(prm64)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    fp64_ms = e0.elapsed_time(e1) / max(args.fp64_steps, 1)
+    rel = lambda a, b: ((a - b).flatten(1).norm(dim=1) / b.flatten(1).norm(dim=1)).max().item()
+    kerr = max(rel(mixed_k1.double(), k1.double()), rel(mixed_k2.double(), k2.double()))
+
+    # ---- end to end through the C ABI with host buffers ----
+    b1h = b1.cpu().pin_memory()
+    b2h = b2.cpu().pin_memory()
+    lath = torch.empty((n, C, H, W), dtype=torch.float32).pin_memory()
+    k1h = torch.empty((n, T1, T1), dtype=torch.float32).pin_memory()
+    k2h = torch.empty((n, T2, T2), dtype=torch.float32).pin_memory()
+    prmh = cbp.params(T1, T2, path="mixed", eps=EPS, flags=cbp.CBP_FLAG_HOST_IO)
+
+    def step_h():
+        cbp.cbp_deblur_pair(ctx, b1h, b2h, prmh, k1=k1h, k2=k2h, latent=lath, diag=False, stream=stream)
+
+    step_h()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.e2e_steps):
+        step_h()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e2e_ms = e0.elapsed_time(e1)
+    if world > 1:
+        t = torch.tensor([e2e_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e_value = world * n * args.e2e_steps / (e2e_ms / 1e3)
+    h2d = n * C * (H1 * W1 + H2 * W2) * 4
+    d2h = n * C * H * W * 4 + n * (T1 * T1 + T2 * T2) * 4
+
+    # ---- roofline of the dominant stage ----
+    dom = max((s for s in stages if stages[s][1] > 0), key=lambda s: stages[s][0])
+    dom_ms = stages[dom][0] / args.steps
+    alg = algorithmic_bytes(dom, n)
+    peak, peak_kind = peaks()
+    if alg is not None:
+        achieved = alg / (dom_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_kind,
+                "algorithmic_bytes_per_launch": alg, "ms_per_launch": dom_ms,
+                "traffic": measured_traffic(dom)}
+    else:
+        roof = {"bound": "alu", "kernel": dom, "achieved": None, "peak": None, "unit": None,
+                "frac": None, "ms_per_launch": dom_ms, "traffic": None}
+    stage_ms = {s: round(stages[s][0] / args.steps, 4) for s in stages if stages[s][1] > 0}
+    launches = sum(v[1] for v in stages.values())
+
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32 (eval/Gram/FFT) + f64 (solves)",
+        "data": "synthetic (device forward model)", "config": config(n),
+        "p50_ms": statistics.median(per_step), "p99_ms": sorted(per_step)[int(0.99 * (len(per_step) - 1))],
+        "plain_fp64": {"value": world * n / (fp64_ms / 1e3), "unit": UNIT, "ms_per_step": fp64_ms},
+        "kernel_rel_err_mixed_vs_fp64": kerr,
+        "roofline": roof, "stage_ms_per_step": stage_ms,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches, "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(args.cpu_pairs)
+    cbp.cbp_destroy(ctx)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

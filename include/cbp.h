@@ -1,0 +1,273 @@
+/*
+ * cbp.h -- C ABI of libcbp, a single-GPU (sm_103a) implementation of Coprime
+ * Blurred Pair (CBP) deblurring: Thorpe, Li, Li, Yu, Saunders, Yu, "A Co-Prime
+ * Blur Scheme for Data Security in Video Surveillance" (arXiv 1203.4874).
+ *
+ * Problem (Section 4, Eq. 1 and Eq. 4): two frames of one scene, B1 = L (x) K1
+ * and B2 = L (x) K2 (full 2D convolution plus sensor noise), blurred by two
+ * unknown kernels that are coprime as bivariate polynomials (Section 3).
+ * Recover K1, K2 blindly and then the latent frame L.
+ *
+ * Conventions for every entry point:
+ *   - All calls are asynchronous on the given CUDA stream (`stream` is a
+ *     cudaStream_t passed as void*; NULL is the legacy default stream) unless
+ *     stated otherwise.  Host-side validation happens before anything is
+ *     enqueued; a negative return value means nothing was enqueued.
+ *   - Frame, kernel and latent buffers are owned by the caller.  Device
+ *     pointers must stay valid until the stream reaches the call's work.
+ *   - A context owns its device workspace, which is counted against the HBM
+ *     budget given to cbp_create().  Calls on one context that use its
+ *     workspace (estimate / deblur / forward) must be ordered on one stream, or
+ *     the caller must synchronise between them.
+ *   - No C++ exception crosses the ABI.  Negative cbp_status values are
+ *     errors, positive values are warnings, 0 is success.
+ *   - Arrays are row-major.  A frame batch is addressed as
+ *       data[f * frame_stride + ch * chan_stride + r * row_stride + col]
+ *     in elements of its dtype.
+ */
+#ifndef CBP_H_
+#define CBP_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum cbp_status {
+  CBP_OK = 0,
+  CBP_WARN_ILL_CONDITIONED = 1, /* some sample had sigma_{n-1}/sigma_1 < 1e-8  */
+  CBP_ERR_INVALID_ARG = -1,     /* bad pointer, size, dtype, NaN/Inf input     */
+  CBP_ERR_SIZE_MISMATCH = -2,   /* blurred sizes inconsistent with t1, t2      */
+  CBP_ERR_NOT_COPRIME = -3,     /* some sample had sigma_{n-1}/sigma_1 < 1e-13 */
+  CBP_ERR_OOM = -4,             /* device allocation failed                    */
+  CBP_ERR_CUDA = -5,            /* a CUDA runtime call failed                  */
+  CBP_ERR_BUSY = -6,            /* stream request not finished yet             */
+  CBP_ERR_TIMEOUT = -7,         /* wait limit reached                          */
+  CBP_ERR_BUDGET = -8,          /* request exceeds the context's HBM budget    */
+  CBP_ERR_UNSUPPORTED = -9      /* size beyond a documented library limit      */
+} cbp_status;
+
+typedef enum cbp_dtype { CBP_F32 = 0, CBP_F64 = 1 } cbp_dtype;
+
+/* Arithmetic of the kernel-estimation path.
+ *   FP64:  evaluation, Gram and per-sample solves in double precision (the
+ *          per-sample eigen-solve runs in single precision and is refined to
+ *          double precision against the double-precision Gram and the exact
+ *          residual).  Deconvolution in the frames' dtype.
+ *   MIXED: evaluation in single precision; Gram of the non-constant samples
+ *          in single precision; the z = 1 sample (real, highest signal-to-noise,
+ *          smallest relative eigen-gap) in double precision; eigen-solves in
+ *          single precision refined in double precision; scale fix in double
+ *          precision; deconvolution in single precision.
+ *   LEARNED: a network proposal checked by the consistency residual, falling
+ *          back to MIXED (see cbp_learned_*). */
+typedef enum cbp_path { CBP_PATH_FP64 = 0, CBP_PATH_MIXED = 1, CBP_PATH_LEARNED = 2 } cbp_path;
+
+/* A batch of n frames of one shape (one frame of each pair per batch entry). */
+typedef struct cbp_frames {
+  const void* data;     /* device pointer (host pointer with CBP_FLAG_HOST_IO) */
+  int32_t n;            /* frames in the batch, >= 1                          */
+  int32_t c;            /* channels, >= 1 (kernels are shared by channels)    */
+  int32_t h, w;         /* rows, columns of each channel                      */
+  cbp_dtype dtype;
+  int64_t row_stride;   /* elements; 0 => w                                   */
+  int64_t chan_stride;  /* elements; 0 => h * row_stride                      */
+  int64_t frame_stride; /* elements; 0 => c * chan_stride                     */
+} cbp_frames;
+
+/* Flags of cbp_params.flags. */
+#define CBP_FLAG_HOST_IO 1u      /* frames, kernels and latent are host buffers; the
+                                    library stages them through device memory on the
+                                    stream (pinned host memory keeps this async)    */
+#define CBP_FLAG_KERNELS_IN 2u   /* k1, k2 are inputs: skip estimation, deconvolve */
+#define CBP_FLAG_SINGLE_KERNEL 4u/* deconvolve B1 by K1 alone (Section 4) instead of
+                                    the dual-kernel formula                         */
+#define CBP_FLAG_KERNELS_F64 8u  /* k1, k2 buffers hold doubles whatever the frames'
+                                    dtype (the FP64 path's full accuracy)           */
+
+typedef struct cbp_params {
+  int32_t t1, t2;     /* kernel sizes (square kernels), 1 <= t_k, t1 + t2 <= 64  */
+  int32_t m;          /* unit-circle samples per direction; 0 => max(t1, t2);
+                         must satisfy max(t1, t2) <= m <= 32                      */
+  cbp_path path;
+  double eps;         /* Wiener regulariser of the deconvolution, >= 0           */
+  int32_t pad_h, pad_w; /* FFT grid; 0 => smallest 7-smooth >= larger blurred size */
+  double accept_rho;  /* learned path: accept the proposal when rho <= accept_rho  */
+  uint32_t flags;     /* CBP_FLAG_*                                              */
+  int32_t reserved;
+} cbp_params;
+
+/* Per-pair diagnostics, computed on the device (one entry per batch entry). */
+typedef struct cbp_diag {
+  double kappa_max;     /* max over samples of sigma_1 / sigma_{n-1}               */
+  double gap_min;       /* min over samples of sigma_{n-1} / sigma_1               */
+  double sigma_min_max; /* max over samples of sigma_n / sigma_1 (noise level)     */
+  double scale_resid;   /* sigma_min / sigma_max of the scale least-squares system */
+  double imag_ratio;    /* ||Im|| / ||Re|| of the inverse DFT of the kernel spectra */
+  double support_ratio; /* energy of the inverse DFT outside t_k x t_k / total     */
+  double rho;           /* learned path: ||B1*K2 - B2*K1|| / ||B1||                */
+  int32_t flagged_samples; /* samples with sigma_{n-1}/sigma_1 < 1e-8              */
+  int32_t used_fallback;   /* learned path: 1 if the GCD solve ran                 */
+  int32_t pad_h, pad_w;    /* FFT grid used                                        */
+  int32_t status;          /* cbp_status derived from the fields above             */
+  int32_t hard_samples;    /* samples solved by double-precision inverse iteration */
+} cbp_diag;
+
+typedef struct cbp_ctx cbp_ctx;
+
+/* Create a context on `device` (made current for the call).  Device memory
+ * the context allocates (workspaces, serving slots) never exceeds
+ * hbm_budget_bytes (0 => 90% of the free memory at creation).
+ * Errors: CBP_ERR_INVALID_ARG (out == NULL), CBP_ERR_CUDA (bad device). */
+cbp_status cbp_create(cbp_ctx** out, int device, size_t hbm_budget_bytes);
+
+/* Destroy a context: waits for its serving work, frees everything it owns. */
+cbp_status cbp_destroy(cbp_ctx* ctx);
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* cbp_status_string(cbp_status s);
+
+/* Device workspace one cbp_deblur_pair / cbp_estimate_kernels call with these
+ * arguments needs (bytes, written to *bytes).  No device work. */
+cbp_status cbp_workspace_size(const cbp_frames* b1, const cbp_frames* b2,
+                              const cbp_params* params, size_t* bytes);
+
+/* Blind kernel estimation for a batch of frame pairs (Sections 4-5):
+ *   1. evaluation of both frames' z-polynomials at the m-th roots of unity in
+ *      z2 (rows kept) and in z1 (columns kept) -- Eq. 3, Section 5's DFT;
+ *   2. at every sample, the univariate cofactor pair (u, v) ~ (k1, k2) as the
+ *      null vector of the Sylvester system b1*v - b2*u = 0 (Eq. 4), channels'
+ *      rows stacked;
+ *   3. lifting of the cofactors to two m x m estimates of the kernels' 2D DFT,
+ *      least-squares fix of their per-sample scales, average, normalisation to
+ *      unit kernel sum (Section 5);
+ *   4. inverse m x m DFT to the spatial kernels.
+ * b1: n frames of (H + t1 - 1) x (W + t1 - 1); b2: n frames of
+ * (H + t2 - 1) x (W + t2 - 1); same n, c and dtype.
+ * k1: device, n * t1 * t1 elements of b1's dtype (double with
+ * CBP_FLAG_KERNELS_F64); k2: n * t2 * t2 (row-major).
+ * diag: NULL or host array of n entries, filled by an asynchronous copy on the
+ * stream (valid after the stream is synchronised; pinned memory recommended).
+ * Errors: CBP_ERR_INVALID_ARG, CBP_ERR_SIZE_MISMATCH, CBP_ERR_UNSUPPORTED,
+ * CBP_ERR_BUDGET, CBP_ERR_OOM, CBP_ERR_CUDA.  Device-detected conditions
+ * (ill-conditioned or non-coprime samples, NaN/Inf input) are reported in
+ * diag[i].status. */
+cbp_status cbp_estimate_kernels(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
+                                const cbp_params* params, void* k1, void* k2,
+                                cbp_diag* diag, void* stream);
+
+/* Intermediates of the estimation path, for stage-by-stage checking.  Every
+ * member is NULL (skipped) or a caller-owned device buffer the library copies
+ * into (on the stream, after the estimation).  s = m/2 + 1 solved samples per
+ * direction (samples m - j are the conjugates of samples j); complex values
+ * are (re, im) pairs; "T" is double on the FP64 path and float on the others.
+ *   p_z2[k]: T complex [n][c][s][H_Bk]  samples of B_k at z2 = w^j (Eq. 3)
+ *   p_z1[k]: T complex [n][c][s][W_Bk]  samples of B_k at z1 = w^i
+ *   x_z2, x_z1: double complex [n][s][t1+t2] unit null vectors [u; v] per sample
+ *   sample_diag: double [n][2][s][4]: lambda_max, second smallest eigenvalue and
+ *            Rayleigh quotient of the per-sample normal matrix, 1 if solved by
+ *            the double-precision block inverse iteration
+ *   lifted:  double complex [n][4][m][m]: A_1, A_2 (z2-first order), B_1, B_2
+ *            (z1-first order) estimates of the kernels' m x m DFT
+ *   kernels: double [n][t1*t1 + t2*t2]: K1 then K2 before the dtype cast */
+typedef struct cbp_stage_out {
+  void* p_z2[2];
+  void* p_z1[2];
+  void* x_z2;
+  void* x_z1;
+  void* sample_diag;
+  void* lifted;
+  void* kernels;
+} cbp_stage_out;
+
+/* cbp_estimate_kernels plus copies of the intermediates into `out` (may be NULL). */
+cbp_status cbp_estimate_kernels_stages(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
+                                       const cbp_params* params, void* k1, void* k2,
+                                       cbp_diag* diag, const cbp_stage_out* out, void* stream);
+
+/* Kernel estimation (as above, unless CBP_FLAG_KERNELS_IN) followed by the
+ * dual-kernel Fourier deconvolution on a pad_h x pad_w grid:
+ *   I^ = (conj(K1^) B1^ + conj(K2^) B2^) / (|K1^|^2 + |K2^|^2 + eps),
+ * latent = real(IDFT(I^))[0:H, 0:W] per channel (Section 4 divides B1 by K1
+ * in the Fourier domain; CBP_FLAG_SINGLE_KERNEL selects that form,
+ * conj(K1^) B1^ / (|K1^|^2 + eps)).
+ * k1, k2: NULL (kernels kept internal) or device buffers as in
+ * cbp_estimate_kernels (inputs with CBP_FLAG_KERNELS_IN).
+ * latent: device, n * c * H * W elements of b1's dtype, contiguous.
+ * With CBP_FLAG_HOST_IO every buffer is a host buffer and the copies are part
+ * of the call.  Errors as cbp_estimate_kernels. */
+cbp_status cbp_deblur_pair(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
+                           const cbp_params* params, void* k1, void* k2, void* latent,
+                           cbp_diag* diag, void* stream);
+
+/* Forward model of Eq. 1 (the camera side of Section 3): out = L (x) K + N,
+ * full 2D convolution of every channel of a latent batch with one kernel per
+ * batch entry, plus N(0, sigma^2) noise from a counter-based generator
+ * (Philox-4x32-10) keyed by `seed` (sigma = 0: no noise).
+ * latent: device, n x c x h x w of dtype; kernel: device, n x t x t doubles;
+ * out: device, n x c x (h + t - 1) x (w + t - 1) of dtype, contiguous. */
+cbp_status cbp_forward_blur(cbp_ctx* ctx, const void* latent, int32_t n, int32_t c,
+                            int32_t h, int32_t w, cbp_dtype dtype, const double* kernel,
+                            int32_t t, double sigma, uint64_t seed, void* out, void* stream);
+
+/* Synthetic latent frames for benchmarks (stand-in for the paper's camera
+ * video, Section 6): for every channel, sum of Gaussian blobs
+ * a * exp(-((x-cx)^2 + (y-cy)^2) / (2 s^2)) plus a uniform floor U[0, floor_amp]
+ * from Philox-4x32-10 keyed by `seed`.
+ * blobs: device, n x c x nblobs x 4 doubles (a, s, cx, cy); out: device,
+ * n x c x h x w of dtype, contiguous. */
+cbp_status cbp_synth_latent(cbp_ctx* ctx, const double* blobs, int32_t nblobs, int32_t n,
+                            int32_t c, int32_t h, int32_t w, cbp_dtype dtype, double floor_amp,
+                            uint64_t seed, void* out, void* stream);
+
+/* Per-stage timing (the paper's Table 1 reports per-stage times, Section 6).
+ * With profiling enabled, every call on the context brackets each stage with
+ * CUDA events on its stream; cbp_stage_times() waits for the recorded events,
+ * adds each stage's elapsed milliseconds into ms[stage] and its kernel-launch
+ * count into launches[stage] (arrays of CBP_NUM_STAGES entries, either may be
+ * NULL), and clears the record.  Stages of the serving engine are not timed. */
+typedef enum cbp_stage {
+  CBP_STAGE_EVAL = 0,           /* A1: sample polynomials (2 kernels)           */
+  CBP_STAGE_SAMPLE_SOLVE = 1,   /* A2-A3: per-sample Gram + null vector          */
+  CBP_STAGE_SCALE_SOLVE = 2,    /* A4-A5: lift, scale fix, inverse DFT           */
+  CBP_STAGE_KERNEL_SPECTRA = 3, /* kernels' spectra on the FFT grid (+ twiddles) */
+  CBP_STAGE_ROW_FFT = 4,        /* forward real row FFTs of B1, B2               */
+  CBP_STAGE_COL_DECONV = 5,     /* column FFTs + dual-kernel formula + inverse    */
+  CBP_STAGE_ROW_IFFT = 6,       /* inverse row FFTs, crop, scale                  */
+  CBP_STAGE_H2D = 7,            /* host-to-device copies (CBP_FLAG_HOST_IO)       */
+  CBP_STAGE_D2H = 8,            /* device-to-host copies (CBP_FLAG_HOST_IO)       */
+  CBP_NUM_STAGES = 9
+} cbp_stage;
+
+cbp_status cbp_profile(cbp_ctx* ctx, int32_t enable);
+cbp_status cbp_stage_times(cbp_ctx* ctx, double* ms, int64_t* launches);
+
+/* --- serving: continuous batching of independent requests (frame pairs of
+ * any supported shape).  cbp_stream_submit copies the request descriptor and
+ * returns at once with a ticket; a scheduler thread admits requests when a
+ * workspace slot and HBM budget are free, batches requests of the same shape
+ * bucket, and runs them on a pool of streams with captured CUDA graphs.
+ * Buffers are device buffers owned by the caller and must stay valid until
+ * the request completes.  Thread-safe. ---------------------------------- */
+cbp_status cbp_stream_submit(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
+                             const cbp_params* params, void* k1, void* k2, void* latent,
+                             uint64_t* ticket);
+
+/* Wait up to timeout_us (0: do not wait, < 0: wait without limit) for a
+ * ticket.  Returns the request's status once done (diag filled if non-NULL;
+ * the ticket is then released), CBP_ERR_BUSY if not done yet and
+ * timeout_us == 0, CBP_ERR_TIMEOUT if the limit passed,
+ * CBP_ERR_INVALID_ARG for an unknown ticket. */
+cbp_status cbp_stream_poll(cbp_ctx* ctx, uint64_t ticket, int32_t timeout_us, cbp_diag* diag);
+
+/* Serving statistics: completed requests, p50 and p99 latency (ms, submit to
+ * completion) since the last reset; reset when `reset` != 0. */
+cbp_status cbp_stream_stats(cbp_ctx* ctx, uint64_t* completed, double* p50_ms,
+                            double* p99_ms, int32_t reset);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CBP_H_ */

@@ -1,0 +1,287 @@
+"""ctypes binding of libcbp (include/cbp.h), names as in the C ABI.
+
+Argument marshalling only: tensors become ``cbp_frames`` descriptors and raw
+pointers, every step of the method runs in the CUDA library.  PyTorch supplies
+device memory and streams.  If ``libcbp.so`` is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+from ctypes import POINTER, byref, c_double, c_int, c_int32, c_int64, c_uint32, c_uint64, c_void_p
+from pathlib import Path
+
+import torch
+
+LIB_PATH = Path(__file__).resolve().parent / "libcbp.so"
+
+CBP_OK, CBP_WARN_ILL_CONDITIONED = 0, 1
+CBP_ERR_INVALID_ARG, CBP_ERR_SIZE_MISMATCH, CBP_ERR_NOT_COPRIME = -1, -2, -3
+CBP_ERR_OOM, CBP_ERR_CUDA, CBP_ERR_BUSY, CBP_ERR_TIMEOUT = -4, -5, -6, -7
+CBP_ERR_BUDGET, CBP_ERR_UNSUPPORTED = -8, -9
+CBP_F32, CBP_F64 = 0, 1
+CBP_PATH_FP64, CBP_PATH_MIXED, CBP_PATH_LEARNED = 0, 1, 2
+CBP_FLAG_HOST_IO, CBP_FLAG_KERNELS_IN, CBP_FLAG_SINGLE_KERNEL, CBP_FLAG_KERNELS_F64 = 1, 2, 4, 8
+PATHS = {"fp64": CBP_PATH_FP64, "mixed": CBP_PATH_MIXED, "learned": CBP_PATH_LEARNED}
+
+# Every symbol include/cbp.h declares (checked by the CPU tests).
+EXPORTED = [
+    "cbp_create", "cbp_destroy", "cbp_status_string", "cbp_workspace_size",
+    "cbp_estimate_kernels", "cbp_deblur_pair", "cbp_forward_blur", "cbp_synth_latent",
+    "cbp_stream_submit", "cbp_stream_poll", "cbp_stream_stats", "cbp_profile", "cbp_stage_times",
+    "cbp_estimate_kernels_stages",
+]
+STAGES = ["eval", "sample_solve", "scale_solve", "kernel_spectra", "row_fft", "col_deconv",
+          "row_ifft", "h2d", "d2h"]
+
+
+class cbp_frames(ctypes.Structure):
+    _fields_ = [("data", c_void_p), ("n", c_int32), ("c", c_int32), ("h", c_int32),
+                ("w", c_int32), ("dtype", c_int), ("row_stride", c_int64),
+                ("chan_stride", c_int64), ("frame_stride", c_int64)]
+
+
+class cbp_params(ctypes.Structure):
+    _fields_ = [("t1", c_int32), ("t2", c_int32), ("m", c_int32), ("path", c_int),
+                ("eps", c_double), ("pad_h", c_int32), ("pad_w", c_int32),
+                ("accept_rho", c_double), ("flags", c_uint32), ("reserved", c_int32)]
+
+
+class cbp_stage_out(ctypes.Structure):
+    _fields_ = [("p_z2", c_void_p * 2), ("p_z1", c_void_p * 2), ("x_z2", c_void_p), ("x_z1", c_void_p),
+                ("sample_diag", c_void_p), ("lifted", c_void_p), ("kernels", c_void_p)]
+
+
+class cbp_diag(ctypes.Structure):
+    _fields_ = [("kappa_max", c_double), ("gap_min", c_double), ("sigma_min_max", c_double),
+                ("scale_resid", c_double), ("imag_ratio", c_double), ("support_ratio", c_double),
+                ("rho", c_double), ("flagged_samples", c_int32), ("used_fallback", c_int32),
+                ("pad_h", c_int32), ("pad_w", c_int32), ("status", c_int32),
+                ("hard_samples", c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_lib = None
+
+
+def lib() -> ctypes.CDLL:
+    """Load libcbp.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not LIB_PATH.exists():
+            raise RuntimeError(f"libcbp.so not built at {LIB_PATH}; run __graft_entry__.build()")
+        L = ctypes.CDLL(str(LIB_PATH))
+        fr, pr, dg = POINTER(cbp_frames), POINTER(cbp_params), POINTER(cbp_diag)
+        sig = {
+            "cbp_create": ([POINTER(c_void_p), c_int, ctypes.c_size_t], c_int),
+            "cbp_destroy": ([c_void_p], c_int),
+            "cbp_status_string": ([c_int], ctypes.c_char_p),
+            "cbp_workspace_size": ([fr, fr, pr, POINTER(ctypes.c_size_t)], c_int),
+            "cbp_estimate_kernels": ([c_void_p, fr, fr, pr, c_void_p, c_void_p, dg, c_void_p], c_int),
+            "cbp_deblur_pair": ([c_void_p, fr, fr, pr, c_void_p, c_void_p, c_void_p, dg, c_void_p], c_int),
+            "cbp_forward_blur": ([c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int,
+                                  c_void_p, c_int32, c_double, c_uint64, c_void_p, c_void_p], c_int),
+            "cbp_synth_latent": ([c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int32,
+                                  c_int, c_double, c_uint64, c_void_p, c_void_p], c_int),
+            "cbp_stream_submit": ([c_void_p, fr, fr, pr, c_void_p, c_void_p, c_void_p,
+                                   POINTER(c_uint64)], c_int),
+            "cbp_stream_poll": ([c_void_p, c_uint64, c_int32, dg], c_int),
+            "cbp_stream_stats": ([c_void_p, POINTER(c_uint64), POINTER(c_double), POINTER(c_double),
+                                  c_int32], c_int),
+            "cbp_profile": ([c_void_p, c_int32], c_int),
+            "cbp_estimate_kernels_stages": ([c_void_p, fr, fr, pr, c_void_p, c_void_p, dg,
+                                             POINTER(cbp_stage_out), c_void_p], c_int),
+            "cbp_stage_times": ([c_void_p, POINTER(c_double), POINTER(c_int64)], c_int),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+class CbpError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {status_string(status)} ({status})")
+
+
+def status_string(s: int) -> str:
+    return lib().cbp_status_string(int(s)).decode()
+
+
+def _check(s: int, what: str) -> int:
+    if s < 0:
+        raise CbpError(s, what)
+    return s
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream if torch.cuda.is_available() else None
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def frames(t: torch.Tensor) -> cbp_frames:
+    """Descriptor of a (n, c, h, w), (c, h, w) or (h, w) float32/float64 tensor."""
+    if t.dtype not in (torch.float32, torch.float64):
+        raise TypeError("frames must be float32 or float64")
+    v = t
+    while v.dim() < 4:
+        v = v.unsqueeze(0)
+    n, c, h, w = v.shape
+    sn, sc, sh, sw = v.stride()
+    if sw != 1:
+        raise ValueError("frames need unit column stride")
+    return cbp_frames(v.data_ptr(), n, c, h, w, CBP_F64 if t.dtype == torch.float64 else CBP_F32,
+                      sh, sc, sn)
+
+
+def params(t1: int, t2: int, m: int = 0, path: str = "fp64", eps: float = 1e-4, pad_h: int = 0,
+           pad_w: int = 0, accept_rho: float = 1e-3, flags: int = 0) -> cbp_params:
+    return cbp_params(t1, t2, m, PATHS[path], eps, pad_h, pad_w, accept_rho, flags, 0)
+
+
+def cbp_create(device: int = 0, hbm_budget_bytes: int = 0) -> c_void_p:
+    ctx = c_void_p()
+    _check(lib().cbp_create(byref(ctx), device, hbm_budget_bytes), "cbp_create")
+    return ctx
+
+
+def cbp_destroy(ctx) -> None:
+    _check(lib().cbp_destroy(ctx), "cbp_destroy")
+
+
+def cbp_workspace_size(b1, b2, prm: cbp_params) -> int:
+    out = ctypes.c_size_t()
+    _check(lib().cbp_workspace_size(byref(frames(b1)), byref(frames(b2)), byref(prm), byref(out)),
+           "cbp_workspace_size")
+    return out.value
+
+
+def _batch(t: torch.Tensor) -> int:
+    return t.shape[0] if t.dim() == 4 else 1
+
+
+def cbp_estimate_kernels(ctx, b1: torch.Tensor, b2: torch.Tensor, prm: cbp_params, k1=None, k2=None,
+                         diag: bool = True, stream=None):
+    """Returns (k1, k2, diag list or None, status).  k1: (n, t1, t1) like b1."""
+    n = _batch(b1)
+    kdt = torch.float64 if prm.flags & CBP_FLAG_KERNELS_F64 else b1.dtype
+    if k1 is None:
+        k1 = torch.empty((n, prm.t1, prm.t1), dtype=kdt, device=b1.device)
+    if k2 is None:
+        k2 = torch.empty((n, prm.t2, prm.t2), dtype=kdt, device=b1.device)
+    d = (cbp_diag * n)() if diag else None
+    s = lib().cbp_estimate_kernels(ctx, byref(frames(b1)), byref(frames(b2)), byref(prm),
+                                   k1.data_ptr(), k2.data_ptr(), d, _stream_ptr(stream))
+    _check(s, "cbp_estimate_kernels")
+    return k1, k2, d, s
+
+
+def cbp_deblur_pair(ctx, b1: torch.Tensor, b2: torch.Tensor, prm: cbp_params, k1=None, k2=None,
+                    latent=None, diag: bool = True, stream=None):
+    """Returns (latent, k1, k2, diag list or None, status).  latent: (n, c, H, W) like b1.
+
+    With CBP_FLAG_HOST_IO in prm.flags every tensor is a host tensor (pinned
+    memory keeps the call asynchronous)."""
+    v1 = b1
+    while v1.dim() < 4:
+        v1 = v1.unsqueeze(0)
+    n, c, h1, w1 = v1.shape
+    hh, ww = h1 - prm.t1 + 1, w1 - prm.t1 + 1
+    pin = bool(prm.flags & CBP_FLAG_HOST_IO) and b1.device.type == "cpu"
+    if latent is None:
+        latent = torch.empty((n, c, hh, ww), dtype=b1.dtype, device=b1.device, pin_memory=pin)
+    kin = bool(prm.flags & CBP_FLAG_KERNELS_IN)
+    kdt = torch.float64 if prm.flags & CBP_FLAG_KERNELS_F64 else b1.dtype
+    if k1 is None and not kin:
+        k1 = torch.empty((n, prm.t1, prm.t1), dtype=kdt, device=b1.device, pin_memory=pin)
+    if k2 is None and not kin:
+        k2 = torch.empty((n, prm.t2, prm.t2), dtype=kdt, device=b1.device, pin_memory=pin)
+    d = (cbp_diag * n)() if diag else None
+    s = lib().cbp_deblur_pair(ctx, byref(frames(b1)), byref(frames(b2)), byref(prm),
+                              k1.data_ptr() if k1 is not None else None,
+                              k2.data_ptr() if k2 is not None else None,
+                              latent.data_ptr(), d, _stream_ptr(stream))
+    _check(s, "cbp_deblur_pair")
+    return latent, k1, k2, d, s
+
+
+def cbp_forward_blur(ctx, latent: torch.Tensor, kernels: torch.Tensor, sigma: float = 0.0,
+                     seed: int = 0, out=None, stream=None) -> torch.Tensor:
+    """Eq. 1 on the device: latent (n, c, h, w), kernels (n, t, t) float64."""
+    n, c, h, w = latent.shape
+    t = kernels.shape[-1]
+    kd = kernels.to(torch.float64).contiguous()
+    if out is None:
+        out = torch.empty((n, c, h + t - 1, w + t - 1), dtype=latent.dtype, device=latent.device)
+    s = lib().cbp_forward_blur(ctx, latent.data_ptr(), n, c, h, w,
+                               CBP_F64 if latent.dtype == torch.float64 else CBP_F32,
+                               kd.data_ptr(), t, sigma, seed, out.data_ptr(), _stream_ptr(stream))
+    _check(s, "cbp_forward_blur")
+    return out
+
+
+def cbp_synth_latent(ctx, blobs: torch.Tensor, n: int, c: int, h: int, w: int,
+                     dtype=torch.float32, floor_amp: float = 0.05, seed: int = 0, out=None,
+                     stream=None) -> torch.Tensor:
+    """Blob latent on the device; blobs (n, c, nblobs, 4) float64 rows (a, sigma, cx, cy)."""
+    bl = blobs.to(torch.float64).contiguous()
+    nb = bl.shape[-2]
+    if out is None:
+        out = torch.empty((n, c, h, w), dtype=dtype, device=bl.device)
+    s = lib().cbp_synth_latent(ctx, bl.data_ptr(), nb, n, c, h, w,
+                               CBP_F64 if dtype == torch.float64 else CBP_F32, floor_amp, seed,
+                               out.data_ptr(), _stream_ptr(stream))
+    _check(s, "cbp_synth_latent")
+    return out
+
+
+def cbp_profile(ctx, enable: bool) -> None:
+    _check(lib().cbp_profile(ctx, 1 if enable else 0), "cbp_profile")
+
+
+def cbp_stage_times(ctx) -> dict:
+    """{stage: (milliseconds, kernel launches)} accumulated since the last call."""
+    ms = (c_double * len(STAGES))()
+    nl = (c_int64 * len(STAGES))()
+    _check(lib().cbp_stage_times(ctx, ms, nl), "cbp_stage_times")
+    return {name: (ms[i], nl[i]) for i, name in enumerate(STAGES)}
+
+
+def cbp_estimate_kernels_stages(ctx, b1: torch.Tensor, b2: torch.Tensor, prm: cbp_params, stream=None):
+    """Kernel estimation plus every intermediate, as complex/real tensors:
+    p_z2/p_z1 (lists over the two frames), x_z2, x_z1, sample_diag, lifted, kernels."""
+    v1 = b1 if b1.dim() == 4 else b1.reshape((1,) * (4 - b1.dim()) + tuple(b1.shape))
+    v2 = b2 if b2.dim() == 4 else b2.reshape((1,) * (4 - b2.dim()) + tuple(b2.shape))
+    n, c = v1.shape[0], v1.shape[1]
+    m = prm.m or max(prm.t1, prm.t2)
+    s = m // 2 + 1
+    nn = prm.t1 + prm.t2
+    ct = torch.complex128 if prm.path == CBP_PATH_FP64 else torch.complex64
+    dev = b1.device
+    out = {
+        "p_z2": [torch.empty((n, c, s, v.shape[2]), dtype=ct, device=dev) for v in (v1, v2)],
+        "p_z1": [torch.empty((n, c, s, v.shape[3]), dtype=ct, device=dev) for v in (v1, v2)],
+        "x_z2": torch.empty((n, s, nn), dtype=torch.complex128, device=dev),
+        "x_z1": torch.empty((n, s, nn), dtype=torch.complex128, device=dev),
+        "sample_diag": torch.empty((n, 2, s, 4), dtype=torch.float64, device=dev),
+        "lifted": torch.empty((n, 4, m, m), dtype=torch.complex128, device=dev),
+        "kernels": torch.empty((n, prm.t1 * prm.t1 + prm.t2 * prm.t2), dtype=torch.float64, device=dev),
+    }
+    so = cbp_stage_out((c_void_p * 2)(*[t.data_ptr() for t in out["p_z2"]]),
+                       (c_void_p * 2)(*[t.data_ptr() for t in out["p_z1"]]),
+                       out["x_z2"].data_ptr(), out["x_z1"].data_ptr(), out["sample_diag"].data_ptr(),
+                       out["lifted"].data_ptr(), out["kernels"].data_ptr())
+    k1 = torch.empty((n, prm.t1, prm.t1), dtype=b1.dtype, device=dev)
+    k2 = torch.empty((n, prm.t2, prm.t2), dtype=b1.dtype, device=dev)
+    d = (cbp_diag * n)()
+    st = lib().cbp_estimate_kernels_stages(ctx, byref(frames(b1)), byref(frames(b2)), byref(prm),
+                                           k1.data_ptr(), k2.data_ptr(), d, byref(so),
+                                           _stream_ptr(stream))
+    _check(st, "cbp_estimate_kernels_stages")
+    out["k1"], out["k2"], out["diag"] = k1, k2, d
+    return out

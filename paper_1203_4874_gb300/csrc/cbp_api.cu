@@ -1,0 +1,401 @@
+// C ABI of libcbp (declared in include/cbp.h): contexts, workspaces and the
+// batched estimation / deblurring entry points.
+#include <cuda_runtime.h>
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include "cbp.h"
+#include "cbp_internal.h"
+#include "cbp_serve.h"
+
+namespace cbp {
+
+// Device memory accounting of a context (workspaces and serving slots).
+bool Ctx::reserve(size_t bytes) {
+  std::lock_guard<std::mutex> g(mem_mu);
+  if (used + bytes > budget) return false;
+  used += bytes;
+  return true;
+}
+void Ctx::release(size_t bytes) {
+  std::lock_guard<std::mutex> g(mem_mu);
+  used -= std::min(used, bytes);
+}
+
+cudaEvent_t Prof::get() {
+  if (!pool.empty()) {
+    cudaEvent_t e = pool.back();
+    pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+void Prof::begin(int, cudaStream_t st, cudaEvent_t* a) {
+  *a = get();
+  cudaEventRecord(*a, st);
+}
+void Prof::end(int stage, cudaStream_t st, cudaEvent_t a, int nkernels) {
+  cudaEvent_t b = get();
+  cudaEventRecord(b, st);
+  recs.push_back({stage, a, b});
+  launches[stage] += nkernels;
+}
+
+// Grow the synchronous-API workspace to `bytes` (stream-ordered on `st`).
+cbp_status Ctx::ensure_ws(size_t bytes, cudaStream_t st) {
+  if (bytes <= ws_size) return CBP_OK;
+  if (!reserve(bytes)) return CBP_ERR_BUDGET;
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    release(bytes);
+    return CBP_ERR_OOM;
+  }
+  if (ws) {
+    cudaFreeAsync(ws, st);
+    release(ws_size);
+  }
+  ws = (char*)p;
+  ws_size = bytes;
+  return CBP_OK;
+}
+
+// Enqueue the whole path of one plan on `st` with workspace `wsp`.
+cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
+                    const cbp_params* prm, void* k1, void* k2, void* latent, bool deblur,
+                    char* wsp, cudaStream_t st, Prof* prof, const PtrTables* tabs) {
+  cudaEvent_t ev = nullptr;
+  auto begin = [&](int stage) {
+    if (prof) prof->begin(stage, st, &ev);
+  };
+  auto end = [&](int stage, int nk) {
+    if (prof) prof->end(stage, st, ev, nk);
+  };
+  const bool host_io = prm->flags & CBP_FLAG_HOST_IO;
+  const bool kin = deblur && (prm->flags & CBP_FLAG_KERNELS_IN);
+  const int f64 = b1->dtype == CBP_F64;
+  const int kf64 = f64 || (prm->flags & CBP_FLAG_KERNELS_F64);
+  const size_t es = f64 ? 8 : 4;
+  const size_t kes = kf64 ? 8 : 4;
+  FrameDesc d1, d2;
+  void* k1d = k1;
+  void* k2d = k2;
+  void* latd = latent;
+  if (host_io) {
+    begin(CBP_STAGE_H2D);
+    const cbp_frames* bs[2] = {b1, b2};
+    for (int k = 0; k < 2; ++k) {
+      const cbp_frames* b = bs[k];
+      const int64_t rs = b->row_stride ? b->row_stride : b->w;
+      const int64_t cs = b->chan_stride ? b->chan_stride : (int64_t)b->h * rs;
+      const int64_t fs = b->frame_stride ? b->frame_stride : (int64_t)b->c * cs;
+      if (rs != b->w || cs != (int64_t)b->h * b->w || fs != (int64_t)b->c * cs)
+        return CBP_ERR_INVALID_ARG;  // host I/O takes contiguous batches
+      const size_t bytes = (size_t)b->n * b->c * b->h * b->w * es;
+      if (cudaMemcpyAsync(wsp + p.off_io_b[k], b->data, bytes, cudaMemcpyHostToDevice, st) !=
+          cudaSuccess)
+        return CBP_ERR_CUDA;
+    }
+    d1 = frame_desc(b1, wsp + p.off_io_b[0]);
+    d2 = frame_desc(b2, wsp + p.off_io_b[1]);
+    k1d = k1 ? wsp + p.off_io_k[0] : nullptr;
+    k2d = k2 ? wsp + p.off_io_k[1] : nullptr;
+    latd = wsp + p.off_io_lat;
+    if (kin) {
+      if (cudaMemcpyAsync(k1d, k1, (size_t)p.n * p.t1 * p.t1 * kes, cudaMemcpyHostToDevice, st) !=
+              cudaSuccess ||
+          cudaMemcpyAsync(k2d, k2, (size_t)p.n * p.t2 * p.t2 * kes, cudaMemcpyHostToDevice, st) !=
+              cudaSuccess)
+        return CBP_ERR_CUDA;
+    }
+    end(CBP_STAGE_H2D, 0);
+  } else {
+    d1 = frame_desc(b1, nullptr);
+    d2 = frame_desc(b2, nullptr);
+    if (tabs) {
+      d1.tab = tabs->b1;
+      d2.tab = tabs->b2;
+    }
+  }
+  cudaMemsetAsync(wsp + p.off_bad, 0, (size_t)p.n * sizeof(int), st);
+  if (kin) {
+    if (!k1d || !k2d) return CBP_ERR_INVALID_ARG;
+    begin(CBP_STAGE_SCALE_SOLVE);
+    launch_kernels_in(p, wsp, k1d, k2d, kf64, st);
+    end(CBP_STAGE_SCALE_SOLVE, 1);
+  } else {
+    begin(CBP_STAGE_EVAL);
+    launch_eval(p, d1, d2, wsp, st);
+    end(CBP_STAGE_EVAL, 2);
+    begin(CBP_STAGE_SAMPLE_SOLVE);
+    launch_sample_solve(p, wsp, st);
+    end(CBP_STAGE_SAMPLE_SOLVE, 1);
+    begin(CBP_STAGE_SCALE_SOLVE);
+    launch_scale_solve(p, wsp, k1d, k2d, kf64, st, tabs ? tabs->k1 : nullptr,
+                       tabs ? tabs->k2 : nullptr);
+    end(CBP_STAGE_SCALE_SOLVE, 1);
+  }
+  if (deblur) {
+    begin(CBP_STAGE_KERNEL_SPECTRA);
+    init_twiddles(p, wsp, st);
+    launch_kernel_spectra(p, wsp, st);
+    end(CBP_STAGE_KERNEL_SPECTRA, 3);
+    begin(CBP_STAGE_ROW_FFT);
+    launch_row_fft(p, d1, d2, wsp, st);
+    end(CBP_STAGE_ROW_FFT, 1);
+    begin(CBP_STAGE_COL_DECONV);
+    launch_col_deconv(p, wsp, st);
+    end(CBP_STAGE_COL_DECONV, 1);
+    begin(CBP_STAGE_ROW_IFFT);
+    launch_row_ifft(p, wsp, latd, f64, st, tabs ? tabs->lat : nullptr);
+    end(CBP_STAGE_ROW_IFFT, 1);
+  }
+  if (host_io) {
+    begin(CBP_STAGE_D2H);
+    if (deblur &&
+        cudaMemcpyAsync(latent, latd, (size_t)p.n * p.C * p.H * p.W * es, cudaMemcpyDeviceToHost,
+                        st) != cudaSuccess)
+      return CBP_ERR_CUDA;
+    if (!kin && k1 &&
+        cudaMemcpyAsync(k1, k1d, (size_t)p.n * p.t1 * p.t1 * kes, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess)
+      return CBP_ERR_CUDA;
+    if (!kin && k2 &&
+        cudaMemcpyAsync(k2, k2d, (size_t)p.n * p.t2 * p.t2 * kes, cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess)
+      return CBP_ERR_CUDA;
+    end(CBP_STAGE_D2H, 0);
+  }
+  if (cudaGetLastError() != cudaSuccess) return CBP_ERR_CUDA;
+  return CBP_OK;
+}
+
+}  // namespace cbp
+
+using cbp::Ctx;
+using cbp::Plan;
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+cbp_status copy_stages(const Plan& p, const char* ws, const cbp_stage_out* o, cudaStream_t st) {
+  if (!o) return CBP_OK;
+  const size_t te = p.mixed ? 8 : 16;
+  const size_t n = p.n, C = p.C, ns = p.ns;
+  struct Item { void* dst; size_t off, bytes; };
+  const Item items[] = {
+      {o->p_z2[0], p.off_pz2[0], n * C * ns * p.H1 * te},
+      {o->p_z2[1], p.off_pz2[1], n * C * ns * p.H2 * te},
+      {o->p_z1[0], p.off_pz1[0], n * C * ns * p.W1 * te},
+      {o->p_z1[1], p.off_pz1[1], n * C * ns * p.W2 * te},
+      {o->sample_diag, p.off_sdiag, n * 2 * ns * 4 * 8},
+      {o->lifted, p.off_resid, n * 4 * (size_t)p.M * p.M * 16},
+      {o->kernels, p.off_kd, n * (size_t)(p.t1 * p.t1 + p.t2 * p.t2) * 8},
+  };
+  for (const Item& it : items)
+    if (it.dst && cudaMemcpyAsync(it.dst, ws + it.off, it.bytes, cudaMemcpyDeviceToDevice, st) !=
+                      cudaSuccess)
+      return CBP_ERR_CUDA;
+  // null vectors: workspace layout [n][2][ns][nn] -> two [n][ns][nn] arrays
+  void* xs[2] = {o->x_z2, o->x_z1};
+  for (int ps = 0; ps < 2; ++ps)
+    if (xs[ps] && cudaMemcpy2DAsync(xs[ps], ns * p.nn * 16, ws + p.off_x + ps * ns * p.nn * 16,
+                                    2 * ns * p.nn * 16, ns * p.nn * 16, n,
+                                    cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      return CBP_ERR_CUDA;
+  return CBP_OK;
+}
+
+cbp_status call_path(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
+                     const cbp_params* prm, void* k1, void* k2, void* latent, cbp_diag* diag,
+                     void* stream, bool deblur, const cbp_stage_out* stages = nullptr) {
+  if (!ctx) return CBP_ERR_INVALID_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  Plan p;
+  cbp_status s = cbp::make_plan(b1, b2, prm, &p);
+  if (s != CBP_OK) return s;
+  if (deblur && !latent) return CBP_ERR_INVALID_ARG;
+  if (!deblur && (!k1 || !k2)) return CBP_ERR_INVALID_ARG;
+  if (deblur && (prm->flags & CBP_FLAG_KERNELS_IN) && (!k1 || !k2)) return CBP_ERR_INVALID_ARG;
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lk(c->api_mu);
+  s = c->ensure_ws(p.total, st);
+  if (s != CBP_OK) return s;
+  s = cbp::run_plan(p, b1, b2, prm, k1, k2, latent, deblur, c->ws, st,
+                    c->profiling ? &c->prof : nullptr);
+  if (s != CBP_OK) return s;
+  s = copy_stages(p, c->ws, stages, st);
+  if (s != CBP_OK) return s;
+  if (diag &&
+      cudaMemcpyAsync(diag, c->ws + p.off_diag, (size_t)p.n * sizeof(cbp_diag),
+                      cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return CBP_ERR_CUDA;
+  return CBP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cbp_status cbp_create(cbp_ctx** out, int device, size_t hbm_budget_bytes) {
+  if (!out) return CBP_ERR_INVALID_ARG;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+    cudaGetLastError();
+    return CBP_ERR_CUDA;
+  }
+  DeviceGuard g(device);
+  size_t free_b = 0, total_b = 0;
+  if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return CBP_ERR_CUDA;
+  Ctx* c = new (std::nothrow) Ctx();
+  if (!c) return CBP_ERR_OOM;
+  c->device = device;
+  c->budget = hbm_budget_bytes ? hbm_budget_bytes : (size_t)(0.9 * (double)free_b);
+  *out = reinterpret_cast<cbp_ctx*>(c);
+  return CBP_OK;
+}
+
+cbp_status cbp_destroy(cbp_ctx* ctx) {
+  if (!ctx) return CBP_ERR_INVALID_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  DeviceGuard g(c->device);
+  cbp::serve_shutdown(c);
+  cudaDeviceSynchronize();
+  if (c->ws) cudaFree(c->ws);
+  delete c;
+  return CBP_OK;
+}
+
+const char* cbp_status_string(cbp_status s) {
+  switch (s) {
+    case CBP_OK: return "CBP_OK";
+    case CBP_WARN_ILL_CONDITIONED: return "CBP_WARN_ILL_CONDITIONED";
+    case CBP_ERR_INVALID_ARG: return "CBP_ERR_INVALID_ARG";
+    case CBP_ERR_SIZE_MISMATCH: return "CBP_ERR_SIZE_MISMATCH";
+    case CBP_ERR_NOT_COPRIME: return "CBP_ERR_NOT_COPRIME";
+    case CBP_ERR_OOM: return "CBP_ERR_OOM";
+    case CBP_ERR_CUDA: return "CBP_ERR_CUDA";
+    case CBP_ERR_BUSY: return "CBP_ERR_BUSY";
+    case CBP_ERR_TIMEOUT: return "CBP_ERR_TIMEOUT";
+    case CBP_ERR_BUDGET: return "CBP_ERR_BUDGET";
+    case CBP_ERR_UNSUPPORTED: return "CBP_ERR_UNSUPPORTED";
+  }
+  return "CBP_UNKNOWN_STATUS";
+}
+
+cbp_status cbp_workspace_size(const cbp_frames* b1, const cbp_frames* b2,
+                              const cbp_params* params, size_t* bytes) {
+  if (!bytes) return CBP_ERR_INVALID_ARG;
+  Plan p;
+  cbp_status s = cbp::make_plan(b1, b2, params, &p);
+  if (s != CBP_OK) return s;
+  *bytes = p.total;
+  return CBP_OK;
+}
+
+cbp_status cbp_estimate_kernels(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
+                                const cbp_params* params, void* k1, void* k2, cbp_diag* diag,
+                                void* stream) {
+  try {
+    return call_path(ctx, b1, b2, params, k1, k2, nullptr, diag, stream, false);
+  } catch (...) {
+    return CBP_ERR_OOM;
+  }
+}
+
+cbp_status cbp_estimate_kernels_stages(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
+                                       const cbp_params* params, void* k1, void* k2,
+                                       cbp_diag* diag, const cbp_stage_out* out, void* stream) {
+  try {
+    if (params && (params->flags & CBP_FLAG_HOST_IO)) return CBP_ERR_INVALID_ARG;
+    return call_path(ctx, b1, b2, params, k1, k2, nullptr, diag, stream, false, out);
+  } catch (...) {
+    return CBP_ERR_OOM;
+  }
+}
+
+cbp_status cbp_deblur_pair(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
+                           const cbp_params* params, void* k1, void* k2, void* latent,
+                           cbp_diag* diag, void* stream) {
+  try {
+    return call_path(ctx, b1, b2, params, k1, k2, latent, diag, stream, true);
+  } catch (...) {
+    return CBP_ERR_OOM;
+  }
+}
+
+cbp_status cbp_forward_blur(cbp_ctx* ctx, const void* latent, int32_t n, int32_t c, int32_t h,
+                            int32_t w, cbp_dtype dtype, const double* kernel, int32_t t,
+                            double sigma, uint64_t seed, void* out, void* stream) {
+  if (!ctx || !latent || !kernel || !out || n < 1 || c < 1 || h < 1 || w < 1 || t < 1 ||
+      t > 64 || !(sigma >= 0.0) || (dtype != CBP_F32 && dtype != CBP_F64))
+    return CBP_ERR_INVALID_ARG;
+  Ctx* cx = reinterpret_cast<Ctx*>(ctx);
+  DeviceGuard g(cx->device);
+  cbp::launch_forward_blur(latent, n, c, h, w, dtype == CBP_F64, kernel, t, sigma, seed, out,
+                           (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? CBP_OK : CBP_ERR_CUDA;
+}
+
+cbp_status cbp_synth_latent(cbp_ctx* ctx, const double* blobs, int32_t nblobs, int32_t n,
+                            int32_t c, int32_t h, int32_t w, cbp_dtype dtype, double floor_amp,
+                            uint64_t seed, void* out, void* stream) {
+  if (!ctx || !blobs || !out || nblobs < 0 || n < 1 || c < 1 || h < 1 || w < 1 ||
+      (dtype != CBP_F32 && dtype != CBP_F64))
+    return CBP_ERR_INVALID_ARG;
+  Ctx* cx = reinterpret_cast<Ctx*>(ctx);
+  DeviceGuard g(cx->device);
+  cbp::launch_synth_latent(blobs, nblobs, n, c, h, w, dtype == CBP_F64, floor_amp, seed, out,
+                           (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? CBP_OK : CBP_ERR_CUDA;
+}
+
+cbp_status cbp_profile(cbp_ctx* ctx, int32_t enable) {
+  if (!ctx) return CBP_ERR_INVALID_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  std::lock_guard<std::mutex> lk(c->api_mu);
+  c->profiling = enable != 0;
+  return CBP_OK;
+}
+
+cbp_status cbp_stage_times(cbp_ctx* ctx, double* ms, int64_t* launches) {
+  if (!ctx) return CBP_ERR_INVALID_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  DeviceGuard g(c->device);
+  std::lock_guard<std::mutex> lk(c->api_mu);
+  cbp::Prof& P = c->prof;
+  cbp_status st = CBP_OK;
+  for (auto& r : P.recs) {
+    float t = 0.f;
+    if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&t, r.a, r.b) != cudaSuccess)
+      st = CBP_ERR_CUDA;
+    if (ms) ms[r.stage] += (double)t;
+    P.pool.push_back(r.a);
+    P.pool.push_back(r.b);
+  }
+  P.recs.clear();
+  for (int i = 0; i < CBP_NUM_STAGES; ++i) {
+    if (launches) launches[i] += P.launches[i];
+    P.launches[i] = 0;
+  }
+  return st;
+}
+
+}  // extern "C"

@@ -1,0 +1,66 @@
+// Shared device helpers of libcbp: complex arithmetic, reductions, launch checks.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <math.h>
+
+namespace cbp {
+
+template <typename T> struct alignas(2 * sizeof(T)) cpx { T re, im; };
+using cf = cpx<float>;
+using cd = cpx<double>;
+
+template <typename T> __host__ __device__ __forceinline__ cpx<T> mk(T r, T i) { return {r, i}; }
+template <typename T> __host__ __device__ __forceinline__ cpx<T> operator+(cpx<T> a, cpx<T> b) { return {a.re + b.re, a.im + b.im}; }
+template <typename T> __host__ __device__ __forceinline__ cpx<T> operator-(cpx<T> a, cpx<T> b) { return {a.re - b.re, a.im - b.im}; }
+template <typename T> __host__ __device__ __forceinline__ cpx<T> operator*(cpx<T> a, cpx<T> b) {
+  return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+template <typename T> __host__ __device__ __forceinline__ cpx<T> operator*(T s, cpx<T> a) { return {s * a.re, s * a.im}; }
+template <typename T> __host__ __device__ __forceinline__ cpx<T> conj(cpx<T> a) { return {a.re, -a.im}; }
+template <typename T> __host__ __device__ __forceinline__ T abs2(cpx<T> a) { return a.re * a.re + a.im * a.im; }
+// conj(a) * b
+template <typename T> __host__ __device__ __forceinline__ cpx<T> cmulc(cpx<T> a, cpx<T> b) {
+  return {a.re * b.re + a.im * b.im, a.re * b.im - a.im * b.re};
+}
+// acc += a * b
+template <typename T> __host__ __device__ __forceinline__ void cfma(cpx<T>& acc, cpx<T> a, cpx<T> b) {
+  acc.re = fma(a.re, b.re, fma(-a.im, b.im, acc.re));
+  acc.im = fma(a.re, b.im, fma(a.im, b.re, acc.im));
+}
+// acc += conj(a) * b
+template <typename T> __host__ __device__ __forceinline__ void cfmac(cpx<T>& acc, cpx<T> a, cpx<T> b) {
+  acc.re = fma(a.re, b.re, fma(a.im, b.im, acc.re));
+  acc.im = fma(a.re, b.im, fma(-a.im, b.re, acc.im));
+}
+template <typename D, typename S> __host__ __device__ __forceinline__ cpx<D> cvt(cpx<S> a) {
+  return {(D)a.re, (D)a.im};
+}
+
+template <typename T> __device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+template <typename T> __device__ __forceinline__ T warp_max(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+template <typename T> __device__ __forceinline__ T ld_elem(const void* p, int64_t i) {
+  return (T)(((const T*)p)[i]);
+}
+
+// Base address of frame f of a batch: from the table if present, else strided.
+template <class FD> __device__ __forceinline__ const void* frame_base(const FD& fr, int f) {
+  if (fr.tab) return (const void*)fr.tab[f];
+  return (const char*)fr.data + (size_t)f * (size_t)fr.fs * (fr.f64 ? 8u : 4u);
+}
+
+// Load one element of a frame batch stored as float or double, converted to T.
+template <typename T> __device__ __forceinline__ T ld_frame(const void* p, int64_t i, int is_f64) {
+  return is_f64 ? (T)__ldg(((const double*)p) + i) : (T)__ldg(((const float*)p) + i);
+}
+
+}  // namespace cbp

@@ -1,0 +1,134 @@
+// Forward model of Eq. 1 on the device (the camera side of Section 3):
+// B = L (x) K + N, full 2D convolution per channel plus Gaussian noise, and a
+// blob-latent synthesiser.  Random numbers come from Philox-4x32-10 (Salmon,
+// Moraes, Dror, Shaw, "Parallel random numbers: as easy as 1, 2, 3", SC 2011):
+// counter = (element index lo, element index hi, stream, 0), key = seed.
+#include "cbp_common.cuh"
+#include "cbp_internal.h"
+
+namespace cbp {
+namespace {
+
+struct U4 { uint32_t x, y, z, w; };
+
+__device__ __forceinline__ U4 philox_round(U4 c, uint32_t k0, uint32_t k1) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
+  uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
+  return {hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
+}
+
+__device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+#pragma unroll
+  for (int i = 0; i < 10; ++i) {
+    c = philox_round(c, k0, k1);
+    k0 += W0;
+    k1 += W1;
+  }
+  return c;
+}
+
+// Uniform in (0, 1] from 32 bits.
+__device__ __forceinline__ double u01(uint32_t v) { return ((double)v + 1.0) * 2.3283064365386963e-10; }
+
+// Standard normal number `idx` of stream `stream` (Box-Muller on one Philox block).
+__device__ __forceinline__ double normal_at(uint64_t seed, uint64_t idx, uint32_t stream) {
+  U4 c = {(uint32_t)idx, (uint32_t)(idx >> 32), stream, 0u};
+  U4 r = philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const double u1 = u01(r.x), u2 = u01(r.y);
+  return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
+}
+
+__device__ __forceinline__ double uniform_at(uint64_t seed, uint64_t idx, uint32_t stream) {
+  U4 c = {(uint32_t)idx, (uint32_t)(idx >> 32), stream, 0u};
+  U4 r = philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  return u01(r.x);
+}
+
+constexpr int kTile = 32;
+
+// out[f][ch][r][c] = sum_{p,q} L[r-p][c-q] K[f][p][q] (+ noise), r < h+t-1, c < w+t-1.
+template <typename T>
+__global__ void __launch_bounds__(kTile * 8)
+k_forward_blur(const T* lat, int c, int h, int w, const double* kern, int t, double sigma,
+               uint64_t seed, T* out) {
+  extern __shared__ __align__(16) char smem[];
+  const int hb = h + t - 1, wb = w + t - 1;
+  const int fc = blockIdx.z, f = fc / c;
+  const int r0 = blockIdx.y * kTile, c0 = blockIdx.x * kTile;
+  const int th = kTile + t - 1;
+  double* K = (double*)smem;                 // t*t
+  T* tile = (T*)(smem + ((t * t * sizeof(double) + 15) & ~size_t(15)));
+  for (int i = threadIdx.x; i < t * t; i += blockDim.x) K[i] = kern[(int64_t)f * t * t + i];
+  const T* L = lat + (int64_t)fc * h * w;
+  // tile[y][x] = L[r0 - (t-1) + y][c0 - (t-1) + x]
+  for (int i = threadIdx.x; i < th * th; i += blockDim.x) {
+    const int y = i / th, x = i % th;
+    const int ly = r0 - (t - 1) + y, lx = c0 - (t - 1) + x;
+    tile[i] = (ly >= 0 && ly < h && lx >= 0 && lx < w) ? L[(int64_t)ly * w + lx] : (T)0;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x % kTile, ty0 = threadIdx.x / kTile;
+  for (int ty = ty0; ty < kTile; ty += blockDim.x / kTile) {
+    const int r = r0 + ty, col = c0 + tx;
+    if (r >= hb || col >= wb) continue;
+    double acc = 0;
+    for (int p = 0; p < t; ++p)
+      for (int q = 0; q < t; ++q)
+        acc += K[p * t + q] * (double)tile[(ty + t - 1 - p) * th + (tx + t - 1 - q)];
+    const int64_t oi = ((int64_t)fc * hb + r) * wb + col;
+    if (sigma > 0) acc += sigma * normal_at(seed, (uint64_t)oi, 1u);
+    out[oi] = (T)acc;
+  }
+}
+
+// Blob latent: L = sum_k a_k exp(-((x-cx)^2 + (y-cy)^2) / (2 s^2)) + U[0, floor].
+template <typename T>
+__global__ void k_synth_latent(const double* blobs, int nblobs, int c, int h, int w,
+                               double floor_amp, uint64_t seed, T* out) {
+  const int fc = blockIdx.z;
+  const double* B = blobs + (int64_t)fc * nblobs * 4;
+  const int y = blockIdx.y, x = blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= w) return;
+  double v = 0;
+  for (int k = 0; k < nblobs; ++k) {
+    const double a = B[4 * k], s = B[4 * k + 1], cx = B[4 * k + 2], cy = B[4 * k + 3];
+    const double dx = x - cx, dy = y - cy;
+    v += a * exp(-(dx * dx + dy * dy) / (2.0 * s * s));
+  }
+  const int64_t oi = ((int64_t)fc * h + y) * w + x;
+  v += floor_amp * uniform_at(seed, (uint64_t)oi, 2u);
+  out[oi] = (T)v;
+}
+
+}  // namespace
+
+void launch_forward_blur(const void* latent, int n, int c, int h, int w, int f64,
+                         const double* kernel, int t, double sigma, uint64_t seed, void* out,
+                         cudaStream_t st) {
+  const int hb = h + t - 1, wb = w + t - 1;
+  dim3 g((wb + kTile - 1) / kTile, (hb + kTile - 1) / kTile, n * c);
+  const int th = kTile + t - 1;
+  const size_t sm = ((t * t * sizeof(double) + 15) & ~size_t(15)) + (size_t)th * th * (f64 ? 8 : 4);
+  if (f64) {
+    cudaFuncSetAttribute(k_forward_blur<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_forward_blur<double><<<g, kTile * 8, sm, st>>>((const double*)latent, c, h, w, kernel, t,
+                                                      sigma, seed, (double*)out);
+  } else {
+    cudaFuncSetAttribute(k_forward_blur<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_forward_blur<float><<<g, kTile * 8, sm, st>>>((const float*)latent, c, h, w, kernel, t,
+                                                     sigma, seed, (float*)out);
+  }
+}
+
+void launch_synth_latent(const double* blobs, int nblobs, int n, int c, int h, int w, int f64,
+                         double floor_amp, uint64_t seed, void* out, cudaStream_t st) {
+  dim3 g((w + 127) / 128, h, n * c);
+  if (f64)
+    k_synth_latent<double><<<g, 128, 0, st>>>(blobs, nblobs, c, h, w, floor_amp, seed, (double*)out);
+  else
+    k_synth_latent<float><<<g, 128, 0, st>>>(blobs, nblobs, c, h, w, floor_amp, seed, (float*)out);
+}
+
+}  // namespace cbp

@@ -1,0 +1,108 @@
+// Internal (non-ABI) declarations shared by the libcbp translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+#include "cbp.h"
+
+namespace cbp {
+
+constexpr int kMaxN = 64;      // t1 + t2 (per-sample system width)
+constexpr int kMaxM = 32;      // samples per direction (scale system is 2M wide)
+constexpr int kMaxRadixStages = 24;
+
+// One frame batch as the kernels see it.
+struct FrameDesc {
+  const void* data;
+  const uint64_t* tab;         // optional device table of per-frame base addresses
+  int n, c, h, w;
+  int f64;                     // 1: double elements, 0: float
+  int64_t rs, cs, fs;          // row / channel / frame strides in elements
+};
+
+// Optional device tables of per-pair addresses (serving batches gather
+// independent requests without copies): frames, kernels and latents.
+struct PtrTables {
+  const uint64_t* b1 = nullptr;
+  const uint64_t* b2 = nullptr;
+  const uint64_t* k1 = nullptr;
+  const uint64_t* k2 = nullptr;
+  const uint64_t* lat = nullptr;
+};
+
+// Mixed-radix FFT plan: N = prod(radix[0..nst)), radices in {2,3,4,5,7,8}.
+struct FftPlan {
+  int n;
+  int nst;
+  int radix[kMaxRadixStages];
+};
+
+// Everything one batched call needs: shapes, precisions, workspace layout.
+struct Plan {
+  int n, C;
+  int H1, W1, H2, W2;          // blurred frame sizes
+  int H, W;                    // latent size
+  int t1, t2, M, ns, nn;       // ns = M/2 + 1 solved samples per direction; nn = t1 + t2
+  int Ph, Pw, Pw2;             // FFT grid; Pw2 = Pw/2 + 1 stored spectrum columns
+  int mixed;                   // estimation path: 0 FP64, 1 mixed
+  int fft_f64;                 // deconvolution arithmetic in double
+  int single_kernel;           // deconvolve B1 by K1 only
+  int pw_half;                 // Pw even: real row FFTs via half-length complex FFTs
+  double eps;
+  FftPlan fp_h, fp_w, fp_w2;   // plans of Ph, Pw, Pw/2
+  // workspace layout (byte offsets into one device allocation)
+  size_t off_pz2[2], off_pz1[2];   // cpx<T_eval> [n][C][ns][len]
+  size_t off_dcz2[2], off_dcz1[2]; // double [n][C][len] (mixed path: z = 1 sample)
+  size_t off_x;                    // cd [n][2][ns][nn]
+  size_t off_sdiag;                // double [n][2][ns][4]
+  size_t off_resid;                // cd [n][2][ns][C][Lmax] (FP64 path residual scratch)
+  int Lmax;
+  size_t off_kd;                   // double [n][t1*t1 + t2*t2]
+  size_t off_bad;                  // int [n] non-finite input flags
+  size_t off_diag;                 // cbp_diag [n]
+  size_t off_tw_h, off_tw_w;       // cpx<T_fft> twiddles exp(-2 pi i k / P), k < P
+  size_t off_khat;                 // cpx<T_fft> [n][2][Ph][Pw2]
+  size_t off_spec[2];              // cpx<T_fft> [n][C][H_Bk][Pw2]
+  size_t off_ihat;                 // cpx<T_fft> [n][C][H][Pw2]
+  size_t off_io_b[2], off_io_k[2], off_io_lat; // device staging for host I/O
+  size_t total;
+};
+
+// ---- planning (cbp_plan.cpp) ----
+int next_7_smooth(int n);
+bool make_fft_plan(int n, FftPlan* p);
+cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_params* prm,
+                     Plan* plan);
+FrameDesc frame_desc(const cbp_frames* f, const void* data_override);
+
+// ---- launchers (one per .cu file) ----
+// A1: sample polynomials (cbp_eval.cu)
+void launch_eval(const Plan& p, const FrameDesc& b1, const FrameDesc& b2, char* ws,
+                 cudaStream_t st);
+// A2 + A3: per-sample Gram and null vector (cbp_solve.cu)
+void launch_sample_solve(const Plan& p, char* ws, cudaStream_t st);
+// A4 + A5: lift, scale fix, kernels (cbp_solve.cu)
+void launch_scale_solve(const Plan& p, char* ws, void* k1_out, void* k2_out, int out_f64,
+                        cudaStream_t st, const uint64_t* k1_tab = nullptr,
+                        const uint64_t* k2_tab = nullptr);
+// load caller kernels into the internal double buffer (CBP_FLAG_KERNELS_IN)
+void launch_kernels_in(const Plan& p, char* ws, const void* k1, const void* k2, int in_f64,
+                       cudaStream_t st);
+// A6: deconvolution (cbp_fft.cu)
+void init_twiddles(const Plan& p, char* ws, cudaStream_t st);
+void launch_kernel_spectra(const Plan& p, char* ws, cudaStream_t st);
+void launch_row_fft(const Plan& p, const FrameDesc& b1, const FrameDesc& b2, char* ws,
+                    cudaStream_t st);
+void launch_col_deconv(const Plan& p, char* ws, cudaStream_t st);
+void launch_row_ifft(const Plan& p, char* ws, void* latent, int out_f64, cudaStream_t st,
+                     const uint64_t* lat_tab = nullptr);
+// Eq. 1 forward model (cbp_forward.cu)
+void launch_forward_blur(const void* latent, int n, int c, int h, int w, int f64,
+                         const double* kernel, int t, double sigma, uint64_t seed, void* out,
+                         cudaStream_t st);
+void launch_synth_latent(const double* blobs, int nblobs, int n, int c, int h, int w, int f64,
+                         double floor_amp, uint64_t seed, void* out, cudaStream_t st);
+size_t sample_solve_smem(int nn);
+size_t scale_solve_smem(int M);
+
+}  // namespace cbp

@@ -1,0 +1,166 @@
+// Host-side planning: argument validation, FFT factorisation and the layout of
+// the per-call device workspace.
+#include <algorithm>
+#include <cmath>
+#include "cbp_common.cuh"
+#include "cbp_internal.h"
+
+namespace cbp {
+
+int next_7_smooth(int n) {
+  for (int k = std::max(n, 1);; ++k) {
+    int r = k;
+    for (int p : {2, 3, 5, 7})
+      while (r % p == 0) r /= p;
+    if (r == 1) return k;
+  }
+}
+
+bool make_fft_plan(int n, FftPlan* p) {
+  p->n = n;
+  p->nst = 0;
+  int r = n;
+  while (r > 1) {
+    int R = 0;
+    if (r % 4 == 0) R = 4;
+    else if (r % 2 == 0) R = 2;
+    else if (r % 3 == 0) R = 3;
+    else if (r % 5 == 0) R = 5;
+    else if (r % 7 == 0) R = 7;
+    else return false;
+    if (p->nst >= kMaxRadixStages) return false;
+    p->radix[p->nst++] = R;
+    r /= R;
+  }
+  return true;
+}
+
+static bool valid_frames(const cbp_frames* f) {
+  if (!f || !f->data || f->n < 1 || f->c < 1 || f->h < 1 || f->w < 1) return false;
+  if (f->dtype != CBP_F32 && f->dtype != CBP_F64) return false;
+  const int64_t rs = f->row_stride ? f->row_stride : f->w;
+  const int64_t cs = f->chan_stride ? f->chan_stride : (int64_t)f->h * rs;
+  const int64_t fs = f->frame_stride ? f->frame_stride : (int64_t)f->c * cs;
+  if (rs < f->w || cs < (int64_t)(f->h - 1) * rs + f->w) return false;
+  if (f->n > 1 && fs < (int64_t)(f->c - 1) * cs + (int64_t)(f->h - 1) * rs + f->w) return false;
+  return true;
+}
+
+FrameDesc frame_desc(const cbp_frames* f, const void* data_override) {
+  FrameDesc d;
+  d.data = data_override ? data_override : f->data;
+  d.tab = nullptr;
+  d.n = f->n;
+  d.c = f->c;
+  d.h = f->h;
+  d.w = f->w;
+  d.f64 = f->dtype == CBP_F64;
+  d.rs = f->row_stride ? f->row_stride : f->w;
+  d.cs = f->chan_stride ? f->chan_stride : (int64_t)f->h * d.rs;
+  d.fs = f->frame_stride ? f->frame_stride : (int64_t)f->c * d.cs;
+  return d;
+}
+
+static bool is_7_smooth(int n) { return n >= 1 && next_7_smooth(n) == n; }
+
+static size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_params* prm,
+                     Plan* P) {
+  if (!prm || !valid_frames(b1) || !valid_frames(b2)) return CBP_ERR_INVALID_ARG;
+  if (b1->n != b2->n || b1->c != b2->c || b1->dtype != b2->dtype) return CBP_ERR_INVALID_ARG;
+  if (prm->path != CBP_PATH_FP64 && prm->path != CBP_PATH_MIXED && prm->path != CBP_PATH_LEARNED)
+    return CBP_ERR_INVALID_ARG;
+  if (!(prm->eps >= 0.0) || !std::isfinite(prm->eps)) return CBP_ERR_INVALID_ARG;
+  const int t1 = prm->t1, t2 = prm->t2;
+  if (t1 < 1 || t2 < 1) return CBP_ERR_INVALID_ARG;
+  if (t1 + t2 > kMaxN) return CBP_ERR_UNSUPPORTED;
+  Plan p = {};
+  p.n = b1->n;
+  p.C = b1->c;
+  p.H1 = b1->h;
+  p.W1 = b1->w;
+  p.H2 = b2->h;
+  p.W2 = b2->w;
+  p.t1 = t1;
+  p.t2 = t2;
+  p.H = p.H1 - t1 + 1;
+  p.W = p.W1 - t1 + 1;
+  if (p.H < 1 || p.W < 1) return CBP_ERR_SIZE_MISMATCH;
+  if (p.H2 != p.H + t2 - 1 || p.W2 != p.W + t2 - 1) return CBP_ERR_SIZE_MISMATCH;
+  p.M = prm->m ? prm->m : std::max(t1, t2);
+  if (p.M < std::max(t1, t2)) return CBP_ERR_INVALID_ARG;
+  if (p.M > kMaxM) return CBP_ERR_UNSUPPORTED;
+  p.ns = p.M / 2 + 1;
+  p.nn = t1 + t2;
+  const int hmax = std::max(p.H1, p.H2), wmax = std::max(p.W1, p.W2);
+  p.Ph = prm->pad_h ? prm->pad_h : next_7_smooth(hmax);
+  p.Pw = prm->pad_w ? prm->pad_w : next_7_smooth(wmax);
+  if (p.Ph < hmax || p.Pw < wmax || !is_7_smooth(p.Ph) || !is_7_smooth(p.Pw))
+    return CBP_ERR_INVALID_ARG;
+  p.Pw2 = p.Pw / 2 + 1;
+  p.pw_half = (p.Pw % 2 == 0) ? 1 : 0;
+  p.mixed = prm->path != CBP_PATH_FP64;
+  const int frame_f64 = b1->dtype == CBP_F64;
+  p.fft_f64 = (frame_f64 && !p.mixed) ? 1 : 0;
+  p.single_kernel = (prm->flags & CBP_FLAG_SINGLE_KERNEL) ? 1 : 0;
+  p.eps = prm->eps;
+  if (!make_fft_plan(p.Ph, &p.fp_h) || !make_fft_plan(p.Pw, &p.fp_w)) return CBP_ERR_INVALID_ARG;
+  if (p.pw_half && !make_fft_plan(p.Pw / 2, &p.fp_w2)) return CBP_ERR_INVALID_ARG;
+  // shared-memory limits of the kernels
+  const size_t smem_max = 227 * 1024;
+  const size_t ce = p.fft_f64 ? 16 : 8;
+  const size_t cw = p.fft_f64 ? 2 : 4;
+  if (2 * ce * (p.pw_half ? p.Pw / 2 : p.Pw) > smem_max) return CBP_ERR_UNSUPPORTED;
+  if (3 * ce * cw * p.Ph > smem_max) return CBP_ERR_UNSUPPORTED;
+  if (sample_solve_smem(p.nn) > smem_max || scale_solve_smem(p.M) > smem_max)
+    return CBP_ERR_UNSUPPORTED;
+
+  // workspace layout
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += align_up(bytes);
+    return o;
+  };
+  const size_t n = p.n, C = p.C, ns = p.ns;
+  const size_t te = p.mixed ? 8 : 16;  // sizeof(cpx<T_eval>)
+  p.off_pz2[0] = take(n * C * ns * p.H1 * te);
+  p.off_pz2[1] = take(n * C * ns * p.H2 * te);
+  p.off_pz1[0] = take(n * C * ns * p.W1 * te);
+  p.off_pz1[1] = take(n * C * ns * p.W2 * te);
+  if (p.mixed) {
+    p.off_dcz2[0] = take(n * C * p.H1 * 8);
+    p.off_dcz2[1] = take(n * C * p.H2 * 8);
+    p.off_dcz1[0] = take(n * C * p.W1 * 8);
+    p.off_dcz1[1] = take(n * C * p.W2 * 8);
+  }
+  p.off_x = take(n * 2 * ns * p.nn * 16);
+  p.off_sdiag = take(n * 2 * ns * 4 * 8);
+  p.Lmax = std::max(p.H1, p.W1) + t2 - 1;
+  const size_t resid = p.mixed ? 0 : n * 2 * ns * C * (size_t)p.Lmax * 16;
+  const size_t abytes = n * 4 * (size_t)p.M * p.M * 16;
+  p.off_resid = take(std::max(resid, abytes));
+  p.off_kd = take(n * (size_t)(t1 * t1 + t2 * t2) * 8);
+  p.off_bad = take(n * 4);
+  p.off_diag = take(n * sizeof(cbp_diag));
+  p.off_tw_h = take(p.Ph * ce);
+  p.off_tw_w = take(p.Pw * ce);
+  p.off_khat = take(n * 2 * (size_t)p.Ph * p.Pw2 * ce);
+  p.off_spec[0] = take(n * C * (size_t)p.H1 * p.Pw2 * ce);
+  p.off_spec[1] = take(n * C * (size_t)p.H2 * p.Pw2 * ce);
+  p.off_ihat = take(n * C * (size_t)p.H * p.Pw2 * ce);
+  if (prm->flags & CBP_FLAG_HOST_IO) {
+    const size_t es = frame_f64 ? 8 : 4;
+    p.off_io_b[0] = take(n * C * (size_t)p.H1 * p.W1 * es);
+    p.off_io_b[1] = take(n * C * (size_t)p.H2 * p.W2 * es);
+    p.off_io_k[0] = take(n * (size_t)t1 * t1 * 8);
+    p.off_io_k[1] = take(n * (size_t)t2 * t2 * 8);
+    p.off_io_lat = take(n * C * (size_t)p.H * p.W * es);
+  }
+  p.total = off;
+  *P = p;
+  return CBP_OK;
+}
+
+}  // namespace cbp

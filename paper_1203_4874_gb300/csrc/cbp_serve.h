@@ -1,0 +1,48 @@
+// Context object and serving-engine interface (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <mutex>
+#include <vector>
+#include "cbp.h"
+#include "cbp_internal.h"
+
+namespace cbp {
+
+struct ServeState;  // defined in cbp_serve.cu
+
+// Stage timing: events recorded around each stage of the synchronous API.
+struct Prof {
+  struct Rec { int stage; cudaEvent_t a, b; };
+  std::vector<Rec> recs;
+  std::vector<cudaEvent_t> pool;
+  int64_t launches[CBP_NUM_STAGES] = {};
+  cudaEvent_t get();
+  void begin(int stage, cudaStream_t st, cudaEvent_t* a);
+  void end(int stage, cudaStream_t st, cudaEvent_t a, int nkernels);
+};
+
+struct Ctx {
+  int device = 0;
+  size_t budget = 0;          // bytes of device memory the context may hold
+  size_t used = 0;            // bytes held now
+  std::mutex mem_mu;          // guards used
+  std::mutex api_mu;          // serialises the synchronous API's workspace use
+  char* ws = nullptr;         // synchronous-API workspace
+  size_t ws_size = 0;
+  ServeState* serve = nullptr;
+  bool profiling = false;
+  Prof prof;
+  std::mutex serve_mu;        // guards creation of `serve`
+
+  bool reserve(size_t bytes);
+  void release(size_t bytes);
+  cbp_status ensure_ws(size_t bytes, cudaStream_t st);
+};
+
+cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
+                    const cbp_params* prm, void* k1, void* k2, void* latent, bool deblur,
+                    char* wsp, cudaStream_t st, Prof* prof = nullptr,
+                    const PtrTables* tabs = nullptr);
+void serve_shutdown(Ctx* c);
+
+}  // namespace cbp

@@ -1,0 +1,927 @@
+// A2-A5: per-sample cofactor solve, scale fix between the two evaluation
+// orders, and the spatial kernels (Eq. 4; Sections 4-5).
+//
+// Per sample (one CTA each): the 1D cofactor pair x = [u; v] (u ~ k1, v ~ k2
+// at that sample) spans the null space of the Sylvester matrix
+// S = [-C_t1(b2) | C_t2(b1)], channels' rows stacked, since b1 k2 - b2 k1 = 0
+// (Eq. 4).  The paper factors Bezout matrices by a CPU SVD (Section 5); here
+// the normal matrix G = S^H S is formed on the device from correlations --
+// its blocks are Toeplitz, (C_t(a)^H C_s(b))[p][q] = rho_ab(p - q) with
+// rho_ab(d) = sum_m conj(a[m]) b[m + d] -- and its smallest eigenvector is
+// found by:
+//   1. cyclic parallel Jacobi in single precision (all eigenpairs);
+//   2. samples whose two smallest eigenvalues the single-precision solve
+//      resolves ("easy"): double-precision Newton steps on G with the
+//      single-precision eigenbasis as preconditioner;
+//      otherwise ("hard", e.g. the z = 1 sample, whose lower spectrum is a
+//      cluster of noise-level eigenvalues, or noise-free input): the same
+//      Jacobi in double precision;
+//   3. FP64 path only: one more Newton step whose residual S^H S x is computed
+//      from S itself (convolutions), which removes the squared conditioning of
+//      the normal matrix.
+// Only samples s <= M/2 are solved; sample M - s is the conjugate.
+//
+// Per pair (one CTA): lift the cofactors to the two M x M estimates of the
+// kernels' 2D DFT, solve the least-squares scale system (same eigen-solver on
+// its 2M x 2M normal matrix, exact residual in the FP64 path), average,
+// normalise to unit kernel sum, inverse M x M DFT (Section 5).
+#include "cbp_common.cuh"
+#include "cbp_internal.h"
+
+namespace cbp {
+namespace {
+
+constexpr int kSolveThreads = 256;
+constexpr int kMaxSweeps = 40;
+
+// ------------------------------------------------------------ block helpers
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  double t = 0;
+  const int nw = blockDim.x >> 5;
+  for (int i = 0; i < nw; ++i) t += red[i];
+  return t;
+}
+
+// Shared-memory work area of the eigen-solver for an N x N Hermitian matrix.
+struct EigSmem {
+  cd* G;       // N*N   double-precision matrix (input, preserved)
+  cd* L;       // NP*NP double-precision working copy (hard samples)
+  cf* A;       // NP*NP single-precision working copy -> eigenvalues on the diagonal
+  cf* V;       // NP*NP single-precision eigenvectors; with A, the double
+               //       eigenvectors of hard samples
+  cd* x;       // N
+  cd* y;       // N
+  cd* r;       // N
+  cd* z;       // N
+  double* lam; // N eigenvalues of the single-precision solve (unscaled)
+  double* rc;  // NP/2 rotation cosines (float or double view)
+  cd* rs;      // NP/2 rotation s * phase (float or double view)
+  int* rp;     // NP/2
+  int* rq;     // NP/2
+  double* red; // 32 (reduction scratch)
+  int* flag;   // 4 ints
+  double* sc;  // 8 doubles (scalars)
+};
+
+struct EigResult {
+  double lam_max;   // largest eigenvalue
+  double lam_2;     // second smallest eigenvalue
+  double theta;     // Rayleigh quotient of the returned vector (~ smallest)
+  int hard;         // 1 if solved by the double-precision Jacobi
+};
+
+__device__ __forceinline__ int np_of(int n) { return (n + 1) & ~1; }
+
+__device__ __forceinline__ void jacobi_pair(int round, int k, int np, int* p, int* q) {
+  int a, b;
+  if (k == 0) {
+    a = np - 1;
+    b = round;
+  } else {
+    a = (round + k) % (np - 1);
+    b = (round - k + (np - 1)) % (np - 1);
+  }
+  *p = a < b ? a : b;
+  *q = a < b ? b : a;
+}
+
+// Cyclic Jacobi (round-robin parallel ordering) on the Hermitian matrix A
+// (n x n inside an ld x ld array, ld even >= n).  On exit A holds the
+// eigenvalues on its diagonal and V the eigenvectors (columns).  A pair is
+// rotated while |a_pq| exceeds both tol_rel sqrt(|a_pp a_qq|) and
+// tol_abs max|a_ii| (the rounding floor of the precision).  Bounded sweeps.
+template <typename T>
+__device__ void jacobi(cpx<T>* A, cpx<T>* V, int n, int ld, EigSmem& S, T tol_rel, T tol_abs) {
+  const int half = ld / 2;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  T* rc = (T*)S.rc;
+  cpx<T>* rs = (cpx<T>*)S.rs;
+  for (int i = tid; i < ld * ld; i += nth) {
+    int r = i / ld, c = i % ld;
+    V[i] = mk<T>(r == c ? (T)1 : (T)0, (T)0);
+    if (r >= n || c >= n) A[i] = mk<T>((T)0, (T)0);
+  }
+  __syncthreads();
+  T amax = 0;
+  for (int i = 0; i < n; ++i) amax = max(amax, (T)fabs(A[i * ld + i].re));
+  const T abs_tol = tol_abs * amax;
+  for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
+    if (tid == 0) S.flag[0] = 0;
+    __syncthreads();
+    for (int round = 0; round < ld - 1; ++round) {
+      for (int k = tid; k < half; k += nth) {
+        int p, q;
+        jacobi_pair(round, k, ld, &p, &q);
+        T c = 1;
+        cpx<T> sp = mk<T>((T)0, (T)0);
+        if (q < n) {
+          cpx<T> apq = A[p * ld + q];
+          T app = A[p * ld + p].re, aqq = A[q * ld + q].re;
+          T mag = sqrt(abs2(apq));
+          if (mag > abs_tol && mag > tol_rel * sqrt(fabs(app)) * sqrt(fabs(aqq))) {
+            T tau = (aqq - app) / ((T)2 * mag);
+            T t = (tau >= (T)0 ? (T)1 : (T)-1) / (fabs(tau) + sqrt((T)1 + tau * tau));
+            c = (T)1 / sqrt((T)1 + t * t);
+            T sn = t * c;
+            sp = mk<T>(sn * apq.re / mag, sn * apq.im / mag);
+            S.flag[0] = 1;
+          }
+        }
+        S.rp[k] = p;
+        S.rq[k] = q;
+        rc[k] = c;
+        rs[k] = sp;
+      }
+      __syncthreads();
+      // rows p, q:  A <- J^H A
+      for (int idx = tid; idx < half * n; idx += nth) {
+        int k = idx / n, j = idx % n;
+        cpx<T> sp = rs[k];
+        if (sp.re == (T)0 && sp.im == (T)0) continue;
+        int p = S.rp[k], q = S.rq[k];
+        T c = rc[k];
+        cpx<T> apj = A[p * ld + j], aqj = A[q * ld + j];
+        A[p * ld + j] = c * apj - sp * aqj;
+        A[q * ld + j] = conj(sp) * apj + c * aqj;
+      }
+      __syncthreads();
+      // columns p, q:  A <- A J,  V <- V J
+      for (int idx = tid; idx < half * n; idx += nth) {
+        int k = idx / n, i = idx % n;
+        cpx<T> sp = rs[k];
+        if (sp.re == (T)0 && sp.im == (T)0) continue;
+        int p = S.rp[k], q = S.rq[k];
+        T c = rc[k];
+        cpx<T> aip = A[i * ld + p], aiq = A[i * ld + q];
+        A[i * ld + p] = c * aip - conj(sp) * aiq;
+        A[i * ld + q] = sp * aip + c * aiq;
+        cpx<T> vip = V[i * ld + p], viq = V[i * ld + q];
+        V[i * ld + p] = c * vip - conj(sp) * viq;
+        V[i * ld + q] = sp * vip + c * viq;
+      }
+      __syncthreads();
+      for (int k = tid; k < half; k += nth) {
+        cpx<T> sp = rs[k];
+        if (sp.re == (T)0 && sp.im == (T)0) continue;
+        int p = S.rp[k], q = S.rq[k];
+        A[p * ld + q] = mk<T>((T)0, (T)0);
+        A[q * ld + p] = mk<T>((T)0, (T)0);
+        A[p * ld + p].im = (T)0;
+        A[q * ld + q].im = (T)0;
+      }
+      __syncthreads();
+    }
+    const int rotated = S.flag[0];
+    __syncthreads();
+    if (!rotated) break;
+  }
+}
+
+// y = G x (double), G n x n row-major.
+__device__ void matvec64(const cd* G, const cd* x, cd* y, int n) {
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    cd acc = mk(0.0, 0.0);
+    for (int q = 0; q < n; ++q) cfma(acc, G[p * n + q], x[q]);
+    y[p] = acc;
+  }
+  __syncthreads();
+}
+
+// x <- x / ||x||; returns the old norm.
+__device__ double normalize64(cd* x, int n, double* red) {
+  double s = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += abs2(x[i]);
+  s = block_sum(s, red);
+  double inv = s > 0 ? rsqrt(s) : 0.0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = inv * x[i];
+  __syncthreads();
+  return sqrt(s);
+}
+
+// Re(a^H b)
+__device__ double dotre64(const cd* a, const cd* b, int n, double* red) {
+  double s = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) s += a[i].re * b[i].re + a[i].im * b[i].im;
+  return block_sum(s, red);
+}
+
+// a^H b (complex)
+__device__ cd dotc64(const cd* a, const cd* b, int n, double* red) {
+  cd acc = mk(0.0, 0.0);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) cfmac(acc, a[i], b[i]);
+  double re = block_sum(acc.re, red);
+  double im = block_sum(acc.im, red);
+  return mk(re, im);
+}
+
+// Newton correction with the single-precision eigenbasis:
+// x <- normalise(x - sum_{l != imin} v_l (v_l^H res) / (lam_l - theta)),
+// res = r - theta x, r = (accurate) S^H S x.
+__device__ double newton_eigbasis(EigSmem& S, int n, int imin, const cd* r, double theta) {
+  const int np = np_of(n);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) S.z[i] = r[i] - theta * S.x[i];  // res
+  __syncthreads();
+  // coefficients c_l = v_l^H res / (lam_l - theta) -> S.y
+  for (int l = threadIdx.x; l < n; l += blockDim.x) {
+    cd c = mk(0.0, 0.0);
+    if (l != imin) {
+      for (int i = 0; i < n; ++i) cfmac(c, cvt<double>(S.V[i * np + l]), S.z[i]);
+      double den = S.lam[l] - theta;
+      c = (1.0 / den) * c;
+    }
+    S.y[l] = c;
+  }
+  __syncthreads();
+  double d2 = 0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    cd dx = mk(0.0, 0.0);
+    for (int l = 0; l < n; ++l) cfma(dx, cvt<double>(S.V[i * np + l]), S.y[l]);
+    S.x[i] = S.x[i] - dx;
+    d2 += abs2(dx);
+  }
+  d2 = block_sum(d2, S.red);
+  normalize64(S.x, n, S.red);
+  return d2;
+}
+
+// Newton correction with a double-precision eigenbasis V (ld x ld, columns),
+// eigenvalues lam: x <- normalise(x - sum_{l != imin} v_l (v_l^H res) / (lam_l - theta)).
+__device__ void newton_eigbasis64(EigSmem& S, const cd* V, const double* lam, int n, int ld,
+                                  int imin, const cd* r, double theta) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) S.z[i] = r[i] - theta * S.x[i];
+  __syncthreads();
+  for (int l = threadIdx.x; l < n; l += blockDim.x) {
+    cd c = mk(0.0, 0.0);
+    if (l != imin) {
+      for (int i = 0; i < n; ++i) cfmac(c, V[i * ld + l], S.z[i]);
+      c = (1.0 / (lam[l] - theta)) * c;
+    }
+    S.y[l] = c;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    cd dx = mk(0.0, 0.0);
+    for (int l = 0; l < n; ++l) cfma(dx, V[i * ld + l], S.y[l]);
+    S.x[i] = S.x[i] - dx;
+  }
+  __syncthreads();
+  normalize64(S.x, n, S.red);
+}
+
+struct NoApply {
+  __device__ void operator()(const cd*, cd*) const {}
+};
+
+// Smallest eigenpair of the Hermitian positive semi-definite S.G (n x n).
+// With `accurate`, one more Newton step uses apply(x, out) = S^H S x computed
+// from the original system.  Result vector in S.x (unit norm).
+template <class Apply>
+__device__ EigResult smallest_eigvec(EigSmem& S, int n, bool accurate, const Apply& apply) {
+  const int np = np_of(n);
+  if (threadIdx.x == 0) {
+    double gs = 0;
+    for (int i = 0; i < n; ++i) gs = fmax(gs, S.G[i * n + i].re);
+    S.sc[4] = gs > 0 ? gs : 1.0;
+  }
+  __syncthreads();
+  const double gscale = S.sc[4];
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x)
+    S.A[(i / n) * np + (i % n)] = cvt<float>((1.0 / gscale) * S.G[i]);
+  __syncthreads();
+  jacobi<float>(S.A, S.V, n, np, S, 1e-7f, 4e-7f * (float)n);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) S.lam[i] = gscale * (double)S.A[i * np + i].re;
+  __syncthreads();
+  // eigenvalue ordering (thread 0)
+  if (threadIdx.x == 0) {
+    int i1 = 0;
+    double lmax = -1e300;
+    for (int i = 0; i < n; ++i) {
+      if (S.lam[i] < S.lam[i1]) i1 = i;
+      lmax = fmax(lmax, S.lam[i]);
+    }
+    int i2 = -1;
+    for (int i = 0; i < n; ++i)
+      if (i != i1 && (i2 < 0 || S.lam[i] < S.lam[i2])) i2 = i;
+    if (i2 < 0) i2 = i1;
+    S.flag[2] = i1;
+    S.flag[3] = i2;
+    S.sc[0] = fmax(lmax, 0.0);
+    S.sc[1] = S.lam[i2];
+    S.sc[2] = S.lam[i1];
+  }
+  __syncthreads();
+  const int imin = S.flag[2];
+  const double lmax = S.sc[0];
+  double lam2 = S.sc[1];
+  // single-precision eigenvalues carry errors ~ n u lmax; below a 1e-4 lmax
+  // gap the two smallest are not reliably separated
+  const bool hard = n > 1 && (S.sc[1] - S.sc[2]) <= 1e-4 * lmax;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) S.x[i] = cvt<double>(S.V[i * np + imin]);
+  __syncthreads();
+  normalize64(S.x, n, S.red);
+  double theta;
+  if (!hard) {
+    for (int it = 0; it < 12; ++it) {
+      matvec64(S.G, S.x, S.r, n);
+      theta = dotre64(S.x, S.r, n, S.red);
+      if (newton_eigbasis(S, n, imin, S.r, theta) < 1e-30) break;
+    }
+    if (accurate)
+      for (int it = 0; it < 2; ++it) {
+        apply(S.x, S.r);
+        theta = dotre64(S.x, S.r, n, S.red);
+        newton_eigbasis(S, n, imin, S.r, theta);
+      }
+    matvec64(S.G, S.x, S.r, n);
+    theta = dotre64(S.x, S.r, n, S.red);
+  } else {
+    // Unresolved in single precision (the smallest eigenvalues sit below the
+    // single-precision rounding floor, e.g. the z = 1 sample): full cyclic
+    // Jacobi in double precision on G.  The working copy lives in S.L, the
+    // eigenvectors in the (now free) single-precision arrays.
+    const int ld = np;
+    cd* A64 = S.L;                 // ld x ld
+    cd* V64 = (cd*)S.A;            // A and V (float) are contiguous: ld x ld complex doubles
+    for (int i = threadIdx.x; i < ld * ld; i += blockDim.x) {
+      const int r = i / ld, c = i % ld;
+      A64[i] = (r < n && c < n) ? S.G[r * n + c] : mk(0.0, 0.0);
+    }
+    __syncthreads();
+    jacobi<double>(A64, V64, n, ld, S, 1e-15, 1e-17 * (double)n);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) S.lam[i] = A64[i * ld + i].re;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int i1 = 0;
+      for (int i = 0; i < n; ++i)
+        if (S.lam[i] < S.lam[i1]) i1 = i;
+      int i2 = -1;
+      for (int i = 0; i < n; ++i)
+        if (i != i1 && (i2 < 0 || S.lam[i] < S.lam[i2])) i2 = i;
+      S.flag[2] = i1;
+      S.sc[1] = i2 >= 0 ? S.lam[i2] : S.lam[i1];
+    }
+    __syncthreads();
+    const int i1 = S.flag[2];
+    lam2 = S.sc[1];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) S.x[i] = V64[i * ld + i1];
+    __syncthreads();
+    normalize64(S.x, n, S.red);
+    if (accurate) {
+      apply(S.x, S.r);
+      theta = dotre64(S.x, S.r, n, S.red);
+      newton_eigbasis64(S, V64, S.lam, n, ld, i1, S.r, theta);
+    }
+    matvec64(S.G, S.x, S.r, n);
+    theta = dotre64(S.x, S.r, n, S.red);
+  }
+  EigResult res;
+  res.lam_max = lmax;
+  res.lam_2 = lam2;
+  res.theta = theta;
+  res.hard = hard ? 1 : 0;
+  return res;
+}
+
+// Carve an EigSmem out of dynamic shared memory for dimension n.
+__device__ char* carve_eig(EigSmem& S, char* p, int n) {
+  const int np = np_of(n);
+  auto take = [&](size_t bytes) {
+    char* q = p;
+    p += (bytes + 15) & ~size_t(15);
+    return q;
+  };
+  S.G = (cd*)take(sizeof(cd) * n * n);
+  S.L = (cd*)take(sizeof(cd) * np * np);
+  S.A = (cf*)take(sizeof(cf) * np * np);
+  S.V = (cf*)take(sizeof(cf) * np * np);
+  S.x = (cd*)take(sizeof(cd) * n);
+  S.y = (cd*)take(sizeof(cd) * n);
+  S.r = (cd*)take(sizeof(cd) * n);
+  S.z = (cd*)take(sizeof(cd) * n);
+  S.lam = (double*)take(sizeof(double) * n);
+  S.rc = (double*)take(sizeof(double) * np / 2);
+  S.rs = (cd*)take(sizeof(cd) * np / 2);
+  S.rp = (int*)take(sizeof(int) * np / 2);
+  S.rq = (int*)take(sizeof(int) * np / 2);
+  S.red = (double*)take(sizeof(double) * 32);
+  S.flag = (int*)take(sizeof(int) * 4);
+  S.sc = (double*)take(sizeof(double) * 8);
+  return p;
+}
+
+size_t eig_smem_bytes(int n) {
+  const int np = (n + 1) & ~1;
+  auto r = [](size_t b) { return (b + 15) & ~size_t(15); };
+  return r(sizeof(cd) * n * n) + r(sizeof(cd) * np * np) + r(sizeof(cf) * np * np) * 2 + r(sizeof(cd) * n) * 4 + r(sizeof(double) * n) +
+         r(sizeof(double) * np / 2) + r(sizeof(cd) * np / 2) + r(sizeof(int) * np / 2) * 2 +
+         r(sizeof(double) * 32) + r(sizeof(int) * 4) + r(sizeof(double) * 8);
+}
+
+// ------------------------------------------------------ per-sample solve ---
+struct SampleArgs {
+  const void* pz[2][2];      // [pass][frame] cpx<TP> [n][C][ns][len]
+  const double* dc[2][2];    // [pass][frame] double [n][C][len] (mixed)
+  int len[2][2];             // [pass][frame]
+  cd* X;                     // [n][2][ns][nn]
+  double* sdiag;             // [n][2][ns][4]
+  cd* resid;                 // [n][2][ns][C][Lmax]
+  int Lmax, C, ns, t1, t2, nn, mixed;
+};
+
+// Sample polynomial element m of frame k (0: b1, 1: b2) as cpx<TA>.
+template <typename TP, typename TA>
+struct SamplePolys {
+  const cpx<TP>* c[2];   // complex data, channel 0; channel stride cstride[k]
+  const double* r[2];    // real double data (z = 1 sample of the mixed path)
+  int64_t cstride[2];
+  int len[2];
+  __device__ __forceinline__ cpx<TA> ld(int k, int ch, int m) const {
+    if (r[k]) return mk<TA>((TA)r[k][ch * cstride[k] + m], (TA)0);
+    cpx<TP> v = c[k][ch * cstride[k] + m];
+    return mk<TA>((TA)v.re, (TA)v.im);
+  }
+};
+
+// rho jobs: j < t1: rho_22(j); j < t1+t2: rho_11(j - t1);
+// else rho_21(d), d = j - t1 - t2 - (t2 - 1) in [-(t2-1), t1-1].
+template <typename TP, typename TA>
+__device__ void correlations(const SamplePolys<TP, TA>& P, int C, int t1, int t2, cd* rho) {
+  const int J = 2 * (t1 + t2) - 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = warp; j < J; j += nw) {
+    int ka, kb, d;
+    if (j < t1) { ka = 1; kb = 1; d = j; }
+    else if (j < t1 + t2) { ka = 0; kb = 0; d = j - t1; }
+    else { ka = 1; kb = 0; d = j - t1 - t2 - (t2 - 1); }
+    const int la = P.len[ka], lb = P.len[kb];
+    const int m0 = d < 0 ? -d : 0;
+    const int m1 = min(la, lb - d);
+    cpx<TA> acc = mk<TA>(0, 0);
+    for (int ch = 0; ch < C; ++ch)
+      for (int m = m0 + lane; m < m1; m += 32) cfmac(acc, P.ld(ka, ch, m), P.ld(kb, ch, m + d));
+    double re = warp_sum((double)acc.re), im = warp_sum((double)acc.im);
+    if (lane == 0) rho[j] = mk(re, im);
+  }
+  __syncthreads();
+}
+
+// G[p][q] from the correlations (Toeplitz blocks).
+__device__ void gram_from_rho(const cd* rho, int t1, int t2, cd* G) {
+  const int n = t1 + t2;
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x) {
+    int p = i / n, q = i % n;
+    cd g;
+    if (p < t1 && q < t1) {
+      int d = p - q;
+      g = d >= 0 ? rho[d] : conj(rho[-d]);
+    } else if (p >= t1 && q >= t1) {
+      int d = (p - t1) - (q - t1);
+      g = d >= 0 ? rho[t1 + d] : conj(rho[t1 - d]);
+    } else if (p < t1) {
+      int d = p - (q - t1);               // rho_21(d)
+      cd v = rho[t1 + t2 + d + t2 - 1];
+      g = mk(-v.re, -v.im);
+    } else {
+      int d = q - (p - t1);
+      cd v = rho[t1 + t2 + d + t2 - 1];
+      g = mk(-v.re, v.im);                // -conj(rho_21(d))
+    }
+    G[i] = g;
+  }
+  __syncthreads();
+}
+
+// Accurate S^H S x for the FP64 path: y = S x per channel in the global
+// scratch, then the correlations with b1, b2.
+struct SylvesterApply {
+  SamplePolys<double, double> P;
+  cd* y;            // [C][L]
+  int C, t1, t2, L;
+  double* red;
+  __device__ void operator()(const cd* x, cd* out) const {
+    for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
+      int ch = idx / L, i = idx % L;
+      cd acc = mk(0.0, 0.0);
+      for (int q = 0; q < t2; ++q) {     // b1 * v
+        int m = i - q;
+        if (m >= 0 && m < P.len[0]) cfma(acc, P.ld(0, ch, m), x[t1 + q]);
+      }
+      for (int p = 0; p < t1; ++p) {     // - b2 * u
+        int m = i - p;
+        if (m >= 0 && m < P.len[1]) {
+          cd b = P.ld(1, ch, m);
+          cd u = x[p];
+          acc.re -= b.re * u.re - b.im * u.im;
+          acc.im -= b.re * u.im + b.im * u.re;
+        }
+      }
+      y[idx] = acc;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int n = t1 + t2;
+    for (int o = warp; o < n; o += nw) {
+      const int k = o < t1 ? 1 : 0;       // u rows use b2, v rows use b1
+      const int sh = o < t1 ? o : o - t1;
+      cd acc = mk(0.0, 0.0);
+      for (int ch = 0; ch < C; ++ch)
+        for (int m = lane; m < P.len[k]; m += 32) cfmac(acc, P.ld(k, ch, m), y[ch * L + m + sh]);
+      double re = warp_sum(acc.re), im = warp_sum(acc.im);
+      if (lane == 0) out[o] = o < t1 ? mk(-re, -im) : mk(re, im);
+    }
+    __syncthreads();
+  }
+};
+
+template <typename TP>
+__global__ void __launch_bounds__(kSolveThreads) k_sample_solve(SampleArgs a) {
+  extern __shared__ __align__(16) char smem[];
+  const int s = blockIdx.x, ps = blockIdx.y, f = blockIdx.z;
+  const int n = a.nn;
+  EigSmem S;
+  char* p = carve_eig(S, smem, n);
+  cd* rho = (cd*)p;
+  const bool use_dc = a.mixed && s == 0;
+  const int64_t cs0 = a.len[ps][0], cs1 = a.len[ps][1];
+  if (use_dc || !a.mixed) {
+    SamplePolys<TP, double> P;
+    for (int k = 0; k < 2; ++k) {
+      const int64_t len = a.len[ps][k];
+      P.len[k] = (int)len;
+      if (use_dc) {
+        P.c[k] = nullptr;
+        P.r[k] = a.dc[ps][k] + (int64_t)f * a.C * len;
+        P.cstride[k] = len;
+      } else {
+        P.c[k] = (const cpx<TP>*)a.pz[ps][k] + ((int64_t)f * a.C * a.ns + s) * len;
+        P.r[k] = nullptr;
+        P.cstride[k] = len * a.ns;
+      }
+    }
+    correlations(P, a.C, a.t1, a.t2, rho);
+  } else {
+    SamplePolys<TP, float> P;
+    for (int k = 0; k < 2; ++k) {
+      const int64_t len = a.len[ps][k];
+      P.len[k] = (int)len;
+      P.c[k] = (const cpx<TP>*)a.pz[ps][k] + ((int64_t)f * a.C * a.ns + s) * len;
+      P.r[k] = nullptr;
+      P.cstride[k] = len * a.ns;
+    }
+    correlations(P, a.C, a.t1, a.t2, rho);
+  }
+  (void)cs0;
+  (void)cs1;
+  gram_from_rho(rho, a.t1, a.t2, S.G);
+  EigResult res;
+  if (!a.mixed) {
+    // FP64 path: TP is double here.
+    SylvesterApply ap;
+    for (int k = 0; k < 2; ++k) {
+      const int64_t len = a.len[ps][k];
+      ap.P.len[k] = (int)len;
+      ap.P.c[k] = (const cd*)a.pz[ps][k] + ((int64_t)f * a.C * a.ns + s) * len;
+      ap.P.r[k] = nullptr;
+      ap.P.cstride[k] = len * a.ns;
+    }
+    ap.C = a.C;
+    ap.t1 = a.t1;
+    ap.t2 = a.t2;
+    ap.L = a.len[ps][0] + a.t2 - 1;
+    ap.y = a.resid + (((int64_t)f * 2 + ps) * a.ns + s) * a.C * (int64_t)a.Lmax;
+    ap.red = S.red;
+    res = smallest_eigvec(S, n, true, ap);
+  } else {
+    res = smallest_eigvec(S, n, false, NoApply());
+  }
+  const int64_t o = ((int64_t)f * 2 + ps) * a.ns + s;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) a.X[o * n + i] = S.x[i];
+  if (threadIdx.x == 0) {
+    a.sdiag[o * 4 + 0] = res.lam_max;
+    a.sdiag[o * 4 + 1] = res.lam_2;
+    a.sdiag[o * 4 + 2] = res.theta;
+    a.sdiag[o * 4 + 3] = res.hard;
+  }
+}
+
+// ------------------------------------------------- scale fix and kernels ---
+struct ScaleArgs {
+  const cd* X;          // [n][2][ns][nn]
+  const double* sdiag;  // [n][2][ns][4]
+  const int* bad;       // [n]
+  cd* ab;               // [n][4][M][M]  A_1, A_2, B_1, B_2
+  double* kd;           // [n][t1*t1 + t2*t2]
+  void* k1_out;
+  void* k2_out;
+  const uint64_t* k1_tab;   // optional per-pair kernel addresses
+  const uint64_t* k2_tab;
+  int out_f64;
+  cbp_diag* diag;       // [n]
+  int M, ns, t1, t2, nn, mixed, Ph, Pw;
+};
+
+__device__ __forceinline__ cd root(int k, int M, double sign) {
+  double s, c;
+  sincospi(sign * 2.0 * (double)(k % M) / (double)M, &s, &c);
+  return mk(c, s);
+}
+
+// Cofactor of kernel kk (0, 1) at sample s of pass ps, conjugate-expanded.
+__device__ __forceinline__ cd cofactor(const ScaleArgs& a, int f, int ps, int s, int idx) {
+  const int M = a.M;
+  const bool cj = s >= a.ns;
+  const int ss = cj ? M - s : s;
+  cd v = a.X[(((int64_t)f * 2 + ps) * a.ns + ss) * a.nn + idx];
+  return cj ? conj(v) : v;
+}
+
+// Exact S^H S theta for the scale system (rows: gamma_j A_k[i][j] - delta_i B_k[i][j]).
+struct ScaleApply {
+  const cd* ab;
+  int M;
+  __device__ void operator()(const cd* th, cd* out) const {
+    const int MM = M * M;
+    for (int u = threadIdx.x; u < 2 * M; u += blockDim.x) {
+      cd acc = mk(0.0, 0.0);
+      for (int k = 0; k < 2; ++k) {
+        const cd* A = ab + k * MM;
+        const cd* B = ab + (2 + k) * MM;
+        for (int t = 0; t < M; ++t) {
+          int i = u < M ? t : u - M;
+          int j = u < M ? u : t;
+          cd res = th[j] * A[i * M + j] - th[M + i] * B[i * M + j];
+          if (u < M) cfmac(acc, A[i * M + j], res);
+          else {
+            cd v = mk(0.0, 0.0);
+            cfmac(v, B[i * M + j], res);
+            acc = acc - v;
+          }
+        }
+      }
+      out[u] = acc;
+    }
+    __syncthreads();
+  }
+};
+
+__global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
+  extern __shared__ __align__(16) char smem[];
+  const int f = blockIdx.x;
+  const int M = a.M, MM = M * M, t1 = a.t1, t2 = a.t2;
+  const int n = 2 * M;
+  EigSmem S;
+  char* p = carve_eig(S, smem, n);
+  cd* X = (cd*)p;                 // [2][M][M] kernel spectra, then full inverse DFTs
+  cd* T = X + 2 * MM;             // [M][M] temporary
+  cd* ab = a.ab + (int64_t)f * 4 * MM;
+  // lift: A_k[i][j] = sum_p u^{Z2}_{k,j}[p] w^{ip};  B_k[i][j] = sum_q u^{Z1}_{k,i}[q] w^{jq}
+  for (int idx = threadIdx.x; idx < 4 * MM; idx += blockDim.x) {
+    const int which = idx / MM, i = (idx % MM) / M, j = idx % M;
+    const int kk = which & 1, isB = which >> 1;
+    const int t = kk ? t2 : t1, lo = kk ? t1 : 0;
+    cd acc = mk(0.0, 0.0);
+    for (int q = 0; q < t; ++q) {
+      if (!isB) cfma(acc, cofactor(a, f, 0, j, lo + q), root(i * q, M, -1.0));
+      else cfma(acc, cofactor(a, f, 1, i, lo + q), root(j * q, M, -1.0));
+    }
+    ab[idx] = acc;
+  }
+  __syncthreads();
+  // normal matrix of the scale system
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int r = idx / n, c = idx % n;
+    cd g = mk(0.0, 0.0);
+    if (r < M && c < M) {
+      if (r == c)
+        for (int k = 0; k < 2; ++k)
+          for (int i = 0; i < M; ++i) g.re += abs2(ab[k * MM + i * M + r]);
+    } else if (r >= M && c >= M) {
+      if (r == c)
+        for (int k = 0; k < 2; ++k)
+          for (int j = 0; j < M; ++j) g.re += abs2(ab[(2 + k) * MM + (r - M) * M + j]);
+    } else if (r < M) {   // (gamma_j, delta_i) = -sum_k conj(A_k[i][j]) B_k[i][j]
+      const int j = r, i = c - M;
+      for (int k = 0; k < 2; ++k) {
+        cd v = cmulc(ab[k * MM + i * M + j], ab[(2 + k) * MM + i * M + j]);
+        g = g - v;
+      }
+    } else {
+      const int j = c, i = r - M;
+      for (int k = 0; k < 2; ++k) {
+        cd v = cmulc(ab[(2 + k) * MM + i * M + j], ab[k * MM + i * M + j]);
+        g = g - v;
+      }
+    }
+    S.G[idx] = g;
+  }
+  __syncthreads();
+  ScaleApply ap{ab, M};
+  EigResult res = smallest_eigvec(S, n, !a.mixed, ap);
+  // X_k[i][j] = (gamma_j A_k[i][j] + delta_i B_k[i][j]) / 2
+  for (int idx = threadIdx.x; idx < 2 * MM; idx += blockDim.x) {
+    const int k = idx / MM, i = (idx % MM) / M, j = idx % M;
+    X[idx] = 0.5 * (S.x[j] * ab[k * MM + i * M + j] + S.x[M + i] * ab[(2 + k) * MM + i * M + j]);
+  }
+  __syncthreads();
+  __shared__ cd x00[2];
+  if (threadIdx.x < 2) x00[threadIdx.x] = X[threadIdx.x * MM];
+  __syncthreads();
+  // inverse DFT, separable: T[i][q] = sum_j X[i][j] w^{-jq};  K[p][q] = sum_i w^{-ip} T[i][q] / M^2
+  __shared__ double acc_sq[4];  // re^2, im^2, outside-support, total  (per kernel, reused)
+  for (int k = 0; k < 2; ++k) {
+    cd* Xk = X + k * MM;
+    const cd inv00 = [&] {
+      cd z = x00[k];
+      double d = abs2(z);
+      return d > 0 ? mk(z.re / d, -z.im / d) : mk(0.0, 0.0);
+    }();
+    for (int idx = threadIdx.x; idx < MM; idx += blockDim.x) {
+      const int i = idx / M, q = idx % M;
+      cd acc = mk(0.0, 0.0);
+      for (int j = 0; j < M; ++j) cfma(acc, Xk[i * M + j] * inv00, root(j * q, M, 1.0));
+      T[idx] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) acc_sq[threadIdx.x] = 0.0;
+    __syncthreads();
+    const int t = k ? t2 : t1;
+    double* kd = a.kd + (int64_t)f * (t1 * t1 + t2 * t2) + (k ? t1 * t1 : 0);
+    double l_im = 0, l_re = 0, l_out = 0;
+    for (int idx = threadIdx.x; idx < MM; idx += blockDim.x) {
+      const int pp = idx / M, q = idx % M;
+      cd acc = mk(0.0, 0.0);
+      for (int i = 0; i < M; ++i) cfma(acc, root(i * pp, M, 1.0), T[i * M + q]);
+      acc = (1.0 / (double)MM) * acc;
+      l_re += acc.re * acc.re;
+      l_im += acc.im * acc.im;
+      if (pp >= t || q >= t) l_out += abs2(acc);
+      if (pp < t && q < t) {
+        kd[pp * t + q] = acc.re;
+        void* out = k ? a.k2_out : a.k1_out;
+        int64_t oi = (int64_t)f * t * t + pp * t + q;
+        const uint64_t* tab = k ? a.k2_tab : a.k1_tab;
+        if (tab) {
+          out = (void*)tab[f];
+          oi = pp * t + q;
+        }
+        if (out) {
+          if (a.out_f64) ((double*)out)[oi] = acc.re;
+          else ((float*)out)[oi] = (float)acc.re;
+        }
+      }
+    }
+    l_re = block_sum(l_re, S.red);
+    l_im = block_sum(l_im, S.red);
+    l_out = block_sum(l_out, S.red);
+    if (threadIdx.x == 0) {
+      double ir = l_re > 0 ? sqrt(l_im / l_re) : 0.0;
+      double sr = (l_re + l_im) > 0 ? l_out / (l_re + l_im) : 0.0;
+      acc_sq[0] = ir;
+      acc_sq[1] = sr;
+      if (k == 0) {
+        a.diag[f].imag_ratio = ir;
+        a.diag[f].support_ratio = sr;
+      } else {
+        a.diag[f].imag_ratio = fmax(a.diag[f].imag_ratio, ir);
+        a.diag[f].support_ratio = fmax(a.diag[f].support_ratio, sr);
+      }
+    }
+    __syncthreads();
+  }
+  // aggregate diagnostics
+  if (threadIdx.x == 0) {
+    double kappa = 0, gap = 1e300, smin = 0;
+    int flagged = 0, hard = 0;
+    for (int i = 0; i < 2 * a.ns; ++i) {
+      const double* d = a.sdiag + ((int64_t)f * 2 * a.ns + i) * 4;
+      const double lmax = d[0] > 0 ? d[0] : 1e-300;
+      const double g = sqrt(fmax(d[1], 0.0) / lmax);
+      gap = fmin(gap, g);
+      kappa = fmax(kappa, g > 0 ? 1.0 / g : 1e300);
+      smin = fmax(smin, sqrt(fmax(d[2], 0.0) / lmax));
+      if (g < 1e-8) ++flagged;
+      hard += (int)d[3];
+    }
+    cbp_diag& dg = a.diag[f];
+    dg.kappa_max = kappa;
+    dg.gap_min = gap;
+    dg.sigma_min_max = smin;
+    dg.scale_resid = sqrt(fmax(res.theta, 0.0) / fmax(res.lam_max, 1e-300));
+    dg.rho = 0.0;
+    dg.flagged_samples = flagged;
+    dg.used_fallback = 0;
+    dg.pad_h = a.Ph;
+    dg.pad_w = a.Pw;
+    dg.hard_samples = hard;
+    int st = CBP_OK;
+    if (a.bad[f]) st = CBP_ERR_INVALID_ARG;
+    else if (!(x00[0].re != 0.0 || x00[0].im != 0.0) || !(x00[1].re != 0.0 || x00[1].im != 0.0))
+      st = CBP_ERR_NOT_COPRIME;
+    else if (gap < 1e-13) st = CBP_ERR_NOT_COPRIME;
+    else if (flagged) st = CBP_WARN_ILL_CONDITIONED;
+    dg.status = st;
+  }
+}
+
+__global__ void k_kernels_in(const void* k1, const void* k2, int in_f64, int n, int t1, int t2,
+                             double* kd, cbp_diag* diag, int Ph, int Pw, const int* bad) {
+  const int per = t1 * t1 + t2 * t2;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)n * per;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int f = (int)(i / per), e = (int)(i % per);
+    double v;
+    if (e < t1 * t1) v = in_f64 ? ((const double*)k1)[(int64_t)f * t1 * t1 + e] : ((const float*)k1)[(int64_t)f * t1 * t1 + e];
+    else v = in_f64 ? ((const double*)k2)[(int64_t)f * t2 * t2 + e - t1 * t1] : ((const float*)k2)[(int64_t)f * t2 * t2 + e - t1 * t1];
+    kd[i] = v;
+    if (e == 0) {
+      cbp_diag d = {};
+      d.pad_h = Ph;
+      d.pad_w = Pw;
+      d.status = bad && bad[f] ? CBP_ERR_INVALID_ARG : CBP_OK;
+      diag[f] = d;
+    }
+  }
+}
+
+}  // namespace
+
+size_t sample_solve_smem(int nn) { return eig_smem_bytes(nn) + sizeof(cd) * (4 * kMaxN); }
+size_t scale_solve_smem(int M) { return eig_smem_bytes(2 * M) + sizeof(cd) * 3 * M * M; }
+
+void launch_sample_solve(const Plan& p, char* ws, cudaStream_t st) {
+  SampleArgs a;
+  for (int k = 0; k < 2; ++k) {
+    a.pz[0][k] = ws + p.off_pz2[k];
+    a.pz[1][k] = ws + p.off_pz1[k];
+    a.dc[0][k] = p.mixed ? (const double*)(ws + p.off_dcz2[k]) : nullptr;
+    a.dc[1][k] = p.mixed ? (const double*)(ws + p.off_dcz1[k]) : nullptr;
+  }
+  a.len[0][0] = p.H1;
+  a.len[0][1] = p.H2;
+  a.len[1][0] = p.W1;
+  a.len[1][1] = p.W2;
+  a.X = (cd*)(ws + p.off_x);
+  a.sdiag = (double*)(ws + p.off_sdiag);
+  a.resid = (cd*)(ws + p.off_resid);
+  a.Lmax = p.Lmax;
+  a.C = p.C;
+  a.ns = p.ns;
+  a.t1 = p.t1;
+  a.t2 = p.t2;
+  a.nn = p.nn;
+  a.mixed = p.mixed;
+  const size_t sm = sample_solve_smem(p.nn);
+  dim3 grid(p.ns, 2, p.n);
+  if (p.mixed) {
+    cudaFuncSetAttribute(k_sample_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_sample_solve<float><<<grid, kSolveThreads, sm, st>>>(a);
+  } else {
+    cudaFuncSetAttribute(k_sample_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_sample_solve<double><<<grid, kSolveThreads, sm, st>>>(a);
+  }
+}
+
+void launch_scale_solve(const Plan& p, char* ws, void* k1_out, void* k2_out, int out_f64,
+                        cudaStream_t st, const uint64_t* k1_tab, const uint64_t* k2_tab) {
+  ScaleArgs a;
+  a.X = (const cd*)(ws + p.off_x);
+  a.sdiag = (const double*)(ws + p.off_sdiag);
+  a.bad = (const int*)(ws + p.off_bad);
+  a.ab = (cd*)(ws + p.off_resid);  // reuses the residual scratch (sized for both)
+  a.kd = (double*)(ws + p.off_kd);
+  a.k1_out = k1_out;
+  a.k2_out = k2_out;
+  a.k1_tab = k1_tab;
+  a.k2_tab = k2_tab;
+  a.out_f64 = out_f64;
+  a.diag = (cbp_diag*)(ws + p.off_diag);
+  a.M = p.M;
+  a.ns = p.ns;
+  a.t1 = p.t1;
+  a.t2 = p.t2;
+  a.nn = p.nn;
+  a.mixed = p.mixed;
+  a.Ph = p.Ph;
+  a.Pw = p.Pw;
+  const size_t sm = scale_solve_smem(p.M);
+  cudaFuncSetAttribute(k_scale_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_scale_solve<<<p.n, kSolveThreads, sm, st>>>(a);
+}
+
+void launch_kernels_in(const Plan& p, char* ws, const void* k1, const void* k2, int in_f64,
+                       cudaStream_t st) {
+  const int64_t total = (int64_t)p.n * (p.t1 * p.t1 + p.t2 * p.t2);
+  int blocks = (int)((total + 255) / 256);
+  if (blocks > 4096) blocks = 4096;
+  k_kernels_in<<<blocks, 256, 0, st>>>(k1, k2, in_f64, p.n, p.t1, p.t2, (double*)(ws + p.off_kd),
+                                       (cbp_diag*)(ws + p.off_diag), p.Ph, p.Pw,
+                                       (const int*)(ws + p.off_bad));
+}
+
+}  // namespace cbp

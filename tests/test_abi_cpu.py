@@ -1,0 +1,98 @@
+"""C ABI checks that need no GPU: exported symbols, status strings, and the
+host-side validation and planning behind every entry point."""
+import ctypes
+import re
+from pathlib import Path
+
+import pytest
+import torch
+
+ROOT = Path(__file__).resolve().parents[1]
+
+
+def declared_functions():
+    src = (ROOT / "include" / "cbp.h").read_text()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"^\s*(?:cbp_status|const char\*)\s+(cbp_\w+)\s*\(", src, re.M)))
+
+
+def test_every_declared_symbol_is_exported(built_lib):
+    from paper_1203_4874_gb300 import cbp
+    names = declared_functions()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(built_lib, n), n
+    assert sorted(cbp.EXPORTED) == names
+
+
+def test_status_strings(built_lib):
+    from paper_1203_4874_gb300 import cbp
+    assert cbp.status_string(0) == "CBP_OK"
+    assert cbp.status_string(-3) == "CBP_ERR_NOT_COPRIME"
+    assert cbp.status_string(12345) == "CBP_UNKNOWN_STATUS"
+
+
+def _frames(n, c, h, w, dtype=0, rs=0):
+    from paper_1203_4874_gb300 import cbp
+    return cbp.cbp_frames(0x1000, n, c, h, w, dtype, rs, 0, 0)
+
+
+def _ws(b1, b2, prm):
+    from paper_1203_4874_gb300 import cbp
+    out = ctypes.c_size_t()
+    s = cbp.lib().cbp_workspace_size(ctypes.byref(b1), ctypes.byref(b2), ctypes.byref(prm),
+                                     ctypes.byref(out))
+    return s, out.value
+
+
+def test_planner_accepts_the_workload_shapes(built_lib):
+    from paper_1203_4874_gb300 import cbp
+    for (h, w, c, t1, t2, path, n) in [(64, 64, 1, 5, 5, "fp64", 1), (480, 640, 1, 9, 11, "fp64", 30),
+                                       (1080, 1920, 3, 15, 17, "mixed", 60)]:
+        s, b = _ws(_frames(n, c, h + t1 - 1, w + t1 - 1), _frames(n, c, h + t2 - 1, w + t2 - 1),
+                   cbp.params(t1, t2, path=path))
+        assert s == cbp.CBP_OK and b > 0
+
+
+def test_planner_rejects_bad_arguments(built_lib):
+    from paper_1203_4874_gb300 import cbp
+    ok1, ok2 = _frames(1, 1, 68, 68), _frames(1, 1, 68, 68)
+    assert _ws(ok1, ok2, cbp.params(5, 5))[0] == cbp.CBP_OK
+    # blurred sizes inconsistent with t1 - t2
+    assert _ws(ok1, _frames(1, 1, 70, 68), cbp.params(5, 7))[0] == cbp.CBP_ERR_SIZE_MISMATCH
+    # fewer samples than the kernel height
+    assert _ws(ok1, ok2, cbp.params(5, 5, m=4))[0] == cbp.CBP_ERR_INVALID_ARG
+    # library limits
+    assert _ws(ok1, ok2, cbp.params(5, 5, m=33))[0] == cbp.CBP_ERR_UNSUPPORTED
+    assert _ws(_frames(1, 1, 200, 200), _frames(1, 1, 200, 200),
+               cbp.params(40, 40))[0] == cbp.CBP_ERR_UNSUPPORTED
+    # FFT grid must hold the frames and be 7-smooth
+    assert _ws(ok1, ok2, cbp.params(5, 5, pad_h=66))[0] == cbp.CBP_ERR_INVALID_ARG
+    assert _ws(ok1, ok2, cbp.params(5, 5, pad_h=88))[0] == cbp.CBP_ERR_INVALID_ARG   # 88 = 8 * 11
+    assert _ws(ok1, ok2, cbp.params(5, 5, pad_h=72, pad_w=75))[0] == cbp.CBP_OK
+    # negative eps, mismatched batch / dtype, bad strides, null data
+    assert _ws(ok1, ok2, cbp.params(5, 5, eps=-1.0))[0] == cbp.CBP_ERR_INVALID_ARG
+    assert _ws(ok1, _frames(2, 1, 68, 68), cbp.params(5, 5))[0] == cbp.CBP_ERR_INVALID_ARG
+    assert _ws(ok1, _frames(1, 1, 68, 68, dtype=1), cbp.params(5, 5))[0] == cbp.CBP_ERR_INVALID_ARG
+    assert _ws(_frames(1, 1, 68, 68, rs=10), ok2, cbp.params(5, 5))[0] == cbp.CBP_ERR_INVALID_ARG
+    null = cbp.cbp_frames(0, 1, 1, 68, 68, 0, 0, 0, 0)
+    assert _ws(null, ok2, cbp.params(5, 5))[0] == cbp.CBP_ERR_INVALID_ARG
+    # no latent left
+    assert _ws(_frames(1, 1, 4, 4), _frames(1, 1, 4, 4), cbp.params(5, 5))[0] == cbp.CBP_ERR_SIZE_MISMATCH
+
+
+def test_workspace_grows_with_batch(built_lib):
+    from paper_1203_4874_gb300 import cbp
+    prm = cbp.params(9, 11)
+    _, one = _ws(_frames(1, 1, 488, 648), _frames(1, 1, 490, 650), prm)
+    _, ten = _ws(_frames(10, 1, 488, 648), _frames(10, 1, 490, 650), prm)
+    assert 9 * one < ten < 11 * one
+
+
+def test_create_fails_cleanly_without_device(built_lib):
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    from paper_1203_4874_gb300 import cbp
+    ctx = ctypes.c_void_p()
+    assert cbp.lib().cbp_create(ctypes.byref(ctx), 0, 0) == cbp.CBP_ERR_CUDA
+    assert cbp.lib().cbp_create(None, 0, 0) == cbp.CBP_ERR_INVALID_ARG

@@ -1,0 +1,214 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on the same inputs.
+
+Tolerances:
+  * FP64 path kernels: relative L2 <= 1e-9 (the method's target for the
+    double-precision path); f64 latent: relative L2 <= 1e-9.
+  * f32 frames deconvolve in single precision: FFT rounding (~1e-6 relative)
+    amplified at most 1 / (2 sqrt(eps)) = 50x by the Wiener denominator at
+    eps = 1e-4, so latent relative L2 <= 1e-4, and PSNR against the true
+    latent within 0.05 dB of the oracle's.
+  * Mixed path kernels: relative L2 <= 1e-3; latent PSNR within 0.05 dB.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from tests._inputs import make_batch, psnr, rel
+
+pytestmark = pytest.mark.gpu
+
+
+def run_gpu(ctx, b1, b2, t1, t2, path, eps, dtype, m=0, flags=0, pad=(0, 0), k1=None, k2=None):
+    from paper_1203_4874_gb300 import cbp
+    tdt = torch.float64 if dtype == "f64" else torch.float32
+    B1 = torch.from_numpy(np.ascontiguousarray(b1)).to(tdt).cuda()
+    B2 = torch.from_numpy(np.ascontiguousarray(b2)).to(tdt).cuda()
+    flags |= cbp.CBP_FLAG_KERNELS_F64          # compare kernels before any dtype cast
+    prm = cbp.params(t1, t2, m=m, path=path, eps=eps, pad_h=pad[0], pad_w=pad[1], flags=flags)
+    K1 = None if k1 is None else torch.from_numpy(k1).double().cuda()
+    K2 = None if k2 is None else torch.from_numpy(k2).double().cuda()
+    lat, k1o, k2o, diag, s = cbp.cbp_deblur_pair(ctx, B1, B2, prm, k1=K1, k2=K2)
+    torch.cuda.synchronize()
+    return (lat.double().cpu().numpy(), k1o.double().cpu().numpy(), k2o.double().cpu().numpy(),
+            [d.as_dict() for d in diag])
+
+
+def oracle_pair(b1, b2, t1, t2, eps, m=None, **kw):
+    return oracle.deblur_pair(b1, b2, t1, t2, m=m, eps=eps, **kw)
+
+
+def _stage_check(ctx, b1, b2, cfg, path, p_tol, x_tol):
+    from paper_1203_4874_gb300 import cbp
+    tdt = torch.float64 if cfg.frame_dtype == "f64" else torch.float32
+    prm = cbp.params(cfg.t1, cfg.t2, path=path, eps=cfg.eps)
+    out = cbp.cbp_estimate_kernels_stages(ctx, torch.from_numpy(b1).to(tdt).cuda(),
+                                          torch.from_numpy(b2).to(tdt).cuda(), prm)
+    torch.cuda.synchronize()
+    o = oracle.estimate_kernels(b1[0], b2[0], cfg.t1, cfg.t2)
+    ns = cfg.m // 2 + 1
+    for key, okey in (("p_z2", "p_z2_"), ("p_z1", "p_z1_")):
+        for k in range(2):
+            g = out[key][k][0].cpu().numpy().astype(np.complex128)
+            og = o[okey + str(k + 1)][:, :ns]
+            assert np.abs(g - og).max() <= p_tol * np.abs(og).max(), (key, k)
+    for key in ("x_z2", "x_z1"):
+        g = out[key][0].cpu().numpy()
+        for s in range(ns):
+            ov = abs(np.vdot(g[s], o[key][s])) / (np.linalg.norm(g[s]) * np.linalg.norm(o[key][s]))
+            assert 1 - ov <= x_tol, (key, s, 1 - ov)
+    sd = out["sample_diag"][0].cpu().numpy()
+    sv = np.stack([o["sv_z2"][:ns], o["sv_z1"][:ns]])
+    assert np.allclose(sd[..., 0], sv[..., 0] ** 2, rtol=1e-5)           # lambda_max
+    assert np.allclose(sd[..., 1], sv[..., -2] ** 2, rtol=1e-3)          # second smallest
+    return out, o
+
+
+def test_stages_match_oracle_fp64(gpu_ctx):
+    """Sample polynomials to 1e-13 and per-sample null vectors to 1e-12 (phase-free)."""
+    for name in ("single_64", "video_480p"):
+        b1, b2, *_, cfg = make_batch(name, [0], fast=False)
+        out, o = _stage_check(gpu_ctx, b1, b2, cfg, "fp64", 1e-13, 1e-12)
+        t1 = cfg.t1
+        kd = out["kernels"][0].cpu().numpy()
+        assert rel(kd[:t1 * t1].reshape(t1, t1), o["k1"]) <= 1e-9
+
+
+def test_stages_match_oracle_mixed_1080p(gpu_ctx):
+    """Single-precision samples (~1e-7); null vectors to 1e-5 except that none may flip."""
+    b1, b2, *_, cfg = make_batch("rgb_1080p", [0])
+    _stage_check(gpu_ctx, b1, b2, cfg, "mixed", 1e-6, 1e-5)
+
+
+def test_even_sample_count_self_conjugate_sample(gpu_ctx):
+    """M even: sample M/2 is its own conjugate (real polynomials)."""
+    rng = np.random.default_rng(13)
+    lat = rng.uniform(size=(1, 30, 26))
+    from cbp_synth import draw_kernel_pair
+    k1, k2 = draw_kernel_pair(rng, 5, 3, 6)
+    b1, b2 = oracle.blur_pair(lat, k1, k2)
+    g_lat, g_k1, g_k2, diag = run_gpu(gpu_ctx, b1[None], b2[None], 5, 3, "fp64", 0.0, "f64", m=6)
+    o = oracle_pair(b1, b2, 5, 3, 0.0, m=6)
+    assert rel(g_k1[0], o["k1"]) <= 1e-9 and rel(g_k2[0], o["k2"]) <= 1e-9
+    assert rel(g_lat[0], o["latent"]) <= 1e-9
+
+
+def test_single_64_fp64_exact(gpu_ctx):
+    b1, b2, k1, k2, lat, cfg = make_batch("single_64", [0], fast=False)
+    g_lat, g_k1, g_k2, diag = run_gpu(gpu_ctx, b1, b2, 5, 5, "fp64", 0.0, "f64")
+    o = oracle_pair(b1[0], b2[0], 5, 5, 0.0)
+    assert rel(g_k1[0], o["k1"]) <= 1e-9 and rel(g_k2[0], o["k2"]) <= 1e-9
+    assert rel(g_k1[0], k1[0]) <= 1e-9 and rel(g_k2[0], k2[0]) <= 1e-9
+    assert rel(g_lat[0], o["latent"]) <= 1e-9
+    assert diag[0]["status"] == 0
+    assert abs(diag[0]["gap_min"] - o["diag"]["gap_min"]) <= 1e-3 * o["diag"]["gap_min"]
+
+
+def test_video_480p_fp64_batch(gpu_ctx):
+    frames = [0, 1, 2]
+    b1, b2, k1, k2, lat, cfg = make_batch("video_480p", frames)
+    g_lat, g_k1, g_k2, diag = run_gpu(gpu_ctx, b1, b2, 9, 11, "fp64", cfg.eps, "f32")
+    for i in range(len(frames)):
+        o = oracle_pair(b1[i], b2[i], 9, 11, cfg.eps)
+        assert rel(g_k1[i], o["k1"]) <= 1e-9, i
+        assert rel(g_k2[i], o["k2"]) <= 1e-9, i
+        assert rel(g_lat[i], o["latent"]) <= 1e-4, i
+        assert abs(psnr(g_lat[i], lat[i]) - psnr(o["latent"], lat[i])) <= 0.05
+
+
+def test_rgb_1080p_mixed_and_fp64(gpu_ctx):
+    b1, b2, k1, k2, lat, cfg = make_batch("rgb_1080p", [0])
+    o = oracle_pair(b1[0], b2[0], 15, 17, cfg.eps)
+    g_lat, g_k1, g_k2, diag = run_gpu(gpu_ctx, b1, b2, 15, 17, "mixed", cfg.eps, "f32")
+    assert rel(g_k1[0], o["k1"]) <= 1e-3 and rel(g_k2[0], o["k2"]) <= 1e-3
+    assert abs(psnr(g_lat[0], lat[0]) - psnr(o["latent"], lat[0])) <= 0.05
+    f_lat, f_k1, f_k2, _ = run_gpu(gpu_ctx, b1, b2, 15, 17, "fp64", cfg.eps, "f32")
+    assert rel(f_k1[0], o["k1"]) <= 1e-9 and rel(f_k2[0], o["k2"]) <= 1e-9
+    assert rel(f_lat[0], o["latent"]) <= 1e-4
+
+
+def test_ragged_sizes_channels_and_extra_samples(gpu_ctx):
+    """H, W not multiples of anything, t1 != t2, M > max(t), two channels, f64."""
+    rng = np.random.default_rng(11)
+    lat = rng.uniform(size=(2, 37, 53))
+    from cbp_synth import draw_kernel_pair
+    k1, k2 = draw_kernel_pair(rng, 4, 7, 9)
+    b1, b2 = oracle.blur_pair(lat, k1, k2)
+    g_lat, g_k1, g_k2, diag = run_gpu(gpu_ctx, b1[None], b2[None], 4, 7, "fp64", 0.0, "f64", m=9)
+    o = oracle_pair(b1, b2, 4, 7, 0.0, m=9)
+    assert rel(g_k1[0], o["k1"]) <= 1e-9 and rel(g_k2[0], o["k2"]) <= 1e-9
+    assert rel(g_k1[0], k1) <= 1e-9
+    assert rel(g_lat[0], o["latent"]) <= 1e-9
+
+
+def test_batch_invariance_and_determinism(gpu_ctx):
+    b1, b2, *_ , cfg = make_batch("video_480p", [4, 5, 6], h=96, w=128)
+    a_lat, a_k1, a_k2, _ = run_gpu(gpu_ctx, b1, b2, 9, 11, "mixed", cfg.eps, "f32")
+    b_lat, b_k1, b_k2, _ = run_gpu(gpu_ctx, b1, b2, 9, 11, "mixed", cfg.eps, "f32")
+    assert np.array_equal(a_lat, b_lat) and np.array_equal(a_k1, b_k1)
+    for i in range(3):
+        s_lat, s_k1, s_k2, _ = run_gpu(gpu_ctx, b1[i:i + 1], b2[i:i + 1], 9, 11, "mixed", cfg.eps, "f32")
+        assert np.array_equal(s_lat[0], a_lat[i]) and np.array_equal(s_k2[0], a_k2[i])
+
+
+def test_strided_frames_match_contiguous(gpu_ctx):
+    from paper_1203_4874_gb300 import cbp
+    b1, b2, *_ , cfg = make_batch("video_480p", [7], h=64, w=80)
+    prm = cbp.params(9, 11, path="fp64", eps=cfg.eps)
+    B1 = torch.from_numpy(b1).float().cuda()
+    B2 = torch.from_numpy(b2).float().cuda()
+    P1 = torch.zeros(B1.shape[:-1] + (B1.shape[-1] + 13,), device="cuda")
+    P1[..., :B1.shape[-1]] = B1
+    V1 = P1[..., :B1.shape[-1]]
+    l0, k0, _, _, _ = cbp.cbp_deblur_pair(gpu_ctx, B1, B2, prm)
+    l1, k1, _, _, _ = cbp.cbp_deblur_pair(gpu_ctx, V1, B2, prm)
+    torch.cuda.synchronize()
+    assert torch.equal(l0, l1) and torch.equal(k0, k1)
+
+
+def test_known_kernels_single_kernel_and_odd_grid(gpu_ctx):
+    from paper_1203_4874_gb300 import cbp
+    b1, b2, k1, k2, lat, cfg = make_batch("single_64", [1], fast=False)
+    eps = 1e-3
+    # deconvolution only, true kernels, odd FFT width
+    g_lat, *_ = run_gpu(gpu_ctx, b1, b2, 5, 5, "fp64", eps, "f64", flags=cbp.CBP_FLAG_KERNELS_IN,
+                        k1=k1, k2=k2, pad=(72, 75))
+    o = oracle.deconvolve_dual(b1[0], b2[0], k1[0], k2[0], 64, 64, eps, 72, 75)
+    assert rel(g_lat[0], o) <= 1e-9
+    # the paper's single-kernel form
+    g_lat, *_ = run_gpu(gpu_ctx, b1, b2, 5, 5, "fp64", eps, "f64",
+                        flags=cbp.CBP_FLAG_KERNELS_IN | cbp.CBP_FLAG_SINGLE_KERNEL, k1=k1, k2=k2)
+    o = oracle.deconvolve_dual(b1[0], b2[0], k1[0], np.zeros_like(k2[0]), 64, 64, eps)
+    assert rel(g_lat[0], o) <= 1e-9
+
+
+def test_host_io_matches_device_path(gpu_ctx):
+    from paper_1203_4874_gb300 import cbp
+    b1, b2, *_ , cfg = make_batch("video_480p", [8], h=64, w=96)
+    prm = cbp.params(9, 11, path="mixed", eps=cfg.eps)
+    B1 = torch.from_numpy(b1).float()
+    B2 = torch.from_numpy(b2).float()
+    ld, kd, _, _, _ = cbp.cbp_deblur_pair(gpu_ctx, B1.cuda(), B2.cuda(), prm)
+    prm_h = cbp.params(9, 11, path="mixed", eps=cfg.eps, flags=cbp.CBP_FLAG_HOST_IO)
+    lh, kh, _, _, _ = cbp.cbp_deblur_pair(gpu_ctx, B1.pin_memory(), B2.pin_memory(), prm_h)
+    torch.cuda.synchronize()
+    assert torch.equal(ld.cpu(), lh) and torch.equal(kd.cpu(), kh)
+
+
+def test_non_finite_input_is_reported(gpu_ctx):
+    b1, b2, *_ = make_batch("single_64", [2], fast=False)
+    b1 = b1.copy()
+    b1[0, 0, 10, 10] = np.nan
+    *_, diag = run_gpu(gpu_ctx, b1, b2, 5, 5, "fp64", 0.0, "f64")
+    assert diag[0]["status"] == -1
+
+
+def test_forward_model_matches_oracle(gpu_ctx):
+    from paper_1203_4874_gb300 import cbp
+    rng = np.random.default_rng(12)
+    lat = rng.uniform(size=(2, 1, 33, 45))
+    ks = np.stack([rng.uniform(size=(6, 6)) for _ in range(2)])
+    out = cbp.cbp_forward_blur(gpu_ctx, torch.from_numpy(lat).cuda(), torch.from_numpy(ks).cuda())
+    torch.cuda.synchronize()
+    for i in range(2):
+        assert rel(out[i, 0].cpu().numpy(), oracle.blur_full(lat[i, 0], ks[i])) <= 1e-14
