@@ -187,6 +187,25 @@ cbp_status cbp_estimate_kernels_stages(cbp_ctx* ctx, const cbp_frames* b1, const
                                        const cbp_params* params, void* k1, void* k2,
                                        cbp_diag* diag, const cbp_stage_out* out, void* stream);
 
+/* cbp_estimate_kernels without any device allocation and without a context.
+ * The paper has no counterpart: this serves callers that may not allocate
+ * device memory -- code under a memory manager that owns every allocation,
+ * real-time paths that must not fail on an allocation, deployments that keep
+ * a fixed device footprint.  The workspace is a fixed 8 MiB device array in
+ * the library (held by every GPU that loads it until the process exits);
+ * problems whose estimation workspace (cbp_workspace_size without the
+ * deconvolution buffers) exceeds it return CBP_ERR_UNSUPPORTED -- one
+ * 1080p RGB pair fits on either path.  Inputs and outputs are as in
+ * cbp_estimate_kernels (device buffers; CBP_FLAG_HOST_IO and
+ * CBP_FLAG_KERNELS_IN are rejected with CBP_ERR_INVALID_ARG).
+ * The first call on a device looks up the array's address with that device
+ * current: make it before any stream capture.  Every call shares the array and
+ * finds the previous call's data in it; calls that overlap on the GPU race on
+ * it, so the caller must order them (one stream, or synchronise). */
+cbp_status cbp_estimate_kernels_noalloc(const cbp_frames* b1, const cbp_frames* b2,
+                                        const cbp_params* params, void* k1, void* k2,
+                                        cbp_diag* diag, void* stream);
+
 /* Kernel estimation (as above, unless CBP_FLAG_KERNELS_IN) followed by the
  * dual-kernel Fourier deconvolution on a pad_h x pad_w grid:
  *   I^ = (conj(K1^) B1^ + conj(K2^) B2^) / (|K1^|^2 + |K2^|^2 + eps),

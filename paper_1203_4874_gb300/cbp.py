@@ -28,7 +28,7 @@ EXPORTED = [
     "cbp_create", "cbp_destroy", "cbp_status_string", "cbp_workspace_size",
     "cbp_estimate_kernels", "cbp_deblur_pair", "cbp_forward_blur", "cbp_synth_latent",
     "cbp_stream_submit", "cbp_stream_poll", "cbp_stream_stats", "cbp_profile", "cbp_stage_times",
-    "cbp_estimate_kernels_stages",
+    "cbp_estimate_kernels_stages", "cbp_estimate_kernels_noalloc",
 ]
 STAGES = ["eval", "sample_solve", "scale_solve", "kernel_spectra", "row_fft", "col_deconv",
           "row_ifft", "h2d", "d2h"]
@@ -90,6 +90,7 @@ def lib() -> ctypes.CDLL:
             "cbp_stream_stats": ([c_void_p, POINTER(c_uint64), POINTER(c_double), POINTER(c_double),
                                   c_int32], c_int),
             "cbp_profile": ([c_void_p, c_int32], c_int),
+            "cbp_estimate_kernels_noalloc": ([fr, fr, pr, c_void_p, c_void_p, dg, c_void_p], c_int),
             "cbp_estimate_kernels_stages": ([c_void_p, fr, fr, pr, c_void_p, c_void_p, dg,
                                              POINTER(cbp_stage_out), c_void_p], c_int),
             "cbp_stage_times": ([c_void_p, POINTER(c_double), POINTER(c_int64)], c_int),
@@ -285,3 +286,16 @@ def cbp_estimate_kernels_stages(ctx, b1: torch.Tensor, b2: torch.Tensor, prm: cb
     _check(st, "cbp_estimate_kernels_stages")
     out["k1"], out["k2"], out["diag"] = k1, k2, d
     return out
+
+
+def cbp_estimate_kernels_noalloc(b1: torch.Tensor, b2: torch.Tensor, prm: cbp_params, k1: torch.Tensor,
+                                 k2: torch.Tensor, diag: bool = True, stream=None):
+    """Kernel estimation in the library's fixed device scratch array, for callers
+    that may not allocate device memory: the caller supplies k1, k2; nothing is
+    allocated on the device.  Returns (diag list or None, status)."""
+    n = _batch(b1)
+    d = (cbp_diag * n)() if diag else None
+    s = lib().cbp_estimate_kernels_noalloc(byref(frames(b1)), byref(frames(b2)), byref(prm),
+                                           k1.data_ptr(), k2.data_ptr(), d, _stream_ptr(stream))
+    _check(s, "cbp_estimate_kernels_noalloc")
+    return d, s

@@ -1,0 +1,89 @@
+// Kernel estimation without any device allocation, for callers that may not
+// allocate device memory.
+//
+// Some callers cannot call cudaMalloc (or anything that allocates) at the
+// point where they need the kernels: code running under a memory manager
+// that owns every device allocation (a custom pool or a fixed arena), code
+// that must not fail on allocation in the middle of a real-time video path,
+// and code that has to keep its device footprint fixed from start-up.  This
+// entry point runs the same estimation kernels as cbp_estimate_kernels, with
+// their workspace placed in one file-scope device array of a fixed size
+// (kNoAllocScratchBytes) that every GPU loading the library holds until the
+// process exits.
+//
+// Set-up: the first call on each device looks the array's device address up
+// (cudaGetSymbolAddress) with that device current and caches it, so make the
+// first call on a device before capturing any stream.  All calls share the
+// one array and it keeps the previous call's contents: calls whose work
+// overlaps on the GPU (different streams, or host threads without ordering)
+// race on it and must be serialised by the caller.
+#include <cuda_runtime.h>
+#include <mutex>
+#include "cbp.h"
+#include "cbp_internal.h"
+
+namespace cbp {
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 8u << 20;   // 8 MiB
+constexpr int kMaxDevices = 64;
+
+static __device__ __align__(256) char g_noalloc_scratch[kNoAllocScratchBytes];
+
+std::mutex g_setup_mu;
+char* g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of the scratch array on the current device (looked up once).
+cbp_status scratch_for_current_device(char** out) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return CBP_ERR_CUDA;
+  }
+  std::lock_guard<std::mutex> g(g_setup_mu);
+  if (!g_scratch_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return CBP_ERR_CUDA;
+    }
+    g_scratch_ptr[dev] = (char*)p;
+  }
+  *out = g_scratch_ptr[dev];
+  return CBP_OK;
+}
+
+}  // namespace
+}  // namespace cbp
+
+extern "C" cbp_status cbp_estimate_kernels_noalloc(const cbp_frames* b1, const cbp_frames* b2,
+                                                   const cbp_params* params, void* k1, void* k2,
+                                                   cbp_diag* diag, void* stream) {
+  using namespace cbp;
+  if (!params || !k1 || !k2) return CBP_ERR_INVALID_ARG;
+  if (params->flags & (CBP_FLAG_HOST_IO | CBP_FLAG_KERNELS_IN)) return CBP_ERR_INVALID_ARG;
+  Plan p;
+  cbp_status s = make_plan(b1, b2, params, &p);
+  if (s != CBP_OK) return s;
+  // The estimation buffers come first in the plan's layout; the deconvolution
+  // buffers (from the twiddle tables on) are not used here.
+  const size_t need = p.off_tw_h;
+  if (need > kNoAllocScratchBytes) return CBP_ERR_UNSUPPORTED;
+  char* ws = nullptr;
+  s = scratch_for_current_device(&ws);
+  if (s != CBP_OK) return s;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int kf64 = b1->dtype == CBP_F64 || (params->flags & CBP_FLAG_KERNELS_F64);
+  const FrameDesc d1 = frame_desc(b1, nullptr), d2 = frame_desc(b2, nullptr);
+  // the non-finite flags accumulate with atomics: they must start at zero
+  if (cudaMemsetAsync(ws + p.off_bad, 0, (size_t)p.n * sizeof(int), st) != cudaSuccess)
+    return CBP_ERR_CUDA;
+  launch_eval(p, d1, d2, ws, st);
+  launch_sample_solve(p, ws, st);
+  launch_scale_solve(p, ws, k1, k2, kf64, st);
+  if (cudaGetLastError() != cudaSuccess) return CBP_ERR_CUDA;
+  if (diag && cudaMemcpyAsync(diag, ws + p.off_diag, (size_t)p.n * sizeof(cbp_diag),
+                              cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return CBP_ERR_CUDA;
+  return CBP_OK;
+}
