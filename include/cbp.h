@@ -54,13 +54,14 @@ typedef enum cbp_dtype { CBP_F32 = 0, CBP_F64 = 1 } cbp_dtype;
 /* Arithmetic of the kernel-estimation path.
  *   FP64:  evaluation, Gram and per-sample solves in double precision (the
  *          per-sample eigen-solve runs in single precision and is refined to
- *          double precision against the double-precision Gram and the exact
- *          residual).  Deconvolution in the frames' dtype.
- *   MIXED: evaluation in single precision; Gram of the non-constant samples
- *          in single precision; the z = 1 sample (real, highest signal-to-noise,
- *          smallest relative eigen-gap) in double precision; eigen-solves in
- *          single precision refined in double precision; scale fix in double
- *          precision; deconvolution in single precision.
+ *          double precision against the double-precision Gram and two
+ *          exact-residual steps).  Deconvolution in the frames' dtype.
+ *   MIXED: evaluation with single-precision arithmetic (float frames are
+ *          folded with an exact hi + lo float accumulation, samples kept in
+ *          double); Gram of the samples other than z = 1 in single precision;
+ *          eigen-solves in single precision refined in double precision (one
+ *          exact-residual step); scale fix in double precision;
+ *          deconvolution in single precision.
  *   LEARNED: a network proposal checked by the consistency residual, falling
  *          back to MIXED (see cbp_learned_*). */
 typedef enum cbp_path { CBP_PATH_FP64 = 0, CBP_PATH_MIXED = 1, CBP_PATH_LEARNED = 2 } cbp_path;
@@ -162,9 +163,9 @@ cbp_status cbp_estimate_kernels(cbp_ctx* ctx, const cbp_frames* b1, const cbp_fr
  * member is NULL (skipped) or a caller-owned device buffer the library copies
  * into (on the stream, after the estimation).  s = m/2 + 1 solved samples per
  * direction (samples m - j are the conjugates of samples j); complex values
- * are (re, im) pairs; "T" is double on the FP64 path and float on the others.
- *   p_z2[k]: T complex [n][c][s][H_Bk]  samples of B_k at z2 = w^j (Eq. 3)
- *   p_z1[k]: T complex [n][c][s][W_Bk]  samples of B_k at z1 = w^i
+ * are (re, im) pairs.
+ *   p_z2[k]: double complex [n][c][s][H_Bk]  samples of B_k at z2 = w^j (Eq. 3)
+ *   p_z1[k]: double complex [n][c][s][W_Bk]  samples of B_k at z1 = w^i
  *   x_z2, x_z1: double complex [n][s][t1+t2] unit null vectors [u; v] per sample
  *   sample_diag: double [n][2][s][4]: lambda_max, second smallest eigenvalue and
  *            Rayleigh quotient of the per-sample normal matrix, 1 if solved by

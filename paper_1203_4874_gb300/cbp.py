@@ -166,15 +166,25 @@ def _batch(t: torch.Tensor) -> int:
     return t.shape[0] if t.dim() == 4 else 1
 
 
+def _out(t, shape, dtype, device, what):
+    """Allocate an output, or check a caller-supplied one: the library writes
+    raw memory and cannot check sizes itself."""
+    if t is None:
+        pin = device.type == "cpu" and torch.cuda.is_available()
+        return torch.empty(shape, dtype=dtype, device=device, pin_memory=pin)
+    if tuple(t.shape) != tuple(shape) or t.dtype != dtype or t.device != device or not t.is_contiguous():
+        raise ValueError(f"{what}: expected contiguous {tuple(shape)} {dtype} on {device}, got "
+                         f"{tuple(t.shape)} {t.dtype} on {t.device}")
+    return t
+
+
 def cbp_estimate_kernels(ctx, b1: torch.Tensor, b2: torch.Tensor, prm: cbp_params, k1=None, k2=None,
                          diag: bool = True, stream=None):
     """Returns (k1, k2, diag list or None, status).  k1: (n, t1, t1) like b1."""
     n = _batch(b1)
     kdt = torch.float64 if prm.flags & CBP_FLAG_KERNELS_F64 else b1.dtype
-    if k1 is None:
-        k1 = torch.empty((n, prm.t1, prm.t1), dtype=kdt, device=b1.device)
-    if k2 is None:
-        k2 = torch.empty((n, prm.t2, prm.t2), dtype=kdt, device=b1.device)
+    k1 = _out(k1, (n, prm.t1, prm.t1), kdt, b1.device, "k1")
+    k2 = _out(k2, (n, prm.t2, prm.t2), kdt, b1.device, "k2")
     d = (cbp_diag * n)() if diag else None
     s = lib().cbp_estimate_kernels(ctx, byref(frames(b1)), byref(frames(b2)), byref(prm),
                                    k1.data_ptr(), k2.data_ptr(), d, _stream_ptr(stream))
@@ -193,15 +203,17 @@ def cbp_deblur_pair(ctx, b1: torch.Tensor, b2: torch.Tensor, prm: cbp_params, k1
         v1 = v1.unsqueeze(0)
     n, c, h1, w1 = v1.shape
     hh, ww = h1 - prm.t1 + 1, w1 - prm.t1 + 1
-    pin = bool(prm.flags & CBP_FLAG_HOST_IO) and b1.device.type == "cpu"
-    if latent is None:
-        latent = torch.empty((n, c, hh, ww), dtype=b1.dtype, device=b1.device, pin_memory=pin)
+    if (b1.device.type == "cpu") != bool(prm.flags & CBP_FLAG_HOST_IO):
+        raise ValueError("host tensors need CBP_FLAG_HOST_IO and device tensors must not set it")
+    latent = _out(latent, (n, c, hh, ww), b1.dtype, b1.device, "latent")
     kin = bool(prm.flags & CBP_FLAG_KERNELS_IN)
     kdt = torch.float64 if prm.flags & CBP_FLAG_KERNELS_F64 else b1.dtype
-    if k1 is None and not kin:
-        k1 = torch.empty((n, prm.t1, prm.t1), dtype=kdt, device=b1.device, pin_memory=pin)
-    if k2 is None and not kin:
-        k2 = torch.empty((n, prm.t2, prm.t2), dtype=kdt, device=b1.device, pin_memory=pin)
+    if kin and (k1 is None or k2 is None):
+        raise ValueError("CBP_FLAG_KERNELS_IN needs k1 and k2")
+    if k1 is not None or not kin:
+        k1 = _out(k1, (n, prm.t1, prm.t1), kdt, b1.device, "k1")
+    if k2 is not None or not kin:
+        k2 = _out(k2, (n, prm.t2, prm.t2), kdt, b1.device, "k2")
     d = (cbp_diag * n)() if diag else None
     s = lib().cbp_deblur_pair(ctx, byref(frames(b1)), byref(frames(b2)), byref(prm),
                               k1.data_ptr() if k1 is not None else None,
@@ -214,11 +226,14 @@ def cbp_deblur_pair(ctx, b1: torch.Tensor, b2: torch.Tensor, prm: cbp_params, k1
 def cbp_forward_blur(ctx, latent: torch.Tensor, kernels: torch.Tensor, sigma: float = 0.0,
                      seed: int = 0, out=None, stream=None) -> torch.Tensor:
     """Eq. 1 on the device: latent (n, c, h, w), kernels (n, t, t) float64."""
+    if not latent.is_contiguous() or latent.dim() != 4:
+        raise ValueError("latent must be a contiguous (n, c, h, w) tensor")
     n, c, h, w = latent.shape
     t = kernels.shape[-1]
     kd = kernels.to(torch.float64).contiguous()
-    if out is None:
-        out = torch.empty((n, c, h + t - 1, w + t - 1), dtype=latent.dtype, device=latent.device)
+    if kd.shape != (n, t, t):
+        raise ValueError("kernels must be (n, t, t)")
+    out = _out(out, (n, c, h + t - 1, w + t - 1), latent.dtype, latent.device, "out")
     s = lib().cbp_forward_blur(ctx, latent.data_ptr(), n, c, h, w,
                                CBP_F64 if latent.dtype == torch.float64 else CBP_F32,
                                kd.data_ptr(), t, sigma, seed, out.data_ptr(), _stream_ptr(stream))
@@ -232,8 +247,9 @@ def cbp_synth_latent(ctx, blobs: torch.Tensor, n: int, c: int, h: int, w: int,
     """Blob latent on the device; blobs (n, c, nblobs, 4) float64 rows (a, sigma, cx, cy)."""
     bl = blobs.to(torch.float64).contiguous()
     nb = bl.shape[-2]
-    if out is None:
-        out = torch.empty((n, c, h, w), dtype=dtype, device=bl.device)
+    if tuple(bl.shape) != (n, c, nb, 4):
+        raise ValueError("blobs must be (n, c, nblobs, 4)")
+    out = _out(out, (n, c, h, w), dtype, bl.device, "out")
     s = lib().cbp_synth_latent(ctx, bl.data_ptr(), nb, n, c, h, w,
                                CBP_F64 if dtype == torch.float64 else CBP_F32, floor_amp, seed,
                                out.data_ptr(), _stream_ptr(stream))
@@ -262,7 +278,7 @@ def cbp_estimate_kernels_stages(ctx, b1: torch.Tensor, b2: torch.Tensor, prm: cb
     m = prm.m or max(prm.t1, prm.t2)
     s = m // 2 + 1
     nn = prm.t1 + prm.t2
-    ct = torch.complex128 if prm.path == CBP_PATH_FP64 else torch.complex64
+    ct = torch.complex128
     dev = b1.device
     out = {
         "p_z2": [torch.empty((n, c, s, v.shape[2]), dtype=ct, device=dev) for v in (v1, v2)],
@@ -277,8 +293,9 @@ def cbp_estimate_kernels_stages(ctx, b1: torch.Tensor, b2: torch.Tensor, prm: cb
                        (c_void_p * 2)(*[t.data_ptr() for t in out["p_z1"]]),
                        out["x_z2"].data_ptr(), out["x_z1"].data_ptr(), out["sample_diag"].data_ptr(),
                        out["lifted"].data_ptr(), out["kernels"].data_ptr())
-    k1 = torch.empty((n, prm.t1, prm.t1), dtype=b1.dtype, device=dev)
-    k2 = torch.empty((n, prm.t2, prm.t2), dtype=b1.dtype, device=dev)
+    kdt = torch.float64 if prm.flags & CBP_FLAG_KERNELS_F64 else b1.dtype
+    k1 = torch.empty((n, prm.t1, prm.t1), dtype=kdt, device=dev)
+    k2 = torch.empty((n, prm.t2, prm.t2), dtype=kdt, device=dev)
     d = (cbp_diag * n)()
     st = lib().cbp_estimate_kernels_stages(ctx, byref(frames(b1)), byref(frames(b2)), byref(prm),
                                            k1.data_ptr(), k2.data_ptr(), d, byref(so),
@@ -294,6 +311,9 @@ def cbp_estimate_kernels_noalloc(b1: torch.Tensor, b2: torch.Tensor, prm: cbp_pa
     that may not allocate device memory: the caller supplies k1, k2; nothing is
     allocated on the device.  Returns (diag list or None, status)."""
     n = _batch(b1)
+    kdt = torch.float64 if prm.flags & CBP_FLAG_KERNELS_F64 else b1.dtype
+    _out(k1, (n, prm.t1, prm.t1), kdt, b1.device, "k1")
+    _out(k2, (n, prm.t2, prm.t2), kdt, b1.device, "k2")
     d = (cbp_diag * n)() if diag else None
     s = lib().cbp_estimate_kernels_noalloc(byref(frames(b1)), byref(frames(b2)), byref(prm),
                                            k1.data_ptr(), k2.data_ptr(), d, _stream_ptr(stream))

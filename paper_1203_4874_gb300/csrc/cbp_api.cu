@@ -195,7 +195,7 @@ struct DeviceGuard {
 
 cbp_status copy_stages(const Plan& p, const char* ws, const cbp_stage_out* o, cudaStream_t st) {
   if (!o) return CBP_OK;
-  const size_t te = p.mixed ? 8 : 16;
+  const size_t te = 16;   // double samples on both paths
   const size_t n = p.n, C = p.C, ns = p.ns;
   struct Item { void* dst; size_t off, bytes; };
   const Item items[] = {

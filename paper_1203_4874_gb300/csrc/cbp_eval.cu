@@ -12,8 +12,10 @@
 // block per row/column, one shared-memory reduction per sample) re-reads the
 // frame once per sample; the fold makes the cost independent of M.
 //
-// Mixed path: bins and samples in float, plus the z = 1 sample (s = 0) as the
-// double-precision sum of the float bins, kept separately (it is real).
+// Float32 frames are folded with an exact float TwoSum accumulation (hi + lo),
+// so the bins -- and the samples, whose M-point DFT runs in double -- carry
+// ~1e-14 relative error on both paths; the mixed path also keeps a float copy
+// of the samples for its single-precision Gram.
 #include "cbp_common.cuh"
 #include "cbp_internal.h"
 
@@ -32,19 +34,51 @@ __device__ __forceinline__ void root_table(cd* tab, int M) {
 }
 
 struct EvalOut {
-  void* pz[2];        // cpx<T> [n][C][ns][len_k]
-  double* dc[2];      // optional, [n][C][len_k]
+  cd* pz[2];          // [n][C][ns][len_k] double samples
+  cf* pzf[2];         // optional single-precision copies (mixed path)
   int* bad;           // [n]
 };
+
+// Running sum of float terms kept exactly as hi + lo (Knuth's TwoSum), so a
+// fold of float32 frames is accurate to ~1e-14 using float arithmetic only.
+struct TwoSum {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = hi + x;
+    const float z = t - hi;
+    lo += (hi - (t - z)) + (x - z);
+    hi = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+struct DoubleSum {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ double value() const { return v; }
+};
+
+// M-point DFT of double bins b[0..M) at sample s: sum_m b[m] w^(s m).
+__device__ __forceinline__ cd bins_dft(const double* b, int bstride, const cd* wtab, int M, int s) {
+  cd p = mk(0.0, 0.0);
+  int e = 0;
+  for (int mm = 0; mm < M; ++mm) {
+    const double v = b[mm * bstride];
+    p.re += v * wtab[e].re;
+    p.im += v * wtab[e].im;
+    e += s;
+    if (e >= M) e -= M;
+  }
+  return p;
+}
 
 // One warp per row.  Lane l (l < g*M, g = floor(32/M)) owns bin m = l mod M
 // and block-group q = l / M; at step k it reads column (k*g + q)*M + m, so
 // the warp reads g*M consecutive elements per step.
-template <typename T>
+template <typename Acc, typename In>
 __global__ void __launch_bounds__(kRowWarps * 32)
 k_eval_rows(FrameDesc f1, FrameDesc f2, int M, int ns, EvalOut out) {
   __shared__ cd wtab[kMaxM];
-  __shared__ T bins[kRowWarps][32];
+  __shared__ double bins[kRowWarps][32];
   root_table(wtab, M);
   __syncthreads();
   const FrameDesc& fr = blockIdx.z ? f2 : f1;
@@ -55,45 +89,33 @@ k_eval_rows(FrameDesc f1, FrameDesc f2, int M, int ns, EvalOut out) {
   if (r >= fr.h) return;                     // whole warp leaves together
   const int g = 32 / M;
   const int m = lane % M, q = lane / M;
-  const void* fb = frame_base(fr, f);
-  const int64_t base = (int64_t)ch * fr.cs + (int64_t)r * fr.rs;
-  T acc = 0;
-  if (q < g) {
-    for (int c = q * M + m; c < fr.w; c += g * M) acc += ld_frame<T>(fb, base + c, fr.f64);
-  }
-  bins[warp][lane] = acc;
+  const In* row = (const In*)frame_base(fr, f) + (int64_t)ch * fr.cs + (int64_t)r * fr.rs;
+  Acc acc;
+  if (q < g)
+    for (int c = q * M + m; c < fr.w; c += g * M) acc.add(__ldg(row + c));
+  bins[warp][lane] = acc.value();
   __syncwarp();
   if (lane < M) {
-    T s = 0;
-    for (int qq = 0; qq < g; ++qq) s += bins[warp][qq * M + lane];
-    bins[warp][lane] = s;   // each lane only rewrites its own slot after reading
+    double v = 0;
+    for (int qq = 0; qq < g; ++qq) v += bins[warp][qq * M + lane];
+    bins[warp][lane] = v;   // each lane only rewrites its own slot after reading
   }
   __syncwarp();
   if (lane < ns) {
-    cpx<T> p = mk<T>(0, 0);
-    for (int mm = 0; mm < M; ++mm) {
-      cd w = wtab[(lane * mm) % M];
-      T b = bins[warp][mm];
-      p.re += b * (T)w.re;
-      p.im += b * (T)w.im;
-    }
-    cpx<T>* dst = (cpx<T>*)out.pz[blockIdx.z];
-    dst[((int64_t)fc * ns + lane) * fr.h + r] = p;
-  }
-  if (out.dc[blockIdx.z] && lane == 0) {
-    double s = 0;
-    for (int mm = 0; mm < M; ++mm) s += (double)bins[warp][mm];
-    out.dc[blockIdx.z][(int64_t)fc * fr.h + r] = s;
+    const cd pv = bins_dft(&bins[warp][0], 1, wtab, M, lane);
+    const int64_t o = ((int64_t)fc * ns + lane) * fr.h + r;
+    out.pz[blockIdx.z][o] = pv;
+    if (out.pzf[blockIdx.z]) out.pzf[blockIdx.z][o] = cvt<float>(pv);
   }
 }
 
 // One thread per column.  Bin m sums rows m, m + M, m + 2M, ...; a warp reads
 // 32 consecutive columns of one row per step.  Also flags non-finite input.
-template <typename T>
+template <typename Acc, typename In>
 __global__ void __launch_bounds__(kColThreads)
 k_eval_cols(FrameDesc f1, FrameDesc f2, int M, int ns, EvalOut out) {
   __shared__ cd wtab[kMaxM];
-  __shared__ T bins[kMaxM][kColThreads];
+  __shared__ double bins[kMaxM][kColThreads];
   root_table(wtab, M);
   __syncthreads();
   const FrameDesc& fr = blockIdx.z ? f2 : f1;
@@ -102,42 +124,34 @@ k_eval_cols(FrameDesc f1, FrameDesc f2, int M, int ns, EvalOut out) {
   const int col = blockIdx.x * kColThreads + threadIdx.x;
   if (blockIdx.x * kColThreads >= fr.w) return;   // uniform per block
   const bool active = col < fr.w;
-  const void* fb = frame_base(fr, f);
-  const int64_t base = (int64_t)ch * fr.cs + col;
+  const In* base = (const In*)frame_base(fr, f) + (int64_t)ch * fr.cs + col;
   bool finite = true;
   for (int m = 0; m < M; ++m) {
-    T acc = 0;
+    Acc acc;
     if (active) {
       int r = m;
       for (; r + 3 * M < fr.h; r += 4 * M) {
-        T a0 = ld_frame<T>(fb, base + (int64_t)r * fr.rs, fr.f64);
-        T a1 = ld_frame<T>(fb, base + (int64_t)(r + M) * fr.rs, fr.f64);
-        T a2 = ld_frame<T>(fb, base + (int64_t)(r + 2 * M) * fr.rs, fr.f64);
-        T a3 = ld_frame<T>(fb, base + (int64_t)(r + 3 * M) * fr.rs, fr.f64);
-        acc += (a0 + a1) + (a2 + a3);
+        const In a0 = __ldg(base + (int64_t)r * fr.rs);
+        const In a1 = __ldg(base + (int64_t)(r + M) * fr.rs);
+        const In a2 = __ldg(base + (int64_t)(r + 2 * M) * fr.rs);
+        const In a3 = __ldg(base + (int64_t)(r + 3 * M) * fr.rs);
+        acc.add(a0);
+        acc.add(a1);
+        acc.add(a2);
+        acc.add(a3);
       }
-      for (; r < fr.h; r += M) acc += ld_frame<T>(fb, base + (int64_t)r * fr.rs, fr.f64);
-      finite = finite && isfinite(acc);
+      for (; r < fr.h; r += M) acc.add(__ldg(base + (int64_t)r * fr.rs));
+      finite = finite && isfinite(acc.value());
     }
-    bins[m][threadIdx.x] = acc;
+    bins[m][threadIdx.x] = acc.value();
   }
   if (!finite) atomicOr(out.bad + f, 1);
   if (!active) return;
-  cpx<T>* dst = (cpx<T>*)out.pz[blockIdx.z];
   for (int s = 0; s < ns; ++s) {
-    cpx<T> p = mk<T>(0, 0);
-    for (int mm = 0; mm < M; ++mm) {
-      cd w = wtab[(s * mm) % M];
-      T b = bins[mm][threadIdx.x];
-      p.re += b * (T)w.re;
-      p.im += b * (T)w.im;
-    }
-    dst[((int64_t)fc * ns + s) * fr.w + col] = p;
-  }
-  if (out.dc[blockIdx.z]) {
-    double s = 0;
-    for (int mm = 0; mm < M; ++mm) s += (double)bins[mm][threadIdx.x];
-    out.dc[blockIdx.z][(int64_t)fc * fr.w + col] = s;
+    const cd pv = bins_dft(&bins[0][threadIdx.x], kColThreads, wtab, M, s);
+    const int64_t o = ((int64_t)fc * ns + s) * fr.w + col;
+    out.pz[blockIdx.z][o] = pv;
+    if (out.pzf[blockIdx.z]) out.pzf[blockIdx.z][o] = cvt<float>(pv);
   }
 }
 
@@ -147,22 +161,22 @@ void launch_eval(const Plan& p, const FrameDesc& b1, const FrameDesc& b2, char* 
                  cudaStream_t st) {
   EvalOut rows, cols;
   for (int k = 0; k < 2; ++k) {
-    rows.pz[k] = ws + p.off_pz2[k];
-    cols.pz[k] = ws + p.off_pz1[k];
-    rows.dc[k] = p.mixed ? (double*)(ws + p.off_dcz2[k]) : nullptr;
-    cols.dc[k] = p.mixed ? (double*)(ws + p.off_dcz1[k]) : nullptr;
+    rows.pz[k] = (cd*)(ws + p.off_pz2[k]);
+    cols.pz[k] = (cd*)(ws + p.off_pz1[k]);
+    rows.pzf[k] = p.mixed ? (cf*)(ws + p.off_pz2f[k]) : nullptr;
+    cols.pzf[k] = p.mixed ? (cf*)(ws + p.off_pz1f[k]) : nullptr;
   }
   rows.bad = cols.bad = (int*)(ws + p.off_bad);
   const int hmax = b1.h > b2.h ? b1.h : b2.h;
   const int wmax = b1.w > b2.w ? b1.w : b2.w;
   dim3 gr((hmax + kRowWarps - 1) / kRowWarps, p.n * p.C, 2);
   dim3 gc((wmax + kColThreads - 1) / kColThreads, p.n * p.C, 2);
-  if (p.mixed) {
-    k_eval_rows<float><<<gr, kRowWarps * 32, 0, st>>>(b1, b2, p.M, p.ns, rows);
-    k_eval_cols<float><<<gc, kColThreads, 0, st>>>(b1, b2, p.M, p.ns, cols);
-  } else {
-    k_eval_rows<double><<<gr, kRowWarps * 32, 0, st>>>(b1, b2, p.M, p.ns, rows);
-    k_eval_cols<double><<<gc, kColThreads, 0, st>>>(b1, b2, p.M, p.ns, cols);
+  if (b1.f64) {   // double frames: double sums
+    k_eval_rows<DoubleSum, double><<<gr, kRowWarps * 32, 0, st>>>(b1, b2, p.M, p.ns, rows);
+    k_eval_cols<DoubleSum, double><<<gc, kColThreads, 0, st>>>(b1, b2, p.M, p.ns, cols);
+  } else {        // float frames: exact float TwoSum accumulation
+    k_eval_rows<TwoSum, float><<<gr, kRowWarps * 32, 0, st>>>(b1, b2, p.M, p.ns, rows);
+    k_eval_cols<TwoSum, float><<<gc, kColThreads, 0, st>>>(b1, b2, p.M, p.ns, cols);
   }
 }
 

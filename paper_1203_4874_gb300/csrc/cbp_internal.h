@@ -51,8 +51,8 @@ struct Plan {
   double eps;
   FftPlan fp_h, fp_w, fp_w2;   // plans of Ph, Pw, Pw/2
   // workspace layout (byte offsets into one device allocation)
-  size_t off_pz2[2], off_pz1[2];   // cpx<T_eval> [n][C][ns][len]
-  size_t off_dcz2[2], off_dcz1[2]; // double [n][C][len] (mixed path: z = 1 sample)
+  size_t off_pz2[2], off_pz1[2];   // cd [n][C][ns][len] sample polynomials (double)
+  size_t off_pz2f[2], off_pz1f[2]; // cf copies for the single-precision Gram (mixed path)
   size_t off_x;                    // cd [n][2][ns][nn]
   size_t off_sdiag;                // double [n][2][ns][4]
   size_t off_resid;                // cd [n][2][ns][C][Lmax] (FP64 path residual scratch)

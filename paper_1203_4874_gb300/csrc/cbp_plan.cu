@@ -124,21 +124,20 @@ cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_param
     return o;
   };
   const size_t n = p.n, C = p.C, ns = p.ns;
-  const size_t te = p.mixed ? 8 : 16;  // sizeof(cpx<T_eval>)
-  p.off_pz2[0] = take(n * C * ns * p.H1 * te);
-  p.off_pz2[1] = take(n * C * ns * p.H2 * te);
-  p.off_pz1[0] = take(n * C * ns * p.W1 * te);
-  p.off_pz1[1] = take(n * C * ns * p.W2 * te);
+  p.off_pz2[0] = take(n * C * ns * p.H1 * 16);
+  p.off_pz2[1] = take(n * C * ns * p.H2 * 16);
+  p.off_pz1[0] = take(n * C * ns * p.W1 * 16);
+  p.off_pz1[1] = take(n * C * ns * p.W2 * 16);
   if (p.mixed) {
-    p.off_dcz2[0] = take(n * C * p.H1 * 8);
-    p.off_dcz2[1] = take(n * C * p.H2 * 8);
-    p.off_dcz1[0] = take(n * C * p.W1 * 8);
-    p.off_dcz1[1] = take(n * C * p.W2 * 8);
+    p.off_pz2f[0] = take(n * C * ns * p.H1 * 8);
+    p.off_pz2f[1] = take(n * C * ns * p.H2 * 8);
+    p.off_pz1f[0] = take(n * C * ns * p.W1 * 8);
+    p.off_pz1f[1] = take(n * C * ns * p.W2 * 8);
   }
   p.off_x = take(n * 2 * ns * p.nn * 16);
   p.off_sdiag = take(n * 2 * ns * 4 * 8);
   p.Lmax = std::max(p.H1, p.W1) + t2 - 1;
-  const size_t resid = p.mixed ? 0 : n * 2 * ns * C * (size_t)p.Lmax * 16;
+  const size_t resid = n * 2 * ns * C * (size_t)p.Lmax * 16;
   const size_t abytes = n * 4 * (size_t)p.M * p.M * 16;
   p.off_resid = take(std::max(resid, abytes));
   p.off_kd = take(n * (size_t)(t1 * t1 + t2 * t2) * 8);

@@ -274,15 +274,12 @@ __device__ void newton_eigbasis64(EigSmem& S, const cd* V, const double* lam, in
   normalize64(S.x, n, S.red);
 }
 
-struct NoApply {
-  __device__ void operator()(const cd*, cd*) const {}
-};
 
 // Smallest eigenpair of the Hermitian positive semi-definite S.G (n x n).
-// With `accurate`, one more Newton step uses apply(x, out) = S^H S x computed
-// from the original system.  Result vector in S.x (unit norm).
+// acc_steps further Newton steps use apply(x, out) = S^H S x computed from the
+// original system (exact residual).  Result vector in S.x (unit norm).
 template <class Apply>
-__device__ EigResult smallest_eigvec(EigSmem& S, int n, bool accurate, const Apply& apply) {
+__device__ EigResult smallest_eigvec(EigSmem& S, int n, int acc_steps, const Apply& apply) {
   const int np = np_of(n);
   if (threadIdx.x == 0) {
     double gs = 0;
@@ -332,8 +329,7 @@ __device__ EigResult smallest_eigvec(EigSmem& S, int n, bool accurate, const App
       theta = dotre64(S.x, S.r, n, S.red);
       if (newton_eigbasis(S, n, imin, S.r, theta) < 1e-30) break;
     }
-    if (accurate)
-      for (int it = 0; it < 2; ++it) {
+    for (int it = 0; it < acc_steps; ++it) {
         apply(S.x, S.r);
         theta = dotre64(S.x, S.r, n, S.red);
         newton_eigbasis(S, n, imin, S.r, theta);
@@ -372,7 +368,7 @@ __device__ EigResult smallest_eigvec(EigSmem& S, int n, bool accurate, const App
     for (int i = threadIdx.x; i < n; i += blockDim.x) S.x[i] = V64[i * ld + i1];
     __syncthreads();
     normalize64(S.x, n, S.red);
-    if (accurate) {
+    if (acc_steps > 0) {
       apply(S.x, S.r);
       theta = dotre64(S.x, S.r, n, S.red);
       newton_eigbasis64(S, V64, S.lam, n, ld, i1, S.r, theta);
@@ -425,8 +421,8 @@ size_t eig_smem_bytes(int n) {
 
 // ------------------------------------------------------ per-sample solve ---
 struct SampleArgs {
-  const void* pz[2][2];      // [pass][frame] cpx<TP> [n][C][ns][len]
-  const double* dc[2][2];    // [pass][frame] double [n][C][len] (mixed)
+  const cd* pz[2][2];        // [pass][frame] double samples [n][C][ns][len]
+  const cf* pzf[2][2];       // [pass][frame] float copies (mixed path), same layout
   int len[2][2];             // [pass][frame]
   cd* X;                     // [n][2][ns][nn]
   double* sdiag;             // [n][2][ns][4]
@@ -437,16 +433,26 @@ struct SampleArgs {
 // Sample polynomial element m of frame k (0: b1, 1: b2) as cpx<TA>.
 template <typename TP, typename TA>
 struct SamplePolys {
-  const cpx<TP>* c[2];   // complex data, channel 0; channel stride cstride[k]
-  const double* r[2];    // real double data (z = 1 sample of the mixed path)
+  const cpx<TP>* c[2];   // channel 0 of the sample; channel stride cstride[k]
   int64_t cstride[2];
   int len[2];
   __device__ __forceinline__ cpx<TA> ld(int k, int ch, int m) const {
-    if (r[k]) return mk<TA>((TA)r[k][ch * cstride[k] + m], (TA)0);
     cpx<TP> v = c[k][ch * cstride[k] + m];
     return mk<TA>((TA)v.re, (TA)v.im);
   }
 };
+
+template <typename TP, typename TA>
+__device__ SamplePolys<TP, TA> sample_polys(const cpx<TP>* const base[2], const int len[2], int f,
+                                            int C, int ns, int s) {
+  SamplePolys<TP, TA> P;
+  for (int k = 0; k < 2; ++k) {
+    P.len[k] = len[k];
+    P.c[k] = base[k] + ((int64_t)f * C * ns + s) * len[k];
+    P.cstride[k] = (int64_t)len[k] * ns;
+  }
+  return P;
+}
 
 // rho jobs: j < t1: rho_22(j); j < t1+t2: rho_11(j - t1);
 // else rho_21(d), d = j - t1 - t2 - (t2 - 1) in [-(t2-1), t1-1].
@@ -539,7 +545,6 @@ struct SylvesterApply {
   }
 };
 
-template <typename TP>
 __global__ void __launch_bounds__(kSolveThreads) k_sample_solve(SampleArgs a) {
   extern __shared__ __align__(16) char smem[];
   const int s = blockIdx.x, ps = blockIdx.y, f = blockIdx.z;
@@ -547,59 +552,26 @@ __global__ void __launch_bounds__(kSolveThreads) k_sample_solve(SampleArgs a) {
   EigSmem S;
   char* p = carve_eig(S, smem, n);
   cd* rho = (cd*)p;
-  const bool use_dc = a.mixed && s == 0;
-  const int64_t cs0 = a.len[ps][0], cs1 = a.len[ps][1];
-  if (use_dc || !a.mixed) {
-    SamplePolys<TP, double> P;
-    for (int k = 0; k < 2; ++k) {
-      const int64_t len = a.len[ps][k];
-      P.len[k] = (int)len;
-      if (use_dc) {
-        P.c[k] = nullptr;
-        P.r[k] = a.dc[ps][k] + (int64_t)f * a.C * len;
-        P.cstride[k] = len;
-      } else {
-        P.c[k] = (const cpx<TP>*)a.pz[ps][k] + ((int64_t)f * a.C * a.ns + s) * len;
-        P.r[k] = nullptr;
-        P.cstride[k] = len * a.ns;
-      }
-    }
-    correlations(P, a.C, a.t1, a.t2, rho);
-  } else {
-    SamplePolys<TP, float> P;
-    for (int k = 0; k < 2; ++k) {
-      const int64_t len = a.len[ps][k];
-      P.len[k] = (int)len;
-      P.c[k] = (const cpx<TP>*)a.pz[ps][k] + ((int64_t)f * a.C * a.ns + s) * len;
-      P.r[k] = nullptr;
-      P.cstride[k] = len * a.ns;
-    }
-    correlations(P, a.C, a.t1, a.t2, rho);
-  }
-  (void)cs0;
-  (void)cs1;
+  // Gram: single precision on the mixed path except at the z = 1 sample
+  // (s = 0: highest signal-to-noise, smallest relative eigen-gaps).
+  if (a.mixed && s != 0)
+    correlations(sample_polys<float, float>(a.pzf[ps], a.len[ps], f, a.C, a.ns, s), a.C, a.t1,
+                 a.t2, rho);
+  else
+    correlations(sample_polys<double, double>(a.pz[ps], a.len[ps], f, a.C, a.ns, s), a.C, a.t1,
+                 a.t2, rho);
   gram_from_rho(rho, a.t1, a.t2, S.G);
-  EigResult res;
-  if (!a.mixed) {
-    // FP64 path: TP is double here.
-    SylvesterApply ap;
-    for (int k = 0; k < 2; ++k) {
-      const int64_t len = a.len[ps][k];
-      ap.P.len[k] = (int)len;
-      ap.P.c[k] = (const cd*)a.pz[ps][k] + ((int64_t)f * a.C * a.ns + s) * len;
-      ap.P.r[k] = nullptr;
-      ap.P.cstride[k] = len * a.ns;
-    }
-    ap.C = a.C;
-    ap.t1 = a.t1;
-    ap.t2 = a.t2;
-    ap.L = a.len[ps][0] + a.t2 - 1;
-    ap.y = a.resid + (((int64_t)f * 2 + ps) * a.ns + s) * a.C * (int64_t)a.Lmax;
-    ap.red = S.red;
-    res = smallest_eigvec(S, n, true, ap);
-  } else {
-    res = smallest_eigvec(S, n, false, NoApply());
-  }
+  // Refinement against the exact residual S^H S x from the double samples:
+  // two steps on the FP64 path, one on the mixed path.
+  SylvesterApply ap;
+  ap.P = sample_polys<double, double>(a.pz[ps], a.len[ps], f, a.C, a.ns, s);
+  ap.C = a.C;
+  ap.t1 = a.t1;
+  ap.t2 = a.t2;
+  ap.L = a.len[ps][0] + a.t2 - 1;
+  ap.y = a.resid + (((int64_t)f * 2 + ps) * a.ns + s) * a.C * (int64_t)a.Lmax;
+  ap.red = S.red;
+  const EigResult res = smallest_eigvec(S, n, a.mixed ? 1 : 2, ap);
   const int64_t o = ((int64_t)f * 2 + ps) * a.ns + s;
   for (int i = threadIdx.x; i < n; i += blockDim.x) a.X[o * n + i] = S.x[i];
   if (threadIdx.x == 0) {
@@ -722,7 +694,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
   }
   __syncthreads();
   ScaleApply ap{ab, M};
-  EigResult res = smallest_eigvec(S, n, !a.mixed, ap);
+  EigResult res = smallest_eigvec(S, n, 2, ap);
   // X_k[i][j] = (gamma_j A_k[i][j] + delta_i B_k[i][j]) / 2
   for (int idx = threadIdx.x; idx < 2 * MM; idx += blockDim.x) {
     const int k = idx / MM, i = (idx % MM) / M, j = idx % M;
@@ -857,10 +829,10 @@ size_t scale_solve_smem(int M) { return eig_smem_bytes(2 * M) + sizeof(cd) * 3 *
 void launch_sample_solve(const Plan& p, char* ws, cudaStream_t st) {
   SampleArgs a;
   for (int k = 0; k < 2; ++k) {
-    a.pz[0][k] = ws + p.off_pz2[k];
-    a.pz[1][k] = ws + p.off_pz1[k];
-    a.dc[0][k] = p.mixed ? (const double*)(ws + p.off_dcz2[k]) : nullptr;
-    a.dc[1][k] = p.mixed ? (const double*)(ws + p.off_dcz1[k]) : nullptr;
+    a.pz[0][k] = (const cd*)(ws + p.off_pz2[k]);
+    a.pz[1][k] = (const cd*)(ws + p.off_pz1[k]);
+    a.pzf[0][k] = p.mixed ? (const cf*)(ws + p.off_pz2f[k]) : nullptr;
+    a.pzf[1][k] = p.mixed ? (const cf*)(ws + p.off_pz1f[k]) : nullptr;
   }
   a.len[0][0] = p.H1;
   a.len[0][1] = p.H2;
@@ -878,13 +850,8 @@ void launch_sample_solve(const Plan& p, char* ws, cudaStream_t st) {
   a.mixed = p.mixed;
   const size_t sm = sample_solve_smem(p.nn);
   dim3 grid(p.ns, 2, p.n);
-  if (p.mixed) {
-    cudaFuncSetAttribute(k_sample_solve<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_sample_solve<float><<<grid, kSolveThreads, sm, st>>>(a);
-  } else {
-    cudaFuncSetAttribute(k_sample_solve<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_sample_solve<double><<<grid, kSolveThreads, sm, st>>>(a);
-  }
+  cudaFuncSetAttribute(k_sample_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_sample_solve<<<grid, kSolveThreads, sm, st>>>(a);
 }
 
 void launch_scale_solve(const Plan& p, char* ws, void* k1_out, void* k2_out, int out_f64,

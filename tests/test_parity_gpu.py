@@ -75,9 +75,35 @@ def test_stages_match_oracle_fp64(gpu_ctx):
 
 
 def test_stages_match_oracle_mixed_1080p(gpu_ctx):
-    """Single-precision samples (~1e-7); null vectors to 1e-5 except that none may flip."""
+    """Mixed path: samples from the exact float fold (1e-12); null vectors after
+    one exact-residual step from a single-precision Gram (1e-8)."""
     b1, b2, *_, cfg = make_batch("rgb_1080p", [0])
-    _stage_check(gpu_ctx, b1, b2, cfg, "mixed", 1e-6, 1e-5)
+    _stage_check(gpu_ctx, b1, b2, cfg, "mixed", 1e-12, 1e-8)
+
+
+def test_full_batch_1080p_as_benchmarked(gpu_ctx):
+    """The benchmark's launch configuration (60 pairs of 1080p RGB per call),
+    built from two host-generated pairs tiled 30 times; every pair's kernels
+    against the oracle (mixed <= 1e-3, FP64 <= 1e-9), latents sampled."""
+    from paper_1203_4874_gb300 import cbp
+    b1, b2, k1, k2, lat, cfg = make_batch("rgb_1080p", [0, 1])
+    refs = [oracle_pair(b1[i], b2[i], 15, 17, cfg.eps) for i in range(2)]
+    idx = [i % 2 for i in range(60)]
+    B1 = torch.from_numpy(b1).float().cuda()[idx].contiguous()
+    B2 = torch.from_numpy(b2).float().cuda()[idx].contiguous()
+    for path, tol in (("mixed", 1e-3), ("fp64", 1e-9)):
+        prm = cbp.params(15, 17, path=path, eps=cfg.eps, flags=cbp.CBP_FLAG_KERNELS_F64)
+        L, K1, K2, diag, _ = cbp.cbp_deblur_pair(gpu_ctx, B1, B2, prm)
+        torch.cuda.synchronize()
+        K1, K2 = K1.cpu().numpy(), K2.cpu().numpy()
+        for f in range(60):
+            o = refs[idx[f]]
+            assert rel(K1[f], o["k1"]) <= tol and rel(K2[f], o["k2"]) <= tol, (path, f)
+        for f in (0, 59):
+            g = L[f].double().cpu().numpy()
+            o = refs[idx[f]]["latent"]
+            assert abs(psnr(g, lat[idx[f]]) - psnr(o, lat[idx[f]])) <= 0.05, (path, f)
+        del L
 
 
 def test_even_sample_count_self_conjugate_sample(gpu_ctx):
