@@ -37,6 +37,14 @@ template <typename D, typename S> __host__ __device__ __forceinline__ cpx<D> cvt
   return {(D)a.re, (D)a.im};
 }
 
+// A complex double held as two float-float numbers (hi + lo each), for
+// extended-precision arithmetic on the single-precision units.
+struct alignas(16) cdf { float rh, rl, ih, il; };
+__host__ __device__ __forceinline__ cdf to_cdf(cd a) {
+  const float rh = (float)a.re, ih = (float)a.im;
+  return {rh, (float)(a.re - (double)rh), ih, (float)(a.im - (double)ih)};
+}
+
 template <typename T> __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

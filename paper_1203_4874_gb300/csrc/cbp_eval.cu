@@ -14,8 +14,8 @@
 //
 // Float32 frames are folded with an exact float TwoSum accumulation (hi + lo),
 // so the bins -- and the samples, whose M-point DFT runs in double -- carry
-// ~1e-14 relative error on both paths; the mixed path also keeps a float copy
-// of the samples for its single-precision Gram.
+// ~1e-14 relative error on both paths; the mixed path also keeps float-float
+// (hi + lo) copies for its extended-precision Gram on the float units.
 #include "cbp_common.cuh"
 #include "cbp_internal.h"
 
@@ -35,7 +35,7 @@ __device__ __forceinline__ void root_table(cd* tab, int M) {
 
 struct EvalOut {
   cd* pz[2];          // [n][C][ns][len_k] double samples
-  cf* pzf[2];         // optional single-precision copies (mixed path)
+  cdf* pzf[2];        // optional float-float copies (mixed path)
   int* bad;           // [n]
 };
 
@@ -105,7 +105,7 @@ k_eval_rows(FrameDesc f1, FrameDesc f2, int M, int ns, EvalOut out) {
     const cd pv = bins_dft(&bins[warp][0], 1, wtab, M, lane);
     const int64_t o = ((int64_t)fc * ns + lane) * fr.h + r;
     out.pz[blockIdx.z][o] = pv;
-    if (out.pzf[blockIdx.z]) out.pzf[blockIdx.z][o] = cvt<float>(pv);
+    if (out.pzf[blockIdx.z]) out.pzf[blockIdx.z][o] = to_cdf(pv);
   }
 }
 
@@ -151,7 +151,7 @@ k_eval_cols(FrameDesc f1, FrameDesc f2, int M, int ns, EvalOut out) {
     const cd pv = bins_dft(&bins[0][threadIdx.x], kColThreads, wtab, M, s);
     const int64_t o = ((int64_t)fc * ns + s) * fr.w + col;
     out.pz[blockIdx.z][o] = pv;
-    if (out.pzf[blockIdx.z]) out.pzf[blockIdx.z][o] = cvt<float>(pv);
+    if (out.pzf[blockIdx.z]) out.pzf[blockIdx.z][o] = to_cdf(pv);
   }
 }
 
@@ -163,8 +163,8 @@ void launch_eval(const Plan& p, const FrameDesc& b1, const FrameDesc& b2, char* 
   for (int k = 0; k < 2; ++k) {
     rows.pz[k] = (cd*)(ws + p.off_pz2[k]);
     cols.pz[k] = (cd*)(ws + p.off_pz1[k]);
-    rows.pzf[k] = p.mixed ? (cf*)(ws + p.off_pz2f[k]) : nullptr;
-    cols.pzf[k] = p.mixed ? (cf*)(ws + p.off_pz1f[k]) : nullptr;
+    rows.pzf[k] = p.mixed ? (cdf*)(ws + p.off_pz2f[k]) : nullptr;
+    cols.pzf[k] = p.mixed ? (cdf*)(ws + p.off_pz1f[k]) : nullptr;
   }
   rows.bad = cols.bad = (int*)(ws + p.off_bad);
   const int hmax = b1.h > b2.h ? b1.h : b2.h;

@@ -23,117 +23,211 @@ namespace {
 
 constexpr int kFftThreads = 256;
 
-// cos / sin (2 pi j / R) for the odd radices
-__constant__ double kC3[3] = {1.0, -0.5, -0.5};
-__constant__ double kS3[3] = {0.0, 0.86602540378443864676, -0.86602540378443864676};
-__constant__ double kC5[5] = {1.0, 0.30901699437494742410, -0.80901699437494742410,
-                              -0.80901699437494742410, 0.30901699437494742410};
-__constant__ double kS5[5] = {0.0, 0.95105651629515357212, 0.58778525229247312917,
-                              -0.58778525229247312917, -0.95105651629515357212};
-__constant__ double kC7[7] = {1.0, 0.62348980185873353053, -0.22252093395631440429,
-                              -0.90096886790241912624, -0.90096886790241912624,
-                              -0.22252093395631440429, 0.62348980185873353053};
-__constant__ double kS7[7] = {0.0, 0.78183148246802980871, 0.97492791218182360702,
-                              0.43388373911755812048, -0.43388373911755812048,
-                              -0.97492791218182360702, -0.78183148246802980871};
+// ------------------------------------------------------------- FFT core ---
+// In-register DFTs of size R (Inv: e^{+i...}, unnormalised), float constants
+// for float data.  Radix 8 = 2 x 4 and radix 9 = 3 x 3 with internal twiddles.
+template <typename T, bool Inv>
+__device__ __forceinline__ cpx<T> mul_i(cpx<T> d) {     // (Inv ? +i : -i) * d
+  return Inv ? mk<T>(-d.im, d.re) : mk<T>(d.im, -d.re);
+}
 
-// In-register DFT of size R; sgn = -1 forward, +1 inverse (unnormalised).
-template <typename T, int R>
-__device__ __forceinline__ void small_dft(cpx<T>* v, T sgn) {
-  if constexpr (R == 2) {
-    cpx<T> a = v[0] + v[1], b = v[0] - v[1];
-    v[0] = a;
-    v[1] = b;
-  } else if constexpr (R == 4) {
-    cpx<T> t0 = v[0] + v[2], t1 = v[0] - v[2], t2 = v[1] + v[3], d = v[1] - v[3];
-    cpx<T> t3 = mk<T>(-sgn * d.im, sgn * d.re);  // sgn * i * d
-    v[0] = t0 + t2;
-    v[2] = t0 - t2;
-    v[1] = t1 + t3;
-    v[3] = t1 - t3;
-  } else {
-    const double* C = R == 3 ? kC3 : (R == 5 ? kC5 : kC7);
-    const double* S = R == 3 ? kS3 : (R == 5 ? kS5 : kS7);
-    constexpr int H = (R - 1) / 2;
-    cpx<T> a[H], b[H];
+template <typename T, bool Inv>
+__device__ __forceinline__ void dft2(cpx<T>& a, cpx<T>& b) {
+  const cpx<T> t = a - b;
+  a = a + b;
+  b = t;
+}
+
+template <typename T, bool Inv>
+__device__ __forceinline__ void dft3(cpx<T>& a, cpx<T>& b, cpx<T>& c) {
+  const T h = (T)0.86602540378443864676;       // sin(2 pi / 3)
+  const cpx<T> sm = b + c, d = b - c;
+  const cpx<T> t1 = a - (T)0.5 * sm;
+  const cpx<T> t2 = h * mul_i<T, Inv>(d);
+  a = a + sm;
+  b = t1 + t2;
+  c = t1 - t2;
+}
+
+template <typename T, bool Inv>
+__device__ __forceinline__ void dft4(cpx<T>& v0, cpx<T>& v1, cpx<T>& v2, cpx<T>& v3) {
+  const cpx<T> t0 = v0 + v2, t1 = v0 - v2, t2 = v1 + v3;
+  const cpx<T> t3 = mul_i<T, Inv>(v1 - v3);
+  v0 = t0 + t2;
+  v2 = t0 - t2;
+  v1 = t1 + t3;
+  v3 = t1 - t3;
+}
+
+// odd prime radix by symmetric pairs; C, S = cos, sin(2 pi j / R)
+template <typename T, bool Inv, int R>
+__device__ __forceinline__ void dft_odd(cpx<T>* v, const T* C, const T* S) {
+  constexpr int H = (R - 1) / 2;
+  cpx<T> a[H], b[H];
+#pragma unroll
+  for (int m = 1; m <= H; ++m) {
+    a[m - 1] = v[m] + v[R - m];
+    b[m - 1] = v[m] - v[R - m];
+  }
+  const cpx<T> x0 = v[0];
+  cpx<T> s0 = x0;
+#pragma unroll
+  for (int m = 0; m < H; ++m) s0 = s0 + a[m];
+  v[0] = s0;
+#pragma unroll
+  for (int k = 1; k <= H; ++k) {
+    cpx<T> re = x0, im = mk<T>(0, 0);
 #pragma unroll
     for (int m = 1; m <= H; ++m) {
-      a[m - 1] = v[m] + v[R - m];
-      b[m - 1] = v[m] - v[R - m];
+      const int j = (k * m) % R;
+      re = re + C[j] * a[m - 1];
+      im = im + S[j] * b[m - 1];
     }
-    cpx<T> x0 = v[0];
-    cpx<T> s0 = x0;
-#pragma unroll
-    for (int m = 0; m < H; ++m) s0 = s0 + a[m];
-    v[0] = s0;
-#pragma unroll
-    for (int k = 1; k <= H; ++k) {
-      cpx<T> re = x0, im = mk<T>(0, 0);
-#pragma unroll
-      for (int m = 1; m <= H; ++m) {
-        const int j = (k * m) % R;
-        const T c = (T)C[j], s = (T)S[j];
-        re = re + c * a[m - 1];
-        im = im + s * b[m - 1];
-      }
-      // X[k] = re + sgn*i*im ; X[R-k] = re - sgn*i*im
-      cpx<T> si = mk<T>(-sgn * im.im, sgn * im.re);
-      v[k] = re + si;
-      v[R - k] = re - si;
-    }
+    const cpx<T> si = mul_i<T, Inv>(im);   // forward: X[k] = re - i im, X[R-k] = re + i im
+    v[k] = re + si;
+    v[R - k] = re - si;
   }
 }
 
-// One Stockham stage of radix R over `nb` transforms of length N stored with
-// stride N (in -> out).  Twiddles w_N^e = tw[e * tstride] (tw of length N * tstride).
-template <typename T, int R>
-__device__ void stockham_stage(const cpx<T>* in, cpx<T>* out, int N, int Ns, int nb,
-                               const cpx<T>* tw, int tstride, T sgn) {
-  const int Nr = N / R;
-  const int estep = N / (Ns * R);
+template <typename T, bool Inv, int R>
+__device__ __forceinline__ void small_dft(cpx<T>* v) {
+  if constexpr (R == 2) {
+    dft2<T, Inv>(v[0], v[1]);
+  } else if constexpr (R == 3) {
+    dft3<T, Inv>(v[0], v[1], v[2]);
+  } else if constexpr (R == 4) {
+    dft4<T, Inv>(v[0], v[1], v[2], v[3]);
+  } else if constexpr (R == 5) {
+    const T C[5] = {(T)1, (T)0.30901699437494742410, (T)-0.80901699437494742410,
+                    (T)-0.80901699437494742410, (T)0.30901699437494742410};
+    const T S[5] = {(T)0, (T)0.95105651629515357212, (T)0.58778525229247312917,
+                    (T)-0.58778525229247312917, (T)-0.95105651629515357212};
+    dft_odd<T, Inv, 5>(v, C, S);
+  } else if constexpr (R == 7) {
+    const T C[7] = {(T)1, (T)0.62348980185873353053, (T)-0.22252093395631440429,
+                    (T)-0.90096886790241912624, (T)-0.90096886790241912624,
+                    (T)-0.22252093395631440429, (T)0.62348980185873353053};
+    const T S[7] = {(T)0, (T)0.78183148246802980871, (T)0.97492791218182360702,
+                    (T)0.43388373911755812048, (T)-0.43388373911755812048,
+                    (T)-0.97492791218182360702, (T)-0.78183148246802980871};
+    dft_odd<T, Inv, 7>(v, C, S);
+  } else if constexpr (R == 8) {
+    // even / odd halves by radix 4, combined with w8^k
+    dft4<T, Inv>(v[0], v[2], v[4], v[6]);
+    dft4<T, Inv>(v[1], v[3], v[5], v[7]);
+    const T r = (T)0.70710678118654752440;
+    const cpx<T> o1 = r * (v[3] + mul_i<T, Inv>(v[3]));     // w8^1 = r (1 -/+ i)
+    const cpx<T> o2 = mul_i<T, Inv>(v[5]);                   // w8^2 = -/+ i
+    const cpx<T> o3 = r * (mul_i<T, Inv>(v[7]) - v[7]);     // w8^3 = r (-1 -/+ i)
+    const cpx<T> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+    v[0] = e0 + v[1];
+    v[4] = e0 - v[1];
+    v[1] = e1 + o1;
+    v[5] = e1 - o1;
+    v[2] = e2 + o2;
+    v[6] = e2 - o2;
+    v[3] = e3 + o3;
+    v[7] = e3 - o3;
+  } else {  // R == 9: 3 x 3
+    dft3<T, Inv>(v[0], v[3], v[6]);
+    dft3<T, Inv>(v[1], v[4], v[7]);
+    dft3<T, Inv>(v[2], v[5], v[8]);
+    // twiddles w9^{n2 k1}: (n2, k1) = (1,1) (1,2) (2,1) (2,2) -> w9^1, w9^2, w9^2, w9^4
+    const T c1 = (T)0.76604444311897803520, s1 = (T)0.64278760968653932632;   // 2 pi / 9
+    const T c2 = (T)0.17364817766693034885, s2 = (T)0.98480775301220805936;   // 4 pi / 9
+    const T c4 = (T)-0.93969262078590838405, s4 = (T)0.34202014332566873304;  // 8 pi / 9
+    const T sg = Inv ? (T)1 : (T)-1;
+    v[4] = v[4] * mk<T>(c1, sg * s1);
+    v[7] = v[7] * mk<T>(c2, sg * s2);
+    v[5] = v[5] * mk<T>(c2, sg * s2);
+    v[8] = v[8] * mk<T>(c4, sg * s4);
+    // v[n2 + 3 k1] holds Y_{n2}[k1]; DFT3 over n2 for each k1 -> X[k1 + 3 k2]
+    cpx<T> a0 = v[0], a1 = v[1], a2 = v[2];
+    dft3<T, Inv>(a0, a1, a2);
+    cpx<T> b0 = v[3], b1 = v[4], b2 = v[5];
+    dft3<T, Inv>(b0, b1, b2);
+    cpx<T> d0 = v[6], d1 = v[7], d2 = v[8];
+    dft3<T, Inv>(d0, d1, d2);
+    v[0] = a0; v[3] = a1; v[6] = a2;
+    v[1] = b0; v[4] = b1; v[7] = b2;
+    v[2] = d0; v[5] = d1; v[8] = d2;
+  }
+}
+
+// One Stockham stage of radix R over nb transforms of length N (stride N),
+// in -> out; tw = this stage's twiddles (shared memory).
+template <typename T, bool Inv, int R>
+__device__ __forceinline__ void stockham_stage(const cpx<T>* __restrict__ in,
+                                               cpx<T>* __restrict__ out, const FftStage& st,
+                                               int N, int nb, const cpx<T>* tw) {
+  const int Nr = st.Nr, Ns = st.Ns;
   for (int idx = threadIdx.x; idx < nb * Nr; idx += blockDim.x) {
-    const int b = idx / Nr, j = idx - b * Nr;
-    const cpx<T>* src = in + (int64_t)b * N;
-    cpx<T>* dst = out + (int64_t)b * N;
-    const int k = j % Ns;
+    const int b = st.mNr ? (int)__umulhi((unsigned)idx, st.mNr) : idx;   // idx / Nr
+    const int j = idx - b * Nr;
+    const int q = st.mNs ? (int)__umulhi((unsigned)j, st.mNs) : j;      // j / Ns
+    const int k = j - q * Ns;
+    const cpx<T>* src = in + b * N + j;
     cpx<T> v[R];
 #pragma unroll
-    for (int r = 0; r < R; ++r) v[r] = src[j + r * Nr];
+    for (int r = 0; r < R; ++r) v[r] = src[r * Nr];
+    if (Ns > 1) {
+      const cpx<T>* w = tw + k * (R - 1);
 #pragma unroll
-    for (int r = 1; r < R; ++r) {
-      cpx<T> w = tw[(int64_t)k * r * estep * tstride];
-      if (sgn > 0) w.im = -w.im;
-      v[r] = v[r] * w;
+      for (int r = 1; r < R; ++r) {
+        cpx<T> ww = w[r - 1];
+        if (Inv) ww.im = -ww.im;
+        v[r] = v[r] * ww;
+      }
     }
-    small_dft<T, R>(v, sgn);
-    const int base = (j / Ns) * Ns * R + k;
+    small_dft<T, Inv, R>(v);
+    cpx<T>* dst = out + b * N + q * Ns * R + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) dst[base + r * Ns] = v[r];
+    for (int r = 0; r < R; ++r) dst[r * Ns] = v[r];
   }
 }
 
-// Full batched FFT in shared memory; returns the buffer holding the result
-// (a or b).  All threads of the block must call it.
-template <typename T>
-__device__ cpx<T>* fft_block(cpx<T>* a, cpx<T>* b, const FftPlan& pl, int nb,
-                             const cpx<T>* tw, int tstride, T sgn) {
-  int Ns = 1;
+// nb transforms in shared memory (a, scratch b); returns the buffer with the
+// result.  tw: the plan's stage twiddles in shared memory.  Block-wide.
+template <typename T, bool Inv>
+__device__ cpx<T>* fft_block(cpx<T>* a, cpx<T>* b, const FftPlan& pl, int nb, const cpx<T>* tw) {
   for (int s = 0; s < pl.nst; ++s) {
-    const int R = pl.radix[s];
-    switch (R) {
-      case 2: stockham_stage<T, 2>(a, b, pl.n, Ns, nb, tw, tstride, sgn); break;
-      case 3: stockham_stage<T, 3>(a, b, pl.n, Ns, nb, tw, tstride, sgn); break;
-      case 4: stockham_stage<T, 4>(a, b, pl.n, Ns, nb, tw, tstride, sgn); break;
-      case 5: stockham_stage<T, 5>(a, b, pl.n, Ns, nb, tw, tstride, sgn); break;
-      default: stockham_stage<T, 7>(a, b, pl.n, Ns, nb, tw, tstride, sgn); break;
+    const FftStage& st = pl.st[s];
+    const cpx<T>* t = tw + st.tw;
+    switch (st.R) {
+      case 2: stockham_stage<T, Inv, 2>(a, b, st, pl.n, nb, t); break;
+      case 3: stockham_stage<T, Inv, 3>(a, b, st, pl.n, nb, t); break;
+      case 4: stockham_stage<T, Inv, 4>(a, b, st, pl.n, nb, t); break;
+      case 5: stockham_stage<T, Inv, 5>(a, b, st, pl.n, nb, t); break;
+      case 7: stockham_stage<T, Inv, 7>(a, b, st, pl.n, nb, t); break;
+      case 8: stockham_stage<T, Inv, 8>(a, b, st, pl.n, nb, t); break;
+      default: stockham_stage<T, Inv, 9>(a, b, st, pl.n, nb, t); break;
     }
     __syncthreads();
-    cpx<T>* t = a;
+    cpx<T>* tmp = a;
     a = b;
-    b = t;
-    Ns *= R;
+    b = tmp;
   }
   return a;
+}
+
+// Stage twiddles of a plan: entry st.tw + k (R-1) + r - 1 = exp(-2 pi i k r / (Ns R)).
+template <typename T>
+__global__ void k_stage_twiddles(FftPlan pl, cpx<T>* out) {
+  for (int s = 0; s < pl.nst; ++s) {
+    const FftStage& st = pl.st[s];
+    const int cnt = st.Ns * (st.R - 1);
+    for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
+      const int k = e / (st.R - 1), r = e % (st.R - 1) + 1;
+      double sn, cs;
+      sincospi(-2.0 * (double)(k * r) / (double)(st.Ns * st.R), &sn, &cs);
+      out[st.tw + e] = mk<T>((T)cs, (T)sn);
+    }
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void load_twiddles(cpx<T>* dst, const cpx<T>* src, int n) {
+  for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
 template <typename T>
@@ -189,47 +283,72 @@ k_kernel_spectra(const double* kd, int t1, int t2, int Ph, int Pw, int Pw2, cons
 struct RowArgs {
   FrameDesc fr[2];
   void* spec[2];     // cpx<T> [n][C][H_Bk][Pw2]
-  int Pw, Pw2, half;
+  int Pw, Pw2, half, nbr;
   FftPlan pl;        // plan of Pw/2 (half) or Pw
 };
 
-// Forward real-to-complex FFT of every row of B1 and B2.
+// Forward real-to-complex FFT of every row of B1 and B2, nbr rows at a time.
+// Shared memory: stage twiddles, then two buffers of nbr rows.
 template <typename T>
-__global__ void __launch_bounds__(kFftThreads) k_row_fft(RowArgs a, const cpx<T>* tw_w) {
+__global__ void __launch_bounds__(kFftThreads)
+k_row_fft(RowArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
   extern __shared__ __align__(16) char smem[];
-  const int N = a.pl.n;
-  cpx<T>* b0 = (cpx<T>*)smem;
-  cpx<T>* b1 = b0 + N;
+  const int N = a.pl.n, NB = a.nbr;
+  cpx<T>* tw = (cpx<T>*)smem;
+  cpx<T>* b0 = tw + ((a.pl.ntw + 1) & ~1);
+  cpx<T>* b1 = b0 + NB * N;
+  load_twiddles(tw, stw, a.pl.ntw);
   const FrameDesc& fr = a.fr[blockIdx.z];
   const int fc = blockIdx.y, f = fc / fr.c, ch = fc % fr.c;
   const int rows_per = (fr.h + gridDim.x - 1) / gridDim.x;
   const int r0 = blockIdx.x * rows_per, r1 = min(fr.h, r0 + rows_per);
   cpx<T>* spec = (cpx<T>*)a.spec[blockIdx.z] + (int64_t)fc * fr.h * a.Pw2;
-  for (int r = r0; r < r1; ++r) {
-    const void* fb = frame_base(fr, f);
-    const int64_t base = (int64_t)ch * fr.cs + (int64_t)r * fr.rs;
-    for (int m = threadIdx.x; m < N; m += blockDim.x) {
-      if (a.half) {
-        const int c0 = 2 * m, c1 = 2 * m + 1;
-        T x0 = c0 < fr.w ? ld_frame<T>(fb, base + c0, fr.f64) : (T)0;
-        T x1 = c1 < fr.w ? ld_frame<T>(fb, base + c1, fr.f64) : (T)0;
-        b0[m] = mk<T>(x0, x1);
+  const void* fb = frame_base(fr, f);
+  for (int rg = r0; rg < r1; rg += NB) {
+    const int nr = min(NB, r1 - rg);
+    for (int rl = 0; rl < nr; ++rl) {
+      const int64_t base = (int64_t)ch * fr.cs + (int64_t)(rg + rl) * fr.rs;
+      cpx<T>* dst = b0 + rl * N;
+      if (a.half && !fr.f64 && ((((uintptr_t)((const float*)fb + base)) & 7) == 0)) {
+        const float2* rp = (const float2*)((const float*)fb + base);
+        const int full = fr.w >> 1;               // complete (x[2m], x[2m+1]) pairs
+        for (int m = threadIdx.x; m < N; m += blockDim.x) {
+          T x0 = 0, x1 = 0;
+          if (m < full) {
+            const float2 v = __ldg(rp + m);
+            x0 = v.x;
+            x1 = v.y;
+          } else if (2 * m < fr.w) {
+            x0 = __ldg((const float*)fb + base + 2 * m);
+          }
+          dst[m] = mk<T>(x0, x1);
+        }
+      } else if (a.half) {
+        for (int m = threadIdx.x; m < N; m += blockDim.x) {
+          const int c0 = 2 * m, c1 = 2 * m + 1;
+          const T x0 = c0 < fr.w ? ld_frame<T>(fb, base + c0, fr.f64) : (T)0;
+          const T x1 = c1 < fr.w ? ld_frame<T>(fb, base + c1, fr.f64) : (T)0;
+          dst[m] = mk<T>(x0, x1);
+        }
       } else {
-        b0[m] = mk<T>(m < fr.w ? ld_frame<T>(fb, base + m, fr.f64) : (T)0, (T)0);
+        for (int m = threadIdx.x; m < N; m += blockDim.x)
+          dst[m] = mk<T>(m < fr.w ? ld_frame<T>(fb, base + m, fr.f64) : (T)0, (T)0);
       }
     }
     __syncthreads();
-    cpx<T>* Z = fft_block<T>(b0, b1, a.pl, 1, tw_w, a.half ? 2 : 1, (T)-1);
-    cpx<T>* dst = spec + (int64_t)r * a.Pw2;
-    for (int k = threadIdx.x; k < a.Pw2; k += blockDim.x) {
-      if (a.half) {
-        const cpx<T> zk = Z[k % N], zc = conj(Z[(N - k) % N]);
-        const cpx<T> e = (T)0.5 * (zk + zc), d = (T)0.5 * (zk - zc);
-        const cpx<T> w = tw_w[k];                 // exp(-2 pi i k / Pw)
-        const cpx<T> wd = w * d;                  // X = e - i * w * d
-        dst[k] = mk<T>(e.re + wd.im, e.im - wd.re);
-      } else {
-        dst[k] = Z[k];
+    cpx<T>* Z = fft_block<T, false>(b0, b1, a.pl, nr, tw);
+    for (int rl = 0; rl < nr; ++rl) {
+      const cpx<T>* z = Z + rl * N;
+      cpx<T>* out = spec + (int64_t)(rg + rl) * a.Pw2;
+      for (int k = threadIdx.x; k < a.Pw2; k += blockDim.x) {
+        if (a.half) {
+          const cpx<T> zk = z[k < N ? k : 0], zc = conj(z[k > 0 ? N - k : 0]);
+          const cpx<T> e = (T)0.5 * (zk + zc), d = (T)0.5 * (zk - zc);
+          const cpx<T> wd = tw_w[k] * d;          // X = e - i w d, w = exp(-2 pi i k / Pw)
+          out[k] = mk<T>(e.re + wd.im, e.im - wd.re);
+        } else {
+          out[k] = z[k];
+        }
       }
     }
     __syncthreads();
@@ -245,13 +364,21 @@ struct ColArgs {
   FftPlan pl;         // plan of Ph
 };
 
+constexpr int kColThreads = 512;
+
 // Column FFTs of both spectra, dual-kernel formula, inverse column FFT.
+// Shared memory: stage twiddles, then three buffers of CW columns.
 template <typename T, int CW>
-__global__ void __launch_bounds__(kFftThreads) k_col_deconv(ColArgs a, const cpx<T>* tw_h) {
+__global__ void __launch_bounds__(kColThreads)
+k_col_deconv(ColArgs a, const cpx<T>* stw) {
   extern __shared__ __align__(16) char smem[];
   const int Ph = a.Ph;
+  cpx<T>* tw = (cpx<T>*)smem;
   cpx<T>* buf[3];
-  for (int i = 0; i < 3; ++i) buf[i] = (cpx<T>*)smem + (int64_t)i * CW * Ph;
+  buf[0] = tw + ((a.pl.ntw + 1) & ~1);
+  buf[1] = buf[0] + CW * Ph;
+  buf[2] = buf[1] + CW * Ph;
+  load_twiddles(tw, stw, a.pl.ntw);
   const int fc = blockIdx.y, f = fc / a.C;
   const int v0 = blockIdx.x * CW;
   const int nv = min(CW, a.Pw2 - v0);
@@ -267,13 +394,13 @@ __global__ void __launch_bounds__(kFftThreads) k_col_deconv(ColArgs a, const cpx
   const cpx<T>* K1 = (const cpx<T>*)a.khat + ((int64_t)f * 2 + 0) * Ph * a.Pw2 + v0;
   const cpx<T>* K2 = (const cpx<T>*)a.khat + ((int64_t)f * 2 + 1) * Ph * a.Pw2 + v0;
   load(buf[0], 0);
-  cpx<T>* r1 = fft_block<T>(buf[0], buf[1], a.pl, CW, tw_h, 1, (T)-1);
+  cpx<T>* r1 = fft_block<T, false>(buf[0], buf[1], a.pl, CW, tw);
   cpx<T>* free1 = r1 == buf[0] ? buf[1] : buf[0];
   cpx<T>* r2 = nullptr;
   cpx<T>* free2 = nullptr;
   if (!a.single) {
     load(buf[2], 1);
-    r2 = fft_block<T>(buf[2], free1, a.pl, CW, tw_h, 1, (T)-1);
+    r2 = fft_block<T, false>(buf[2], free1, a.pl, CW, tw);
     free2 = r2 == buf[2] ? free1 : buf[2];
   }
   const T eps = (T)a.eps;
@@ -292,7 +419,7 @@ __global__ void __launch_bounds__(kFftThreads) k_col_deconv(ColArgs a, const cpx
     r1[vl * Ph + u] = inv * num;
   }
   __syncthreads();
-  cpx<T>* res = fft_block<T>(r1, a.single ? free1 : free2, a.pl, CW, tw_h, 1, (T)1);
+  cpx<T>* res = fft_block<T, true>(r1, a.single ? free1 : free2, a.pl, CW, tw);
   cpx<T>* dst = (cpx<T>*)a.ihat + (int64_t)fc * a.H * a.Pw2 + v0;
   for (int idx = threadIdx.x; idx < CW * a.H; idx += blockDim.x) {
     const int u = idx / CW, vl = idx % CW;
@@ -305,55 +432,83 @@ struct IRowArgs {
   void* latent;      // TO [n][C][H][W]
   const uint64_t* lat_tab;  // optional per-pair latent addresses ([C][H][W] each)
   int out_f64;
-  int n, H, W, Pw, Pw2, half;
+  int n, H, W, Pw, Pw2, half, nbr;
   double scale;      // 1 / (Ph * Pw)
   FftPlan pl;
 };
 
-// Inverse complex-to-real FFT of every row, crop and scale.
+// Inverse complex-to-real FFT of every row, crop and scale, nbr rows at a time.
 template <typename T>
-__global__ void __launch_bounds__(kFftThreads) k_row_ifft(IRowArgs a, const cpx<T>* tw_w) {
+__global__ void __launch_bounds__(kFftThreads)
+k_row_ifft(IRowArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
   extern __shared__ __align__(16) char smem[];
-  const int N = a.pl.n;
-  cpx<T>* b0 = (cpx<T>*)smem;
-  cpx<T>* b1 = b0 + N;
+  const int N = a.pl.n, NB = a.nbr;
+  cpx<T>* tw = (cpx<T>*)smem;
+  cpx<T>* b0 = tw + ((a.pl.ntw + 1) & ~1);
+  cpx<T>* b1 = b0 + NB * N;
+  load_twiddles(tw, stw, a.pl.ntw);
   const int fc = blockIdx.y;
   const int rows_per = (a.H + gridDim.x - 1) / gridDim.x;
   const int r0 = blockIdx.x * rows_per, r1 = min(a.H, r0 + rows_per);
   const cpx<T>* src = (const cpx<T>*)a.ihat + (int64_t)fc * a.H * a.Pw2;
-  for (int r = r0; r < r1; ++r) {
-    const cpx<T>* X = src + (int64_t)r * a.Pw2;
-    for (int k = threadIdx.x; k < N; k += blockDim.x) {
-      if (a.half) {
-        const cpx<T> xk = X[k], xc = conj(X[N - k]);
-        const cpx<T> e = (T)0.5 * (xk + xc), d = (T)0.5 * (xk - xc);
-        const cpx<T> w = conj(tw_w[k]);        // exp(+2 pi i k / Pw)
-        const cpx<T> o = w * d;
-        b0[k] = mk<T>(e.re - o.im, e.im + o.re);   // E + i O
-      } else {
-        b0[k] = k < a.Pw2 ? X[k] : conj(X[N - k]);
+  void* outp = a.latent;
+  int64_t obase = (int64_t)fc * a.H * a.W;
+  if (a.lat_tab) {
+    const int C = gridDim.y / a.n;
+    outp = (void*)a.lat_tab[fc / C];
+    obase = (int64_t)(fc % C) * a.H * a.W;
+  }
+  const T sc = (T)a.scale;
+  for (int rg = r0; rg < r1; rg += NB) {
+    const int nr = min(NB, r1 - rg);
+    for (int rl = 0; rl < nr; ++rl) {
+      const cpx<T>* X = src + (int64_t)(rg + rl) * a.Pw2;
+      cpx<T>* dst = b0 + rl * N;
+      for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        if (a.half) {
+          const cpx<T> xk = X[k], xc = conj(X[N - k]);
+          const cpx<T> e = (T)0.5 * (xk + xc), d = (T)0.5 * (xk - xc);
+          const cpx<T> o = conj(tw_w[k]) * d;     // exp(+2 pi i k / Pw) d
+          dst[k] = mk<T>(e.re - o.im, e.im + o.re);  // E + i O
+        } else {
+          dst[k] = k < a.Pw2 ? X[k] : conj(X[N - k]);
+        }
       }
     }
     __syncthreads();
-    cpx<T>* z = fft_block<T>(b0, b1, a.pl, 1, tw_w, a.half ? 2 : 1, (T)1);
-    int64_t ob = ((int64_t)fc * a.H + r) * a.W;
-    void* outp = a.latent;
-    if (a.lat_tab) {
-      const int C = gridDim.y / a.n;
-      outp = (void*)a.lat_tab[fc / C];
-      ob = ((int64_t)(fc % C) * a.H + r) * a.W;
-    }
-    const T sc = (T)a.scale;
-    for (int c = threadIdx.x; c < a.W; c += blockDim.x) {
-      T v;
-      if (a.half) v = (c & 1) ? (T)2 * z[c >> 1].im : (T)2 * z[c >> 1].re;
-      else v = z[c].re;
-      v *= sc;
-      if (a.out_f64) ((double*)outp)[ob + c] = (double)v;
-      else ((float*)outp)[ob + c] = (float)v;
+    cpx<T>* Z = fft_block<T, true>(b0, b1, a.pl, nr, tw);
+    for (int rl = 0; rl < nr; ++rl) {
+      const cpx<T>* z = Z + rl * N;
+      const int64_t ob = obase + (int64_t)(rg + rl) * a.W;
+      if (a.half && !a.out_f64 && (((ob * 4 + (uintptr_t)outp) & 7) == 0)) {
+        float2* o2 = (float2*)((float*)outp + ob);
+        for (int m = threadIdx.x; m < (a.W >> 1); m += blockDim.x)
+          o2[m] = make_float2((float)((T)2 * sc * z[m].re), (float)((T)2 * sc * z[m].im));
+        if ((a.W & 1) && threadIdx.x == 0)
+          ((float*)outp)[ob + a.W - 1] = (float)((T)2 * sc * z[a.W >> 1].re);
+      } else {
+        for (int c = threadIdx.x; c < a.W; c += blockDim.x) {
+          T v;
+          if (a.half) v = (c & 1) ? (T)2 * z[c >> 1].im : (T)2 * z[c >> 1].re;
+          else v = z[c].re;
+          v *= sc;
+          if (a.out_f64) ((double*)outp)[ob + c] = (double)v;
+          else ((float*)outp)[ob + c] = (float)v;
+        }
+      }
     }
     __syncthreads();
   }
+}
+
+// rows per CTA iteration: two row buffers + twiddles within ~72 KB
+inline int rows_per_iter(int N, int ntw, size_t ce) {
+  const long budget = 72 * 1024 / (long)ce - (long)((ntw + 1) & ~1);
+  int nb = (int)(budget / (2L * N));
+  if (nb < 1) nb = 1;
+  if (nb > 8) nb = 8;
+  while (nb > 1 && (long)nb * N > 65535) --nb;
+  return nb;
 }
 
 template <typename T>
@@ -379,12 +534,14 @@ void run_row_fft(const Plan& p, const FrameDesc& b1, const FrameDesc& b2, char* 
   a.Pw2 = p.Pw2;
   a.half = p.pw_half;
   a.pl = plw;
+  a.nbr = rows_per_iter(plw.n, plw.ntw, sizeof(cpx<T>));
   const int hmax = p.H1 > p.H2 ? p.H1 : p.H2;
-  const int chunks = (hmax + 7) / 8;
+  const int chunks = (hmax + 2 * a.nbr - 1) / (2 * a.nbr);
   dim3 g(chunks, p.n * p.C, p.single_kernel ? 1 : 2);
-  const size_t sm = 2 * sizeof(cpx<T>) * plw.n;
+  const size_t sm = sizeof(cpx<T>) * (((plw.ntw + 1) & ~1) + 2 * (size_t)a.nbr * plw.n);
   cudaFuncSetAttribute(k_row_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_row_fft<T><<<g, kFftThreads, sm, st>>>(a, (const cpx<T>*)(ws + p.off_tw_w));
+  k_row_fft<T><<<g, kFftThreads, sm, st>>>(a, (const cpx<T>*)(ws + p.off_tw_w),
+                                           (const cpx<T>*)(ws + p.off_stw_r));
 }
 
 template <typename T>
@@ -405,9 +562,9 @@ void run_col_deconv(const Plan& p, char* ws, cudaStream_t st) {
   a.pl = p.fp_h;
   constexpr int CW = sizeof(T) == 4 ? 4 : 2;
   dim3 g((p.Pw2 + CW - 1) / CW, p.n * p.C);
-  const size_t sm = 3 * sizeof(cpx<T>) * CW * p.Ph;
+  const size_t sm = sizeof(cpx<T>) * (((p.fp_h.ntw + 1) & ~1) + 3 * (size_t)CW * p.Ph);
   cudaFuncSetAttribute(k_col_deconv<T, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_col_deconv<T, CW><<<g, kFftThreads, sm, st>>>(a, (const cpx<T>*)(ws + p.off_tw_h));
+  k_col_deconv<T, CW><<<g, kColThreads, sm, st>>>(a, (const cpx<T>*)(ws + p.off_stw_h));
 }
 
 template <typename T>
@@ -418,8 +575,8 @@ void run_row_ifft(const Plan& p, char* ws, void* latent, int out_f64, cudaStream
   a.ihat = ws + p.off_ihat;
   a.latent = latent;
   a.lat_tab = lat_tab;
-  a.n = p.n;
   a.out_f64 = out_f64;
+  a.n = p.n;
   a.H = p.H;
   a.W = p.W;
   a.Pw = p.Pw;
@@ -427,22 +584,28 @@ void run_row_ifft(const Plan& p, char* ws, void* latent, int out_f64, cudaStream
   a.half = p.pw_half;
   a.scale = 1.0 / ((double)p.Ph * (double)p.Pw);
   a.pl = plw;
-  dim3 g((p.H + 7) / 8, p.n * p.C);
-  const size_t sm = 2 * sizeof(cpx<T>) * plw.n;
+  a.nbr = rows_per_iter(plw.n, plw.ntw, sizeof(cpx<T>));
+  dim3 g((p.H + 2 * a.nbr - 1) / (2 * a.nbr), p.n * p.C);
+  const size_t sm = sizeof(cpx<T>) * (((plw.ntw + 1) & ~1) + 2 * (size_t)a.nbr * plw.n);
   cudaFuncSetAttribute(k_row_ifft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_row_ifft<T><<<g, kFftThreads, sm, st>>>(a, (const cpx<T>*)(ws + p.off_tw_w));
+  k_row_ifft<T><<<g, kFftThreads, sm, st>>>(a, (const cpx<T>*)(ws + p.off_tw_w),
+                                            (const cpx<T>*)(ws + p.off_stw_r));
 }
 
 }  // namespace
 
+template <typename T>
+void run_twiddles(const Plan& p, char* ws, cudaStream_t st) {
+  k_twiddles<T><<<(p.Ph + 255) / 256, 256, 0, st>>>((cpx<T>*)(ws + p.off_tw_h), p.Ph);
+  k_twiddles<T><<<(p.Pw + 255) / 256, 256, 0, st>>>((cpx<T>*)(ws + p.off_tw_w), p.Pw);
+  const FftPlan& plw = p.pw_half ? p.fp_w2 : p.fp_w;
+  k_stage_twiddles<T><<<(p.Ph + 255) / 256, 256, 0, st>>>(p.fp_h, (cpx<T>*)(ws + p.off_stw_h));
+  k_stage_twiddles<T><<<(plw.n + 255) / 256, 256, 0, st>>>(plw, (cpx<T>*)(ws + p.off_stw_r));
+}
+
 void init_twiddles(const Plan& p, char* ws, cudaStream_t st) {
-  if (p.fft_f64) {
-    k_twiddles<double><<<(p.Ph + 255) / 256, 256, 0, st>>>((cd*)(ws + p.off_tw_h), p.Ph);
-    k_twiddles<double><<<(p.Pw + 255) / 256, 256, 0, st>>>((cd*)(ws + p.off_tw_w), p.Pw);
-  } else {
-    k_twiddles<float><<<(p.Ph + 255) / 256, 256, 0, st>>>((cf*)(ws + p.off_tw_h), p.Ph);
-    k_twiddles<float><<<(p.Pw + 255) / 256, 256, 0, st>>>((cf*)(ws + p.off_tw_w), p.Pw);
-  }
+  if (p.fft_f64) run_twiddles<double>(p, ws, st);
+  else run_twiddles<float>(p, ws, st);
 }
 
 void launch_kernel_spectra(const Plan& p, char* ws, cudaStream_t st) {

@@ -9,7 +9,7 @@ namespace cbp {
 
 constexpr int kMaxN = 64;      // t1 + t2 (per-sample system width)
 constexpr int kMaxM = 32;      // samples per direction (scale system is 2M wide)
-constexpr int kMaxRadixStages = 24;
+constexpr int kMaxRadixStages = 16;
 
 // One frame batch as the kernels see it.
 struct FrameDesc {
@@ -30,11 +30,22 @@ struct PtrTables {
   const uint64_t* lat = nullptr;
 };
 
-// Mixed-radix FFT plan: N = prod(radix[0..nst)), radices in {2,3,4,5,7,8}.
+// One Stockham stage of radix R: Ns = product of the earlier radices, Nr = N / R,
+// magic multipliers mNs, mNr for exact division by Ns and Nr (0 encodes 1),
+// and the offset of the stage's twiddles w_{Ns R}^{k r} (k < Ns, 1 <= r < R)
+// in the plan's twiddle table.
+struct FftStage {
+  int R, Ns, Nr;
+  uint32_t mNs, mNr;
+  int tw;
+};
+
+// Mixed-radix FFT plan: N = prod of the stages' radices (9, 8, 7, 5, 4, 3, 2).
 struct FftPlan {
   int n;
   int nst;
-  int radix[kMaxRadixStages];
+  int ntw;                     // twiddle-table entries (N - 1, at least 1)
+  FftStage st[kMaxRadixStages];
 };
 
 // Everything one batched call needs: shapes, precisions, workspace layout.
@@ -52,7 +63,7 @@ struct Plan {
   FftPlan fp_h, fp_w, fp_w2;   // plans of Ph, Pw, Pw/2
   // workspace layout (byte offsets into one device allocation)
   size_t off_pz2[2], off_pz1[2];   // cd [n][C][ns][len] sample polynomials (double)
-  size_t off_pz2f[2], off_pz1f[2]; // cf copies for the single-precision Gram (mixed path)
+  size_t off_pz2f[2], off_pz1f[2]; // cdf float-float copies for the mixed path's Gram
   size_t off_x;                    // cd [n][2][ns][nn]
   size_t off_sdiag;                // double [n][2][ns][4]
   size_t off_resid;                // cd [n][2][ns][C][Lmax] (FP64 path residual scratch)
@@ -61,6 +72,7 @@ struct Plan {
   size_t off_bad;                  // int [n] non-finite input flags
   size_t off_diag;                 // cbp_diag [n]
   size_t off_tw_h, off_tw_w;       // cpx<T_fft> twiddles exp(-2 pi i k / P), k < P
+  size_t off_stw_h, off_stw_r;     // cpx<T_fft> stage twiddles of the column and row plans
   size_t off_khat;                 // cpx<T_fft> [n][2][Ph][Pw2]
   size_t off_spec[2];              // cpx<T_fft> [n][C][H_Bk][Pw2]
   size_t off_ihat;                 // cpx<T_fft> [n][C][H][Pw2]

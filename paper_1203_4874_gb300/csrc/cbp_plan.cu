@@ -16,22 +16,35 @@ int next_7_smooth(int n) {
   }
 }
 
+static uint32_t magic_div(int d) {
+  return d <= 1 ? 0u : (uint32_t)(((uint64_t(1) << 32) + (uint64_t)d - 1) / (uint64_t)d);
+}
+
 bool make_fft_plan(int n, FftPlan* p) {
+  if (n < 1) return false;
   p->n = n;
   p->nst = 0;
-  int r = n;
+  int r = n, Ns = 1, off = 0;
   while (r > 1) {
     int R = 0;
-    if (r % 4 == 0) R = 4;
-    else if (r % 2 == 0) R = 2;
-    else if (r % 3 == 0) R = 3;
-    else if (r % 5 == 0) R = 5;
-    else if (r % 7 == 0) R = 7;
-    else return false;
-    if (p->nst >= kMaxRadixStages) return false;
-    p->radix[p->nst++] = R;
+    for (int cand : {9, 8, 7, 5, 4, 3, 2})
+      if (r % cand == 0) {
+        R = cand;
+        break;
+      }
+    if (!R || p->nst >= kMaxRadixStages) return false;
+    FftStage& st = p->st[p->nst++];
+    st.R = R;
+    st.Ns = Ns;
+    st.Nr = n / R;
+    st.mNs = magic_div(Ns);
+    st.mNr = magic_div(st.Nr);
+    st.tw = off;
+    off += Ns * (R - 1);
+    Ns *= R;
     r /= R;
   }
+  p->ntw = off > 0 ? off : 1;
   return true;
 }
 
@@ -111,8 +124,10 @@ cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_param
   const size_t smem_max = 227 * 1024;
   const size_t ce = p.fft_f64 ? 16 : 8;
   const size_t cw = p.fft_f64 ? 2 : 4;
-  if (2 * ce * (p.pw_half ? p.Pw / 2 : p.Pw) > smem_max) return CBP_ERR_UNSUPPORTED;
-  if (3 * ce * cw * p.Ph > smem_max) return CBP_ERR_UNSUPPORTED;
+  const size_t nrow = p.pw_half ? p.Pw / 2 : p.Pw;
+  // one row buffer pair + stage twiddles; exact magic division needs rows * N < 2^16
+  if ((2 + 1) * ce * nrow > smem_max || nrow > 16384) return CBP_ERR_UNSUPPORTED;
+  if ((3 * cw + 1) * ce * p.Ph > smem_max || cw * p.Ph > 65536) return CBP_ERR_UNSUPPORTED;
   if (sample_solve_smem(p.nn) > smem_max || scale_solve_smem(p.M) > smem_max)
     return CBP_ERR_UNSUPPORTED;
 
@@ -129,10 +144,10 @@ cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_param
   p.off_pz1[0] = take(n * C * ns * p.W1 * 16);
   p.off_pz1[1] = take(n * C * ns * p.W2 * 16);
   if (p.mixed) {
-    p.off_pz2f[0] = take(n * C * ns * p.H1 * 8);
-    p.off_pz2f[1] = take(n * C * ns * p.H2 * 8);
-    p.off_pz1f[0] = take(n * C * ns * p.W1 * 8);
-    p.off_pz1f[1] = take(n * C * ns * p.W2 * 8);
+    p.off_pz2f[0] = take(n * C * ns * p.H1 * 16);
+    p.off_pz2f[1] = take(n * C * ns * p.H2 * 16);
+    p.off_pz1f[0] = take(n * C * ns * p.W1 * 16);
+    p.off_pz1f[1] = take(n * C * ns * p.W2 * 16);
   }
   p.off_x = take(n * 2 * ns * p.nn * 16);
   p.off_sdiag = take(n * 2 * ns * 4 * 8);
@@ -145,6 +160,8 @@ cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_param
   p.off_diag = take(n * sizeof(cbp_diag));
   p.off_tw_h = take(p.Ph * ce);
   p.off_tw_w = take(p.Pw * ce);
+  p.off_stw_h = take((size_t)p.fp_h.ntw * ce);
+  p.off_stw_r = take((size_t)(p.pw_half ? p.fp_w2.ntw : p.fp_w.ntw) * ce);
   p.off_khat = take(n * 2 * (size_t)p.Ph * p.Pw2 * ce);
   p.off_spec[0] = take(n * C * (size_t)p.H1 * p.Pw2 * ce);
   p.off_spec[1] = take(n * C * (size_t)p.H2 * p.Pw2 * ce);

@@ -50,7 +50,8 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 // Shared-memory work area of the eigen-solver for an N x N Hermitian matrix.
 struct EigSmem {
   cd* G;       // N*N   double-precision matrix (input, preserved)
-  cd* L;       // NP*NP double-precision working copy (hard samples)
+  cd* L;       // NP*NP double-precision working area (hard samples)
+  cd* Q;       // NP*NP double-precision orthonormal basis (hard samples)
   cf* A;       // NP*NP single-precision working copy -> eigenvalues on the diagonal
   cf* V;       // NP*NP single-precision eigenvectors; with A, the double
                //       eigenvectors of hard samples
@@ -90,26 +91,58 @@ __device__ __forceinline__ void jacobi_pair(int round, int k, int np, int* p, in
   *q = a < b ? b : a;
 }
 
+// Scalar helpers so one Jacobi serves real (float, double) and complex data.
+__device__ __forceinline__ float re_(float x) { return x; }
+__device__ __forceinline__ double re_(double x) { return x; }
+template <typename T> __device__ __forceinline__ T re_(cpx<T> x) { return x.re; }
+__device__ __forceinline__ float cj_(float x) { return x; }
+__device__ __forceinline__ double cj_(double x) { return x; }
+template <typename T> __device__ __forceinline__ cpx<T> cj_(cpx<T> x) { return conj(x); }
+__device__ __forceinline__ float a2_(float x) { return x * x; }
+__device__ __forceinline__ double a2_(double x) { return x * x; }
+template <typename T> __device__ __forceinline__ T a2_(cpx<T> x) { return abs2(x); }
+template <typename E> struct Ops;
+template <> struct Ops<float> {
+  static __device__ float z() { return 0.f; }
+  static __device__ float o() { return 1.f; }
+  static __device__ void clear_im(float&) {}
+  static __device__ bool nz(float x) { return x != 0.f; }
+};
+template <> struct Ops<double> {
+  static __device__ double z() { return 0.0; }
+  static __device__ double o() { return 1.0; }
+  static __device__ void clear_im(double&) {}
+  static __device__ bool nz(double x) { return x != 0.0; }
+};
+template <typename T> struct Ops<cpx<T>> {
+  static __device__ cpx<T> z() { return mk<T>((T)0, (T)0); }
+  static __device__ cpx<T> o() { return mk<T>((T)1, (T)0); }
+  static __device__ void clear_im(cpx<T>& x) { x.im = (T)0; }
+  static __device__ bool nz(cpx<T> x) { return x.re != (T)0 || x.im != (T)0; }
+};
+
 // Cyclic Jacobi (round-robin parallel ordering) on the Hermitian matrix A
-// (n x n inside an ld x ld array, ld even >= n).  On exit A holds the
-// eigenvalues on its diagonal and V the eigenvectors (columns).  A pair is
-// rotated while |a_pq| exceeds both tol_rel sqrt(|a_pp a_qq|) and
-// tol_abs max|a_ii| (the rounding floor of the precision).  Bounded sweeps.
-template <typename T>
-__device__ void jacobi(cpx<T>* A, cpx<T>* V, int n, int ld, EigSmem& S, T tol_rel, T tol_abs) {
+// (n x n inside an ld x ld array, ld even >= n; element type E real or
+// complex, real type R).  V enters as the identity unless keep_v, and leaves
+// with the eigenvectors (columns); A leaves with the eigenvalues on its
+// diagonal.  A pair is rotated while |a_pq| exceeds both
+// tol_rel sqrt(|a_pp a_qq|) and tol_abs max|a_ii| (the rounding floor of the
+// precision).  Bounded sweeps.
+template <typename E, typename R>
+__device__ void jacobi(E* A, E* V, int n, int ld, EigSmem& S, R tol_rel, R tol_abs) {
   const int half = ld / 2;
   const int tid = threadIdx.x, nth = blockDim.x;
-  T* rc = (T*)S.rc;
-  cpx<T>* rs = (cpx<T>*)S.rs;
+  R* rc = (R*)S.rc;
+  E* rs = (E*)S.rs;
   for (int i = tid; i < ld * ld; i += nth) {
-    int r = i / ld, c = i % ld;
-    V[i] = mk<T>(r == c ? (T)1 : (T)0, (T)0);
-    if (r >= n || c >= n) A[i] = mk<T>((T)0, (T)0);
+    const int r = i / ld, c = i % ld;
+    V[i] = r == c ? Ops<E>::o() : Ops<E>::z();
+    if (r >= n || c >= n) A[i] = Ops<E>::z();
   }
   __syncthreads();
-  T amax = 0;
-  for (int i = 0; i < n; ++i) amax = max(amax, (T)fabs(A[i * ld + i].re));
-  const T abs_tol = tol_abs * amax;
+  R amax = 0;
+  for (int i = 0; i < n; ++i) amax = max(amax, (R)fabs(re_(A[i * ld + i])));
+  const R abs_tol = tol_abs * amax;
   for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
     if (tid == 0) S.flag[0] = 0;
     __syncthreads();
@@ -117,18 +150,17 @@ __device__ void jacobi(cpx<T>* A, cpx<T>* V, int n, int ld, EigSmem& S, T tol_re
       for (int k = tid; k < half; k += nth) {
         int p, q;
         jacobi_pair(round, k, ld, &p, &q);
-        T c = 1;
-        cpx<T> sp = mk<T>((T)0, (T)0);
+        R c = 1;
+        E sp = Ops<E>::z();
         if (q < n) {
-          cpx<T> apq = A[p * ld + q];
-          T app = A[p * ld + p].re, aqq = A[q * ld + q].re;
-          T mag = sqrt(abs2(apq));
+          const E apq = A[p * ld + q];
+          const R app = re_(A[p * ld + p]), aqq = re_(A[q * ld + q]);
+          const R mag = sqrt(a2_(apq));
           if (mag > abs_tol && mag > tol_rel * sqrt(fabs(app)) * sqrt(fabs(aqq))) {
-            T tau = (aqq - app) / ((T)2 * mag);
-            T t = (tau >= (T)0 ? (T)1 : (T)-1) / (fabs(tau) + sqrt((T)1 + tau * tau));
-            c = (T)1 / sqrt((T)1 + t * t);
-            T sn = t * c;
-            sp = mk<T>(sn * apq.re / mag, sn * apq.im / mag);
+            const R tau = (aqq - app) / ((R)2 * mag);
+            const R t = (tau >= (R)0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
+            c = (R)1 / sqrt((R)1 + t * t);
+            sp = ((t * c) / mag) * apq;           // s * phase(a_pq)
             S.flag[0] = 1;
           }
         }
@@ -140,39 +172,39 @@ __device__ void jacobi(cpx<T>* A, cpx<T>* V, int n, int ld, EigSmem& S, T tol_re
       __syncthreads();
       // rows p, q:  A <- J^H A
       for (int idx = tid; idx < half * n; idx += nth) {
-        int k = idx / n, j = idx % n;
-        cpx<T> sp = rs[k];
-        if (sp.re == (T)0 && sp.im == (T)0) continue;
-        int p = S.rp[k], q = S.rq[k];
-        T c = rc[k];
-        cpx<T> apj = A[p * ld + j], aqj = A[q * ld + j];
+        const int k = idx / n, j = idx % n;
+        const E sp = rs[k];
+        if (!Ops<E>::nz(sp)) continue;
+        const int p = S.rp[k], q = S.rq[k];
+        const R c = rc[k];
+        const E apj = A[p * ld + j], aqj = A[q * ld + j];
         A[p * ld + j] = c * apj - sp * aqj;
-        A[q * ld + j] = conj(sp) * apj + c * aqj;
+        A[q * ld + j] = cj_(sp) * apj + c * aqj;
       }
       __syncthreads();
       // columns p, q:  A <- A J,  V <- V J
       for (int idx = tid; idx < half * n; idx += nth) {
-        int k = idx / n, i = idx % n;
-        cpx<T> sp = rs[k];
-        if (sp.re == (T)0 && sp.im == (T)0) continue;
-        int p = S.rp[k], q = S.rq[k];
-        T c = rc[k];
-        cpx<T> aip = A[i * ld + p], aiq = A[i * ld + q];
-        A[i * ld + p] = c * aip - conj(sp) * aiq;
+        const int k = idx / n, i = idx % n;
+        const E sp = rs[k];
+        if (!Ops<E>::nz(sp)) continue;
+        const int p = S.rp[k], q = S.rq[k];
+        const R c = rc[k];
+        const E aip = A[i * ld + p], aiq = A[i * ld + q];
+        A[i * ld + p] = c * aip - cj_(sp) * aiq;
         A[i * ld + q] = sp * aip + c * aiq;
-        cpx<T> vip = V[i * ld + p], viq = V[i * ld + q];
-        V[i * ld + p] = c * vip - conj(sp) * viq;
+        const E vip = V[i * ld + p], viq = V[i * ld + q];
+        V[i * ld + p] = c * vip - cj_(sp) * viq;
         V[i * ld + q] = sp * vip + c * viq;
       }
       __syncthreads();
       for (int k = tid; k < half; k += nth) {
-        cpx<T> sp = rs[k];
-        if (sp.re == (T)0 && sp.im == (T)0) continue;
-        int p = S.rp[k], q = S.rq[k];
-        A[p * ld + q] = mk<T>((T)0, (T)0);
-        A[q * ld + p] = mk<T>((T)0, (T)0);
-        A[p * ld + p].im = (T)0;
-        A[q * ld + q].im = (T)0;
+        const E sp = rs[k];
+        if (!Ops<E>::nz(sp)) continue;
+        const int p = S.rp[k], q = S.rq[k];
+        A[p * ld + q] = Ops<E>::z();
+        A[q * ld + p] = Ops<E>::z();
+        Ops<E>::clear_im(A[p * ld + p]);
+        Ops<E>::clear_im(A[q * ld + q]);
       }
       __syncthreads();
     }
@@ -180,6 +212,12 @@ __device__ void jacobi(cpx<T>* A, cpx<T>* V, int n, int ld, EigSmem& S, T tol_re
     __syncthreads();
     if (!rotated) break;
   }
+}
+
+// Component i of single-precision eigenvector l (real or complex storage).
+__device__ __forceinline__ cd v32(const EigSmem& S, bool real, int np, int i, int l) {
+  if (real) return mk((double)((const float*)S.V)[i * np + l], 0.0);
+  return cvt<double>(S.V[i * np + l]);
 }
 
 // y = G x (double), G n x n row-major.
@@ -223,7 +261,7 @@ __device__ cd dotc64(const cd* a, const cd* b, int n, double* red) {
 // Newton correction with the single-precision eigenbasis:
 // x <- normalise(x - sum_{l != imin} v_l (v_l^H res) / (lam_l - theta)),
 // res = r - theta x, r = (accurate) S^H S x.
-__device__ double newton_eigbasis(EigSmem& S, int n, int imin, const cd* r, double theta) {
+__device__ double newton_eigbasis(EigSmem& S, bool real, int n, int imin, const cd* r, double theta) {
   const int np = np_of(n);
   for (int i = threadIdx.x; i < n; i += blockDim.x) S.z[i] = r[i] - theta * S.x[i];  // res
   __syncthreads();
@@ -231,7 +269,7 @@ __device__ double newton_eigbasis(EigSmem& S, int n, int imin, const cd* r, doub
   for (int l = threadIdx.x; l < n; l += blockDim.x) {
     cd c = mk(0.0, 0.0);
     if (l != imin) {
-      for (int i = 0; i < n; ++i) cfmac(c, cvt<double>(S.V[i * np + l]), S.z[i]);
+      for (int i = 0; i < n; ++i) cfmac(c, v32(S, real, np, i, l), S.z[i]);
       double den = S.lam[l] - theta;
       c = (1.0 / den) * c;
     }
@@ -241,7 +279,7 @@ __device__ double newton_eigbasis(EigSmem& S, int n, int imin, const cd* r, doub
   double d2 = 0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     cd dx = mk(0.0, 0.0);
-    for (int l = 0; l < n; ++l) cfma(dx, cvt<double>(S.V[i * np + l]), S.y[l]);
+    for (int l = 0; l < n; ++l) cfma(dx, v32(S, real, np, i, l), S.y[l]);
     S.x[i] = S.x[i] - dx;
     d2 += abs2(dx);
   }
@@ -275,11 +313,35 @@ __device__ void newton_eigbasis64(EigSmem& S, const cd* V, const double* lam, in
 }
 
 
-// Smallest eigenpair of the Hermitian positive semi-definite S.G (n x n).
-// acc_steps further Newton steps use apply(x, out) = S^H S x computed from the
-// original system (exact residual).  Result vector in S.x (unit norm).
+// Orthonormalise the n columns of Q (n x n, leading dimension ld) in double
+// precision: modified Gram-Schmidt with the projections of all later columns
+// done in parallel, applied twice.
+__device__ void orthonormalize_cols(cd* Q, int n, int ld, double* red) {
+  for (int pass = 0; pass < 2; ++pass)
+    for (int k = 0; k < n; ++k) {
+      double s2 = 0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) s2 += abs2(Q[i * ld + k]);
+      s2 = block_sum(s2, red);
+      const double inv = s2 > 0 ? rsqrt(s2) : 0.0;
+      for (int i = threadIdx.x; i < n; i += blockDim.x) Q[i * ld + k] = inv * Q[i * ld + k];
+      __syncthreads();
+      // column j > k: q_j -= (q_k^H q_j) q_k; thread per (j, i) after a per-j dot
+      for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
+        cd d = mk(0.0, 0.0);
+        for (int i = 0; i < n; ++i) cfmac(d, Q[i * ld + k], Q[i * ld + j]);
+        for (int i = 0; i < n; ++i) Q[i * ld + j] = Q[i * ld + j] - d * Q[i * ld + k];
+      }
+      __syncthreads();
+    }
+}
+
+// Smallest eigenpair of the Hermitian positive semi-definite S.G (n x n; real
+// symmetric when `real`).  acc_steps further Newton steps use
+// apply(x, out) = S^H S x computed from the original system (exact residual).
+// Result vector in S.x (unit norm).
 template <class Apply>
-__device__ EigResult smallest_eigvec(EigSmem& S, int n, int acc_steps, const Apply& apply) {
+__device__ EigResult smallest_eigvec(EigSmem& S, int n, bool real, int acc_steps,
+                                     const Apply& apply) {
   const int np = np_of(n);
   if (threadIdx.x == 0) {
     double gs = 0;
@@ -288,13 +350,22 @@ __device__ EigResult smallest_eigvec(EigSmem& S, int n, int acc_steps, const App
   }
   __syncthreads();
   const double gscale = S.sc[4];
-  for (int i = threadIdx.x; i < n * n; i += blockDim.x)
-    S.A[(i / n) * np + (i % n)] = cvt<float>((1.0 / gscale) * S.G[i]);
+  // 1. all eigenpairs in single precision
+  if (real) {
+    float* A = (float*)S.A;
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x)
+      A[(i / n) * np + (i % n)] = (float)(S.G[i].re / gscale);
+    __syncthreads();
+    jacobi<float, float>(A, (float*)S.V, n, np, S, 1e-7f, 4e-7f * (float)n);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) S.lam[i] = gscale * (double)A[i * np + i];
+  } else {
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x)
+      S.A[(i / n) * np + (i % n)] = cvt<float>((1.0 / gscale) * S.G[i]);
+    __syncthreads();
+    jacobi<cf, float>(S.A, S.V, n, np, S, 1e-7f, 4e-7f * (float)n);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) S.lam[i] = gscale * (double)S.A[i * np + i].re;
+  }
   __syncthreads();
-  jacobi<float>(S.A, S.V, n, np, S, 1e-7f, 4e-7f * (float)n);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) S.lam[i] = gscale * (double)S.A[i * np + i].re;
-  __syncthreads();
-  // eigenvalue ordering (thread 0)
   if (threadIdx.x == 0) {
     int i1 = 0;
     double lmax = -1e300;
@@ -307,7 +378,6 @@ __device__ EigResult smallest_eigvec(EigSmem& S, int n, int acc_steps, const App
       if (i != i1 && (i2 < 0 || S.lam[i] < S.lam[i2])) i2 = i;
     if (i2 < 0) i2 = i1;
     S.flag[2] = i1;
-    S.flag[3] = i2;
     S.sc[0] = fmax(lmax, 0.0);
     S.sc[1] = S.lam[i2];
     S.sc[2] = S.lam[i1];
@@ -319,38 +389,94 @@ __device__ EigResult smallest_eigvec(EigSmem& S, int n, int acc_steps, const App
   // single-precision eigenvalues carry errors ~ n u lmax; below a 1e-4 lmax
   // gap the two smallest are not reliably separated
   const bool hard = n > 1 && (S.sc[1] - S.sc[2]) <= 1e-4 * lmax;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) S.x[i] = cvt<double>(S.V[i * np + imin]);
-  __syncthreads();
-  normalize64(S.x, n, S.red);
   double theta;
   if (!hard) {
+    // 2a. Newton steps in double precision on G, preconditioned by the
+    // single-precision eigenbasis
+    for (int i = threadIdx.x; i < n; i += blockDim.x) S.x[i] = v32(S, real, np, i, imin);
+    __syncthreads();
+    normalize64(S.x, n, S.red);
     for (int it = 0; it < 12; ++it) {
       matvec64(S.G, S.x, S.r, n);
       theta = dotre64(S.x, S.r, n, S.red);
-      if (newton_eigbasis(S, n, imin, S.r, theta) < 1e-30) break;
+      if (newton_eigbasis(S, real, n, imin, S.r, theta) < 1e-30) break;
     }
     for (int it = 0; it < acc_steps; ++it) {
-        apply(S.x, S.r);
-        theta = dotre64(S.x, S.r, n, S.red);
-        newton_eigbasis(S, n, imin, S.r, theta);
-      }
-    matvec64(S.G, S.x, S.r, n);
-    theta = dotre64(S.x, S.r, n, S.red);
+      apply(S.x, S.r);
+      theta = dotre64(S.x, S.r, n, S.red);
+      newton_eigbasis(S, real, n, imin, S.r, theta);
+    }
   } else {
-    // Unresolved in single precision (the smallest eigenvalues sit below the
-    // single-precision rounding floor, e.g. the z = 1 sample): full cyclic
-    // Jacobi in double precision on G.  The working copy lives in S.L, the
-    // eigenvectors in the (now free) single-precision arrays.
-    const int ld = np;
-    cd* A64 = S.L;                 // ld x ld
-    cd* V64 = (cd*)S.A;            // A and V (float) are contiguous: ld x ld complex doubles
-    for (int i = threadIdx.x; i < ld * ld; i += blockDim.x) {
-      const int r = i / ld, c = i % ld;
-      A64[i] = (r < n && c < n) ? S.G[r * n + c] : mk(0.0, 0.0);
+    // 2b. Unresolved in single precision (the smallest eigenvalues sit below
+    // its rounding floor, e.g. the z = 1 sample): Jacobi in double precision,
+    // started from the single-precision eigenbasis made orthonormal in double
+    // precision, so only the unresolved cluster still needs rotations.
+    cd* Q = S.Q;
+    cd* T1 = S.L;
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x)
+      Q[(i / n) * np + (i % n)] = v32(S, real, np, i / n, i % n);
+    __syncthreads();
+    orthonormalize_cols(Q, n, np, S.red);
+    // T1 = G Q
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int i = idx / n, l = idx % n;
+      cd acc = mk(0.0, 0.0);
+      for (int j = 0; j < n; ++j) cfma(acc, S.G[i * n + j], Q[j * np + l]);
+      T1[i * np + l] = acc;
     }
     __syncthreads();
-    jacobi<double>(A64, V64, n, ld, S, 1e-15, 1e-17 * (double)n);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) S.lam[i] = A64[i * ld + i].re;
+    // A0 = Q^H T1 into the (now free) single-precision area; W into T1's area
+    // after A0 is formed
+    cd* A0 = (cd*)S.A;
+    for (int idx = threadIdx.x; idx < np * np; idx += blockDim.x) {
+      const int i = idx / np, l = idx % np;
+      cd acc = mk(0.0, 0.0);
+      if (i < n && l < n)
+        for (int j = 0; j < n; ++j) cfmac(acc, Q[j * np + i], T1[j * np + l]);
+      if (real) ((double*)A0)[idx] = acc.re;
+      else A0[idx] = acc;
+    }
+    __syncthreads();
+    if (real) {   // exact symmetry, then real Jacobi
+      double* A = (double*)A0;
+      for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int i = idx / n, l = idx % n;
+        if (l > i) {
+          const double m = 0.5 * (A[i * np + l] + A[l * np + i]);
+          A[i * np + l] = m;
+          A[l * np + i] = m;
+        }
+      }
+      __syncthreads();
+      jacobi<double, double>(A, (double*)T1, n, np, S, 1e-15, 1e-17 * (double)n);
+      for (int i = threadIdx.x; i < n; i += blockDim.x) S.lam[i] = A[i * np + i];
+    } else {
+      for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        const int i = idx / n, l = idx % n;
+        if (l > i) {
+          const cd m = 0.5 * (A0[i * np + l] + conj(A0[l * np + i]));
+          A0[i * np + l] = m;
+          A0[l * np + i] = conj(m);
+        } else if (l == i) {
+          A0[i * np + i].im = 0.0;
+        }
+      }
+      __syncthreads();
+      jacobi<cd, double>(A0, T1, n, np, S, 1e-15, 1e-17 * (double)n);
+      for (int i = threadIdx.x; i < n; i += blockDim.x) S.lam[i] = A0[i * np + i].re;
+    }
+    __syncthreads();
+    // V64 = Q W, into the A0 area (its diagonal is saved in lam; W stays in T1)
+    cd* V64 = A0;
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int i = idx / n, l = idx % n;
+      cd acc = mk(0.0, 0.0);
+      if (real)
+        for (int j = 0; j < n; ++j) acc = acc + ((const double*)T1)[j * np + l] * Q[i * np + j];
+      else
+        for (int j = 0; j < n; ++j) cfma(acc, Q[i * np + j], T1[j * np + l]);
+      V64[i * np + l] = acc;
+    }
     __syncthreads();
     if (threadIdx.x == 0) {
       int i1 = 0;
@@ -365,17 +491,17 @@ __device__ EigResult smallest_eigvec(EigSmem& S, int n, int acc_steps, const App
     __syncthreads();
     const int i1 = S.flag[2];
     lam2 = S.sc[1];
-    for (int i = threadIdx.x; i < n; i += blockDim.x) S.x[i] = V64[i * ld + i1];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) S.x[i] = V64[i * np + i1];
     __syncthreads();
     normalize64(S.x, n, S.red);
     if (acc_steps > 0) {
       apply(S.x, S.r);
       theta = dotre64(S.x, S.r, n, S.red);
-      newton_eigbasis64(S, V64, S.lam, n, ld, i1, S.r, theta);
+      newton_eigbasis64(S, V64, S.lam, n, np, i1, S.r, theta);
     }
-    matvec64(S.G, S.x, S.r, n);
-    theta = dotre64(S.x, S.r, n, S.red);
   }
+  matvec64(S.G, S.x, S.r, n);
+  theta = dotre64(S.x, S.r, n, S.red);
   EigResult res;
   res.lam_max = lmax;
   res.lam_2 = lam2;
@@ -394,6 +520,7 @@ __device__ char* carve_eig(EigSmem& S, char* p, int n) {
   };
   S.G = (cd*)take(sizeof(cd) * n * n);
   S.L = (cd*)take(sizeof(cd) * np * np);
+  S.Q = (cd*)take(sizeof(cd) * np * np);
   S.A = (cf*)take(sizeof(cf) * np * np);
   S.V = (cf*)take(sizeof(cf) * np * np);
   S.x = (cd*)take(sizeof(cd) * n);
@@ -414,7 +541,7 @@ __device__ char* carve_eig(EigSmem& S, char* p, int n) {
 size_t eig_smem_bytes(int n) {
   const int np = (n + 1) & ~1;
   auto r = [](size_t b) { return (b + 15) & ~size_t(15); };
-  return r(sizeof(cd) * n * n) + r(sizeof(cd) * np * np) + r(sizeof(cf) * np * np) * 2 + r(sizeof(cd) * n) * 4 + r(sizeof(double) * n) +
+  return r(sizeof(cd) * n * n) + r(sizeof(cd) * np * np) * 2 + r(sizeof(cf) * np * np) * 2 + r(sizeof(cd) * n) * 4 + r(sizeof(double) * n) +
          r(sizeof(double) * np / 2) + r(sizeof(cd) * np / 2) + r(sizeof(int) * np / 2) * 2 +
          r(sizeof(double) * 32) + r(sizeof(int) * 4) + r(sizeof(double) * 8);
 }
@@ -422,12 +549,12 @@ size_t eig_smem_bytes(int n) {
 // ------------------------------------------------------ per-sample solve ---
 struct SampleArgs {
   const cd* pz[2][2];        // [pass][frame] double samples [n][C][ns][len]
-  const cf* pzf[2][2];       // [pass][frame] float copies (mixed path), same layout
+  const cdf* pzf[2][2];      // [pass][frame] float-float copies (mixed path), same layout
   int len[2][2];             // [pass][frame]
   cd* X;                     // [n][2][ns][nn]
   double* sdiag;             // [n][2][ns][4]
   cd* resid;                 // [n][2][ns][C][Lmax]
-  int Lmax, C, ns, t1, t2, nn, mixed;
+  int Lmax, C, ns, t1, t2, nn, M, mixed;
 };
 
 // Sample polynomial element m of frame k (0: b1, 1: b2) as cpx<TA>.
@@ -473,6 +600,103 @@ __device__ void correlations(const SamplePolys<TP, TA>& P, int C, int t1, int t2
       for (int m = m0 + lane; m < m1; m += 32) cfmac(acc, P.ld(ka, ch, m), P.ld(kb, ch, m + d));
     double re = warp_sum((double)acc.re), im = warp_sum((double)acc.im);
     if (lane == 0) rho[j] = mk(re, im);
+  }
+  __syncthreads();
+}
+
+// rho jobs as above for real samples (z = 1, and z = -1 when M is even):
+// real double correlations of the real parts.
+__device__ void correlations_real(const SamplePolys<double, double>& P, int C, int t1, int t2,
+                                  cd* rho) {
+  const int J = 2 * (t1 + t2) - 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = warp; j < J; j += nw) {
+    int ka, kb, d;
+    if (j < t1) { ka = 1; kb = 1; d = j; }
+    else if (j < t1 + t2) { ka = 0; kb = 0; d = j - t1; }
+    else { ka = 1; kb = 0; d = j - t1 - t2 - (t2 - 1); }
+    const int la = P.len[ka], lb = P.len[kb];
+    const int m0 = d < 0 ? -d : 0;
+    const int m1 = min(la, lb - d);
+    double acc = 0;
+    for (int ch = 0; ch < C; ++ch) {
+      const cd* a = P.c[ka] + ch * P.cstride[ka];
+      const cd* b = P.c[kb] + ch * P.cstride[kb];
+      for (int m = m0 + lane; m < m1; m += 32) acc = fma(a[m].re, b[m + d].re, acc);
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) rho[j] = mk(acc, 0.0);
+  }
+  __syncthreads();
+}
+
+// Float-float accumulation (hi + lo) on the single-precision units.
+struct FF {
+  float hi = 0.f, lo = 0.f;
+  // += a * b for float-float a, b: exact product of the high parts (FMA) plus
+  // the cross terms, added with TwoSum and renormalised.
+  __device__ __forceinline__ void mac(float ah, float al, float bh, float bl) {
+    const float p = ah * bh;
+    float e = fmaf(ah, bh, -p);
+    e = fmaf(ah, bl, fmaf(al, bh, e));
+    const float t = hi + p;
+    const float z = t - hi;
+    const float err = (hi - (t - z)) + (p - z);
+    const float l = lo + err + e;
+    hi = t + l;                    // renormalise (Fast2Sum, |t| >= |l|)
+    lo = l - (hi - t);
+  }
+  __device__ __forceinline__ void add(float bh, float bl) {
+    const float t = hi + bh;
+    const float z = t - hi;
+    const float err = (hi - (t - z)) + (bh - z);
+    const float l = lo + err + bl;
+    hi = t + l;
+    lo = l - (hi - t);
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+
+__device__ __forceinline__ FF warp_sum_ff(FF v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const float h = __shfl_xor_sync(0xffffffffu, v.hi, o);
+    const float l = __shfl_xor_sync(0xffffffffu, v.lo, o);
+    v.add(h, l);
+  }
+  return v;
+}
+
+// rho jobs as above from float-float samples: conj(a) b accumulated in
+// float-float, about 1e-13 relative, on the single-precision units.
+__device__ void correlations_ff(const cdf* const base[2], const int len[2], int f, int C, int ns,
+                                int s, int t1, int t2, cd* rho) {
+  const int J = 2 * (t1 + t2) - 1;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int j = warp; j < J; j += nw) {
+    int ka, kb, d;
+    if (j < t1) { ka = 1; kb = 1; d = j; }
+    else if (j < t1 + t2) { ka = 0; kb = 0; d = j - t1; }
+    else { ka = 1; kb = 0; d = j - t1 - t2 - (t2 - 1); }
+    const int la = len[ka], lb = len[kb];
+    const int m0 = d < 0 ? -d : 0;
+    const int m1 = min(la, lb - d);
+    FF re, im;
+    for (int ch = 0; ch < C; ++ch) {
+      const cdf* a = base[ka] + ((int64_t)(f * C + ch) * ns + s) * la;
+      const cdf* b = base[kb] + ((int64_t)(f * C + ch) * ns + s) * lb;
+      for (int m = m0 + lane; m < m1; m += 32) {
+        const cdf x = a[m], y = b[m + d];
+        // conj(x) y = (xr yr + xi yi) + i (xr yi - xi yr)
+        re.mac(x.rh, x.rl, y.rh, y.rl);
+        re.mac(x.ih, x.il, y.ih, y.il);
+        im.mac(x.rh, x.rl, y.ih, y.il);
+        im.mac(-x.ih, -x.il, y.rh, y.rl);
+      }
+    }
+    re = warp_sum_ff(re);
+    im = warp_sum_ff(im);
+    if (lane == 0) rho[j] = mk(re.value(), im.value());
   }
   __syncthreads();
 }
@@ -552,26 +776,27 @@ __global__ void __launch_bounds__(kSolveThreads) k_sample_solve(SampleArgs a) {
   EigSmem S;
   char* p = carve_eig(S, smem, n);
   cd* rho = (cd*)p;
-  // Gram: single precision on the mixed path except at the z = 1 sample
-  // (s = 0: highest signal-to-noise, smallest relative eigen-gaps).
-  if (a.mixed && s != 0)
-    correlations(sample_polys<float, float>(a.pzf[ps], a.len[ps], f, a.C, a.ns, s), a.C, a.t1,
-                 a.t2, rho);
-  else
-    correlations(sample_polys<double, double>(a.pz[ps], a.len[ps], f, a.C, a.ns, s), a.C, a.t1,
-                 a.t2, rho);
+  // Real samples (z = 1; z = -1 when M is even) have real Gram matrices.
+  const bool real = s == 0 || 2 * s == a.M;
+  const SamplePolys<double, double> P64 =
+      sample_polys<double, double>(a.pz[ps], a.len[ps], f, a.C, a.ns, s);
+  if (real) correlations_real(P64, a.C, a.t1, a.t2, rho);
+  else if (a.mixed) correlations_ff(a.pzf[ps], a.len[ps], f, a.C, a.ns, s, a.t1, a.t2, rho);
+  else correlations(P64, a.C, a.t1, a.t2, rho);
   gram_from_rho(rho, a.t1, a.t2, S.G);
-  // Refinement against the exact residual S^H S x from the double samples:
-  // two steps on the FP64 path, one on the mixed path.
+  // FP64 path: two Newton steps against the exact residual S^H S x from the
+  // double samples (removes the squared conditioning of the normal matrix).
+  // Mixed path: the float-float / double normal matrix is accurate to ~1e-13,
+  // enough for its tolerance, and no residual steps are taken.
   SylvesterApply ap;
-  ap.P = sample_polys<double, double>(a.pz[ps], a.len[ps], f, a.C, a.ns, s);
+  ap.P = P64;
   ap.C = a.C;
   ap.t1 = a.t1;
   ap.t2 = a.t2;
   ap.L = a.len[ps][0] + a.t2 - 1;
   ap.y = a.resid + (((int64_t)f * 2 + ps) * a.ns + s) * a.C * (int64_t)a.Lmax;
   ap.red = S.red;
-  const EigResult res = smallest_eigvec(S, n, a.mixed ? 1 : 2, ap);
+  const EigResult res = smallest_eigvec(S, n, real, a.mixed ? 0 : 2, ap);
   const int64_t o = ((int64_t)f * 2 + ps) * a.ns + s;
   for (int i = threadIdx.x; i < n; i += blockDim.x) a.X[o * n + i] = S.x[i];
   if (threadIdx.x == 0) {
@@ -694,7 +919,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
   }
   __syncthreads();
   ScaleApply ap{ab, M};
-  EigResult res = smallest_eigvec(S, n, 2, ap);
+  EigResult res = smallest_eigvec(S, n, false, 2, ap);
   // X_k[i][j] = (gamma_j A_k[i][j] + delta_i B_k[i][j]) / 2
   for (int idx = threadIdx.x; idx < 2 * MM; idx += blockDim.x) {
     const int k = idx / MM, i = (idx % MM) / M, j = idx % M;
@@ -831,8 +1056,8 @@ void launch_sample_solve(const Plan& p, char* ws, cudaStream_t st) {
   for (int k = 0; k < 2; ++k) {
     a.pz[0][k] = (const cd*)(ws + p.off_pz2[k]);
     a.pz[1][k] = (const cd*)(ws + p.off_pz1[k]);
-    a.pzf[0][k] = p.mixed ? (const cf*)(ws + p.off_pz2f[k]) : nullptr;
-    a.pzf[1][k] = p.mixed ? (const cf*)(ws + p.off_pz1f[k]) : nullptr;
+    a.pzf[0][k] = p.mixed ? (const cdf*)(ws + p.off_pz2f[k]) : nullptr;
+    a.pzf[1][k] = p.mixed ? (const cdf*)(ws + p.off_pz1f[k]) : nullptr;
   }
   a.len[0][0] = p.H1;
   a.len[0][1] = p.H2;
@@ -847,6 +1072,7 @@ void launch_sample_solve(const Plan& p, char* ws, cudaStream_t st) {
   a.t1 = p.t1;
   a.t2 = p.t2;
   a.nn = p.nn;
+  a.M = p.M;
   a.mixed = p.mixed;
   const size_t sm = sample_solve_smem(p.nn);
   dim3 grid(p.ns, 2, p.n);
