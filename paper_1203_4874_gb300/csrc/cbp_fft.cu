@@ -243,8 +243,8 @@ __global__ void k_twiddles(cpx<T>* tw, int n) {
 // kv[p][v] = sum_q K[p][q] w_Pw^{vq} (double), then K^[u][v] = sum_p kv[p][v] w_Ph^{up}.
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads)
-k_kernel_spectra(const double* kd, int t1, int t2, int Ph, int Pw, int Pw2, const cpx<T>* tw_h,
-                 const cpx<T>* tw_w, cpx<T>* khat) {
+k_kernel_spectra(const double* kd, int t1, int t2, int Ph, int Pw, int Pw2, int Pw2p,
+                 const cpx<T>* tw_h, const cpx<T>* tw_w, cpx<T>* khat) {
   constexpr int CW = 16;
   __shared__ cpx<T> kv[kMaxN * CW];
   const int k = blockIdx.y, f = blockIdx.z;
@@ -265,7 +265,7 @@ k_kernel_spectra(const double* kd, int t1, int t2, int Ph, int Pw, int Pw2, cons
     kv[idx] = cvt<T>(acc);
   }
   __syncthreads();
-  cpx<T>* out = khat + ((int64_t)f * 2 + k) * Ph * Pw2;
+  cpx<T>* out = khat + ((int64_t)f * 2 + k) * Ph * Pw2p;
   for (int idx = threadIdx.x; idx < Ph * CW; idx += blockDim.x) {
     const int u = idx / CW, vl = idx % CW, v = v0 + vl;
     if (v >= Pw2) continue;
@@ -276,14 +276,14 @@ k_kernel_spectra(const double* kd, int t1, int t2, int Ph, int Pw, int Pw2, cons
       e += u;
       if (e >= Ph) e -= Ph;
     }
-    out[(int64_t)u * Pw2 + v] = acc;
+    out[(int64_t)u * Pw2p + v] = acc;
   }
 }
 
 struct RowArgs {
   FrameDesc fr[2];
   void* spec[2];     // cpx<T> [n][C][H_Bk][Pw2]
-  int Pw, Pw2, half, nbr;
+  int Pw, Pw2, Pw2p, half, nbr;
   FftPlan pl;        // plan of Pw/2 (half) or Pw
 };
 
@@ -302,7 +302,7 @@ k_row_fft(RowArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
   const int fc = blockIdx.y, f = fc / fr.c, ch = fc % fr.c;
   const int rows_per = (fr.h + gridDim.x - 1) / gridDim.x;
   const int r0 = blockIdx.x * rows_per, r1 = min(fr.h, r0 + rows_per);
-  cpx<T>* spec = (cpx<T>*)a.spec[blockIdx.z] + (int64_t)fc * fr.h * a.Pw2;
+  cpx<T>* spec = (cpx<T>*)a.spec[blockIdx.z] + (int64_t)fc * fr.h * a.Pw2p;
   const void* fb = frame_base(fr, f);
   for (int rg = r0; rg < r1; rg += NB) {
     const int nr = min(NB, r1 - rg);
@@ -339,7 +339,7 @@ k_row_fft(RowArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
     cpx<T>* Z = fft_block<T, false>(b0, b1, a.pl, nr, tw);
     for (int rl = 0; rl < nr; ++rl) {
       const cpx<T>* z = Z + rl * N;
-      cpx<T>* out = spec + (int64_t)(rg + rl) * a.Pw2;
+      cpx<T>* out = spec + (int64_t)(rg + rl) * a.Pw2p;
       for (int k = threadIdx.x; k < a.Pw2; k += blockDim.x) {
         if (a.half) {
           const cpx<T> zk = z[k < N ? k : 0], zc = conj(z[k > 0 ? N - k : 0]);
@@ -356,74 +356,161 @@ k_row_fft(RowArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
 }
 
 struct ColArgs {
-  void* spec[2];      // cpx<T> [n][C][H_Bk][Pw2]
-  const void* khat;   // cpx<T> [n][2][Ph][Pw2]
-  void* ihat;         // cpx<T> [n][C][H][Pw2]
-  int H1, H2, H, C, Ph, Pw2, single;
+  void* spec[2];      // cpx<T> [n][C][H_Bk][Pw2p]
+  const void* khat;   // cpx<T> [n][2][Ph][Pw2p]
+  void* ihat;         // cpx<T> [n][C][H][Pw2p]
+  const void* stw;    // stage twiddles of the Ph plan (read through L1)
+  int H1, H2, H, C, Ph, Pw2, Pw2p, single;
   double eps;
   FftPlan pl;         // plan of Ph
 };
 
 constexpr int kColThreads = 512;
 
-// Column FFTs of both spectra, dual-kernel formula, inverse column FFT.
-// Shared memory: stage twiddles, then three buffers of CW columns.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, int src_bytes) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gsrc), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+__device__ __forceinline__ cf ldg_cpx(const cf* p) {
+  const float2 v = __ldg((const float2*)p);
+  return mk(v.x, v.y);
+}
+__device__ __forceinline__ cd ldg_cpx(const cd* p) {
+  const double2 v = __ldg((const double2*)p);
+  return mk(v.x, v.y);
+}
+
+// Stockham stage over NB transforms interleaved in shared memory: element j
+// of transform b at j * NB + b (consecutive threads take consecutive b).
+template <typename T, bool Inv, int R, int NB>
+__device__ __forceinline__ void stockham_stage_il(const cpx<T>* __restrict__ in,
+                                                  cpx<T>* __restrict__ out, const FftStage& st,
+                                                  const cpx<T>* __restrict__ tw) {
+  const int Nr = st.Nr, Ns = st.Ns;
+  for (int idx = threadIdx.x; idx < NB * Nr; idx += blockDim.x) {
+    const int b = idx % NB, j = idx / NB;
+    const int q = st.mNs ? (int)__umulhi((unsigned)j, st.mNs) : j;
+    const int k = j - q * Ns;
+    const cpx<T>* src = in + j * NB + b;
+    cpx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[r * Nr * NB];
+    if (Ns > 1) {
+      const cpx<T>* w = tw + st.tw + k * (R - 1);
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        cpx<T> ww = ldg_cpx(w + r - 1);
+        if (Inv) ww.im = -ww.im;
+        v[r] = v[r] * ww;
+      }
+    }
+    small_dft<T, Inv, R>(v);
+    cpx<T>* dst = out + (q * Ns * R + k) * NB + b;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[r * Ns * NB] = v[r];
+  }
+}
+
+template <typename T, bool Inv, int NB>
+__device__ cpx<T>* fft_block_il(cpx<T>* a, cpx<T>* b, const FftPlan& pl, const cpx<T>* tw) {
+  for (int s = 0; s < pl.nst; ++s) {
+    const FftStage& st = pl.st[s];
+    switch (st.R) {
+      case 2: stockham_stage_il<T, Inv, 2, NB>(a, b, st, tw); break;
+      case 3: stockham_stage_il<T, Inv, 3, NB>(a, b, st, tw); break;
+      case 4: stockham_stage_il<T, Inv, 4, NB>(a, b, st, tw); break;
+      case 5: stockham_stage_il<T, Inv, 5, NB>(a, b, st, tw); break;
+      case 7: stockham_stage_il<T, Inv, 7, NB>(a, b, st, tw); break;
+      case 8: stockham_stage_il<T, Inv, 8, NB>(a, b, st, tw); break;
+      default: stockham_stage_il<T, Inv, 9, NB>(a, b, st, tw); break;
+    }
+    __syncthreads();
+    cpx<T>* tmp = a;
+    a = b;
+    b = tmp;
+  }
+  return a;
+}
+
+// Asynchronous copy of a CW-column strip of one spectrum (rows < Hk; rows
+// Hk..Ph-1 and columns >= Pw2 zero-filled) into an interleaved buffer.
 template <typename T, int CW>
-__global__ void __launch_bounds__(kColThreads)
-k_col_deconv(ColArgs a, const cpx<T>* stw) {
+__device__ __forceinline__ void load_strip_async(cpx<T>* dst, const cpx<T>* src, int Hk, int Ph,
+                                                 int Pw2p, int ncols) {
+  constexpr int E16 = 16 / (int)sizeof(cpx<T>);     // elements per 16-byte chunk
+  constexpr int CH = CW / E16;                      // chunks per row
+  for (int idx = threadIdx.x; idx < Ph * CH; idx += blockDim.x) {
+    const int u = idx / CH, c = idx % CH;
+    const int valid = u < Hk ? min(E16, max(0, ncols - c * E16)) : 0;
+    const cpx<T>* g = valid ? src + (int64_t)u * Pw2p + c * E16 : src;
+    cp_async16(dst + u * CW + c * E16, g, valid * (int)sizeof(cpx<T>));
+  }
+  cp_async_commit();
+}
+
+// Column FFTs of both spectra, dual-kernel formula, inverse column FFT.  Both
+// frames' strips are fetched asynchronously up front; the second arrives
+// while the first is transformed.  Three interleaved buffers of CW columns.
+template <typename T, int CW>
+__global__ void __launch_bounds__(kColThreads, 2)
+k_col_deconv(ColArgs a) {
   extern __shared__ __align__(16) char smem[];
   const int Ph = a.Ph;
-  cpx<T>* tw = (cpx<T>*)smem;
-  cpx<T>* buf[3];
-  buf[0] = tw + ((a.pl.ntw + 1) & ~1);
-  buf[1] = buf[0] + CW * Ph;
-  buf[2] = buf[1] + CW * Ph;
-  load_twiddles(tw, stw, a.pl.ntw);
+  cpx<T>* buf0 = (cpx<T>*)smem;
+  cpx<T>* buf1 = buf0 + CW * Ph;
+  cpx<T>* buf2 = buf1 + CW * Ph;
+  const cpx<T>* tw = (const cpx<T>*)a.stw;
   const int fc = blockIdx.y, f = fc / a.C;
   const int v0 = blockIdx.x * CW;
   const int nv = min(CW, a.Pw2 - v0);
-  auto load = [&](cpx<T>* dst, int k) {
-    const int Hk = k ? a.H2 : a.H1;
-    const cpx<T>* src = (const cpx<T>*)a.spec[k] + (int64_t)fc * Hk * a.Pw2 + v0;
-    for (int idx = threadIdx.x; idx < CW * Ph; idx += blockDim.x) {
-      const int u = idx / CW, vl = idx % CW;
-      dst[vl * Ph + u] = (u < Hk && vl < nv) ? src[(int64_t)u * a.Pw2 + vl] : mk<T>(0, 0);
-    }
-    __syncthreads();
-  };
-  const cpx<T>* K1 = (const cpx<T>*)a.khat + ((int64_t)f * 2 + 0) * Ph * a.Pw2 + v0;
-  const cpx<T>* K2 = (const cpx<T>*)a.khat + ((int64_t)f * 2 + 1) * Ph * a.Pw2 + v0;
-  load(buf[0], 0);
-  cpx<T>* r1 = fft_block<T, false>(buf[0], buf[1], a.pl, CW, tw);
-  cpx<T>* free1 = r1 == buf[0] ? buf[1] : buf[0];
+  load_strip_async<T, CW>(buf0, (const cpx<T>*)a.spec[0] + (int64_t)fc * a.H1 * a.Pw2p + v0, a.H1,
+                          Ph, a.Pw2p, nv);
+  if (!a.single)
+    load_strip_async<T, CW>(buf2, (const cpx<T>*)a.spec[1] + (int64_t)fc * a.H2 * a.Pw2p + v0,
+                            a.H2, Ph, a.Pw2p, nv);
+  if (a.single) cp_async_wait<0>();
+  else cp_async_wait<1>();
+  __syncthreads();
+  cpx<T>* r1 = fft_block_il<T, false, CW>(buf0, buf1, a.pl, tw);
+  cpx<T>* free1 = r1 == buf0 ? buf1 : buf0;
   cpx<T>* r2 = nullptr;
   cpx<T>* free2 = nullptr;
   if (!a.single) {
-    load(buf[2], 1);
-    r2 = fft_block<T, false>(buf[2], free1, a.pl, CW, tw);
-    free2 = r2 == buf[2] ? free1 : buf[2];
+    cp_async_wait<0>();
+    __syncthreads();
+    r2 = fft_block_il<T, false, CW>(buf2, free1, a.pl, tw);
+    free2 = r2 == buf2 ? free1 : buf2;
   }
+  const cpx<T>* K1 = (const cpx<T>*)a.khat + ((int64_t)f * 2 + 0) * Ph * a.Pw2p + v0;
+  const cpx<T>* K2 = (const cpx<T>*)a.khat + ((int64_t)f * 2 + 1) * Ph * a.Pw2p + v0;
   const T eps = (T)a.eps;
   for (int idx = threadIdx.x; idx < CW * Ph; idx += blockDim.x) {
     const int u = idx / CW, vl = idx % CW;
     if (vl >= nv) continue;
-    const cpx<T> k1 = K1[(int64_t)u * a.Pw2 + vl];
-    cpx<T> num = cmulc(k1, r1[vl * Ph + u]);
+    const cpx<T> k1 = K1[(int64_t)u * a.Pw2p + vl];
+    cpx<T> num = cmulc(k1, r1[idx]);
     T den = abs2(k1) + eps;
     if (!a.single) {
-      const cpx<T> k2 = K2[(int64_t)u * a.Pw2 + vl];
-      num = num + cmulc(k2, r2[vl * Ph + u]);
+      const cpx<T> k2 = K2[(int64_t)u * a.Pw2p + vl];
+      num = num + cmulc(k2, r2[idx]);
       den += abs2(k2);
     }
     const T inv = den != (T)0 ? (T)1 / den : (T)0;
-    r1[vl * Ph + u] = inv * num;
+    r1[idx] = inv * num;
   }
   __syncthreads();
-  cpx<T>* res = fft_block<T, true>(r1, a.single ? free1 : free2, a.pl, CW, tw);
-  cpx<T>* dst = (cpx<T>*)a.ihat + (int64_t)fc * a.H * a.Pw2 + v0;
+  cpx<T>* res = fft_block_il<T, true, CW>(r1, a.single ? free1 : free2, a.pl, tw);
+  cpx<T>* dst = (cpx<T>*)a.ihat + (int64_t)fc * a.H * a.Pw2p + v0;
   for (int idx = threadIdx.x; idx < CW * a.H; idx += blockDim.x) {
     const int u = idx / CW, vl = idx % CW;
-    if (vl < nv) dst[(int64_t)u * a.Pw2 + vl] = res[vl * Ph + u];
+    if (vl < nv) dst[(int64_t)u * a.Pw2p + vl] = res[idx];
   }
 }
 
@@ -432,7 +519,7 @@ struct IRowArgs {
   void* latent;      // TO [n][C][H][W]
   const uint64_t* lat_tab;  // optional per-pair latent addresses ([C][H][W] each)
   int out_f64;
-  int n, H, W, Pw, Pw2, half, nbr;
+  int n, H, W, Pw, Pw2, Pw2p, half, nbr;
   double scale;      // 1 / (Ph * Pw)
   FftPlan pl;
 };
@@ -450,7 +537,7 @@ k_row_ifft(IRowArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
   const int fc = blockIdx.y;
   const int rows_per = (a.H + gridDim.x - 1) / gridDim.x;
   const int r0 = blockIdx.x * rows_per, r1 = min(a.H, r0 + rows_per);
-  const cpx<T>* src = (const cpx<T>*)a.ihat + (int64_t)fc * a.H * a.Pw2;
+  const cpx<T>* src = (const cpx<T>*)a.ihat + (int64_t)fc * a.H * a.Pw2p;
   void* outp = a.latent;
   int64_t obase = (int64_t)fc * a.H * a.W;
   if (a.lat_tab) {
@@ -462,7 +549,7 @@ k_row_ifft(IRowArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
   for (int rg = r0; rg < r1; rg += NB) {
     const int nr = min(NB, r1 - rg);
     for (int rl = 0; rl < nr; ++rl) {
-      const cpx<T>* X = src + (int64_t)(rg + rl) * a.Pw2;
+      const cpx<T>* X = src + (int64_t)(rg + rl) * a.Pw2p;
       cpx<T>* dst = b0 + rl * N;
       for (int k = threadIdx.x; k < N; k += blockDim.x) {
         if (a.half) {
@@ -517,7 +604,7 @@ void run_kernel_spectra(const Plan& p, char* ws, cudaStream_t st) {
   const cpx<T>* tw_w = (const cpx<T>*)(ws + p.off_tw_w);
   dim3 g((p.Pw2 + 15) / 16, 2, p.n);
   k_kernel_spectra<T><<<g, kFftThreads, 0, st>>>((const double*)(ws + p.off_kd), p.t1, p.t2, p.Ph,
-                                                 p.Pw, p.Pw2, tw_h, tw_w,
+                                                 p.Pw, p.Pw2, p.Pw2p, tw_h, tw_w,
                                                  (cpx<T>*)(ws + p.off_khat));
 }
 
@@ -532,6 +619,7 @@ void run_row_fft(const Plan& p, const FrameDesc& b1, const FrameDesc& b2, char* 
   a.spec[1] = ws + p.off_spec[1];
   a.Pw = p.Pw;
   a.Pw2 = p.Pw2;
+  a.Pw2p = p.Pw2p;
   a.half = p.pw_half;
   a.pl = plw;
   a.nbr = rows_per_iter(plw.n, plw.ntw, sizeof(cpx<T>));
@@ -551,20 +639,22 @@ void run_col_deconv(const Plan& p, char* ws, cudaStream_t st) {
   a.spec[1] = ws + p.off_spec[1];
   a.khat = ws + p.off_khat;
   a.ihat = ws + p.off_ihat;
+  a.stw = ws + p.off_stw_h;
   a.H1 = p.H1;
   a.H2 = p.H2;
   a.H = p.H;
   a.C = p.C;
   a.Ph = p.Ph;
   a.Pw2 = p.Pw2;
+  a.Pw2p = p.Pw2p;
   a.single = p.single_kernel;
   a.eps = p.eps;
   a.pl = p.fp_h;
   constexpr int CW = sizeof(T) == 4 ? 4 : 2;
   dim3 g((p.Pw2 + CW - 1) / CW, p.n * p.C);
-  const size_t sm = sizeof(cpx<T>) * (((p.fp_h.ntw + 1) & ~1) + 3 * (size_t)CW * p.Ph);
+  const size_t sm = sizeof(cpx<T>) * 3 * (size_t)CW * p.Ph;
   cudaFuncSetAttribute(k_col_deconv<T, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_col_deconv<T, CW><<<g, kColThreads, sm, st>>>(a, (const cpx<T>*)(ws + p.off_stw_h));
+  k_col_deconv<T, CW><<<g, kColThreads, sm, st>>>(a);
 }
 
 template <typename T>
@@ -581,6 +671,7 @@ void run_row_ifft(const Plan& p, char* ws, void* latent, int out_f64, cudaStream
   a.W = p.W;
   a.Pw = p.Pw;
   a.Pw2 = p.Pw2;
+  a.Pw2p = p.Pw2p;
   a.half = p.pw_half;
   a.scale = 1.0 / ((double)p.Ph * (double)p.Pw);
   a.pl = plw;

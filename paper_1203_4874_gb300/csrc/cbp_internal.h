@@ -55,6 +55,7 @@ struct Plan {
   int H, W;                    // latent size
   int t1, t2, M, ns, nn;       // ns = M/2 + 1 solved samples per direction; nn = t1 + t2
   int Ph, Pw, Pw2;             // FFT grid; Pw2 = Pw/2 + 1 stored spectrum columns
+  int Pw2p;                    // row pitch of the spectra: Pw2 rounded up to even
   int mixed;                   // estimation path: 0 FP64, 1 mixed
   int fft_f64;                 // deconvolution arithmetic in double
   int single_kernel;           // deconvolve B1 by K1 only
@@ -73,9 +74,9 @@ struct Plan {
   size_t off_diag;                 // cbp_diag [n]
   size_t off_tw_h, off_tw_w;       // cpx<T_fft> twiddles exp(-2 pi i k / P), k < P
   size_t off_stw_h, off_stw_r;     // cpx<T_fft> stage twiddles of the column and row plans
-  size_t off_khat;                 // cpx<T_fft> [n][2][Ph][Pw2]
-  size_t off_spec[2];              // cpx<T_fft> [n][C][H_Bk][Pw2]
-  size_t off_ihat;                 // cpx<T_fft> [n][C][H][Pw2]
+  size_t off_khat;                 // cpx<T_fft> [n][2][Ph][Pw2p]
+  size_t off_spec[2];              // cpx<T_fft> [n][C][H_Bk][Pw2p]
+  size_t off_ihat;                 // cpx<T_fft> [n][C][H][Pw2p]
   size_t off_io_b[2], off_io_k[2], off_io_lat; // device staging for host I/O
   size_t total;
 };

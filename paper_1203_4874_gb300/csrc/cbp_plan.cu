@@ -112,6 +112,7 @@ cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_param
   if (p.Ph < hmax || p.Pw < wmax || !is_7_smooth(p.Ph) || !is_7_smooth(p.Pw))
     return CBP_ERR_INVALID_ARG;
   p.Pw2 = p.Pw / 2 + 1;
+  p.Pw2p = p.Pw2 + (p.Pw2 & 1);
   p.pw_half = (p.Pw % 2 == 0) ? 1 : 0;
   p.mixed = prm->path != CBP_PATH_FP64;
   const int frame_f64 = b1->dtype == CBP_F64;
@@ -127,7 +128,7 @@ cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_param
   const size_t nrow = p.pw_half ? p.Pw / 2 : p.Pw;
   // one row buffer pair + stage twiddles; exact magic division needs rows * N < 2^16
   if ((2 + 1) * ce * nrow > smem_max || nrow > 16384) return CBP_ERR_UNSUPPORTED;
-  if ((3 * cw + 1) * ce * p.Ph > smem_max || cw * p.Ph > 65536) return CBP_ERR_UNSUPPORTED;
+  if (3 * cw * ce * p.Ph > smem_max || cw * p.Ph > 65536) return CBP_ERR_UNSUPPORTED;
   if (sample_solve_smem(p.nn) > smem_max || scale_solve_smem(p.M) > smem_max)
     return CBP_ERR_UNSUPPORTED;
 
@@ -162,10 +163,10 @@ cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_param
   p.off_tw_w = take(p.Pw * ce);
   p.off_stw_h = take((size_t)p.fp_h.ntw * ce);
   p.off_stw_r = take((size_t)(p.pw_half ? p.fp_w2.ntw : p.fp_w.ntw) * ce);
-  p.off_khat = take(n * 2 * (size_t)p.Ph * p.Pw2 * ce);
-  p.off_spec[0] = take(n * C * (size_t)p.H1 * p.Pw2 * ce);
-  p.off_spec[1] = take(n * C * (size_t)p.H2 * p.Pw2 * ce);
-  p.off_ihat = take(n * C * (size_t)p.H * p.Pw2 * ce);
+  p.off_khat = take(n * 2 * (size_t)p.Ph * p.Pw2p * ce);
+  p.off_spec[0] = take(n * C * (size_t)p.H1 * p.Pw2p * ce);
+  p.off_spec[1] = take(n * C * (size_t)p.H2 * p.Pw2p * ce);
+  p.off_ihat = take(n * C * (size_t)p.H * p.Pw2p * ce);
   if (prm->flags & CBP_FLAG_HOST_IO) {
     const size_t es = frame_f64 ? 8 : 4;
     p.off_io_b[0] = take(n * C * (size_t)p.H1 * p.W1 * es);
