@@ -41,9 +41,16 @@ def _stale() -> bool:
     return any(d.stat().st_mtime > t for d in deps)
 
 
+def _extra_flags() -> list:
+    """Extra nvcc flags from CBP_NVCC_FLAGS (e.g. -DCBP_PHASE_TIMING for a
+    build that prints per-phase cycle counts of the solver kernels)."""
+    return os.environ.get("CBP_NVCC_FLAGS", "").split()
+
+
 def _compile(src: Path, verbose_ptxas: bool) -> Path:
     obj = BUILD / (src.stem + ".o")
-    cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, f"-I{INCLUDE}", f"-I{CSRC}", "-c", str(src), "-o", str(obj)]
+    cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, *_extra_flags(), f"-I{INCLUDE}", f"-I{CSRC}", "-c", str(src),
+           "-o", str(obj)]
     if verbose_ptxas:
         cmd[1:1] = ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)

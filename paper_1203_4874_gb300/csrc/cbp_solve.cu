@@ -27,12 +27,28 @@
 // normalise to unit kernel sum, inverse M x M DFT (Section 5).
 #include "cbp_common.cuh"
 #include "cbp_internal.h"
+#ifdef CBP_PHASE_TIMING
+#include <cstdio>
+#endif
 
 namespace cbp {
 namespace {
 
 constexpr int kSolveThreads = 256;
-constexpr int kMaxSweeps = 40;
+
+// Optional per-phase cycle counts (build with -DCBP_PHASE_TIMING): thread 0 of
+// a few blocks prints the clock64 deltas between the solver's phases.
+#ifdef CBP_PHASE_TIMING
+#define CBP_TICK(arr, i) \
+  do {                   \
+    if (threadIdx.x == 0) (arr)[i] = clock64(); \
+  } while (0)
+#else
+#define CBP_TICK(arr, i) \
+  do {                   \
+  } while (0)
+#endif
+constexpr int kMaxSweeps = 15;
 
 // ------------------------------------------------------------ block helpers
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -101,6 +117,8 @@ template <typename T> __device__ __forceinline__ cpx<T> cj_(cpx<T> x) { return c
 __device__ __forceinline__ float a2_(float x) { return x * x; }
 __device__ __forceinline__ double a2_(double x) { return x * x; }
 template <typename T> __device__ __forceinline__ T a2_(cpx<T> x) { return abs2(x); }
+__device__ __forceinline__ double warp_sum_e(double v) { return warp_sum(v); }
+__device__ __forceinline__ cd warp_sum_e(cd v) { return mk(warp_sum(v.re), warp_sum(v.im)); }
 template <typename E> struct Ops;
 template <> struct Ops<float> {
   static __device__ float z() { return 0.f; }
@@ -121,23 +139,63 @@ template <typename T> struct Ops<cpx<T>> {
   static __device__ bool nz(cpx<T> x) { return x.re != (T)0 || x.im != (T)0; }
 };
 
-// Cyclic Jacobi (round-robin parallel ordering) on the Hermitian matrix A
-// (n x n inside an ld x ld array, ld even >= n; element type E real or
-// complex, real type R).  V enters as the identity unless keep_v, and leaves
-// with the eigenvectors (columns); A leaves with the eigenvalues on its
-// diagonal.  A pair is rotated while |a_pq| exceeds both
-// tol_rel sqrt(|a_pp a_qq|) and tol_abs max|a_ii| (the rounding floor of the
-// precision).  Bounded sweeps.
+// Reciprocal and reciprocal square root in double precision from a float seed
+// refined by two Newton steps (y <- y (2 - x y), y <- y (3 - x y^2) / 2); valid
+// for x within the float range.  Cheap on a GPU whose double pipe is slow.
+__device__ __forceinline__ double rcp_d(double x) {
+  double y = (double)(1.0f / (float)x);
+  y = y * fma(-x, y, 2.0);
+  return y * fma(-x, y, 2.0);
+}
+__device__ __forceinline__ double rsqrt_d(double x) {
+  double y = (double)rsqrtf((float)x);
+  y = y * fma(-0.5 * x * y, y, 1.5);
+  return y * fma(-0.5 * x * y, y, 1.5);
+}
+__device__ __forceinline__ float rcp_d(float x) { return 1.0f / x; }
+__device__ __forceinline__ float rsqrt_d(float x) { return rsqrtf(x); }
+
+// Jacobi rotation for the 2x2 Hermitian block [[app, apq], [conj(apq), aqq]]:
+// returns false (identity) unless |apq| exceeds both thresholds; otherwise c
+// and sp = s * apq / |apq| with c^2 + s^2 = 1 to working precision.
 template <typename E, typename R>
-__device__ void jacobi(E* A, E* V, int n, int ld, EigSmem& S, R tol_rel, R tol_abs) {
-  const int half = ld / 2;
+__device__ __forceinline__ bool jacobi_rotation(E apq, R app, R aqq, R abs_tol, R tol_rel, R& c, E& sp) {
+  const R a2 = a2_(apq);
+  const R lim = max(abs_tol, tol_rel * sqrt(fabs(app)) * sqrt(fabs(aqq)));
+  if (!(a2 > lim * lim)) return false;
+  const R rmag = rsqrt_d(a2);                         // 1 / |apq|
+  const R tau = (aqq - app) * (R)0.5 * rmag;
+  R t;
+  if (fabs(tau) > (R)1e15) {
+    t = (R)0.5 * rcp_d(tau);                          // tan of a tiny angle
+  } else {
+    const R h = (R)1 + tau * tau;
+    const R root = h * rsqrt_d(h);                    // sqrt(1 + tau^2)
+    t = (tau >= (R)0 ? (R)1 : (R)-1) * rcp_d(fabs(tau) + root);
+  }
+  c = rsqrt_d((R)1 + t * t);
+  sp = (t * c * rmag) * apq;
+  return true;
+}
+
+// Cyclic Jacobi (round-robin parallel ordering) on the Hermitian matrix A
+// (n x n inside an npad x npad block, npad even >= n, stored with row stride
+// ld = npad + 1 so column walks are free of bank conflicts; element type E real or
+// complex, real type R).  V leaves with the eigenvectors (columns); A leaves
+// with the eigenvalues on its diagonal.  A pair is rotated while |a_pq|
+// exceeds both tol_rel sqrt(|a_pp a_qq|) and tol_abs max|a_ii|; tol_abs is set
+// a few times above the precision's rounding floor (~n u max|a_ii|), below
+// which rotations only stir rounding noise.  At most kMaxSweeps sweeps.
+template <typename E, typename R>
+__device__ void jacobi(E* A, E* V, int n, int npad, int ld, EigSmem& S, R tol_rel, R tol_abs) {
+  const int half = npad / 2;
   const int tid = threadIdx.x, nth = blockDim.x;
   R* rc = (R*)S.rc;
   E* rs = (E*)S.rs;
-  for (int i = tid; i < ld * ld; i += nth) {
-    const int r = i / ld, c = i % ld;
-    V[i] = r == c ? Ops<E>::o() : Ops<E>::z();
-    if (r >= n || c >= n) A[i] = Ops<E>::z();
+  for (int i = tid; i < npad * npad; i += nth) {
+    const int r = i / npad, c = i % npad;
+    V[r * ld + c] = r == c ? Ops<E>::o() : Ops<E>::z();
+    if (r >= n || c >= n) A[r * ld + c] = Ops<E>::z();
   }
   __syncthreads();
   R amax = 0;
@@ -146,24 +204,16 @@ __device__ void jacobi(E* A, E* V, int n, int ld, EigSmem& S, R tol_rel, R tol_a
   for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
     if (tid == 0) S.flag[0] = 0;
     __syncthreads();
-    for (int round = 0; round < ld - 1; ++round) {
+    for (int round = 0; round < npad - 1; ++round) {
       for (int k = tid; k < half; k += nth) {
         int p, q;
-        jacobi_pair(round, k, ld, &p, &q);
+        jacobi_pair(round, k, npad, &p, &q);
         R c = 1;
         E sp = Ops<E>::z();
-        if (q < n) {
-          const E apq = A[p * ld + q];
-          const R app = re_(A[p * ld + p]), aqq = re_(A[q * ld + q]);
-          const R mag = sqrt(a2_(apq));
-          if (mag > abs_tol && mag > tol_rel * sqrt(fabs(app)) * sqrt(fabs(aqq))) {
-            const R tau = (aqq - app) / ((R)2 * mag);
-            const R t = (tau >= (R)0 ? (R)1 : (R)-1) / (fabs(tau) + sqrt((R)1 + tau * tau));
-            c = (R)1 / sqrt((R)1 + t * t);
-            sp = ((t * c) / mag) * apq;           // s * phase(a_pq)
-            S.flag[0] = 1;
-          }
-        }
+        if (q < n &&
+            jacobi_rotation<E, R>(A[p * ld + q], re_(A[p * ld + p]), re_(A[q * ld + q]), abs_tol,
+                                  tol_rel, c, sp))
+          S.flag[0] = 1;
         S.rp[k] = p;
         S.rq[k] = q;
         rc[k] = c;
@@ -210,6 +260,7 @@ __device__ void jacobi(E* A, E* V, int n, int ld, EigSmem& S, R tol_rel, R tol_a
     }
     const int rotated = S.flag[0];
     __syncthreads();
+    if (tid == 0) S.flag[1] = sweep + 1;
     if (!rotated) break;
   }
 }
@@ -220,12 +271,15 @@ __device__ __forceinline__ cd v32(const EigSmem& S, bool real, int np, int i, in
   return cvt<double>(S.V[i * np + l]);
 }
 
-// y = G x (double), G n x n row-major.
+// y = G x (double), G n x n row-major; one warp per row.
 __device__ void matvec64(const cd* G, const cd* x, cd* y, int n) {
-  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int p = warp; p < n; p += nw) {
     cd acc = mk(0.0, 0.0);
-    for (int q = 0; q < n; ++q) cfma(acc, G[p * n + q], x[q]);
-    y[p] = acc;
+    for (int q = lane; q < n; q += 32) cfma(acc, G[p * n + q], x[q]);
+    acc.re = warp_sum(acc.re);
+    acc.im = warp_sum(acc.im);
+    if (lane == 0) y[p] = acc;
   }
   __syncthreads();
 }
@@ -249,87 +303,69 @@ __device__ double dotre64(const cd* a, const cd* b, int n, double* red) {
   return block_sum(s, red);
 }
 
-// a^H b (complex)
-__device__ cd dotc64(const cd* a, const cd* b, int n, double* red) {
-  cd acc = mk(0.0, 0.0);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) cfmac(acc, a[i], b[i]);
-  double re = block_sum(acc.re, red);
-  double im = block_sum(acc.im, red);
-  return mk(re, im);
-}
 
-// Newton correction with the single-precision eigenbasis:
-// x <- normalise(x - sum_{l != imin} v_l (v_l^H res) / (lam_l - theta)),
-// res = r - theta x, r = (accurate) S^H S x.
-__device__ double newton_eigbasis(EigSmem& S, bool real, int n, int imin, const cd* r, double theta) {
-  const int np = np_of(n);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) S.z[i] = r[i] - theta * S.x[i];  // res
+// Newton correction with a double-precision eigenbasis V (ld x ld, columns),
+// eigenvalues lam: x <- normalise(x - sum_{l != imin} v_l (v_l^H res) / (lam_l - theta)),
+// res = r - theta x.  Warp-parallel products.  Returns ||dx||^2.
+__device__ double newton_eigbasis64(EigSmem& S, const cd* V, const double* lam, int n, int ld,
+                                    int imin, const cd* r, double theta) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) S.z[i] = r[i] - theta * S.x[i];
   __syncthreads();
-  // coefficients c_l = v_l^H res / (lam_l - theta) -> S.y
-  for (int l = threadIdx.x; l < n; l += blockDim.x) {
+  for (int l = warp; l < n; l += nw) {
     cd c = mk(0.0, 0.0);
-    if (l != imin) {
-      for (int i = 0; i < n; ++i) cfmac(c, v32(S, real, np, i, l), S.z[i]);
-      double den = S.lam[l] - theta;
-      c = (1.0 / den) * c;
-    }
-    S.y[l] = c;
+    if (l != imin)
+      for (int i = lane; i < n; i += 32) cfmac(c, V[i * ld + l], S.z[i]);
+    c.re = warp_sum(c.re);
+    c.im = warp_sum(c.im);
+    if (lane == 0) S.y[l] = l != imin ? (1.0 / (lam[l] - theta)) * c : mk(0.0, 0.0);
   }
   __syncthreads();
   double d2 = 0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+  for (int i = warp; i < n; i += nw) {
     cd dx = mk(0.0, 0.0);
-    for (int l = 0; l < n; ++l) cfma(dx, v32(S, real, np, i, l), S.y[l]);
-    S.x[i] = S.x[i] - dx;
-    d2 += abs2(dx);
+    for (int l = lane; l < n; l += 32) cfma(dx, V[i * ld + l], S.y[l]);
+    dx.re = warp_sum(dx.re);
+    dx.im = warp_sum(dx.im);
+    if (lane == 0) {
+      S.x[i] = S.x[i] - dx;
+      d2 += abs2(dx);
+    }
   }
   d2 = block_sum(d2, S.red);
   normalize64(S.x, n, S.red);
   return d2;
 }
 
-// Newton correction with a double-precision eigenbasis V (ld x ld, columns),
-// eigenvalues lam: x <- normalise(x - sum_{l != imin} v_l (v_l^H res) / (lam_l - theta)).
-__device__ void newton_eigbasis64(EigSmem& S, const cd* V, const double* lam, int n, int ld,
-                                  int imin, const cd* r, double theta) {
-  for (int i = threadIdx.x; i < n; i += blockDim.x) S.z[i] = r[i] - theta * S.x[i];
-  __syncthreads();
-  for (int l = threadIdx.x; l < n; l += blockDim.x) {
-    cd c = mk(0.0, 0.0);
-    if (l != imin) {
-      for (int i = 0; i < n; ++i) cfmac(c, V[i * ld + l], S.z[i]);
-      c = (1.0 / (lam[l] - theta)) * c;
-    }
-    S.y[l] = c;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    cd dx = mk(0.0, 0.0);
-    for (int l = 0; l < n; ++l) cfma(dx, V[i * ld + l], S.y[l]);
-    S.x[i] = S.x[i] - dx;
-  }
-  __syncthreads();
-  normalize64(S.x, n, S.red);
-}
-
+__device__ __forceinline__ void fma_(double& acc, double a, double b) { acc = fma(a, b, acc); }
+__device__ __forceinline__ void fma_(cd& acc, cd a, cd b) { cfma(acc, a, b); }
+__device__ __forceinline__ void fmac_(double& acc, double a, double b) { acc = fma(a, b, acc); }
+__device__ __forceinline__ void fmac_(cd& acc, cd a, cd b) { cfmac(acc, a, b); }
+__device__ __forceinline__ double from_cd(cd v, double) { return v.re; }
+__device__ __forceinline__ cd from_cd(cd v, cd) { return v; }
+__device__ __forceinline__ cd to_cd(double v) { return mk(v, 0.0); }
+__device__ __forceinline__ cd to_cd(cd v) { return v; }
 
 // Orthonormalise the n columns of Q (n x n, leading dimension ld) in double
 // precision: modified Gram-Schmidt with the projections of all later columns
 // done in parallel, applied twice.
-__device__ void orthonormalize_cols(cd* Q, int n, int ld, double* red) {
+template <typename E>
+__device__ void orthonormalize_cols(E* Q, int n, int ld, double* red) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int pass = 0; pass < 2; ++pass)
     for (int k = 0; k < n; ++k) {
       double s2 = 0;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) s2 += abs2(Q[i * ld + k]);
+      for (int i = threadIdx.x; i < n; i += blockDim.x) s2 += a2_(Q[i * ld + k]);
       s2 = block_sum(s2, red);
       const double inv = s2 > 0 ? rsqrt(s2) : 0.0;
       for (int i = threadIdx.x; i < n; i += blockDim.x) Q[i * ld + k] = inv * Q[i * ld + k];
       __syncthreads();
-      // column j > k: q_j -= (q_k^H q_j) q_k; thread per (j, i) after a per-j dot
-      for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) {
-        cd d = mk(0.0, 0.0);
-        for (int i = 0; i < n; ++i) cfmac(d, Q[i * ld + k], Q[i * ld + j]);
-        for (int i = 0; i < n; ++i) Q[i * ld + j] = Q[i * ld + j] - d * Q[i * ld + k];
+      // q_j -= (q_k^H q_j) q_k for every j > k: one warp per column
+      for (int j = k + 1 + warp; j < n; j += nw) {
+        E d = Ops<E>::z();
+        for (int i = lane; i < n; i += 32) fmac_(d, Q[i * ld + k], Q[i * ld + j]);
+        d = warp_sum_e(d);
+        for (int i = lane; i < n; i += 32) Q[i * ld + j] = Q[i * ld + j] - d * Q[i * ld + k];
       }
       __syncthreads();
     }
@@ -339,10 +375,82 @@ __device__ void orthonormalize_cols(cd* Q, int n, int ld, double* red) {
 // symmetric when `real`).  acc_steps further Newton steps use
 // apply(x, out) = S^H S x computed from the original system (exact residual).
 // Result vector in S.x (unit norm).
+// Double-precision eigen-decomposition of S.G (element type E: double for real
+// samples, cd otherwise) started from the single-precision eigenvectors.  On
+// exit: eigenvalues in S.lam, the double eigenvectors (as cd, stride ld) in the
+// single-precision area, S.sc[1] = second smallest eigenvalue; returns the
+// index of the smallest.
+template <typename E>
+__device__ int hard_eig(EigSmem& S, int n, int np, int ld, double gscale, long long* tk) {
+  const bool real = sizeof(E) == sizeof(double);
+  E* Q = (E*)S.Q;
+  E* T1 = (E*)S.L;
+  for (int i = threadIdx.x; i < n * n; i += blockDim.x)
+    Q[(i / n) * ld + (i % n)] = from_cd(v32(S, real, ld, i / n, i % n), E());
+  __syncthreads();
+  orthonormalize_cols<E>(Q, n, ld, S.red);
+  if (tk) CBP_TICK(tk, 6);
+  // T1 = (G / gscale) Q
+  const double ig = 1.0 / gscale;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, l = idx % n;
+    E acc = Ops<E>::z();
+    for (int j = 0; j < n; ++j) fma_(acc, from_cd(ig * S.G[i * n + j], E()), Q[j * ld + l]);
+    T1[i * ld + l] = acc;
+  }
+  __syncthreads();
+  // A0 = Q^H T1 (Hermitian by construction up to rounding: symmetrised)
+  E* A0 = (E*)S.A;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, l = idx % n;
+    E acc = Ops<E>::z();
+    for (int j = 0; j < n; ++j) fmac_(acc, Q[j * ld + i], T1[j * ld + l]);
+    A0[i * ld + l] = acc;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, l = idx % n;
+    if (l > i) {
+      const E m = 0.5 * (A0[i * ld + l] + cj_(A0[l * ld + i]));
+      A0[i * ld + l] = m;
+      A0[l * ld + i] = cj_(m);
+    } else if (l == i) {
+      Ops<E>::clear_im(A0[i * ld + i]);
+    }
+  }
+  __syncthreads();
+  if (tk) CBP_TICK(tk, 7);
+  jacobi<E, double>(A0, T1, n, np, ld, S, 1e-15, 4e-16 * (double)n);
+  if (tk) CBP_TICK(tk, 8);
+  for (int i = threadIdx.x; i < n; i += blockDim.x) S.lam[i] = gscale * re_(A0[i * ld + i]);
+  __syncthreads();
+  // V64 = Q W (as cd) over the A0 area, whose eigenvalues are already in S.lam
+  cd* V64 = (cd*)S.A;
+  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+    const int i = idx / n, l = idx % n;
+    E acc = Ops<E>::z();
+    for (int j = 0; j < n; ++j) fma_(acc, Q[i * ld + j], T1[j * ld + l]);
+    V64[i * ld + l] = to_cd(acc);
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int a = 0;
+    for (int i = 0; i < n; ++i)
+      if (S.lam[i] < S.lam[a]) a = i;
+    int b = -1;
+    for (int i = 0; i < n; ++i)
+      if (i != a && (b < 0 || S.lam[i] < S.lam[b])) b = i;
+    S.flag[2] = a;
+    S.sc[1] = b >= 0 ? S.lam[b] : S.lam[a];
+  }
+  __syncthreads();
+  return S.flag[2];
+}
+
 template <class Apply>
 __device__ EigResult smallest_eigvec(EigSmem& S, int n, bool real, int acc_steps,
-                                     const Apply& apply) {
-  const int np = np_of(n);
+                                     const Apply& apply, long long* tk = nullptr) {
+  const int np = np_of(n), ld = np + 1;
   if (threadIdx.x == 0) {
     double gs = 0;
     for (int i = 0; i < n; ++i) gs = fmax(gs, S.G[i * n + i].re);
@@ -354,18 +462,19 @@ __device__ EigResult smallest_eigvec(EigSmem& S, int n, bool real, int acc_steps
   if (real) {
     float* A = (float*)S.A;
     for (int i = threadIdx.x; i < n * n; i += blockDim.x)
-      A[(i / n) * np + (i % n)] = (float)(S.G[i].re / gscale);
+      A[(i / n) * ld + (i % n)] = (float)(S.G[i].re / gscale);
     __syncthreads();
-    jacobi<float, float>(A, (float*)S.V, n, np, S, 1e-7f, 4e-7f * (float)n);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) S.lam[i] = gscale * (double)A[i * np + i];
+    jacobi<float, float>(A, (float*)S.V, n, np, ld, S, 1e-7f, 2e-6f * (float)n);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) S.lam[i] = gscale * (double)A[i * ld + i];
   } else {
     for (int i = threadIdx.x; i < n * n; i += blockDim.x)
-      S.A[(i / n) * np + (i % n)] = cvt<float>((1.0 / gscale) * S.G[i]);
+      S.A[(i / n) * ld + (i % n)] = cvt<float>((1.0 / gscale) * S.G[i]);
     __syncthreads();
-    jacobi<cf, float>(S.A, S.V, n, np, S, 1e-7f, 4e-7f * (float)n);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) S.lam[i] = gscale * (double)S.A[i * np + i].re;
+    jacobi<cf, float>(S.A, S.V, n, np, ld, S, 1e-7f, 2e-6f * (float)n);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) S.lam[i] = gscale * (double)S.A[i * ld + i].re;
   }
   __syncthreads();
+  if (tk) CBP_TICK(tk, 3);
   if (threadIdx.x == 0) {
     int i1 = 0;
     double lmax = -1e300;
@@ -393,113 +502,42 @@ __device__ EigResult smallest_eigvec(EigSmem& S, int n, bool real, int acc_steps
   if (!hard) {
     // 2a. Newton steps in double precision on G, preconditioned by the
     // single-precision eigenbasis
-    for (int i = threadIdx.x; i < n; i += blockDim.x) S.x[i] = v32(S, real, np, i, imin);
+    cd* V64 = S.L;   // the single-precision eigenbasis in double, stride ld
+    for (int i = threadIdx.x; i < n * n; i += blockDim.x)
+      V64[(i / n) * ld + (i % n)] = v32(S, real, ld, i / n, i % n);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) S.x[i] = v32(S, real, ld, i, imin);
     __syncthreads();
     normalize64(S.x, n, S.red);
     for (int it = 0; it < 12; ++it) {
       matvec64(S.G, S.x, S.r, n);
       theta = dotre64(S.x, S.r, n, S.red);
-      if (newton_eigbasis(S, real, n, imin, S.r, theta) < 1e-30) break;
+      if (newton_eigbasis64(S, V64, S.lam, n, ld, imin, S.r, theta) < 1e-30) break;
     }
     for (int it = 0; it < acc_steps; ++it) {
       apply(S.x, S.r);
       theta = dotre64(S.x, S.r, n, S.red);
-      newton_eigbasis(S, real, n, imin, S.r, theta);
+      newton_eigbasis64(S, V64, S.lam, n, ld, imin, S.r, theta);
     }
   } else {
     // 2b. Unresolved in single precision (the smallest eigenvalues sit below
     // its rounding floor, e.g. the z = 1 sample): Jacobi in double precision,
     // started from the single-precision eigenbasis made orthonormal in double
-    // precision, so only the unresolved cluster still needs rotations.
-    cd* Q = S.Q;
-    cd* T1 = S.L;
-    for (int i = threadIdx.x; i < n * n; i += blockDim.x)
-      Q[(i / n) * np + (i % n)] = v32(S, real, np, i / n, i % n);
-    __syncthreads();
-    orthonormalize_cols(Q, n, np, S.red);
-    // T1 = G Q
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-      const int i = idx / n, l = idx % n;
-      cd acc = mk(0.0, 0.0);
-      for (int j = 0; j < n; ++j) cfma(acc, S.G[i * n + j], Q[j * np + l]);
-      T1[i * np + l] = acc;
-    }
-    __syncthreads();
-    // A0 = Q^H T1 into the (now free) single-precision area; W into T1's area
-    // after A0 is formed
-    cd* A0 = (cd*)S.A;
-    for (int idx = threadIdx.x; idx < np * np; idx += blockDim.x) {
-      const int i = idx / np, l = idx % np;
-      cd acc = mk(0.0, 0.0);
-      if (i < n && l < n)
-        for (int j = 0; j < n; ++j) cfmac(acc, Q[j * np + i], T1[j * np + l]);
-      if (real) ((double*)A0)[idx] = acc.re;
-      else A0[idx] = acc;
-    }
-    __syncthreads();
-    if (real) {   // exact symmetry, then real Jacobi
-      double* A = (double*)A0;
-      for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-        const int i = idx / n, l = idx % n;
-        if (l > i) {
-          const double m = 0.5 * (A[i * np + l] + A[l * np + i]);
-          A[i * np + l] = m;
-          A[l * np + i] = m;
-        }
-      }
-      __syncthreads();
-      jacobi<double, double>(A, (double*)T1, n, np, S, 1e-15, 1e-17 * (double)n);
-      for (int i = threadIdx.x; i < n; i += blockDim.x) S.lam[i] = A[i * np + i];
-    } else {
-      for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-        const int i = idx / n, l = idx % n;
-        if (l > i) {
-          const cd m = 0.5 * (A0[i * np + l] + conj(A0[l * np + i]));
-          A0[i * np + l] = m;
-          A0[l * np + i] = conj(m);
-        } else if (l == i) {
-          A0[i * np + i].im = 0.0;
-        }
-      }
-      __syncthreads();
-      jacobi<cd, double>(A0, T1, n, np, S, 1e-15, 1e-17 * (double)n);
-      for (int i = threadIdx.x; i < n; i += blockDim.x) S.lam[i] = A0[i * np + i].re;
-    }
-    __syncthreads();
-    // V64 = Q W, into the A0 area (its diagonal is saved in lam; W stays in T1)
-    cd* V64 = A0;
-    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-      const int i = idx / n, l = idx % n;
-      cd acc = mk(0.0, 0.0);
-      if (real)
-        for (int j = 0; j < n; ++j) acc = acc + ((const double*)T1)[j * np + l] * Q[i * np + j];
-      else
-        for (int j = 0; j < n; ++j) cfma(acc, Q[i * np + j], T1[j * np + l]);
-      V64[i * np + l] = acc;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      int i1 = 0;
-      for (int i = 0; i < n; ++i)
-        if (S.lam[i] < S.lam[i1]) i1 = i;
-      int i2 = -1;
-      for (int i = 0; i < n; ++i)
-        if (i != i1 && (i2 < 0 || S.lam[i] < S.lam[i2])) i2 = i;
-      S.flag[2] = i1;
-      S.sc[1] = i2 >= 0 ? S.lam[i2] : S.lam[i1];
-    }
-    __syncthreads();
-    const int i1 = S.flag[2];
+    // precision, so mostly the unresolved cluster still needs rotations.
+    int i1;
+    if (real) i1 = hard_eig<double>(S, n, np, ld, gscale, tk);
+    else i1 = hard_eig<cd>(S, n, np, ld, gscale, tk);
     lam2 = S.sc[1];
-    for (int i = threadIdx.x; i < n; i += blockDim.x) S.x[i] = V64[i * np + i1];
+    cd* V64 = (cd*)S.A;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) S.x[i] = V64[i * ld + i1];
     __syncthreads();
     normalize64(S.x, n, S.red);
     if (acc_steps > 0) {
       apply(S.x, S.r);
       theta = dotre64(S.x, S.r, n, S.red);
-      newton_eigbasis64(S, V64, S.lam, n, np, i1, S.r, theta);
+      newton_eigbasis64(S, V64, S.lam, n, ld, i1, S.r, theta);
     }
   }
+  if (tk) CBP_TICK(tk, 4);
   matvec64(S.G, S.x, S.r, n);
   theta = dotre64(S.x, S.r, n, S.red);
   EigResult res;
@@ -519,10 +557,10 @@ __device__ char* carve_eig(EigSmem& S, char* p, int n) {
     return q;
   };
   S.G = (cd*)take(sizeof(cd) * n * n);
-  S.L = (cd*)take(sizeof(cd) * np * np);
-  S.Q = (cd*)take(sizeof(cd) * np * np);
-  S.A = (cf*)take(sizeof(cf) * np * np);
-  S.V = (cf*)take(sizeof(cf) * np * np);
+  S.L = (cd*)take(sizeof(cd) * np * (np + 1));
+  S.Q = (cd*)take(sizeof(cd) * np * (np + 1));
+  S.A = (cf*)take(sizeof(cf) * np * (np + 1));
+  S.V = (cf*)take(sizeof(cf) * np * (np + 1));
   S.x = (cd*)take(sizeof(cd) * n);
   S.y = (cd*)take(sizeof(cd) * n);
   S.r = (cd*)take(sizeof(cd) * n);
@@ -541,7 +579,7 @@ __device__ char* carve_eig(EigSmem& S, char* p, int n) {
 size_t eig_smem_bytes(int n) {
   const int np = (n + 1) & ~1;
   auto r = [](size_t b) { return (b + 15) & ~size_t(15); };
-  return r(sizeof(cd) * n * n) + r(sizeof(cd) * np * np) * 2 + r(sizeof(cf) * np * np) * 2 + r(sizeof(cd) * n) * 4 + r(sizeof(double) * n) +
+  return r(sizeof(cd) * n * n) + r(sizeof(cd) * np * (np + 1)) * 2 + r(sizeof(cf) * np * (np + 1)) * 2 + r(sizeof(cd) * n) * 4 + r(sizeof(double) * n) +
          r(sizeof(double) * np / 2) + r(sizeof(cd) * np / 2) + r(sizeof(int) * np / 2) * 2 +
          r(sizeof(double) * 32) + r(sizeof(int) * 4) + r(sizeof(double) * 8);
 }
@@ -681,19 +719,34 @@ __device__ void correlations_ff(const cdf* const base[2], const int len[2], int 
     const int la = len[ka], lb = len[kb];
     const int m0 = d < 0 ? -d : 0;
     const int m1 = min(la, lb - d);
-    FF re, im;
+    FF re0, im0, re1, im1;    // two independent chains per lane for ILP
     for (int ch = 0; ch < C; ++ch) {
       const cdf* a = base[ka] + ((int64_t)(f * C + ch) * ns + s) * la;
       const cdf* b = base[kb] + ((int64_t)(f * C + ch) * ns + s) * lb;
-      for (int m = m0 + lane; m < m1; m += 32) {
-        const cdf x = a[m], y = b[m + d];
+      int m = m0 + lane;
+      for (; m + 32 < m1; m += 64) {
+        const cdf x = a[m], y = b[m + d], u = a[m + 32], v = b[m + 32 + d];
         // conj(x) y = (xr yr + xi yi) + i (xr yi - xi yr)
-        re.mac(x.rh, x.rl, y.rh, y.rl);
-        re.mac(x.ih, x.il, y.ih, y.il);
-        im.mac(x.rh, x.rl, y.ih, y.il);
-        im.mac(-x.ih, -x.il, y.rh, y.rl);
+        re0.mac(x.rh, x.rl, y.rh, y.rl);
+        re1.mac(u.rh, u.rl, v.rh, v.rl);
+        im0.mac(x.rh, x.rl, y.ih, y.il);
+        im1.mac(u.rh, u.rl, v.ih, v.il);
+        re0.mac(x.ih, x.il, y.ih, y.il);
+        re1.mac(u.ih, u.il, v.ih, v.il);
+        im0.mac(-x.ih, -x.il, y.rh, y.rl);
+        im1.mac(-u.ih, -u.il, v.rh, v.rl);
+      }
+      if (m < m1) {
+        const cdf x = a[m], y = b[m + d];
+        re0.mac(x.rh, x.rl, y.rh, y.rl);
+        re0.mac(x.ih, x.il, y.ih, y.il);
+        im0.mac(x.rh, x.rl, y.ih, y.il);
+        im0.mac(-x.ih, -x.il, y.rh, y.rl);
       }
     }
+    FF re = re0, im = im0;
+    re.add(re1.hi, re1.lo);
+    im.add(im1.hi, im1.lo);
     re = warp_sum_ff(re);
     im = warp_sum_ff(im);
     if (lane == 0) rho[j] = mk(re.value(), im.value());
@@ -776,6 +829,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_sample_solve(SampleArgs a) {
   EigSmem S;
   char* p = carve_eig(S, smem, n);
   cd* rho = (cd*)p;
+  long long tk[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
+  CBP_TICK(tk, 0);
   // Real samples (z = 1; z = -1 when M is even) have real Gram matrices.
   const bool real = s == 0 || 2 * s == a.M;
   const SamplePolys<double, double> P64 =
@@ -783,7 +838,9 @@ __global__ void __launch_bounds__(kSolveThreads) k_sample_solve(SampleArgs a) {
   if (real) correlations_real(P64, a.C, a.t1, a.t2, rho);
   else if (a.mixed) correlations_ff(a.pzf[ps], a.len[ps], f, a.C, a.ns, s, a.t1, a.t2, rho);
   else correlations(P64, a.C, a.t1, a.t2, rho);
+  CBP_TICK(tk, 1);
   gram_from_rho(rho, a.t1, a.t2, S.G);
+  CBP_TICK(tk, 2);
   // FP64 path: two Newton steps against the exact residual S^H S x from the
   // double samples (removes the squared conditioning of the normal matrix).
   // Mixed path: the float-float / double normal matrix is accurate to ~1e-13,
@@ -796,7 +853,16 @@ __global__ void __launch_bounds__(kSolveThreads) k_sample_solve(SampleArgs a) {
   ap.L = a.len[ps][0] + a.t2 - 1;
   ap.y = a.resid + (((int64_t)f * 2 + ps) * a.ns + s) * a.C * (int64_t)a.Lmax;
   ap.red = S.red;
-  const EigResult res = smallest_eigvec(S, n, real, a.mixed ? 0 : 2, ap);
+  const EigResult res = smallest_eigvec(S, n, real, a.mixed ? 0 : 2, ap, tk);
+  CBP_TICK(tk, 5);
+#ifdef CBP_PHASE_TIMING
+  if (threadIdx.x == 0 && f < 2)
+    printf("sample f=%d pass=%d s=%d real=%d hard=%d | corr %lld gram %lld jacobi32 %lld refine %lld "
+           "tail %lld | mgs %lld xform %lld jacobi64 %lld (%d sweeps)\n",
+           f, ps, s, (int)real, res.hard, tk[1] - tk[0], tk[2] - tk[1], tk[3] - tk[2],
+           tk[4] - tk[3], tk[5] - tk[4], res.hard ? tk[6] - tk[3] : 0LL,
+           res.hard ? tk[7] - tk[6] : 0LL, res.hard ? tk[8] - tk[7] : 0LL, S.flag[1]);
+#endif
   const int64_t o = ((int64_t)f * 2 + ps) * a.ns + s;
   for (int i = threadIdx.x; i < n; i += blockDim.x) a.X[o * n + i] = S.x[i];
   if (threadIdx.x == 0) {
@@ -823,10 +889,10 @@ struct ScaleArgs {
   int M, ns, t1, t2, nn, mixed, Ph, Pw;
 };
 
-__device__ __forceinline__ cd root(int k, int M, double sign) {
-  double s, c;
-  sincospi(sign * 2.0 * (double)(k % M) / (double)M, &s, &c);
-  return mk(c, s);
+// w^k (sign -1) or w^-k (sign +1), w = exp(-2 pi i / M), from a table of w^j, j < M.
+__device__ __forceinline__ cd root(const cd* wt, int k, int M, double sign) {
+  const cd w = wt[k % M];
+  return sign < 0 ? w : conj(w);
 }
 
 // Cofactor of kernel kk (0, 1) at sample s of pass ps, conjugate-expanded.
@@ -876,6 +942,13 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
   char* p = carve_eig(S, smem, n);
   cd* X = (cd*)p;                 // [2][M][M] kernel spectra, then full inverse DFTs
   cd* T = X + 2 * MM;             // [M][M] temporary
+  __shared__ cd wt[kMaxM];
+  for (int k = threadIdx.x; k < M; k += blockDim.x) {
+    double sn, cs;
+    sincospi(-2.0 * (double)k / (double)M, &sn, &cs);
+    wt[k] = mk(cs, sn);
+  }
+  __syncthreads();
   cd* ab = a.ab + (int64_t)f * 4 * MM;
   // lift: A_k[i][j] = sum_p u^{Z2}_{k,j}[p] w^{ip};  B_k[i][j] = sum_q u^{Z1}_{k,i}[q] w^{jq}
   for (int idx = threadIdx.x; idx < 4 * MM; idx += blockDim.x) {
@@ -884,8 +957,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
     const int t = kk ? t2 : t1, lo = kk ? t1 : 0;
     cd acc = mk(0.0, 0.0);
     for (int q = 0; q < t; ++q) {
-      if (!isB) cfma(acc, cofactor(a, f, 0, j, lo + q), root(i * q, M, -1.0));
-      else cfma(acc, cofactor(a, f, 1, i, lo + q), root(j * q, M, -1.0));
+      if (!isB) cfma(acc, cofactor(a, f, 0, j, lo + q), root(wt, i * q, M, -1.0));
+      else cfma(acc, cofactor(a, f, 1, i, lo + q), root(wt, j * q, M, -1.0));
     }
     ab[idx] = acc;
   }
@@ -941,7 +1014,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
     for (int idx = threadIdx.x; idx < MM; idx += blockDim.x) {
       const int i = idx / M, q = idx % M;
       cd acc = mk(0.0, 0.0);
-      for (int j = 0; j < M; ++j) cfma(acc, Xk[i * M + j] * inv00, root(j * q, M, 1.0));
+      for (int j = 0; j < M; ++j) cfma(acc, Xk[i * M + j] * inv00, root(wt, j * q, M, 1.0));
       T[idx] = acc;
     }
     __syncthreads();
@@ -953,7 +1026,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
     for (int idx = threadIdx.x; idx < MM; idx += blockDim.x) {
       const int pp = idx / M, q = idx % M;
       cd acc = mk(0.0, 0.0);
-      for (int i = 0; i < M; ++i) cfma(acc, root(i * pp, M, 1.0), T[i * M + q]);
+      for (int i = 0; i < M; ++i) cfma(acc, root(wt, i * pp, M, 1.0), T[i * M + q]);
       acc = (1.0 / (double)MM) * acc;
       l_re += acc.re * acc.re;
       l_im += acc.im * acc.im;
