@@ -37,6 +37,8 @@ H, W, C, T1, T2, SIGMA, EPS = 1080, 1920, 3, 15, 17, 1e-3, 1e-4
 H1, W1, H2, W2 = H + T1 - 1, W + T1 - 1, H + T2 - 1, W + T2 - 1
 PH, PW = 1120, 1944          # smallest 7-smooth sizes >= 1096, 1936
 PW2 = PW // 2 + 1
+M = max(T1, T2)              # unit-circle samples (the default)
+NS = M // 2 + 1              # samples solved per direction
 
 
 def config(pairs):
@@ -55,15 +57,16 @@ def algorithmic_bytes(stage: str, n: int) -> float | None:
     khat = n * 2 * PH * PW2 * 8
     ihat = n * C * H * PW2 * 8
     lat = n * C * H * W * 4
+    bins = n * C * M * (H1 + H2 + W1 + W2) * 8
+    samples = n * C * NS * (H1 + H2 + W1 + W2) * 16 * 2   # double + float-float copies
     return {
-        "eval": fr,                                # two kernels, each reads one direction
-        "row_fft": fr + spec,
+        "eval": bins + samples,                    # fold bins -> samples
+        "row_fft": fr + spec + bins,               # one read of the frames: folds + row FFTs
         "col_deconv": spec + khat + ihat,
         "row_ifft": ihat + lat,
     }.get(stage)
 
 
-STAGE_LAUNCHES = {"eval": 2}
 STAGE_FILES = {"eval": "cbp_eval.cu", "sample_solve": "cbp_solve.cu", "scale_solve": "cbp_solve.cu",
                "kernel_spectra": "cbp_fft.cu", "row_fft": "cbp_fft.cu", "col_deconv": "cbp_fft.cu",
                "row_ifft": "cbp_fft.cu"}

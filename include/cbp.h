@@ -249,11 +249,13 @@ cbp_status cbp_synth_latent(cbp_ctx* ctx, const double* blobs, int32_t nblobs, i
  * count into launches[stage] (arrays of CBP_NUM_STAGES entries, either may be
  * NULL), and clears the record.  Stages of the serving engine are not timed. */
 typedef enum cbp_stage {
-  CBP_STAGE_EVAL = 0,           /* A1: sample polynomials (2 kernels)           */
+  CBP_STAGE_EVAL = 0,           /* A1: fold bins -> samples (deblur: 1 kernel;
+                                   estimate only: fold row pass + bins, 2)       */
   CBP_STAGE_SAMPLE_SOLVE = 1,   /* A2-A3: per-sample Gram + null vector          */
   CBP_STAGE_SCALE_SOLVE = 2,    /* A4-A5: lift, scale fix, inverse DFT           */
   CBP_STAGE_KERNEL_SPECTRA = 3, /* kernels' spectra on the FFT grid (+ twiddles) */
-  CBP_STAGE_ROW_FFT = 4,        /* forward real row FFTs of B1, B2               */
+  CBP_STAGE_ROW_FFT = 4,        /* one read of B1, B2: A1 folds + forward real
+                                   row FFTs                                      */
   CBP_STAGE_COL_DECONV = 5,     /* column FFTs + dual-kernel formula + inverse    */
   CBP_STAGE_ROW_IFFT = 6,       /* inverse row FFTs, crop, scale                  */
   CBP_STAGE_H2D = 7,            /* host-to-device copies (CBP_FLAG_HOST_IO)       */

@@ -127,10 +127,21 @@ cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
     begin(CBP_STAGE_SCALE_SOLVE);
     launch_kernels_in(p, wsp, k1d, k2d, kf64, st);
     end(CBP_STAGE_SCALE_SOLVE, 1);
-  } else {
+  }
+  if (deblur) {
+    begin(CBP_STAGE_KERNEL_SPECTRA);   // FFT twiddle tables
+    init_twiddles(p, wsp, st);
+    end(CBP_STAGE_KERNEL_SPECTRA, 4);
+    // one read of the frames: A1 folds and the A6 forward row FFTs together
+    begin(CBP_STAGE_ROW_FFT);
+    launch_row_pass(p, d1, d2, wsp, st, !kin, true);
+    end(CBP_STAGE_ROW_FFT, 1);
+  }
+  if (!kin) {
     begin(CBP_STAGE_EVAL);
-    launch_eval(p, d1, d2, wsp, st);
-    end(CBP_STAGE_EVAL, 2);
+    if (deblur) launch_fold_dft(p, wsp, st);
+    else launch_eval(p, d1, d2, wsp, st);
+    end(CBP_STAGE_EVAL, deblur ? 1 : 2);
     begin(CBP_STAGE_SAMPLE_SOLVE);
     launch_sample_solve(p, wsp, st);
     end(CBP_STAGE_SAMPLE_SOLVE, 1);
@@ -141,12 +152,8 @@ cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
   }
   if (deblur) {
     begin(CBP_STAGE_KERNEL_SPECTRA);
-    init_twiddles(p, wsp, st);
     launch_kernel_spectra(p, wsp, st);
-    end(CBP_STAGE_KERNEL_SPECTRA, 3);
-    begin(CBP_STAGE_ROW_FFT);
-    launch_row_fft(p, d1, d2, wsp, st);
-    end(CBP_STAGE_ROW_FFT, 1);
+    end(CBP_STAGE_KERNEL_SPECTRA, 1);
     begin(CBP_STAGE_COL_DECONV);
     launch_col_deconv(p, wsp, st);
     end(CBP_STAGE_COL_DECONV, 1);

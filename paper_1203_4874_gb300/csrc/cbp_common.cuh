@@ -45,6 +45,24 @@ __host__ __device__ __forceinline__ cdf to_cdf(cd a) {
   return {rh, (float)(a.re - (double)rh), ih, (float)(a.im - (double)ih)};
 }
 
+// Running sum of float terms kept exactly as hi + lo (Knuth's TwoSum), so a
+// fold of float32 frames is accurate to ~1e-14 using float arithmetic only.
+struct TwoSum {
+  float hi = 0.f, lo = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = hi + x;
+    const float z = t - hi;
+    lo += (hi - (t - z)) + (x - z);
+    hi = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+};
+struct DoubleSum {
+  double v = 0.0;
+  __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ double value() const { return v; }
+};
+
 template <typename T> __device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);

@@ -171,10 +171,10 @@ __device__ __forceinline__ void stockham_stage(const cpx<T>* __restrict__ in,
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = src[r * Nr];
     if (Ns > 1) {
-      const cpx<T>* w = tw + k * (R - 1);
+      const cpx<T>* w = tw + k;       // r-major: consecutive k are consecutive words
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        cpx<T> ww = w[r - 1];
+        cpx<T> ww = w[(r - 1) * Ns];
         if (Inv) ww.im = -ww.im;
         v[r] = v[r] * ww;
       }
@@ -210,14 +210,15 @@ __device__ cpx<T>* fft_block(cpx<T>* a, cpx<T>* b, const FftPlan& pl, int nb, co
   return a;
 }
 
-// Stage twiddles of a plan: entry st.tw + k (R-1) + r - 1 = exp(-2 pi i k r / (Ns R)).
+// Stage twiddles of a plan: entry st.tw + (r-1) Ns + k = exp(-2 pi i k r / (Ns R)),
+// r-major so that the threads of a stage (consecutive k) read consecutive entries.
 template <typename T>
 __global__ void k_stage_twiddles(FftPlan pl, cpx<T>* out) {
   for (int s = 0; s < pl.nst; ++s) {
     const FftStage& st = pl.st[s];
     const int cnt = st.Ns * (st.R - 1);
     for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < cnt; e += gridDim.x * blockDim.x) {
-      const int k = e / (st.R - 1), r = e % (st.R - 1) + 1;
+      const int r = e / st.Ns + 1, k = e % st.Ns;
       double sn, cs;
       sincospi(-2.0 * (double)(k * r) / (double)(st.Ns * st.R), &sn, &cs);
       out[st.tw + e] = mk<T>((T)cs, (T)sn);
@@ -280,97 +281,16 @@ k_kernel_spectra(const double* kd, int t1, int t2, int Ph, int Pw, int Pw2, int 
   }
 }
 
-struct RowArgs {
-  FrameDesc fr[2];
-  void* spec[2];     // cpx<T> [n][C][H_Bk][Pw2]
-  int Pw, Pw2, Pw2p, half, nbr;
-  FftPlan pl;        // plan of Pw/2 (half) or Pw
-};
-
-// Forward real-to-complex FFT of every row of B1 and B2, nbr rows at a time.
-// Shared memory: stage twiddles, then two buffers of nbr rows.
-template <typename T>
-__global__ void __launch_bounds__(kFftThreads)
-k_row_fft(RowArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
-  extern __shared__ __align__(16) char smem[];
-  const int N = a.pl.n, NB = a.nbr;
-  cpx<T>* tw = (cpx<T>*)smem;
-  cpx<T>* b0 = tw + ((a.pl.ntw + 1) & ~1);
-  cpx<T>* b1 = b0 + NB * N;
-  load_twiddles(tw, stw, a.pl.ntw);
-  const FrameDesc& fr = a.fr[blockIdx.z];
-  const int fc = blockIdx.y, f = fc / fr.c, ch = fc % fr.c;
-  const int rows_per = (fr.h + gridDim.x - 1) / gridDim.x;
-  const int r0 = blockIdx.x * rows_per, r1 = min(fr.h, r0 + rows_per);
-  cpx<T>* spec = (cpx<T>*)a.spec[blockIdx.z] + (int64_t)fc * fr.h * a.Pw2p;
-  const void* fb = frame_base(fr, f);
-  for (int rg = r0; rg < r1; rg += NB) {
-    const int nr = min(NB, r1 - rg);
-    for (int rl = 0; rl < nr; ++rl) {
-      const int64_t base = (int64_t)ch * fr.cs + (int64_t)(rg + rl) * fr.rs;
-      cpx<T>* dst = b0 + rl * N;
-      if (a.half && !fr.f64 && ((((uintptr_t)((const float*)fb + base)) & 7) == 0)) {
-        const float2* rp = (const float2*)((const float*)fb + base);
-        const int full = fr.w >> 1;               // complete (x[2m], x[2m+1]) pairs
-        for (int m = threadIdx.x; m < N; m += blockDim.x) {
-          T x0 = 0, x1 = 0;
-          if (m < full) {
-            const float2 v = __ldg(rp + m);
-            x0 = v.x;
-            x1 = v.y;
-          } else if (2 * m < fr.w) {
-            x0 = __ldg((const float*)fb + base + 2 * m);
-          }
-          dst[m] = mk<T>(x0, x1);
-        }
-      } else if (a.half) {
-        for (int m = threadIdx.x; m < N; m += blockDim.x) {
-          const int c0 = 2 * m, c1 = 2 * m + 1;
-          const T x0 = c0 < fr.w ? ld_frame<T>(fb, base + c0, fr.f64) : (T)0;
-          const T x1 = c1 < fr.w ? ld_frame<T>(fb, base + c1, fr.f64) : (T)0;
-          dst[m] = mk<T>(x0, x1);
-        }
-      } else {
-        for (int m = threadIdx.x; m < N; m += blockDim.x)
-          dst[m] = mk<T>(m < fr.w ? ld_frame<T>(fb, base + m, fr.f64) : (T)0, (T)0);
-      }
-    }
-    __syncthreads();
-    cpx<T>* Z = fft_block<T, false>(b0, b1, a.pl, nr, tw);
-    for (int rl = 0; rl < nr; ++rl) {
-      const cpx<T>* z = Z + rl * N;
-      cpx<T>* out = spec + (int64_t)(rg + rl) * a.Pw2p;
-      for (int k = threadIdx.x; k < a.Pw2; k += blockDim.x) {
-        if (a.half) {
-          const cpx<T> zk = z[k < N ? k : 0], zc = conj(z[k > 0 ? N - k : 0]);
-          const cpx<T> e = (T)0.5 * (zk + zc), d = (T)0.5 * (zk - zc);
-          const cpx<T> wd = tw_w[k] * d;          // X = e - i w d, w = exp(-2 pi i k / Pw)
-          out[k] = mk<T>(e.re + wd.im, e.im - wd.re);
-        } else {
-          out[k] = z[k];
-        }
-      }
-    }
-    __syncthreads();
-  }
-}
-
-struct ColArgs {
-  void* spec[2];      // cpx<T> [n][C][H_Bk][Pw2p]
-  const void* khat;   // cpx<T> [n][2][Ph][Pw2p]
-  void* ihat;         // cpx<T> [n][C][H][Pw2p]
-  const void* stw;    // stage twiddles of the Ph plan (read through L1)
-  int H1, H2, H, C, Ph, Pw2, Pw2p, single;
-  double eps;
-  FftPlan pl;         // plan of Ph
-};
-
-constexpr int kColThreads = 512;
-
+// ------------------------------------------------- asynchronous copies ---
 __device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc, int src_bytes) {
   const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gsrc), "r"(src_bytes)
                : "memory");
+}
+template <int B>
+__device__ __forceinline__ void cp_async_small(void* smem_dst, const void* gsrc) {   // B = 4 or 8
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gsrc), "n"(B) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
@@ -386,6 +306,252 @@ __device__ __forceinline__ cd ldg_cpx(const cd* p) {
   const double2 v = __ldg((const double2*)p);
   return mk(v.x, v.y);
 }
+
+// ------------------------------------------ row pass (A1 folds + A6 rows) ---
+//
+// One read of every row of B1 and B2 serves both the evaluation folds of A1
+// and the forward row FFTs of A6.  A block owns the rows r = x, x + X, x + 2X,
+// ... (x = blockIdx.x, X = gridDim.x) of one frame channel; with X = M every
+// row of a block has the same residue r mod M, so the block alone completes
+// column-fold bin x:  Fz1[x][c] = sum_{r = x mod M} B[r][c].  Each row's own
+// fold Fz2[m][r] = sum_{c = m mod M} B[r][c] is finished as the row passes.
+// The bins are exact float sums (TwoSum hi + lo) stored as double; the M-point
+// DFT over the bins (k_fold_dft, cbp_eval.cu) gives the samples.
+//
+// Rows arrive by cp.async into a double-buffered staging area, nbr rows per
+// group, the next group in flight while the current one is folded and
+// transformed.
+struct RowPassArgs {
+  FrameDesc fr[2];
+  void* spec[2];       // cpx<T> [n][C][H_Bk][Pw2p] (FFT)
+  double* bins_r[2];   // [n C][M][H_Bk] row-fold bins (FOLD)
+  double* bins_c[2];   // [n C][M][W_Bk] column-fold bins (FOLD)
+  int* bad;            // [n] non-finite input flags (FOLD)
+  int M;
+  int fft_frames;      // frames whose rows are transformed (1: single-kernel form)
+  int Pw, Pw2, Pw2p, half, nbr, rw;
+  int wl;              // width the shared-memory layout is sized for (max W_Bk)
+  FftPlan pl;          // plan of Pw/2 (half) or Pw
+};
+
+constexpr int kRowWarps = kFftThreads / 32;
+
+template <typename In> struct FoldAcc;
+template <> struct FoldAcc<float> { using type = TwoSum; };
+template <> struct FoldAcc<double> { using type = DoubleSum; };
+
+// Shared-memory layout of the row pass (byte offsets); one definition for the
+// kernel and its launcher.
+struct RowPassSmem {
+  size_t tw, b0, b1, raw0, raw1, colacc, rb, rph, total;
+};
+__host__ __device__ inline size_t rp_align(size_t x) { return (x + 15) & ~size_t(15); }
+__host__ __device__ inline RowPassSmem row_pass_layout(int N, int ntw, int W, int nbr, int rw,
+                                                       size_t ce, size_t es, bool fold, bool fft) {
+  RowPassSmem L;
+  size_t o = 0;
+  L.tw = o;
+  if (fft) o += rp_align((size_t)((ntw + 1) & ~1) * ce);
+  L.b0 = o;
+  if (fft) o += rp_align((size_t)nbr * N * ce);
+  L.b1 = o;
+  if (fft) o += rp_align((size_t)nbr * N * ce);
+  L.raw0 = o;
+  o += rp_align((size_t)nbr * rw * es);
+  L.raw1 = o;
+  o += rp_align((size_t)nbr * rw * es);
+  L.colacc = o;
+  if (fold) o += rp_align((size_t)W * 8);
+  L.rb = o;
+  if (fold) o += rp_align((size_t)kRowWarps * 32 * 8);
+  L.rph = o;
+  o += rp_align(2 * (size_t)nbr * sizeof(int));
+  L.total = o;
+  return L;
+}
+
+// Issue the copies of nr rows (row i at element offset rowoff(i) of fb) into
+// the staging rows dst + i * rw, each at its own 16-byte phase ph_i (element
+// c of row i lands at dst[i * rw + ph_i + c]).  Elements before a row's first
+// 16-byte boundary go by element-sized copies, the rest by 16-byte chunks, the
+// last one partial; nothing outside the row is read.
+template <typename In, class RowOff>
+__device__ __forceinline__ void stage_rows_async(In* dst, int* rph, const In* fb, const RowOff& rowoff,
+                                                 int nr, int W, int rw) {
+  constexpr int E = 16 / (int)sizeof(In);
+  const int tasks = (E - 1) + (W + E - 1) / E;
+  for (int idx = threadIdx.x; idx < nr * tasks; idx += blockDim.x) {
+    const int i = idx / tasks, t = idx - i * tasks;
+    const In* row = fb + rowoff(i);
+    const int ph = (int)(((uintptr_t)row / sizeof(In)) & (E - 1));
+    const int head = ph ? min(E - ph, W) : 0;
+    In* drow = dst + i * rw + ph;
+    if (t < E - 1) {                                   // head element t
+      if (t < head) cp_async_small<(int)sizeof(In)>(drow + t, row + t);
+    } else {
+      const int c0 = head + (t - (E - 1)) * E;          // chunk start element
+      if (c0 < W) cp_async16(drow + c0, row + c0, min(E, W - c0) * (int)sizeof(In));
+    }
+    if (t == 0) rph[i] = ph;
+  }
+}
+
+template <typename T, typename In, bool FOLD, bool FFT>
+__global__ void __launch_bounds__(kFftThreads)
+k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
+  using Acc = typename FoldAcc<In>::type;
+  extern __shared__ __align__(16) char smem[];
+  const FrameDesc& fr = a.fr[blockIdx.z];
+  const int N = a.pl.n, NB = a.nbr, W = fr.w, M = a.M;
+  const bool fft = FFT && (int)blockIdx.z < a.fft_frames;
+  const RowPassSmem L = row_pass_layout(N, a.pl.ntw, a.wl, NB, a.rw, sizeof(cpx<T>), sizeof(In),
+                                        FOLD, FFT);
+  cpx<T>* tw = (cpx<T>*)(smem + L.tw);
+  cpx<T>* b0 = (cpx<T>*)(smem + L.b0);
+  cpx<T>* b1 = (cpx<T>*)(smem + L.b1);
+  In* const raw0 = (In*)(smem + L.raw0);
+  In* const raw1 = (In*)(smem + L.raw1);
+  Acc* colacc = (Acc*)(smem + L.colacc);
+  double* rb = (double*)(smem + L.rb);
+  int* rph = (int*)(smem + L.rph);
+  if (fft) load_twiddles(tw, stw, a.pl.ntw);
+  if (FOLD)
+    for (int c = threadIdx.x; c < W; c += blockDim.x) colacc[c] = Acc();
+  const int fc = blockIdx.y, f = fc / fr.c, ch = fc % fr.c;
+  const int x0 = blockIdx.x, X = gridDim.x;
+  const int nrows = x0 < fr.h ? (fr.h - x0 + X - 1) / X : 0;
+  const int ngroups = (nrows + NB - 1) / NB;
+  const In* fb = (const In*)frame_base(fr, f) + (int64_t)ch * fr.cs;
+  auto row_of = [&](int g, int i) { return x0 + (g * NB + i) * X; };
+  if (ngroups > 0) {
+    stage_rows_async<In>(raw0, rph, fb, [&](int i) { return (int64_t)row_of(0, i) * fr.rs; },
+                         min(NB, nrows), W, a.rw);
+  }
+  cp_async_commit();
+  cpx<T>* spec = fft ? (cpx<T>*)a.spec[blockIdx.z] + (int64_t)fc * fr.h * a.Pw2p : nullptr;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int g = 0; g < ngroups; ++g) {
+    const int nr = min(NB, nrows - g * NB);
+    if (g + 1 < ngroups) {
+      const int g1 = g + 1;
+      stage_rows_async<In>((g1 & 1) ? raw1 : raw0, rph + (g1 & 1) * NB, fb,
+                           [&](int i) { return (int64_t)row_of(g1, i) * fr.rs; },
+                           min(NB, nrows - g1 * NB), W, a.rw);
+    }
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    const In* rw0 = (g & 1) ? raw1 : raw0;
+    const int* ph = rph + (g & 1) * NB;
+    if (FOLD) {
+      // column folds: this block's bin, one thread per column
+      for (int c = threadIdx.x; c < W; c += blockDim.x) {
+        Acc acc = colacc[c];
+        for (int i = 0; i < nr; ++i) acc.add(rw0[i * a.rw + ph[i] + c]);
+        colacc[c] = acc;
+      }
+      // row folds: wpr warps per row, each over a run of whole M-column steps;
+      // lane l < gM owns bin l mod M
+      const int wpr = kRowWarps / nr;
+      if (warp < wpr * nr) {
+        const int i = warp / wpr, sg = warp - i * wpr;
+        const int gm = (32 / M) * M;
+        const int nsteps = (W + gm - 1) / gm, sps = (nsteps + wpr - 1) / wpr;
+        Acc acc;
+        if (lane < gm) {
+          const In* rowp = rw0 + i * a.rw + ph[i];
+          const int e = min(nsteps, (sg + 1) * sps);
+          for (int st = sg * sps; st < e; ++st) {
+            const int c = st * gm + lane;
+            if (c < W) acc.add(rowp[c]);
+          }
+        }
+        rb[warp * 32 + lane] = acc.value();
+      }
+    }
+    if (fft) {
+      for (int i = 0; i < nr; ++i) {
+        const In* rowp = rw0 + i * a.rw + ph[i];
+        cpx<T>* dst = b0 + i * N;
+        if (a.half && sizeof(In) == 4 && (ph[i] & 1) == 0) {
+          // pairs (x[2m], x[2m+1]) are 8-byte aligned in the staging row
+          const float2* r2 = (const float2*)rowp;
+          const int full = W >> 1;
+          for (int m = threadIdx.x; m < N; m += blockDim.x) {
+            T x0 = 0, x1 = 0;
+            if (m < full) {
+              const float2 v = r2[m];
+              x0 = v.x;
+              x1 = v.y;
+            } else if (2 * m < W) {
+              x0 = (T)rowp[2 * m];
+            }
+            dst[m] = mk<T>(x0, x1);
+          }
+        } else if (a.half) {
+          for (int m = threadIdx.x; m < N; m += blockDim.x) {
+            const int c0 = 2 * m, c1 = 2 * m + 1;
+            dst[m] = mk<T>(c0 < W ? (T)rowp[c0] : (T)0, c1 < W ? (T)rowp[c1] : (T)0);
+          }
+        } else {
+          for (int m = threadIdx.x; m < N; m += blockDim.x) dst[m] = mk<T>(m < W ? (T)rowp[m] : (T)0, (T)0);
+        }
+      }
+    }
+    __syncthreads();
+    if (FOLD) {
+      const int wpr = kRowWarps / nr, q = 32 / M;
+      for (int t = threadIdx.x; t < nr * M; t += blockDim.x) {
+        const int i = t / M, m = t - i * M;
+        double v = 0;
+        for (int sg = 0; sg < wpr; ++sg)
+          for (int qq = 0; qq < q; ++qq) v += rb[(i * wpr + sg) * 32 + qq * M + m];
+        a.bins_r[blockIdx.z][((int64_t)fc * M + m) * fr.h + row_of(g, i)] = v;
+      }
+    }
+    if (fft) {
+      cpx<T>* Z = fft_block<T, false>(b0, b1, a.pl, nr, tw);
+      for (int i = 0; i < nr; ++i) {
+        const cpx<T>* z = Z + i * N;
+        cpx<T>* out = spec + (int64_t)row_of(g, i) * a.Pw2p;
+        for (int k = threadIdx.x; k < a.Pw2; k += blockDim.x) {
+          if (a.half) {
+            const cpx<T> zk = z[k < N ? k : 0], zc = conj(z[k > 0 ? N - k : 0]);
+            const cpx<T> e = (T)0.5 * (zk + zc), d = (T)0.5 * (zk - zc);
+            const cpx<T> wd = tw_w[k] * d;          // X = e - i w d, w = exp(-2 pi i k / Pw)
+            out[k] = mk<T>(e.re + wd.im, e.im - wd.re);
+          } else {
+            out[k] = z[k];
+          }
+        }
+      }
+    }
+    __syncthreads();
+  }
+  cp_async_wait<0>();
+  if (FOLD) {
+    bool finite = true;
+    double* dst = a.bins_c[blockIdx.z] + ((int64_t)fc * M + x0) * W;
+    for (int c = threadIdx.x; c < W; c += blockDim.x) {
+      const double v = colacc[c].value();
+      finite = finite && isfinite(v);
+      dst[c] = v;
+    }
+    if (__syncthreads_or(!finite) && threadIdx.x == 0) atomicOr(a.bad + f, 1);
+  }
+}
+
+constexpr int kColThreads = 512;
+
+struct ColArgs {
+  void* spec[2];      // cpx<T> [n][C][H_Bk][Pw2p]
+  const void* khat;   // cpx<T> [n][2][Ph][Pw2p]
+  void* ihat;         // cpx<T> [n][C][H][Pw2p]
+  const void* stw;    // stage twiddles of the Ph plan (read through L1)
+  int H1, H2, H, C, Ph, Pw2, Pw2p, single;
+  double eps;
+  FftPlan pl;         // plan of Ph
+};
 
 // Stockham stage over NB transforms interleaved in shared memory: element j
 // of transform b at j * NB + b (consecutive threads take consecutive b).
@@ -403,10 +569,10 @@ __device__ __forceinline__ void stockham_stage_il(const cpx<T>* __restrict__ in,
 #pragma unroll
     for (int r = 0; r < R; ++r) v[r] = src[r * Nr * NB];
     if (Ns > 1) {
-      const cpx<T>* w = tw + st.tw + k * (R - 1);
+      const cpx<T>* w = tw + st.tw + k;
 #pragma unroll
       for (int r = 1; r < R; ++r) {
-        cpx<T> ww = ldg_cpx(w + r - 1);
+        cpx<T> ww = ldg_cpx(w + (r - 1) * Ns);
         if (Inv) ww.im = -ww.im;
         v[r] = v[r] * ww;
       }
@@ -608,28 +774,59 @@ void run_kernel_spectra(const Plan& p, char* ws, cudaStream_t st) {
                                                  (cpx<T>*)(ws + p.off_khat));
 }
 
-template <typename T>
-void run_row_fft(const Plan& p, const FrameDesc& b1, const FrameDesc& b2, char* ws,
-                 cudaStream_t st) {
-  const FftPlan& plw = p.pw_half ? p.fp_w2 : p.fp_w;
-  RowArgs a;
+// Shared-memory target of the row pass: two resident blocks per SM.
+constexpr size_t kRowPassSmemTarget = 112 * 1024;
+
+template <typename T, typename In, bool FOLD, bool FFT>
+void run_row_pass_t(const Plan& p, const RowPassArgs& a, int gx, int gz, char* ws,
+                    cudaStream_t st) {
+  const RowPassSmem L = row_pass_layout(a.pl.n, a.pl.ntw, a.wl, a.nbr, a.rw, sizeof(cpx<T>),
+                                        sizeof(In), FOLD, FFT);
+  cudaFuncSetAttribute(k_row_pass<T, In, FOLD, FFT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)L.total);
+  k_row_pass<T, In, FOLD, FFT><<<dim3(gx, p.n * p.C, gz), kFftThreads, L.total, st>>>(
+      a, (const cpx<T>*)(ws + p.off_tw_w), (const cpx<T>*)(ws + p.off_stw_r));
+}
+
+template <typename T, typename In>
+void run_row_pass(const Plan& p, const FrameDesc& b1, const FrameDesc& b2, char* ws,
+                  cudaStream_t st, bool fold, bool fft) {
+  RowPassArgs a;
   a.fr[0] = b1;
   a.fr[1] = b2;
   a.spec[0] = ws + p.off_spec[0];
   a.spec[1] = ws + p.off_spec[1];
+  for (int k = 0; k < 2; ++k) {
+    a.bins_r[k] = (double*)(ws + p.off_fbr[k]);
+    a.bins_c[k] = (double*)(ws + p.off_fbc[k]);
+  }
+  a.bad = (int*)(ws + p.off_bad);
+  a.M = p.M;
+  a.fft_frames = p.single_kernel ? 1 : 2;
   a.Pw = p.Pw;
   a.Pw2 = p.Pw2;
   a.Pw2p = p.Pw2p;
   a.half = p.pw_half;
-  a.pl = plw;
-  a.nbr = rows_per_iter(plw.n, plw.ntw, sizeof(cpx<T>));
+  a.pl = p.pw_half ? p.fp_w2 : p.fp_w;
+  a.wl = p.W1 > p.W2 ? p.W1 : p.W2;
+  constexpr int E = 16 / (int)sizeof(In);
+  a.rw = ((a.wl + 2 * E + E - 1) / E) * E;
+  // rows per group: the most (up to 4) that keep two blocks per SM
+  a.nbr = 1;
+  for (int nb = 4; nb >= 1; nb >>= 1) {
+    const RowPassSmem L = row_pass_layout(a.pl.n, a.pl.ntw, a.wl, nb, a.rw, sizeof(cpx<T>),
+                                          sizeof(In), fold, fft);
+    if (L.total <= kRowPassSmemTarget && (!fft || (long)nb * a.pl.n <= 65535)) {
+      a.nbr = nb;
+      break;
+    }
+  }
   const int hmax = p.H1 > p.H2 ? p.H1 : p.H2;
-  const int chunks = (hmax + 2 * a.nbr - 1) / (2 * a.nbr);
-  dim3 g(chunks, p.n * p.C, p.single_kernel ? 1 : 2);
-  const size_t sm = sizeof(cpx<T>) * (((plw.ntw + 1) & ~1) + 2 * (size_t)a.nbr * plw.n);
-  cudaFuncSetAttribute(k_row_fft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_row_fft<T><<<g, kFftThreads, sm, st>>>(a, (const cpx<T>*)(ws + p.off_tw_w),
-                                           (const cpx<T>*)(ws + p.off_stw_r));
+  const int gx = fold ? p.M : (hmax + 31) / 32;
+  const int gz = fold ? 2 : a.fft_frames;
+  if (fold && fft) run_row_pass_t<T, In, true, true>(p, a, gx, gz, ws, st);
+  else if (fft) run_row_pass_t<T, In, false, true>(p, a, gx, gz, ws, st);
+  else run_row_pass_t<float, In, true, false>(p, a, gx, gz, ws, st);
 }
 
 template <typename T>
@@ -704,10 +901,24 @@ void launch_kernel_spectra(const Plan& p, char* ws, cudaStream_t st) {
   else run_kernel_spectra<float>(p, ws, st);
 }
 
-void launch_row_fft(const Plan& p, const FrameDesc& b1, const FrameDesc& b2, char* ws,
-                    cudaStream_t st) {
-  if (p.fft_f64) run_row_fft<double>(p, b1, b2, ws, st);
-  else run_row_fft<float>(p, b1, b2, ws, st);
+void launch_row_pass(const Plan& p, const FrameDesc& b1, const FrameDesc& b2, char* ws,
+                     cudaStream_t st, bool fold, bool fft) {
+  if (!fold && !fft) return;
+  if (fft && p.fft_f64) {
+    if (b1.f64) run_row_pass<double, double>(p, b1, b2, ws, st, fold, fft);
+    else run_row_pass<double, float>(p, b1, b2, ws, st, fold, fft);
+  } else {
+    if (b1.f64) run_row_pass<float, double>(p, b1, b2, ws, st, fold, fft);
+    else run_row_pass<float, float>(p, b1, b2, ws, st, fold, fft);
+  }
+}
+
+size_t row_pass_min_smem(const Plan& p) {
+  const FftPlan& pl = p.pw_half ? p.fp_w2 : p.fp_w;
+  const int wl = p.W1 > p.W2 ? p.W1 : p.W2;
+  const size_t ce = p.fft_f64 ? 16 : 8;
+  const int rw = ((wl + 4 + 1) / 2) * 2;   // staging pitch for 8-byte elements (the widest)
+  return row_pass_layout(pl.n, pl.ntw, wl, 1, rw, ce, 8, true, true).total;
 }
 
 void launch_col_deconv(const Plan& p, char* ws, cudaStream_t st) {

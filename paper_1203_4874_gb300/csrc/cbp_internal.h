@@ -65,6 +65,7 @@ struct Plan {
   // workspace layout (byte offsets into one device allocation)
   size_t off_pz2[2], off_pz1[2];   // cd [n][C][ns][len] sample polynomials (double)
   size_t off_pz2f[2], off_pz1f[2]; // cdf float-float copies for the mixed path's Gram
+  size_t off_fbr[2], off_fbc[2];   // double [n][C][M][H_Bk] row / [n][C][M][W_Bk] column fold bins
   size_t off_x;                    // cd [n][2][ns][nn]
   size_t off_sdiag;                // double [n][2][ns][4]
   size_t off_resid;                // cd [n][2][ns][C][Lmax] (FP64 path residual scratch)
@@ -89,9 +90,12 @@ cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_param
 FrameDesc frame_desc(const cbp_frames* f, const void* data_override);
 
 // ---- launchers (one per .cu file) ----
-// A1: sample polynomials (cbp_eval.cu)
+// A1: sample polynomials (cbp_eval.cu): the fold-only row pass, then the
+// bins' M-point DFTs.  In a deblurring call the folds ride on the row FFT pass
+// (launch_row_pass with fold and fft) and only launch_fold_dft follows.
 void launch_eval(const Plan& p, const FrameDesc& b1, const FrameDesc& b2, char* ws,
                  cudaStream_t st);
+void launch_fold_dft(const Plan& p, char* ws, cudaStream_t st);
 // A2 + A3: per-sample Gram and null vector (cbp_solve.cu)
 void launch_sample_solve(const Plan& p, char* ws, cudaStream_t st);
 // A4 + A5: lift, scale fix, kernels (cbp_solve.cu)
@@ -104,8 +108,11 @@ void launch_kernels_in(const Plan& p, char* ws, const void* k1, const void* k2, 
 // A6: deconvolution (cbp_fft.cu)
 void init_twiddles(const Plan& p, char* ws, cudaStream_t st);
 void launch_kernel_spectra(const Plan& p, char* ws, cudaStream_t st);
-void launch_row_fft(const Plan& p, const FrameDesc& b1, const FrameDesc& b2, char* ws,
-                    cudaStream_t st);
+// One read of every frame row: A1 folds (fold) and/or A6 forward row FFTs (fft).
+void launch_row_pass(const Plan& p, const FrameDesc& b1, const FrameDesc& b2, char* ws,
+                     cudaStream_t st, bool fold, bool fft);
+// shared memory of the row pass at one row per group (the planner's limit check)
+size_t row_pass_min_smem(const Plan& p);
 void launch_col_deconv(const Plan& p, char* ws, cudaStream_t st);
 void launch_row_ifft(const Plan& p, char* ws, void* latent, int out_f64, cudaStream_t st,
                      const uint64_t* lat_tab = nullptr);

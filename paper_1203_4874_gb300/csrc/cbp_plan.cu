@@ -126,8 +126,8 @@ cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_param
   const size_t ce = p.fft_f64 ? 16 : 8;
   const size_t cw = p.fft_f64 ? 2 : 4;
   const size_t nrow = p.pw_half ? p.Pw / 2 : p.Pw;
-  // one row buffer pair + stage twiddles; exact magic division needs rows * N < 2^16
-  if ((2 + 1) * ce * nrow > smem_max || nrow > 16384) return CBP_ERR_UNSUPPORTED;
+  // row pass at one row per group; exact magic division needs rows * N < 2^16
+  if (row_pass_min_smem(p) > smem_max || nrow > 16384) return CBP_ERR_UNSUPPORTED;
   if (3 * cw * ce * p.Ph > smem_max || cw * p.Ph > 65536) return CBP_ERR_UNSUPPORTED;
   if (sample_solve_smem(p.nn) > smem_max || scale_solve_smem(p.M) > smem_max)
     return CBP_ERR_UNSUPPORTED;
@@ -149,6 +149,10 @@ cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_param
     p.off_pz2f[1] = take(n * C * ns * p.H2 * 16);
     p.off_pz1f[0] = take(n * C * ns * p.W1 * 16);
     p.off_pz1f[1] = take(n * C * ns * p.W2 * 16);
+  }
+  for (int k = 0; k < 2; ++k) {
+    p.off_fbr[k] = take(n * C * (size_t)p.M * (k ? p.H2 : p.H1) * 8);
+    p.off_fbc[k] = take(n * C * (size_t)p.M * (k ? p.W2 : p.W1) * 8);
   }
   p.off_x = take(n * 2 * ns * p.nn * 16);
   p.off_sdiag = take(n * 2 * ns * 4 * 8);
