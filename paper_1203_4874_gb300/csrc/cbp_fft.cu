@@ -334,34 +334,41 @@ struct RowPassArgs {
   FftPlan pl;          // plan of Pw/2 (half) or Pw
 };
 
-constexpr int kRowWarps = kFftThreads / 32;
+constexpr int kRowPassThreads = 512;
+constexpr int kRowWarps = kRowPassThreads / 32;
+constexpr int kColRegs = 4;          // column-fold accumulators per thread held in registers
 
 template <typename In> struct FoldAcc;
 template <> struct FoldAcc<float> { using type = TwoSum; };
 template <> struct FoldAcc<double> { using type = DoubleSum; };
 
 // Shared-memory layout of the row pass (byte offsets); one definition for the
-// kernel and its launcher.
+// kernel and its launcher.  The FFT's second buffer reuses the group's staging
+// rows once they are consumed, when they are large enough (b1_alias); column
+// accumulators live in registers unless W exceeds kColRegs per thread.
 struct RowPassSmem {
   size_t tw, b0, b1, raw0, raw1, colacc, rb, rph, total;
+  bool b1_alias, col_smem;
 };
 __host__ __device__ inline size_t rp_align(size_t x) { return (x + 15) & ~size_t(15); }
 __host__ __device__ inline RowPassSmem row_pass_layout(int N, int ntw, int W, int nbr, int rw,
                                                        size_t ce, size_t es, bool fold, bool fft) {
   RowPassSmem L;
+  L.b1_alias = (size_t)N * ce <= (size_t)rw * es;
+  L.col_smem = fold && W > kColRegs * kRowPassThreads;
   size_t o = 0;
   L.tw = o;
   if (fft) o += rp_align((size_t)((ntw + 1) & ~1) * ce);
   L.b0 = o;
   if (fft) o += rp_align((size_t)nbr * N * ce);
   L.b1 = o;
-  if (fft) o += rp_align((size_t)nbr * N * ce);
+  if (fft && !L.b1_alias) o += rp_align((size_t)nbr * N * ce);
   L.raw0 = o;
   o += rp_align((size_t)nbr * rw * es);
   L.raw1 = o;
   o += rp_align((size_t)nbr * rw * es);
   L.colacc = o;
-  if (fold) o += rp_align((size_t)W * 8);
+  if (L.col_smem) o += rp_align((size_t)W * 8);
   L.rb = o;
   if (fold) o += rp_align((size_t)kRowWarps * 32 * 8);
   L.rph = o;
@@ -397,7 +404,7 @@ __device__ __forceinline__ void stage_rows_async(In* dst, int* rph, const In* fb
 }
 
 template <typename T, typename In, bool FOLD, bool FFT>
-__global__ void __launch_bounds__(kFftThreads)
+__global__ void __launch_bounds__(kRowPassThreads)
 k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
   using Acc = typename FoldAcc<In>::type;
   extern __shared__ __align__(16) char smem[];
@@ -408,14 +415,14 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
                                         FOLD, FFT);
   cpx<T>* tw = (cpx<T>*)(smem + L.tw);
   cpx<T>* b0 = (cpx<T>*)(smem + L.b0);
-  cpx<T>* b1 = (cpx<T>*)(smem + L.b1);
   In* const raw0 = (In*)(smem + L.raw0);
   In* const raw1 = (In*)(smem + L.raw1);
   Acc* colacc = (Acc*)(smem + L.colacc);
   double* rb = (double*)(smem + L.rb);
   int* rph = (int*)(smem + L.rph);
   if (fft) load_twiddles(tw, stw, a.pl.ntw);
-  if (FOLD)
+  Acc creg[kColRegs];
+  if (FOLD && L.col_smem)
     for (int c = threadIdx.x; c < W; c += blockDim.x) colacc[c] = Acc();
   const int fc = blockIdx.y, f = fc / fr.c, ch = fc % fr.c;
   const int x0 = blockIdx.x, X = gridDim.x;
@@ -441,14 +448,23 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();
-    const In* rw0 = (g & 1) ? raw1 : raw0;
+    In* const rw0 = (g & 1) ? raw1 : raw0;
     const int* ph = rph + (g & 1) * NB;
     if (FOLD) {
       // column folds: this block's bin, one thread per column
-      for (int c = threadIdx.x; c < W; c += blockDim.x) {
-        Acc acc = colacc[c];
-        for (int i = 0; i < nr; ++i) acc.add(rw0[i * a.rw + ph[i] + c]);
-        colacc[c] = acc;
+      if (!L.col_smem) {
+#pragma unroll
+        for (int j = 0; j < kColRegs; ++j) {
+          const int c = threadIdx.x + j * kRowPassThreads;
+          if (c < W)
+            for (int i = 0; i < nr; ++i) creg[j].add(rw0[i * a.rw + ph[i] + c]);
+        }
+      } else {
+        for (int c = threadIdx.x; c < W; c += blockDim.x) {
+          Acc acc = colacc[c];
+          for (int i = 0; i < nr; ++i) acc.add(rw0[i * a.rw + ph[i] + c]);
+          colacc[c] = acc;
+        }
       }
       // row folds: wpr warps per row, each over a run of whole M-column steps;
       // lane l < gM owns bin l mod M
@@ -510,6 +526,9 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
       }
     }
     if (fft) {
+      // the staging rows of this group are consumed: they serve as the
+      // FFT's second buffer when large enough
+      cpx<T>* b1 = L.b1_alias ? (cpx<T>*)rw0 : (cpx<T>*)(smem + L.b1);
       cpx<T>* Z = fft_block<T, false>(b0, b1, a.pl, nr, tw);
       for (int i = 0; i < nr; ++i) {
         const cpx<T>* z = Z + i * N;
@@ -532,10 +551,22 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
   if (FOLD) {
     bool finite = true;
     double* dst = a.bins_c[blockIdx.z] + ((int64_t)fc * M + x0) * W;
-    for (int c = threadIdx.x; c < W; c += blockDim.x) {
-      const double v = colacc[c].value();
-      finite = finite && isfinite(v);
-      dst[c] = v;
+    if (!L.col_smem) {
+#pragma unroll
+      for (int j = 0; j < kColRegs; ++j) {
+        const int c = threadIdx.x + j * kRowPassThreads;
+        if (c < W) {
+          const double v = creg[j].value();
+          finite = finite && isfinite(v);
+          dst[c] = v;
+        }
+      }
+    } else {
+      for (int c = threadIdx.x; c < W; c += blockDim.x) {
+        const double v = colacc[c].value();
+        finite = finite && isfinite(v);
+        dst[c] = v;
+      }
     }
     if (__syncthreads_or(!finite) && threadIdx.x == 0) atomicOr(a.bad + f, 1);
   }
@@ -690,19 +721,65 @@ struct IRowArgs {
   FftPlan pl;
 };
 
-// Inverse complex-to-real FFT of every row, crop and scale, nbr rows at a time.
+// Shared-memory layout of the inverse row pass: stage twiddles, the FFT
+// buffer, two staging buffers of nbr spectrum rows (pitch Pw2p, 16-byte
+// aligned); the FFT's second buffer is the consumed staging rows when a row
+// fits in them (N <= Pw2p, the half-length transform), else its own.
+struct IRowSmem {
+  size_t tw, b0, b1, raw0, raw1, total;
+  bool b1_alias;
+};
+__host__ __device__ inline IRowSmem irow_layout(int N, int ntw, int Pw2p, int nbr, size_t ce) {
+  IRowSmem L;
+  L.b1_alias = N <= Pw2p;
+  size_t o = 0;
+  L.tw = o;
+  o += rp_align((size_t)((ntw + 1) & ~1) * ce);
+  L.b0 = o;
+  o += rp_align((size_t)nbr * N * ce);
+  L.b1 = o;
+  if (!L.b1_alias) o += rp_align((size_t)nbr * N * ce);
+  L.raw0 = o;
+  o += rp_align((size_t)nbr * Pw2p * ce);
+  L.raw1 = o;
+  o += rp_align((size_t)nbr * Pw2p * ce);
+  L.total = o;
+  return L;
+}
+
+// cp.async of nr spectrum rows (Pw2 entries each, 16-byte aligned rows of
+// pitch Pw2p) into dst rows of pitch Pw2p; the last chunk may be partial.
+template <typename T, class RowPtr>
+__device__ __forceinline__ void stage_spec_rows_async(cpx<T>* dst, const RowPtr& rowp, int nr,
+                                                      int Pw2, int Pw2p) {
+  constexpr int E = 16 / (int)sizeof(cpx<T>);
+  const int tasks = (Pw2 + E - 1) / E;
+  for (int idx = threadIdx.x; idx < nr * tasks; idx += blockDim.x) {
+    const int i = idx / tasks, c0 = (idx - i * tasks) * E;
+    cp_async16(dst + i * Pw2p + c0, rowp(i) + c0, min(E, Pw2 - c0) * (int)sizeof(cpx<T>));
+  }
+}
+
+// Inverse complex-to-real FFT of every row, crop and scale.  A block owns the
+// rows x, x + X, ... (x = blockIdx.x, X = gridDim.x) of one frame channel, nbr
+// at a time, the next group's spectrum rows in flight (cp.async) while the
+// current group is transformed.
 template <typename T>
-__global__ void __launch_bounds__(kFftThreads)
+__global__ void __launch_bounds__(kRowPassThreads)
 k_row_ifft(IRowArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
   extern __shared__ __align__(16) char smem[];
   const int N = a.pl.n, NB = a.nbr;
-  cpx<T>* tw = (cpx<T>*)smem;
-  cpx<T>* b0 = tw + ((a.pl.ntw + 1) & ~1);
-  cpx<T>* b1 = b0 + NB * N;
+  const IRowSmem L = irow_layout(N, a.pl.ntw, a.Pw2p, NB, sizeof(cpx<T>));
+  cpx<T>* tw = (cpx<T>*)(smem + L.tw);
+  cpx<T>* b0 = (cpx<T>*)(smem + L.b0);
+  cpx<T>* const raw0 = (cpx<T>*)(smem + L.raw0);
+  cpx<T>* const raw1 = (cpx<T>*)(smem + L.raw1);
   load_twiddles(tw, stw, a.pl.ntw);
   const int fc = blockIdx.y;
-  const int rows_per = (a.H + gridDim.x - 1) / gridDim.x;
-  const int r0 = blockIdx.x * rows_per, r1 = min(a.H, r0 + rows_per);
+  const int x0 = blockIdx.x, X = gridDim.x;
+  const int nrows = x0 < a.H ? (a.H - x0 + X - 1) / X : 0;
+  const int ngroups = (nrows + NB - 1) / NB;
+  auto row_of = [&](int g, int i) { return x0 + (g * NB + i) * X; };
   const cpx<T>* src = (const cpx<T>*)a.ihat + (int64_t)fc * a.H * a.Pw2p;
   void* outp = a.latent;
   int64_t obase = (int64_t)fc * a.H * a.W;
@@ -711,28 +788,42 @@ k_row_ifft(IRowArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
     outp = (void*)a.lat_tab[fc / C];
     obase = (int64_t)(fc % C) * a.H * a.W;
   }
+  if (ngroups > 0)
+    stage_spec_rows_async<T>(raw0, [&](int i) { return src + (int64_t)row_of(0, i) * a.Pw2p; },
+                             min(NB, nrows), a.Pw2, a.Pw2p);
+  cp_async_commit();
   const T sc = (T)a.scale;
-  for (int rg = r0; rg < r1; rg += NB) {
-    const int nr = min(NB, r1 - rg);
-    for (int rl = 0; rl < nr; ++rl) {
-      const cpx<T>* X = src + (int64_t)(rg + rl) * a.Pw2p;
-      cpx<T>* dst = b0 + rl * N;
+  for (int g = 0; g < ngroups; ++g) {
+    const int nr = min(NB, nrows - g * NB);
+    if (g + 1 < ngroups) {
+      const int g1 = g + 1;
+      stage_spec_rows_async<T>((g1 & 1) ? raw1 : raw0,
+                               [&](int i) { return src + (int64_t)row_of(g1, i) * a.Pw2p; },
+                               min(NB, nrows - g1 * NB), a.Pw2, a.Pw2p);
+    }
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();
+    cpx<T>* const rw0 = (g & 1) ? raw1 : raw0;
+    for (int i = 0; i < nr; ++i) {
+      const cpx<T>* Xr = rw0 + i * a.Pw2p;
+      cpx<T>* dst = b0 + i * N;
       for (int k = threadIdx.x; k < N; k += blockDim.x) {
         if (a.half) {
-          const cpx<T> xk = X[k], xc = conj(X[N - k]);
+          const cpx<T> xk = Xr[k], xc = conj(Xr[N - k]);
           const cpx<T> e = (T)0.5 * (xk + xc), d = (T)0.5 * (xk - xc);
-          const cpx<T> o = conj(tw_w[k]) * d;     // exp(+2 pi i k / Pw) d
-          dst[k] = mk<T>(e.re - o.im, e.im + o.re);  // E + i O
+          const cpx<T> o = conj(ldg_cpx(tw_w + k)) * d;   // exp(+2 pi i k / Pw) d
+          dst[k] = mk<T>(e.re - o.im, e.im + o.re);        // E + i O
         } else {
-          dst[k] = k < a.Pw2 ? X[k] : conj(X[N - k]);
+          dst[k] = k < a.Pw2 ? Xr[k] : conj(Xr[N - k]);
         }
       }
     }
     __syncthreads();
-    cpx<T>* Z = fft_block<T, true>(b0, b1, a.pl, nr, tw);
-    for (int rl = 0; rl < nr; ++rl) {
-      const cpx<T>* z = Z + rl * N;
-      const int64_t ob = obase + (int64_t)(rg + rl) * a.W;
+    cpx<T>* Z = fft_block<T, true>(b0, L.b1_alias ? rw0 : (cpx<T>*)(smem + L.b1), a.pl, nr, tw);
+    for (int i = 0; i < nr; ++i) {
+      const cpx<T>* z = Z + i * N;
+      const int64_t ob = obase + (int64_t)row_of(g, i) * a.W;
       if (a.half && !a.out_f64 && (((ob * 4 + (uintptr_t)outp) & 7) == 0)) {
         float2* o2 = (float2*)((float*)outp + ob);
         for (int m = threadIdx.x; m < (a.W >> 1); m += blockDim.x)
@@ -752,17 +843,9 @@ k_row_ifft(IRowArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
     }
     __syncthreads();
   }
+  cp_async_wait<0>();
 }
 
-// rows per CTA iteration: two row buffers + twiddles within ~72 KB
-inline int rows_per_iter(int N, int ntw, size_t ce) {
-  const long budget = 72 * 1024 / (long)ce - (long)((ntw + 1) & ~1);
-  int nb = (int)(budget / (2L * N));
-  if (nb < 1) nb = 1;
-  if (nb > 8) nb = 8;
-  while (nb > 1 && (long)nb * N > 65535) --nb;
-  return nb;
-}
 
 template <typename T>
 void run_kernel_spectra(const Plan& p, char* ws, cudaStream_t st) {
@@ -784,7 +867,7 @@ void run_row_pass_t(const Plan& p, const RowPassArgs& a, int gx, int gz, char* w
                                         sizeof(In), FOLD, FFT);
   cudaFuncSetAttribute(k_row_pass<T, In, FOLD, FFT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        (int)L.total);
-  k_row_pass<T, In, FOLD, FFT><<<dim3(gx, p.n * p.C, gz), kFftThreads, L.total, st>>>(
+  k_row_pass<T, In, FOLD, FFT><<<dim3(gx, p.n * p.C, gz), kRowPassThreads, L.total, st>>>(
       a, (const cpx<T>*)(ws + p.off_tw_w), (const cpx<T>*)(ws + p.off_stw_r));
 }
 
@@ -811,9 +894,9 @@ void run_row_pass(const Plan& p, const FrameDesc& b1, const FrameDesc& b2, char*
   a.wl = p.W1 > p.W2 ? p.W1 : p.W2;
   constexpr int E = 16 / (int)sizeof(In);
   a.rw = ((a.wl + 2 * E + E - 1) / E) * E;
-  // rows per group: the most (up to 4) that keep two blocks per SM
+  // rows per group: the most (up to 8) that keep two blocks per SM
   a.nbr = 1;
-  for (int nb = 4; nb >= 1; nb >>= 1) {
+  for (int nb = 8; nb >= 1; nb >>= 1) {
     const RowPassSmem L = row_pass_layout(a.pl.n, a.pl.ntw, a.wl, nb, a.rw, sizeof(cpx<T>),
                                           sizeof(In), fold, fft);
     if (L.total <= kRowPassSmemTarget && (!fft || (long)nb * a.pl.n <= 65535)) {
@@ -872,12 +955,19 @@ void run_row_ifft(const Plan& p, char* ws, void* latent, int out_f64, cudaStream
   a.half = p.pw_half;
   a.scale = 1.0 / ((double)p.Ph * (double)p.Pw);
   a.pl = plw;
-  a.nbr = rows_per_iter(plw.n, plw.ntw, sizeof(cpx<T>));
-  dim3 g((p.H + 2 * a.nbr - 1) / (2 * a.nbr), p.n * p.C);
-  const size_t sm = sizeof(cpx<T>) * (((plw.ntw + 1) & ~1) + 2 * (size_t)a.nbr * plw.n);
+  a.nbr = 1;
+  for (int nb = 8; nb >= 1; nb >>= 1) {
+    if (irow_layout(plw.n, plw.ntw, p.Pw2p, nb, sizeof(cpx<T>)).total <= kRowPassSmemTarget &&
+        (long)nb * plw.n <= 65535) {
+      a.nbr = nb;
+      break;
+    }
+  }
+  const size_t sm = irow_layout(plw.n, plw.ntw, p.Pw2p, a.nbr, sizeof(cpx<T>)).total;
+  dim3 g((p.H + 31) / 32, p.n * p.C);
   cudaFuncSetAttribute(k_row_ifft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_row_ifft<T><<<g, kFftThreads, sm, st>>>(a, (const cpx<T>*)(ws + p.off_tw_w),
-                                            (const cpx<T>*)(ws + p.off_stw_r));
+  k_row_ifft<T><<<g, kRowPassThreads, sm, st>>>(a, (const cpx<T>*)(ws + p.off_tw_w),
+                                                (const cpx<T>*)(ws + p.off_stw_r));
 }
 
 }  // namespace
@@ -918,7 +1008,9 @@ size_t row_pass_min_smem(const Plan& p) {
   const int wl = p.W1 > p.W2 ? p.W1 : p.W2;
   const size_t ce = p.fft_f64 ? 16 : 8;
   const int rw = ((wl + 4 + 1) / 2) * 2;   // staging pitch for 8-byte elements (the widest)
-  return row_pass_layout(pl.n, pl.ntw, wl, 1, rw, ce, 8, true, true).total;
+  const size_t fwd = row_pass_layout(pl.n, pl.ntw, wl, 1, rw, ce, 8, true, true).total;
+  const size_t inv = irow_layout(pl.n, pl.ntw, p.Pw2p, 1, ce).total;
+  return fwd > inv ? fwd : inv;
 }
 
 void launch_col_deconv(const Plan& p, char* ws, cudaStream_t st) {
