@@ -17,6 +17,9 @@
 // Zero padding is implicit: rows >= H_Bk and columns >= W_Bk are never read.
 #include "cbp_common.cuh"
 #include "cbp_internal.h"
+#ifdef CBP_PHASE_TIMING
+#include <cstdio>
+#endif
 
 namespace cbp {
 namespace {
@@ -242,42 +245,68 @@ __global__ void k_twiddles(cpx<T>* tw, int n) {
 
 // Kernel spectra K^_k[u][v], u < Ph, v < Pw2, from the double kernels:
 // kv[p][v] = sum_q K[p][q] w_Pw^{vq} (double), then K^[u][v] = sum_p kv[p][v] w_Ph^{up}.
+// Spectra of both kernels on the Ph x Pw grid (Pw/2 + 1 columns kept):
+//   K^(u, v) = sum_p w_H^(u p) R_p(v),   R_p(v) = sum_q K[p][q] w_W^(q v).
+// A block takes 32 columns of one kernel: first the t row transforms R_p(v)
+// (lane = column), then every u with lanes on consecutive columns (one
+// coalesced 256-byte row segment per warp store), UB rows at a time so that
+// each R_p(v) read serves UB outputs; the row twiddles w_H^(u p) sit in shared
+// memory and are read as broadcasts.
+constexpr int kSpecCols = 32;
+constexpr int kSpecRows = 4;
+
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads)
 k_kernel_spectra(const double* kd, int t1, int t2, int Ph, int Pw, int Pw2, int Pw2p,
                  const cpx<T>* tw_h, const cpx<T>* tw_w, cpx<T>* khat) {
-  constexpr int CW = 16;
-  __shared__ cpx<T> kv[kMaxN * CW];
+  extern __shared__ __align__(16) char smem[];
+  cpx<T>* kv = (cpx<T>*)smem;                       // [t][kSpecCols]
+  cpx<T>* twh = kv + kMaxN * kSpecCols;             // [Ph]
   const int k = blockIdx.y, f = blockIdx.z;
   const int t = k ? t2 : t1;
   const double* K = kd + (int64_t)f * (t1 * t1 + t2 * t2) + (k ? t1 * t1 : 0);
-  const int v0 = blockIdx.x * CW;
-  for (int idx = threadIdx.x; idx < t * CW; idx += blockDim.x) {
-    const int p = idx / CW, vl = idx % CW, v = v0 + vl;
-    cd acc = mk(0.0, 0.0);
+  const int v0 = blockIdx.x * kSpecCols;
+  for (int i = threadIdx.x; i < Ph; i += blockDim.x) twh[i] = tw_h[i];
+  for (int idx = threadIdx.x; idx < t * kSpecCols; idx += blockDim.x) {
+    const int p = idx / kSpecCols, vl = idx % kSpecCols, v = v0 + vl;
+    cpx<T> acc = mk<T>(0, 0);
     if (v < Pw2) {
       int e = 0;                              // (v q) mod Pw, incrementally
       for (int q = 0; q < t; ++q) {
-        acc = acc + K[p * t + q] * cvt<double>(tw_w[e]);
+        acc = acc + (T)K[p * t + q] * tw_w[e];
         e += v;
         if (e >= Pw) e -= Pw;
       }
     }
-    kv[idx] = cvt<T>(acc);
+    kv[idx] = acc;
   }
   __syncthreads();
   cpx<T>* out = khat + ((int64_t)f * 2 + k) * Ph * Pw2p;
-  for (int idx = threadIdx.x; idx < Ph * CW; idx += blockDim.x) {
-    const int u = idx / CW, vl = idx % CW, v = v0 + vl;
-    if (v >= Pw2) continue;
-    cpx<T> acc = mk<T>(0, 0);
-    int e = 0;                                // (u p) mod Ph, incrementally
-    for (int p = 0; p < t; ++p) {
-      cfma(acc, kv[p * CW + vl], tw_h[e]);
-      e += u;
-      if (e >= Ph) e -= Ph;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const int v = v0 + lane;
+  for (int u0 = warp * kSpecRows; u0 < Ph; u0 += nw * kSpecRows) {
+    cpx<T> acc[kSpecRows];
+    int e[kSpecRows], du[kSpecRows];          // (u p) mod Ph per row, incrementally
+#pragma unroll
+    for (int j = 0; j < kSpecRows; ++j) {
+      acc[j] = mk<T>(0, 0);
+      e[j] = 0;
+      du[j] = u0 + j < Ph ? u0 + j : 0;       // rows past Ph are computed as u = 0, not stored
     }
-    out[(int64_t)u * Pw2p + v] = acc;
+    for (int p = 0; p < t; ++p) {
+      const cpx<T> r = kv[p * kSpecCols + lane];
+#pragma unroll
+      for (int j = 0; j < kSpecRows; ++j) {
+        cfma(acc[j], r, twh[e[j]]);
+        e[j] += du[j];
+        if (e[j] >= Ph) e[j] -= Ph;
+      }
+    }
+    if (v < Pw2) {
+#pragma unroll
+      for (int j = 0; j < kSpecRows; ++j)
+        if (u0 + j < Ph) out[(int64_t)(u0 + j) * Pw2p + v] = acc[j];
+    }
   }
 }
 
@@ -335,8 +364,27 @@ struct RowPassArgs {
 };
 
 constexpr int kRowPassThreads = 512;
+
+// Optional per-phase cycle counts of the row pass (build with
+// -DCBP_PHASE_TIMING): thread 0 accumulates clock64 deltas between the phases
+// and one block prints them.
+#ifdef CBP_PHASE_TIMING
+#define RP_MARK(i)                                  \
+  do {                                              \
+    if (threadIdx.x == 0) {                         \
+      const long long now = clock64();              \
+      rp_t[i] += now - rp_last;                     \
+      rp_last = now;                                \
+    }                                               \
+  } while (0)
+#else
+#define RP_MARK(i) \
+  do {             \
+  } while (0)
+#endif
 constexpr int kRowWarps = kRowPassThreads / 32;
 constexpr int kColRegs = 4;          // column-fold accumulators per thread held in registers
+constexpr int kMaxRowGroup = 8;      // rows per group at most
 
 template <typename In> struct FoldAcc;
 template <> struct FoldAcc<float> { using type = TwoSum; };
@@ -387,19 +435,20 @@ __device__ __forceinline__ void stage_rows_async(In* dst, int* rph, const In* fb
                                                  int nr, int W, int rw) {
   constexpr int E = 16 / (int)sizeof(In);
   const int tasks = (E - 1) + (W + E - 1) / E;
-  for (int idx = threadIdx.x; idx < nr * tasks; idx += blockDim.x) {
-    const int i = idx / tasks, t = idx - i * tasks;
+  for (int i = 0; i < nr; ++i) {
     const In* row = fb + rowoff(i);
     const int ph = (int)(((uintptr_t)row / sizeof(In)) & (E - 1));
     const int head = ph ? min(E - ph, W) : 0;
     In* drow = dst + i * rw + ph;
-    if (t < E - 1) {                                   // head element t
-      if (t < head) cp_async_small<(int)sizeof(In)>(drow + t, row + t);
-    } else {
-      const int c0 = head + (t - (E - 1)) * E;          // chunk start element
-      if (c0 < W) cp_async16(drow + c0, row + c0, min(E, W - c0) * (int)sizeof(In));
+    for (int t = threadIdx.x; t < tasks; t += blockDim.x) {
+      if (t < E - 1) {                                 // head element t
+        if (t < head) cp_async_small<(int)sizeof(In)>(drow + t, row + t);
+      } else {
+        const int c0 = head + (t - (E - 1)) * E;        // chunk start element
+        if (c0 < W) cp_async16(drow + c0, row + c0, min(E, W - c0) * (int)sizeof(In));
+      }
     }
-    if (t == 0) rph[i] = ph;
+    if (threadIdx.x == 0) rph[i] = ph;
   }
 }
 
@@ -437,8 +486,13 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
   cp_async_commit();
   cpx<T>* spec = fft ? (cpx<T>*)a.spec[blockIdx.z] + (int64_t)fc * fr.h * a.Pw2p : nullptr;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#ifdef CBP_PHASE_TIMING
+  long long rp_t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  long long rp_last = clock64();
+#endif
   for (int g = 0; g < ngroups; ++g) {
     const int nr = min(NB, nrows - g * NB);
+    RP_MARK(7);
     if (g + 1 < ngroups) {
       const int g1 = g + 1;
       stage_rows_async<In>((g1 & 1) ? raw1 : raw0, rph + (g1 & 1) * NB, fb,
@@ -446,45 +500,56 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
                            min(NB, nrows - g1 * NB), W, a.rw);
     }
     cp_async_commit();
+    RP_MARK(0);
     cp_async_wait<1>();
     __syncthreads();
+    RP_MARK(1);
     In* const rw0 = (g & 1) ? raw1 : raw0;
     const int* ph = rph + (g & 1) * NB;
     if (FOLD) {
+      const In* rowp[kMaxRowGroup];
+#pragma unroll
+      for (int i = 0; i < kMaxRowGroup; ++i) rowp[i] = rw0 + i * a.rw + (i < nr ? ph[i] : 0);
       // column folds: this block's bin, one thread per column
       if (!L.col_smem) {
 #pragma unroll
         for (int j = 0; j < kColRegs; ++j) {
           const int c = threadIdx.x + j * kRowPassThreads;
-          if (c < W)
-            for (int i = 0; i < nr; ++i) creg[j].add(rw0[i * a.rw + ph[i] + c]);
+          if (c < W) {
+#pragma unroll
+            for (int i = 0; i < kMaxRowGroup; ++i)
+              if (i < nr) creg[j].add(rowp[i][c]);
+          }
         }
       } else {
         for (int c = threadIdx.x; c < W; c += blockDim.x) {
           Acc acc = colacc[c];
-          for (int i = 0; i < nr; ++i) acc.add(rw0[i * a.rw + ph[i] + c]);
+#pragma unroll
+          for (int i = 0; i < kMaxRowGroup; ++i)
+            if (i < nr) acc.add(rowp[i][c]);
           colacc[c] = acc;
         }
       }
-      // row folds: wpr warps per row, each over a run of whole M-column steps;
-      // lane l < gM owns bin l mod M
-      const int wpr = kRowWarps / nr;
-      if (warp < wpr * nr) {
-        const int i = warp / wpr, sg = warp - i * wpr;
-        const int gm = (32 / M) * M;
-        const int nsteps = (W + gm - 1) / gm, sps = (nsteps + wpr - 1) / wpr;
+      // row folds: task (i, sg, m) sums columns c = m mod M of row i over
+      // segment sg; nseg segments per (row, bin) fill the block
+      const int nseg = max(1, kRowPassThreads / (nr * M));
+      const int nsteps = (W + M - 1) / M, sps = (nsteps + nseg - 1) / nseg;
+      const int t = threadIdx.x;
+      if (t < nr * M * nseg) {
+        const int i = t / (M * nseg), r = t - i * (M * nseg), sg = r / M, m = r - sg * M;
         Acc acc;
-        if (lane < gm) {
-          const In* rowp = rw0 + i * a.rw + ph[i];
-          const int e = min(nsteps, (sg + 1) * sps);
-          for (int st = sg * sps; st < e; ++st) {
-            const int c = st * gm + lane;
-            if (c < W) acc.add(rowp[c]);
-          }
-        }
-        rb[warp * 32 + lane] = acc.value();
+        const In* rp = rowp[0];
+#pragma unroll
+        for (int ii = 1; ii < kMaxRowGroup; ++ii)
+          if (ii == i) rp = rowp[ii];
+        const int e = min(nsteps, (sg + 1) * sps);
+        int c = sg * sps * M + m;
+        for (int st = sg * sps; st < e; ++st, c += M)
+          if (c < W) acc.add(rp[c]);
+        rb[t] = acc.value();
       }
     }
+    RP_MARK(2);
     if (fft) {
       for (int i = 0; i < nr; ++i) {
         const In* rowp = rw0 + i * a.rw + ph[i];
@@ -515,13 +580,13 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
       }
     }
     __syncthreads();
+    RP_MARK(3);
     if (FOLD) {
-      const int wpr = kRowWarps / nr, q = 32 / M;
+      const int nseg = max(1, kRowPassThreads / (nr * M));
       for (int t = threadIdx.x; t < nr * M; t += blockDim.x) {
         const int i = t / M, m = t - i * M;
         double v = 0;
-        for (int sg = 0; sg < wpr; ++sg)
-          for (int qq = 0; qq < q; ++qq) v += rb[(i * wpr + sg) * 32 + qq * M + m];
+        for (int sg = 0; sg < nseg; ++sg) v += rb[(i * nseg + sg) * M + m];
         a.bins_r[blockIdx.z][((int64_t)fc * M + m) * fr.h + row_of(g, i)] = v;
       }
     }
@@ -530,6 +595,7 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
       // FFT's second buffer when large enough
       cpx<T>* b1 = L.b1_alias ? (cpx<T>*)rw0 : (cpx<T>*)(smem + L.b1);
       cpx<T>* Z = fft_block<T, false>(b0, b1, a.pl, nr, tw);
+      RP_MARK(4);
       for (int i = 0; i < nr; ++i) {
         const cpx<T>* z = Z + i * N;
         cpx<T>* out = spec + (int64_t)row_of(g, i) * a.Pw2p;
@@ -545,8 +611,16 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
         }
       }
     }
+    RP_MARK(5);
     __syncthreads();
+    RP_MARK(6);
   }
+#ifdef CBP_PHASE_TIMING
+  if (threadIdx.x == 0 && blockIdx.x == 1 && blockIdx.y < 2)
+    printf("row_pass fold=%d fft=%d z=%d groups=%d nb=%d | issue %lld wait %lld folds %lld convert+sync %lld "
+           "fft %lld post %lld endsync %lld loop %lld\n", (int)FOLD, (int)fft, (int)blockIdx.z,
+           ngroups, NB, rp_t[0], rp_t[1], rp_t[2], rp_t[3], rp_t[4], rp_t[5], rp_t[6], rp_t[7]);
+#endif
   cp_async_wait<0>();
   if (FOLD) {
     bool finite = true;
@@ -851,10 +925,12 @@ template <typename T>
 void run_kernel_spectra(const Plan& p, char* ws, cudaStream_t st) {
   const cpx<T>* tw_h = (const cpx<T>*)(ws + p.off_tw_h);
   const cpx<T>* tw_w = (const cpx<T>*)(ws + p.off_tw_w);
-  dim3 g((p.Pw2 + 15) / 16, 2, p.n);
-  k_kernel_spectra<T><<<g, kFftThreads, 0, st>>>((const double*)(ws + p.off_kd), p.t1, p.t2, p.Ph,
-                                                 p.Pw, p.Pw2, p.Pw2p, tw_h, tw_w,
-                                                 (cpx<T>*)(ws + p.off_khat));
+  dim3 g((p.Pw2 + kSpecCols - 1) / kSpecCols, 2, p.n);
+  const size_t sm = sizeof(cpx<T>) * ((size_t)kMaxN * kSpecCols + p.Ph);
+  cudaFuncSetAttribute(k_kernel_spectra<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_kernel_spectra<T><<<g, kFftThreads, sm, st>>>((const double*)(ws + p.off_kd), p.t1, p.t2, p.Ph,
+                                                  p.Pw, p.Pw2, p.Pw2p, tw_h, tw_w,
+                                                  (cpx<T>*)(ws + p.off_khat));
 }
 
 // Shared-memory target of the row pass: two resident blocks per SM.

@@ -508,11 +508,20 @@ __device__ EigResult smallest_eigvec(EigSmem& S, int n, bool real, int acc_steps
     for (int i = threadIdx.x; i < n; i += blockDim.x) S.x[i] = v32(S, real, ld, i, imin);
     __syncthreads();
     normalize64(S.x, n, S.red);
-    for (int it = 0; it < 12; ++it) {
+    // The steps converge linearly with a small ratio (the eigenbasis is
+    // accurate to single precision); stop once a step no longer shrinks the
+    // correction by 4x -- it has reached the double-precision floor -- or it
+    // vanishes.
+    double d2prev = 1e300;
+    int it = 0;
+    for (; it < 12; ++it) {
       matvec64(S.G, S.x, S.r, n);
       theta = dotre64(S.x, S.r, n, S.red);
-      if (newton_eigbasis64(S, V64, S.lam, n, ld, imin, S.r, theta) < 1e-30) break;
+      const double d2 = newton_eigbasis64(S, V64, S.lam, n, ld, imin, S.r, theta);
+      if (d2 < 1e-30 || d2 > 0.25 * d2prev) break;
+      d2prev = d2;
     }
+    if (threadIdx.x == 0) S.flag[3] = it + 1;
     for (int it = 0; it < acc_steps; ++it) {
       apply(S.x, S.r);
       theta = dotre64(S.x, S.r, n, S.red);
@@ -824,7 +833,10 @@ struct SylvesterApply {
 
 __global__ void __launch_bounds__(kSolveThreads) k_sample_solve(SampleArgs a) {
   extern __shared__ __align__(16) char smem[];
-  const int s = blockIdx.x, ps = blockIdx.y, f = blockIdx.z;
+  // The sample index varies slowest, so the z = 1 and neighbouring samples
+  // of every pair -- the slow ones, resolved in double precision -- start
+  // first and the short samples fill in behind them.
+  const int f = blockIdx.x, ps = blockIdx.y, s = blockIdx.z;
   const int n = a.nn;
   EigSmem S;
   char* p = carve_eig(S, smem, n);
@@ -858,10 +870,11 @@ __global__ void __launch_bounds__(kSolveThreads) k_sample_solve(SampleArgs a) {
 #ifdef CBP_PHASE_TIMING
   if (threadIdx.x == 0 && f < 2)
     printf("sample f=%d pass=%d s=%d real=%d hard=%d | corr %lld gram %lld jacobi32 %lld refine %lld "
-           "tail %lld | mgs %lld xform %lld jacobi64 %lld (%d sweeps)\n",
+           "tail %lld | mgs %lld xform %lld jacobi64 %lld (%d sweeps, %d newton)\n",
            f, ps, s, (int)real, res.hard, tk[1] - tk[0], tk[2] - tk[1], tk[3] - tk[2],
            tk[4] - tk[3], tk[5] - tk[4], res.hard ? tk[6] - tk[3] : 0LL,
-           res.hard ? tk[7] - tk[6] : 0LL, res.hard ? tk[8] - tk[7] : 0LL, S.flag[1]);
+           res.hard ? tk[7] - tk[6] : 0LL, res.hard ? tk[8] - tk[7] : 0LL, S.flag[1],
+           res.hard ? 0 : S.flag[3]);
 #endif
   const int64_t o = ((int64_t)f * 2 + ps) * a.ns + s;
   for (int i = threadIdx.x; i < n; i += blockDim.x) a.X[o * n + i] = S.x[i];
@@ -1148,7 +1161,7 @@ void launch_sample_solve(const Plan& p, char* ws, cudaStream_t st) {
   a.M = p.M;
   a.mixed = p.mixed;
   const size_t sm = sample_solve_smem(p.nn);
-  dim3 grid(p.ns, 2, p.n);
+  dim3 grid(p.n, 2, p.ns);
   cudaFuncSetAttribute(k_sample_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_sample_solve<<<grid, kSolveThreads, sm, st>>>(a);
 }
