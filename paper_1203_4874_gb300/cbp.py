@@ -319,3 +319,44 @@ def cbp_estimate_kernels_noalloc(b1: torch.Tensor, b2: torch.Tensor, prm: cbp_pa
                                            k1.data_ptr(), k2.data_ptr(), d, _stream_ptr(stream))
     _check(s, "cbp_estimate_kernels_noalloc")
     return d, s
+
+
+# ---------------------------------------------------------------- serving --
+def cbp_stream_submit(ctx, b1: torch.Tensor, b2: torch.Tensor, prm: cbp_params, k1: torch.Tensor,
+                      k2: torch.Tensor, latent: torch.Tensor | None = None) -> int:
+    """Queue one frame pair (device tensors, batch of one) with the serving
+    engine; latent None asks for the kernels only.  Every tensor must stay
+    alive until the request completes.  Returns the ticket."""
+    if _batch(b1) != 1 or _batch(b2) != 1:
+        raise ValueError("a serving request is one frame pair")
+    if prm.flags & CBP_FLAG_HOST_IO:
+        raise ValueError("the serving engine takes device tensors")
+    v1 = b1
+    while v1.dim() < 4:
+        v1 = v1.unsqueeze(0)
+    _, c, h1, w1 = v1.shape
+    kdt = torch.float64 if prm.flags & CBP_FLAG_KERNELS_F64 else b1.dtype
+    _out(k1, (1, prm.t1, prm.t1), kdt, b1.device, "k1")
+    _out(k2, (1, prm.t2, prm.t2), kdt, b1.device, "k2")
+    if latent is not None:
+        _out(latent, (1, c, h1 - prm.t1 + 1, w1 - prm.t1 + 1), b1.dtype, b1.device, "latent")
+    t = c_uint64()
+    s = lib().cbp_stream_submit(ctx, byref(frames(b1)), byref(frames(b2)), byref(prm), k1.data_ptr(),
+                                k2.data_ptr(), latent.data_ptr() if latent is not None else None,
+                                byref(t))
+    _check(s, "cbp_stream_submit")
+    return t.value
+
+
+def cbp_stream_poll(ctx, ticket: int, timeout_us: int = -1):
+    """(status, diag) of a ticket: the request's status once done (the ticket
+    is then released), CBP_ERR_BUSY / CBP_ERR_TIMEOUT while it is not."""
+    d = cbp_diag()
+    s = lib().cbp_stream_poll(ctx, ticket, int(timeout_us), byref(d))
+    return s, d
+
+
+def cbp_stream_stats(ctx, reset: bool = False) -> dict:
+    n, p50, p99 = c_uint64(), c_double(), c_double()
+    _check(lib().cbp_stream_stats(ctx, byref(n), byref(p50), byref(p99), int(reset)), "cbp_stream_stats")
+    return {"completed": n.value, "p50_ms": p50.value, "p99_ms": p99.value}

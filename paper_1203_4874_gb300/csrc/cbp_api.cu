@@ -123,9 +123,10 @@ cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
   }
   cudaMemsetAsync(wsp + p.off_bad, 0, (size_t)p.n * sizeof(int), st);
   if (kin) {
-    if (!k1d || !k2d) return CBP_ERR_INVALID_ARG;
+    if ((!k1d || !k2d) && !(tabs && tabs->k1 && tabs->k2)) return CBP_ERR_INVALID_ARG;
     begin(CBP_STAGE_SCALE_SOLVE);
-    launch_kernels_in(p, wsp, k1d, k2d, kf64, st);
+    launch_kernels_in(p, wsp, k1d, k2d, kf64, st, tabs ? tabs->k1 : nullptr,
+                      tabs ? tabs->k2 : nullptr);
     end(CBP_STAGE_SCALE_SOLVE, 1);
   }
   if (deblur) {

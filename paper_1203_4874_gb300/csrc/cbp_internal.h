@@ -104,7 +104,8 @@ void launch_scale_solve(const Plan& p, char* ws, void* k1_out, void* k2_out, int
                         const uint64_t* k2_tab = nullptr);
 // load caller kernels into the internal double buffer (CBP_FLAG_KERNELS_IN)
 void launch_kernels_in(const Plan& p, char* ws, const void* k1, const void* k2, int in_f64,
-                       cudaStream_t st);
+                       cudaStream_t st, const uint64_t* k1_tab = nullptr,
+                       const uint64_t* k2_tab = nullptr);
 // A6: deconvolution (cbp_fft.cu)
 void init_twiddles(const Plan& p, char* ws, cudaStream_t st);
 void launch_kernel_spectra(const Plan& p, char* ws, cudaStream_t st);

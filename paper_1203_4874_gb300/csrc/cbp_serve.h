@@ -10,6 +10,9 @@ namespace cbp {
 
 struct ServeState;  // defined in cbp_serve.cu
 
+// Request flags the serving engine does not take (it works on device buffers).
+constexpr int kServeRejectFlags = CBP_FLAG_HOST_IO;
+
 // Stage timing: events recorded around each stage of the synchronous API.
 struct Prof {
   struct Rec { int stage; cudaEvent_t a, b; };

@@ -1113,14 +1113,19 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
 }
 
 __global__ void k_kernels_in(const void* k1, const void* k2, int in_f64, int n, int t1, int t2,
-                             double* kd, cbp_diag* diag, int Ph, int Pw, const int* bad) {
+                             double* kd, cbp_diag* diag, int Ph, int Pw, const int* bad,
+                             const uint64_t* k1_tab, const uint64_t* k2_tab) {
   const int per = t1 * t1 + t2 * t2;
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < (int64_t)n * per;
        i += (int64_t)gridDim.x * blockDim.x) {
     const int f = (int)(i / per), e = (int)(i % per);
-    double v;
-    if (e < t1 * t1) v = in_f64 ? ((const double*)k1)[(int64_t)f * t1 * t1 + e] : ((const float*)k1)[(int64_t)f * t1 * t1 + e];
-    else v = in_f64 ? ((const double*)k2)[(int64_t)f * t2 * t2 + e - t1 * t1] : ((const float*)k2)[(int64_t)f * t2 * t2 + e - t1 * t1];
+    // kernel k of pair f: from the table if given, else the contiguous batch
+    const bool second = e >= t1 * t1;
+    const int tk = second ? t2 : t1, ek = second ? e - t1 * t1 : e;
+    const uint64_t* tab = second ? k2_tab : k1_tab;
+    const void* base = tab ? (const void*)tab[f] : (second ? k2 : k1);
+    const int64_t o = tab ? ek : (int64_t)f * tk * tk + ek;
+    const double v = in_f64 ? ((const double*)base)[o] : (double)((const float*)base)[o];
     kd[i] = v;
     if (e == 0) {
       cbp_diag d = {};
@@ -1194,13 +1199,13 @@ void launch_scale_solve(const Plan& p, char* ws, void* k1_out, void* k2_out, int
 }
 
 void launch_kernels_in(const Plan& p, char* ws, const void* k1, const void* k2, int in_f64,
-                       cudaStream_t st) {
+                       cudaStream_t st, const uint64_t* k1_tab, const uint64_t* k2_tab) {
   const int64_t total = (int64_t)p.n * (p.t1 * p.t1 + p.t2 * p.t2);
   int blocks = (int)((total + 255) / 256);
   if (blocks > 4096) blocks = 4096;
   k_kernels_in<<<blocks, 256, 0, st>>>(k1, k2, in_f64, p.n, p.t1, p.t2, (double*)(ws + p.off_kd),
                                        (cbp_diag*)(ws + p.off_diag), p.Ph, p.Pw,
-                                       (const int*)(ws + p.off_bad));
+                                       (const int*)(ws + p.off_bad), k1_tab, k2_tab);
 }
 
 }  // namespace cbp
