@@ -173,6 +173,113 @@ def make_inputs(ctx, n: int, seed0: int, device):
     return b1, b2, k1, k2
 
 
+# ------------------------------------------------------------- serving ---
+SERVE_RES = [(240, 320), (480, 640), (720, 1280), (1080, 1920)]
+SERVE_SIZES = [7, 9, 11, 13, 15, 17]
+
+
+def serving_bench(seconds: float, device, seed: int = 5150, cameras: int = 16, rate: float = 30.0,
+                  pool: int = 4, budget_gb: float = 150.0):
+    """Camera workload through the serving engine: `cameras` cameras, each with
+    a resolution from SERVE_RES and odd kernel sizes in 7..17 drawn once, new
+    kernels per frame (a pool of `pool` synthetic pairs per camera), Poisson
+    arrivals at `rate` pairs/s per camera, grayscale f32, noise sigma 1e-3.
+    One second of the same traffic warms the engine (graph captures) first."""
+    import threading
+    import numpy as np
+    import torch
+    from cbp_synth.generators import _rng, blob_params, draw_kernel_pair
+    from paper_1203_4874_gb300 import cbp
+
+    ctx = cbp.cbp_create(device.index or 0, int(budget_gb * 2**30))
+    rng = _rng(seed)
+    cams = []
+    for cam in range(cameras):
+        h, w = SERVE_RES[int(rng.integers(len(SERVE_RES)))]
+        t1 = SERVE_SIZES[int(rng.integers(len(SERVE_SIZES)))]
+        t2 = SERVE_SIZES[int(rng.integers(len(SERVE_SIZES)))]
+        pairs = []
+        for f in range(pool):
+            r = _rng(seed * 1000 + cam * pool + f)
+            a, b = draw_kernel_pair(r, t1, t2, max(t1, t2), "mixture")
+            bl = torch.from_numpy(blob_params(r, h, w)[None, None]).to(device)
+            lat = cbp.cbp_synth_latent(ctx, bl, 1, 1, h, w, torch.float32, 0.05, seed + cam * pool + f)
+            k1 = torch.from_numpy(a[None]).to(device)
+            k2 = torch.from_numpy(b[None]).to(device)
+            b1 = cbp.cbp_forward_blur(ctx, lat, k1, SIGMA, 2 * (cam * pool + f) + 1)
+            b2 = cbp.cbp_forward_blur(ctx, lat, k2, SIGMA, 2 * (cam * pool + f) + 2)
+            pairs.append((b1, b2))
+        prm = cbp.params(t1, t2, path="mixed", eps=EPS)
+        cams.append({"h": h, "w": w, "t1": t1, "t2": t2, "pairs": pairs, "prm": prm})
+    torch.cuda.synchronize()
+
+    def trace(duration, seed_arr):
+        r = np.random.default_rng(seed_arr)
+        ev = []
+        for cam in range(cameras):
+            t = r.exponential(1.0 / rate)
+            while t < duration:
+                ev.append((t, cam))
+                t += r.exponential(1.0 / rate)
+        return sorted(ev)
+
+    def run(events):
+        outq, done, lock = [], threading.Event(), threading.Lock()
+        statuses = []
+
+        def poller():
+            i = 0
+            while True:
+                with lock:
+                    item = outq[i] if i < len(outq) else None
+                if item is None:
+                    if done.is_set():
+                        with lock:
+                            if i >= len(outq):
+                                return
+                    time.sleep(0.0002)
+                    continue
+                s, _ = cbp.cbp_stream_poll(ctx, item[0], -1)
+                statuses.append(s)
+                with lock:
+                    outq[i] = None          # the request's buffers may go
+                i += 1
+
+        th = threading.Thread(target=poller)
+        th.start()
+        t0 = time.perf_counter()
+        count = [0] * cameras
+        for t, cam in events:
+            c = cams[cam]
+            b1, b2 = c["pairs"][count[cam] % pool]
+            count[cam] += 1
+            k1 = torch.empty((1, c["t1"], c["t1"]), dtype=torch.float32, device=device)
+            k2 = torch.empty((1, c["t2"], c["t2"]), dtype=torch.float32, device=device)
+            lat = torch.empty((1, 1, c["h"], c["w"]), dtype=torch.float32, device=device)
+            while time.perf_counter() - t0 < t:
+                pass
+            tk = cbp.cbp_stream_submit(ctx, b1, b2, c["prm"], k1, k2, lat)
+            with lock:
+                outq.append((tk, k1, k2, lat))
+        done.set()
+        th.join()
+        return time.perf_counter() - t0, statuses
+
+    run(trace(1.0, seed + 1))
+    cbp.cbp_stream_stats(ctx, reset=True)
+    events = trace(seconds, seed + 2)
+    wall, statuses = run(events)
+    st = cbp.cbp_stream_stats(ctx)
+    cbp.cbp_destroy(ctx)
+    ok = sum(1 for s in statuses if s >= 0)
+    return {"workload": f"{cameras} cameras, resolutions {SERVE_RES}, odd kernel sizes 7..17, new kernels "
+                        f"per frame, Poisson {rate:g} pairs/s per camera, grayscale f32, noise sigma 1e-3, "
+                        f"mixed path, budget {budget_gb:g} GB",
+            "seconds": seconds, "requests": len(events), "ok": ok, "value": ok / wall,
+            "unit": "frame-pairs/s", "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+            "cameras": [{"h": c["h"], "w": c["w"], "t1": c["t1"], "t2": c["t2"]} for c in cams]}
+
+
 # ------------------------------------------------------- CPU oracle sample --
 def cpu_worker(pairs: int):
     """Time the FP64 oracle on `pairs` pairs of the workload (host cores)."""
@@ -263,6 +370,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--serve-seconds", type=float, default=6.0,
+                    help="seconds of the camera serving trace (0: skip)")
     ap.add_argument("--cpu-worker", type=int, default=0)
     args = ap.parse_args()
     if args.cpu_worker:
@@ -399,6 +508,8 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches, "clocks": clk,
     }
+    if rank == 0 and args.serve_seconds > 0:
+        result["serving"] = serving_bench(args.serve_seconds, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(args.cpu_pairs)
     cbp.cbp_destroy(ctx)
