@@ -260,7 +260,9 @@ typedef enum cbp_stage {
   CBP_STAGE_ROW_IFFT = 6,       /* inverse row FFTs, crop, scale                  */
   CBP_STAGE_H2D = 7,            /* host-to-device copies (CBP_FLAG_HOST_IO)       */
   CBP_STAGE_D2H = 8,            /* device-to-host copies (CBP_FLAG_HOST_IO)       */
-  CBP_NUM_STAGES = 9
+  CBP_STAGE_PROPOSAL = 9,       /* learned path: network proposal                */
+  CBP_STAGE_GATE = 10,          /* learned path: proposal spectra + residual gate */
+  CBP_NUM_STAGES = 11
 } cbp_stage;
 
 cbp_status cbp_profile(cbp_ctx* ctx, int32_t enable);
@@ -288,6 +290,58 @@ cbp_status cbp_stream_poll(cbp_ctx* ctx, uint64_t ticket, int32_t timeout_us, cb
  * completion) since the last reset; reset when `reset` != 0. */
 cbp_status cbp_stream_stats(cbp_ctx* ctx, uint64_t* completed, double* p50_ms,
                             double* p99_ms, int32_t reset);
+
+/* --- learned kernel proposal (CBP_PATH_LEARNED) --------------------------
+ * A small network proposes both kernels from the two blurred frames (an
+ * addition to the paper, whose kernels come only from the GCD solve of
+ * Sections 4-5): the luma (channel mean) of each frame, area-downsampled to
+ * 256 x 256, then conv 3x3 stride 2 pad 1 (2 -> 32) + ReLU, conv 3x3 stride 2
+ * pad 1 (32 -> 32) + ReLU, conv 3x3 stride 4 pad 1 (32 -> 32) + ReLU,
+ * conv 2x2 (32 -> 2), softmax over each channel's 15 x 15 logits: K1, K2.
+ * Activations bfloat16, weights and accumulation float32.  A weight vector is
+ * cbp_cnn_param_count() floats: w1 [32][2][3][3], b1 [32], w2 [32][32][3][3],
+ * b2 [32], w3 [32][32][3][3], b3 [32], w4 [2][32][2][2], b4 [2].
+ *
+ * With params->path == CBP_PATH_LEARNED (t1 == t2 == 15, weights loaded by
+ * cbp_learned_load) cbp_deblur_pair runs the network, computes the
+ * consistency residual rho = ||B1*K2 - B2*K1|| / ||B1|| of the proposal
+ * (circular convolutions on the deconvolution grid, via Parseval) and keeps
+ * the proposal where rho <= accept_rho; the other pairs take the mixed
+ * GCD solve.  diag.rho and diag.used_fallback report the decision. */
+typedef struct cbp_cnn_trace {   /* optional device float32 copies; NULL skips */
+  float* input;    /* [n][2][256][256] network input                          */
+  float* act[3];   /* [n][32][128][128], [n][32][64][64], [n][32][16][16]     */
+  float* logits;   /* [n][2][15][15]                                          */
+  float* grad;     /* [param count] batch-loss gradient (training step only)   */
+} cbp_cnn_trace;
+
+typedef struct cbp_adamw {
+  float lr, beta1, beta2, eps, weight_decay;  /* decoupled weight decay      */
+  int32_t step;                                 /* 1 for the first step       */
+} cbp_adamw;
+
+size_t cbp_cnn_param_count(void);
+
+/* Proposals for n pairs: kernels = device float32 [n][2][15][15] (K1, K2).
+ * weights: device float32 vector, or NULL for the context's loaded weights.
+ * Frames as for cbp_estimate_kernels (any size; both of one dtype).  Async. */
+cbp_status cbp_cnn_forward(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
+                           const float* weights, float* kernels, cbp_cnn_trace* trace,
+                           void* stream);
+
+/* One training step on n pairs: loss = mean over pairs and entries of
+ * (K - k_true)^2, k_true device float32 [n][2][15][15]; backward pass, then
+ * AdamW on the device float32 weights with moments adam_m, adam_v (same
+ * length, zero before the first step).  loss: device float32 [1] or NULL. */
+cbp_status cbp_cnn_train_step(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
+                              const float* k_true, float* weights, float* adam_m, float* adam_v,
+                              const cbp_adamw* hp, float* loss, cbp_cnn_trace* trace,
+                              void* stream);
+
+/* Load weights for CBP_PATH_LEARNED from a file: 8 bytes "CBPCNN1\0", int32
+ * side (256), int32 count (cbp_cnn_param_count()), count float32 values,
+ * little-endian.  Synchronous. */
+cbp_status cbp_learned_load(cbp_ctx* ctx, const char* weights_path);
 
 #ifdef __cplusplus
 }

@@ -28,10 +28,11 @@ EXPORTED = [
     "cbp_create", "cbp_destroy", "cbp_status_string", "cbp_workspace_size",
     "cbp_estimate_kernels", "cbp_deblur_pair", "cbp_forward_blur", "cbp_synth_latent",
     "cbp_stream_submit", "cbp_stream_poll", "cbp_stream_stats", "cbp_profile", "cbp_stage_times",
-    "cbp_estimate_kernels_stages", "cbp_estimate_kernels_noalloc",
+    "cbp_estimate_kernels_stages", "cbp_estimate_kernels_noalloc", "cbp_cnn_param_count",
+    "cbp_cnn_forward", "cbp_cnn_train_step", "cbp_learned_load",
 ]
 STAGES = ["eval", "sample_solve", "scale_solve", "kernel_spectra", "row_fft", "col_deconv",
-          "row_ifft", "h2d", "d2h"]
+          "row_ifft", "h2d", "d2h", "proposal", "gate"]
 
 
 class cbp_frames(ctypes.Structure):
@@ -49,6 +50,15 @@ class cbp_params(ctypes.Structure):
 class cbp_stage_out(ctypes.Structure):
     _fields_ = [("p_z2", c_void_p * 2), ("p_z1", c_void_p * 2), ("x_z2", c_void_p), ("x_z1", c_void_p),
                 ("sample_diag", c_void_p), ("lifted", c_void_p), ("kernels", c_void_p)]
+
+
+class cbp_cnn_trace(ctypes.Structure):
+    _fields_ = [("input", c_void_p), ("act", c_void_p * 3), ("logits", c_void_p), ("grad", c_void_p)]
+
+
+class cbp_adamw(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("weight_decay", ctypes.c_float), ("step", c_int32)]
 
 
 class cbp_diag(ctypes.Structure):
@@ -94,6 +104,12 @@ def lib() -> ctypes.CDLL:
             "cbp_estimate_kernels_stages": ([c_void_p, fr, fr, pr, c_void_p, c_void_p, dg,
                                              POINTER(cbp_stage_out), c_void_p], c_int),
             "cbp_stage_times": ([c_void_p, POINTER(c_double), POINTER(c_int64)], c_int),
+            "cbp_cnn_param_count": ([], ctypes.c_size_t),
+            "cbp_cnn_forward": ([c_void_p, fr, fr, c_void_p, c_void_p, POINTER(cbp_cnn_trace), c_void_p],
+                                c_int),
+            "cbp_cnn_train_step": ([c_void_p, fr, fr, c_void_p, c_void_p, c_void_p, c_void_p,
+                                    POINTER(cbp_adamw), c_void_p, POINTER(cbp_cnn_trace), c_void_p], c_int),
+            "cbp_learned_load": ([c_void_p, ctypes.c_char_p], c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -360,3 +376,82 @@ def cbp_stream_stats(ctx, reset: bool = False) -> dict:
     n, p50, p99 = c_uint64(), c_double(), c_double()
     _check(lib().cbp_stream_stats(ctx, byref(n), byref(p50), byref(p99), int(reset)), "cbp_stream_stats")
     return {"completed": n.value, "p50_ms": p50.value, "p99_ms": p99.value}
+
+
+# ------------------------------------------------------ learned proposal --
+CNN_SIDE, CNN_T = 256, 15
+
+
+def cbp_cnn_param_count() -> int:
+    return int(lib().cbp_cnn_param_count())
+
+
+def _trace(trace: dict | None):
+    if not trace:
+        return None
+    t = cbp_cnn_trace()
+    t.input = trace["input"].data_ptr() if trace.get("input") is not None else None
+    for i, a in enumerate(trace.get("act", [None] * 3)):
+        t.act[i] = a.data_ptr() if a is not None else None
+    t.logits = trace["logits"].data_ptr() if trace.get("logits") is not None else None
+    t.grad = trace["grad"].data_ptr() if trace.get("grad") is not None else None
+    return byref(t)
+
+
+def cnn_trace_buffers(n: int, device, grad: bool = False) -> dict:
+    f = dict(dtype=torch.float32, device=device)
+    tr = {"input": torch.empty((n, 2, CNN_SIDE, CNN_SIDE), **f),
+          "act": [torch.empty((n, 32, CNN_SIDE // 2, CNN_SIDE // 2), **f),
+                  torch.empty((n, 32, CNN_SIDE // 4, CNN_SIDE // 4), **f),
+                  torch.empty((n, 32, CNN_SIDE // 16, CNN_SIDE // 16), **f)],
+          "logits": torch.empty((n, 2, CNN_T, CNN_T), **f)}
+    if grad:
+        tr["grad"] = torch.empty(cbp_cnn_param_count(), **f)
+    return tr
+
+
+def cbp_cnn_forward(ctx, b1: torch.Tensor, b2: torch.Tensor, weights: torch.Tensor | None = None,
+                    trace: dict | None = None, stream=None) -> torch.Tensor:
+    """Proposed kernels [n][2][15][15] (float32) for n pairs."""
+    n = _batch(b1)
+    k = torch.empty((n, 2, CNN_T, CNN_T), dtype=torch.float32, device=b1.device)
+    if weights is not None:
+        _out(weights, (cbp_cnn_param_count(),), torch.float32, b1.device, "weights")
+    s = lib().cbp_cnn_forward(ctx, byref(frames(b1)), byref(frames(b2)),
+                              weights.data_ptr() if weights is not None else None, k.data_ptr(),
+                              _trace(trace), _stream_ptr(stream))
+    _check(s, "cbp_cnn_forward")
+    return k
+
+
+def cbp_cnn_train_step(ctx, b1, b2, k_true: torch.Tensor, weights: torch.Tensor, m: torch.Tensor,
+                       v: torch.Tensor, step: int, lr: float, beta1: float = 0.9, beta2: float = 0.999,
+                       eps: float = 1e-8, weight_decay: float = 1e-4, loss: torch.Tensor | None = None,
+                       trace: dict | None = None, stream=None) -> None:
+    n = _batch(b1)
+    P = cbp_cnn_param_count()
+    for t, nm in ((weights, "weights"), (m, "adam_m"), (v, "adam_v")):
+        _out(t, (P,), torch.float32, b1.device, nm)
+    _out(k_true, (n, 2, CNN_T, CNN_T), torch.float32, b1.device, "k_true")
+    hp = cbp_adamw(lr, beta1, beta2, eps, weight_decay, step)
+    s = lib().cbp_cnn_train_step(ctx, byref(frames(b1)), byref(frames(b2)), k_true.data_ptr(),
+                                 weights.data_ptr(), m.data_ptr(), v.data_ptr(), byref(hp),
+                                 loss.data_ptr() if loss is not None else None, _trace(trace),
+                                 _stream_ptr(stream))
+    _check(s, "cbp_cnn_train_step")
+
+
+def save_cnn_weights(path, weights) -> None:
+    """Write a weight vector in the file format cbp_learned_load reads."""
+    import numpy as np
+    w = np.asarray(weights.detach().cpu() if hasattr(weights, "detach") else weights, dtype="<f4")
+    if w.size != cbp_cnn_param_count():
+        raise ValueError("wrong number of weights")
+    with open(path, "wb") as f:
+        f.write(b"CBPCNN1\0")
+        f.write(np.array([CNN_SIDE, w.size], dtype="<i4").tobytes())
+        f.write(w.tobytes())
+
+
+def cbp_learned_load(ctx, path) -> None:
+    _check(lib().cbp_learned_load(ctx, str(path).encode()), "cbp_learned_load")

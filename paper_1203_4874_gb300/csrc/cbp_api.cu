@@ -64,10 +64,30 @@ cbp_status Ctx::ensure_ws(size_t bytes, cudaStream_t st) {
   return CBP_OK;
 }
 
+// Grow the standalone network calls' workspace (stream-ordered on `st`).
+cbp_status Ctx::ensure_cnn_ws(size_t bytes, cudaStream_t st) {
+  if (bytes <= cnn_ws_size) return CBP_OK;
+  if (!reserve(bytes)) return CBP_ERR_BUDGET;
+  void* p = nullptr;
+  if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    release(bytes);
+    return CBP_ERR_OOM;
+  }
+  if (cnn_ws) {
+    cudaFreeAsync(cnn_ws, st);
+    release(cnn_ws_size);
+  }
+  cnn_ws = (char*)p;
+  cnn_ws_size = bytes;
+  return CBP_OK;
+}
+
 // Enqueue the whole path of one plan on `st` with workspace `wsp`.
 cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
                     const cbp_params* prm, void* k1, void* k2, void* latent, bool deblur,
-                    char* wsp, cudaStream_t st, Prof* prof, const PtrTables* tabs) {
+                    char* wsp, cudaStream_t st, Prof* prof, const PtrTables* tabs,
+                    const float* cnn_w) {
   cudaEvent_t ev = nullptr;
   auto begin = [&](int stage) {
     if (prof) prof->begin(stage, st, &ev);
@@ -129,7 +149,16 @@ cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
                       tabs ? tabs->k2 : nullptr);
     end(CBP_STAGE_SCALE_SOLVE, 1);
   }
-  if (deblur) {
+  if (p.learned && !cnn_w) return CBP_ERR_INVALID_ARG;   // no weights loaded
+  const bool fft = deblur || p.learned;
+  if (p.learned) {
+    // learned path: the network's proposal, written where the estimate goes
+    begin(CBP_STAGE_PROPOSAL);
+    cnn_forward(d1, d2, p.n, cnn_w, wsp + p.off_cnn, st);
+    cnn_to_kd(wsp + p.off_cnn, p.n, (double*)(wsp + p.off_kd), st);
+    end(CBP_STAGE_PROPOSAL, 7);
+  }
+  if (fft) {
     begin(CBP_STAGE_KERNEL_SPECTRA);   // FFT twiddle tables
     init_twiddles(p, wsp, st);
     end(CBP_STAGE_KERNEL_SPECTRA, 4);
@@ -138,11 +167,18 @@ cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
     launch_row_pass(p, d1, d2, wsp, st, !kin, true);
     end(CBP_STAGE_ROW_FFT, 1);
   }
+  if (p.learned) {
+    // consistency residual of the proposal; accepted pairs skip the solves
+    begin(CBP_STAGE_GATE);
+    launch_kernel_spectra(p, wsp, st);
+    launch_residual_gate(p, wsp, st);
+    end(CBP_STAGE_GATE, 3);
+  }
   if (!kin) {
     begin(CBP_STAGE_EVAL);
-    if (deblur) launch_fold_dft(p, wsp, st);
+    if (fft) launch_fold_dft(p, wsp, st);
     else launch_eval(p, d1, d2, wsp, st);
-    end(CBP_STAGE_EVAL, deblur ? 1 : 2);
+    end(CBP_STAGE_EVAL, fft ? 1 : 2);
     begin(CBP_STAGE_SAMPLE_SOLVE);
     launch_sample_solve(p, wsp, st);
     end(CBP_STAGE_SAMPLE_SOLVE, 1);
@@ -246,7 +282,7 @@ cbp_status call_path(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
   s = c->ensure_ws(p.total, st);
   if (s != CBP_OK) return s;
   s = cbp::run_plan(p, b1, b2, prm, k1, k2, latent, deblur, c->ws, st,
-                    c->profiling ? &c->prof : nullptr);
+                    c->profiling ? &c->prof : nullptr, nullptr, c->cnn_w);
   if (s != CBP_OK) return s;
   s = copy_stages(p, c->ws, stages, st);
   if (s != CBP_OK) return s;
@@ -287,6 +323,8 @@ cbp_status cbp_destroy(cbp_ctx* ctx) {
   cbp::serve_shutdown(c);
   cudaDeviceSynchronize();
   if (c->ws) cudaFree(c->ws);
+  if (c->cnn_ws) cudaFree(c->cnn_ws);
+  if (c->cnn_w) cudaFree(c->cnn_w);
   delete c;
   return CBP_OK;
 }

@@ -653,8 +653,9 @@ struct ColArgs {
   const void* khat;   // cpx<T> [n][2][Ph][Pw2p]
   void* ihat;         // cpx<T> [n][C][H][Pw2p]
   const void* stw;    // stage twiddles of the Ph plan (read through L1)
-  int H1, H2, H, C, Ph, Pw2, Pw2p, single;
+  int H1, H2, H, C, Ph, Pw, Pw2, Pw2p, single;
   double eps;
+  double* rpart;      // residual mode: [n][C][strips][2] partial sums
   FftPlan pl;         // plan of Ph
 };
 
@@ -729,7 +730,13 @@ __device__ __forceinline__ void load_strip_async(cpx<T>* dst, const cpx<T>* src,
 // Column FFTs of both spectra, dual-kernel formula, inverse column FFT.  Both
 // frames' strips are fetched asynchronously up front; the second arrives
 // while the first is transformed.  Three interleaved buffers of CW columns.
-template <typename T, int CW>
+//
+// Residual mode (RESID, learned path): instead of deconvolving, the strip's
+// part of the consistency residual of the kernels in khat,
+//   sum |K2^ B1^ - K1^ B2^|^2 and sum |B1^|^2  over the strip's (u, v),
+// each half-spectrum column counted twice except v = 0 and v = Pw/2 (its own
+// mirror); by Parseval their ratio is rho^2 of the circular convolutions.
+template <typename T, int CW, bool RESID>
 __global__ void __launch_bounds__(kColThreads, 2)
 k_col_deconv(ColArgs a) {
   extern __shared__ __align__(16) char smem[];
@@ -761,6 +768,37 @@ k_col_deconv(ColArgs a) {
   }
   const cpx<T>* K1 = (const cpx<T>*)a.khat + ((int64_t)f * 2 + 0) * Ph * a.Pw2p + v0;
   const cpx<T>* K2 = (const cpx<T>*)a.khat + ((int64_t)f * 2 + 1) * Ph * a.Pw2p + v0;
+  if (RESID) {
+    double num = 0.0, den = 0.0;
+    for (int idx = threadIdx.x; idx < CW * Ph; idx += blockDim.x) {
+      const int u = idx / CW, vl = idx % CW, v = v0 + vl;
+      if (vl >= nv) continue;
+      const double wv = (v == 0 || 2 * v == a.Pw) ? 1.0 : 2.0;
+      const cpx<T> k1 = K1[(int64_t)u * a.Pw2p + vl], k2 = K2[(int64_t)u * a.Pw2p + vl];
+      const cpx<T> r = k2 * r1[idx] - k1 * r2[idx];
+      num += wv * (double)abs2(r);
+      den += wv * (double)abs2(r1[idx]);
+    }
+    __shared__ double red[2][kColThreads / 32];
+    num = warp_sum(num);
+    den = warp_sum(den);
+    if ((threadIdx.x & 31) == 0) {
+      red[0][threadIdx.x >> 5] = num;
+      red[1][threadIdx.x >> 5] = den;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sn = 0.0, sd = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        sn += red[0][w];
+        sd += red[1][w];
+      }
+      double* o = a.rpart + ((int64_t)fc * gridDim.x + blockIdx.x) * 2;
+      o[0] = sn;
+      o[1] = sd;
+    }
+    return;
+  }
   const T eps = (T)a.eps;
   for (int idx = threadIdx.x; idx < CW * Ph; idx += blockDim.x) {
     const int u = idx / CW, vl = idx % CW;
@@ -988,7 +1026,7 @@ void run_row_pass(const Plan& p, const FrameDesc& b1, const FrameDesc& b2, char*
   else run_row_pass_t<float, In, true, false>(p, a, gx, gz, ws, st);
 }
 
-template <typename T>
+template <typename T, bool RESID>
 void run_col_deconv(const Plan& p, char* ws, cudaStream_t st) {
   ColArgs a;
   a.spec[0] = ws + p.off_spec[0];
@@ -1001,16 +1039,37 @@ void run_col_deconv(const Plan& p, char* ws, cudaStream_t st) {
   a.H = p.H;
   a.C = p.C;
   a.Ph = p.Ph;
+  a.Pw = p.Pw;
   a.Pw2 = p.Pw2;
   a.Pw2p = p.Pw2p;
-  a.single = p.single_kernel;
+  a.single = RESID ? 0 : p.single_kernel;
   a.eps = p.eps;
+  a.rpart = RESID ? (double*)(ws + p.off_rpart) : nullptr;
   a.pl = p.fp_h;
   constexpr int CW = sizeof(T) == 4 ? 4 : 2;
   dim3 g((p.Pw2 + CW - 1) / CW, p.n * p.C);
   const size_t sm = sizeof(cpx<T>) * 3 * (size_t)CW * p.Ph;
-  cudaFuncSetAttribute(k_col_deconv<T, CW>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_col_deconv<T, CW><<<g, kColThreads, sm, st>>>(a);
+  cudaFuncSetAttribute(k_col_deconv<T, CW, RESID>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)sm);
+  k_col_deconv<T, CW, RESID><<<g, kColThreads, sm, st>>>(a);
+}
+
+// Learned path: rho and the accept flag of every pair from the partial sums
+// (fixed summation order).
+__global__ void k_gate(const double* rpart, int n, int C, int strips, double accept_rho, int* acc,
+                       double* rho) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n) return;
+  double num = 0.0, den = 0.0;
+  for (int ch = 0; ch < C; ++ch)
+    for (int s = 0; s < strips; ++s) {
+      const double* o = rpart + (((int64_t)f * C + ch) * strips + s) * 2;
+      num += o[0];
+      den += o[1];
+    }
+  const double r = den > 0.0 ? sqrt(num / den) : INFINITY;
+  rho[f] = r;
+  acc[f] = r <= accept_rho ? 1 : 0;
 }
 
 template <typename T>
@@ -1090,14 +1149,22 @@ size_t row_pass_min_smem(const Plan& p) {
 }
 
 void launch_col_deconv(const Plan& p, char* ws, cudaStream_t st) {
-  if (p.fft_f64) run_col_deconv<double>(p, ws, st);
-  else run_col_deconv<float>(p, ws, st);
+  if (p.fft_f64) run_col_deconv<double, false>(p, ws, st);
+  else run_col_deconv<float, false>(p, ws, st);
 }
 
 void launch_row_ifft(const Plan& p, char* ws, void* latent, int out_f64, cudaStream_t st,
                      const uint64_t* lat_tab) {
   if (p.fft_f64) run_row_ifft<double>(p, ws, latent, out_f64, st, lat_tab);
   else run_row_ifft<float>(p, ws, latent, out_f64, st, lat_tab);
+}
+
+void launch_residual_gate(const Plan& p, char* ws, cudaStream_t st) {
+  if (p.fft_f64) run_col_deconv<double, true>(p, ws, st);
+  else run_col_deconv<float, true>(p, ws, st);
+  k_gate<<<(p.n + 127) / 128, 128, 0, st>>>((const double*)(ws + p.off_rpart), p.n, p.C, p.col_strips,
+                                            p.accept_rho, (int*)(ws + p.off_acc),
+                                            (double*)(ws + p.off_rho));
 }
 
 }  // namespace cbp

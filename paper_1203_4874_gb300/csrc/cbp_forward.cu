@@ -40,6 +40,23 @@ __device__ __forceinline__ double normal_at(uint64_t seed, uint64_t idx, uint32_
   return sqrt(-2.0 * log(u1)) * cospi(2.0 * u2);
 }
 
+// The same normal number in single precision (float frames).
+__device__ __forceinline__ float normal_at_f(uint64_t seed, uint64_t idx, uint32_t stream) {
+  U4 c = {(uint32_t)idx, (uint32_t)(idx >> 32), stream, 0u};
+  U4 r = philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
+  const float u1 = ((float)(r.x >> 8) + 1.0f) * 5.9604644775390625e-8f;   // (0, 1], 24 bits
+  const float u2 = ((float)(r.y >> 8) + 1.0f) * 5.9604644775390625e-8f;
+  return sqrtf(-2.0f * logf(u1)) * cospif(2.0f * u2);
+}
+
+template <typename T> __device__ __forceinline__ T normal_t(uint64_t seed, uint64_t idx, uint32_t stream);
+template <> __device__ __forceinline__ double normal_t<double>(uint64_t s, uint64_t i, uint32_t st) {
+  return normal_at(s, i, st);
+}
+template <> __device__ __forceinline__ float normal_t<float>(uint64_t s, uint64_t i, uint32_t st) {
+  return normal_at_f(s, i, st);
+}
+
 __device__ __forceinline__ double uniform_at(uint64_t seed, uint64_t idx, uint32_t stream) {
   U4 c = {(uint32_t)idx, (uint32_t)(idx >> 32), stream, 0u};
   U4 r = philox4x32_10(c, (uint32_t)seed, (uint32_t)(seed >> 32));
@@ -48,7 +65,9 @@ __device__ __forceinline__ double uniform_at(uint64_t seed, uint64_t idx, uint32
 
 constexpr int kTile = 32;
 
-// out[f][ch][r][c] = sum_{p,q} L[r-p][c-q] K[f][p][q] (+ noise), r < h+t-1, c < w+t-1.
+// out[f][ch][r][c] = sum_{p,q} L[r-p][c-q] K[f][p][q] (+ noise), r < h+t-1, c < w+t-1,
+// accumulated in the frame precision (double frames: double, float frames:
+// float -- the data only has to be Eq. 1 to the precision it is stored in).
 template <typename T>
 __global__ void __launch_bounds__(kTile * 8)
 k_forward_blur(const T* lat, int c, int h, int w, const double* kern, int t, double sigma,
@@ -58,9 +77,9 @@ k_forward_blur(const T* lat, int c, int h, int w, const double* kern, int t, dou
   const int fc = blockIdx.z, f = fc / c;
   const int r0 = blockIdx.y * kTile, c0 = blockIdx.x * kTile;
   const int th = kTile + t - 1;
-  double* K = (double*)smem;                 // t*t
+  T* K = (T*)smem;                           // t*t
   T* tile = (T*)(smem + ((t * t * sizeof(double) + 15) & ~size_t(15)));
-  for (int i = threadIdx.x; i < t * t; i += blockDim.x) K[i] = kern[(int64_t)f * t * t + i];
+  for (int i = threadIdx.x; i < t * t; i += blockDim.x) K[i] = (T)kern[(int64_t)f * t * t + i];
   const T* L = lat + (int64_t)fc * h * w;
   // tile[y][x] = L[r0 - (t-1) + y][c0 - (t-1) + x]
   for (int i = threadIdx.x; i < th * th; i += blockDim.x) {
@@ -73,13 +92,13 @@ k_forward_blur(const T* lat, int c, int h, int w, const double* kern, int t, dou
   for (int ty = ty0; ty < kTile; ty += blockDim.x / kTile) {
     const int r = r0 + ty, col = c0 + tx;
     if (r >= hb || col >= wb) continue;
-    double acc = 0;
+    T acc = 0;
     for (int p = 0; p < t; ++p)
       for (int q = 0; q < t; ++q)
-        acc += K[p * t + q] * (double)tile[(ty + t - 1 - p) * th + (tx + t - 1 - q)];
+        acc = fma(K[p * t + q], tile[(ty + t - 1 - p) * th + (tx + t - 1 - q)], acc);
     const int64_t oi = ((int64_t)fc * hb + r) * wb + col;
-    if (sigma > 0) acc += sigma * normal_at(seed, (uint64_t)oi, 1u);
-    out[oi] = (T)acc;
+    if (sigma > 0) acc += (T)sigma * normal_t<T>(seed, (uint64_t)oi, 1u);
+    out[oi] = acc;
   }
 }
 
@@ -91,15 +110,16 @@ __global__ void k_synth_latent(const double* blobs, int nblobs, int c, int h, in
   const double* B = blobs + (int64_t)fc * nblobs * 4;
   const int y = blockIdx.y, x = blockIdx.x * blockDim.x + threadIdx.x;
   if (x >= w) return;
-  double v = 0;
+  // in the frame precision, like the blur
+  T v = 0;
   for (int k = 0; k < nblobs; ++k) {
-    const double a = B[4 * k], s = B[4 * k + 1], cx = B[4 * k + 2], cy = B[4 * k + 3];
-    const double dx = x - cx, dy = y - cy;
-    v += a * exp(-(dx * dx + dy * dy) / (2.0 * s * s));
+    const T a = (T)B[4 * k], s = (T)B[4 * k + 1], cx = (T)B[4 * k + 2], cy = (T)B[4 * k + 3];
+    const T dx = (T)x - cx, dy = (T)y - cy;
+    v += a * exp(-(dx * dx + dy * dy) / ((T)2 * s * s));
   }
   const int64_t oi = ((int64_t)fc * h + y) * w + x;
-  v += floor_amp * uniform_at(seed, (uint64_t)oi, 2u);
-  out[oi] = (T)v;
+  v += (T)(floor_amp * uniform_at(seed, (uint64_t)oi, 2u));
+  out[oi] = v;
 }
 
 }  // namespace

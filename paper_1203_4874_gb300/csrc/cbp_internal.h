@@ -8,6 +8,9 @@
 namespace cbp {
 
 constexpr int kMaxN = 64;      // t1 + t2 (per-sample system width)
+constexpr int kCnnSide = 256;  // learned proposal: network input side
+constexpr int kCnnT = 15;      // learned proposal: kernel side
+constexpr int kCnnParams = 19362;
 constexpr int kMaxM = 32;      // samples per direction (scale system is 2M wide)
 constexpr int kMaxRadixStages = 16;
 
@@ -60,6 +63,9 @@ struct Plan {
   int fft_f64;                 // deconvolution arithmetic in double
   int single_kernel;           // deconvolve B1 by K1 only
   int pw_half;                 // Pw even: real row FFTs via half-length complex FFTs
+  int learned;                 // learned path: proposal + consistency gate first
+  int col_strips;              // column strips of the column pass
+  double accept_rho;
   double eps;
   FftPlan fp_h, fp_w, fp_w2;   // plans of Ph, Pw, Pw/2
   // workspace layout (byte offsets into one device allocation)
@@ -79,6 +85,10 @@ struct Plan {
   size_t off_spec[2];              // cpx<T_fft> [n][C][H_Bk][Pw2p]
   size_t off_ihat;                 // cpx<T_fft> [n][C][H][Pw2p]
   size_t off_io_b[2], off_io_k[2], off_io_lat; // device staging for host I/O
+  size_t off_cnn;                  // learned path: network workspace
+  size_t off_acc;                  // int [n] proposal accepted
+  size_t off_rho;                  // double [n] consistency residual of the proposal
+  size_t off_rpart;                // double [n][C][col_strips][2] residual partial sums
   size_t total;
 };
 
@@ -117,6 +127,18 @@ size_t row_pass_min_smem(const Plan& p);
 void launch_col_deconv(const Plan& p, char* ws, cudaStream_t st);
 void launch_row_ifft(const Plan& p, char* ws, void* latent, int out_f64, cudaStream_t st,
                      const uint64_t* lat_tab = nullptr);
+// learned path: consistency residual of the kernels in kd (column pass in
+// residual mode, then the per-pair gate: rho, accepted)
+void launch_residual_gate(const Plan& p, char* ws, cudaStream_t st);
+// learned proposal (cbp_cnn.cu)
+size_t cnn_workspace(int n, bool train);
+void cnn_forward(const FrameDesc& b1, const FrameDesc& b2, int n, const float* prm, char* ws,
+                 cudaStream_t st, const cbp_cnn_trace* tr = nullptr);
+const float* cnn_kernels(char* ws, int n);
+void cnn_to_kd(char* ws, int n, double* kd, cudaStream_t st);
+void cnn_train_step(const FrameDesc& b1, const FrameDesc& b2, int n, const float* kt, float* prm,
+                    float* m, float* v, const cbp_adamw& hp, float* loss, char* ws, cudaStream_t st,
+                    const cbp_cnn_trace* tr = nullptr);
 // Eq. 1 forward model (cbp_forward.cu)
 void launch_forward_blur(const void* latent, int n, int c, int h, int w, int f64,
                          const double* kernel, int t, double sigma, uint64_t seed, void* out,

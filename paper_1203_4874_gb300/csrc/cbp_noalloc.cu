@@ -62,6 +62,7 @@ extern "C" cbp_status cbp_estimate_kernels_noalloc(const cbp_frames* b1, const c
   using namespace cbp;
   if (!params || !k1 || !k2) return CBP_ERR_INVALID_ARG;
   if (params->flags & (CBP_FLAG_HOST_IO | CBP_FLAG_KERNELS_IN)) return CBP_ERR_INVALID_ARG;
+  if (params->path == CBP_PATH_LEARNED) return CBP_ERR_UNSUPPORTED;   // needs the FFT workspace
   Plan p;
   cbp_status s = make_plan(b1, b2, params, &p);
   if (s != CBP_OK) return s;

@@ -118,6 +118,10 @@ cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_param
   const int frame_f64 = b1->dtype == CBP_F64;
   p.fft_f64 = (frame_f64 && !p.mixed) ? 1 : 0;
   p.single_kernel = (prm->flags & CBP_FLAG_SINGLE_KERNEL) ? 1 : 0;
+  p.learned = prm->path == CBP_PATH_LEARNED ? 1 : 0;
+  if (p.learned && (t1 != kCnnT || t2 != kCnnT)) return CBP_ERR_UNSUPPORTED;  // network output size
+  if (p.learned && !(prm->accept_rho >= 0.0)) return CBP_ERR_INVALID_ARG;
+  p.accept_rho = prm->accept_rho;
   p.eps = prm->eps;
   if (!make_fft_plan(p.Ph, &p.fp_h) || !make_fft_plan(p.Pw, &p.fp_w)) return CBP_ERR_INVALID_ARG;
   if (p.pw_half && !make_fft_plan(p.Pw / 2, &p.fp_w2)) return CBP_ERR_INVALID_ARG;
@@ -171,6 +175,13 @@ cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_param
   p.off_spec[0] = take(n * C * (size_t)p.H1 * p.Pw2p * ce);
   p.off_spec[1] = take(n * C * (size_t)p.H2 * p.Pw2p * ce);
   p.off_ihat = take(n * C * (size_t)p.H * p.Pw2p * ce);
+  p.col_strips = (p.Pw2 + (int)cw - 1) / (int)cw;
+  if (p.learned) {
+    p.off_cnn = take(cnn_workspace(p.n, false));
+    p.off_acc = take(n * 4);
+    p.off_rho = take(n * 8);
+    p.off_rpart = take(n * C * (size_t)p.col_strips * 2 * 8);
+  }
   if (prm->flags & CBP_FLAG_HOST_IO) {
     const size_t es = frame_f64 ? 8 : 4;
     p.off_io_b[0] = take(n * C * (size_t)p.H1 * p.W1 * es);

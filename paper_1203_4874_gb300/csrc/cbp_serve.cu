@@ -218,7 +218,7 @@ struct ServeState {
       // the data addresses come from the tables; non-null placeholders
       // satisfy the argument checks
       rs = run_plan(p, &f1, &f2, &r0.prm, r0.k1, r0.k2, r0.lat, r0.lat != nullptr, e->mem, s.st,
-                    nullptr, &t);
+                    nullptr, &t, ctx->cnn_w);
       if (cudaStreamEndCapture(s.st, &g) != cudaSuccess) rs = CBP_ERR_CUDA;
     }
     if (rs == CBP_OK && (!g || cudaGraphInstantiate(&e->exec, g, 0) != cudaSuccess)) rs = CBP_ERR_CUDA;

@@ -36,16 +36,20 @@ struct Ctx {
   bool profiling = false;
   Prof prof;
   std::mutex serve_mu;        // guards creation of `serve`
+  float* cnn_w = nullptr;     // learned-path weights (cbp_learned_load)
+  char* cnn_ws = nullptr;     // workspace of the standalone network calls
+  size_t cnn_ws_size = 0;
 
   bool reserve(size_t bytes);
   void release(size_t bytes);
   cbp_status ensure_ws(size_t bytes, cudaStream_t st);
+  cbp_status ensure_cnn_ws(size_t bytes, cudaStream_t st);
 };
 
 cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
                     const cbp_params* prm, void* k1, void* k2, void* latent, bool deblur,
                     char* wsp, cudaStream_t st, Prof* prof = nullptr,
-                    const PtrTables* tabs = nullptr);
+                    const PtrTables* tabs = nullptr, const float* cnn_w = nullptr);
 void serve_shutdown(Ctx* c);
 
 }  // namespace cbp

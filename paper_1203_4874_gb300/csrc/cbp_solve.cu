@@ -601,6 +601,7 @@ struct SampleArgs {
   cd* X;                     // [n][2][ns][nn]
   double* sdiag;             // [n][2][ns][4]
   cd* resid;                 // [n][2][ns][C][Lmax]
+  const int* accepted;       // learned path: pairs whose proposal passed the gate (skipped)
   int Lmax, C, ns, t1, t2, nn, M, mixed;
 };
 
@@ -837,6 +838,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_sample_solve(SampleArgs a) {
   // of every pair -- the slow ones, resolved in double precision -- start
   // first and the short samples fill in behind them.
   const int f = blockIdx.x, ps = blockIdx.y, s = blockIdx.z;
+  if (a.accepted && a.accepted[f]) return;   // the proposal stands; nothing to solve
   const int n = a.nn;
   EigSmem S;
   char* p = carve_eig(S, smem, n);
@@ -899,6 +901,8 @@ struct ScaleArgs {
   const uint64_t* k2_tab;
   int out_f64;
   cbp_diag* diag;       // [n]
+  const int* accepted;  // learned path: proposal passed the gate (kernels already in kd)
+  const double* rho;    // learned path: consistency residual of the proposal
   int M, ns, t1, t2, nn, mixed, Ph, Pw;
 };
 
@@ -949,6 +953,35 @@ struct ScaleApply {
 __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
   extern __shared__ __align__(16) char smem[];
   const int f = blockIdx.x;
+  if (a.accepted && a.accepted[f]) {
+    // learned path, proposal accepted: its kernels (in kd) are the result
+    const int per = a.t1 * a.t1 + a.t2 * a.t2;
+    const double* kd = a.kd + (int64_t)f * per;
+    for (int e = threadIdx.x; e < per; e += blockDim.x) {
+      const int k = e >= a.t1 * a.t1, t = k ? a.t2 : a.t1, ek = k ? e - a.t1 * a.t1 : e;
+      void* out = k ? a.k2_out : a.k1_out;
+      int64_t oi = (int64_t)f * t * t + ek;
+      const uint64_t* tab = k ? a.k2_tab : a.k1_tab;
+      if (tab) {
+        out = (void*)tab[f];
+        oi = ek;
+      }
+      if (out) {
+        if (a.out_f64) ((double*)out)[oi] = kd[e];
+        else ((float*)out)[oi] = (float)kd[e];
+      }
+    }
+    if (threadIdx.x == 0) {
+      cbp_diag d = {};
+      d.rho = a.rho[f];
+      d.used_fallback = 0;
+      d.pad_h = a.Ph;
+      d.pad_w = a.Pw;
+      d.status = a.bad[f] ? CBP_ERR_INVALID_ARG : CBP_OK;
+      a.diag[f] = d;
+    }
+    return;
+  }
   const int M = a.M, MM = M * M, t1 = a.t1, t2 = a.t2;
   const int n = 2 * M;
   EigSmem S;
@@ -1096,9 +1129,9 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
     dg.gap_min = gap;
     dg.sigma_min_max = smin;
     dg.scale_resid = sqrt(fmax(res.theta, 0.0) / fmax(res.lam_max, 1e-300));
-    dg.rho = 0.0;
+    dg.rho = a.rho ? a.rho[f] : 0.0;
     dg.flagged_samples = flagged;
-    dg.used_fallback = 0;
+    dg.used_fallback = a.accepted ? 1 : 0;
     dg.pad_h = a.Ph;
     dg.pad_w = a.Pw;
     dg.hard_samples = hard;
@@ -1165,6 +1198,7 @@ void launch_sample_solve(const Plan& p, char* ws, cudaStream_t st) {
   a.nn = p.nn;
   a.M = p.M;
   a.mixed = p.mixed;
+  a.accepted = p.learned ? (const int*)(ws + p.off_acc) : nullptr;
   const size_t sm = sample_solve_smem(p.nn);
   dim3 grid(p.n, 2, p.ns);
   cudaFuncSetAttribute(k_sample_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -1193,6 +1227,8 @@ void launch_scale_solve(const Plan& p, char* ws, void* k1_out, void* k2_out, int
   a.mixed = p.mixed;
   a.Ph = p.Ph;
   a.Pw = p.Pw;
+  a.accepted = p.learned ? (const int*)(ws + p.off_acc) : nullptr;
+  a.rho = p.learned ? (const double*)(ws + p.off_rho) : nullptr;
   const size_t sm = scale_solve_smem(p.M);
   cudaFuncSetAttribute(k_scale_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_scale_solve<<<p.n, kSolveThreads, sm, st>>>(a);

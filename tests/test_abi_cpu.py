@@ -13,7 +13,7 @@ ROOT = Path(__file__).resolve().parents[1]
 def declared_functions():
     src = (ROOT / "include" / "cbp.h").read_text()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:cbp_status|const char\*)\s+(cbp_\w+)\s*\(", src, re.M)))
+    return sorted(set(re.findall(r"^\s*(?:cbp_status|const char\*|size_t)\s+(cbp_\w+)\s*\(", src, re.M)))
 
 
 def test_every_declared_symbol_is_exported(built_lib):

@@ -238,3 +238,18 @@ def test_forward_model_matches_oracle(gpu_ctx):
     torch.cuda.synchronize()
     for i in range(2):
         assert rel(out[i, 0].cpu().numpy(), oracle.blur_full(lat[i, 0], ks[i])) <= 1e-14
+    # float frames: Eq. 1 accumulated in float32 (the precision they are stored in)
+    lat32 = lat.astype(np.float32)
+    ks15 = np.stack([rng.uniform(size=(15, 15)) for _ in range(2)])
+    out32 = cbp.cbp_forward_blur(gpu_ctx, torch.from_numpy(lat32).cuda(), torch.from_numpy(ks15).cuda())
+    torch.cuda.synchronize()
+    for i in range(2):
+        ref = oracle.blur_full(lat32[i, 0].astype(np.float64), ks15[i])
+        # float taps and a float sum of t^2 = 225 positive terms: at most about
+        # (t^2 + 1) u = 1.3e-5 relative, typically ~2e-7
+        assert rel(out32[i, 0].double().cpu().numpy(), ref) <= 2e-6
+    # noise: sample mean and variance of sigma * N(0, 1) on a zero latent
+    z = torch.zeros((1, 1, 400, 400), dtype=torch.float32, device="cuda")
+    delta = torch.zeros((1, 1, 1), dtype=torch.float64, device="cuda")
+    nz = cbp.cbp_forward_blur(gpu_ctx, z, delta, sigma=1e-3, seed=5).double().cpu().numpy()
+    assert abs(nz.mean()) < 2e-5 and abs(nz.std() / 1e-3 - 1) < 1e-2
