@@ -147,7 +147,7 @@ class ClockSampler:
 
 
 # ----------------------------------------------------------------- inputs ---
-def make_inputs(ctx, n: int, seed0: int, device):
+def make_inputs(ctx, n: int, seed0: int, device, t1: int = T1, t2: int = T2):
     """Kernels and blob parameters drawn on the host (cbp_synth), latents and
     blurred frames synthesised on the device by the library's forward model."""
     import numpy as np
@@ -159,7 +159,7 @@ def make_inputs(ctx, n: int, seed0: int, device):
     for f in range(n):
         rng = _rng(seed0 + f)
         blobs.append(np.stack([blob_params(rng, H, W) for _ in range(C)]))
-        a, b = draw_kernel_pair(rng, T1, T2, max(T1, T2), "mixture")
+        a, b = draw_kernel_pair(rng, t1, t2, max(t1, t2), "mixture")
         k1s.append(a)
         k2s.append(b)
     k1 = torch.from_numpy(np.stack(k1s)).to(device)
@@ -280,6 +280,42 @@ def serving_bench(seconds: float, device, seed: int = 5150, cameras: int = 16, r
             "cameras": [{"h": c["h"], "w": c["w"], "t1": c["t1"], "t2": c["t2"]} for c in cams]}
 
 
+# ---------------------------------------------------------- learned path --
+def learned_bench(ctx, n: int, device, steps: int = 3) -> dict:
+    """The learned kernel proposal at 1080p (both kernels 15 x 15, the
+    network's output size; RGB f32, noise sigma 1e-3): learned path (network,
+    consistency gate, GCD-solve fallback) against the mixed path on the same
+    pairs, each timed over `steps` calls after one warm-up call."""
+    import torch
+    from paper_1203_4874_gb300 import cbp
+
+    cbp.cbp_learned_load(ctx, ROOT / "paper_1203_4874_gb300" / "cnn_weights.bin")
+    b1, b2, _, _ = make_inputs(ctx, n, 4_000_000, device, 15, 15)
+    lat = torch.empty((n, C, H, W), dtype=torch.float32, device=device)
+    k1 = torch.empty((n, 15, 15), dtype=torch.float32, device=device)
+    k2 = torch.empty_like(k1)
+    out = {}
+    for path in ("learned", "mixed"):
+        prm = cbp.params(15, 15, path=path, eps=EPS, accept_rho=1e-3)
+        d = None
+        for i in range(steps + 1):
+            if i == 1:
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+            _, _, _, d, _ = cbp.cbp_deblur_pair(ctx, b1, b2, prm, k1=k1, k2=k2, latent=lat,
+                                                diag=(i == steps))
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / steps
+        out[path] = {"value": n / dt, "ms_per_step": 1e3 * dt}
+        if path == "learned":
+            rho = [x.rho for x in d]
+            out[path]["accepted"] = sum(1 for x in d if x.used_fallback == 0)
+            out[path]["rho_median"] = float(sorted(rho)[len(rho) // 2])
+    return {"workload": f"{n} pairs/step, 1920x1080x3 f32, both kernels 15x15 (mixture), noise sigma 1e-3, "
+                        "accept_rho 1e-3, trained weights (200k pairs)", "unit": UNIT,
+            "learned": out["learned"], "mixed": out["mixed"]}
+
+
 # ------------------------------------------------------- CPU oracle sample --
 def cpu_worker(pairs: int):
     """Time the FP64 oracle on `pairs` pairs of the workload (host cores)."""
@@ -370,6 +406,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-path measurement")
     ap.add_argument("--serve-seconds", type=float, default=6.0,
                     help="seconds of the camera serving trace (0: skip)")
     ap.add_argument("--cpu-worker", type=int, default=0)
@@ -508,6 +545,8 @@ def main():
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches, "clocks": clk,
     }
+    if rank == 0 and not args.no_learned:
+        result["learned"] = learned_bench(ctx, n, dev)
     if rank == 0 and args.serve_seconds > 0:
         result["serving"] = serving_bench(args.serve_seconds, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

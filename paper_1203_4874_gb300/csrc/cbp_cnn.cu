@@ -83,26 +83,30 @@ __global__ void __launch_bounds__(kCnnThreads) k_cnn_input(FrameDesc f1, FrameDe
   const int o = blockIdx.x * blockDim.x + threadIdx.x;
   if (o >= kCnnSide * kCnnSide) return;
   const int y = o / kCnnSide, x = o % kCnnSide;
-  const double fy = (double)fr.h / kCnnSide, fx = (double)fr.w / kCnnSide;
-  const double ay = y * fy, by = (y + 1) * fy, ax = x * fx, bx = (x + 1) * fx;
-  const int r0 = (int)floor(ay), r1 = min(fr.h, (int)ceil(by));
-  const int c0 = (int)floor(ax), c1 = min(fr.w, (int)ceil(bx));
+  // cell bounds in exact integer arithmetic: [y h / S, (y + 1) h / S)
+  const int r0 = (int)(((int64_t)y * fr.h) / kCnnSide);
+  const int r1 = min(fr.h, (int)(((int64_t)(y + 1) * fr.h + kCnnSide - 1) / kCnnSide));
+  const int c0 = (int)(((int64_t)x * fr.w) / kCnnSide);
+  const int c1 = min(fr.w, (int)(((int64_t)(x + 1) * fr.w + kCnnSide - 1) / kCnnSide));
+  // overlaps in units of 1/S input cells: [y h, (y+1) h) against [r S, (r+1) S)
+  const int ya = y * fr.h, yb = (y + 1) * fr.h, xa = x * fr.w, xb = (x + 1) * fr.w;
   const void* base = frame_base(fr, f);
-  const float inv_c = 1.0f / (float)fr.c;
   float acc = 0.f;
   for (int r = r0; r < r1; ++r) {
-    const float wy = (float)((fmin(by, (double)(r + 1)) - fmax(ay, (double)r)) / fy);
+    const int wy = min(yb, (r + 1) * kCnnSide) - max(ya, r * kCnnSide);
+    const int64_t rb = (int64_t)r * fr.rs;
     float row = 0.f;
     for (int c = c0; c < c1; ++c) {
-      const float wx = (float)((fmin(bx, (double)(c + 1)) - fmax(ax, (double)c)) / fx);
+      const int wx = min(xb, (c + 1) * kCnnSide) - max(xa, c * kCnnSide);
       float v = 0.f;
-      for (int ch = 0; ch < fr.c; ++ch)
-        v += ld_frame<float>(base, (int64_t)ch * fr.cs + (int64_t)r * fr.rs + c, fr.f64);
-      row += wx * v;
+      for (int ch = 0; ch < fr.c; ++ch) v += ld_frame<float>(base, (int64_t)ch * fr.cs + rb + c, fr.f64);
+      row = fmaf((float)wx, v, row);
     }
-    acc += wy * row;
+    acc = fmaf((float)wy, row, acc);
   }
-  x0[((int64_t)f * 2 + z) * kCnnSide * kCnnSide + o] = __float2bfloat16(acc * inv_c);
+  // weights were in 1/S units of an input cell; the cell area is h w / S^2
+  const float norm = 1.0f / ((float)fr.h * (float)fr.w * (float)fr.c);
+  x0[((int64_t)f * 2 + z) * kCnnSide * kCnnSide + o] = __float2bfloat16(acc * norm);
 }
 
 template <typename TO> __device__ __forceinline__ TO to_out(float v);
