@@ -24,15 +24,32 @@ bool make_fft_plan(int n, FftPlan* p) {
   if (n < 1) return false;
   p->n = n;
   p->nst = 0;
-  int r = n, Ns = 1, off = 0;
-  while (r > 1) {
+  // radices, largest first; then an odd radix moved to the front: the first
+  // stage writes its outputs R elements apart, and an odd stride keeps those
+  // shared-memory stores free of bank conflicts
+  int radix[kMaxRadixStages];
+  int nr = 0;
+  for (int r = n; r > 1;) {
     int R = 0;
     for (int cand : {9, 8, 7, 5, 4, 3, 2})
       if (r % cand == 0) {
         R = cand;
         break;
       }
-    if (!R || p->nst >= kMaxRadixStages) return false;
+    if (!R || nr >= kMaxRadixStages) return false;
+    radix[nr++] = R;
+    r /= R;
+  }
+  for (int i = 0; i < nr; ++i)
+    if (radix[i] & 1) {
+      const int R = radix[i];
+      for (int j = i; j > 0; --j) radix[j] = radix[j - 1];
+      radix[0] = R;
+      break;
+    }
+  int Ns = 1, off = 0;
+  for (int i = 0; i < nr; ++i) {
+    const int R = radix[i];
     FftStage& st = p->st[p->nst++];
     st.R = R;
     st.Ns = Ns;
@@ -42,7 +59,6 @@ bool make_fft_plan(int n, FftPlan* p) {
     st.tw = off;
     off += Ns * (R - 1);
     Ns *= R;
-    r /= R;
   }
   p->ntw = off > 0 ? off : 1;
   return true;

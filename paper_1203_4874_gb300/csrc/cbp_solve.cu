@@ -447,9 +447,13 @@ __device__ int hard_eig(EigSmem& S, int n, int np, int ld, double gscale, long l
   return S.flag[2];
 }
 
+// acc_easy / acc_hard: Newton steps against the exact residual (apply) for
+// samples resolved in single precision / in double precision; the latter only
+// where the double gap lambda_2 - lambda_1 is below hard_gap lambda_max.
 template <class Apply>
-__device__ EigResult smallest_eigvec(EigSmem& S, int n, bool real, int acc_steps,
-                                     const Apply& apply, long long* tk = nullptr) {
+__device__ EigResult smallest_eigvec(EigSmem& S, int n, bool real, int acc_easy, int acc_hard,
+                                     double hard_gap, const Apply& apply,
+                                     long long* tk = nullptr) {
   const int np = np_of(n), ld = np + 1;
   if (threadIdx.x == 0) {
     double gs = 0;
@@ -522,7 +526,7 @@ __device__ EigResult smallest_eigvec(EigSmem& S, int n, bool real, int acc_steps
       d2prev = d2;
     }
     if (threadIdx.x == 0) S.flag[3] = it + 1;
-    for (int it = 0; it < acc_steps; ++it) {
+    for (int it = 0; it < acc_easy; ++it) {
       apply(S.x, S.r);
       theta = dotre64(S.x, S.r, n, S.red);
       newton_eigbasis64(S, V64, S.lam, n, ld, imin, S.r, theta);
@@ -540,7 +544,8 @@ __device__ EigResult smallest_eigvec(EigSmem& S, int n, bool real, int acc_steps
     for (int i = threadIdx.x; i < n; i += blockDim.x) S.x[i] = V64[i * ld + i1];
     __syncthreads();
     normalize64(S.x, n, S.red);
-    if (acc_steps > 0) {
+    const int steps = lam2 - S.lam[i1] < hard_gap * lmax ? acc_hard : 0;
+    for (int it = 0; it < steps; ++it) {
       apply(S.x, S.r);
       theta = dotre64(S.x, S.r, n, S.red);
       newton_eigbasis64(S, V64, S.lam, n, ld, i1, S.r, theta);
@@ -797,7 +802,41 @@ struct SylvesterApply {
   cd* y;            // [C][L]
   int C, t1, t2, L;
   double* red;
+  bool real;        // real sample (z = 1, or z = -1 for even M): real arithmetic
   __device__ void operator()(const cd* x, cd* out) const {
+    if (real) apply_real(x, out);
+    else apply_complex(x, out);
+  }
+  // real samples: P and x are real, so are S x and S^T S x
+  __device__ void apply_real(const cd* x, cd* out) const {
+    for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
+      const int ch = idx / L, i = idx % L;
+      double acc = 0.0;
+      for (int q = 0; q < t2; ++q) {     // b1 * v
+        const int m = i - q;
+        if (m >= 0 && m < P.len[0]) acc = fma(P.ld(0, ch, m).re, x[t1 + q].re, acc);
+      }
+      for (int p = 0; p < t1; ++p) {     // - b2 * u
+        const int m = i - p;
+        if (m >= 0 && m < P.len[1]) acc = fma(-P.ld(1, ch, m).re, x[p].re, acc);
+      }
+      y[idx] = mk(acc, 0.0);
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const int n = t1 + t2;
+    for (int o = warp; o < n; o += nw) {
+      const int k = o < t1 ? 1 : 0;
+      const int sh = o < t1 ? o : o - t1;
+      double acc = 0.0;
+      for (int ch = 0; ch < C; ++ch)
+        for (int m = lane; m < P.len[k]; m += 32) acc = fma(P.ld(k, ch, m).re, y[ch * L + m + sh].re, acc);
+      const double re = warp_sum(acc);
+      if (lane == 0) out[o] = mk(o < t1 ? -re : re, 0.0);
+    }
+    __syncthreads();
+  }
+  __device__ void apply_complex(const cd* x, cd* out) const {
     for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
       int ch = idx / L, i = idx % L;
       cd acc = mk(0.0, 0.0);
@@ -855,10 +894,14 @@ __global__ void __launch_bounds__(kSolveThreads) k_sample_solve(SampleArgs a) {
   CBP_TICK(tk, 1);
   gram_from_rho(rho, a.t1, a.t2, S.G);
   CBP_TICK(tk, 2);
-  // FP64 path: two Newton steps against the exact residual S^H S x from the
-  // double samples (removes the squared conditioning of the normal matrix).
-  // Mixed path: the float-float / double normal matrix is accurate to ~1e-13,
-  // enough for its tolerance, and no residual steps are taken.
+  // Newton steps against the exact residual S^H S x from the double samples
+  // (they remove the squared conditioning of the normal matrix).  FP64 path:
+  // two for samples resolved in single precision, one after the double
+  // Jacobi of the others.  Mixed path: none where single precision resolved
+  // the sample (its float-float / double normal matrix is accurate to ~1e-13),
+  // one after the double Jacobi where the two smallest eigenvalues are closer
+  // than 1e-6 lambda_max (the z = 1 samples: ~1e-8 apart, where the normal
+  // matrix alone leaves ~1e-5 in x).
   SylvesterApply ap;
   ap.P = P64;
   ap.C = a.C;
@@ -867,7 +910,9 @@ __global__ void __launch_bounds__(kSolveThreads) k_sample_solve(SampleArgs a) {
   ap.L = a.len[ps][0] + a.t2 - 1;
   ap.y = a.resid + (((int64_t)f * 2 + ps) * a.ns + s) * a.C * (int64_t)a.Lmax;
   ap.red = S.red;
-  const EigResult res = smallest_eigvec(S, n, real, a.mixed ? 0 : 2, ap, tk);
+  ap.real = real;
+  const EigResult res = smallest_eigvec(S, n, real, a.mixed ? 0 : 2, 1, a.mixed ? 1e-6 : 1e300,
+                                       ap, tk);
   CBP_TICK(tk, 5);
 #ifdef CBP_PHASE_TIMING
   if (threadIdx.x == 0 && f < 2)
@@ -1038,7 +1083,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
   }
   __syncthreads();
   ScaleApply ap{ab, M};
-  EigResult res = smallest_eigvec(S, n, false, 2, ap);
+  EigResult res = smallest_eigvec(S, n, false, 2, 1, 1e300, ap);
   // X_k[i][j] = (gamma_j A_k[i][j] + delta_i B_k[i][j]) / 2
   for (int idx = threadIdx.x; idx < 2 * MM; idx += blockDim.x) {
     const int k = idx / MM, i = (idx % MM) / M, j = idx % M;
