@@ -64,6 +64,18 @@ cbp_status Ctx::ensure_ws(size_t bytes, cudaStream_t st) {
   return CBP_OK;
 }
 
+cbp_status Ctx::ensure_chunk_streams() {
+  if (chunk_ready) return CBP_OK;
+  for (int i = 0; i < kMaxChunks; ++i)
+    if (cudaStreamCreateWithFlags(&chunk_st[i], cudaStreamNonBlocking) != cudaSuccess)
+      return CBP_ERR_CUDA;
+  for (int i = 0; i <= kMaxChunks; ++i)
+    if (cudaEventCreateWithFlags(&chunk_ev[i], cudaEventDisableTiming) != cudaSuccess)
+      return CBP_ERR_CUDA;
+  chunk_ready = true;
+  return CBP_OK;
+}
+
 // Grow the standalone network calls' workspace (stream-ordered on `st`).
 cbp_status Ctx::ensure_cnn_ws(size_t bytes, cudaStream_t st) {
   if (bytes <= cnn_ws_size) return CBP_OK;
@@ -265,6 +277,29 @@ cbp_status copy_stages(const Plan& p, const char* ws, const cbp_stage_out* o, cu
   return CBP_OK;
 }
 
+// A batch is split into this many chunks (each with its own plan and
+// workspace region) on the context's internal streams when it holds at least
+// kMinChunkPairs pairs per chunk: the chunks' kernels fill each other's idle
+// SMs and tails (the scale solve, for one, runs one block per pair).  Pairs
+// are independent, so the results do not depend on the split.
+constexpr int kChunks = 2;
+constexpr int kMinChunkPairs = 8;
+
+// The frames / outputs of pairs [start, start + count) of a batch.
+cbp_frames frames_slice(const cbp_frames* f, int start, int count) {
+  cbp_frames s = *f;
+  const int64_t rs = f->row_stride ? f->row_stride : f->w;
+  const int64_t cs = f->chan_stride ? f->chan_stride : (int64_t)f->h * rs;
+  const int64_t fs = f->frame_stride ? f->frame_stride : (int64_t)f->c * cs;
+  const size_t es = f->dtype == CBP_F64 ? 8 : 4;
+  s.data = (const char*)f->data + (size_t)start * (size_t)fs * es;
+  s.n = count;
+  s.row_stride = rs;
+  s.chan_stride = cs;
+  s.frame_stride = fs;
+  return s;
+}
+
 cbp_status call_path(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
                      const cbp_params* prm, void* k1, void* k2, void* latent, cbp_diag* diag,
                      void* stream, bool deblur, const cbp_stage_out* stages = nullptr) {
@@ -279,17 +314,62 @@ cbp_status call_path(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
   DeviceGuard g(c->device);
   cudaStream_t st = (cudaStream_t)stream;
   std::lock_guard<std::mutex> lk(c->api_mu);
-  s = c->ensure_ws(p.total, st);
+  const int nch = (!c->profiling && !stages && p.n >= kChunks * kMinChunkPairs) ? kChunks : 1;
+  if (nch == 1) {
+    s = c->ensure_ws(p.total, st);
+    if (s != CBP_OK) return s;
+    s = cbp::run_plan(p, b1, b2, prm, k1, k2, latent, deblur, c->ws, st,
+                      c->profiling ? &c->prof : nullptr, nullptr, c->cnn_w);
+    if (s != CBP_OK) return s;
+    s = copy_stages(p, c->ws, stages, st);
+    if (s != CBP_OK) return s;
+    if (diag &&
+        cudaMemcpyAsync(diag, c->ws + p.off_diag, (size_t)p.n * sizeof(cbp_diag),
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      return CBP_ERR_CUDA;
+    return CBP_OK;
+  }
+  // chunked: plans, workspace regions, fork from the caller's stream
+  s = c->ensure_chunk_streams();
   if (s != CBP_OK) return s;
-  s = cbp::run_plan(p, b1, b2, prm, k1, k2, latent, deblur, c->ws, st,
-                    c->profiling ? &c->prof : nullptr, nullptr, c->cnn_w);
+  Plan cp[Ctx::kMaxChunks];
+  cbp_frames f1[Ctx::kMaxChunks], f2[Ctx::kMaxChunks];
+  int start[Ctx::kMaxChunks + 1];
+  size_t off[Ctx::kMaxChunks + 1];
+  start[0] = 0;
+  off[0] = 0;
+  for (int i = 0; i < nch; ++i) {
+    start[i + 1] = (int)((int64_t)p.n * (i + 1) / nch);
+    f1[i] = frames_slice(b1, start[i], start[i + 1] - start[i]);
+    f2[i] = frames_slice(b2, start[i], start[i + 1] - start[i]);
+    s = cbp::make_plan(&f1[i], &f2[i], prm, &cp[i]);
+    if (s != CBP_OK) return s;
+    off[i + 1] = off[i] + ((cp[i].total + 255) & ~size_t(255));
+  }
+  s = c->ensure_ws(off[nch], st);
   if (s != CBP_OK) return s;
-  s = copy_stages(p, c->ws, stages, st);
-  if (s != CBP_OK) return s;
-  if (diag &&
-      cudaMemcpyAsync(diag, c->ws + p.off_diag, (size_t)p.n * sizeof(cbp_diag),
-                      cudaMemcpyDeviceToHost, st) != cudaSuccess)
-    return CBP_ERR_CUDA;
+  if (cudaEventRecord(c->chunk_ev[c->kMaxChunks], st) != cudaSuccess) return CBP_ERR_CUDA;
+  const bool kf64 = b1->dtype == CBP_F64 || (prm->flags & CBP_FLAG_KERNELS_F64);
+  const size_t kes = kf64 ? 8 : 4, les = b1->dtype == CBP_F64 ? 8 : 4;
+  const size_t lat_pair = (size_t)p.C * p.H * p.W * les;
+  for (int i = 0; i < nch; ++i) {
+    cudaStream_t cs = c->chunk_st[i];
+    if (cudaStreamWaitEvent(cs, c->chunk_ev[c->kMaxChunks], 0) != cudaSuccess) return CBP_ERR_CUDA;
+    const size_t a = (size_t)start[i];
+    void* ck1 = k1 ? (char*)k1 + a * p.t1 * p.t1 * kes : nullptr;
+    void* ck2 = k2 ? (char*)k2 + a * p.t2 * p.t2 * kes : nullptr;
+    void* clat = latent ? (char*)latent + a * lat_pair : nullptr;
+    char* w = c->ws + off[i];
+    s = cbp::run_plan(cp[i], &f1[i], &f2[i], prm, ck1, ck2, clat, deblur, w, cs, nullptr, nullptr,
+                      c->cnn_w);
+    if (s != CBP_OK) return s;
+    if (diag && cudaMemcpyAsync(diag + a, w + cp[i].off_diag, (size_t)cp[i].n * sizeof(cbp_diag),
+                                cudaMemcpyDeviceToHost, cs) != cudaSuccess)
+      return CBP_ERR_CUDA;
+    if (cudaEventRecord(c->chunk_ev[i], cs) != cudaSuccess ||
+        cudaStreamWaitEvent(st, c->chunk_ev[i], 0) != cudaSuccess)
+      return CBP_ERR_CUDA;
+  }
   return CBP_OK;
 }
 
@@ -323,6 +403,10 @@ cbp_status cbp_destroy(cbp_ctx* ctx) {
   cbp::serve_shutdown(c);
   cudaDeviceSynchronize();
   if (c->ws) cudaFree(c->ws);
+  for (int i = 0; i < Ctx::kMaxChunks; ++i)
+    if (c->chunk_st[i]) cudaStreamDestroy(c->chunk_st[i]);
+  for (int i = 0; i <= Ctx::kMaxChunks; ++i)
+    if (c->chunk_ev[i]) cudaEventDestroy(c->chunk_ev[i]);
   if (c->cnn_ws) cudaFree(c->cnn_ws);
   if (c->cnn_w) cudaFree(c->cnn_w);
   delete c;

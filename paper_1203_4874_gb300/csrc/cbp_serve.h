@@ -35,6 +35,12 @@ struct Ctx {
   ServeState* serve = nullptr;
   bool profiling = false;
   Prof prof;
+  // internal streams and fork/join events of chunked synchronous calls
+  static constexpr int kMaxChunks = 4;
+  cudaStream_t chunk_st[kMaxChunks] = {};
+  cudaEvent_t chunk_ev[kMaxChunks + 1] = {};
+  bool chunk_ready = false;
+  cbp_status ensure_chunk_streams();
   std::mutex serve_mu;        // guards creation of `serve`
   float* cnn_w = nullptr;     // learned-path weights (cbp_learned_load)
   char* cnn_ws = nullptr;     // workspace of the standalone network calls
