@@ -277,12 +277,12 @@ cbp_status copy_stages(const Plan& p, const char* ws, const cbp_stage_out* o, cu
   return CBP_OK;
 }
 
-// A batch is split into this many chunks (each with its own plan and
-// workspace region) on the context's internal streams when it holds at least
-// kMinChunkPairs pairs per chunk: the chunks' kernels fill each other's idle
+// A batch is split into up to kChunks chunks of at least kMinChunkPairs pairs
+// (each with its own plan and workspace region) on the context's internal
+// streams: the chunks' kernels fill each other's idle
 // SMs and tails (the scale solve, for one, runs one block per pair).  Pairs
 // are independent, so the results do not depend on the split.
-constexpr int kChunks = 2;
+constexpr int kChunks = 3;
 constexpr int kMinChunkPairs = 8;
 
 // The frames / outputs of pairs [start, start + count) of a batch.
@@ -314,7 +314,7 @@ cbp_status call_path(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
   DeviceGuard g(c->device);
   cudaStream_t st = (cudaStream_t)stream;
   std::lock_guard<std::mutex> lk(c->api_mu);
-  const int nch = (!c->profiling && !stages && p.n >= kChunks * kMinChunkPairs) ? kChunks : 1;
+  const int nch = (c->profiling || stages) ? 1 : std::max(1, std::min(kChunks, p.n / kMinChunkPairs));
   if (nch == 1) {
     s = c->ensure_ws(p.total, st);
     if (s != CBP_OK) return s;
