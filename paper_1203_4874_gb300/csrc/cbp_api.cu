@@ -154,6 +154,7 @@ cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
     }
   }
   cudaMemsetAsync(wsp + p.off_bad, 0, (size_t)p.n * sizeof(int), st);
+  cudaMemsetAsync(wsp + p.off_err, 0, sizeof(int), st);
   if (kin) {
     if ((!k1d || !k2d) && !(tabs && tabs->k1 && tabs->k2)) return CBP_ERR_INVALID_ARG;
     begin(CBP_STAGE_SCALE_SOLVE);

@@ -327,6 +327,48 @@ __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// Bulk (TMA) copies completed on an mbarrier.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+// global -> this block's shared memory, `bytes` a multiple of 16, both ends 16-byte aligned
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+// Wait for phase `parity` of the barrier, giving up after `limit` polls.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit) {
+  const uint32_t a = smem_addr(bar);
+  for (int i = 0; i < limit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+constexpr int kWaitLimit = 1 << 20;
+
 __device__ __forceinline__ cf ldg_cpx(const cf* p) {
   const float2 v = __ldg((const float2*)p);
   return mk(v.x, v.y);
@@ -356,6 +398,7 @@ struct RowPassArgs {
   double* bins_r[2];   // [n C][M][H_Bk] row-fold bins (FOLD)
   double* bins_c[2];   // [n C][M][W_Bk] column-fold bins (FOLD)
   int* bad;            // [n] non-finite input flags (FOLD)
+  int* err;            // set when a copy does not complete in time
   int M;
   int fft_frames;      // frames whose rows are transformed (1: single-kernel form)
   int Pw, Pw2, Pw2p, half, nbr, rw;
@@ -395,7 +438,7 @@ template <> struct FoldAcc<double> { using type = DoubleSum; };
 // rows once they are consumed, when they are large enough (b1_alias); column
 // accumulators live in registers unless W exceeds kColRegs per thread.
 struct RowPassSmem {
-  size_t tw, b0, b1, raw0, raw1, colacc, rb, rph, total;
+  size_t tw, b0, b1, raw0, raw1, colacc, rb, rph, mbar, total;
   bool b1_alias, col_smem;
 };
 __host__ __device__ inline size_t rp_align(size_t x) { return (x + 15) & ~size_t(15); }
@@ -421,35 +464,67 @@ __host__ __device__ inline RowPassSmem row_pass_layout(int N, int ntw, int W, in
   if (fold) o += rp_align((size_t)kRowWarps * 32 * 8);
   L.rph = o;
   o += rp_align(2 * (size_t)nbr * sizeof(int));
+  L.mbar = o;
+  o += rp_align(2 * sizeof(uint64_t));
   L.total = o;
   return L;
 }
 
-// Issue the copies of nr rows (row i at element offset rowoff(i) of fb) into
-// the staging rows dst + i * rw, each at its own 16-byte phase ph_i (element
-// c of row i lands at dst[i * rw + ph_i + c]).  Elements before a row's first
-// 16-byte boundary go by element-sized copies, the rest by 16-byte chunks, the
-// last one partial; nothing outside the row is read.
+// One element a thread fetched for a staging row, stored later.
+template <typename In> struct Edge {
+  In v;
+  int at;   // index in the staging buffer, -1: none
+};
+
+// Stage nr rows (row i at element offset rowoff(i) of fb) into the rows
+// dst + i * rw, each at its own 16-byte phase ph_i (element c of row i lands at
+// dst[i * rw + ph_i + c]).  Thread 0 moves each row's 16-byte-aligned body
+// with one bulk (TMA) copy completing on `bar`; the few elements before the
+// first and after the last 16-byte boundary are loaded by other threads into
+// the returned Edge, which the caller stores before the rows are read (so the
+// load's latency overlaps other work).  Nothing outside the rows is read.
 template <typename In, class RowOff>
-__device__ __forceinline__ void stage_rows_async(In* dst, int* rph, const In* fb, const RowOff& rowoff,
-                                                 int nr, int W, int rw) {
+__device__ __forceinline__ Edge<In> stage_rows_bulk(In* dst, int* rph, const In* fb,
+                                                    const RowOff& rowoff, int nr, int W, int rw,
+                                                    uint64_t* bar) {
   constexpr int E = 16 / (int)sizeof(In);
-  const int tasks = (E - 1) + (W + E - 1) / E;
-  for (int i = 0; i < nr; ++i) {
-    const In* row = fb + rowoff(i);
-    const int ph = (int)(((uintptr_t)row / sizeof(In)) & (E - 1));
-    const int head = ph ? min(E - ph, W) : 0;
-    In* drow = dst + i * rw + ph;
-    for (int t = threadIdx.x; t < tasks; t += blockDim.x) {
-      if (t < E - 1) {                                 // head element t
-        if (t < head) cp_async_small<(int)sizeof(In)>(drow + t, row + t);
-      } else {
-        const int c0 = head + (t - (E - 1)) * E;        // chunk start element
-        if (c0 < W) cp_async16(drow + c0, row + c0, min(E, W - c0) * (int)sizeof(In));
-      }
+  auto geom = [&](int i, const In*& row, int& ph, int& head, int& body) {
+    row = fb + rowoff(i);
+    ph = (int)(((uintptr_t)row / sizeof(In)) & (E - 1));
+    head = ph ? min(E - ph, W) : 0;
+    body = ((W - head) / E) * E;                    // elements in whole 16-byte chunks
+  };
+  if (threadIdx.x == 0) {
+    uint32_t total = 0;
+    for (int i = 0; i < nr; ++i) {
+      const In* row;
+      int ph, head, body;
+      geom(i, row, ph, head, body);
+      total += (uint32_t)(body * sizeof(In));
+      rph[i] = ph;
     }
-    if (threadIdx.x == 0) rph[i] = ph;
+    mbar_expect_tx(bar, total);
+    for (int i = 0; i < nr; ++i) {
+      const In* row;
+      int ph, head, body;
+      geom(i, row, ph, head, body);
+      if (body) bulk_g2s(dst + i * rw + ph + head, row + head, (uint32_t)(body * sizeof(In)), bar);
+    }
   }
+  Edge<In> e{(In)0, -1};
+  const int t = (int)threadIdx.x - 32;   // warps other than thread 0's
+  if (t >= 0 && t < nr * 2 * E) {
+    const int i = t / (2 * E), sl = t - i * (2 * E);
+    const In* row;
+    int ph, head, body;
+    geom(i, row, ph, head, body);
+    const int c = sl < E ? sl : head + body + (sl - E);
+    if ((sl < E && sl < head) || (sl >= E && c < W)) {
+      e.v = row[c];
+      e.at = i * rw + ph + c;
+    }
+  }
+  return e;
 }
 
 template <typename T, typename In, bool FOLD, bool FFT>
@@ -469,6 +544,14 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
   Acc* colacc = (Acc*)(smem + L.colacc);
   double* rb = (double*)(smem + L.rb);
   int* rph = (int*)(smem + L.rph);
+  uint64_t* bars = (uint64_t*)(smem + L.mbar);   // one per staging buffer
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t par = 0u;   // bit b: phase parity of buffer b's next completion
   if (fft) load_twiddles(tw, stw, a.pl.ntw);
   Acc creg[kColRegs];
   if (FOLD && L.col_smem)
@@ -480,10 +563,11 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
   const In* fb = (const In*)frame_base(fr, f) + (int64_t)ch * fr.cs;
   auto row_of = [&](int g, int i) { return x0 + (g * NB + i) * X; };
   if (ngroups > 0) {
-    stage_rows_async<In>(raw0, rph, fb, [&](int i) { return (int64_t)row_of(0, i) * fr.rs; },
-                         min(NB, nrows), W, a.rw);
+    const Edge<In> e0 = stage_rows_bulk<In>(raw0, rph, fb,
+                                            [&](int i) { return (int64_t)row_of(0, i) * fr.rs; },
+                                            min(NB, nrows), W, a.rw, &bars[0]);
+    if (e0.at >= 0) raw0[e0.at] = e0.v;
   }
-  cp_async_commit();
   cpx<T>* spec = fft ? (cpx<T>*)a.spec[blockIdx.z] + (int64_t)fc * fr.h * a.Pw2p : nullptr;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 #ifdef CBP_PHASE_TIMING
@@ -493,16 +577,23 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
   for (int g = 0; g < ngroups; ++g) {
     const int nr = min(NB, nrows - g * NB);
     RP_MARK(7);
+    Edge<In> en{(In)0, -1};
     if (g + 1 < ngroups) {
       const int g1 = g + 1;
-      stage_rows_async<In>((g1 & 1) ? raw1 : raw0, rph + (g1 & 1) * NB, fb,
-                           [&](int i) { return (int64_t)row_of(g1, i) * fr.rs; },
-                           min(NB, nrows - g1 * NB), W, a.rw);
+      en = stage_rows_bulk<In>((g1 & 1) ? raw1 : raw0, rph + (g1 & 1) * NB, fb,
+                               [&](int i) { return (int64_t)row_of(g1, i) * fr.rs; },
+                               min(NB, nrows - g1 * NB), W, a.rw, &bars[g1 & 1]);
     }
-    cp_async_commit();
     RP_MARK(0);
-    cp_async_wait<1>();
-    __syncthreads();
+    const bool arrived = mbar_wait(&bars[g & 1], (par >> (g & 1)) & 1u, kWaitLimit);
+    par ^= 1u << (g & 1);
+    if (__syncthreads_or(!arrived)) {
+      // a copy did not complete in time: report it, wait (bounded) for the
+      // other buffer's copies still in flight, and leave
+      if (threadIdx.x == 0) atomicOr(a.err, 1);
+      if (g + 1 < ngroups) mbar_wait(&bars[(g + 1) & 1], (par >> ((g + 1) & 1)) & 1u, kWaitLimit);
+      return;
+    }
     RP_MARK(1);
     In* const rw0 = (g & 1) ? raw1 : raw0;
     const int* ph = rph + (g & 1) * NB;
@@ -612,6 +703,11 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
       }
     }
     RP_MARK(5);
+    // the next group's edge elements (their buffer is not touched by this group)
+    if (en.at >= 0) (((g + 1) & 1) ? raw1 : raw0)[en.at] = en.v;
+    // this group's staging rows (also the FFT's scratch) are rewritten by the
+    // next bulk copy: order their generic-proxy accesses before it
+    fence_proxy_async();
     __syncthreads();
     RP_MARK(6);
   }
@@ -621,7 +717,6 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
            "fft %lld post %lld endsync %lld loop %lld\n", (int)FOLD, (int)fft, (int)blockIdx.z,
            ngroups, NB, rp_t[0], rp_t[1], rp_t[2], rp_t[3], rp_t[4], rp_t[5], rp_t[6], rp_t[7]);
 #endif
-  cp_async_wait<0>();
   if (FOLD) {
     bool finite = true;
     double* dst = a.bins_c[blockIdx.z] + ((int64_t)fc * M + x0) * W;
@@ -998,6 +1093,7 @@ void run_row_pass(const Plan& p, const FrameDesc& b1, const FrameDesc& b2, char*
     a.bins_c[k] = (double*)(ws + p.off_fbc[k]);
   }
   a.bad = (int*)(ws + p.off_bad);
+  a.err = (int*)(ws + p.off_err);
   a.M = p.M;
   a.fft_frames = p.single_kernel ? 1 : 2;
   a.Pw = p.Pw;

@@ -78,6 +78,7 @@ struct Plan {
   int Lmax;
   size_t off_kd;                   // double [n][t1*t1 + t2*t2]
   size_t off_bad;                  // int [n] non-finite input flags
+  size_t off_err;                  // int: set by a kernel whose copy did not complete in time
   size_t off_diag;                 // cbp_diag [n]
   size_t off_tw_h, off_tw_w;       // cpx<T_fft> twiddles exp(-2 pi i k / P), k < P
   size_t off_stw_h, off_stw_r;     // cpx<T_fft> stage twiddles of the column and row plans

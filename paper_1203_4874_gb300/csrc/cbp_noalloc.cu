@@ -77,7 +77,8 @@ extern "C" cbp_status cbp_estimate_kernels_noalloc(const cbp_frames* b1, const c
   const int kf64 = b1->dtype == CBP_F64 || (params->flags & CBP_FLAG_KERNELS_F64);
   const FrameDesc d1 = frame_desc(b1, nullptr), d2 = frame_desc(b2, nullptr);
   // the non-finite flags accumulate with atomics: they must start at zero
-  if (cudaMemsetAsync(ws + p.off_bad, 0, (size_t)p.n * sizeof(int), st) != cudaSuccess)
+  if (cudaMemsetAsync(ws + p.off_bad, 0, (size_t)p.n * sizeof(int), st) != cudaSuccess ||
+      cudaMemsetAsync(ws + p.off_err, 0, sizeof(int), st) != cudaSuccess)
     return CBP_ERR_CUDA;
   launch_eval(p, d1, d2, ws, st);
   launch_sample_solve(p, ws, st);

@@ -182,6 +182,7 @@ cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_param
   p.off_resid = take(std::max(resid, abytes));
   p.off_kd = take(n * (size_t)(t1 * t1 + t2 * t2) * 8);
   p.off_bad = take(n * 4);
+  p.off_err = take(4);
   p.off_diag = take(n * sizeof(cbp_diag));
   p.off_tw_h = take(p.Ph * ce);
   p.off_tw_w = take(p.Pw * ce);

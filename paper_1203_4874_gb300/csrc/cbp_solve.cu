@@ -938,6 +938,7 @@ struct ScaleArgs {
   const cd* X;          // [n][2][ns][nn]
   const double* sdiag;  // [n][2][ns][4]
   const int* bad;       // [n]
+  const int* err;       // set when a copy of an earlier kernel did not complete in time
   cd* ab;               // [n][4][M][M]  A_1, A_2, B_1, B_2
   double* kd;           // [n][t1*t1 + t2*t2]
   void* k1_out;
@@ -1022,7 +1023,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
       d.used_fallback = 0;
       d.pad_h = a.Ph;
       d.pad_w = a.Pw;
-      d.status = a.bad[f] ? CBP_ERR_INVALID_ARG : CBP_OK;
+      d.status = *a.err ? CBP_ERR_TIMEOUT : a.bad[f] ? CBP_ERR_INVALID_ARG : CBP_OK;
       a.diag[f] = d;
     }
     return;
@@ -1181,7 +1182,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
     dg.pad_w = a.Pw;
     dg.hard_samples = hard;
     int st = CBP_OK;
-    if (a.bad[f]) st = CBP_ERR_INVALID_ARG;
+    if (*a.err) st = CBP_ERR_TIMEOUT;
+    else if (a.bad[f]) st = CBP_ERR_INVALID_ARG;
     else if (!(x00[0].re != 0.0 || x00[0].im != 0.0) || !(x00[1].re != 0.0 || x00[1].im != 0.0))
       st = CBP_ERR_NOT_COPRIME;
     else if (gap < 1e-13) st = CBP_ERR_NOT_COPRIME;
@@ -1256,6 +1258,7 @@ void launch_scale_solve(const Plan& p, char* ws, void* k1_out, void* k2_out, int
   a.X = (const cd*)(ws + p.off_x);
   a.sdiag = (const double*)(ws + p.off_sdiag);
   a.bad = (const int*)(ws + p.off_bad);
+  a.err = (const int*)(ws + p.off_err);
   a.ab = (cd*)(ws + p.off_resid);  // reuses the residual scratch (sized for both)
   a.kd = (double*)(ws + p.off_kd);
   a.k1_out = k1_out;
