@@ -67,6 +67,27 @@ def algorithmic_bytes(stage: str, n: int) -> float | None:
     }.get(stage)
 
 
+def algorithmic_flops(stage: str, n: int) -> float | None:
+    """Floating-point operations a compute-bound stage must do per launch, for
+    n pairs, counted on the method's arithmetic (a complex multiply-add = 8):
+    per solved sample (M/2 + 1 per direction) the 2 (t1 + t2) - 1 Toeplitz
+    correlations over the channels' samples, and ~7 sweeps of parallel Jacobi
+    on the (t1 + t2)-square Hermitian normal matrix (every rotation updates
+    two rows and two columns of A and two columns of V)."""
+    if stage != "sample_solve":
+        return None
+    nn = T1 + T2
+    lags = 2 * nn - 1
+    corr = NS * lags * C * (H1 + W1) * 8                  # both directions
+    jacobi = 2 * NS * 7 * (nn - 1) * (nn // 2) * (3 * 2 * nn) * 8
+    return float(n * (corr + jacobi))
+
+
+def fp32_peak_tflops(sm_mhz: float) -> float:
+    """152 SMs x 128 FP32 lanes x 2 flops (FMA) x SM clock."""
+    return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
 STAGE_FILES = {"eval": "cbp_eval.cu", "sample_solve": "cbp_solve.cu", "scale_solve": "cbp_solve.cu",
                "kernel_spectra": "cbp_fft.cu", "row_fft": "cbp_fft.cu", "col_deconv": "cbp_fft.cu",
                "row_ifft": "cbp_fft.cu"}
@@ -535,6 +556,14 @@ def main():
                 "frac": achieved / peak, "peak_source": peak_kind,
                 "algorithmic_bytes_per_launch": alg, "ms_per_launch": dom_ms,
                 "traffic": measured_traffic(dom)}
+    elif algorithmic_flops(dom, n) is not None:
+        fl = algorithmic_flops(dom, n)
+        achieved = fl / (dom_ms / 1e3) / 1e12
+        mhz = clk.get("sm_mhz") or 2070.0
+        pk = fp32_peak_tflops(mhz)
+        roof = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                "frac": achieved / pk, "peak_source": f"derived: 152 SMs x 128 FP32 lanes x 2 x {mhz:.0f} MHz",
+                "algorithmic_flops_per_launch": fl, "ms_per_launch": dom_ms, "traffic": None}
     else:
         roof = {"bound": "alu", "kernel": dom, "achieved": None, "peak": None, "unit": None,
                 "frac": None, "ms_per_launch": dom_ms, "traffic": None}

@@ -192,8 +192,9 @@ __device__ __forceinline__ void stockham_stage(const cpx<T>* __restrict__ in,
 // nb transforms in shared memory (a, scratch b); returns the buffer with the
 // result.  tw: the plan's stage twiddles in shared memory.  Block-wide.
 template <typename T, bool Inv>
-__device__ cpx<T>* fft_block(cpx<T>* a, cpx<T>* b, const FftPlan& pl, int nb, const cpx<T>* tw) {
-  for (int s = 0; s < pl.nst; ++s) {
+__device__ cpx<T>* fft_block(cpx<T>* a, cpx<T>* b, const FftPlan& pl, int nb, const cpx<T>* tw,
+                             int first = 0) {
+  for (int s = first; s < pl.nst; ++s) {
     const FftStage& st = pl.st[s];
     const cpx<T>* t = tw + st.tw;
     switch (st.R) {
@@ -476,6 +477,57 @@ template <typename In> struct Edge {
   int at;   // index in the staging buffer, -1: none
 };
 
+// First Stockham stage (Ns = 1) of the forward row transforms, reading the
+// staged float/double rows directly: element m of row i is (x[2m], x[2m+1])
+// for the half-length transform (Pw even), else (x[m], 0), zero past W.
+// Pairs are read as one 8-byte load when the row's phase keeps them aligned.
+template <typename T, int R, typename In>
+__device__ __forceinline__ void stage_first_raw(const In* raw, const int* ph, int rw, int W, bool half,
+                                                cpx<T>* out, const FftStage& st, int N, int nb) {
+  const int Nr = st.Nr;
+  for (int idx = threadIdx.x; idx < nb * Nr; idx += blockDim.x) {
+    const int b = st.mNr ? (int)__umulhi((unsigned)idx, st.mNr) : idx;   // idx / Nr
+    const int j = idx - b * Nr;
+    const In* row = raw + b * rw + ph[b];
+    const bool pair8 = half && sizeof(In) == 4 && (ph[b] & 1) == 0;
+    cpx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int m = j + r * Nr;
+      if (half) {
+        const int c0 = 2 * m;
+        if (pair8 && c0 + 1 < W) {
+          const float2 x = *(const float2*)(row + c0);
+          v[r] = mk<T>((T)x.x, (T)x.y);
+        } else {
+          v[r] = mk<T>(c0 < W ? (T)row[c0] : (T)0, c0 + 1 < W ? (T)row[c0 + 1] : (T)0);
+        }
+      } else {
+        v[r] = mk<T>(m < W ? (T)row[m] : (T)0, (T)0);
+      }
+    }
+    small_dft<T, false, R>(v);
+    cpx<T>* dst = out + b * N + j * R;   // Ns = 1: outputs of butterfly j are contiguous
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[r] = v[r];
+  }
+}
+
+template <typename T, typename In>
+__device__ __forceinline__ void first_stage_raw(const In* raw, const int* ph, int rw, int W, bool half,
+                                                cpx<T>* out, const FftPlan& pl, int nb) {
+  const FftStage& st = pl.st[0];
+  switch (st.R) {
+    case 2: stage_first_raw<T, 2, In>(raw, ph, rw, W, half, out, st, pl.n, nb); break;
+    case 3: stage_first_raw<T, 3, In>(raw, ph, rw, W, half, out, st, pl.n, nb); break;
+    case 4: stage_first_raw<T, 4, In>(raw, ph, rw, W, half, out, st, pl.n, nb); break;
+    case 5: stage_first_raw<T, 5, In>(raw, ph, rw, W, half, out, st, pl.n, nb); break;
+    case 7: stage_first_raw<T, 7, In>(raw, ph, rw, W, half, out, st, pl.n, nb); break;
+    case 8: stage_first_raw<T, 8, In>(raw, ph, rw, W, half, out, st, pl.n, nb); break;
+    default: stage_first_raw<T, 9, In>(raw, ph, rw, W, half, out, st, pl.n, nb); break;
+  }
+}
+
 // Stage nr rows (row i at element offset rowoff(i) of fb) into the rows
 // dst + i * rw, each at its own 16-byte phase ph_i (element c of row i lands at
 // dst[i * rw + ph_i + c]).  Thread 0 moves each row's 16-byte-aligned body
@@ -641,35 +693,8 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
       }
     }
     RP_MARK(2);
-    if (fft) {
-      for (int i = 0; i < nr; ++i) {
-        const In* rowp = rw0 + i * a.rw + ph[i];
-        cpx<T>* dst = b0 + i * N;
-        if (a.half && sizeof(In) == 4 && (ph[i] & 1) == 0) {
-          // pairs (x[2m], x[2m+1]) are 8-byte aligned in the staging row
-          const float2* r2 = (const float2*)rowp;
-          const int full = W >> 1;
-          for (int m = threadIdx.x; m < N; m += blockDim.x) {
-            T x0 = 0, x1 = 0;
-            if (m < full) {
-              const float2 v = r2[m];
-              x0 = v.x;
-              x1 = v.y;
-            } else if (2 * m < W) {
-              x0 = (T)rowp[2 * m];
-            }
-            dst[m] = mk<T>(x0, x1);
-          }
-        } else if (a.half) {
-          for (int m = threadIdx.x; m < N; m += blockDim.x) {
-            const int c0 = 2 * m, c1 = 2 * m + 1;
-            dst[m] = mk<T>(c0 < W ? (T)rowp[c0] : (T)0, c1 < W ? (T)rowp[c1] : (T)0);
-          }
-        } else {
-          for (int m = threadIdx.x; m < N; m += blockDim.x) dst[m] = mk<T>(m < W ? (T)rowp[m] : (T)0, (T)0);
-        }
-      }
-    }
+    // first FFT stage straight from the staging rows into b0
+    if (fft) first_stage_raw<T, In>(rw0, ph, a.rw, W, a.half, b0, a.pl, nr);
     __syncthreads();
     RP_MARK(3);
     if (FOLD) {
@@ -685,7 +710,7 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
       // the staging rows of this group are consumed: they serve as the
       // FFT's second buffer when large enough
       cpx<T>* b1 = L.b1_alias ? (cpx<T>*)rw0 : (cpx<T>*)(smem + L.b1);
-      cpx<T>* Z = fft_block<T, false>(b0, b1, a.pl, nr, tw);
+      cpx<T>* Z = fft_block<T, false>(b0, b1, a.pl, nr, tw, 1);
       RP_MARK(4);
       for (int i = 0; i < nr; ++i) {
         const cpx<T>* z = Z + i * N;

@@ -450,9 +450,11 @@ __device__ int hard_eig(EigSmem& S, int n, int np, int ld, double gscale, long l
 // acc_easy / acc_hard: Newton steps against the exact residual (apply) for
 // samples resolved in single precision / in double precision; the latter only
 // where the double gap lambda_2 - lambda_1 is below hard_gap lambda_max.
+// newton_tol: the Newton steps on the normal matrix stop once a step moves x
+// (unit norm) by less than this.
 template <class Apply>
 __device__ EigResult smallest_eigvec(EigSmem& S, int n, bool real, int acc_easy, int acc_hard,
-                                     double hard_gap, const Apply& apply,
+                                     double hard_gap, double newton_tol, const Apply& apply,
                                      long long* tk = nullptr) {
   const int np = np_of(n), ld = np + 1;
   if (threadIdx.x == 0) {
@@ -522,7 +524,7 @@ __device__ EigResult smallest_eigvec(EigSmem& S, int n, bool real, int acc_easy,
       matvec64(S.G, S.x, S.r, n);
       theta = dotre64(S.x, S.r, n, S.red);
       const double d2 = newton_eigbasis64(S, V64, S.lam, n, ld, imin, S.r, theta);
-      if (d2 < 1e-30 || d2 > 0.25 * d2prev) break;
+      if (d2 < newton_tol * newton_tol || d2 > 0.25 * d2prev) break;
       d2prev = d2;
     }
     if (threadIdx.x == 0) S.flag[3] = it + 1;
@@ -911,7 +913,10 @@ __global__ void __launch_bounds__(kSolveThreads) k_sample_solve(SampleArgs a) {
   ap.y = a.resid + (((int64_t)f * 2 + ps) * a.ns + s) * a.C * (int64_t)a.Lmax;
   ap.red = S.red;
   ap.real = real;
+  // mixed path: null vectors to ~1e-9 keep the kernels ~1e-4 from the FP64
+  // path at the worst conditioning met (bar 1e-3); FP64 path: to the floor
   const EigResult res = smallest_eigvec(S, n, real, a.mixed ? 0 : 2, 1, a.mixed ? 1e-6 : 1e300,
+                                       a.mixed ? 1e-9 : 1e-15,
                                        ap, tk);
   CBP_TICK(tk, 5);
 #ifdef CBP_PHASE_TIMING
@@ -1084,7 +1089,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
   }
   __syncthreads();
   ScaleApply ap{ab, M};
-  EigResult res = smallest_eigvec(S, n, false, 2, 1, 1e300, ap);
+  EigResult res = smallest_eigvec(S, n, false, 2, 1, 1e300, 1e-15, ap);
   // X_k[i][j] = (gamma_j A_k[i][j] + delta_i B_k[i][j]) / 2
   for (int idx = threadIdx.x; idx < 2 * MM; idx += blockDim.x) {
     const int k = idx / MM, i = (idx % MM) / M, j = idx % M;
