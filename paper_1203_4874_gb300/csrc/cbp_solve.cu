@@ -232,7 +232,9 @@ __device__ void jacobi(E* A, E* V, int n, int npad, int ld, EigSmem& S, R tol_re
         A[q * ld + j] = cj_(sp) * apj + c * aqj;
       }
       __syncthreads();
-      // columns p, q:  A <- A J,  V <- V J
+      // columns p, q:  A <- A J,  V <- V J.  The rotated pair's own entries
+      // are set exactly: a_pq = a_qp = 0, a_pp and a_qq real (only this
+      // thread of rows p and q writes them).
       for (int idx = tid; idx < half * n; idx += nth) {
         const int k = idx / n, i = idx % n;
         const E sp = rs[k];
@@ -240,21 +242,19 @@ __device__ void jacobi(E* A, E* V, int n, int npad, int ld, EigSmem& S, R tol_re
         const int p = S.rp[k], q = S.rq[k];
         const R c = rc[k];
         const E aip = A[i * ld + p], aiq = A[i * ld + q];
-        A[i * ld + p] = c * aip - cj_(sp) * aiq;
-        A[i * ld + q] = sp * aip + c * aiq;
+        E np = c * aip - cj_(sp) * aiq, nq = sp * aip + c * aiq;
+        if (i == p) {
+          Ops<E>::clear_im(np);
+          nq = Ops<E>::z();
+        } else if (i == q) {
+          np = Ops<E>::z();
+          Ops<E>::clear_im(nq);
+        }
+        A[i * ld + p] = np;
+        A[i * ld + q] = nq;
         const E vip = V[i * ld + p], viq = V[i * ld + q];
         V[i * ld + p] = c * vip - cj_(sp) * viq;
         V[i * ld + q] = sp * vip + c * viq;
-      }
-      __syncthreads();
-      for (int k = tid; k < half; k += nth) {
-        const E sp = rs[k];
-        if (!Ops<E>::nz(sp)) continue;
-        const int p = S.rp[k], q = S.rq[k];
-        A[p * ld + q] = Ops<E>::z();
-        A[q * ld + p] = Ops<E>::z();
-        Ops<E>::clear_im(A[p * ld + p]);
-        Ops<E>::clear_im(A[q * ld + q]);
       }
       __syncthreads();
     }
@@ -689,17 +689,17 @@ __device__ void correlations_real(const SamplePolys<double, double>& P, int C, i
 struct FF {
   float hi = 0.f, lo = 0.f;
   // += a * b for float-float a, b: exact product of the high parts (FMA) plus
-  // the cross terms, added with TwoSum and renormalised.
+  // the cross terms; the high part by TwoSum, every rounding term into lo
+  // (renormalised only when sums are combined: over a lane's ~100 terms lo
+  // stays ~1e-13 of the diagonal of the normal matrix).
   __device__ __forceinline__ void mac(float ah, float al, float bh, float bl) {
     const float p = ah * bh;
     float e = fmaf(ah, bh, -p);
     e = fmaf(ah, bl, fmaf(al, bh, e));
     const float t = hi + p;
     const float z = t - hi;
-    const float err = (hi - (t - z)) + (p - z);
-    const float l = lo + err + e;
-    hi = t + l;                    // renormalise (Fast2Sum, |t| >= |l|)
-    lo = l - (hi - t);
+    lo += ((hi - (t - z)) + (p - z)) + e;
+    hi = t;
   }
   __device__ __forceinline__ void add(float bh, float bl) {
     const float t = hi + bh;
