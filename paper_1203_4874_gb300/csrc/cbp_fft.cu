@@ -922,17 +922,18 @@ k_col_deconv(ColArgs a) {
   const T eps = (T)a.eps;
   for (int idx = threadIdx.x; idx < CW * Ph; idx += blockDim.x) {
     const int u = idx / CW, vl = idx % CW;
-    if (vl >= nv) continue;
-    const cpx<T> k1 = K1[(int64_t)u * a.Pw2p + vl];
-    cpx<T> num = cmulc(k1, r1[idx]);
-    T den = abs2(k1) + eps;
-    if (!a.single) {
-      const cpx<T> k2 = K2[(int64_t)u * a.Pw2p + vl];
-      num = num + cmulc(k2, r2[idx]);
-      den += abs2(k2);
+    if (vl < nv) {
+      const cpx<T> k1 = ldg_cpx(K1 + (int64_t)u * a.Pw2p + vl);
+      const cpx<T> k2 = a.single ? mk<T>(0, 0) : ldg_cpx(K2 + (int64_t)u * a.Pw2p + vl);
+      cpx<T> num = cmulc(k1, r1[idx]);
+      T den = abs2(k1) + eps;
+      if (!a.single) {
+        num = num + cmulc(k2, r2[idx]);
+        den += abs2(k2);
+      }
+      const T inv = den != (T)0 ? (T)1 / den : (T)0;
+      r1[idx] = inv * num;
     }
-    const T inv = den != (T)0 ? (T)1 / den : (T)0;
-    r1[idx] = inv * num;
   }
   __syncthreads();
   cpx<T>* res = fft_block_il<T, true, CW>(r1, a.single ? free1 : free2, a.pl, tw);
@@ -948,6 +949,7 @@ struct IRowArgs {
   void* latent;      // TO [n][C][H][W]
   const uint64_t* lat_tab;  // optional per-pair latent addresses ([C][H][W] each)
   int out_f64;
+  int* err;          // set when a copy does not complete in time
   int n, H, W, Pw, Pw2, Pw2p, half, nbr;
   double scale;      // 1 / (Ph * Pw)
   FftPlan pl;
@@ -958,7 +960,7 @@ struct IRowArgs {
 // aligned); the FFT's second buffer is the consumed staging rows when a row
 // fits in them (N <= Pw2p, the half-length transform), else its own.
 struct IRowSmem {
-  size_t tw, b0, b1, raw0, raw1, total;
+  size_t tw, b0, b1, raw0, raw1, mbar, total;
   bool b1_alias;
 };
 __host__ __device__ inline IRowSmem irow_layout(int N, int ntw, int Pw2p, int nbr, size_t ce) {
@@ -975,27 +977,77 @@ __host__ __device__ inline IRowSmem irow_layout(int N, int ntw, int Pw2p, int nb
   o += rp_align((size_t)nbr * Pw2p * ce);
   L.raw1 = o;
   o += rp_align((size_t)nbr * Pw2p * ce);
+  L.mbar = o;
+  o += rp_align(2 * sizeof(uint64_t));
   L.total = o;
   return L;
 }
 
-// cp.async of nr spectrum rows (Pw2 entries each, 16-byte aligned rows of
-// pitch Pw2p) into dst rows of pitch Pw2p; the last chunk may be partial.
+// Bulk (TMA) copies of nr spectrum rows (whole rows of pitch Pw2p, 16-byte
+// aligned) into dst rows of the same pitch, completing on `bar` (thread 0).
 template <typename T, class RowPtr>
-__device__ __forceinline__ void stage_spec_rows_async(cpx<T>* dst, const RowPtr& rowp, int nr,
-                                                      int Pw2, int Pw2p) {
-  constexpr int E = 16 / (int)sizeof(cpx<T>);
-  const int tasks = (Pw2 + E - 1) / E;
-  for (int idx = threadIdx.x; idx < nr * tasks; idx += blockDim.x) {
-    const int i = idx / tasks, c0 = (idx - i * tasks) * E;
-    cp_async16(dst + i * Pw2p + c0, rowp(i) + c0, min(E, Pw2 - c0) * (int)sizeof(cpx<T>));
+__device__ __forceinline__ void stage_spec_rows_bulk(cpx<T>* dst, const RowPtr& rowp, int nr,
+                                                     int Pw2p, uint64_t* bar) {
+  if (threadIdx.x == 0) {
+    const uint32_t bytes = (uint32_t)(Pw2p * sizeof(cpx<T>));
+    mbar_expect_tx(bar, bytes * (uint32_t)nr);
+    for (int i = 0; i < nr; ++i) bulk_g2s(dst + i * Pw2p, rowp(i), bytes, bar);
+  }
+}
+
+// First inverse Stockham stage (Ns = 1), reading the staged spectrum rows
+// directly: element m of the half-length transform is E + i O, E and O the
+// even and odd parts of X[m] and conj(X[N - m]) (O with the twiddle
+// exp(+2 pi i m / Pw)); for odd Pw, element m is the Hermitian extension of X.
+template <typename T, int R>
+__device__ __forceinline__ void stage_first_spec(const cpx<T>* raw, int Pw2p, const cpx<T>* tw_w,
+                                                 bool half, int Pw2, cpx<T>* out,
+                                                 const FftStage& st, int N, int nb) {
+  const int Nr = st.Nr;
+  for (int idx = threadIdx.x; idx < nb * Nr; idx += blockDim.x) {
+    const int b = st.mNr ? (int)__umulhi((unsigned)idx, st.mNr) : idx;   // idx / Nr
+    const int j = idx - b * Nr;
+    const cpx<T>* Xr = raw + b * Pw2p;
+    cpx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int m = j + r * Nr;
+      if (half) {
+        const cpx<T> xk = Xr[m], xc = conj(Xr[N - m]);
+        const cpx<T> e = (T)0.5 * (xk + xc), d = (T)0.5 * (xk - xc);
+        const cpx<T> o = conj(ldg_cpx(tw_w + m)) * d;   // exp(+2 pi i m / Pw) d
+        v[r] = mk<T>(e.re - o.im, e.im + o.re);          // E + i O
+      } else {
+        v[r] = m < Pw2 ? Xr[m] : conj(Xr[N - m]);
+      }
+    }
+    small_dft<T, true, R>(v);
+    cpx<T>* dst = out + b * N + j * R;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[r] = v[r];
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void first_stage_spec(const cpx<T>* raw, int Pw2p, const cpx<T>* tw_w,
+                                                 bool half, int Pw2, cpx<T>* out, const FftPlan& pl,
+                                                 int nb) {
+  const FftStage& st = pl.st[0];
+  switch (st.R) {
+    case 2: stage_first_spec<T, 2>(raw, Pw2p, tw_w, half, Pw2, out, st, pl.n, nb); break;
+    case 3: stage_first_spec<T, 3>(raw, Pw2p, tw_w, half, Pw2, out, st, pl.n, nb); break;
+    case 4: stage_first_spec<T, 4>(raw, Pw2p, tw_w, half, Pw2, out, st, pl.n, nb); break;
+    case 5: stage_first_spec<T, 5>(raw, Pw2p, tw_w, half, Pw2, out, st, pl.n, nb); break;
+    case 7: stage_first_spec<T, 7>(raw, Pw2p, tw_w, half, Pw2, out, st, pl.n, nb); break;
+    case 8: stage_first_spec<T, 8>(raw, Pw2p, tw_w, half, Pw2, out, st, pl.n, nb); break;
+    default: stage_first_spec<T, 9>(raw, Pw2p, tw_w, half, Pw2, out, st, pl.n, nb); break;
   }
 }
 
 // Inverse complex-to-real FFT of every row, crop and scale.  A block owns the
 // rows x, x + X, ... (x = blockIdx.x, X = gridDim.x) of one frame channel, nbr
-// at a time, the next group's spectrum rows in flight (cp.async) while the
-// current group is transformed.
+// at a time, the next group's spectrum rows in flight (bulk copies on an
+// mbarrier per staging buffer) while the current group is transformed.
 template <typename T>
 __global__ void __launch_bounds__(kRowPassThreads)
 k_row_ifft(IRowArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
@@ -1006,6 +1058,14 @@ k_row_ifft(IRowArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
   cpx<T>* b0 = (cpx<T>*)(smem + L.b0);
   cpx<T>* const raw0 = (cpx<T>*)(smem + L.raw0);
   cpx<T>* const raw1 = (cpx<T>*)(smem + L.raw1);
+  uint64_t* bars = (uint64_t*)(smem + L.mbar);
+  if (threadIdx.x == 0) {
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t par = 0u;   // bit b: phase parity of buffer b's next completion
   load_twiddles(tw, stw, a.pl.ntw);
   const int fc = blockIdx.y;
   const int x0 = blockIdx.x, X = gridDim.x;
@@ -1021,38 +1081,31 @@ k_row_ifft(IRowArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
     obase = (int64_t)(fc % C) * a.H * a.W;
   }
   if (ngroups > 0)
-    stage_spec_rows_async<T>(raw0, [&](int i) { return src + (int64_t)row_of(0, i) * a.Pw2p; },
-                             min(NB, nrows), a.Pw2, a.Pw2p);
-  cp_async_commit();
+    stage_spec_rows_bulk<T>(raw0, [&](int i) { return src + (int64_t)row_of(0, i) * a.Pw2p; },
+                            min(NB, nrows), a.Pw2p, &bars[0]);
   const T sc = (T)a.scale;
   for (int g = 0; g < ngroups; ++g) {
     const int nr = min(NB, nrows - g * NB);
     if (g + 1 < ngroups) {
       const int g1 = g + 1;
-      stage_spec_rows_async<T>((g1 & 1) ? raw1 : raw0,
-                               [&](int i) { return src + (int64_t)row_of(g1, i) * a.Pw2p; },
-                               min(NB, nrows - g1 * NB), a.Pw2, a.Pw2p);
+      stage_spec_rows_bulk<T>((g1 & 1) ? raw1 : raw0,
+                              [&](int i) { return src + (int64_t)row_of(g1, i) * a.Pw2p; },
+                              min(NB, nrows - g1 * NB), a.Pw2p, &bars[g1 & 1]);
     }
-    cp_async_commit();
-    cp_async_wait<1>();
-    __syncthreads();
+    const bool arrived = mbar_wait(&bars[g & 1], (par >> (g & 1)) & 1u, kWaitLimit);
+    par ^= 1u << (g & 1);
+    if (__syncthreads_or(!arrived)) {
+      // a copy did not complete in time: report it, wait (bounded) for the
+      // other buffer's copies still in flight, and leave
+      if (threadIdx.x == 0) atomicOr(a.err, 1);
+      if (g + 1 < ngroups) mbar_wait(&bars[(g + 1) & 1], (par >> ((g + 1) & 1)) & 1u, kWaitLimit);
+      return;
+    }
     cpx<T>* const rw0 = (g & 1) ? raw1 : raw0;
-    for (int i = 0; i < nr; ++i) {
-      const cpx<T>* Xr = rw0 + i * a.Pw2p;
-      cpx<T>* dst = b0 + i * N;
-      for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        if (a.half) {
-          const cpx<T> xk = Xr[k], xc = conj(Xr[N - k]);
-          const cpx<T> e = (T)0.5 * (xk + xc), d = (T)0.5 * (xk - xc);
-          const cpx<T> o = conj(ldg_cpx(tw_w + k)) * d;   // exp(+2 pi i k / Pw) d
-          dst[k] = mk<T>(e.re - o.im, e.im + o.re);        // E + i O
-        } else {
-          dst[k] = k < a.Pw2 ? Xr[k] : conj(Xr[N - k]);
-        }
-      }
-    }
+    // first inverse stage straight from the staged spectrum rows into b0
+    first_stage_spec<T>(rw0, a.Pw2p, tw_w, a.half, a.Pw2, b0, a.pl, nr);
     __syncthreads();
-    cpx<T>* Z = fft_block<T, true>(b0, L.b1_alias ? rw0 : (cpx<T>*)(smem + L.b1), a.pl, nr, tw);
+    cpx<T>* Z = fft_block<T, true>(b0, L.b1_alias ? rw0 : (cpx<T>*)(smem + L.b1), a.pl, nr, tw, 1);
     for (int i = 0; i < nr; ++i) {
       const cpx<T>* z = Z + i * N;
       const int64_t ob = obase + (int64_t)row_of(g, i) * a.W;
@@ -1073,9 +1126,11 @@ k_row_ifft(IRowArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
         }
       }
     }
+    // the staging rows of this group (also the FFT's scratch) are rewritten
+    // by a later bulk copy: order their generic-proxy accesses before it
+    fence_proxy_async();
     __syncthreads();
   }
-  cp_async_wait<0>();
 }
 
 
@@ -1202,6 +1257,7 @@ void run_row_ifft(const Plan& p, char* ws, void* latent, int out_f64, cudaStream
   a.latent = latent;
   a.lat_tab = lat_tab;
   a.out_f64 = out_f64;
+  a.err = (int*)(ws + p.off_err);
   a.n = p.n;
   a.H = p.H;
   a.W = p.W;
