@@ -113,7 +113,8 @@ typedef struct cbp_diag {
   int32_t used_fallback;   /* learned path: 1 if the GCD solve ran                 */
   int32_t pad_h, pad_w;    /* FFT grid used                                        */
   int32_t status;          /* cbp_status derived from the fields above             */
-  int32_t hard_samples;    /* samples solved by double-precision inverse iteration */
+  int32_t hard_samples;    /* samples whose two smallest normal-matrix eigenvalues
+                              are within 1e-4 of the largest (near-degenerate)  */
 } cbp_diag;
 
 typedef struct cbp_ctx cbp_ctx;

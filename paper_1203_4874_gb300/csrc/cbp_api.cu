@@ -8,6 +8,9 @@
 #include <new>
 #include "cbp.h"
 #include "cbp_internal.h"
+#ifdef CBP_DEBUG_ERRORS
+#include <cstdio>
+#endif
 #include "cbp_serve.h"
 
 namespace cbp {
@@ -227,7 +230,11 @@ cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
       return CBP_ERR_CUDA;
     end(CBP_STAGE_D2H, 0);
   }
-  if (cudaGetLastError() != cudaSuccess) return CBP_ERR_CUDA;
+  const cudaError_t ce = cudaGetLastError();
+#ifdef CBP_DEBUG_ERRORS
+  if (ce != cudaSuccess) fprintf(stderr, "cbp: %s\n", cudaGetErrorString(ce));
+#endif
+  if (ce != cudaSuccess) return CBP_ERR_CUDA;
   return CBP_OK;
 }
 

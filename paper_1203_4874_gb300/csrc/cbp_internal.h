@@ -73,6 +73,7 @@ struct Plan {
   size_t off_pz2f[2], off_pz1f[2]; // cdf float-float copies for the mixed path's Gram
   size_t off_fbr[2], off_fbc[2];   // double [n][C][M][H_Bk] row / [n][C][M][W_Bk] column fold bins
   size_t off_x;                    // cd [n][2][ns][nn]
+  size_t off_gall;                 // cd [n][2][ns][nn][nn] per-sample normal matrices
   size_t off_sdiag;                // double [n][2][ns][4]
   size_t off_resid;                // cd [n][2][ns][C][Lmax] (FP64 path residual scratch)
   int Lmax;

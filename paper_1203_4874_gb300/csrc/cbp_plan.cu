@@ -175,6 +175,7 @@ cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_param
     p.off_fbc[k] = take(n * C * (size_t)p.M * (k ? p.W2 : p.W1) * 8);
   }
   p.off_x = take(n * 2 * ns * p.nn * 16);
+  p.off_gall = take(n * 2 * ns * (size_t)p.nn * p.nn * 16);
   p.off_sdiag = take(n * 2 * ns * 4 * 8);
   p.Lmax = std::max(p.H1, p.W1) + t2 - 1;
   const size_t resid = n * 2 * ns * C * (size_t)p.Lmax * 16;

@@ -1,28 +1,27 @@
 // A2-A5: per-sample cofactor solve, scale fix between the two evaluation
 // orders, and the spatial kernels (Eq. 4; Sections 4-5).
 //
-// Per sample (one CTA each): the 1D cofactor pair x = [u; v] (u ~ k1, v ~ k2
+// Per sample: the 1D cofactor pair x = [u; v] (u ~ k1, v ~ k2
 // at that sample) spans the null space of the Sylvester matrix
 // S = [-C_t1(b2) | C_t2(b1)], channels' rows stacked, since b1 k2 - b2 k1 = 0
 // (Eq. 4).  The paper factors Bezout matrices by a CPU SVD (Section 5); here
 // the normal matrix G = S^H S is formed on the device from correlations --
 // its blocks are Toeplitz, (C_t(a)^H C_s(b))[p][q] = rho_ab(p - q) with
-// rho_ab(d) = sum_m conj(a[m]) b[m + d] -- and its smallest eigenvector is
-// found by:
-//   1. cyclic parallel Jacobi in single precision (all eigenpairs);
-//   2. samples whose two smallest eigenvalues the single-precision solve
-//      resolves ("easy"): double-precision Newton steps on G with the
-//      single-precision eigenbasis as preconditioner;
-//      otherwise ("hard", e.g. the z = 1 sample, whose lower spectrum is a
-//      cluster of noise-level eigenvalues, or noise-free input): the same
-//      Jacobi in double precision;
-//   3. FP64 path only: one more Newton step whose residual S^H S x is computed
-//      from S itself (convolutions), which removes the squared conditioning of
-//      the normal matrix.
+// rho_ab(d) = sum_m conj(a[m]) b[m + d] -- by one CTA per sample
+// (k_sample_gram), and its smallest eigenvector is found by one warp per
+// sample (k_sample_solve, cbp_tri.cuh):
+//   1. Householder reduction to a real tridiagonal T in double precision;
+//   2. Sturm-count multisection for the two smallest eigenvalues of T;
+//   3. inverse iteration on T, x = Q y;
+//   4. Newton steps (Olsen's form, solved through T) whose residual S^H S x
+//      is computed from S itself (convolutions), which removes the squared
+//      conditioning of the normal matrix: FP64 path always, mixed path where
+//      the two smallest eigenvalues are nearly degenerate (the z = 1
+//      samples, whose lower spectrum is a cluster of noise-level eigenvalues).
 // Only samples s <= M/2 are solved; sample M - s is the conjugate.
 //
 // Per pair (one CTA): lift the cofactors to the two M x M estimates of the
-// kernels' 2D DFT, solve the least-squares scale system (same eigen-solver on
+// kernels' 2D DFT, solve the least-squares scale system (block Jacobi eigen-solver on
 // its 2M x 2M normal matrix, exact residual in the FP64 path), average,
 // normalise to unit kernel sum, inverse M x M DFT (Section 5).
 #include "cbp_common.cuh"
@@ -609,7 +608,9 @@ struct SampleArgs {
   double* sdiag;             // [n][2][ns][4]
   cd* resid;                 // [n][2][ns][C][Lmax]
   const int* accepted;       // learned path: pairs whose proposal passed the gate (skipped)
+  cd* G;                     // [n][2][ns][nn][nn] normal matrices
   int Lmax, C, ns, t1, t2, nn, M, mixed;
+  int nfr;                   // pairs in the call
 };
 
 // Sample polynomial element m of frame k (0: b1, 1: b2) as cpx<TA>.
@@ -799,11 +800,15 @@ __device__ void gram_from_rho(const cd* rho, int t1, int t2, cd* G) {
 
 // Accurate S^H S x for the FP64 path: y = S x per channel in the global
 // scratch, then the correlations with b1, b2.
+#include "cbp_tri.cuh"
+
+// S^H S x from the double samples (the exact operator of the refinement
+// steps; y holds S x), by the whole CTA (BLOCK) or by the calling warp.
+template <bool BLOCK>
 struct SylvesterApply {
   SamplePolys<double, double> P;
   cd* y;            // [C][L]
   int C, t1, t2, L;
-  double* red;
   bool real;        // real sample (z = 1, or z = -1 for even M): real arithmetic
   __device__ void operator()(const cd* x, cd* out) const {
     if (real) apply_real(x, out);
@@ -811,7 +816,11 @@ struct SylvesterApply {
   }
   // real samples: P and x are real, so are S x and S^T S x
   __device__ void apply_real(const cd* x, cd* out) const {
-    for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int tid = BLOCK ? threadIdx.x : lane, nth = BLOCK ? blockDim.x : 32;
+    const int wid = BLOCK ? threadIdx.x >> 5 : 0, nw = BLOCK ? blockDim.x >> 5 : 1;
+    team_sync<BLOCK>();
+    for (int idx = tid; idx < C * L; idx += nth) {
       const int ch = idx / L, i = idx % L;
       double acc = 0.0;
       for (int q = 0; q < t2; ++q) {     // b1 * v
@@ -824,10 +833,9 @@ struct SylvesterApply {
       }
       y[idx] = mk(acc, 0.0);
     }
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    team_sync<BLOCK>();
     const int n = t1 + t2;
-    for (int o = warp; o < n; o += nw) {
+    for (int o = wid; o < n; o += nw) {
       const int k = o < t1 ? 1 : 0;
       const int sh = o < t1 ? o : o - t1;
       double acc = 0.0;
@@ -836,10 +844,14 @@ struct SylvesterApply {
       const double re = warp_sum(acc);
       if (lane == 0) out[o] = mk(o < t1 ? -re : re, 0.0);
     }
-    __syncthreads();
+    team_sync<BLOCK>();
   }
   __device__ void apply_complex(const cd* x, cd* out) const {
-    for (int idx = threadIdx.x; idx < C * L; idx += blockDim.x) {
+    const int lane = threadIdx.x & 31;
+    const int tid = BLOCK ? threadIdx.x : lane, nth = BLOCK ? blockDim.x : 32;
+    const int wid = BLOCK ? threadIdx.x >> 5 : 0, nw = BLOCK ? blockDim.x >> 5 : 1;
+    team_sync<BLOCK>();
+    for (int idx = tid; idx < C * L; idx += nth) {
       int ch = idx / L, i = idx % L;
       cd acc = mk(0.0, 0.0);
       for (int q = 0; q < t2; ++q) {     // b1 * v
@@ -857,10 +869,9 @@ struct SylvesterApply {
       }
       y[idx] = acc;
     }
-    __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    team_sync<BLOCK>();
     const int n = t1 + t2;
-    for (int o = warp; o < n; o += nw) {
+    for (int o = wid; o < n; o += nw) {
       const int k = o < t1 ? 1 : 0;       // u rows use b2, v rows use b1
       const int sh = o < t1 ? o : o - t1;
       cd acc = mk(0.0, 0.0);
@@ -869,23 +880,16 @@ struct SylvesterApply {
       double re = warp_sum(acc.re), im = warp_sum(acc.im);
       if (lane == 0) out[o] = o < t1 ? mk(-re, -im) : mk(re, im);
     }
-    __syncthreads();
+    team_sync<BLOCK>();
   }
 };
 
-__global__ void __launch_bounds__(kSolveThreads) k_sample_solve(SampleArgs a) {
-  extern __shared__ __align__(16) char smem[];
-  // The sample index varies slowest, so the z = 1 and neighbouring samples
-  // of every pair -- the slow ones, resolved in double precision -- start
-  // first and the short samples fill in behind them.
+// A2: per sample, the correlations and the Toeplitz-block normal matrix, into
+// the global array of normal matrices.
+__global__ void __launch_bounds__(kSolveThreads) k_sample_gram(SampleArgs a) {
+  __shared__ cd rho[4 * kMaxN];
   const int f = blockIdx.x, ps = blockIdx.y, s = blockIdx.z;
   if (a.accepted && a.accepted[f]) return;   // the proposal stands; nothing to solve
-  const int n = a.nn;
-  EigSmem S;
-  char* p = carve_eig(S, smem, n);
-  cd* rho = (cd*)p;
-  long long tk[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
-  CBP_TICK(tk, 0);
   // Real samples (z = 1; z = -1 when M is even) have real Gram matrices.
   const bool real = s == 0 || 2 * s == a.M;
   const SamplePolys<double, double> P64 =
@@ -893,48 +897,86 @@ __global__ void __launch_bounds__(kSolveThreads) k_sample_solve(SampleArgs a) {
   if (real) correlations_real(P64, a.C, a.t1, a.t2, rho);
   else if (a.mixed) correlations_ff(a.pzf[ps], a.len[ps], f, a.C, a.ns, s, a.t1, a.t2, rho);
   else correlations(P64, a.C, a.t1, a.t2, rho);
-  CBP_TICK(tk, 1);
-  gram_from_rho(rho, a.t1, a.t2, S.G);
-  CBP_TICK(tk, 2);
-  // Newton steps against the exact residual S^H S x from the double samples
-  // (they remove the squared conditioning of the normal matrix).  FP64 path:
-  // two for samples resolved in single precision, one after the double
-  // Jacobi of the others.  Mixed path: none where single precision resolved
-  // the sample (its float-float / double normal matrix is accurate to ~1e-13),
-  // one after the double Jacobi where the two smallest eigenvalues are closer
-  // than 1e-6 lambda_max (the z = 1 samples: ~1e-8 apart, where the normal
-  // matrix alone leaves ~1e-5 in x).
-  SylvesterApply ap;
-  ap.P = P64;
-  ap.C = a.C;
-  ap.t1 = a.t1;
-  ap.t2 = a.t2;
-  ap.L = a.len[ps][0] + a.t2 - 1;
-  ap.y = a.resid + (((int64_t)f * 2 + ps) * a.ns + s) * a.C * (int64_t)a.Lmax;
-  ap.red = S.red;
-  ap.real = real;
-  // mixed path: null vectors to ~1e-9 keep the kernels ~1e-4 from the FP64
-  // path at the worst conditioning met (bar 1e-3); FP64 path: to the floor
-  const EigResult res = smallest_eigvec(S, n, real, a.mixed ? 0 : 2, 1, a.mixed ? 1e-6 : 1e300,
-                                       a.mixed ? 1e-9 : 1e-15,
-                                       ap, tk);
-  CBP_TICK(tk, 5);
-#ifdef CBP_PHASE_TIMING
-  if (threadIdx.x == 0 && f < 2)
-    printf("sample f=%d pass=%d s=%d real=%d hard=%d | corr %lld gram %lld jacobi32 %lld refine %lld "
-           "tail %lld | mgs %lld xform %lld jacobi64 %lld (%d sweeps, %d newton)\n",
-           f, ps, s, (int)real, res.hard, tk[1] - tk[0], tk[2] - tk[1], tk[3] - tk[2],
-           tk[4] - tk[3], tk[5] - tk[4], res.hard ? tk[6] - tk[3] : 0LL,
-           res.hard ? tk[7] - tk[6] : 0LL, res.hard ? tk[8] - tk[7] : 0LL, S.flag[1],
-           res.hard ? 0 : S.flag[3]);
-#endif
   const int64_t o = ((int64_t)f * 2 + ps) * a.ns + s;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) a.X[o * n + i] = S.x[i];
-  if (threadIdx.x == 0) {
+  gram_from_rho(rho, a.t1, a.t2, a.G + o * a.nn * a.nn);
+}
+
+// A3: the null vector of every sample's normal matrix (tridiagonal
+// reduction, Sturm multisection, inverse iteration, refinement steps against
+// S^H S as configured below).  The first nreal CTAs take one real sample each
+// (z = 1, and z = -1 for even M: their refinement, the costliest step, runs
+// on the whole CTA); the others take one complex sample per warp.
+__global__ void k_sample_solve(SampleArgs a, int nreal) {
+  extern __shared__ __align__(16) char smem[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpc = blockDim.x >> 5;
+  const int n = a.nn;
+  const int nrs = (a.M % 2 == 0) ? 2 : 1, ncs = a.ns - nrs;   // real / complex samples per pass
+  const bool real = (int)blockIdx.x < nreal;
+  int f, ps, s;
+  if (real) {
+    const int r = blockIdx.x;
+    f = r / (2 * nrs);
+    ps = (r / nrs) & 1;
+    s = (r % nrs) ? a.M / 2 : 0;
+  } else {
+    const int c = ((int)blockIdx.x - nreal) * wpc + warp;
+    if (c >= a.nfr * 2 * ncs) return;          // whole warp leaves together
+    f = c / (2 * ncs);
+    ps = (c / ncs) & 1;
+    s = 1 + c % ncs;
+  }
+  if (a.accepted && a.accepted[f]) return;   // the proposal stands; nothing to solve
+  const int64_t o = ((int64_t)f * 2 + ps) * a.ns + s;
+  const TriWs W = carve_tri(smem + (real ? 0 : (size_t)warp * tri_ws_bytes(n)), n);
+  const cd* G = a.G + o * n * n;
+#ifdef CBP_PHASE_TIMING
+  long long tkv[6] = {0, 0, 0, 0, 0, 0};
+  long long* tk = f == 0 ? tkv : nullptr;
+#else
+  long long* tk = nullptr;
+#endif
+  // Refinement against S^H S (it removes the squared conditioning of the
+  // normal matrix).  FP64 path: two steps, one where the two smallest
+  // eigenvalues are within 1e-4 lambda_max.  Mixed path: one step where they
+  // are within 1e-6 lambda_max (the z = 1 samples: ~1e-9 apart, where the
+  // float-float normal matrix alone leaves ~1e-4 in x), none elsewhere.
+  const int far = a.mixed ? 0 : 2;
+  const double gap = a.mixed ? 1e-6 : 1e-4;
+  TriResult res;
+  if (real) {
+    SylvesterApply<true> ap;
+    ap.P = sample_polys<double, double>(a.pz[ps], a.len[ps], f, a.C, a.ns, s);
+    ap.C = a.C;
+    ap.t1 = a.t1;
+    ap.t2 = a.t2;
+    ap.L = a.len[ps][0] + a.t2 - 1;
+    ap.y = a.resid + o * a.C * (int64_t)a.Lmax;
+    ap.real = true;
+    res = tri_smallest<double, true>(W, G, n, far, 1, gap, ap, tk);
+    if (warp != 0) return;
+  } else {
+    SylvesterApply<false> ap;
+    ap.P = sample_polys<double, double>(a.pz[ps], a.len[ps], f, a.C, a.ns, s);
+    ap.C = a.C;
+    ap.t1 = a.t1;
+    ap.t2 = a.t2;
+    ap.L = a.len[ps][0] + a.t2 - 1;
+    ap.y = a.resid + o * a.C * (int64_t)a.Lmax;
+    ap.real = false;
+    res = tri_smallest<cd, false>(W, G, n, far, 1, gap, ap, tk);
+  }
+#ifdef CBP_PHASE_TIMING
+  if (tk && lane == 0)
+    printf("tri pass=%d s=%d real=%d near=%d | reduce %lld bisect %lld invit %lld newton %lld "
+           "theta %lld\n", ps, s, (int)real, res.near_degenerate, tkv[1] - tkv[0], tkv[2] - tkv[1],
+           tkv[3] - tkv[2], tkv[4] - tkv[3], tkv[5] - tkv[4]);
+#endif
+  for (int i = lane; i < n; i += 32) a.X[o * n + i] = W.x[i];
+  if (lane == 0) {
     a.sdiag[o * 4 + 0] = res.lam_max;
     a.sdiag[o * 4 + 1] = res.lam_2;
     a.sdiag[o * 4 + 2] = res.theta;
-    a.sdiag[o * 4 + 3] = res.hard;
+    a.sdiag[o * 4 + 3] = res.near_degenerate;
   }
 }
 
@@ -1224,7 +1266,7 @@ __global__ void k_kernels_in(const void* k1, const void* k2, int in_f64, int n, 
 
 }  // namespace
 
-size_t sample_solve_smem(int nn) { return eig_smem_bytes(nn) + sizeof(cd) * (4 * kMaxN); }
+size_t sample_solve_smem(int nn) { return tri_ws_bytes(nn); }
 size_t scale_solve_smem(int M) { return eig_smem_bytes(2 * M) + sizeof(cd) * 3 * M * M; }
 
 void launch_sample_solve(const Plan& p, char* ws, cudaStream_t st) {
@@ -1251,10 +1293,18 @@ void launch_sample_solve(const Plan& p, char* ws, cudaStream_t st) {
   a.M = p.M;
   a.mixed = p.mixed;
   a.accepted = p.learned ? (const int*)(ws + p.off_acc) : nullptr;
-  const size_t sm = sample_solve_smem(p.nn);
+  a.G = (cd*)(ws + p.off_gall);
   dim3 grid(p.n, 2, p.ns);
+  k_sample_gram<<<grid, kSolveThreads, 0, st>>>(a);
+  // warps (samples) per CTA: up to 4 within ~110 KB of shared memory
+  const int nrs = (p.M % 2 == 0) ? 2 : 1, ncs = p.ns - nrs;
+  const int nreal = p.n * 2 * nrs, ncomplex = p.n * 2 * ncs;
+  const size_t per = tri_ws_bytes(p.nn);
+  const int wpc = (int)std::max<size_t>(1, std::min<size_t>(4, (110u << 10) / per));
+  const size_t sm = per * wpc;
+  a.nfr = p.n;
   cudaFuncSetAttribute(k_sample_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_sample_solve<<<grid, kSolveThreads, sm, st>>>(a);
+  k_sample_solve<<<nreal + (ncomplex + wpc - 1) / wpc, 32 * wpc, sm, st>>>(a, nreal);
 }
 
 void launch_scale_solve(const Plan& p, char* ws, void* k1_out, void* k2_out, int out_f64,

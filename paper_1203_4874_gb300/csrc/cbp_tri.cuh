@@ -1,0 +1,599 @@
+// Smallest eigenpair of a Hermitian (or real symmetric) n x n matrix by one
+// warp, n <= 64: the null vector of the per-sample normal matrix G = S^H S
+// (Eq. 4; Section 5 takes it from an SVD of the Bezout/Sylvester matrix).
+//
+//   1. Householder reduction to a real symmetric tridiagonal T = Q^H G Q
+//      (reflectors H_k = I - tau_k v_k v_k^H chosen so that beta_k is real);
+//   2. Sturm counts by multisection (each lane counts at its own shift) for
+//      the two smallest and the largest eigenvalue of T: single-precision
+//      rounds down to the single-precision floor, then double-precision
+//      rounds inside the widened brackets;
+//   3. inverse iteration on T - sigma I (tridiagonal LU with row interchanges)
+//      with sigma inside the bracket of the smallest eigenvalue;
+//   4. x = Q y;
+//   5. optional Newton steps against an exact operator (S^H S applied through
+//      S): the correction equation (G - theta) d = -r, d orthogonal to x, is
+//      solved through T in Olsen's form d = -(G - theta)^{-1} r +
+//      eps (G - theta)^{-1} x.
+//
+// Every step is O(n^2) per lane-column except the reduction (O(n^3) in all),
+// and all but the first bisection rounds run in double precision: a GPU whose
+// double pipe is narrow spends its time on the reduction's rank-2 updates,
+// n^3 / 3 complex multiply-adds in all.  Sign and exponent tests use the
+// integer pipe; reciprocals start from a single-precision seed.
+//
+// Lane l owns the columns l and l + 32.  The matrix is stored in full with row
+// stride n; lane i touches element (j, i) of row j, so every access of a row
+// is contiguous across the warp.  Included inside namespace cbp::(anonymous)
+// of the solver's translation unit, after its scalar helpers (fma_, to_cd,
+// re_, cj_, a2_, Ops).
+
+__device__ __forceinline__ double im_(double) { return 0.0; }
+__device__ __forceinline__ double im_(cd x) { return x.im; }
+template <typename E> __device__ __forceinline__ E mk_e(double re, double im);
+template <> __device__ __forceinline__ double mk_e<double>(double re, double) { return re; }
+template <> __device__ __forceinline__ cd mk_e<cd>(double re, double im) { return mk(re, im); }
+__device__ __forceinline__ double mul_(double a, double b) { return a * b; }
+__device__ __forceinline__ cd mul_(cd a, cd b) { return a * b; }
+__device__ __forceinline__ double sc_(double s, double a) { return s * a; }
+__device__ __forceinline__ cd sc_(double s, cd a) { return s * a; }
+
+// Per-warp work area.
+struct TriWs {
+  void* A;        // E[n * n]: the matrix; row k then holds reflector v_k (k+1..n-1)
+  void* tau;      // E[n]
+  void* w;        // E[n]
+  double* d;      // [n] diagonal of T
+  double* e;      // [n] off-diagonal of T: e[k] couples rows k and k + 1
+  double* e2;     // [n] e^2
+  double* u0;     // [n] LU of T - sigma I: diagonal of U
+  double* u1;     // [n] first superdiagonal of U
+  double* u2;     // [n] second superdiagonal of U (row interchanges)
+  double* lm;     // [n] multipliers
+  int* piv;       // [n] 1 where rows k and k + 1 were interchanged
+  float* df;      // [n] d in single precision
+  float* e2f;     // [n] e^2 in single precision
+  int* iv;        // [4] values broadcast to the CTA
+  cd* x;          // [n] the eigenvector of G
+  cd* r;          // [n] residual
+  cd* z;          // [n] scratch (T coordinates)
+  cd* q;          // [n] scratch (T coordinates)
+};
+
+// Bytes of one warp's work area; a multiple of 128, so that every warp's area
+// (placed back to back) and each of its 16-byte-aligned parts stay aligned.
+__host__ __device__ inline size_t tri_ws_bytes(int n) {
+  const size_t b = (size_t)16 * ((size_t)n * n + 2 * n) + (size_t)8 * 7 * n + (size_t)4 * 3 * n +
+                   16 + (size_t)16 * 4 * n + 16 * 18;   // + alignment of the 18 parts
+  return (b + 127) & ~size_t(127);
+}
+
+__device__ inline TriWs carve_tri(char* p, int n) {
+  TriWs W;
+  auto take = [&](size_t bytes) {
+    char* q = p;
+    p += (bytes + 15) & ~size_t(15);
+    return q;
+  };
+  W.A = take((size_t)16 * n * n);
+  W.tau = take((size_t)16 * n);
+  W.w = take((size_t)16 * n);
+  W.x = (cd*)take((size_t)16 * n);
+  W.r = (cd*)take((size_t)16 * n);
+  W.z = (cd*)take((size_t)16 * n);
+  W.q = (cd*)take((size_t)16 * n);
+  W.d = (double*)take((size_t)8 * n);
+  W.e = (double*)take((size_t)8 * n);
+  W.e2 = (double*)take((size_t)8 * n);
+  W.u0 = (double*)take((size_t)8 * n);
+  W.u1 = (double*)take((size_t)8 * n);
+  W.u2 = (double*)take((size_t)8 * n);
+  W.lm = (double*)take((size_t)8 * n);
+  W.piv = (int*)take((size_t)4 * n);
+  W.df = (float*)take((size_t)4 * n);
+  W.e2f = (float*)take((size_t)4 * n);
+  W.iv = (int*)take(16);
+  return W;
+}
+
+// 1. Householder reduction.  On return T = (d, e), tau and the reflectors
+// (row k of A from column k + 1 on, v_k[k + 1] = 1) describe
+// Q = H_0 H_1 ... H_{n-2} with A_in = Q T Q^H.
+template <typename E>
+__device__ void tri_reduce(E* A, E* tau, E* w, double* d, double* e, int n) {
+  const int lane = threadIdx.x & 31;
+  for (int k = 0; k + 1 < n; ++k) {
+    const int k1 = k + 1;
+    E* vk = A + (size_t)k * n;             // row k = conj(column k)
+    const E alpha = cj_(vk[k1]);
+    double xn2 = 0.0;
+    for (int i = lane; i < n; i += 32)
+      if (i > k1) xn2 += a2_(vk[i]);
+    xn2 = warp_sum(xn2);
+    const double ar = re_(alpha), ai = im_(alpha);
+    E tk = Ops<E>::z();
+    double beta = ar;
+    if (xn2 > 0.0 || ai != 0.0) {
+      // H^H (alpha, x) = (beta, 0) with beta real, |beta| = |(alpha, x)|
+      beta = -copysign(sqrt(ar * ar + ai * ai + xn2), ar);
+      const double ib = 1.0 / beta;
+      tk = mk_e<E>((beta - ar) * ib, -ai * ib);
+      // v = x / (alpha - beta)
+      const double dr = ar - beta, dn = 1.0 / (dr * dr + ai * ai);
+      const E scl = mk_e<E>(dr * dn, -ai * dn);
+      __syncwarp();
+      for (int i = lane; i < n; i += 32) {
+        if (i > k1) vk[i] = mul_(cj_(vk[i]), scl);
+        else if (i == k1) vk[i] = Ops<E>::o();
+      }
+    } else {
+      __syncwarp();
+      for (int i = lane; i < n; i += 32)
+        if (i == k1) vk[i] = Ops<E>::o();
+    }
+    if (lane == 0) {
+      d[k] = re_(A[(size_t)k * n + k]);
+      e[k] = beta;
+      tau[k] = tk;
+    }
+    __syncwarp();
+    if (!Ops<E>::nz(tk)) continue;
+    // y = tau A v over the trailing block; w = y - (1/2) conj(tau) (v^H y) v
+    E y[2];
+    E dotl = Ops<E>::z();
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int i = lane + 32 * c;
+      y[c] = Ops<E>::z();
+      if (i > k && i < n) {
+        E acc = Ops<E>::z();
+        for (int j = k1; j < n; ++j) fma_(acc, cj_(A[(size_t)j * n + i]), vk[j]);
+        y[c] = mul_(tk, acc);
+        fma_(dotl, cj_(vk[i]), y[c]);
+      }
+    }
+    const E dot = warp_sum_e(dotl);
+    const double hc = 0.5 * re_(mul_(cj_(tk), dot));
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int i = lane + 32 * c;
+      if (i > k && i < n) {
+        y[c] = y[c] - sc_(hc, vk[i]);
+        w[i] = y[c];
+      }
+    }
+    __syncwarp();
+    // A <- A - v w^H - w v^H on the trailing block
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int i = lane + 32 * c;
+      if (i > k && i < n) {
+        const E cw = cj_(y[c]), cv = cj_(vk[i]);
+        for (int j = k1; j < n; ++j) {
+          E t = mul_(vk[j], cw);
+          fma_(t, w[j], cv);
+          A[(size_t)j * n + i] = A[(size_t)j * n + i] - t;
+        }
+      }
+    }
+    __syncwarp();
+  }
+  if (lane == 0) d[n - 1] = re_(A[(size_t)(n - 1) * n + n - 1]);
+  __syncwarp();
+}
+
+// Sign and zero tests of a double on the integer pipe.
+__device__ __forceinline__ bool dneg(double x) { return __double_as_longlong(x) < 0; }
+__device__ __forceinline__ bool dzero(double x) { return (__double_as_longlong(x) << 1) == 0; }
+__device__ __forceinline__ int dexp(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }
+
+// Number of eigenvalues of T below sig: sign changes of the leading principal
+// minors p_i = det(T_i - sig I) (p_i = (d_i - sig) p_{i-1} - e_{i-1}^2 p_{i-2};
+// a zero minor takes the sign opposite to its predecessor's).  The minors
+// are rescaled by powers of two when they leave [2^-600, 2^600].
+__device__ __forceinline__ int sturm_count(const double* d, const double* e2, int n, double sig) {
+  double pm = 1.0, p = d[0] - sig;
+  bool negp = dneg(p) || dzero(p);
+  int cnt = negp ? 1 : 0;
+  for (int i = 1; i < n; ++i) {
+    const double pn = fma(d[i] - sig, p, -e2[i - 1] * pm);
+    pm = p;
+    p = pn;
+    const bool neg = dzero(p) ? !negp : dneg(p);
+    cnt += neg != negp;
+    negp = neg;
+    if ((i & 7) == 0) {
+      const int ex = max(dexp(p), dexp(pm));
+      if (ex > 1023 + 600) {
+        p *= 0x1p-600;
+        pm *= 0x1p-600;
+      } else if (ex < 1023 - 600 && ex > 0) {
+        p *= 0x1p600;
+        pm *= 0x1p600;
+      }
+    }
+  }
+  return cnt;
+}
+
+// The same count in single precision, in ratio form q_i = p_i / p_{i-1}
+// (a ratio below tiny in magnitude is taken as -tiny).  It is exact for a
+// matrix within a few single-precision units of ||T|| of T.
+__device__ __forceinline__ int sturm_count_f(const float* d, const float* e2, int n, float sig,
+                                             float tiny) {
+  float q = d[0] - sig;
+  if (fabsf(q) < tiny) q = -tiny;
+  int cnt = q < 0.f ? 1 : 0;
+  for (int i = 1; i < n; ++i) {
+    q = (d[i] - sig) - __fdividef(e2[i - 1], q);
+    if (fabsf(q) < tiny) q = -tiny;
+    cnt += q < 0.f ? 1 : 0;
+  }
+  return cnt;
+}
+
+// One multisection round for the t-th smallest eigenvalue (t = 0, 1, ...):
+// lanes count at 32 interior points of [lo, hi]; the bracket shrinks 33x.
+// Brackets of eigenvalues 1 and n - 1 are narrowed from the same counts.
+struct Bracket {
+  double lo, hi;
+};
+__device__ __forceinline__ void shrink(Bracket& b, unsigned above, double sig) {
+  const int first = above ? __ffs(above) - 1 : 32;
+  const double slo = __shfl_sync(0xffffffffu, sig, first > 0 ? first - 1 : 0);
+  const double shi = __shfl_sync(0xffffffffu, sig, first < 32 ? first : 31);
+  if (first > 0) b.lo = fmax(b.lo, slo);
+  if (first < 32) b.hi = fmin(b.hi, shi);
+}
+// One round on bracket t; the counts narrow all nb brackets (target
+// eigenvalue index which[m] each).  SINGLE: counts in single precision at
+// shifts rounded to single precision.
+template <bool SINGLE>
+__device__ void multisect(const TriWs& W, int n, int t, Bracket* br, int nb, const int* which,
+                          float tiny_f) {
+  const int lane = threadIdx.x & 31;
+  const double h = (br[t].hi - br[t].lo) * (1.0 / 33.0);
+  double sig = fma(h, (double)(lane + 1), br[t].lo);
+  int c;
+  if (SINGLE) {
+    const float sf = (float)sig;
+    sig = (double)sf;
+    c = sturm_count_f(W.df, W.e2f, n, sf, tiny_f);
+  } else {
+    c = sturm_count(W.d, W.e2, n, sig);
+  }
+  for (int m = 0; m < nb; ++m) {
+    const unsigned above = __ballot_sync(0xffffffffu, c > which[m]);
+    shrink(br[m], above, sig);
+  }
+}
+
+// 3. LU of the tridiagonal T - sig I with row interchanges (lane 0 only);
+// pivots below tiny = u ||T|| in magnitude become +-tiny.  u0 keeps the
+// reciprocals of U's diagonal.
+__device__ __forceinline__ double rcp_safe(double x) {
+  return fabs(x) > 1e-30 && fabs(x) < 1e30 ? rcp_d(x) : 1.0 / x;
+}
+__device__ __forceinline__ double rsqrt_safe(double x) {
+  return x > 1e-30 && x < 1e30 ? rsqrt_d(x) : 1.0 / sqrt(x);
+}
+__device__ __forceinline__ double clamp_pivot(double x, double tiny) {
+  return fabs(x) >= tiny ? x : (dneg(x) ? -tiny : tiny);
+}
+__device__ void tri_lu(const TriWs& W, int n, double sig, double tiny) {
+  if ((threadIdx.x & 31) != 0) return;
+  for (int i = 0; i < n; ++i) {
+    W.u0[i] = W.d[i] - sig;
+    W.u1[i] = i + 1 < n ? W.e[i] : 0.0;
+    W.u2[i] = 0.0;
+  }
+  for (int i = 0; i + 1 < n; ++i) {
+    const double sub = W.e[i];   // element (i + 1, i)
+    const double piv = W.u0[i];
+    if (fabs(piv) >= fabs(sub)) {
+      const double r = rcp_safe(clamp_pivot(piv, tiny));
+      const double m = sub * r;
+      W.lm[i] = m;
+      W.piv[i] = 0;
+      W.u0[i] = r;
+      W.u0[i + 1] -= m * W.u1[i];
+    } else {
+      const double r = rcp_safe(sub);
+      const double m = piv * r;
+      const double a1 = W.u0[i + 1], b1 = W.u1[i + 1];
+      W.lm[i] = m;
+      W.piv[i] = 1;
+      W.u0[i] = r;
+      W.u0[i + 1] = W.u1[i] - m * a1;
+      W.u1[i + 1] = -m * b1;
+      W.u1[i] = a1;
+      W.u2[i] = b1;
+    }
+  }
+  W.u0[n - 1] = rcp_safe(clamp_pivot(W.u0[n - 1], tiny));
+}
+
+// Solve (T - sig I) z = b in place (lane 0 only), b complex.
+__device__ void tri_solve(const TriWs& W, int n, cd* b) {
+  if ((threadIdx.x & 31) != 0) return;
+  for (int i = 0; i + 1 < n; ++i) {
+    if (W.piv[i]) {
+      const cd t = b[i];
+      b[i] = b[i + 1];
+      b[i + 1] = t;
+    }
+    b[i + 1] = b[i + 1] - W.lm[i] * b[i];
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    cd v = b[i];
+    if (i + 1 < n) v = v - W.u1[i] * b[i + 1];
+    if (i + 2 < n) v = v - W.u2[i] * b[i + 2];
+    b[i] = W.u0[i] * v;
+  }
+}
+
+// Apply Q (back = true: b <- Q b) or Q^H (b <- Q^H b) to b (n, complex).
+template <typename E>
+__device__ void tri_apply_q(const E* A, const E* tau, int n, cd* b, bool back) {
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+  for (int s = 0; s + 1 < n; ++s) {
+    const int k = back ? n - 2 - s : s;
+    const cd tk = to_cd(tau[k]);
+    if (tk.re == 0.0 && tk.im == 0.0) continue;
+    const E* vk = A + (size_t)k * n;
+    cd acc = mk(0.0, 0.0);
+    for (int i = lane; i < n; i += 32)
+      if (i > k) cfmac(acc, to_cd(vk[i]), b[i]);   // v^H b
+    acc = mk(warp_sum(acc.re), warp_sum(acc.im));
+    const cd f = (back ? tk : conj(tk)) * acc;
+    __syncwarp();
+    for (int i = lane; i < n; i += 32)
+      if (i > k) b[i] = b[i] - f * to_cd(vk[i]);
+    __syncwarp();
+  }
+}
+
+__device__ __forceinline__ double tri_norm2(const cd* b, int n) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = lane; i < n; i += 32) s += abs2(b[i]);
+  return warp_sum(s);
+}
+
+struct TriResult {
+  double lam_min, lam_2, lam_max;   // eigenvalues of G (T's, scaled back)
+  double theta;                     // x^H G x
+  int near_degenerate;              // lam_2 - lam_min <= 1e-4 lam_max
+};
+
+// CTA- or warp-wide barrier.
+template <bool BLOCK> __device__ __forceinline__ void team_sync() {
+  if (BLOCK) __syncthreads();
+  else __syncwarp();
+}
+
+// Steps 1-4 by one warp: T, the eigenvalue brackets, x.  Returns the number
+// of refinement steps to take; fills res (eigenvalues), gs (the power-of-two
+// scale of G) and tnorm.
+template <typename E>
+__device__ int tri_solve_lead(const TriWs& W, const cd* G, int n, int steps_far, int steps_near,
+                              double refine_gap, TriResult& res, double& gs, double& tnorm,
+                              long long* tk) {
+  const int lane = threadIdx.x & 31;
+  E* A = (E*)W.A;
+  E* tau = (E*)W.tau;
+  // scale by a power of two so that the largest diagonal entry is in [1/2, 1)
+  double gmax = 0.0;
+  for (int i = lane; i < n; i += 32) gmax = fmax(gmax, G[(size_t)i * n + i].re);
+  gmax = warp_max(gmax);
+  if (!(gmax > 0.0)) {   // zero matrix: every vector is a null vector
+    for (int i = lane; i < n; i += 32) W.x[i] = mk(i == 0 ? 1.0 : 0.0, 0.0);
+    __syncwarp();
+    res.lam_min = res.lam_2 = res.lam_max = 0.0;
+    res.near_degenerate = 1;
+    gs = 1.0;
+    tnorm = 0.0;
+    return 0;
+  }
+  int ex;
+  frexp(gmax, &ex);
+  gs = ldexp(1.0, ex);
+  const double igs = ldexp(1.0, -ex);
+  for (int idx = lane; idx < n * n; idx += 32) {
+    if constexpr (sizeof(E) == sizeof(double)) A[idx] = mk_e<E>(G[idx].re * igs, 0.0);
+    else A[idx] = mk_e<E>(G[idx].re * igs, G[idx].im * igs);
+  }
+  __syncwarp();
+  if (tk && lane == 0) tk[0] = clock64();
+  tri_reduce<E>(A, tau, (E*)W.w, W.d, W.e, n);
+  if (tk && lane == 0) tk[1] = clock64();
+  // Gershgorin interval of T; single-precision copies
+  double glo = 1e300, ghi = -1e300;
+  for (int i = lane; i < n; i += 32) {
+    const double rad = (i > 0 ? fabs(W.e[i - 1]) : 0.0) + (i + 1 < n ? fabs(W.e[i]) : 0.0);
+    glo = fmin(glo, W.d[i] - rad);
+    ghi = fmax(ghi, W.d[i] + rad);
+    const double e2 = i + 1 < n ? W.e[i] * W.e[i] : 0.0;
+    W.e2[i] = e2;
+    W.df[i] = (float)W.d[i];
+    W.e2f[i] = (float)e2;
+  }
+  glo = -warp_max(-glo);
+  ghi = warp_max(ghi);
+  tnorm = fmax(fabs(glo), fabs(ghi));
+  const double eps = 2.220446049250313e-16;
+  glo -= 4.0 * eps * tnorm + 1e-300;
+  ghi += 4.0 * eps * tnorm + 1e-300;
+  __syncwarp();
+  // 2. brackets of eigenvalues 0, 1 and n - 1
+  const int which[3] = {0, n > 1 ? 1 : 0, n - 1};
+  Bracket br[3] = {{glo, ghi}, {glo, ghi}, {glo, ghi}};
+  // single-precision rounds while a bracket is wider than its floor
+  const double fl = 1e-5 * tnorm;
+  const float tiny_f = (float)(1e-30 * fmax(tnorm, 1e-8));
+  for (int round = 0; round < 12; ++round) {
+    int t = -1;
+    for (int m = 2; m >= 0; --m)
+      if (br[m].hi - br[m].lo > fl) t = m;
+    if (t < 0) break;
+    multisect<true>(W, n, t, br, 3, which, tiny_f);
+  }
+  // widen by the single-precision error bound; check the ends in double
+  // precision (a wrong end falls back to the Gershgorin interval)
+  for (int m = 0; m < 3; ++m) {
+    br[m].lo = fmax(glo, br[m].lo - 4e-6 * tnorm);
+    br[m].hi = fmin(ghi, br[m].hi + 4e-6 * tnorm);
+  }
+  {
+    const int m = lane % 3, end = (lane / 3) & 1;
+    const double sig = end ? br[m].hi : br[m].lo;
+    const int c = lane < 6 ? sturm_count(W.d, W.e2, n, sig) : 0;
+    const bool bad = lane < 6 && (end ? c <= which[m] : c > which[m]);
+    const unsigned badm = __ballot_sync(0xffffffffu, bad);
+    for (int m2 = 0; m2 < 3; ++m2)
+      if (badm & (0x9u << m2)) br[m2] = Bracket{glo, ghi};
+  }
+  const double tol_abs = 8.0 * eps * tnorm;
+  for (int round = 0; round < 40; ++round) {
+    // isolated well enough: the inverse iteration contracts by 1e-4 per step
+    const double w0 = br[0].hi - br[0].lo;
+    if (w0 <= tol_abs || (n > 1 && br[1].lo > br[0].hi && w0 <= 1e-4 * (br[1].lo - br[0].hi)))
+      break;
+    multisect<false>(W, n, 0, br, 3, which, tiny_f);
+  }
+  if (n > 1) {
+    for (int round = 0; round < 40; ++round) {
+      const double w1 = br[1].hi - br[1].lo;
+      if (w1 <= fmax(tol_abs, 1e-5 * fabs(br[1].hi))) break;
+      multisect<false>(W, n, 1, br, 3, which, tiny_f);
+    }
+  }
+  for (int round = 0; round < 40; ++round) {
+    const double w2 = br[2].hi - br[2].lo;
+    if (w2 <= fmax(tol_abs, 1e-7 * fabs(br[2].hi))) break;
+    multisect<false>(W, n, 2, br, 3, which, tiny_f);
+  }
+  if (tk && lane == 0) tk[2] = clock64();
+  const double lam0 = 0.5 * (br[0].lo + br[0].hi);
+  const double lam1 = n > 1 ? 0.5 * (br[1].lo + br[1].hi) : lam0;
+  const double lamn = 0.5 * (br[2].lo + br[2].hi);
+  // 3. inverse iteration (three steps) from a fixed start vector
+  tri_lu(W, n, lam0, eps * tnorm);
+  for (int i = lane; i < n; i += 32) W.z[i] = mk(1.0 + 0.25 * (double)((i * 7) % 5), 0.0);
+  __syncwarp();
+  for (int it = 0; it < 3; ++it) {
+    tri_solve(W, n, W.z);
+    __syncwarp();
+    const double nz = tri_norm2(W.z, n);
+    const double sc = nz > 0.0 ? rsqrt_safe(nz) : 1.0;
+    for (int i = lane; i < n; i += 32) W.z[i] = sc * W.z[i];
+    __syncwarp();
+  }
+  // 4. x = Q y
+  for (int i = lane; i < n; i += 32) W.x[i] = W.z[i];
+  tri_apply_q<E>(A, tau, n, W.x, true);
+  {
+    const double sc = rsqrt_safe(tri_norm2(W.x, n));
+    for (int i = lane; i < n; i += 32) W.x[i] = sc * W.x[i];
+    __syncwarp();
+  }
+  if (tk && lane == 0) tk[3] = clock64();
+  res.lam_min = gs * lam0;
+  res.lam_2 = gs * lam1;
+  res.lam_max = gs * lamn;
+  res.near_degenerate = n > 1 && (lam1 - lam0) <= 1e-4 * lamn ? 1 : 0;
+  const bool near = n > 1 && (lam1 - lam0) <= refine_gap * lamn;
+  return near ? steps_near : steps_far;
+}
+
+// One refinement step by the lead warp after r = (exact operator) x: Olsen's
+// correction through T (step 5).
+template <typename E>
+__device__ void tri_olsen(const TriWs& W, int n, double gs, double tnorm) {
+  const int lane = threadIdx.x & 31;
+  const E* A = (const E*)W.A;
+  const E* tau = (const E*)W.tau;
+  const double eps = 2.220446049250313e-16, igs = 1.0 / gs;
+  cd th = mk(0.0, 0.0);
+  for (int i = lane; i < n; i += 32) cfmac(th, W.x[i], W.r[i]);
+  const double theta = warp_sum(th.re);
+  for (int i = lane; i < n; i += 32) {
+    W.r[i] = W.r[i] - theta * W.x[i];
+    W.q[i] = W.x[i];
+  }
+  // to T coordinates: r~ = Q^H r, y~ = Q^H x
+  tri_apply_q<E>(A, tau, n, W.r, false);
+  tri_apply_q<E>(A, tau, n, W.q, false);
+  tri_lu(W, n, theta * igs, eps * tnorm);
+  for (int i = lane; i < n; i += 32) W.z[i] = W.q[i];
+  __syncwarp();
+  tri_solve(W, n, W.r);    // u = (T - theta)^{-1} r~
+  tri_solve(W, n, W.z);    // z = (T - theta)^{-1} y~
+  __syncwarp();
+  cd nu = mk(0.0, 0.0), de = mk(0.0, 0.0);
+  for (int i = lane; i < n; i += 32) {
+    cfmac(nu, W.q[i], W.r[i]);
+    cfmac(de, W.q[i], W.z[i]);
+  }
+  nu = mk(warp_sum(nu.re), warp_sum(nu.im));
+  de = mk(warp_sum(de.re), warp_sum(de.im));
+  const double dd = abs2(de);
+  const cd epsn = dd > 0.0 ? (1.0 / dd) * (nu * conj(de)) : mk(0.0, 0.0);
+  // d = (-u + eps z) / gs in T coordinates, then back
+  for (int i = lane; i < n; i += 32) W.z[i] = igs * (epsn * W.z[i] - W.r[i]);
+  tri_apply_q<E>(A, tau, n, W.z, true);
+  for (int i = lane; i < n; i += 32) W.x[i] = W.x[i] + W.z[i];
+  __syncwarp();
+  const double sc = rsqrt_safe(tri_norm2(W.x, n));
+  for (int i = lane; i < n; i += 32) W.x[i] = sc * W.x[i];
+  __syncwarp();
+}
+
+// G: the n x n matrix (row-major, global or shared memory).  Result in W.x
+// (unit norm).  Steps of the exact-operator refinement: `steps_far` when the
+// two smallest eigenvalues are more than refine_gap * lam_max apart,
+// `steps_near` otherwise.  apply(x, out): out = (exact operator) x, by the
+// whole CTA (BLOCK) or by the calling warp.  BLOCK: every thread of the CTA
+// calls; warp 0 does all but the operator; the result is valid in warp 0.
+template <typename E, bool BLOCK, class Apply>
+__device__ TriResult tri_smallest(const TriWs& W, const cd* G, int n, int steps_far,
+                                  int steps_near, double refine_gap, const Apply& apply,
+                                  long long* tk = nullptr) {
+  const int lane = threadIdx.x & 31;
+  const bool lead = !BLOCK || threadIdx.x < 32;
+  TriResult res = {};
+  double gs = 1.0, tnorm = 0.0;
+  int steps = 0;
+  if (lead) {
+    steps = tri_solve_lead<E>(W, G, n, steps_far, steps_near, refine_gap, res, gs, tnorm, tk);
+    if (BLOCK && lane == 0) W.iv[0] = steps;
+  }
+  if (BLOCK) {
+    __syncthreads();
+    steps = W.iv[0];
+  }
+  for (int it = 0; it < steps; ++it) {
+    apply(W.x, W.r);
+    team_sync<BLOCK>();
+    if (lead) tri_olsen<E>(W, n, gs, tnorm);
+    team_sync<BLOCK>();
+  }
+  if (tk && lead && lane == 0) tk[4] = clock64();
+  if (lead) {
+    // theta = x^H G x
+    cd th = mk(0.0, 0.0);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int i = lane + 32 * c;
+      if (i < n) {
+        cd gx = mk(0.0, 0.0);
+        for (int j = 0; j < n; ++j) cfmac(gx, G[(size_t)j * n + i], W.x[j]);   // (G x)_i
+        cfmac(th, W.x[i], gx);
+      }
+    }
+    res.theta = warp_sum(th.re);
+  }
+  if (tk && lead && lane == 0) tk[5] = clock64();
+  return res;
+}
