@@ -316,6 +316,7 @@ cbp_status call_path(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
   Plan p;
   cbp_status s = cbp::make_plan(b1, b2, prm, &p);
   if (s != CBP_OK) return s;
+  p.pz_all = stages ? 1 : 0;   // the stage outputs hold double samples
   if (deblur && !latent) return CBP_ERR_INVALID_ARG;
   if (!deblur && (!k1 || !k2)) return CBP_ERR_INVALID_ARG;
   if (deblur && (prm->flags & CBP_FLAG_KERNELS_IN) && (!k1 || !k2)) return CBP_ERR_INVALID_ARG;

@@ -55,12 +55,22 @@ struct TwoSum {
     lo += (hi - (t - z)) + (x - z);
     hi = t;
   }
+  __device__ __forceinline__ void merge(const TwoSum& o) {
+    add(o.hi);
+    lo += o.lo;
+  }
   __device__ __forceinline__ double value() const { return (double)hi + (double)lo; }
+  __device__ __forceinline__ bool finite() const { return isfinite(hi) && isfinite(lo); }
+  // 8-byte bin: (hi, lo) as two floats
+  __device__ __forceinline__ void store(void* p) const { *(float2*)p = make_float2(hi, lo); }
 };
 struct DoubleSum {
   double v = 0.0;
   __device__ __forceinline__ void add(double x) { v += x; }
+  __device__ __forceinline__ void merge(const DoubleSum& o) { v += o.v; }
   __device__ __forceinline__ double value() const { return v; }
+  __device__ __forceinline__ bool finite() const { return isfinite(v); }
+  __device__ __forceinline__ void store(void* p) const { *(double*)p = v; }
 };
 
 template <typename T> __device__ __forceinline__ T warp_sum(T v) {

@@ -16,9 +16,12 @@
 // fold makes the cost independent of M.
 //
 // Float32 frames are folded with an exact float TwoSum accumulation (hi + lo),
-// so the bins -- and the samples, whose M-point DFT runs in double -- carry
-// ~1e-14 relative error on both paths; the mixed path also keeps float-float
-// (hi + lo) copies for its extended-precision Gram on the float units.
+// so the bins -- and the samples -- carry ~1e-14 relative error on both paths.
+// The FP64 path takes the M-point DFT in double precision.  The mixed path
+// takes it in float-float arithmetic on the single-precision units (a GPU's
+// double pipe is narrow) and keeps the samples as float-float pairs (its
+// Gram is float-float too); double copies are written for the real samples
+// (z = 1, z = -1), whose Gram and refinement run in double precision.
 #include "cbp_common.cuh"
 #include "cbp_internal.h"
 
@@ -28,17 +31,29 @@ namespace {
 constexpr int kDftThreads = 128;
 
 struct FoldDftArgs {
-  const double* bins[4];   // [pass * 2 + frame]; pass 0: row bins, 1: column bins; [n C][M][len]
+  const void* bins[4];     // [pass * 2 + frame]; pass 0: row bins, 1: column bins; [n C][M][len]
   cd* pz[4];               // [n C][ns][len] samples
   cdf* pzf[4];             // float-float copies (mixed path) or null
   int len[4];
   int M, ns;
+  int pz_all;              // float-float kernel: double copies of every sample, not only the real ones
 };
+
+// 8-byte bin m of a position: (hi, lo) floats (F32) or a double.
+template <bool F32>
+__device__ __forceinline__ double bin_at(const void* b, int64_t i) {
+  if (F32) {
+    const float2 v = ((const float2*)b)[i];
+    return (double)v.x + (double)v.y;
+  }
+  return ((const double*)b)[i];
+}
 
 // M-point DFT of each position's M real bins, samples s < ns, using the
 // symmetry of the roots: with e_m = b_m + b_(M-m), o_m = b_m - b_(M-m),
 //   P_s = b_0 + sum_{m=1..(M-1)/2} (e_m cos(2 pi s m / M) - i o_m sin(2 pi s m / M))
 //         [+ (-1)^s b_(M/2) when M is even].
+template <bool F32>
 __global__ void __launch_bounds__(kDftThreads) k_fold_dft(FoldDftArgs a) {
   __shared__ double cs[kMaxM], sn[kMaxM];
   for (int k = threadIdx.x; k < a.M; k += blockDim.x) sincospi(2.0 * (double)k / (double)a.M, &sn[k], &cs[k]);
@@ -46,15 +61,16 @@ __global__ void __launch_bounds__(kDftThreads) k_fold_dft(FoldDftArgs a) {
   const int z = blockIdx.z, fc = blockIdx.y, M = a.M, len = a.len[z];
   const int pos = blockIdx.x * blockDim.x + threadIdx.x;
   if (pos >= len) return;
-  const double* b = a.bins[z] + (int64_t)fc * M * len + pos;
+  const int64_t b = (int64_t)fc * M * len + pos;
+  const void* bb = a.bins[z];
   const int h = (M - 1) / 2;
-  const double b0 = b[0];
-  const double bh = (M % 2 == 0) ? b[(int64_t)(M / 2) * len] : 0.0;
+  const double b0 = bin_at<F32>(bb, b);
+  const double bh = (M % 2 == 0) ? bin_at<F32>(bb, b + (int64_t)(M / 2) * len) : 0.0;
   double ev[kMaxM / 2], od[kMaxM / 2];
 #pragma unroll
   for (int m = 1; m <= kMaxM / 2; ++m) {
     if (m > h) break;
-    const double u = b[(int64_t)m * len], v = b[(int64_t)(M - m) * len];
+    const double u = bin_at<F32>(bb, b + (int64_t)m * len), v = bin_at<F32>(bb, b + (int64_t)(M - m) * len);
     ev[m - 1] = u + v;
     od[m - 1] = u - v;
   }
@@ -77,14 +93,92 @@ __global__ void __launch_bounds__(kDftThreads) k_fold_dft(FoldDftArgs a) {
   }
 }
 
+// Float-float arithmetic (hi + lo pairs of floats).
+struct F2 {
+  float hi, lo;
+};
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {   // TwoSum of the high parts, low parts added
+  const float s = a.hi + b.hi, z = s - a.hi;
+  const float e = ((a.hi - (s - z)) + (b.hi - z)) + (a.lo + b.lo);
+  const float hi = s + e;
+  return {hi, e - (hi - s)};
+}
+__device__ __forceinline__ F2 f2_neg(F2 a) { return {-a.hi, -a.lo}; }
+// acc += a * c, the low part left unnormalised (renormalise once at the end):
+// exact product of the high parts (FMA), cross terms, TwoSum into hi
+__device__ __forceinline__ void f2_mac(F2& acc, F2 a, F2 c) {
+  const float p = a.hi * c.hi;
+  float e = fmaf(a.hi, c.hi, -p);
+  e = fmaf(a.hi, c.lo, fmaf(a.lo, c.hi, e));
+  const float t = acc.hi + p, z = t - acc.hi;
+  acc.lo += ((acc.hi - (t - z)) + (p - z)) + e;
+  acc.hi = t;
+}
+__device__ __forceinline__ F2 f2_norm(F2 a) {
+  const float hi = a.hi + a.lo;
+  return {hi, a.lo - (hi - a.hi)};
+}
+
+// The same DFT in float-float arithmetic from (hi, lo) bins of float32 frames:
+// ~1e-14 of the terms' magnitudes, like the bins themselves.
+__global__ void __launch_bounds__(kDftThreads) k_fold_dft_ff(FoldDftArgs a) {
+  __shared__ F2 cs[kMaxM], sn[kMaxM];
+  for (int k = threadIdx.x; k < a.M; k += blockDim.x) {
+    double s, c;
+    sincospi(2.0 * (double)k / (double)a.M, &s, &c);
+    const float ch = (float)c, sh = (float)s;
+    cs[k] = {ch, (float)(c - (double)ch)};
+    sn[k] = {sh, (float)(s - (double)sh)};
+  }
+  __syncthreads();
+  const int z = blockIdx.z, fc = blockIdx.y, M = a.M, len = a.len[z];
+  const int pos = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= len) return;
+  const float2* bb = (const float2*)a.bins[z] + (int64_t)fc * M * len + pos;
+  auto bin = [&](int m) {
+    const float2 v = bb[(int64_t)m * len];
+    return F2{v.x, v.y};
+  };
+  const int h = (M - 1) / 2;
+  const F2 b0 = bin(0);
+  const F2 bh = (M % 2 == 0) ? bin(M / 2) : F2{0.f, 0.f};
+  F2 ev[kMaxM / 2], od[kMaxM / 2];
+#pragma unroll
+  for (int m = 1; m <= kMaxM / 2; ++m) {
+    if (m > h) break;
+    const F2 u = bin(m), v = bin(M - m);
+    ev[m - 1] = f2_add(u, v);
+    od[m - 1] = f2_add(u, f2_neg(v));
+  }
+  cd* out = a.pz[z] + (int64_t)fc * a.ns * len + pos;
+  cdf* outf = a.pzf[z] + (int64_t)fc * a.ns * len + pos;
+  for (int s = 0; s < a.ns; ++s) {
+    F2 re = f2_add(b0, (s & 1) ? f2_neg(bh) : bh), im = {0.f, 0.f};
+    int k = 0;
+#pragma unroll
+    for (int m = 1; m <= kMaxM / 2; ++m) {
+      if (m > h) break;
+      k += s;
+      if (k >= M) k -= M;
+      f2_mac(re, ev[m - 1], cs[k]);
+      f2_mac(im, f2_neg(od[m - 1]), sn[k]);
+    }
+    re = f2_norm(re);
+    im = f2_norm(im);
+    outf[(int64_t)s * len] = cdf{re.hi, re.lo, im.hi, im.lo};
+    if (a.pz_all || s == 0 || 2 * s == M)
+      out[(int64_t)s * len] = mk((double)re.hi + (double)re.lo, (double)im.hi + (double)im.lo);
+  }
+}
+
 }  // namespace
 
 void launch_fold_dft(const Plan& p, char* ws, cudaStream_t st) {
   FoldDftArgs a;
   int maxlen = 0;
   for (int k = 0; k < 2; ++k) {
-    a.bins[k] = (const double*)(ws + p.off_fbr[k]);
-    a.bins[2 + k] = (const double*)(ws + p.off_fbc[k]);
+    a.bins[k] = ws + p.off_fbr[k];
+    a.bins[2 + k] = ws + p.off_fbc[k];
     a.pz[k] = (cd*)(ws + p.off_pz2[k]);
     a.pz[2 + k] = (cd*)(ws + p.off_pz1[k]);
     a.pzf[k] = p.mixed ? (cdf*)(ws + p.off_pz2f[k]) : nullptr;
@@ -97,8 +191,13 @@ void launch_fold_dft(const Plan& p, char* ws, cudaStream_t st) {
   for (int k = 0; k < 4; ++k) maxlen = a.len[k] > maxlen ? a.len[k] : maxlen;
   a.M = p.M;
   a.ns = p.ns;
+  a.pz_all = p.pz_all;
   dim3 g((maxlen + kDftThreads - 1) / kDftThreads, p.n * p.C, 4);
-  k_fold_dft<<<g, kDftThreads, 0, st>>>(a);
+  // bins of float32 frames are (hi, lo) pairs; the mixed path of float32
+  // frames takes the float-float kernel
+  if (!p.frames_f64 && p.mixed) k_fold_dft_ff<<<g, kDftThreads, 0, st>>>(a);
+  else if (!p.frames_f64) k_fold_dft<true><<<g, kDftThreads, 0, st>>>(a);
+  else k_fold_dft<false><<<g, kDftThreads, 0, st>>>(a);
 }
 
 void launch_eval(const Plan& p, const FrameDesc& b1, const FrameDesc& b2, char* ws,

@@ -387,8 +387,9 @@ __device__ __forceinline__ cd ldg_cpx(const cd* p) {
 // row of a block has the same residue r mod M, so the block alone completes
 // column-fold bin x:  Fz1[x][c] = sum_{r = x mod M} B[r][c].  Each row's own
 // fold Fz2[m][r] = sum_{c = m mod M} B[r][c] is finished as the row passes.
-// The bins are exact float sums (TwoSum hi + lo) stored as double; the M-point
-// DFT over the bins (k_fold_dft, cbp_eval.cu) gives the samples.
+// The bins of float32 frames are exact float sums kept as the TwoSum pair
+// (hi, lo) of floats, those of float64 frames doubles (8 bytes either way);
+// the M-point DFT over the bins (k_fold_dft, cbp_eval.cu) gives the samples.
 //
 // Rows arrive by cp.async into a double-buffered staging area, nbr rows per
 // group, the next group in flight while the current one is folded and
@@ -396,8 +397,8 @@ __device__ __forceinline__ cd ldg_cpx(const cd* p) {
 struct RowPassArgs {
   FrameDesc fr[2];
   void* spec[2];       // cpx<T> [n][C][H_Bk][Pw2p] (FFT)
-  double* bins_r[2];   // [n C][M][H_Bk] row-fold bins (FOLD)
-  double* bins_c[2];   // [n C][M][W_Bk] column-fold bins (FOLD)
+  void* bins_r[2];     // [n C][M][H_Bk] row-fold bins, 8 bytes each (FOLD)
+  void* bins_c[2];     // [n C][M][W_Bk] column-fold bins (FOLD)
   int* bad;            // [n] non-finite input flags (FOLD)
   int* err;            // set when a copy does not complete in time
   int M;
@@ -594,7 +595,7 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
   In* const raw0 = (In*)(smem + L.raw0);
   In* const raw1 = (In*)(smem + L.raw1);
   Acc* colacc = (Acc*)(smem + L.colacc);
-  double* rb = (double*)(smem + L.rb);
+  Acc* rb = (Acc*)(smem + L.rb);
   int* rph = (int*)(smem + L.rph);
   uint64_t* bars = (uint64_t*)(smem + L.mbar);   // one per staging buffer
   if (threadIdx.x == 0) {
@@ -689,7 +690,7 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
         int c = sg * sps * M + m;
         for (int st = sg * sps; st < e; ++st, c += M)
           if (c < W) acc.add(rp[c]);
-        rb[t] = acc.value();
+        rb[t] = acc;
       }
     }
     RP_MARK(2);
@@ -701,9 +702,9 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
       const int nseg = max(1, kRowPassThreads / (nr * M));
       for (int t = threadIdx.x; t < nr * M; t += blockDim.x) {
         const int i = t / M, m = t - i * M;
-        double v = 0;
-        for (int sg = 0; sg < nseg; ++sg) v += rb[(i * nseg + sg) * M + m];
-        a.bins_r[blockIdx.z][((int64_t)fc * M + m) * fr.h + row_of(g, i)] = v;
+        Acc v = rb[(i * nseg) * M + m];
+        for (int sg = 1; sg < nseg; ++sg) v.merge(rb[(i * nseg + sg) * M + m]);
+        v.store((char*)a.bins_r[blockIdx.z] + 8 * (((int64_t)fc * M + m) * fr.h + row_of(g, i)));
       }
     }
     if (fft) {
@@ -744,22 +745,20 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
 #endif
   if (FOLD) {
     bool finite = true;
-    double* dst = a.bins_c[blockIdx.z] + ((int64_t)fc * M + x0) * W;
+    char* dst = (char*)a.bins_c[blockIdx.z] + 8 * (((int64_t)fc * M + x0) * W);
     if (!L.col_smem) {
 #pragma unroll
       for (int j = 0; j < kColRegs; ++j) {
         const int c = threadIdx.x + j * kRowPassThreads;
         if (c < W) {
-          const double v = creg[j].value();
-          finite = finite && isfinite(v);
-          dst[c] = v;
+          finite = finite && creg[j].finite();
+          creg[j].store(dst + 8 * (size_t)c);
         }
       }
     } else {
       for (int c = threadIdx.x; c < W; c += blockDim.x) {
-        const double v = colacc[c].value();
-        finite = finite && isfinite(v);
-        dst[c] = v;
+        finite = finite && colacc[c].finite();
+        colacc[c].store(dst + 8 * (size_t)c);
       }
     }
     if (__syncthreads_or(!finite) && threadIdx.x == 0) atomicOr(a.bad + f, 1);
@@ -1169,8 +1168,8 @@ void run_row_pass(const Plan& p, const FrameDesc& b1, const FrameDesc& b2, char*
   a.spec[0] = ws + p.off_spec[0];
   a.spec[1] = ws + p.off_spec[1];
   for (int k = 0; k < 2; ++k) {
-    a.bins_r[k] = (double*)(ws + p.off_fbr[k]);
-    a.bins_c[k] = (double*)(ws + p.off_fbc[k]);
+    a.bins_r[k] = ws + p.off_fbr[k];
+    a.bins_c[k] = ws + p.off_fbc[k];
   }
   a.bad = (int*)(ws + p.off_bad);
   a.err = (int*)(ws + p.off_err);

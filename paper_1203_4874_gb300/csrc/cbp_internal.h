@@ -61,6 +61,8 @@ struct Plan {
   int Pw2p;                    // row pitch of the spectra: Pw2 rounded up to even
   int mixed;                   // estimation path: 0 FP64, 1 mixed
   int fft_f64;                 // deconvolution arithmetic in double
+  int frames_f64;              // float64 frames (fold bins are doubles, else (hi, lo) float pairs)
+  int pz_all;                  // mixed path: double copies of every sample (stage outputs)
   int single_kernel;           // deconvolve B1 by K1 only
   int pw_half;                 // Pw even: real row FFTs via half-length complex FFTs
   int learned;                 // learned path: proposal + consistency gate first
@@ -71,7 +73,7 @@ struct Plan {
   // workspace layout (byte offsets into one device allocation)
   size_t off_pz2[2], off_pz1[2];   // cd [n][C][ns][len] sample polynomials (double)
   size_t off_pz2f[2], off_pz1f[2]; // cdf float-float copies for the mixed path's Gram
-  size_t off_fbr[2], off_fbc[2];   // double [n][C][M][H_Bk] row / [n][C][M][W_Bk] column fold bins
+  size_t off_fbr[2], off_fbc[2];   // 8-byte [n][C][M][H_Bk] row / [n][C][M][W_Bk] column fold bins
   size_t off_x;                    // cd [n][2][ns][nn]
   size_t off_gall;                 // cd [n][2][ns][nn][nn] per-sample normal matrices
   size_t off_sdiag;                // double [n][2][ns][4]

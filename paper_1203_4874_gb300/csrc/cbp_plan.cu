@@ -133,6 +133,7 @@ cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_param
   p.mixed = prm->path != CBP_PATH_FP64;
   const int frame_f64 = b1->dtype == CBP_F64;
   p.fft_f64 = (frame_f64 && !p.mixed) ? 1 : 0;
+  p.frames_f64 = frame_f64;
   p.single_kernel = (prm->flags & CBP_FLAG_SINGLE_KERNEL) ? 1 : 0;
   p.learned = prm->path == CBP_PATH_LEARNED ? 1 : 0;
   if (p.learned && (t1 != kCnnT || t2 != kCnnT)) return CBP_ERR_UNSUPPORTED;  // network output size

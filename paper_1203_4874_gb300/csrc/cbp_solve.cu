@@ -804,65 +804,59 @@ __device__ void gram_from_rho(const cd* rho, int t1, int t2, cd* G) {
 
 // S^H S x from the double samples (the exact operator of the refinement
 // steps; y holds S x), by the whole CTA (BLOCK) or by the calling warp.
+// S = [-C_t1(b2) | C_t2(b1)] (channels' rows stacked):
+//   (S x)[ch][i] = sum_q b1[ch][i - q] v_q - sum_p b2[ch][i - p] u_p,
+//   (S^H y)_u[p] = -sum_ch sum_m conj(b2[ch][m]) y[ch][m + p], likewise v with b1.
 template <bool BLOCK>
 struct SylvesterApply {
   SamplePolys<double, double> P;
+  const cdf* F[2];  // float-float samples (mixed path, complex samples) or null: read instead of P
+  int64_t fstride[2];
   cd* y;            // [C][L]
   int C, t1, t2, L;
   bool real;        // real sample (z = 1, or z = -1 for even M): real arithmetic
   __device__ void operator()(const cd* x, cd* out) const {
-    if (real) apply_real(x, out);
-    else apply_complex(x, out);
+    if (real) run<true, false>(x, out);
+    else if (F[0]) run<false, true>(x, out);
+    else run<false, false>(x, out);
   }
-  // real samples: P and x are real, so are S x and S^T S x
-  __device__ void apply_real(const cd* x, cd* out) const {
+  template <bool FFS>
+  __device__ __forceinline__ cd ld(const void* row, int m) const {
+    if (FFS) {
+      const cdf v = ((const cdf*)row)[m];
+      return mk((double)v.rh + (double)v.rl, (double)v.ih + (double)v.il);
+    }
+    return ((const cd*)row)[m];
+  }
+  __device__ __forceinline__ const void* row(int k, int ch, bool ffs) const {
+    if (ffs) return (const void*)((k ? F[1] : F[0]) + ch * (k ? fstride[1] : fstride[0]));
+    return (const void*)((k ? P.c[1] : P.c[0]) + ch * (k ? P.cstride[1] : P.cstride[0]));
+  }
+  template <bool REAL, bool FFS>
+  __device__ void run(const cd* x, cd* out) const {
     const int lane = threadIdx.x & 31;
     const int tid = BLOCK ? threadIdx.x : lane, nth = BLOCK ? blockDim.x : 32;
     const int wid = BLOCK ? threadIdx.x >> 5 : 0, nw = BLOCK ? blockDim.x >> 5 : 1;
+    const int len0 = P.len[0], len1 = P.len[1];
     team_sync<BLOCK>();
     for (int idx = tid; idx < C * L; idx += nth) {
-      const int ch = idx / L, i = idx % L;
-      double acc = 0.0;
-      for (int q = 0; q < t2; ++q) {     // b1 * v
-        const int m = i - q;
-        if (m >= 0 && m < P.len[0]) acc = fma(P.ld(0, ch, m).re, x[t1 + q].re, acc);
-      }
-      for (int p = 0; p < t1; ++p) {     // - b2 * u
-        const int m = i - p;
-        if (m >= 0 && m < P.len[1]) acc = fma(-P.ld(1, ch, m).re, x[p].re, acc);
-      }
-      y[idx] = mk(acc, 0.0);
-    }
-    team_sync<BLOCK>();
-    const int n = t1 + t2;
-    for (int o = wid; o < n; o += nw) {
-      const int k = o < t1 ? 1 : 0;
-      const int sh = o < t1 ? o : o - t1;
-      double acc = 0.0;
-      for (int ch = 0; ch < C; ++ch)
-        for (int m = lane; m < P.len[k]; m += 32) acc = fma(P.ld(k, ch, m).re, y[ch * L + m + sh].re, acc);
-      const double re = warp_sum(acc);
-      if (lane == 0) out[o] = mk(o < t1 ? -re : re, 0.0);
-    }
-    team_sync<BLOCK>();
-  }
-  __device__ void apply_complex(const cd* x, cd* out) const {
-    const int lane = threadIdx.x & 31;
-    const int tid = BLOCK ? threadIdx.x : lane, nth = BLOCK ? blockDim.x : 32;
-    const int wid = BLOCK ? threadIdx.x >> 5 : 0, nw = BLOCK ? blockDim.x >> 5 : 1;
-    team_sync<BLOCK>();
-    for (int idx = tid; idx < C * L; idx += nth) {
-      int ch = idx / L, i = idx % L;
+      const int ch = idx / L, i = idx - ch * L;
+      const void* r0 = row(0, ch, FFS);
+      const void* r1 = row(1, ch, FFS);
       cd acc = mk(0.0, 0.0);
-      for (int q = 0; q < t2; ++q) {     // b1 * v
-        int m = i - q;
-        if (m >= 0 && m < P.len[0]) cfma(acc, P.ld(0, ch, m), x[t1 + q]);
+      const int q0 = max(0, i - len0 + 1), q1 = min(t2 - 1, i);
+      for (int q = q0; q <= q1; ++q) {     // b1 * v
+        const cd b = ld<FFS>(r0, i - q);
+        if (REAL) acc.re = fma(b.re, x[t1 + q].re, acc.re);
+        else cfma(acc, b, x[t1 + q]);
       }
-      for (int p = 0; p < t1; ++p) {     // - b2 * u
-        int m = i - p;
-        if (m >= 0 && m < P.len[1]) {
-          cd b = P.ld(1, ch, m);
-          cd u = x[p];
+      const int p0 = max(0, i - len1 + 1), p1 = min(t1 - 1, i);
+      for (int p = p0; p <= p1; ++p) {     // - b2 * u
+        const cd b = ld<FFS>(r1, i - p);
+        if (REAL) {
+          acc.re = fma(-b.re, x[p].re, acc.re);
+        } else {
+          const cd u = x[p];
           acc.re -= b.re * u.re - b.im * u.im;
           acc.im -= b.re * u.im + b.im * u.re;
         }
@@ -874,10 +868,18 @@ struct SylvesterApply {
     for (int o = wid; o < n; o += nw) {
       const int k = o < t1 ? 1 : 0;       // u rows use b2, v rows use b1
       const int sh = o < t1 ? o : o - t1;
+      const int lk = k ? len1 : len0;
       cd acc = mk(0.0, 0.0);
-      for (int ch = 0; ch < C; ++ch)
-        for (int m = lane; m < P.len[k]; m += 32) cfmac(acc, P.ld(k, ch, m), y[ch * L + m + sh]);
-      double re = warp_sum(acc.re), im = warp_sum(acc.im);
+      for (int ch = 0; ch < C; ++ch) {
+        const void* rk = row(k, ch, FFS);
+        const cd* yr = y + ch * L + sh;
+        for (int m = lane; m < lk; m += 32) {
+          const cd b = ld<FFS>(rk, m);
+          if (REAL) acc.re = fma(b.re, yr[m].re, acc.re);
+          else cfmac(acc, b, yr[m]);
+        }
+      }
+      const double re = warp_sum(acc.re), im = REAL ? 0.0 : warp_sum(acc.im);
       if (lane == 0) out[o] = o < t1 ? mk(-re, -im) : mk(re, im);
     }
     team_sync<BLOCK>();
@@ -936,11 +938,12 @@ __global__ void k_sample_solve(SampleArgs a, int nreal) {
   long long* tk = nullptr;
 #endif
   // Refinement against S^H S (it removes the squared conditioning of the
-  // normal matrix).  FP64 path: two steps, one where the two smallest
-  // eigenvalues are within 1e-4 lambda_max.  Mixed path: one step where they
-  // are within 1e-6 lambda_max (the z = 1 samples: ~1e-9 apart, where the
-  // float-float normal matrix alone leaves ~1e-4 in x), none elsewhere.
-  const int far = a.mixed ? 0 : 2;
+  // normal matrix; one step through T, accurate to double precision, takes x
+  // to the double-precision floor).  FP64 path: one step.  Mixed path: one
+  // step where the two smallest eigenvalues are within 1e-6 lambda_max (the
+  // z = 1 samples: ~1e-9 apart, where the float-float normal matrix alone
+  // leaves ~1e-4 in x), none elsewhere.
+  const int far = a.mixed ? 0 : 1;
   const double gap = a.mixed ? 1e-6 : 1e-4;
   TriResult res;
   if (real) {
@@ -951,6 +954,7 @@ __global__ void k_sample_solve(SampleArgs a, int nreal) {
     ap.t2 = a.t2;
     ap.L = a.len[ps][0] + a.t2 - 1;
     ap.y = a.resid + o * a.C * (int64_t)a.Lmax;
+    ap.F[0] = ap.F[1] = nullptr;
     ap.real = true;
     res = tri_smallest<double, true>(W, G, n, far, 1, gap, ap, tk);
     if (warp != 0) return;
@@ -962,6 +966,13 @@ __global__ void k_sample_solve(SampleArgs a, int nreal) {
     ap.t2 = a.t2;
     ap.L = a.len[ps][0] + a.t2 - 1;
     ap.y = a.resid + o * a.C * (int64_t)a.Lmax;
+    ap.F[0] = ap.F[1] = nullptr;
+    if (a.mixed) {   // the mixed path keeps complex samples as float-float pairs only
+      for (int k = 0; k < 2; ++k) {
+        ap.F[k] = a.pzf[ps][k] + ((int64_t)f * a.C * a.ns + s) * a.len[ps][k];
+        ap.fstride[k] = (int64_t)a.len[ps][k] * a.ns;
+      }
+    }
     ap.real = false;
     res = tri_smallest<cd, false>(W, G, n, far, 1, gap, ap, tk);
   }
