@@ -974,7 +974,8 @@ __global__ void k_sample_solve(SampleArgs a, int nreal) {
       }
     }
     ap.real = false;
-    res = tri_smallest<cd, false>(W, G, n, far, 1, gap, ap, tk);
+    // mixed path: single-precision T and Newton steps against G first
+    res = tri_smallest<cd, false>(W, G, n, far, 1, gap, ap, tk, a.mixed != 0);
   }
 #ifdef CBP_PHASE_TIMING
   if (tk && lane == 0)

@@ -29,18 +29,30 @@
 // re_, cj_, a2_, Ops).
 
 __device__ __forceinline__ double im_(double) { return 0.0; }
-__device__ __forceinline__ double im_(cd x) { return x.im; }
-template <typename E> __device__ __forceinline__ E mk_e(double re, double im);
-template <> __device__ __forceinline__ double mk_e<double>(double re, double) { return re; }
-template <> __device__ __forceinline__ cd mk_e<cd>(double re, double im) { return mk(re, im); }
+__device__ __forceinline__ float im_(float) { return 0.f; }
+template <typename T> __device__ __forceinline__ T im_(cpx<T> x) { return x.im; }
+template <typename E, typename R> __device__ __forceinline__ E mk_e(R re, R im);
+template <> __device__ __forceinline__ double mk_e<double, double>(double re, double) { return re; }
+template <> __device__ __forceinline__ cd mk_e<cd, double>(double re, double im) { return mk(re, im); }
+template <> __device__ __forceinline__ cf mk_e<cf, float>(float re, float im) { return mk(re, im); }
 __device__ __forceinline__ double mul_(double a, double b) { return a * b; }
-__device__ __forceinline__ cd mul_(cd a, cd b) { return a * b; }
+template <typename T> __device__ __forceinline__ cpx<T> mul_(cpx<T> a, cpx<T> b) { return a * b; }
 __device__ __forceinline__ double sc_(double s, double a) { return s * a; }
-__device__ __forceinline__ cd sc_(double s, cd a) { return s * a; }
+template <typename T> __device__ __forceinline__ cpx<T> sc_(T s, cpx<T> a) { return s * a; }
+__device__ __forceinline__ void fma_(cf& acc, cf a, cf b) { cfma(acc, a, b); }
+__device__ __forceinline__ cf warp_sum_e(cf v) { return mk(warp_sum(v.re), warp_sum(v.im)); }
+// real scalar type of an element type
+template <typename E> struct RealOf { using type = E; };
+template <typename T> struct RealOf<cpx<T>> { using type = T; };
+// reflector element -> vector element
+__device__ __forceinline__ cd to_v(double x, cd) { return mk(x, 0.0); }
+__device__ __forceinline__ cd to_v(cd x, cd) { return x; }
+__device__ __forceinline__ cf to_v(cf x, cf) { return x; }
 
 // Per-warp work area.
 struct TriWs {
-  void* A;        // E[n * n]: the matrix; row k then holds reflector v_k (k+1..n-1)
+  void* A;        // E[n * n]: the matrix; row k then holds reflector v_k (k+1..n-1); 16 (n^2 + n)
+                  // bytes: the single-precision path keeps Q (cf [n][n + 1]) behind its reflectors
   void* tau;      // E[n]
   void* w;        // E[n]
   double* d;      // [n] diagonal of T
@@ -63,7 +75,7 @@ struct TriWs {
 // Bytes of one warp's work area; a multiple of 128, so that every warp's area
 // (placed back to back) and each of its 16-byte-aligned parts stay aligned.
 __host__ __device__ inline size_t tri_ws_bytes(int n) {
-  const size_t b = (size_t)16 * ((size_t)n * n + 2 * n) + (size_t)8 * 7 * n + (size_t)4 * 3 * n +
+  const size_t b = (size_t)16 * ((size_t)n * n + 3 * n) + (size_t)8 * 7 * n + (size_t)4 * 3 * n +
                    16 + (size_t)16 * 4 * n + 16 * 18;   // + alignment of the 18 parts
   return (b + 127) & ~size_t(127);
 }
@@ -75,7 +87,7 @@ __device__ inline TriWs carve_tri(char* p, int n) {
     p += (bytes + 15) & ~size_t(15);
     return q;
   };
-  W.A = take((size_t)16 * n * n);
+  W.A = take((size_t)16 * n * n + (size_t)16 * n);
   W.tau = take((size_t)16 * n);
   W.w = take((size_t)16 * n);
   W.x = (cd*)take((size_t)16 * n);
@@ -100,27 +112,29 @@ __device__ inline TriWs carve_tri(char* p, int n) {
 // (row k of A from column k + 1 on, v_k[k + 1] = 1) describe
 // Q = H_0 H_1 ... H_{n-2} with A_in = Q T Q^H.
 template <typename E>
-__device__ void tri_reduce(E* A, E* tau, E* w, double* d, double* e, int n) {
+__device__ void tri_reduce(E* A, E* tau, E* w, typename RealOf<E>::type* d,
+                           typename RealOf<E>::type* e, int n) {
+  using R = typename RealOf<E>::type;
   const int lane = threadIdx.x & 31;
   for (int k = 0; k + 1 < n; ++k) {
     const int k1 = k + 1;
     E* vk = A + (size_t)k * n;             // row k = conj(column k)
     const E alpha = cj_(vk[k1]);
-    double xn2 = 0.0;
+    R xn2 = R(0);
     for (int i = lane; i < n; i += 32)
       if (i > k1) xn2 += a2_(vk[i]);
     xn2 = warp_sum(xn2);
-    const double ar = re_(alpha), ai = im_(alpha);
+    const R ar = re_(alpha), ai = im_(alpha);
     E tk = Ops<E>::z();
-    double beta = ar;
-    if (xn2 > 0.0 || ai != 0.0) {
+    R beta = ar;
+    if (xn2 > R(0) || ai != R(0)) {
       // H^H (alpha, x) = (beta, 0) with beta real, |beta| = |(alpha, x)|
       beta = -copysign(sqrt(ar * ar + ai * ai + xn2), ar);
-      const double ib = 1.0 / beta;
-      tk = mk_e<E>((beta - ar) * ib, -ai * ib);
+      const R ib = R(1) / beta;
+      tk = mk_e<E, R>((beta - ar) * ib, -ai * ib);
       // v = x / (alpha - beta)
-      const double dr = ar - beta, dn = 1.0 / (dr * dr + ai * ai);
-      const E scl = mk_e<E>(dr * dn, -ai * dn);
+      const R dr = ar - beta, dn = R(1) / (dr * dr + ai * ai);
+      const E scl = mk_e<E, R>(dr * dn, -ai * dn);
       __syncwarp();
       for (int i = lane; i < n; i += 32) {
         if (i > k1) vk[i] = mul_(cj_(vk[i]), scl);
@@ -146,14 +160,20 @@ __device__ void tri_reduce(E* A, E* tau, E* w, double* d, double* e, int n) {
       const int i = lane + 32 * c;
       y[c] = Ops<E>::z();
       if (i > k && i < n) {
-        E acc = Ops<E>::z();
-        for (int j = k1; j < n; ++j) fma_(acc, cj_(A[(size_t)j * n + i]), vk[j]);
+        E acc = Ops<E>::z(), acc1 = Ops<E>::z();   // two chains for latency
+        int j = k1;
+        for (; j + 1 < n; j += 2) {
+          fma_(acc, cj_(A[(size_t)j * n + i]), vk[j]);
+          fma_(acc1, cj_(A[(size_t)(j + 1) * n + i]), vk[j + 1]);
+        }
+        if (j < n) fma_(acc, cj_(A[(size_t)j * n + i]), vk[j]);
+        acc = acc + acc1;
         y[c] = mul_(tk, acc);
         fma_(dotl, cj_(vk[i]), y[c]);
       }
     }
     const E dot = warp_sum_e(dotl);
-    const double hc = 0.5 * re_(mul_(cj_(tk), dot));
+    const R hc = R(0.5) * re_(mul_(cj_(tk), dot));
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       const int i = lane + 32 * c;
@@ -280,76 +300,91 @@ __device__ __forceinline__ double rsqrt_safe(double x) {
 __device__ __forceinline__ double clamp_pivot(double x, double tiny) {
   return fabs(x) >= tiny ? x : (dneg(x) ? -tiny : tiny);
 }
-__device__ void tri_lu(const TriWs& W, int n, double sig, double tiny) {
+__device__ __forceinline__ float rcp_safe(float x) { return 1.0f / x; }
+__device__ __forceinline__ float clamp_pivot(float x, float tiny) {
+  return fabsf(x) >= tiny ? x : (x < 0.f ? -tiny : tiny);
+}
+template <typename R>
+__device__ void tri_lu(const R* d, const R* e, R* u0, R* u1, R* u2, R* lm, int* pv, int n, R sig,
+                       R tiny) {
   if ((threadIdx.x & 31) != 0) return;
   for (int i = 0; i < n; ++i) {
-    W.u0[i] = W.d[i] - sig;
-    W.u1[i] = i + 1 < n ? W.e[i] : 0.0;
-    W.u2[i] = 0.0;
+    u0[i] = d[i] - sig;
+    u1[i] = i + 1 < n ? e[i] : R(0);
+    u2[i] = R(0);
   }
   for (int i = 0; i + 1 < n; ++i) {
-    const double sub = W.e[i];   // element (i + 1, i)
-    const double piv = W.u0[i];
+    const R sub = e[i];   // element (i + 1, i)
+    const R piv = u0[i];
     if (fabs(piv) >= fabs(sub)) {
-      const double r = rcp_safe(clamp_pivot(piv, tiny));
-      const double m = sub * r;
-      W.lm[i] = m;
-      W.piv[i] = 0;
-      W.u0[i] = r;
-      W.u0[i + 1] -= m * W.u1[i];
+      const R r = rcp_safe(clamp_pivot(piv, tiny));
+      const R m = sub * r;
+      lm[i] = m;
+      pv[i] = 0;
+      u0[i] = r;
+      u0[i + 1] -= m * u1[i];
     } else {
-      const double r = rcp_safe(sub);
-      const double m = piv * r;
-      const double a1 = W.u0[i + 1], b1 = W.u1[i + 1];
-      W.lm[i] = m;
-      W.piv[i] = 1;
-      W.u0[i] = r;
-      W.u0[i + 1] = W.u1[i] - m * a1;
-      W.u1[i + 1] = -m * b1;
-      W.u1[i] = a1;
-      W.u2[i] = b1;
+      const R r = rcp_safe(sub);
+      const R m = piv * r;
+      const R a1 = u0[i + 1], b1 = u1[i + 1];
+      lm[i] = m;
+      pv[i] = 1;
+      u0[i] = r;
+      u0[i + 1] = u1[i] - m * a1;
+      u1[i + 1] = -m * b1;
+      u1[i] = a1;
+      u2[i] = b1;
     }
   }
-  W.u0[n - 1] = rcp_safe(clamp_pivot(W.u0[n - 1], tiny));
+  u0[n - 1] = rcp_safe(clamp_pivot(u0[n - 1], tiny));
+}
+__device__ __forceinline__ void tri_lu(const TriWs& W, int n, double sig, double tiny) {
+  tri_lu<double>(W.d, W.e, W.u0, W.u1, W.u2, W.lm, W.piv, n, sig, tiny);
 }
 
-// Solve (T - sig I) z = b in place (lane 0 only), b complex.
-__device__ void tri_solve(const TriWs& W, int n, cd* b) {
+// Solve (T - sig I) z = b in place from tri_lu's factors (lane 0 only).
+template <typename R, typename V>
+__device__ void tri_solve(const R* u0, const R* u1, const R* u2, const R* lm, const int* pv, int n,
+                          V* b) {
   if ((threadIdx.x & 31) != 0) return;
   for (int i = 0; i + 1 < n; ++i) {
-    if (W.piv[i]) {
-      const cd t = b[i];
+    if (pv[i]) {
+      const V t = b[i];
       b[i] = b[i + 1];
       b[i + 1] = t;
     }
-    b[i + 1] = b[i + 1] - W.lm[i] * b[i];
+    b[i + 1] = b[i + 1] - lm[i] * b[i];
   }
   for (int i = n - 1; i >= 0; --i) {
-    cd v = b[i];
-    if (i + 1 < n) v = v - W.u1[i] * b[i + 1];
-    if (i + 2 < n) v = v - W.u2[i] * b[i + 2];
-    b[i] = W.u0[i] * v;
+    V v = b[i];
+    if (i + 1 < n) v = v - u1[i] * b[i + 1];
+    if (i + 2 < n) v = v - u2[i] * b[i + 2];
+    b[i] = u0[i] * v;
   }
 }
+__device__ __forceinline__ void tri_solve(const TriWs& W, int n, cd* b) {
+  tri_solve<double, cd>(W.u0, W.u1, W.u2, W.lm, W.piv, n, b);
+}
 
-// Apply Q (back = true: b <- Q b) or Q^H (b <- Q^H b) to b (n, complex).
-template <typename E>
-__device__ void tri_apply_q(const E* A, const E* tau, int n, cd* b, bool back) {
+// Apply Q (back = true: b <- Q b) or Q^H (b <- Q^H b) to b (n, complex V).
+template <typename E, typename V>
+__device__ void tri_apply_q(const E* A, const E* tau, int n, V* b, bool back) {
+  using R = typename RealOf<V>::type;
   const int lane = threadIdx.x & 31;
   __syncwarp();
   for (int s = 0; s + 1 < n; ++s) {
     const int k = back ? n - 2 - s : s;
-    const cd tk = to_cd(tau[k]);
-    if (tk.re == 0.0 && tk.im == 0.0) continue;
+    const V tk = to_v(tau[k], V());
+    if (tk.re == R(0) && tk.im == R(0)) continue;
     const E* vk = A + (size_t)k * n;
-    cd acc = mk(0.0, 0.0);
+    V acc = mk(R(0), R(0));
     for (int i = lane; i < n; i += 32)
-      if (i > k) cfmac(acc, to_cd(vk[i]), b[i]);   // v^H b
+      if (i > k) cfmac(acc, to_v(vk[i], V()), b[i]);   // v^H b
     acc = mk(warp_sum(acc.re), warp_sum(acc.im));
-    const cd f = (back ? tk : conj(tk)) * acc;
+    const V f = (back ? tk : conj(tk)) * acc;
     __syncwarp();
     for (int i = lane; i < n; i += 32)
-      if (i > k) b[i] = b[i] - f * to_cd(vk[i]);
+      if (i > k) b[i] = b[i] - f * to_v(vk[i], V());
     __syncwarp();
   }
 }
@@ -492,7 +527,7 @@ __device__ int tri_solve_lead(const TriWs& W, const cd* G, int n, int steps_far,
   }
   // 4. x = Q y
   for (int i = lane; i < n; i += 32) W.x[i] = W.z[i];
-  tri_apply_q<E>(A, tau, n, W.x, true);
+  tri_apply_q<E, cd>(A, tau, n, W.x, true);
   {
     const double sc = rsqrt_safe(tri_norm2(W.x, n));
     for (int i = lane; i < n; i += 32) W.x[i] = sc * W.x[i];
@@ -505,6 +540,198 @@ __device__ int tri_solve_lead(const TriWs& W, const cd* G, int n, int steps_far,
   res.near_degenerate = n > 1 && (lam1 - lam0) <= 1e-4 * lamn ? 1 : 0;
   const bool near = n > 1 && (lam1 - lam0) <= refine_gap * lamn;
   return near ? steps_near : steps_far;
+}
+
+// Steps 1-4 in single precision, then Newton steps in Olsen's form against
+// G itself: the residual G x - theta x in double precision, the correction
+// equation solved through the single-precision T (contraction ~n u ||T|| /
+// gap per step), until the correction stops shrinking or falls below 1e-10.
+// For complex matrices whose two smallest eigenvalues single precision
+// separates by more than 1e-4 lambda_max; returns false, having changed
+// nothing but the work area, for the others (they take tri_solve_lead).
+__device__ bool tri_solve_lead_sp(const TriWs& W, const cd* G, int n, TriResult& res, double& gs,
+                                  double& tnorm, long long* tk) {
+  const int lane = threadIdx.x & 31;
+  cf* A = (cf*)W.A;
+  cf* tau = (cf*)W.tau;
+  float* d = W.df;
+  float* e = (float*)W.e;
+  float* u0 = (float*)W.u0;
+  float* u1 = (float*)W.u1;
+  float* u2 = (float*)W.u2;
+  float* lm = (float*)W.lm;
+  double gmax = 0.0;
+  for (int i = lane; i < n; i += 32) gmax = fmax(gmax, G[(size_t)i * n + i].re);
+  gmax = warp_max(gmax);
+  if (!(gmax > 0.0)) return false;
+  int ex;
+  frexp(gmax, &ex);
+  gs = ldexp(1.0, ex);
+  const double igs = ldexp(1.0, -ex);
+  const float igsf = (float)igs;
+  for (int idx = lane; idx < n * n; idx += 32)
+    A[idx] = mk((float)G[idx].re * igsf, (float)G[idx].im * igsf);
+  __syncwarp();
+  if (tk && lane == 0) tk[0] = clock64();
+  tri_reduce<cf>(A, tau, (cf*)W.w, d, e, n);
+  if (tk && lane == 0) tk[1] = clock64();
+  float glo = 1e30f, ghi = -1e30f;
+  for (int i = lane; i < n; i += 32) {
+    const float rad = (i > 0 ? fabsf(e[i - 1]) : 0.f) + (i + 1 < n ? fabsf(e[i]) : 0.f);
+    glo = fminf(glo, d[i] - rad);
+    ghi = fmaxf(ghi, d[i] + rad);
+    W.e2f[i] = i + 1 < n ? e[i] * e[i] : 0.f;
+  }
+  glo = -warp_max(-glo);
+  ghi = warp_max(ghi);
+  tnorm = fmax(fabs((double)glo), fabs((double)ghi));
+  __syncwarp();
+  const int which[3] = {0, 1, n - 1};
+  const double eb = 4e-6 * tnorm;     // single-precision error bound of the counts
+  Bracket br[3];
+  for (int m = 0; m < 3; ++m) br[m] = Bracket{(double)glo - eb, (double)ghi + eb};
+  const float tiny_f = (float)(1e-30 * fmax(tnorm, 1e-8));
+  for (int round = 0; round < 14; ++round) {
+    int t = -1;
+    for (int m = 2; m >= 0; --m)
+      if (br[m].hi - br[m].lo > 0.25 * eb) t = m;
+    if (t < 0) break;
+    multisect<true>(W, n, t, br, 3, which, tiny_f);
+  }
+  const double lam0 = 0.5 * (br[0].lo + br[0].hi), lam1 = 0.5 * (br[1].lo + br[1].hi);
+  const double lamn = 0.5 * (br[2].lo + br[2].hi);
+  // separated beyond the error bounds?
+  if (!((br[1].lo - eb) - (br[0].hi + eb) > 1e-4 * lamn)) return false;
+  if (tk && lane == 0) tk[2] = clock64();
+  // inverse iteration in single precision (three steps)
+  tri_lu<float>(d, e, u0, u1, u2, lm, W.piv, n, (float)lam0, (float)(1.2e-7 * tnorm));
+  cf* y = (cf*)W.z;
+  for (int i = lane; i < n; i += 32) y[i] = mk(1.0f + 0.25f * (float)((i * 7) % 5), 0.f);
+  __syncwarp();
+  for (int it = 0; it < 3; ++it) {
+    tri_solve<float, cf>(u0, u1, u2, lm, W.piv, n, y);
+    __syncwarp();
+    float s2 = 0.f;
+    for (int i = lane; i < n; i += 32) s2 += abs2(y[i]);
+    s2 = warp_sum(s2);
+    const float sc = s2 > 0.f ? rsqrtf(s2) : 1.f;
+    for (int i = lane; i < n; i += 32) y[i] = sc * y[i];
+    __syncwarp();
+  }
+  // Q explicitly (lane i builds column i: H_0 ... H_{n-2} e_i), row stride n + 1
+  cf* Q = A + (size_t)n * n;
+  const int lq = n + 1;
+  for (int i = lane; i < n; i += 32) {
+    for (int j = 0; j < n; ++j) Q[(size_t)j * lq + i] = mk(j == i ? 1.f : 0.f, 0.f);
+    for (int k = n - 2; k >= 0; --k) {
+      const cf tk = tau[k];
+      if (tk.re == 0.f && tk.im == 0.f) continue;
+      const cf* vk = A + (size_t)k * n;
+      cf s0 = mk(0.f, 0.f), s1 = mk(0.f, 0.f);
+      int j = k + 1;
+      for (; j + 1 < n; j += 2) {
+        cfmac(s0, vk[j], Q[(size_t)j * lq + i]);
+        cfmac(s1, vk[j + 1], Q[(size_t)(j + 1) * lq + i]);
+      }
+      if (j < n) cfmac(s0, vk[j], Q[(size_t)j * lq + i]);
+      const cf f = tk * (s0 + s1);
+      for (int jj = k + 1; jj < n; ++jj) Q[(size_t)jj * lq + i] = Q[(size_t)jj * lq + i] - f * vk[jj];
+    }
+  }
+  __syncwarp();
+  // x = Q y
+  for (int i = lane; i < n; i += 32) {
+    cf acc = mk(0.f, 0.f);
+    for (int j = 0; j < n; ++j) cfma(acc, Q[(size_t)i * lq + j], y[j]);
+    W.x[i] = mk((double)acc.re, (double)acc.im);
+  }
+  __syncwarp();
+  {
+    const double sc = rsqrt_safe(tri_norm2(W.x, n));
+    for (int i = lane; i < n; i += 32) W.x[i] = sc * W.x[i];
+    __syncwarp();
+  }
+  if (tk && lane == 0) tk[3] = clock64();
+  // Newton steps against G
+  cf* rt = (cf*)W.q;          // Q^H r, then u
+  cf* zt = rt + n;            // Q^H x, then z
+  cf* yt = (cf*)W.z;          // Q^H x
+  cf* yq = yt + n;            // x in single precision
+  cf* rq = (cf*)W.r;          // r in single precision, then d~
+  double dprev = 1e300;
+  for (int it = 0; it < 8; ++it) {
+    cd gx[2];
+    cd th = mk(0.0, 0.0);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int i = lane + 32 * c;
+      gx[c] = mk(0.0, 0.0);
+      if (i < n) {
+        for (int j = 0; j < n; ++j) cfmac(gx[c], G[(size_t)j * n + i], W.x[j]);   // (G x)_i
+        cfmac(th, W.x[i], gx[c]);
+      }
+    }
+    const double theta = warp_sum(th.re);
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int i = lane + 32 * c;
+      if (i < n) {
+        const cd r = gx[c] - theta * W.x[i];
+        rq[i] = mk((float)r.re, (float)r.im);
+        yq[i] = mk((float)W.x[i].re, (float)W.x[i].im);
+      }
+    }
+    __syncwarp();
+    // r~ = Q^H r, y~ = Q^H x (lane i: column i of Q)
+    for (int i = lane; i < n; i += 32) {
+      cf a0 = mk(0.f, 0.f), a1 = mk(0.f, 0.f);
+      for (int j = 0; j < n; ++j) {
+        const cf q = Q[(size_t)j * lq + i];
+        cfmac(a0, q, yq[j]);
+        cfmac(a1, q, rq[j]);
+      }
+      yt[i] = a0;
+      zt[i] = a0;
+      rt[i] = a1;
+    }
+    tri_lu<float>(d, e, u0, u1, u2, lm, W.piv, n, (float)(theta * igs), (float)(1.2e-7 * tnorm));
+    __syncwarp();
+    tri_solve<float, cf>(u0, u1, u2, lm, W.piv, n, rt);   // u
+    tri_solve<float, cf>(u0, u1, u2, lm, W.piv, n, zt);   // z
+    __syncwarp();
+    cf nu = mk(0.f, 0.f), de = mk(0.f, 0.f);
+    for (int i = lane; i < n; i += 32) {
+      cfmac(nu, yt[i], rt[i]);
+      cfmac(de, yt[i], zt[i]);
+    }
+    nu = mk(warp_sum(nu.re), warp_sum(nu.im));
+    de = mk(warp_sum(de.re), warp_sum(de.im));
+    const float dd = abs2(de);
+    const cf epsn = dd > 0.f ? (1.0f / dd) * (nu * conj(de)) : mk(0.f, 0.f);
+    const float ig = (float)igs;
+    for (int i = lane; i < n; i += 32) rq[i] = ig * (epsn * zt[i] - rt[i]);
+    __syncwarp();
+    float d2 = 0.f;
+    for (int i = lane; i < n; i += 32) {   // d = Q d~ (lane i: row i of Q)
+      cf acc = mk(0.f, 0.f);
+      for (int j = 0; j < n; ++j) cfma(acc, Q[(size_t)i * lq + j], rq[j]);
+      W.x[i] = W.x[i] + mk((double)acc.re, (double)acc.im);
+      d2 += abs2(acc);
+    }
+    d2 = warp_sum(d2);
+    __syncwarp();
+    const double sc = rsqrt_safe(tri_norm2(W.x, n));
+    for (int i = lane; i < n; i += 32) W.x[i] = sc * W.x[i];
+    __syncwarp();
+    const double dn = sqrt((double)d2);
+    if (dn < 1e-10 || dn > 0.25 * dprev) break;
+    dprev = dn;
+  }
+  res.lam_min = gs * lam0;
+  res.lam_2 = gs * lam1;
+  res.lam_max = gs * lamn;
+  res.near_degenerate = 0;
+  return true;
 }
 
 // One refinement step by the lead warp after r = (exact operator) x: Olsen's
@@ -523,8 +750,8 @@ __device__ void tri_olsen(const TriWs& W, int n, double gs, double tnorm) {
     W.q[i] = W.x[i];
   }
   // to T coordinates: r~ = Q^H r, y~ = Q^H x
-  tri_apply_q<E>(A, tau, n, W.r, false);
-  tri_apply_q<E>(A, tau, n, W.q, false);
+  tri_apply_q<E, cd>(A, tau, n, W.r, false);
+  tri_apply_q<E, cd>(A, tau, n, W.q, false);
   tri_lu(W, n, theta * igs, eps * tnorm);
   for (int i = lane; i < n; i += 32) W.z[i] = W.q[i];
   __syncwarp();
@@ -542,7 +769,7 @@ __device__ void tri_olsen(const TriWs& W, int n, double gs, double tnorm) {
   const cd epsn = dd > 0.0 ? (1.0 / dd) * (nu * conj(de)) : mk(0.0, 0.0);
   // d = (-u + eps z) / gs in T coordinates, then back
   for (int i = lane; i < n; i += 32) W.z[i] = igs * (epsn * W.z[i] - W.r[i]);
-  tri_apply_q<E>(A, tau, n, W.z, true);
+  tri_apply_q<E, cd>(A, tau, n, W.z, true);
   for (int i = lane; i < n; i += 32) W.x[i] = W.x[i] + W.z[i];
   __syncwarp();
   const double sc = rsqrt_safe(tri_norm2(W.x, n));
@@ -556,17 +783,21 @@ __device__ void tri_olsen(const TriWs& W, int n, double gs, double tnorm) {
 // `steps_near` otherwise.  apply(x, out): out = (exact operator) x, by the
 // whole CTA (BLOCK) or by the calling warp.  BLOCK: every thread of the CTA
 // calls; warp 0 does all but the operator; the result is valid in warp 0.
+// single: complex matrices try the single-precision solve first.
 template <typename E, bool BLOCK, class Apply>
 __device__ TriResult tri_smallest(const TriWs& W, const cd* G, int n, int steps_far,
                                   int steps_near, double refine_gap, const Apply& apply,
-                                  long long* tk = nullptr) {
+                                  long long* tk = nullptr, bool single = false) {
   const int lane = threadIdx.x & 31;
   const bool lead = !BLOCK || threadIdx.x < 32;
   TriResult res = {};
   double gs = 1.0, tnorm = 0.0;
   int steps = 0;
   if (lead) {
-    steps = tri_solve_lead<E>(W, G, n, steps_far, steps_near, refine_gap, res, gs, tnorm, tk);
+    if (single && n > 2 && tri_solve_lead_sp(W, G, n, res, gs, tnorm, tk))
+      steps = 0;
+    else
+      steps = tri_solve_lead<E>(W, G, n, steps_far, steps_near, refine_gap, res, gs, tnorm, tk);
     if (BLOCK && lane == 0) W.iv[0] = steps;
   }
   if (BLOCK) {
