@@ -128,15 +128,30 @@ class ClockSampler:
         self.device = device
         self.proc = None
         self.out = None
+        self.skip = 0
 
     def start(self):
+        """Start sampling every 100 ms; returns once the first sample is in, so
+        that the timed region that follows is covered from its start."""
+        self.skip = 0
         try:
             self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", str(self.device)], stdout=self.out, stderr=subprocess.DEVNULL)
+                 "-lms", "100", "-i", str(self.device)], stdout=self.out, stderr=subprocess.DEVNULL)
         except OSError:
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < 10.0 and self.proc.poll() is None:
+            if Path(self.out.name).read_text().strip():
+                break
+            time.sleep(0.02)
+
+    def mark(self):
+        """Samples taken before this call (warm-up) are not counted."""
+        if self.proc:
+            self.skip = len([l for l in Path(self.out.name).read_text().splitlines() if l.strip()])
 
     def stop(self):
         if not self.proc:
@@ -148,6 +163,7 @@ class ClockSampler:
             self.proc.kill()
         self.out.flush()
         rows = [l.split(",") for l in Path(self.out.name).read_text().splitlines() if l.strip()]
+        rows = rows[max(0, self.skip - 1):]   # the sample just before the region, and those in it
         os.unlink(self.out.name)
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
@@ -475,6 +491,7 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    clocks.mark()
     ev[0].record(stream)
     for i in range(args.steps):
         step()

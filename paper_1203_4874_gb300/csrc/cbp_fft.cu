@@ -245,16 +245,15 @@ __global__ void k_twiddles(cpx<T>* tw, int n) {
 }
 
 // Kernel spectra K^_k[u][v], u < Ph, v < Pw2, from the double kernels:
-// kv[p][v] = sum_q K[p][q] w_Pw^{vq} (double), then K^[u][v] = sum_p kv[p][v] w_Ph^{up}.
 // Spectra of both kernels on the Ph x Pw grid (Pw/2 + 1 columns kept):
 //   K^(u, v) = sum_p w_H^(u p) R_p(v),   R_p(v) = sum_q K[p][q] w_W^(q v).
-// A block takes 32 columns of one kernel: first the t row transforms R_p(v)
-// (lane = column), then every u with lanes on consecutive columns (one
-// coalesced 256-byte row segment per warp store), UB rows at a time so that
-// each R_p(v) read serves UB outputs; the row twiddles w_H^(u p) sit in shared
-// memory and are read as broadcasts.
-constexpr int kSpecCols = 32;
-constexpr int kSpecRows = 4;
+// A block takes 64 columns of one kernel: first the t row transforms R_p(v),
+// then every u with each lane on two columns (v, v + 32: coalesced 256-byte
+// row segments per warp store), kSpecRows rows at a time so that each R_p(v)
+// read serves kSpecRows outputs and each row twiddle w_H^(u p) (shared
+// memory, read as a broadcast) serves two.
+constexpr int kSpecCols = 64;
+constexpr int kSpecRows = 8;
 
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads)
@@ -284,29 +283,34 @@ k_kernel_spectra(const double* kd, int t1, int t2, int Ph, int Pw, int Pw2, int 
   __syncthreads();
   cpx<T>* out = khat + ((int64_t)f * 2 + k) * Ph * Pw2p;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  const int v = v0 + lane;
+  const int va = v0 + lane, vb = v0 + 32 + lane;
   for (int u0 = warp * kSpecRows; u0 < Ph; u0 += nw * kSpecRows) {
-    cpx<T> acc[kSpecRows];
+    cpx<T> acc[kSpecRows][2];
     int e[kSpecRows], du[kSpecRows];          // (u p) mod Ph per row, incrementally
 #pragma unroll
     for (int j = 0; j < kSpecRows; ++j) {
-      acc[j] = mk<T>(0, 0);
+      acc[j][0] = acc[j][1] = mk<T>(0, 0);
       e[j] = 0;
       du[j] = u0 + j < Ph ? u0 + j : 0;       // rows past Ph are computed as u = 0, not stored
     }
     for (int p = 0; p < t; ++p) {
-      const cpx<T> r = kv[p * kSpecCols + lane];
+      const cpx<T> ra = kv[p * kSpecCols + lane], rb = kv[p * kSpecCols + 32 + lane];
 #pragma unroll
       for (int j = 0; j < kSpecRows; ++j) {
-        cfma(acc[j], r, twh[e[j]]);
+        const cpx<T> w = twh[e[j]];
+        cfma(acc[j][0], ra, w);
+        cfma(acc[j][1], rb, w);
         e[j] += du[j];
         if (e[j] >= Ph) e[j] -= Ph;
       }
     }
-    if (v < Pw2) {
 #pragma unroll
-      for (int j = 0; j < kSpecRows; ++j)
-        if (u0 + j < Ph) out[(int64_t)(u0 + j) * Pw2p + v] = acc[j];
+    for (int j = 0; j < kSpecRows; ++j) {
+      if (u0 + j < Ph) {
+        cpx<T>* o = out + (int64_t)(u0 + j) * Pw2p;
+        if (va < Pw2) o[va] = acc[j][0];
+        if (vb < Pw2) o[vb] = acc[j][1];
+      }
     }
   }
 }

@@ -21,8 +21,9 @@
 // Only samples s <= M/2 are solved; sample M - s is the conjugate.
 //
 // Per pair (one CTA): lift the cofactors to the two M x M estimates of the
-// kernels' 2D DFT, solve the least-squares scale system (block Jacobi eigen-solver on
-// its 2M x 2M normal matrix, exact residual in the FP64 path), average,
+// kernels' 2D DFT, solve the least-squares scale system (the tridiagonal
+// eigen-solver on its 2M x 2M normal matrix, one exact-residual step on the
+// FP64 path), average,
 // normalise to unit kernel sum, inverse M x M DFT (Section 5).
 #include "cbp_common.cuh"
 #include "cbp_internal.h"
@@ -47,7 +48,6 @@ constexpr int kSolveThreads = 256;
   do {                   \
   } while (0)
 #endif
-constexpr int kMaxSweeps = 15;
 
 // ------------------------------------------------------------ block helpers
 __device__ __forceinline__ double block_sum(double v, double* red) {
@@ -62,51 +62,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;
 }
 
-// Shared-memory work area of the eigen-solver for an N x N Hermitian matrix.
-struct EigSmem {
-  cd* G;       // N*N   double-precision matrix (input, preserved)
-  cd* L;       // NP*NP double-precision working area (hard samples)
-  cd* Q;       // NP*NP double-precision orthonormal basis (hard samples)
-  cf* A;       // NP*NP single-precision working copy -> eigenvalues on the diagonal
-  cf* V;       // NP*NP single-precision eigenvectors; with A, the double
-               //       eigenvectors of hard samples
-  cd* x;       // N
-  cd* y;       // N
-  cd* r;       // N
-  cd* z;       // N
-  double* lam; // N eigenvalues of the single-precision solve (unscaled)
-  double* rc;  // NP/2 rotation cosines (float or double view)
-  cd* rs;      // NP/2 rotation s * phase (float or double view)
-  int* rp;     // NP/2
-  int* rq;     // NP/2
-  double* red; // 32 (reduction scratch)
-  int* flag;   // 4 ints
-  double* sc;  // 8 doubles (scalars)
-};
-
-struct EigResult {
-  double lam_max;   // largest eigenvalue
-  double lam_2;     // second smallest eigenvalue
-  double theta;     // Rayleigh quotient of the returned vector (~ smallest)
-  int hard;         // 1 if solved by the double-precision Jacobi
-};
-
-__device__ __forceinline__ int np_of(int n) { return (n + 1) & ~1; }
-
-__device__ __forceinline__ void jacobi_pair(int round, int k, int np, int* p, int* q) {
-  int a, b;
-  if (k == 0) {
-    a = np - 1;
-    b = round;
-  } else {
-    a = (round + k) % (np - 1);
-    b = (round - k + (np - 1)) % (np - 1);
-  }
-  *p = a < b ? a : b;
-  *q = a < b ? b : a;
-}
-
-// Scalar helpers so one Jacobi serves real (float, double) and complex data.
+// Scalar helpers so one solver serves real (float, double) and complex data.
 __device__ __forceinline__ float re_(float x) { return x; }
 __device__ __forceinline__ double re_(double x) { return x; }
 template <typename T> __device__ __forceinline__ T re_(cpx<T> x) { return x.re; }
@@ -119,12 +75,6 @@ template <typename T> __device__ __forceinline__ T a2_(cpx<T> x) { return abs2(x
 __device__ __forceinline__ double warp_sum_e(double v) { return warp_sum(v); }
 __device__ __forceinline__ cd warp_sum_e(cd v) { return mk(warp_sum(v.re), warp_sum(v.im)); }
 template <typename E> struct Ops;
-template <> struct Ops<float> {
-  static __device__ float z() { return 0.f; }
-  static __device__ float o() { return 1.f; }
-  static __device__ void clear_im(float&) {}
-  static __device__ bool nz(float x) { return x != 0.f; }
-};
 template <> struct Ops<double> {
   static __device__ double z() { return 0.0; }
   static __device__ double o() { return 1.0; }
@@ -154,450 +104,10 @@ __device__ __forceinline__ double rsqrt_d(double x) {
 __device__ __forceinline__ float rcp_d(float x) { return 1.0f / x; }
 __device__ __forceinline__ float rsqrt_d(float x) { return rsqrtf(x); }
 
-// Jacobi rotation for the 2x2 Hermitian block [[app, apq], [conj(apq), aqq]]:
-// returns false (identity) unless |apq| exceeds both thresholds; otherwise c
-// and sp = s * apq / |apq| with c^2 + s^2 = 1 to working precision.
-template <typename E, typename R>
-__device__ __forceinline__ bool jacobi_rotation(E apq, R app, R aqq, R abs_tol, R tol_rel, R& c, E& sp) {
-  const R a2 = a2_(apq);
-  const R lim = max(abs_tol, tol_rel * sqrt(fabs(app)) * sqrt(fabs(aqq)));
-  if (!(a2 > lim * lim)) return false;
-  const R rmag = rsqrt_d(a2);                         // 1 / |apq|
-  const R tau = (aqq - app) * (R)0.5 * rmag;
-  R t;
-  if (fabs(tau) > (R)1e15) {
-    t = (R)0.5 * rcp_d(tau);                          // tan of a tiny angle
-  } else {
-    const R h = (R)1 + tau * tau;
-    const R root = h * rsqrt_d(h);                    // sqrt(1 + tau^2)
-    t = (tau >= (R)0 ? (R)1 : (R)-1) * rcp_d(fabs(tau) + root);
-  }
-  c = rsqrt_d((R)1 + t * t);
-  sp = (t * c * rmag) * apq;
-  return true;
-}
-
-// Cyclic Jacobi (round-robin parallel ordering) on the Hermitian matrix A
-// (n x n inside an npad x npad block, npad even >= n, stored with row stride
-// ld = npad + 1 so column walks are free of bank conflicts; element type E real or
-// complex, real type R).  V leaves with the eigenvectors (columns); A leaves
-// with the eigenvalues on its diagonal.  A pair is rotated while |a_pq|
-// exceeds both tol_rel sqrt(|a_pp a_qq|) and tol_abs max|a_ii|; tol_abs is set
-// a few times above the precision's rounding floor (~n u max|a_ii|), below
-// which rotations only stir rounding noise.  At most kMaxSweeps sweeps.
-template <typename E, typename R>
-__device__ void jacobi(E* A, E* V, int n, int npad, int ld, EigSmem& S, R tol_rel, R tol_abs) {
-  const int half = npad / 2;
-  const int tid = threadIdx.x, nth = blockDim.x;
-  R* rc = (R*)S.rc;
-  E* rs = (E*)S.rs;
-  for (int i = tid; i < npad * npad; i += nth) {
-    const int r = i / npad, c = i % npad;
-    V[r * ld + c] = r == c ? Ops<E>::o() : Ops<E>::z();
-    if (r >= n || c >= n) A[r * ld + c] = Ops<E>::z();
-  }
-  __syncthreads();
-  R amax = 0;
-  for (int i = 0; i < n; ++i) amax = max(amax, (R)fabs(re_(A[i * ld + i])));
-  const R abs_tol = tol_abs * amax;
-  for (int sweep = 0; sweep < kMaxSweeps; ++sweep) {
-    if (tid == 0) S.flag[0] = 0;
-    __syncthreads();
-    for (int round = 0; round < npad - 1; ++round) {
-      for (int k = tid; k < half; k += nth) {
-        int p, q;
-        jacobi_pair(round, k, npad, &p, &q);
-        R c = 1;
-        E sp = Ops<E>::z();
-        if (q < n &&
-            jacobi_rotation<E, R>(A[p * ld + q], re_(A[p * ld + p]), re_(A[q * ld + q]), abs_tol,
-                                  tol_rel, c, sp))
-          S.flag[0] = 1;
-        S.rp[k] = p;
-        S.rq[k] = q;
-        rc[k] = c;
-        rs[k] = sp;
-      }
-      __syncthreads();
-      // rows p, q:  A <- J^H A
-      for (int idx = tid; idx < half * n; idx += nth) {
-        const int k = idx / n, j = idx % n;
-        const E sp = rs[k];
-        if (!Ops<E>::nz(sp)) continue;
-        const int p = S.rp[k], q = S.rq[k];
-        const R c = rc[k];
-        const E apj = A[p * ld + j], aqj = A[q * ld + j];
-        A[p * ld + j] = c * apj - sp * aqj;
-        A[q * ld + j] = cj_(sp) * apj + c * aqj;
-      }
-      __syncthreads();
-      // columns p, q:  A <- A J,  V <- V J.  The rotated pair's own entries
-      // are set exactly: a_pq = a_qp = 0, a_pp and a_qq real (only this
-      // thread of rows p and q writes them).
-      for (int idx = tid; idx < half * n; idx += nth) {
-        const int k = idx / n, i = idx % n;
-        const E sp = rs[k];
-        if (!Ops<E>::nz(sp)) continue;
-        const int p = S.rp[k], q = S.rq[k];
-        const R c = rc[k];
-        const E aip = A[i * ld + p], aiq = A[i * ld + q];
-        E np = c * aip - cj_(sp) * aiq, nq = sp * aip + c * aiq;
-        if (i == p) {
-          Ops<E>::clear_im(np);
-          nq = Ops<E>::z();
-        } else if (i == q) {
-          np = Ops<E>::z();
-          Ops<E>::clear_im(nq);
-        }
-        A[i * ld + p] = np;
-        A[i * ld + q] = nq;
-        const E vip = V[i * ld + p], viq = V[i * ld + q];
-        V[i * ld + p] = c * vip - cj_(sp) * viq;
-        V[i * ld + q] = sp * vip + c * viq;
-      }
-      __syncthreads();
-    }
-    const int rotated = S.flag[0];
-    __syncthreads();
-    if (tid == 0) S.flag[1] = sweep + 1;
-    if (!rotated) break;
-  }
-}
-
-// Component i of single-precision eigenvector l (real or complex storage).
-__device__ __forceinline__ cd v32(const EigSmem& S, bool real, int np, int i, int l) {
-  if (real) return mk((double)((const float*)S.V)[i * np + l], 0.0);
-  return cvt<double>(S.V[i * np + l]);
-}
-
-// y = G x (double), G n x n row-major; one warp per row.
-__device__ void matvec64(const cd* G, const cd* x, cd* y, int n) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int p = warp; p < n; p += nw) {
-    cd acc = mk(0.0, 0.0);
-    for (int q = lane; q < n; q += 32) cfma(acc, G[p * n + q], x[q]);
-    acc.re = warp_sum(acc.re);
-    acc.im = warp_sum(acc.im);
-    if (lane == 0) y[p] = acc;
-  }
-  __syncthreads();
-}
-
-// x <- x / ||x||; returns the old norm.
-__device__ double normalize64(cd* x, int n, double* red) {
-  double s = 0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += abs2(x[i]);
-  s = block_sum(s, red);
-  double inv = s > 0 ? rsqrt(s) : 0.0;
-  __syncthreads();
-  for (int i = threadIdx.x; i < n; i += blockDim.x) x[i] = inv * x[i];
-  __syncthreads();
-  return sqrt(s);
-}
-
-// Re(a^H b)
-__device__ double dotre64(const cd* a, const cd* b, int n, double* red) {
-  double s = 0;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) s += a[i].re * b[i].re + a[i].im * b[i].im;
-  return block_sum(s, red);
-}
-
-
-// Newton correction with a double-precision eigenbasis V (ld x ld, columns),
-// eigenvalues lam: x <- normalise(x - sum_{l != imin} v_l (v_l^H res) / (lam_l - theta)),
-// res = r - theta x.  Warp-parallel products.  Returns ||dx||^2.
-__device__ double newton_eigbasis64(EigSmem& S, const cd* V, const double* lam, int n, int ld,
-                                    int imin, const cd* r, double theta) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) S.z[i] = r[i] - theta * S.x[i];
-  __syncthreads();
-  for (int l = warp; l < n; l += nw) {
-    cd c = mk(0.0, 0.0);
-    if (l != imin)
-      for (int i = lane; i < n; i += 32) cfmac(c, V[i * ld + l], S.z[i]);
-    c.re = warp_sum(c.re);
-    c.im = warp_sum(c.im);
-    if (lane == 0) S.y[l] = l != imin ? (1.0 / (lam[l] - theta)) * c : mk(0.0, 0.0);
-  }
-  __syncthreads();
-  double d2 = 0;
-  for (int i = warp; i < n; i += nw) {
-    cd dx = mk(0.0, 0.0);
-    for (int l = lane; l < n; l += 32) cfma(dx, V[i * ld + l], S.y[l]);
-    dx.re = warp_sum(dx.re);
-    dx.im = warp_sum(dx.im);
-    if (lane == 0) {
-      S.x[i] = S.x[i] - dx;
-      d2 += abs2(dx);
-    }
-  }
-  d2 = block_sum(d2, S.red);
-  normalize64(S.x, n, S.red);
-  return d2;
-}
-
 __device__ __forceinline__ void fma_(double& acc, double a, double b) { acc = fma(a, b, acc); }
 __device__ __forceinline__ void fma_(cd& acc, cd a, cd b) { cfma(acc, a, b); }
-__device__ __forceinline__ void fmac_(double& acc, double a, double b) { acc = fma(a, b, acc); }
-__device__ __forceinline__ void fmac_(cd& acc, cd a, cd b) { cfmac(acc, a, b); }
-__device__ __forceinline__ double from_cd(cd v, double) { return v.re; }
-__device__ __forceinline__ cd from_cd(cd v, cd) { return v; }
 __device__ __forceinline__ cd to_cd(double v) { return mk(v, 0.0); }
 __device__ __forceinline__ cd to_cd(cd v) { return v; }
-
-// Orthonormalise the n columns of Q (n x n, leading dimension ld) in double
-// precision: modified Gram-Schmidt with the projections of all later columns
-// done in parallel, applied twice.
-template <typename E>
-__device__ void orthonormalize_cols(E* Q, int n, int ld, double* red) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int pass = 0; pass < 2; ++pass)
-    for (int k = 0; k < n; ++k) {
-      double s2 = 0;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) s2 += a2_(Q[i * ld + k]);
-      s2 = block_sum(s2, red);
-      const double inv = s2 > 0 ? rsqrt(s2) : 0.0;
-      for (int i = threadIdx.x; i < n; i += blockDim.x) Q[i * ld + k] = inv * Q[i * ld + k];
-      __syncthreads();
-      // q_j -= (q_k^H q_j) q_k for every j > k: one warp per column
-      for (int j = k + 1 + warp; j < n; j += nw) {
-        E d = Ops<E>::z();
-        for (int i = lane; i < n; i += 32) fmac_(d, Q[i * ld + k], Q[i * ld + j]);
-        d = warp_sum_e(d);
-        for (int i = lane; i < n; i += 32) Q[i * ld + j] = Q[i * ld + j] - d * Q[i * ld + k];
-      }
-      __syncthreads();
-    }
-}
-
-// Smallest eigenpair of the Hermitian positive semi-definite S.G (n x n; real
-// symmetric when `real`).  acc_steps further Newton steps use
-// apply(x, out) = S^H S x computed from the original system (exact residual).
-// Result vector in S.x (unit norm).
-// Double-precision eigen-decomposition of S.G (element type E: double for real
-// samples, cd otherwise) started from the single-precision eigenvectors.  On
-// exit: eigenvalues in S.lam, the double eigenvectors (as cd, stride ld) in the
-// single-precision area, S.sc[1] = second smallest eigenvalue; returns the
-// index of the smallest.
-template <typename E>
-__device__ int hard_eig(EigSmem& S, int n, int np, int ld, double gscale, long long* tk) {
-  const bool real = sizeof(E) == sizeof(double);
-  E* Q = (E*)S.Q;
-  E* T1 = (E*)S.L;
-  for (int i = threadIdx.x; i < n * n; i += blockDim.x)
-    Q[(i / n) * ld + (i % n)] = from_cd(v32(S, real, ld, i / n, i % n), E());
-  __syncthreads();
-  orthonormalize_cols<E>(Q, n, ld, S.red);
-  if (tk) CBP_TICK(tk, 6);
-  // T1 = (G / gscale) Q
-  const double ig = 1.0 / gscale;
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int i = idx / n, l = idx % n;
-    E acc = Ops<E>::z();
-    for (int j = 0; j < n; ++j) fma_(acc, from_cd(ig * S.G[i * n + j], E()), Q[j * ld + l]);
-    T1[i * ld + l] = acc;
-  }
-  __syncthreads();
-  // A0 = Q^H T1 (Hermitian by construction up to rounding: symmetrised)
-  E* A0 = (E*)S.A;
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int i = idx / n, l = idx % n;
-    E acc = Ops<E>::z();
-    for (int j = 0; j < n; ++j) fmac_(acc, Q[j * ld + i], T1[j * ld + l]);
-    A0[i * ld + l] = acc;
-  }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int i = idx / n, l = idx % n;
-    if (l > i) {
-      const E m = 0.5 * (A0[i * ld + l] + cj_(A0[l * ld + i]));
-      A0[i * ld + l] = m;
-      A0[l * ld + i] = cj_(m);
-    } else if (l == i) {
-      Ops<E>::clear_im(A0[i * ld + i]);
-    }
-  }
-  __syncthreads();
-  if (tk) CBP_TICK(tk, 7);
-  jacobi<E, double>(A0, T1, n, np, ld, S, 1e-15, 4e-16 * (double)n);
-  if (tk) CBP_TICK(tk, 8);
-  for (int i = threadIdx.x; i < n; i += blockDim.x) S.lam[i] = gscale * re_(A0[i * ld + i]);
-  __syncthreads();
-  // V64 = Q W (as cd) over the A0 area, whose eigenvalues are already in S.lam
-  cd* V64 = (cd*)S.A;
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
-    const int i = idx / n, l = idx % n;
-    E acc = Ops<E>::z();
-    for (int j = 0; j < n; ++j) fma_(acc, Q[i * ld + j], T1[j * ld + l]);
-    V64[i * ld + l] = to_cd(acc);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    int a = 0;
-    for (int i = 0; i < n; ++i)
-      if (S.lam[i] < S.lam[a]) a = i;
-    int b = -1;
-    for (int i = 0; i < n; ++i)
-      if (i != a && (b < 0 || S.lam[i] < S.lam[b])) b = i;
-    S.flag[2] = a;
-    S.sc[1] = b >= 0 ? S.lam[b] : S.lam[a];
-  }
-  __syncthreads();
-  return S.flag[2];
-}
-
-// acc_easy / acc_hard: Newton steps against the exact residual (apply) for
-// samples resolved in single precision / in double precision; the latter only
-// where the double gap lambda_2 - lambda_1 is below hard_gap lambda_max.
-// newton_tol: the Newton steps on the normal matrix stop once a step moves x
-// (unit norm) by less than this.
-template <class Apply>
-__device__ EigResult smallest_eigvec(EigSmem& S, int n, bool real, int acc_easy, int acc_hard,
-                                     double hard_gap, double newton_tol, const Apply& apply,
-                                     long long* tk = nullptr) {
-  const int np = np_of(n), ld = np + 1;
-  if (threadIdx.x == 0) {
-    double gs = 0;
-    for (int i = 0; i < n; ++i) gs = fmax(gs, S.G[i * n + i].re);
-    S.sc[4] = gs > 0 ? gs : 1.0;
-  }
-  __syncthreads();
-  const double gscale = S.sc[4];
-  // 1. all eigenpairs in single precision
-  if (real) {
-    float* A = (float*)S.A;
-    for (int i = threadIdx.x; i < n * n; i += blockDim.x)
-      A[(i / n) * ld + (i % n)] = (float)(S.G[i].re / gscale);
-    __syncthreads();
-    jacobi<float, float>(A, (float*)S.V, n, np, ld, S, 1e-7f, 2e-6f * (float)n);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) S.lam[i] = gscale * (double)A[i * ld + i];
-  } else {
-    for (int i = threadIdx.x; i < n * n; i += blockDim.x)
-      S.A[(i / n) * ld + (i % n)] = cvt<float>((1.0 / gscale) * S.G[i]);
-    __syncthreads();
-    jacobi<cf, float>(S.A, S.V, n, np, ld, S, 1e-7f, 2e-6f * (float)n);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) S.lam[i] = gscale * (double)S.A[i * ld + i].re;
-  }
-  __syncthreads();
-  if (tk) CBP_TICK(tk, 3);
-  if (threadIdx.x == 0) {
-    int i1 = 0;
-    double lmax = -1e300;
-    for (int i = 0; i < n; ++i) {
-      if (S.lam[i] < S.lam[i1]) i1 = i;
-      lmax = fmax(lmax, S.lam[i]);
-    }
-    int i2 = -1;
-    for (int i = 0; i < n; ++i)
-      if (i != i1 && (i2 < 0 || S.lam[i] < S.lam[i2])) i2 = i;
-    if (i2 < 0) i2 = i1;
-    S.flag[2] = i1;
-    S.sc[0] = fmax(lmax, 0.0);
-    S.sc[1] = S.lam[i2];
-    S.sc[2] = S.lam[i1];
-  }
-  __syncthreads();
-  const int imin = S.flag[2];
-  const double lmax = S.sc[0];
-  double lam2 = S.sc[1];
-  // single-precision eigenvalues carry errors ~ n u lmax; below a 1e-4 lmax
-  // gap the two smallest are not reliably separated
-  const bool hard = n > 1 && (S.sc[1] - S.sc[2]) <= 1e-4 * lmax;
-  double theta;
-  if (!hard) {
-    // 2a. Newton steps in double precision on G, preconditioned by the
-    // single-precision eigenbasis
-    cd* V64 = S.L;   // the single-precision eigenbasis in double, stride ld
-    for (int i = threadIdx.x; i < n * n; i += blockDim.x)
-      V64[(i / n) * ld + (i % n)] = v32(S, real, ld, i / n, i % n);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) S.x[i] = v32(S, real, ld, i, imin);
-    __syncthreads();
-    normalize64(S.x, n, S.red);
-    // The steps converge linearly with a small ratio (the eigenbasis is
-    // accurate to single precision); stop once a step no longer shrinks the
-    // correction by 4x -- it has reached the double-precision floor -- or it
-    // vanishes.
-    double d2prev = 1e300;
-    int it = 0;
-    for (; it < 12; ++it) {
-      matvec64(S.G, S.x, S.r, n);
-      theta = dotre64(S.x, S.r, n, S.red);
-      const double d2 = newton_eigbasis64(S, V64, S.lam, n, ld, imin, S.r, theta);
-      if (d2 < newton_tol * newton_tol || d2 > 0.25 * d2prev) break;
-      d2prev = d2;
-    }
-    if (threadIdx.x == 0) S.flag[3] = it + 1;
-    for (int it = 0; it < acc_easy; ++it) {
-      apply(S.x, S.r);
-      theta = dotre64(S.x, S.r, n, S.red);
-      newton_eigbasis64(S, V64, S.lam, n, ld, imin, S.r, theta);
-    }
-  } else {
-    // 2b. Unresolved in single precision (the smallest eigenvalues sit below
-    // its rounding floor, e.g. the z = 1 sample): Jacobi in double precision,
-    // started from the single-precision eigenbasis made orthonormal in double
-    // precision, so mostly the unresolved cluster still needs rotations.
-    int i1;
-    if (real) i1 = hard_eig<double>(S, n, np, ld, gscale, tk);
-    else i1 = hard_eig<cd>(S, n, np, ld, gscale, tk);
-    lam2 = S.sc[1];
-    cd* V64 = (cd*)S.A;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) S.x[i] = V64[i * ld + i1];
-    __syncthreads();
-    normalize64(S.x, n, S.red);
-    const int steps = lam2 - S.lam[i1] < hard_gap * lmax ? acc_hard : 0;
-    for (int it = 0; it < steps; ++it) {
-      apply(S.x, S.r);
-      theta = dotre64(S.x, S.r, n, S.red);
-      newton_eigbasis64(S, V64, S.lam, n, ld, i1, S.r, theta);
-    }
-  }
-  if (tk) CBP_TICK(tk, 4);
-  matvec64(S.G, S.x, S.r, n);
-  theta = dotre64(S.x, S.r, n, S.red);
-  EigResult res;
-  res.lam_max = lmax;
-  res.lam_2 = lam2;
-  res.theta = theta;
-  res.hard = hard ? 1 : 0;
-  return res;
-}
-
-// Carve an EigSmem out of dynamic shared memory for dimension n.
-__device__ char* carve_eig(EigSmem& S, char* p, int n) {
-  const int np = np_of(n);
-  auto take = [&](size_t bytes) {
-    char* q = p;
-    p += (bytes + 15) & ~size_t(15);
-    return q;
-  };
-  S.G = (cd*)take(sizeof(cd) * n * n);
-  S.L = (cd*)take(sizeof(cd) * np * (np + 1));
-  S.Q = (cd*)take(sizeof(cd) * np * (np + 1));
-  S.A = (cf*)take(sizeof(cf) * np * (np + 1));
-  S.V = (cf*)take(sizeof(cf) * np * (np + 1));
-  S.x = (cd*)take(sizeof(cd) * n);
-  S.y = (cd*)take(sizeof(cd) * n);
-  S.r = (cd*)take(sizeof(cd) * n);
-  S.z = (cd*)take(sizeof(cd) * n);
-  S.lam = (double*)take(sizeof(double) * n);
-  S.rc = (double*)take(sizeof(double) * np / 2);
-  S.rs = (cd*)take(sizeof(cd) * np / 2);
-  S.rp = (int*)take(sizeof(int) * np / 2);
-  S.rq = (int*)take(sizeof(int) * np / 2);
-  S.red = (double*)take(sizeof(double) * 32);
-  S.flag = (int*)take(sizeof(int) * 4);
-  S.sc = (double*)take(sizeof(double) * 8);
-  return p;
-}
-
-size_t eig_smem_bytes(int n) {
-  const int np = (n + 1) & ~1;
-  auto r = [](size_t b) { return (b + 15) & ~size_t(15); };
-  return r(sizeof(cd) * n * n) + r(sizeof(cd) * np * (np + 1)) * 2 + r(sizeof(cf) * np * (np + 1)) * 2 + r(sizeof(cd) * n) * 4 + r(sizeof(double) * n) +
-         r(sizeof(double) * np / 2) + r(sizeof(cd) * np / 2) + r(sizeof(int) * np / 2) * 2 +
-         r(sizeof(double) * 32) + r(sizeof(int) * 4) + r(sizeof(double) * 8);
-}
 
 // ------------------------------------------------------ per-sample solve ---
 struct SampleArgs {
@@ -1055,6 +565,14 @@ struct ScaleApply {
   }
 };
 
+// Shared memory of k_scale_solve: the normal matrix (2M x 2M complex), block
+// reduction scratch (32 doubles), X and T (3 M^2 complex), then the
+// tridiagonal solver's work area.
+__host__ __device__ inline size_t scale_tri_offset(int M) {
+  return (sizeof(cd) * 4 * M * M + 32 * sizeof(double) + sizeof(cd) * 3 * M * M + 127) &
+         ~size_t(127);
+}
+
 __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
   extern __shared__ __align__(16) char smem[];
   const int f = blockIdx.x;
@@ -1089,8 +607,9 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
   }
   const int M = a.M, MM = M * M, t1 = a.t1, t2 = a.t2;
   const int n = 2 * M;
-  EigSmem S;
-  char* p = carve_eig(S, smem, n);
+  cd* Gs = (cd*)smem;                   // [n][n] normal matrix
+  double* red = (double*)(Gs + n * n);   // block reductions
+  char* p = (char*)(red + 32);
   cd* X = (cd*)p;                 // [2][M][M] kernel spectra, then full inverse DFTs
   cd* T = X + 2 * MM;             // [M][M] temporary
   __shared__ cd wt[kMaxM];
@@ -1139,15 +658,21 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
         g = g - v;
       }
     }
-    S.G[idx] = g;
+    Gs[idx] = g;
   }
   __syncthreads();
+  // Null vector of the scale system by the warp-level tridiagonal solver, one
+  // refinement step against the exact operator (FP64 path); the mixed path
+  // takes its single-precision T with Newton steps against the double G.
   ScaleApply ap{ab, M};
-  EigResult res = smallest_eigvec(S, n, false, 2, 1, 1e300, 1e-15, ap);
+  const TriWs W = carve_tri(smem + scale_tri_offset(M), n);
+  const TriResult res = tri_smallest<cd, true>(W, Gs, n, 1, 1, 1e300, ap, nullptr, a.mixed != 0);
+  __syncthreads();
+  const cd* xs = W.x;
   // X_k[i][j] = (gamma_j A_k[i][j] + delta_i B_k[i][j]) / 2
   for (int idx = threadIdx.x; idx < 2 * MM; idx += blockDim.x) {
     const int k = idx / MM, i = (idx % MM) / M, j = idx % M;
-    X[idx] = 0.5 * (S.x[j] * ab[k * MM + i * M + j] + S.x[M + i] * ab[(2 + k) * MM + i * M + j]);
+    X[idx] = 0.5 * (xs[j] * ab[k * MM + i * M + j] + xs[M + i] * ab[(2 + k) * MM + i * M + j]);
   }
   __syncthreads();
   __shared__ cd x00[2];
@@ -1197,9 +722,9 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
         }
       }
     }
-    l_re = block_sum(l_re, S.red);
-    l_im = block_sum(l_im, S.red);
-    l_out = block_sum(l_out, S.red);
+    l_re = block_sum(l_re, red);
+    l_im = block_sum(l_im, red);
+    l_out = block_sum(l_out, red);
     if (threadIdx.x == 0) {
       double ir = l_re > 0 ? sqrt(l_im / l_re) : 0.0;
       double sr = (l_re + l_im) > 0 ? l_out / (l_re + l_im) : 0.0;
@@ -1279,7 +804,7 @@ __global__ void k_kernels_in(const void* k1, const void* k2, int in_f64, int n, 
 }  // namespace
 
 size_t sample_solve_smem(int nn) { return tri_ws_bytes(nn); }
-size_t scale_solve_smem(int M) { return eig_smem_bytes(2 * M) + sizeof(cd) * 3 * M * M; }
+size_t scale_solve_smem(int M) { return scale_tri_offset(M) + tri_ws_bytes(2 * M); }
 
 void launch_sample_solve(const Plan& p, char* ws, cudaStream_t st) {
   SampleArgs a;
