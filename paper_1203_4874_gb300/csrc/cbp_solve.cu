@@ -234,50 +234,77 @@ __device__ __forceinline__ FF warp_sum_ff(FF v) {
 }
 
 // rho jobs as above from float-float samples: conj(a) b accumulated in
-// float-float, about 1e-13 relative, on the single-precision units.
+// float-float, about 1e-13 relative, on the single-precision units.  The
+// samples pass through shared memory in tiles of kGramChunk positions (plus a
+// halo of kMaxN each side, zero outside the polynomials, so every product
+// outside a lag's overlap is an exact zero); warp w takes the lags
+// j = w, w + 8, ..., a lane the positions lane + 32 r of each tile.  The next
+// tile's loads are in flight while the current one is summed.
+constexpr int kGramChunk = 256;
+constexpr int kGramTile = kGramChunk + 2 * kMaxN;
+constexpr int kGramLags = 8;     // lags per warp and pass
+constexpr int kGramPre = (2 * kGramTile + kSolveThreads - 1) / kSolveThreads;
+
 __device__ void correlations_ff(const cdf* const base[2], const int len[2], int f, int C, int ns,
-                                int s, int t1, int t2, cd* rho) {
+                                int s, int t1, int t2, cd* rho, cdf* tile /* [2][kGramTile] */) {
   const int J = 2 * (t1 + t2) - 1;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int j = warp; j < J; j += nw) {
-    int ka, kb, d;
-    if (j < t1) { ka = 1; kb = 1; d = j; }
-    else if (j < t1 + t2) { ka = 0; kb = 0; d = j - t1; }
-    else { ka = 1; kb = 0; d = j - t1 - t2 - (t2 - 1); }
-    const int la = len[ka], lb = len[kb];
-    const int m0 = d < 0 ? -d : 0;
-    const int m1 = min(la, lb - d);
-    FF re0, im0, re1, im1;    // two independent chains per lane for ILP
-    for (int ch = 0; ch < C; ++ch) {
-      const cdf* a = base[ka] + ((int64_t)(f * C + ch) * ns + s) * la;
-      const cdf* b = base[kb] + ((int64_t)(f * C + ch) * ns + s) * lb;
-      int m = m0 + lane;
-      for (; m + 32 < m1; m += 64) {
-        const cdf x = a[m], y = b[m + d], u = a[m + 32], v = b[m + 32 + d];
-        // conj(x) y = (xr yr + xi yi) + i (xr yi - xi yr)
-        re0.mac(x.rh, x.rl, y.rh, y.rl);
-        re1.mac(u.rh, u.rl, v.rh, v.rl);
-        im0.mac(x.rh, x.rl, y.ih, y.il);
-        im1.mac(u.rh, u.rl, v.ih, v.il);
-        re0.mac(x.ih, x.il, y.ih, y.il);
-        re1.mac(u.ih, u.il, v.ih, v.il);
-        im0.mac(-x.ih, -x.il, y.rh, y.rl);
-        im1.mac(-u.ih, -u.il, v.rh, v.rl);
+  const int maxlen = max(len[0], len[1]);
+  const int nchunk = (maxlen + kGramChunk - 1) / kGramChunk;
+  const int iters = C * nchunk;
+  const cdf zero = {0.f, 0.f, 0.f, 0.f};
+  auto fetch = [&](int it, cdf* pre) {
+    const int ch = it / nchunk, m0 = (it - ch * nchunk) * kGramChunk - kMaxN;
+#pragma unroll
+    for (int q = 0; q < kGramPre; ++q) {
+      const int e = threadIdx.x + q * kSolveThreads;
+      const int k = e / kGramTile, g = m0 + (e - k * kGramTile);
+      pre[q] = zero;
+      if (e < 2 * kGramTile && g >= 0 && g < len[k])
+        pre[q] = base[k][((int64_t)(f * C + ch) * ns + s) * len[k] + g];
+    }
+  };
+  for (int j0 = 0; j0 < J; j0 += kGramLags * nw) {     // passes over the lags
+    FF re[kGramLags], im[kGramLags];
+    cdf pre[kGramPre];
+    fetch(0, pre);
+    for (int it = 0; it < iters; ++it) {
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < kGramPre; ++q) {
+        const int e = threadIdx.x + q * kSolveThreads;
+        if (e < 2 * kGramTile) tile[e] = pre[q];
       }
-      if (m < m1) {
-        const cdf x = a[m], y = b[m + d];
-        re0.mac(x.rh, x.rl, y.rh, y.rl);
-        re0.mac(x.ih, x.il, y.ih, y.il);
-        im0.mac(x.rh, x.rl, y.ih, y.il);
-        im0.mac(-x.ih, -x.il, y.rh, y.rl);
+      __syncthreads();
+      if (it + 1 < iters) fetch(it + 1, pre);
+#pragma unroll
+      for (int q = 0; q < kGramLags; ++q) {
+        const int j = j0 + warp + q * nw;
+        if (j >= J) break;
+        int ka, kb, d;
+        if (j < t1) { ka = 1; kb = 1; d = j; }
+        else if (j < t1 + t2) { ka = 0; kb = 0; d = j - t1; }
+        else { ka = 1; kb = 0; d = j - t1 - t2 - (t2 - 1); }
+        const cdf* A = tile + ka * kGramTile + kMaxN;
+        const cdf* B = tile + kb * kGramTile + kMaxN + d;
+#pragma unroll 4
+        for (int r = 0; r < kGramChunk / 32; ++r) {
+          const int m = lane + 32 * r;
+          const cdf x = A[m], y = B[m];
+          // conj(x) y = (xr yr + xi yi) + i (xr yi - xi yr)
+          re[q].mac(x.rh, x.rl, y.rh, y.rl);
+          re[q].mac(x.ih, x.il, y.ih, y.il);
+          im[q].mac(x.rh, x.rl, y.ih, y.il);
+          im[q].mac(-x.ih, -x.il, y.rh, y.rl);
+        }
       }
     }
-    FF re = re0, im = im0;
-    re.add(re1.hi, re1.lo);
-    im.add(im1.hi, im1.lo);
-    re = warp_sum_ff(re);
-    im = warp_sum_ff(im);
-    if (lane == 0) rho[j] = mk(re.value(), im.value());
+#pragma unroll
+    for (int q = 0; q < kGramLags; ++q) {
+      const int j = j0 + warp + q * nw;
+      const FF sr = warp_sum_ff(re[q]), si = warp_sum_ff(im[q]);
+      if (j < J && lane == 0) rho[j] = mk(sr.value(), si.value());
+    }
   }
   __syncthreads();
 }
@@ -400,6 +427,7 @@ struct SylvesterApply {
 // the global array of normal matrices.
 __global__ void __launch_bounds__(kSolveThreads) k_sample_gram(SampleArgs a) {
   __shared__ cd rho[4 * kMaxN];
+  __shared__ cdf tile[2 * kGramTile];
   const int f = blockIdx.x, ps = blockIdx.y, s = blockIdx.z;
   if (a.accepted && a.accepted[f]) return;   // the proposal stands; nothing to solve
   // Real samples (z = 1; z = -1 when M is even) have real Gram matrices.
@@ -407,7 +435,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_sample_gram(SampleArgs a) {
   const SamplePolys<double, double> P64 =
       sample_polys<double, double>(a.pz[ps], a.len[ps], f, a.C, a.ns, s);
   if (real) correlations_real(P64, a.C, a.t1, a.t2, rho);
-  else if (a.mixed) correlations_ff(a.pzf[ps], a.len[ps], f, a.C, a.ns, s, a.t1, a.t2, rho);
+  else if (a.mixed) correlations_ff(a.pzf[ps], a.len[ps], f, a.C, a.ns, s, a.t1, a.t2, rho, tile);
   else correlations(P64, a.C, a.t1, a.t2, rho);
   const int64_t o = ((int64_t)f * 2 + ps) * a.ns + s;
   gram_from_rho(rho, a.t1, a.t2, a.G + o * a.nn * a.nn);
