@@ -216,6 +216,60 @@ __device__ cpx<T>* fft_block(cpx<T>* a, cpx<T>* b, const FftPlan& pl, int nb, co
 
 // Stage twiddles of a plan: entry st.tw + (r-1) Ns + k = exp(-2 pi i k r / (Ns R)),
 // r-major so that the threads of a stage (consecutive k) read consecutive entries.
+// One Stockham stage with the plan fixed at compile time (radix R, stride NS,
+// length N, twiddle offset TWO): strides and divisors are immediates.
+template <typename T, bool Inv, int R, int NS, int N, int TWO>
+__device__ __forceinline__ void stockham_stage_fixed(const cpx<T>* __restrict__ in,
+                                                     cpx<T>* __restrict__ out, int nb,
+                                                     const cpx<T>* tw) {
+  constexpr int NR = N / R;
+  for (int idx = threadIdx.x; idx < nb * NR; idx += blockDim.x) {
+    const int b = idx / NR, j = idx - b * NR;
+    const int q = j / NS, k = j - q * NS;
+    const cpx<T>* src = in + b * N + j;
+    cpx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[r * NR];
+    if (NS > 1) {
+      const cpx<T>* w = tw + TWO + k;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        cpx<T> ww = w[(r - 1) * NS];
+        if (Inv) ww.im = -ww.im;
+        v[r] = v[r] * ww;
+      }
+    }
+    small_dft<T, Inv, R>(v);
+    cpx<T>* dst = out + b * N + q * NS * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[r * NS] = v[r];
+  }
+}
+
+// Stages 1-3 of the fixed four-stage plan R0..R3 of N (stage 0 is fused into
+// the callers' first stage); returns the buffer with the result.
+template <typename T, bool Inv, int N, int R0, int R1, int R2, int R3>
+__device__ __forceinline__ cpx<T>* fft_rest_fixed(cpx<T>* a, cpx<T>* b, int nb, const cpx<T>* tw) {
+  constexpr int N1 = R0, N2 = R0 * R1, N3 = R0 * R1 * R2;
+  constexpr int O1 = (R0 - 1), O2 = O1 + N1 * (R1 - 1), O3 = O2 + N2 * (R2 - 1);
+  stockham_stage_fixed<T, Inv, R1, N1, N, O1>(a, b, nb, tw);
+  __syncthreads();
+  stockham_stage_fixed<T, Inv, R2, N2, N, O2>(b, a, nb, tw);
+  __syncthreads();
+  stockham_stage_fixed<T, Inv, R3, N3, N, O3>(a, b, nb, tw);
+  __syncthreads();
+  return b;
+}
+
+template <int N, int R0, int R1, int R2, int R3>
+__host__ __device__ inline bool plan_is(const FftPlan& pl) {
+  return pl.n == N && pl.nst == 4 && pl.st[0].R == R0 && pl.st[1].R == R1 && pl.st[2].R == R2 &&
+         pl.st[3].R == R3;
+}
+
+// The row transforms' plan of the 1080p grid: half-length 972 = 9 9 4 3.
+#define CBP_ROW_PLAN 972, 9, 9, 4, 3
+
 template <typename T>
 __global__ void k_stage_twiddles(FftPlan pl, cpx<T>* out) {
   for (int s = 0; s < pl.nst; ++s) {
@@ -486,12 +540,14 @@ template <typename In> struct Edge {
 // staged float/double rows directly: element m of row i is (x[2m], x[2m+1])
 // for the half-length transform (Pw even), else (x[m], 0), zero past W.
 // Pairs are read as one 8-byte load when the row's phase keeps them aligned.
-template <typename T, int R, typename In>
+// NC > 0: the transform length fixed at compile time (strides and divisors
+// become immediates).
+template <typename T, int R, typename In, int NC = 0>
 __device__ __forceinline__ void stage_first_raw(const In* raw, const int* ph, int rw, int W, bool half,
-                                                cpx<T>* out, const FftStage& st, int N, int nb) {
-  const int Nr = st.Nr;
+                                                cpx<T>* out, const FftStage& st, int N_, int nb) {
+  const int Nr = NC ? NC / R : st.Nr, N = NC ? NC : N_;
   for (int idx = threadIdx.x; idx < nb * Nr; idx += blockDim.x) {
-    const int b = st.mNr ? (int)__umulhi((unsigned)idx, st.mNr) : idx;   // idx / Nr
+    const int b = NC ? idx / (NC / R) : st.mNr ? (int)__umulhi((unsigned)idx, st.mNr) : idx;
     const int j = idx - b * Nr;
     const In* row = raw + b * rw + ph[b];
     const bool pair8 = half && sizeof(In) == 4 && (ph[b] & 1) == 0;
@@ -699,7 +755,12 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
     }
     RP_MARK(2);
     // first FFT stage straight from the staging rows into b0
-    if (fft) first_stage_raw<T, In>(rw0, ph, a.rw, W, a.half, b0, a.pl, nr);
+    if (fft) {
+      if (plan_is<CBP_ROW_PLAN>(a.pl))
+        stage_first_raw<T, 9, In, 972>(rw0, ph, a.rw, W, a.half, b0, a.pl.st[0], 972, nr);
+      else
+        first_stage_raw<T, In>(rw0, ph, a.rw, W, a.half, b0, a.pl, nr);
+    }
     __syncthreads();
     RP_MARK(3);
     if (FOLD) {
@@ -715,7 +776,8 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
       // the staging rows of this group are consumed: they serve as the
       // FFT's second buffer when large enough
       cpx<T>* b1 = L.b1_alias ? (cpx<T>*)rw0 : (cpx<T>*)(smem + L.b1);
-      cpx<T>* Z = fft_block<T, false>(b0, b1, a.pl, nr, tw, 1);
+      cpx<T>* Z = plan_is<CBP_ROW_PLAN>(a.pl) ? fft_rest_fixed<T, false, CBP_ROW_PLAN>(b0, b1, nr, tw)
+                                              : fft_block<T, false>(b0, b1, a.pl, nr, tw, 1);
       RP_MARK(4);
       for (int i = 0; i < nr; ++i) {
         const cpx<T>* z = Z + i * N;
@@ -834,6 +896,63 @@ __device__ cpx<T>* fft_block_il(cpx<T>* a, cpx<T>* b, const FftPlan& pl, const c
   return a;
 }
 
+// The same transform with the plan fixed at compile time (four stages,
+// radices R0..R3 of N): every stride, twiddle offset and divisor becomes an
+// immediate, so the stage's loads and stores index from one base register.
+// Plans of other sizes take fft_block_il.
+template <typename T, bool Inv, int R, int NS, int N, int NB, int TWO, int NT>
+__device__ __forceinline__ void stockham_stage_il_fixed(const cpx<T>* __restrict__ in,
+                                                        cpx<T>* __restrict__ out,
+                                                        const cpx<T>* __restrict__ tw) {
+  constexpr int NR = N / R;
+  for (int idx = threadIdx.x; idx < NB * NR; idx += NT) {
+    const int b = idx % NB, j = idx / NB;
+    const int q = j / NS, k = j - q * NS;
+    const cpx<T>* src = in + j * NB + b;
+    cpx<T> v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = src[r * NR * NB];
+    if (NS > 1) {
+      const cpx<T>* w = tw + TWO + k;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        cpx<T> ww = ldg_cpx(w + (r - 1) * NS);
+        if (Inv) ww.im = -ww.im;
+        v[r] = v[r] * ww;
+      }
+    }
+    small_dft<T, Inv, R>(v);
+    cpx<T>* dst = out + (q * NS * R + k) * NB + b;
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[r * NS * NB] = v[r];
+  }
+}
+
+template <typename T, bool Inv, int NB, int NT, int N, int R0, int R1, int R2, int R3>
+__device__ __forceinline__ cpx<T>* fft_il_fixed(cpx<T>* a, cpx<T>* b, const cpx<T>* tw) {
+  constexpr int N1 = R0, N2 = R0 * R1, N3 = R0 * R1 * R2;
+  constexpr int O1 = (R0 - 1), O2 = O1 + N1 * (R1 - 1), O3 = O2 + N2 * (R2 - 1);
+  stockham_stage_il_fixed<T, Inv, R0, 1, N, NB, 0, NT>(a, b, tw);
+  __syncthreads();
+  stockham_stage_il_fixed<T, Inv, R1, N1, N, NB, O1, NT>(b, a, tw);
+  __syncthreads();
+  stockham_stage_il_fixed<T, Inv, R2, N2, N, NB, O2, NT>(a, b, tw);
+  __syncthreads();
+  stockham_stage_il_fixed<T, Inv, R3, N3, N, NB, O3, NT>(b, a, tw);
+  __syncthreads();
+  return a;
+}
+
+// Column transforms of the column pass: the fixed plan of the 1080p grid
+// (Ph = 1120 = 7 8 5 4) or the general one.
+template <typename T, bool Inv, int NB>
+__device__ __forceinline__ cpx<T>* fft_il(cpx<T>* a, cpx<T>* b, const FftPlan& pl,
+                                          const cpx<T>* tw) {
+  if (plan_is<1120, 7, 8, 5, 4>(pl))
+    return fft_il_fixed<T, Inv, NB, kColThreads, 1120, 7, 8, 5, 4>(a, b, tw);
+  return fft_block_il<T, Inv, NB>(a, b, pl, tw);
+}
+
 // Asynchronous copy of a CW-column strip of one spectrum (rows < Hk; rows
 // Hk..Ph-1 and columns >= Pw2 zero-filled) into an interleaved buffer.
 template <typename T, int CW>
@@ -879,14 +998,14 @@ k_col_deconv(ColArgs a) {
   if (a.single) cp_async_wait<0>();
   else cp_async_wait<1>();
   __syncthreads();
-  cpx<T>* r1 = fft_block_il<T, false, CW>(buf0, buf1, a.pl, tw);
+  cpx<T>* r1 = fft_il<T, false, CW>(buf0, buf1, a.pl, tw);
   cpx<T>* free1 = r1 == buf0 ? buf1 : buf0;
   cpx<T>* r2 = nullptr;
   cpx<T>* free2 = nullptr;
   if (!a.single) {
     cp_async_wait<0>();
     __syncthreads();
-    r2 = fft_block_il<T, false, CW>(buf2, free1, a.pl, tw);
+    r2 = fft_il<T, false, CW>(buf2, free1, a.pl, tw);
     free2 = r2 == buf2 ? free1 : buf2;
   }
   const cpx<T>* K1 = (const cpx<T>*)a.khat + ((int64_t)f * 2 + 0) * Ph * a.Pw2p + v0;
@@ -939,7 +1058,7 @@ k_col_deconv(ColArgs a) {
     }
   }
   __syncthreads();
-  cpx<T>* res = fft_block_il<T, true, CW>(r1, a.single ? free1 : free2, a.pl, tw);
+  cpx<T>* res = fft_il<T, true, CW>(r1, a.single ? free1 : free2, a.pl, tw);
   cpx<T>* dst = (cpx<T>*)a.ihat + (int64_t)fc * a.H * a.Pw2p + v0;
   for (int idx = threadIdx.x; idx < CW * a.H; idx += blockDim.x) {
     const int u = idx / CW, vl = idx % CW;
@@ -1002,13 +1121,13 @@ __device__ __forceinline__ void stage_spec_rows_bulk(cpx<T>* dst, const RowPtr& 
 // directly: element m of the half-length transform is E + i O, E and O the
 // even and odd parts of X[m] and conj(X[N - m]) (O with the twiddle
 // exp(+2 pi i m / Pw)); for odd Pw, element m is the Hermitian extension of X.
-template <typename T, int R>
+template <typename T, int R, int NC = 0>
 __device__ __forceinline__ void stage_first_spec(const cpx<T>* raw, int Pw2p, const cpx<T>* tw_w,
                                                  bool half, int Pw2, cpx<T>* out,
-                                                 const FftStage& st, int N, int nb) {
-  const int Nr = st.Nr;
+                                                 const FftStage& st, int N_, int nb) {
+  const int Nr = NC ? NC / R : st.Nr, N = NC ? NC : N_;
   for (int idx = threadIdx.x; idx < nb * Nr; idx += blockDim.x) {
-    const int b = st.mNr ? (int)__umulhi((unsigned)idx, st.mNr) : idx;   // idx / Nr
+    const int b = NC ? idx / (NC / R) : st.mNr ? (int)__umulhi((unsigned)idx, st.mNr) : idx;
     const int j = idx - b * Nr;
     const cpx<T>* Xr = raw + b * Pw2p;
     cpx<T> v[R];
@@ -1106,9 +1225,14 @@ k_row_ifft(IRowArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
     }
     cpx<T>* const rw0 = (g & 1) ? raw1 : raw0;
     // first inverse stage straight from the staged spectrum rows into b0
-    first_stage_spec<T>(rw0, a.Pw2p, tw_w, a.half, a.Pw2, b0, a.pl, nr);
+    if (plan_is<CBP_ROW_PLAN>(a.pl))
+      stage_first_spec<T, 9, 972>(rw0, a.Pw2p, tw_w, a.half, a.Pw2, b0, a.pl.st[0], 972, nr);
+    else
+      first_stage_spec<T>(rw0, a.Pw2p, tw_w, a.half, a.Pw2, b0, a.pl, nr);
     __syncthreads();
-    cpx<T>* Z = fft_block<T, true>(b0, L.b1_alias ? rw0 : (cpx<T>*)(smem + L.b1), a.pl, nr, tw, 1);
+    cpx<T>* b1 = L.b1_alias ? rw0 : (cpx<T>*)(smem + L.b1);
+    cpx<T>* Z = plan_is<CBP_ROW_PLAN>(a.pl) ? fft_rest_fixed<T, true, CBP_ROW_PLAN>(b0, b1, nr, tw)
+                                            : fft_block<T, true>(b0, b1, a.pl, nr, tw, 1);
     for (int i = 0; i < nr; ++i) {
       const cpx<T>* z = Z + i * N;
       const int64_t ob = obase + (int64_t)row_of(g, i) * a.W;
