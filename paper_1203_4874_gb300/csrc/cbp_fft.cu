@@ -779,18 +779,20 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
       cpx<T>* Z = plan_is<CBP_ROW_PLAN>(a.pl) ? fft_rest_fixed<T, false, CBP_ROW_PLAN>(b0, b1, nr, tw)
                                               : fft_block<T, false>(b0, b1, a.pl, nr, tw, 1);
       RP_MARK(4);
-      for (int i = 0; i < nr; ++i) {
-        const cpx<T>* z = Z + i * N;
-        cpx<T>* out = spec + (int64_t)row_of(g, i) * a.Pw2p;
-        for (int k = threadIdx.x; k < a.Pw2; k += blockDim.x) {
-          if (a.half) {
-            const cpx<T> zk = z[k < N ? k : 0], zc = conj(z[k > 0 ? N - k : 0]);
+      // a thread keeps its output columns k (and their twiddle) over the rows
+      for (int k = threadIdx.x; k < a.Pw2; k += blockDim.x) {
+        if (a.half) {
+          const int ka = k < N ? k : 0, kb = k > 0 ? N - k : 0;
+          const cpx<T> w = tw_w[k];                 // X = e - i w d, w = exp(-2 pi i k / Pw)
+          for (int i = 0; i < nr; ++i) {
+            const cpx<T>* z = Z + i * N;
+            const cpx<T> zk = z[ka], zc = conj(z[kb]);
             const cpx<T> e = (T)0.5 * (zk + zc), d = (T)0.5 * (zk - zc);
-            const cpx<T> wd = tw_w[k] * d;          // X = e - i w d, w = exp(-2 pi i k / Pw)
-            out[k] = mk<T>(e.re + wd.im, e.im - wd.re);
-          } else {
-            out[k] = z[k];
+            const cpx<T> wd = w * d;
+            spec[(int64_t)row_of(g, i) * a.Pw2p + k] = mk<T>(e.re + wd.im, e.im - wd.re);
           }
+        } else {
+          for (int i = 0; i < nr; ++i) spec[(int64_t)row_of(g, i) * a.Pw2p + k] = Z[i * N + k];
         }
       }
     }
@@ -953,6 +955,10 @@ __device__ __forceinline__ cpx<T>* fft_il(cpx<T>* a, cpx<T>* b, const FftPlan& p
   return fft_block_il<T, Inv, NB>(a, b, pl, tw);
 }
 
+// 1 / x: the correctly rounded single-precision reciprocal, or a double division.
+__device__ __forceinline__ float recip(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip(double x) { return 1.0 / x; }
+
 // Asynchronous copy of a CW-column strip of one spectrum (rows < Hk; rows
 // Hk..Ph-1 and columns >= Pw2 zero-filled) into an interleaved buffer.
 template <typename T, int CW>
@@ -960,11 +966,15 @@ __device__ __forceinline__ void load_strip_async(cpx<T>* dst, const cpx<T>* src,
                                                  int Pw2p, int ncols) {
   constexpr int E16 = 16 / (int)sizeof(cpx<T>);     // elements per 16-byte chunk
   constexpr int CH = CW / E16;                      // chunks per row
-  for (int idx = threadIdx.x; idx < Ph * CH; idx += blockDim.x) {
-    const int u = idx / CH, c = idx % CH;
-    const int valid = u < Hk ? min(E16, max(0, ncols - c * E16)) : 0;
-    const cpx<T>* g = valid ? src + (int64_t)u * Pw2p + c * E16 : src;
-    cp_async16(dst + u * CW + c * E16, g, valid * (int)sizeof(cpx<T>));
+  static_assert(kColThreads % CH == 0, "column pass: threads per strip row");
+  constexpr int kStep = kColThreads / CH;           // a thread keeps its chunk column
+  const int c = threadIdx.x % CH;
+  const int vbytes = min(E16, max(0, ncols - c * E16)) * (int)sizeof(cpx<T>);
+  const cpx<T>* g = src + (int64_t)(threadIdx.x / CH) * Pw2p + c * E16;
+  const int64_t gstep = (int64_t)kStep * Pw2p;
+  for (int u = threadIdx.x / CH; u < Ph; u += kStep, g += gstep) {
+    const int valid = u < Hk ? vbytes : 0;
+    cp_async16(dst + u * CW + c * E16, valid ? g : src, valid);
   }
   cp_async_commit();
 }
@@ -1042,27 +1052,34 @@ k_col_deconv(ColArgs a) {
     return;
   }
   const T eps = (T)a.eps;
-  for (int idx = threadIdx.x; idx < CW * Ph; idx += blockDim.x) {
-    const int u = idx / CW, vl = idx % CW;
-    if (vl < nv) {
-      const cpx<T> k1 = ldg_cpx(K1 + (int64_t)u * a.Pw2p + vl);
-      const cpx<T> k2 = a.single ? mk<T>(0, 0) : ldg_cpx(K2 + (int64_t)u * a.Pw2p + vl);
+  // a thread keeps one column (kColThreads is a multiple of CW) and steps
+  // down the rows
+  static_assert(kColThreads % CW == 0, "column pass: threads per row group");
+  constexpr int kRowStep = kColThreads / CW;
+  const int vl = threadIdx.x % CW;
+  if (vl < nv) {
+    const int64_t kstep = (int64_t)kRowStep * a.Pw2p;
+    const cpx<T>* k1p = K1 + (int64_t)(threadIdx.x / CW) * a.Pw2p + vl;
+    const cpx<T>* k2p = K2 + (int64_t)(threadIdx.x / CW) * a.Pw2p + vl;
+    for (int idx = threadIdx.x; idx < CW * Ph; idx += kColThreads, k1p += kstep, k2p += kstep) {
+      const cpx<T> k1 = ldg_cpx(k1p);
+      const cpx<T> k2 = a.single ? mk<T>(0, 0) : ldg_cpx(k2p);
       cpx<T> num = cmulc(k1, r1[idx]);
       T den = abs2(k1) + eps;
       if (!a.single) {
         num = num + cmulc(k2, r2[idx]);
         den += abs2(k2);
       }
-      const T inv = den != (T)0 ? (T)1 / den : (T)0;
-      r1[idx] = inv * num;
+      r1[idx] = (den != (T)0 ? recip(den) : (T)0) * num;
     }
   }
   __syncthreads();
   cpx<T>* res = fft_il<T, true, CW>(r1, a.single ? free1 : free2, a.pl, tw);
-  cpx<T>* dst = (cpx<T>*)a.ihat + (int64_t)fc * a.H * a.Pw2p + v0;
-  for (int idx = threadIdx.x; idx < CW * a.H; idx += blockDim.x) {
-    const int u = idx / CW, vl = idx % CW;
-    if (vl < nv) dst[(int64_t)u * a.Pw2p + vl] = res[idx];
+  if (vl < nv) {
+    cpx<T>* dst = (cpx<T>*)a.ihat + (int64_t)fc * a.H * a.Pw2p + v0 +
+                  (int64_t)(threadIdx.x / CW) * a.Pw2p + vl;
+    const int64_t dstep = (int64_t)kRowStep * a.Pw2p;
+    for (int idx = threadIdx.x; idx < CW * a.H; idx += kColThreads, dst += dstep) *dst = res[idx];
   }
 }
 
