@@ -711,45 +711,63 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
     In* const rw0 = (g & 1) ? raw1 : raw0;
     const int* ph = rph + (g & 1) * NB;
     if (FOLD) {
-      const In* rowp[kMaxRowGroup];
-#pragma unroll
-      for (int i = 0; i < kMaxRowGroup; ++i) rowp[i] = rw0 + i * a.rw + (i < nr ? ph[i] : 0);
-      // column folds: this block's bin, one thread per column
+      // element c of staged row i is rw0[roff(i) + c]
+      auto roff = [&](int i) { return i * a.rw + ph[i]; };
+      // column folds: this block's bin, one thread per column (full groups
+      // without per-row tests)
       if (!L.col_smem) {
+        if (nr == kMaxRowGroup) {
+          int off[kMaxRowGroup];
 #pragma unroll
-        for (int j = 0; j < kColRegs; ++j) {
-          const int c = threadIdx.x + j * kRowPassThreads;
-          if (c < W) {
+          for (int i = 0; i < kMaxRowGroup; ++i) off[i] = roff(i);
 #pragma unroll
-            for (int i = 0; i < kMaxRowGroup; ++i)
-              if (i < nr) creg[j].add(rowp[i][c]);
+          for (int j = 0; j < kColRegs; ++j) {
+            const int c = threadIdx.x + j * kRowPassThreads;
+            if (c < W) {
+#pragma unroll
+              for (int i = 0; i < kMaxRowGroup; ++i) creg[j].add(rw0[off[i] + c]);
+            }
+          }
+        } else {
+          for (int i = 0; i < nr; ++i) {
+            const In* rp = rw0 + roff(i);
+#pragma unroll
+            for (int j = 0; j < kColRegs; ++j) {
+              const int c = threadIdx.x + j * kRowPassThreads;
+              if (c < W) creg[j].add(rp[c]);
+            }
           }
         }
       } else {
         for (int c = threadIdx.x; c < W; c += blockDim.x) {
           Acc acc = colacc[c];
-#pragma unroll
-          for (int i = 0; i < kMaxRowGroup; ++i)
-            if (i < nr) acc.add(rowp[i][c]);
+          for (int i = 0; i < nr; ++i) acc.add(rw0[roff(i) + c]);
           colacc[c] = acc;
         }
       }
       // row folds: task (i, sg, m) sums columns c = m mod M of row i over
-      // segment sg; nseg segments per (row, bin) fill the block
+      // segment sg; nseg segments per (row, bin) fill the block.  Only the
+      // last step of a row can pass W; two accumulators for latency.
       const int nseg = max(1, kRowPassThreads / (nr * M));
       const int nsteps = (W + M - 1) / M, sps = (nsteps + nseg - 1) / nseg;
       const int t = threadIdx.x;
       if (t < nr * M * nseg) {
         const int i = t / (M * nseg), r = t - i * (M * nseg), sg = r / M, m = r - sg * M;
-        Acc acc;
-        const In* rp = rowp[0];
-#pragma unroll
-        for (int ii = 1; ii < kMaxRowGroup; ++ii)
-          if (ii == i) rp = rowp[ii];
-        const int e = min(nsteps, (sg + 1) * sps);
-        int c = sg * sps * M + m;
-        for (int st = sg * sps; st < e; ++st, c += M)
-          if (c < W) acc.add(rp[c]);
+        Acc acc, acc2;
+        const In* rp = rw0 + roff(i);
+        const int st0 = sg * sps, e = min(nsteps, st0 + sps), ef = min(e, nsteps - 1);
+        int st = st0, c = st0 * M + m;
+        for (; st + 1 < ef; st += 2, c += 2 * M) {
+          acc.add(rp[c]);
+          acc2.add(rp[c + M]);
+        }
+        if (st < ef) {
+          acc.add(rp[c]);
+          ++st;
+          c += M;
+        }
+        if (st < e && c < W) acc.add(rp[c]);
+        acc.merge(acc2);
         rb[t] = acc;
       }
     }
