@@ -948,18 +948,66 @@ __device__ __forceinline__ void stockham_stage_il_fixed(const cpx<T>* __restrict
   }
 }
 
+// The same stage for single precision and four interleaved transforms with a
+// thread on two neighbouring transforms: one 16-byte shared access per element
+// pair, and the index work and twiddles of a butterfly serve both.
+template <bool Inv, int R, int NS, int N, int TWO, int NT>
+__device__ __forceinline__ void stockham_stage_il_fixed_x2(const cf* __restrict__ in,
+                                                           cf* __restrict__ out,
+                                                           const cf* __restrict__ tw) {
+  constexpr int NR = N / R;
+  for (int idx = threadIdx.x; idx < 2 * NR; idx += NT) {
+    const int h = idx & 1, j = idx >> 1;
+    const int q = j / NS, k = j - q * NS;
+    const float4* src = reinterpret_cast<const float4*>(in + j * 4 + 2 * h);
+    cf v0[R], v1[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const float4 x = src[r * NR * 2];
+      v0[r] = mk(x.x, x.y);
+      v1[r] = mk(x.z, x.w);
+    }
+    if (NS > 1) {
+      const cf* w = tw + TWO + k;
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        cf ww = ldg_cpx(w + (r - 1) * NS);
+        if (Inv) ww.im = -ww.im;
+        v0[r] = v0[r] * ww;
+        v1[r] = v1[r] * ww;
+      }
+    }
+    small_dft<float, Inv, R>(v0);
+    small_dft<float, Inv, R>(v1);
+    float4* dst = reinterpret_cast<float4*>(out + (q * NS * R + k) * 4 + 2 * h);
+#pragma unroll
+    for (int r = 0; r < R; ++r) dst[r * NS * 2] = make_float4(v0[r].re, v0[r].im, v1[r].re, v1[r].im);
+  }
+}
+
 template <typename T, bool Inv, int NB, int NT, int N, int R0, int R1, int R2, int R3>
 __device__ __forceinline__ cpx<T>* fft_il_fixed(cpx<T>* a, cpx<T>* b, const cpx<T>* tw) {
   constexpr int N1 = R0, N2 = R0 * R1, N3 = R0 * R1 * R2;
   constexpr int O1 = (R0 - 1), O2 = O1 + N1 * (R1 - 1), O3 = O2 + N2 * (R2 - 1);
-  stockham_stage_il_fixed<T, Inv, R0, 1, N, NB, 0, NT>(a, b, tw);
-  __syncthreads();
-  stockham_stage_il_fixed<T, Inv, R1, N1, N, NB, O1, NT>(b, a, tw);
-  __syncthreads();
-  stockham_stage_il_fixed<T, Inv, R2, N2, N, NB, O2, NT>(a, b, tw);
-  __syncthreads();
-  stockham_stage_il_fixed<T, Inv, R3, N3, N, NB, O3, NT>(b, a, tw);
-  __syncthreads();
+  if constexpr (sizeof(T) == 4 && NB == 4) {
+    stockham_stage_il_fixed_x2<Inv, R0, 1, N, 0, NT>(a, b, tw);
+    __syncthreads();
+    stockham_stage_il_fixed_x2<Inv, R1, N1, N, O1, NT>(b, a, tw);
+    __syncthreads();
+    stockham_stage_il_fixed_x2<Inv, R2, N2, N, O2, NT>(a, b, tw);
+    __syncthreads();
+    stockham_stage_il_fixed_x2<Inv, R3, N3, N, O3, NT>(b, a, tw);
+    __syncthreads();
+  } else {
+    stockham_stage_il_fixed<T, Inv, R0, 1, N, NB, 0, NT>(a, b, tw);
+    __syncthreads();
+    stockham_stage_il_fixed<T, Inv, R1, N1, N, NB, O1, NT>(b, a, tw);
+    __syncthreads();
+    stockham_stage_il_fixed<T, Inv, R2, N2, N, NB, O2, NT>(a, b, tw);
+    __syncthreads();
+    stockham_stage_il_fixed<T, Inv, R3, N3, N, NB, O3, NT>(b, a, tw);
+    __syncthreads();
+  }
   return a;
 }
 
