@@ -304,8 +304,8 @@ __global__ void k_twiddles(cpx<T>* tw, int n) {
 // A block takes 64 columns of one kernel: first the t row transforms R_p(v),
 // then every u with each lane on two columns (v, v + 32: coalesced 256-byte
 // row segments per warp store), kSpecRows rows at a time so that each R_p(v)
-// read serves kSpecRows outputs and each row twiddle w_H^(u p) (shared
-// memory, read as a broadcast) serves two.
+// read serves kSpecRows outputs; the sum over p by Horner's rule in
+// z = w_H^u (one complex multiply-add per term, no twiddle indexing).
 constexpr int kSpecCols = 64;
 constexpr int kSpecRows = 8;
 
@@ -338,24 +338,22 @@ k_kernel_spectra(const double* kd, int t1, int t2, int Ph, int Pw, int Pw2, int 
   cpx<T>* out = khat + ((int64_t)f * 2 + k) * Ph * Pw2p;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const int va = v0 + lane, vb = v0 + 32 + lane;
+  // Horner's rule in z = w_H^u: K^(u, v) = (...(R_{t-1}(v) z + R_{t-2}(v)) z + ...) + R_0(v)
   for (int u0 = warp * kSpecRows; u0 < Ph; u0 += nw * kSpecRows) {
-    cpx<T> acc[kSpecRows][2];
-    int e[kSpecRows], du[kSpecRows];          // (u p) mod Ph per row, incrementally
+    cpx<T> acc[kSpecRows][2], z[kSpecRows];
+    const cpx<T> ra = kv[(t - 1) * kSpecCols + lane], rb = kv[(t - 1) * kSpecCols + 32 + lane];
 #pragma unroll
     for (int j = 0; j < kSpecRows; ++j) {
-      acc[j][0] = acc[j][1] = mk<T>(0, 0);
-      e[j] = 0;
-      du[j] = u0 + j < Ph ? u0 + j : 0;       // rows past Ph are computed as u = 0, not stored
+      z[j] = twh[u0 + j < Ph ? u0 + j : 0];   // rows past Ph are computed as u = 0, not stored
+      acc[j][0] = ra;
+      acc[j][1] = rb;
     }
-    for (int p = 0; p < t; ++p) {
-      const cpx<T> ra = kv[p * kSpecCols + lane], rb = kv[p * kSpecCols + 32 + lane];
+    for (int p = t - 2; p >= 0; --p) {
+      const cpx<T> ca = kv[p * kSpecCols + lane], cb = kv[p * kSpecCols + 32 + lane];
 #pragma unroll
       for (int j = 0; j < kSpecRows; ++j) {
-        const cpx<T> w = twh[e[j]];
-        cfma(acc[j][0], ra, w);
-        cfma(acc[j][1], rb, w);
-        e[j] += du[j];
-        if (e[j] >= Ph) e[j] -= Ph;
+        acc[j][0] = acc[j][0] * z[j] + ca;
+        acc[j][1] = acc[j][1] * z[j] + cb;
       }
     }
 #pragma unroll
