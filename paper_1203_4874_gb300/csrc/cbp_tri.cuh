@@ -66,6 +66,7 @@ struct TriWs {
   float* df;      // [n] d in single precision
   float* e2f;     // [n] e^2 in single precision
   int* iv;        // [4] values broadcast to the CTA
+  void* part;     // [8][n] complex: per-warp partial sums of the CTA's reduction
   cd* x;          // [n] the eigenvector of G
   cd* r;          // [n] residual
   cd* z;          // [n] scratch (T coordinates)
@@ -76,7 +77,7 @@ struct TriWs {
 // (placed back to back) and each of its 16-byte-aligned parts stay aligned.
 __host__ __device__ inline size_t tri_ws_bytes(int n) {
   const size_t b = (size_t)16 * ((size_t)n * n + 3 * n) + (size_t)8 * 7 * n + (size_t)4 * 3 * n +
-                   16 + (size_t)16 * 4 * n + 16 * 18;   // + alignment of the 18 parts
+                   16 + (size_t)16 * 4 * n + (size_t)16 * 8 * n + 16 * 19;   // + alignment of the 19 parts
   return (b + 127) & ~size_t(127);
 }
 
@@ -105,6 +106,7 @@ __device__ inline TriWs carve_tri(char* p, int n) {
   W.df = (float*)take((size_t)4 * n);
   W.e2f = (float*)take((size_t)4 * n);
   W.iv = (int*)take(16);
+  W.part = take((size_t)16 * 8 * n);
   return W;
 }
 
@@ -206,6 +208,117 @@ __device__ void tri_reduce(E* A, E* tau, E* w, typename RealOf<E>::type* d,
 __device__ __forceinline__ bool dneg(double x) { return __double_as_longlong(x) < 0; }
 __device__ __forceinline__ bool dzero(double x) { return (__double_as_longlong(x) << 1) == 0; }
 __device__ __forceinline__ int dexp(double x) { return (__double2hiint(x) >> 20) & 0x7ff; }
+
+// The same reduction by all warps of the CTA (real samples, whose solve has a
+// CTA to itself): the lead warp forms each reflector; the matrix-vector
+// product and the rank-2 update are split by rows j = w (mod warps), the
+// product's per-warp partial sums meeting in part[w][i].
+template <typename E>
+__device__ void tri_reduce_block(E* A, E* tau, E* w, typename RealOf<E>::type* d,
+                                 typename RealOf<E>::type* e, int n, E* part /* [8][n] */) {
+  using R = typename RealOf<E>::type;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int nw = min(8, (int)(blockDim.x >> 5));   // warps taking part
+  if (warp >= nw) {                                 // the others only keep the barriers
+    for (int k = 0; k + 1 < n; ++k) {
+      __syncthreads();
+      if (!Ops<E>::nz(tau[k])) continue;
+      __syncthreads();
+      __syncthreads();
+      __syncthreads();
+    }
+    __syncthreads();
+    return;
+  }
+  for (int k = 0; k + 1 < n; ++k) {
+    const int k1 = k + 1;
+    E* vk = A + (size_t)k * n;
+    if (warp == 0) {
+      const E alpha = cj_(vk[k1]);
+      R xn2 = R(0);
+      for (int i = lane; i < n; i += 32)
+        if (i > k1) xn2 += a2_(vk[i]);
+      xn2 = warp_sum(xn2);
+      const R ar = re_(alpha), ai = im_(alpha);
+      E tk = Ops<E>::z();
+      R beta = ar;
+      if (xn2 > R(0) || ai != R(0)) {
+        beta = -copysign(sqrt(ar * ar + ai * ai + xn2), ar);
+        const R ib = R(1) / beta;
+        tk = mk_e<E, R>((beta - ar) * ib, -ai * ib);
+        const R dr = ar - beta, dn = R(1) / (dr * dr + ai * ai);
+        const E scl = mk_e<E, R>(dr * dn, -ai * dn);
+        __syncwarp();
+        for (int i = lane; i < n; i += 32) {
+          if (i > k1) vk[i] = mul_(cj_(vk[i]), scl);
+          else if (i == k1) vk[i] = Ops<E>::o();
+        }
+      } else {
+        __syncwarp();
+        for (int i = lane; i < n; i += 32)
+          if (i == k1) vk[i] = Ops<E>::o();
+      }
+      if (lane == 0) {
+        d[k] = re_(A[(size_t)k * n + k]);
+        e[k] = beta;
+        tau[k] = tk;
+      }
+    }
+    __syncthreads();
+    const E tk = tau[k];
+    if (!Ops<E>::nz(tk)) continue;
+    // partial products over this warp's rows
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int i = lane + 32 * c;
+      if (i > k && i < n) {
+        E acc = Ops<E>::z();
+        for (int j = k1 + warp; j < n; j += nw) fma_(acc, cj_(A[(size_t)j * n + i]), vk[j]);
+        part[warp * n + i] = acc;
+      }
+    }
+    __syncthreads();
+    if (warp == 0) {
+      E y[2];
+      E dotl = Ops<E>::z();
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int i = lane + 32 * c;
+        y[c] = Ops<E>::z();
+        if (i > k && i < n) {
+          E acc = part[i];
+          for (int ww = 1; ww < nw; ++ww) acc = acc + part[ww * n + i];
+          y[c] = mul_(tk, acc);
+          fma_(dotl, cj_(vk[i]), y[c]);
+        }
+      }
+      const E dot = warp_sum_e(dotl);
+      const R hc = R(0.5) * re_(mul_(cj_(tk), dot));
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int i = lane + 32 * c;
+        if (i > k && i < n) w[i] = y[c] - sc_(hc, vk[i]);
+      }
+    }
+    __syncthreads();
+    // rank-2 update of this warp's rows
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int i = lane + 32 * c;
+      if (i > k && i < n) {
+        const E cw = cj_(w[i]), cv = cj_(vk[i]);
+        for (int j = k1 + warp; j < n; j += nw) {
+          E t = mul_(vk[j], cw);
+          fma_(t, w[j], cv);
+          A[(size_t)j * n + i] = A[(size_t)j * n + i] - t;
+        }
+      }
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) d[n - 1] = re_(A[(size_t)(n - 1) * n + n - 1]);
+  __syncthreads();
+}
 
 // Number of eigenvalues of T below sig: sign changes of the leading principal
 // minors p_i = det(T_i - sig I) (p_i = (d_i - sig) p_{i-1} - e_{i-1}^2 p_{i-2};
@@ -414,7 +527,7 @@ template <bool BLOCK> __device__ __forceinline__ void team_sync() {
 template <typename E>
 __device__ int tri_solve_lead(const TriWs& W, const cd* G, int n, int steps_far, int steps_near,
                               double refine_gap, TriResult& res, double& gs, double& tnorm,
-                              long long* tk) {
+                              long long* tk, bool prereduced = false) {
   const int lane = threadIdx.x & 31;
   E* A = (E*)W.A;
   E* tau = (E*)W.tau;
@@ -435,14 +548,16 @@ __device__ int tri_solve_lead(const TriWs& W, const cd* G, int n, int steps_far,
   frexp(gmax, &ex);
   gs = ldexp(1.0, ex);
   const double igs = ldexp(1.0, -ex);
-  for (int idx = lane; idx < n * n; idx += 32) {
-    if constexpr (sizeof(E) == sizeof(double)) A[idx] = mk_e<E>(G[idx].re * igs, 0.0);
-    else A[idx] = mk_e<E>(G[idx].re * igs, G[idx].im * igs);
+  if (!prereduced) {   // else the caller's CTA has reduced G * igs already
+    for (int idx = lane; idx < n * n; idx += 32) {
+      if constexpr (sizeof(E) == sizeof(double)) A[idx] = mk_e<E, double>(G[idx].re * igs, 0.0);
+      else A[idx] = mk_e<E, double>(G[idx].re * igs, G[idx].im * igs);
+    }
+    __syncwarp();
+    if (tk && lane == 0) tk[0] = clock64();
+    tri_reduce<E>(A, tau, (E*)W.w, W.d, W.e, n);
+    if (tk && lane == 0) tk[1] = clock64();
   }
-  __syncwarp();
-  if (tk && lane == 0) tk[0] = clock64();
-  tri_reduce<E>(A, tau, (E*)W.w, W.d, W.e, n);
-  if (tk && lane == 0) tk[1] = clock64();
   // Gershgorin interval of T; single-precision copies
   double glo = 1e300, ghi = -1e300;
   for (int i = lane; i < n; i += 32) {
@@ -547,7 +662,8 @@ __device__ int tri_solve_lead(const TriWs& W, const cd* G, int n, int steps_far,
 // equation solved through the single-precision T (contraction ~n u ||T|| /
 // gap per step), until the correction stops shrinking or falls below 1e-10.
 // For complex matrices whose two smallest eigenvalues single precision
-// separates by more than 1e-4 lambda_max; returns false, having changed
+// separates by more than 3e-5 lambda_max (contraction <~ 0.1 per step, at
+// most 12 steps); returns false, having changed
 // nothing but the work area, for the others (they take tri_solve_lead).
 __device__ bool tri_solve_lead_sp(const TriWs& W, const cd* G, int n, TriResult& res, double& gs,
                                   double& tnorm, long long* tk) {
@@ -601,7 +717,7 @@ __device__ bool tri_solve_lead_sp(const TriWs& W, const cd* G, int n, TriResult&
   const double lam0 = 0.5 * (br[0].lo + br[0].hi), lam1 = 0.5 * (br[1].lo + br[1].hi);
   const double lamn = 0.5 * (br[2].lo + br[2].hi);
   // separated beyond the error bounds?
-  if (!((br[1].lo - eb) - (br[0].hi + eb) > 1e-4 * lamn)) return false;
+  if (!((br[1].lo - eb) - (br[0].hi + eb) > 3e-5 * lamn)) return false;
   if (tk && lane == 0) tk[2] = clock64();
   // inverse iteration in single precision (three steps)
   tri_lu<float>(d, e, u0, u1, u2, lm, W.piv, n, (float)lam0, (float)(1.2e-7 * tnorm));
@@ -659,7 +775,7 @@ __device__ bool tri_solve_lead_sp(const TriWs& W, const cd* G, int n, TriResult&
   cf* yq = yt + n;            // x in single precision
   cf* rq = (cf*)W.r;          // r in single precision, then d~
   double dprev = 1e300;
-  for (int it = 0; it < 8; ++it) {
+  for (int it = 0; it < 12; ++it) {
     cd gx[2];
     cd th = mk(0.0, 0.0);
 #pragma unroll
@@ -730,7 +846,7 @@ __device__ bool tri_solve_lead_sp(const TriWs& W, const cd* G, int n, TriResult&
   res.lam_min = gs * lam0;
   res.lam_2 = gs * lam1;
   res.lam_max = gs * lamn;
-  res.near_degenerate = 0;
+  res.near_degenerate = (lam1 - lam0) <= 1e-4 * lamn ? 1 : 0;
   return true;
 }
 
@@ -793,11 +909,33 @@ __device__ TriResult tri_smallest(const TriWs& W, const cd* G, int n, int steps_
   TriResult res = {};
   double gs = 1.0, tnorm = 0.0;
   int steps = 0;
+  bool pre = false;
+  if (BLOCK && !single) {
+    // the CTA reduces G * 2^-ex together (ex from the largest diagonal entry)
+    double gmax = 0.0;
+    for (int i = lane; i < n; i += 32) gmax = fmax(gmax, G[(size_t)i * n + i].re);
+    gmax = warp_max(gmax);
+    if (gmax > 0.0) {
+      int ex;
+      frexp(gmax, &ex);
+      const double igs = ldexp(1.0, -ex);
+      E* A = (E*)W.A;
+      for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+        if constexpr (sizeof(E) == sizeof(double)) A[idx] = mk_e<E, double>(G[idx].re * igs, 0.0);
+        else A[idx] = mk_e<E, double>(G[idx].re * igs, G[idx].im * igs);
+      }
+      __syncthreads();
+      if (tk && threadIdx.x == 0) tk[0] = clock64();
+      tri_reduce_block<E>(A, (E*)W.tau, (E*)W.w, W.d, W.e, n, (E*)W.part);
+      if (tk && threadIdx.x == 0) tk[1] = clock64();
+      pre = true;
+    }
+  }
   if (lead) {
     if (single && n > 2 && tri_solve_lead_sp(W, G, n, res, gs, tnorm, tk))
       steps = 0;
     else
-      steps = tri_solve_lead<E>(W, G, n, steps_far, steps_near, refine_gap, res, gs, tnorm, tk);
+      steps = tri_solve_lead<E>(W, G, n, steps_far, steps_near, refine_gap, res, gs, tnorm, tk, pre);
     if (BLOCK && lane == 0) W.iv[0] = steps;
   }
   if (BLOCK) {
