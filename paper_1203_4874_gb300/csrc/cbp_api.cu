@@ -69,11 +69,15 @@ cbp_status Ctx::ensure_ws(size_t bytes, cudaStream_t st) {
 
 cbp_status Ctx::ensure_chunk_streams() {
   if (chunk_ready) return CBP_OK;
-  for (int i = 0; i < kMaxChunks; ++i)
+  for (int i = 0; i < kChunkStreams; ++i)
     if (cudaStreamCreateWithFlags(&chunk_st[i], cudaStreamNonBlocking) != cudaSuccess)
       return CBP_ERR_CUDA;
+  if (cudaStreamCreateWithFlags(&io_st, cudaStreamNonBlocking) != cudaSuccess) return CBP_ERR_CUDA;
   for (int i = 0; i <= kMaxChunks; ++i)
     if (cudaEventCreateWithFlags(&chunk_ev[i], cudaEventDisableTiming) != cudaSuccess)
+      return CBP_ERR_CUDA;
+  for (int i = 0; i < kMaxChunks; ++i)
+    if (cudaEventCreateWithFlags(&io_ev[i], cudaEventDisableTiming) != cudaSuccess)
       return CBP_ERR_CUDA;
   chunk_ready = true;
   return CBP_OK;
@@ -102,7 +106,7 @@ cbp_status Ctx::ensure_cnn_ws(size_t bytes, cudaStream_t st) {
 cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
                     const cbp_params* prm, void* k1, void* k2, void* latent, bool deblur,
                     char* wsp, cudaStream_t st, Prof* prof, const PtrTables* tabs,
-                    const float* cnn_w) {
+                    const float* cnn_w, bool h2d_done) {
   cudaEvent_t ev = nullptr;
   auto begin = [&](int stage) {
     if (prof) prof->begin(stage, st, &ev);
@@ -131,8 +135,9 @@ cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
       if (rs != b->w || cs != (int64_t)b->h * b->w || fs != (int64_t)b->c * cs)
         return CBP_ERR_INVALID_ARG;  // host I/O takes contiguous batches
       const size_t bytes = (size_t)b->n * b->c * b->h * b->w * es;
-      if (cudaMemcpyAsync(wsp + p.off_io_b[k], b->data, bytes, cudaMemcpyHostToDevice, st) !=
-          cudaSuccess)
+      if (!h2d_done &&
+          cudaMemcpyAsync(wsp + p.off_io_b[k], b->data, bytes, cudaMemcpyHostToDevice, st) !=
+              cudaSuccess)
         return CBP_ERR_CUDA;
     }
     d1 = frame_desc(b1, wsp + p.off_io_b[0]);
@@ -140,7 +145,7 @@ cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
     k1d = k1 ? wsp + p.off_io_k[0] : nullptr;
     k2d = k2 ? wsp + p.off_io_k[1] : nullptr;
     latd = wsp + p.off_io_lat;
-    if (kin) {
+    if (kin && !h2d_done) {
       if (cudaMemcpyAsync(k1d, k1, (size_t)p.n * p.t1 * p.t1 * kes, cudaMemcpyHostToDevice, st) !=
               cudaSuccess ||
           cudaMemcpyAsync(k2d, k2, (size_t)p.n * p.t2 * p.t2 * kes, cudaMemcpyHostToDevice, st) !=
@@ -285,13 +290,23 @@ cbp_status copy_stages(const Plan& p, const char* ws, const cbp_stage_out* o, cu
   return CBP_OK;
 }
 
-// A batch is split into up to kChunks chunks of at least kMinChunkPairs pairs
+// A batch is split into up to kChunks chunks (kIoChunks with host I/O) of at
+// least kMinChunkPairs pairs
 // (each with its own plan and workspace region) on the context's internal
 // streams: the chunks' kernels fill each other's idle
 // SMs and tails (the scale solve, for one, runs one block per pair).  Pairs
 // are independent, so the results do not depend on the split.
 constexpr int kChunks = 3;
+constexpr int kIoChunks = Ctx::kMaxChunks;
 constexpr int kMinChunkPairs = 8;
+
+// Host I/O takes contiguous batches.
+bool contiguous(const cbp_frames* b) {
+  const int64_t rs = b->row_stride ? b->row_stride : b->w;
+  const int64_t cs = b->chan_stride ? b->chan_stride : (int64_t)b->h * rs;
+  const int64_t fs = b->frame_stride ? b->frame_stride : (int64_t)b->c * cs;
+  return rs == b->w && cs == (int64_t)b->h * b->w && fs == (int64_t)b->c * cs;
+}
 
 // The frames / outputs of pairs [start, start + count) of a batch.
 cbp_frames frames_slice(const cbp_frames* f, int start, int count) {
@@ -323,7 +338,11 @@ cbp_status call_path(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
   DeviceGuard g(c->device);
   cudaStream_t st = (cudaStream_t)stream;
   std::lock_guard<std::mutex> lk(c->api_mu);
-  const int nch = (c->profiling || stages) ? 1 : std::max(1, std::min(kChunks, p.n / kMinChunkPairs));
+  const bool host_io = (prm->flags & CBP_FLAG_HOST_IO) != 0;
+  if (host_io && (!contiguous(b1) || !contiguous(b2))) return CBP_ERR_INVALID_ARG;
+  const int nch = (c->profiling || stages)
+                      ? 1
+                      : std::max(1, std::min(host_io ? kIoChunks : kChunks, p.n / kMinChunkPairs));
   if (nch == 1) {
     s = c->ensure_ws(p.total, st);
     if (s != CBP_OK) return s;
@@ -361,16 +380,40 @@ cbp_status call_path(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
   const bool kf64 = b1->dtype == CBP_F64 || (prm->flags & CBP_FLAG_KERNELS_F64);
   const size_t kes = kf64 ? 8 : 4, les = b1->dtype == CBP_F64 ? 8 : 4;
   const size_t lat_pair = (size_t)p.C * p.H * p.W * les;
+  const bool kin = (prm->flags & CBP_FLAG_KERNELS_IN) != 0;
+  // Host I/O: the chunks' inputs go over on one copy stream in chunk order, so
+  // chunk i computes while the inputs of chunks > i are still in flight and
+  // its results go back while later chunks compute.
+  if (host_io && cudaStreamWaitEvent(c->io_st, c->chunk_ev[c->kMaxChunks], 0) != cudaSuccess)
+    return CBP_ERR_CUDA;
   for (int i = 0; i < nch; ++i) {
-    cudaStream_t cs = c->chunk_st[i];
+    cudaStream_t cs = c->chunk_st[i % Ctx::kChunkStreams];
     if (cudaStreamWaitEvent(cs, c->chunk_ev[c->kMaxChunks], 0) != cudaSuccess) return CBP_ERR_CUDA;
     const size_t a = (size_t)start[i];
     void* ck1 = k1 ? (char*)k1 + a * p.t1 * p.t1 * kes : nullptr;
     void* ck2 = k2 ? (char*)k2 + a * p.t2 * p.t2 * kes : nullptr;
     void* clat = latent ? (char*)latent + a * lat_pair : nullptr;
     char* w = c->ws + off[i];
+    if (host_io) {
+      const cbp_frames* fs[2] = {&f1[i], &f2[i]};
+      for (int k = 0; k < 2; ++k) {
+        const cbp_frames* f = fs[k];
+        const size_t bytes = (size_t)f->n * f->c * f->h * f->w * les;
+        if (cudaMemcpyAsync(w + cp[i].off_io_b[k], f->data, bytes, cudaMemcpyHostToDevice,
+                            c->io_st) != cudaSuccess)
+          return CBP_ERR_CUDA;
+      }
+      if (kin && (cudaMemcpyAsync(w + cp[i].off_io_k[0], ck1, (size_t)cp[i].n * p.t1 * p.t1 * kes,
+                                  cudaMemcpyHostToDevice, c->io_st) != cudaSuccess ||
+                  cudaMemcpyAsync(w + cp[i].off_io_k[1], ck2, (size_t)cp[i].n * p.t2 * p.t2 * kes,
+                                  cudaMemcpyHostToDevice, c->io_st) != cudaSuccess))
+        return CBP_ERR_CUDA;
+      if (cudaEventRecord(c->io_ev[i], c->io_st) != cudaSuccess ||
+          cudaStreamWaitEvent(cs, c->io_ev[i], 0) != cudaSuccess)
+        return CBP_ERR_CUDA;
+    }
     s = cbp::run_plan(cp[i], &f1[i], &f2[i], prm, ck1, ck2, clat, deblur, w, cs, nullptr, nullptr,
-                      c->cnn_w);
+                      c->cnn_w, host_io);
     if (s != CBP_OK) return s;
     if (diag && cudaMemcpyAsync(diag + a, w + cp[i].off_diag, (size_t)cp[i].n * sizeof(cbp_diag),
                                 cudaMemcpyDeviceToHost, cs) != cudaSuccess)
@@ -412,10 +455,13 @@ cbp_status cbp_destroy(cbp_ctx* ctx) {
   cbp::serve_shutdown(c);
   cudaDeviceSynchronize();
   if (c->ws) cudaFree(c->ws);
-  for (int i = 0; i < Ctx::kMaxChunks; ++i)
+  for (int i = 0; i < Ctx::kChunkStreams; ++i)
     if (c->chunk_st[i]) cudaStreamDestroy(c->chunk_st[i]);
+  if (c->io_st) cudaStreamDestroy(c->io_st);
   for (int i = 0; i <= Ctx::kMaxChunks; ++i)
     if (c->chunk_ev[i]) cudaEventDestroy(c->chunk_ev[i]);
+  for (int i = 0; i < Ctx::kMaxChunks; ++i)
+    if (c->io_ev[i]) cudaEventDestroy(c->io_ev[i]);
   if (c->cnn_ws) cudaFree(c->cnn_ws);
   if (c->cnn_w) cudaFree(c->cnn_w);
   delete c;

@@ -36,9 +36,12 @@ struct Ctx {
   bool profiling = false;
   Prof prof;
   // internal streams and fork/join events of chunked synchronous calls
-  static constexpr int kMaxChunks = 4;
-  cudaStream_t chunk_st[kMaxChunks] = {};
+  static constexpr int kMaxChunks = 8;        // chunks of one call
+  static constexpr int kChunkStreams = 3;     // compute streams they rotate over
+  cudaStream_t chunk_st[kChunkStreams] = {};
+  cudaStream_t io_st = nullptr;               // host-to-device copies of host-I/O calls, in order
   cudaEvent_t chunk_ev[kMaxChunks + 1] = {};
+  cudaEvent_t io_ev[kMaxChunks] = {};
   bool chunk_ready = false;
   cbp_status ensure_chunk_streams();
   std::mutex serve_mu;        // guards creation of `serve`
@@ -55,7 +58,8 @@ struct Ctx {
 cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
                     const cbp_params* prm, void* k1, void* k2, void* latent, bool deblur,
                     char* wsp, cudaStream_t st, Prof* prof = nullptr,
-                    const PtrTables* tabs = nullptr, const float* cnn_w = nullptr);
+                    const PtrTables* tabs = nullptr, const float* cnn_w = nullptr,
+                    bool h2d_done = false);   // host I/O: inputs already copied by the caller
 void serve_shutdown(Ctx* c);
 
 }  // namespace cbp

@@ -221,6 +221,23 @@ def test_host_io_matches_device_path(gpu_ctx):
     assert torch.equal(ld.cpu(), lh) and torch.equal(kd.cpu(), kh)
 
 
+def test_host_io_chunked_pipeline_matches_device_path(gpu_ctx):
+    """40 pairs with host I/O: the call splits into five chunks whose inputs go over in
+    order on one copy stream while earlier chunks compute (three compute streams);
+    every pair's latent and kernels equal the device-resident call's."""
+    from paper_1203_4874_gb300 import cbp
+    b1, b2, *_, cfg = make_batch("video_480p", [8, 9, 10, 11, 12], h=64, w=96)
+    idx = [(7 * i) % 5 for i in range(40)]
+    B1 = torch.from_numpy(b1).float()[idx].contiguous()
+    B2 = torch.from_numpy(b2).float()[idx].contiguous()
+    prm = cbp.params(9, 11, path="mixed", eps=cfg.eps)
+    ld, kd, kd2, _, _ = cbp.cbp_deblur_pair(gpu_ctx, B1.cuda(), B2.cuda(), prm)
+    prm_h = cbp.params(9, 11, path="mixed", eps=cfg.eps, flags=cbp.CBP_FLAG_HOST_IO)
+    lh, kh, kh2, _, _ = cbp.cbp_deblur_pair(gpu_ctx, B1.pin_memory(), B2.pin_memory(), prm_h)
+    torch.cuda.synchronize()
+    assert torch.equal(ld.cpu(), lh) and torch.equal(kd.cpu(), kh) and torch.equal(kd2.cpu(), kh2)
+
+
 def test_non_finite_input_is_reported(gpu_ctx):
     b1, b2, *_ = make_batch("single_64", [2], fast=False)
     b1 = b1.copy()
