@@ -502,6 +502,33 @@ __device__ void tri_apply_q(const E* A, const E* tau, int n, V* b, bool back) {
   }
 }
 
+// Real reflectors on a real vector (real samples): half the work of the
+// complex form.
+__device__ void tri_apply_q_r(const double* A, const double* tau, int n, double* b, bool back) {
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+  for (int s = 0; s + 1 < n; ++s) {
+    const int k = back ? n - 2 - s : s;
+    const double tk = tau[k];
+    if (tk == 0.0) continue;
+    const double* vk = A + (size_t)k * n;
+    double acc = 0.0;
+    for (int i = lane; i < n; i += 32)
+      if (i > k) acc = fma(vk[i], b[i], acc);
+    const double f = tk * warp_sum(acc);
+    __syncwarp();
+    for (int i = lane; i < n; i += 32)
+      if (i > k) b[i] = fma(-f, vk[i], b[i]);
+    __syncwarp();
+  }
+}
+__device__ __forceinline__ double tri_norm2_r(const double* b, int n) {
+  const int lane = threadIdx.x & 31;
+  double s = 0.0;
+  for (int i = lane; i < n; i += 32) s = fma(b[i], b[i], s);
+  return warp_sum(s);
+}
+
 __device__ __forceinline__ double tri_norm2(const cd* b, int n) {
   const int lane = threadIdx.x & 31;
   double s = 0.0;
@@ -628,22 +655,37 @@ __device__ int tri_solve_lead(const TriWs& W, const cd* G, int n, int steps_far,
   const double lam0 = 0.5 * (br[0].lo + br[0].hi);
   const double lam1 = n > 1 ? 0.5 * (br[1].lo + br[1].hi) : lam0;
   const double lamn = 0.5 * (br[2].lo + br[2].hi);
-  // 3. inverse iteration (three steps) from a fixed start vector
+  // 3. inverse iteration (three steps) from a fixed start vector; 4. x = Q y
   tri_lu(W, n, lam0, eps * tnorm);
-  for (int i = lane; i < n; i += 32) W.z[i] = mk(1.0 + 0.25 * (double)((i * 7) % 5), 0.0);
-  __syncwarp();
-  for (int it = 0; it < 3; ++it) {
-    tri_solve(W, n, W.z);
+  if constexpr (sizeof(E) == sizeof(double)) {   // real: real vectors throughout
+    double* y = (double*)W.z;
+    for (int i = lane; i < n; i += 32) y[i] = 1.0 + 0.25 * (double)((i * 7) % 5);
     __syncwarp();
-    const double nz = tri_norm2(W.z, n);
-    const double sc = nz > 0.0 ? rsqrt_safe(nz) : 1.0;
-    for (int i = lane; i < n; i += 32) W.z[i] = sc * W.z[i];
+    for (int it = 0; it < 3; ++it) {
+      tri_solve<double, double>(W.u0, W.u1, W.u2, W.lm, W.piv, n, y);
+      __syncwarp();
+      const double nz = tri_norm2_r(y, n);
+      const double sc = nz > 0.0 ? rsqrt_safe(nz) : 1.0;
+      for (int i = lane; i < n; i += 32) y[i] = sc * y[i];
+      __syncwarp();
+    }
+    tri_apply_q_r((const double*)A, (const double*)tau, n, y, true);
+    const double sc = rsqrt_safe(tri_norm2_r(y, n));
+    for (int i = lane; i < n; i += 32) W.x[i] = mk(sc * y[i], 0.0);
     __syncwarp();
-  }
-  // 4. x = Q y
-  for (int i = lane; i < n; i += 32) W.x[i] = W.z[i];
-  tri_apply_q<E, cd>(A, tau, n, W.x, true);
-  {
+  } else {
+    for (int i = lane; i < n; i += 32) W.z[i] = mk(1.0 + 0.25 * (double)((i * 7) % 5), 0.0);
+    __syncwarp();
+    for (int it = 0; it < 3; ++it) {
+      tri_solve(W, n, W.z);
+      __syncwarp();
+      const double nz = tri_norm2(W.z, n);
+      const double sc = nz > 0.0 ? rsqrt_safe(nz) : 1.0;
+      for (int i = lane; i < n; i += 32) W.z[i] = sc * W.z[i];
+      __syncwarp();
+    }
+    for (int i = lane; i < n; i += 32) W.x[i] = W.z[i];
+    tri_apply_q<E, cd>(A, tau, n, W.x, true);
     const double sc = rsqrt_safe(tri_norm2(W.x, n));
     for (int i = lane; i < n; i += 32) W.x[i] = sc * W.x[i];
     __syncwarp();
@@ -858,6 +900,42 @@ __device__ void tri_olsen(const TriWs& W, int n, double gs, double tnorm) {
   const E* A = (const E*)W.A;
   const E* tau = (const E*)W.tau;
   const double eps = 2.220446049250313e-16, igs = 1.0 / gs;
+  if constexpr (sizeof(E) == sizeof(double)) {   // real sample: real vectors
+    double th = 0.0;
+    for (int i = lane; i < n; i += 32) th = fma(W.x[i].re, W.r[i].re, th);
+    const double theta = warp_sum(th);
+    double* ru = (double*)W.q;        // Q^T r, then u
+    double* yt = ru + n;              // Q^T x
+    double* zt = (double*)W.z;        // z, then the correction
+    for (int i = lane; i < n; i += 32) {
+      ru[i] = W.r[i].re - theta * W.x[i].re;
+      yt[i] = W.x[i].re;
+    }
+    tri_apply_q_r((const double*)A, (const double*)tau, n, ru, false);
+    tri_apply_q_r((const double*)A, (const double*)tau, n, yt, false);
+    tri_lu(W, n, theta * igs, eps * tnorm);
+    for (int i = lane; i < n; i += 32) zt[i] = yt[i];
+    __syncwarp();
+    tri_solve<double, double>(W.u0, W.u1, W.u2, W.lm, W.piv, n, ru);
+    tri_solve<double, double>(W.u0, W.u1, W.u2, W.lm, W.piv, n, zt);
+    __syncwarp();
+    double nu = 0.0, de = 0.0;
+    for (int i = lane; i < n; i += 32) {
+      nu = fma(yt[i], ru[i], nu);
+      de = fma(yt[i], zt[i], de);
+    }
+    nu = warp_sum(nu);
+    de = warp_sum(de);
+    const double ep = de != 0.0 ? nu / de : 0.0;
+    for (int i = lane; i < n; i += 32) zt[i] = igs * (ep * zt[i] - ru[i]);
+    tri_apply_q_r((const double*)A, (const double*)tau, n, zt, true);
+    for (int i = lane; i < n; i += 32) W.x[i] = mk(W.x[i].re + zt[i], 0.0);
+    __syncwarp();
+    const double sc = rsqrt_safe(tri_norm2(W.x, n));
+    for (int i = lane; i < n; i += 32) W.x[i] = sc * W.x[i];
+    __syncwarp();
+    return;
+  }
   cd th = mk(0.0, 0.0);
   for (int i = lane; i < n; i += 32) cfmac(th, W.x[i], W.r[i]);
   const double theta = warp_sum(th.re);
