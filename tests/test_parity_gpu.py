@@ -167,6 +167,25 @@ def test_ragged_sizes_channels_and_extra_samples(gpu_ctx):
     assert rel(g_lat[0], o["latent"]) <= 1e-9
 
 
+def test_largest_kernels_two_columns_per_lane(gpu_ctx):
+    """t1 + t2 = 60 (per-sample systems of 60 unknowns, the scale system 2M = 62):
+    the warp-level solvers' lanes each own two columns.  Noise-free f64 frames:
+    FP64 path within 1e-9 of the oracle and of the true kernels; mixed path within
+    1e-6 of the FP64 path (bar 1e-3)."""
+    rng = np.random.default_rng(29)
+    lat = rng.uniform(size=(2, 40, 44))
+    from cbp_synth import draw_kernel_pair
+    k1, k2 = draw_kernel_pair(rng, 29, 31, 31)
+    b1, b2 = oracle.blur_pair(lat, k1, k2)
+    g_lat, g_k1, g_k2, _ = run_gpu(gpu_ctx, b1[None], b2[None], 29, 31, "fp64", 0.0, "f64")
+    o = oracle_pair(b1, b2, 29, 31, 0.0)
+    assert rel(g_k1[0], o["k1"]) <= 1e-9 and rel(g_k2[0], o["k2"]) <= 1e-9
+    assert rel(g_k1[0], k1) <= 1e-9 and rel(g_k2[0], k2) <= 1e-9
+    assert rel(g_lat[0], o["latent"]) <= 1e-9
+    _, m_k1, m_k2, _ = run_gpu(gpu_ctx, b1[None], b2[None], 29, 31, "mixed", 0.0, "f64")
+    assert rel(m_k1[0], g_k1[0]) <= 1e-6 and rel(m_k2[0], g_k2[0]) <= 1e-6
+
+
 def test_batch_invariance_and_determinism(gpu_ctx):
     b1, b2, *_ , cfg = make_batch("video_480p", [4, 5, 6], h=96, w=128)
     a_lat, a_k1, a_k2, _ = run_gpu(gpu_ctx, b1, b2, 9, 11, "mixed", cfg.eps, "f32")
