@@ -77,7 +77,8 @@ cbp_status Ctx::ensure_chunk_streams() {
     if (cudaEventCreateWithFlags(&chunk_ev[i], cudaEventDisableTiming) != cudaSuccess)
       return CBP_ERR_CUDA;
   for (int i = 0; i < kMaxChunks; ++i)
-    if (cudaEventCreateWithFlags(&io_ev[i], cudaEventDisableTiming) != cudaSuccess)
+    if (cudaEventCreateWithFlags(&io_ev[i], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&read_ev[i], cudaEventDisableTiming) != cudaSuccess)
       return CBP_ERR_CUDA;
   chunk_ready = true;
   return CBP_OK;
@@ -106,7 +107,7 @@ cbp_status Ctx::ensure_cnn_ws(size_t bytes, cudaStream_t st) {
 cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
                     const cbp_params* prm, void* k1, void* k2, void* latent, bool deblur,
                     char* wsp, cudaStream_t st, Prof* prof, const PtrTables* tabs,
-                    const float* cnn_w, bool h2d_done) {
+                    const float* cnn_w, bool h2d_done, cudaEvent_t after_read) {
   cudaEvent_t ev = nullptr;
   auto begin = [&](int stage) {
     if (prof) prof->begin(stage, st, &ev);
@@ -188,6 +189,7 @@ cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
     launch_row_pass(p, d1, d2, wsp, st, !kin, true);
     end(CBP_STAGE_ROW_FFT, 1);
   }
+  if (after_read && cudaEventRecord(after_read, st) != cudaSuccess) return CBP_ERR_CUDA;
   if (p.learned) {
     // consistency residual of the proposal; accepted pairs skip the solves
     begin(CBP_STAGE_GATE);
@@ -412,8 +414,13 @@ cbp_status call_path(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
           cudaStreamWaitEvent(cs, c->io_ev[i], 0) != cudaSuccess)
         return CBP_ERR_CUDA;
     }
+    // Device-resident calls: chunk i starts once chunk i - 1 has read its
+    // frames, so the chunks run out of phase (one's latency-bound solves
+    // beside another's bandwidth-bound FFT passes).
+    if (!host_io && i > 0 && cudaStreamWaitEvent(cs, c->read_ev[i - 1], 0) != cudaSuccess)
+      return CBP_ERR_CUDA;
     s = cbp::run_plan(cp[i], &f1[i], &f2[i], prm, ck1, ck2, clat, deblur, w, cs, nullptr, nullptr,
-                      c->cnn_w, host_io);
+                      c->cnn_w, host_io, host_io ? nullptr : c->read_ev[i]);
     if (s != CBP_OK) return s;
     if (diag && cudaMemcpyAsync(diag + a, w + cp[i].off_diag, (size_t)cp[i].n * sizeof(cbp_diag),
                                 cudaMemcpyDeviceToHost, cs) != cudaSuccess)
@@ -460,8 +467,10 @@ cbp_status cbp_destroy(cbp_ctx* ctx) {
   if (c->io_st) cudaStreamDestroy(c->io_st);
   for (int i = 0; i <= Ctx::kMaxChunks; ++i)
     if (c->chunk_ev[i]) cudaEventDestroy(c->chunk_ev[i]);
-  for (int i = 0; i < Ctx::kMaxChunks; ++i)
+  for (int i = 0; i < Ctx::kMaxChunks; ++i) {
     if (c->io_ev[i]) cudaEventDestroy(c->io_ev[i]);
+    if (c->read_ev[i]) cudaEventDestroy(c->read_ev[i]);
+  }
   if (c->cnn_ws) cudaFree(c->cnn_ws);
   if (c->cnn_w) cudaFree(c->cnn_w);
   delete c;

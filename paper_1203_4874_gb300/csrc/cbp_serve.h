@@ -42,6 +42,7 @@ struct Ctx {
   cudaStream_t io_st = nullptr;               // host-to-device copies of host-I/O calls, in order
   cudaEvent_t chunk_ev[kMaxChunks + 1] = {};
   cudaEvent_t io_ev[kMaxChunks] = {};
+  cudaEvent_t read_ev[kMaxChunks] = {};      // chunk i has read its frames (row pass done)
   bool chunk_ready = false;
   cbp_status ensure_chunk_streams();
   std::mutex serve_mu;        // guards creation of `serve`
@@ -59,7 +60,8 @@ cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
                     const cbp_params* prm, void* k1, void* k2, void* latent, bool deblur,
                     char* wsp, cudaStream_t st, Prof* prof = nullptr,
                     const PtrTables* tabs = nullptr, const float* cnn_w = nullptr,
-                    bool h2d_done = false);   // host I/O: inputs already copied by the caller
+                    bool h2d_done = false,    // host I/O: inputs already copied by the caller
+                    cudaEvent_t after_read = nullptr);  // recorded once the frames are read
 void serve_shutdown(Ctx* c);
 
 }  // namespace cbp
