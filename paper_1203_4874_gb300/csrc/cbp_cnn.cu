@@ -109,6 +109,81 @@ __global__ void __launch_bounds__(kCnnThreads) k_cnn_input(FrameDesc f1, FrameDe
   x0[((int64_t)f * 2 + z) * kCnnSide * kCnnSide + o] = __float2bfloat16(acc * norm);
 }
 
+// The same resampling with one CTA per output row: the input rows of the row's
+// cells are read once, coalesced (a thread per input column), weighted by
+// their overlaps and summed over rows and channels into a shared column
+// profile; each output cell then sums its columns' profile with the column
+// overlaps.  Widths up to kCnnMaxW.
+constexpr int kCnnMaxW = 8192;
+constexpr int kCnnColsPT = 8;
+template <typename In>
+__device__ __forceinline__ void cnn_profile_cols(const In* base, const FrameDesc& fr, int r0, int r1,
+                                                 int ya, int yb, float* prof) {
+  float col[kCnnColsPT], v[kCnnColsPT];
+#pragma unroll
+  for (int j = 0; j < kCnnColsPT; ++j) col[j] = 0.f;
+  for (int r = r0; r < r1; ++r) {
+    const int wy = min(yb, (r + 1) * kCnnSide) - max(ya, r * kCnnSide);
+#pragma unroll
+    for (int j = 0; j < kCnnColsPT; ++j) v[j] = 0.f;
+    for (int ch = 0; ch < fr.c; ++ch) {
+      const In* row = base + (int64_t)ch * fr.cs + (int64_t)r * fr.rs + threadIdx.x;
+#pragma unroll
+      for (int j = 0; j < kCnnColsPT; ++j)
+        if ((int)threadIdx.x + j * kCnnThreads < fr.w) v[j] += (float)__ldg(row + j * kCnnThreads);
+    }
+#pragma unroll
+    for (int j = 0; j < kCnnColsPT; ++j) col[j] = fmaf((float)wy, v[j], col[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < kCnnColsPT; ++j) {
+    const int c = threadIdx.x + j * kCnnThreads;
+    if (c < fr.w) prof[c] = col[j];
+  }
+}
+
+__global__ void __launch_bounds__(kCnnThreads) k_cnn_input_rows(FrameDesc f1, FrameDesc f2, bf16* x0) {
+  __shared__ float prof[kCnnMaxW];
+  const int y = blockIdx.x, z = blockIdx.y, f = blockIdx.z;
+  const FrameDesc& fr = z ? f2 : f1;
+  const int r0 = (int)(((int64_t)y * fr.h) / kCnnSide);
+  const int r1 = min(fr.h, (int)(((int64_t)(y + 1) * fr.h + kCnnSide - 1) / kCnnSide));
+  const int ya = y * fr.h, yb = (y + 1) * fr.h;
+  const void* base = frame_base(fr, f);
+  if (fr.w <= kCnnColsPT * kCnnThreads) {
+    // kCnnColsPT columns per thread: their loads of one (row, channel) are in
+    // flight together
+    if (fr.f64) cnn_profile_cols<double>((const double*)base, fr, r0, r1, ya, yb, prof);
+    else cnn_profile_cols<float>((const float*)base, fr, r0, r1, ya, yb, prof);
+  } else {
+    for (int c = threadIdx.x; c < fr.w; c += blockDim.x) {
+      float col = 0.f;
+      for (int r = r0; r < r1; ++r) {
+        const int wy = min(yb, (r + 1) * kCnnSide) - max(ya, r * kCnnSide);
+        const int64_t rb = (int64_t)r * fr.rs + c;
+        float v = 0.f;
+        for (int ch = 0; ch < fr.c; ++ch) v += ld_frame<float>(base, (int64_t)ch * fr.cs + rb, fr.f64);
+        col = fmaf((float)wy, v, col);
+      }
+      prof[c] = col;
+    }
+  }
+  __syncthreads();
+  const float norm = 1.0f / ((float)fr.h * (float)fr.w * (float)fr.c);
+  for (int x = threadIdx.x; x < kCnnSide; x += blockDim.x) {
+    const int c0 = (int)(((int64_t)x * fr.w) / kCnnSide);
+    const int c1 = min(fr.w, (int)(((int64_t)(x + 1) * fr.w + kCnnSide - 1) / kCnnSide));
+    const int xa = x * fr.w, xb = (x + 1) * fr.w;
+    float acc = 0.f;
+    for (int c = c0; c < c1; ++c) {
+      const int wx = min(xb, (c + 1) * kCnnSide) - max(xa, c * kCnnSide);
+      acc = fmaf((float)wx, prof[c], acc);
+    }
+    x0[((int64_t)f * 2 + z) * kCnnSide * kCnnSide + (int64_t)y * kCnnSide + x] =
+        __float2bfloat16(acc * norm);
+  }
+}
+
 template <typename TO> __device__ __forceinline__ TO to_out(float v);
 template <> __device__ __forceinline__ bf16 to_out<bf16>(float v) { return __float2bfloat16(v); }
 template <> __device__ __forceinline__ float to_out<float>(float v) { return v; }
@@ -139,6 +214,81 @@ __global__ void __launch_bounds__(kCnnThreads) k_conv_fwd(const bf16* x, const f
   }
   if (L.relu) acc = fmaxf(acc, 0.f);
   y[(((int64_t)n * L.cout + co) * L.hout + oy) * L.hout + ox] = to_out<TO>(acc);
+}
+
+// The same convolution for 32 output channels, all computed by each thread for
+// kConvPos output positions: an input value is read once per position and
+// serves 32 channels, a weight (shared memory, [ci][u][v][co] so that the 32
+// channels of one tap are one broadcast row) serves kConvPos positions.
+constexpr int kConvPos = 2;
+constexpr int kConvCo = 32;
+template <typename TO>
+__global__ void __launch_bounds__(kCnnThreads) k_conv_fwd32(const bf16* x, const float* prm, TO* y,
+                                                            Layer L) {
+  extern __shared__ float ws[];   // [cin * k * k][32]
+  const int n = blockIdx.z;
+  const int kk = L.k * L.k, per = L.cin * kk;
+  for (int i = threadIdx.x; i < per * kConvCo; i += blockDim.x) {
+    const int co = i / per, t = i - co * per;     // parameter order [co][ci][u][v]
+    ws[t * kConvCo + co] = prm[L.woff + i];
+  }
+  __syncthreads();
+  const int npos = L.hout * L.hout;
+  const int o0 = (blockIdx.x * blockDim.x + threadIdx.x) * kConvPos;
+  if (o0 >= npos) return;
+  int oy[kConvPos], ox[kConvPos];
+  bool ok[kConvPos];
+#pragma unroll
+  for (int q = 0; q < kConvPos; ++q) {
+    ok[q] = o0 + q < npos;
+    const int o = ok[q] ? o0 + q : o0;
+    oy[q] = o / L.hout;
+    ox[q] = o % L.hout;
+  }
+  float acc[kConvPos][kConvCo];
+#pragma unroll
+  for (int c = 0; c < kConvCo; ++c) {
+    const float b = prm[L.boff + c];
+#pragma unroll
+    for (int q = 0; q < kConvPos; ++q) acc[q][c] = b;
+  }
+  for (int ci = 0; ci < L.cin; ++ci) {
+    const bf16* xc = x + ((int64_t)n * L.cin + ci) * L.hin * L.hin;
+    for (int u = 0; u < L.k; ++u) {
+      for (int v = 0; v < L.k; ++v) {
+        float xv[kConvPos];
+#pragma unroll
+        for (int q = 0; q < kConvPos; ++q) {
+          const int iy = oy[q] * L.s - L.p + u, ix = ox[q] * L.s - L.p + v;
+          xv[q] = (iy >= 0 && iy < L.hin && ix >= 0 && ix < L.hin)
+                      ? __bfloat162float(xc[iy * L.hin + ix])
+                      : 0.f;
+        }
+        const float4* wr = reinterpret_cast<const float4*>(ws + ((ci * L.k + u) * L.k + v) * kConvCo);
+#pragma unroll
+        for (int c4 = 0; c4 < kConvCo / 4; ++c4) {
+          const float4 w = wr[c4];
+#pragma unroll
+          for (int q = 0; q < kConvPos; ++q) {
+            acc[q][4 * c4 + 0] = fmaf(w.x, xv[q], acc[q][4 * c4 + 0]);
+            acc[q][4 * c4 + 1] = fmaf(w.y, xv[q], acc[q][4 * c4 + 1]);
+            acc[q][4 * c4 + 2] = fmaf(w.z, xv[q], acc[q][4 * c4 + 2]);
+            acc[q][4 * c4 + 3] = fmaf(w.w, xv[q], acc[q][4 * c4 + 3]);
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < kConvPos; ++q) {
+    if (!ok[q]) continue;
+#pragma unroll
+    for (int c = 0; c < kConvCo; ++c) {
+      float a = acc[q][c];
+      if (L.relu) a = fmaxf(a, 0.f);
+      y[(((int64_t)n * L.cout + c) * L.hout + oy[q]) * L.hout + ox[q]] = to_out<TO>(a);
+    }
+  }
 }
 
 // Softmax of each (pair, head) over its 225 logits; with targets, the loss
@@ -297,6 +447,14 @@ __global__ void k_cnn_to_kd(const float* K, int n, double* kd) {
 
 void launch_conv_fwd(const bf16* x, const float* prm, void* y, int li, int n, cudaStream_t st) {
   const Layer L = cnn_layer(li);
+  if (L.cout == kConvCo) {   // 32 output channels per thread
+    const int per_block = kCnnThreads * kConvPos;
+    dim3 g((L.hout * L.hout + per_block - 1) / per_block, 1, n);
+    const size_t sm = sizeof(float) * L.cin * L.k * L.k * kConvCo;
+    cudaFuncSetAttribute(k_conv_fwd32<bf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_conv_fwd32<bf16><<<g, kCnnThreads, sm, st>>>(x, prm, (bf16*)y, L);
+    return;
+  }
   dim3 g((L.hout * L.hout + kCnnThreads - 1) / kCnnThreads, L.cout, n);
   const size_t sm = sizeof(float) * L.cin * L.k * L.k;
   if (li == 3) k_conv_fwd<float><<<g, kCnnThreads, sm, st>>>(x, prm, (float*)y, L);
@@ -316,7 +474,10 @@ void cnn_forward(const FrameDesc& b1, const FrameDesc& b2, int n, const float* p
   const CnnWs L = cnn_ws_layout(n, false);
   bf16* x0 = (bf16*)(ws + L.x0);
   bf16* a[3] = {(bf16*)(ws + L.a1), (bf16*)(ws + L.a2), (bf16*)(ws + L.a3)};
-  k_cnn_input<<<dim3(kCnnSide * kCnnSide / kCnnThreads, 2, n), kCnnThreads, 0, st>>>(b1, b2, x0);
+  if (b1.w <= kCnnMaxW && b2.w <= kCnnMaxW)
+    k_cnn_input_rows<<<dim3(kCnnSide, 2, n), kCnnThreads, 0, st>>>(b1, b2, x0);
+  else
+    k_cnn_input<<<dim3(kCnnSide * kCnnSide / kCnnThreads, 2, n), kCnnThreads, 0, st>>>(b1, b2, x0);
   launch_conv_fwd(x0, prm, a[0], 0, n, st);
   launch_conv_fwd(a[0], prm, a[1], 1, n, st);
   launch_conv_fwd(a[1], prm, a[2], 2, n, st);

@@ -1085,15 +1085,25 @@ k_col_deconv(ColArgs a) {
   const cpx<T>* K1 = (const cpx<T>*)a.khat + ((int64_t)f * 2 + 0) * Ph * a.Pw2p + v0;
   const cpx<T>* K2 = (const cpx<T>*)a.khat + ((int64_t)f * 2 + 1) * Ph * a.Pw2p + v0;
   if (RESID) {
+    // a thread keeps one column and steps down the rows; its sums (about
+    // Ph / kRowStep terms) in the spectra's precision, the block's in double
     double num = 0.0, den = 0.0;
-    for (int idx = threadIdx.x; idx < CW * Ph; idx += blockDim.x) {
-      const int u = idx / CW, vl = idx % CW, v = v0 + vl;
-      if (vl >= nv) continue;
+    constexpr int kRowStep = kColThreads / CW;
+    const int vl = threadIdx.x % CW, v = v0 + vl;
+    if (vl < nv) {
+      const int64_t kstep = (int64_t)kRowStep * a.Pw2p;
+      const cpx<T>* k1p = K1 + (int64_t)(threadIdx.x / CW) * a.Pw2p + vl;
+      const cpx<T>* k2p = K2 + (int64_t)(threadIdx.x / CW) * a.Pw2p + vl;
+      T tn = (T)0, td = (T)0;
+      for (int idx = threadIdx.x; idx < CW * Ph; idx += kColThreads, k1p += kstep, k2p += kstep) {
+        const cpx<T> k1 = ldg_cpx(k1p), k2 = ldg_cpx(k2p);
+        const cpx<T> r = k2 * r1[idx] - k1 * r2[idx];
+        tn += abs2(r);
+        td += abs2(r1[idx]);
+      }
       const double wv = (v == 0 || 2 * v == a.Pw) ? 1.0 : 2.0;
-      const cpx<T> k1 = K1[(int64_t)u * a.Pw2p + vl], k2 = K2[(int64_t)u * a.Pw2p + vl];
-      const cpx<T> r = k2 * r1[idx] - k1 * r2[idx];
-      num += wv * (double)abs2(r);
-      den += wv * (double)abs2(r1[idx]);
+      num = wv * (double)tn;
+      den = wv * (double)td;
     }
     __shared__ double red[2][kColThreads / 32];
     num = warp_sum(num);
@@ -1440,20 +1450,37 @@ void run_col_deconv(const Plan& p, char* ws, cudaStream_t st) {
 
 // Learned path: rho and the accept flag of every pair from the partial sums
 // (fixed summation order).
-__global__ void k_gate(const double* rpart, int n, int C, int strips, double accept_rho, int* acc,
-                       double* rho) {
-  const int f = blockIdx.x * blockDim.x + threadIdx.x;
-  if (f >= n) return;
+// One CTA per pair: the pair's C * strips partial sums, reduced in a fixed
+// order (deterministic), then rho and the decision.
+constexpr int kGateThreads = 128;
+__global__ void __launch_bounds__(kGateThreads) k_gate(const double* rpart, int n, int C, int strips,
+                                                      double accept_rho, int* acc, double* rho) {
+  const int f = blockIdx.x;
+  const int m = C * strips;
+  const double* o = rpart + (int64_t)f * m * 2;
   double num = 0.0, den = 0.0;
-  for (int ch = 0; ch < C; ++ch)
-    for (int s = 0; s < strips; ++s) {
-      const double* o = rpart + (((int64_t)f * C + ch) * strips + s) * 2;
-      num += o[0];
-      den += o[1];
+  for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    num += o[2 * i];
+    den += o[2 * i + 1];
+  }
+  __shared__ double red[2][kGateThreads / 32];
+  num = warp_sum(num);
+  den = warp_sum(den);
+  if ((threadIdx.x & 31) == 0) {
+    red[0][threadIdx.x >> 5] = num;
+    red[1][threadIdx.x >> 5] = den;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double sn = 0.0, sd = 0.0;
+    for (int w = 0; w < kGateThreads / 32; ++w) {
+      sn += red[0][w];
+      sd += red[1][w];
     }
-  const double r = den > 0.0 ? sqrt(num / den) : INFINITY;
-  rho[f] = r;
-  acc[f] = r <= accept_rho ? 1 : 0;
+    const double r = sd > 0.0 ? sqrt(sn / sd) : INFINITY;
+    rho[f] = r;
+    acc[f] = r <= accept_rho ? 1 : 0;
+  }
 }
 
 template <typename T>
@@ -1547,7 +1574,7 @@ void launch_row_ifft(const Plan& p, char* ws, void* latent, int out_f64, cudaStr
 void launch_residual_gate(const Plan& p, char* ws, cudaStream_t st) {
   if (p.fft_f64) run_col_deconv<double, true>(p, ws, st);
   else run_col_deconv<float, true>(p, ws, st);
-  k_gate<<<(p.n + 127) / 128, 128, 0, st>>>((const double*)(ws + p.off_rpart), p.n, p.C, p.col_strips,
+  k_gate<<<p.n, kGateThreads, 0, st>>>((const double*)(ws + p.off_rpart), p.n, p.C, p.col_strips,
                                             p.accept_rho, (int*)(ws + p.off_acc),
                                             (double*)(ws + p.off_rho));
 }
