@@ -58,7 +58,7 @@ struct Plan {
   int H, W;                    // latent size
   int t1, t2, M, ns, nn;       // ns = M/2 + 1 solved samples per direction; nn = t1 + t2
   int Ph, Pw, Pw2;             // FFT grid; Pw2 = Pw/2 + 1 stored spectrum columns
-  int Pw2p;                    // row pitch of the spectra: Pw2 rounded up to even
+  int Pw2p;                    // row pitch of the spectra: Pw2 rounded up to a multiple of 4
   int mixed;                   // estimation path: 0 FP64, 1 mixed
   int fft_f64;                 // deconvolution arithmetic in double
   int frames_f64;              // float64 frames (fold bins are doubles, else (hi, lo) float pairs)

@@ -128,7 +128,7 @@ cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_param
   if (p.Ph < hmax || p.Pw < wmax || !is_7_smooth(p.Ph) || !is_7_smooth(p.Pw))
     return CBP_ERR_INVALID_ARG;
   p.Pw2 = p.Pw / 2 + 1;
-  p.Pw2p = p.Pw2 + (p.Pw2 & 1);
+  p.Pw2p = (p.Pw2 + 3) & ~3;   // 32-byte rows for float spectra: a 4-column strip row is one sector
   p.pw_half = (p.Pw % 2 == 0) ? 1 : 0;
   p.mixed = prm->path != CBP_PATH_FP64;
   const int frame_f64 = b1->dtype == CBP_F64;
