@@ -8,7 +8,7 @@
 #include <new>
 #include "cbp.h"
 #include "cbp_internal.h"
-#ifdef CBP_DEBUG_ERRORS
+#if defined(CBP_DEBUG_ERRORS) || defined(CBP_TIMELINE)
 #include <cstdio>
 #endif
 #include "cbp_serve.h"
@@ -378,6 +378,14 @@ cbp_status call_path(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
   }
   s = c->ensure_ws(off[nch], st);
   if (s != CBP_OK) return s;
+#ifdef CBP_TIMELINE
+  // Diagnostic build: per-chunk stage events against a start event, printed
+  // once the call completes (the call becomes synchronous).
+  static cbp::Prof tl[Ctx::kMaxChunks];
+  cudaEvent_t tl0 = nullptr;
+  cudaEventCreate(&tl0);
+  cudaEventRecord(tl0, st);
+#endif
   if (cudaEventRecord(c->chunk_ev[c->kMaxChunks], st) != cudaSuccess) return CBP_ERR_CUDA;
   const bool kf64 = b1->dtype == CBP_F64 || (prm->flags & CBP_FLAG_KERNELS_F64);
   const size_t kes = kf64 ? 8 : 4, les = b1->dtype == CBP_F64 ? 8 : 4;
@@ -419,7 +427,12 @@ cbp_status call_path(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
     // beside another's bandwidth-bound FFT passes).
     if (!host_io && i > 0 && cudaStreamWaitEvent(cs, c->read_ev[i - 1], 0) != cudaSuccess)
       return CBP_ERR_CUDA;
-    s = cbp::run_plan(cp[i], &f1[i], &f2[i], prm, ck1, ck2, clat, deblur, w, cs, nullptr, nullptr,
+#ifdef CBP_TIMELINE
+    cbp::Prof* tlp = &tl[i];
+#else
+    cbp::Prof* tlp = nullptr;
+#endif
+    s = cbp::run_plan(cp[i], &f1[i], &f2[i], prm, ck1, ck2, clat, deblur, w, cs, tlp, nullptr,
                       c->cnn_w, host_io, host_io ? nullptr : c->read_ev[i]);
     if (s != CBP_OK) return s;
     if (diag && cudaMemcpyAsync(diag + a, w + cp[i].off_diag, (size_t)cp[i].n * sizeof(cbp_diag),
@@ -429,6 +442,22 @@ cbp_status call_path(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
         cudaStreamWaitEvent(st, c->chunk_ev[i], 0) != cudaSuccess)
       return CBP_ERR_CUDA;
   }
+#ifdef CBP_TIMELINE
+  cudaStreamSynchronize(st);
+  for (int i = 0; i < nch; ++i) {
+    for (const cbp::Prof::Rec& r : tl[i].recs) {
+      float ta = 0.f, tb = 0.f;
+      cudaEventElapsedTime(&ta, tl0, r.a);
+      cudaEventElapsedTime(&tb, tl0, r.b);
+      printf("timeline chunk=%d stage=%d begin=%.4f end=%.4f\n", i, r.stage, ta, tb);
+      tl[i].pool.push_back(r.a);
+      tl[i].pool.push_back(r.b);
+    }
+    tl[i].recs.clear();
+  }
+  fflush(stdout);
+  cudaEventDestroy(tl0);
+#endif
   return CBP_OK;
 }
 

@@ -635,6 +635,13 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
   }
   const int M = a.M, MM = M * M, t1 = a.t1, t2 = a.t2;
   const int n = 2 * M;
+#ifdef CBP_PHASE_TIMING
+  long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0}, tkv[6] = {0, 0, 0, 0, 0, 0};
+  long long* tk = f < 2 ? tkv : nullptr;
+#else
+  long long* tk = nullptr;
+#endif
+  CBP_TICK(ph, 0);
   cd* Gs = (cd*)smem;                   // [n][n] normal matrix
   double* red = (double*)(Gs + n * n);   // block reductions
   char* p = (char*)(red + 32);
@@ -661,6 +668,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
     ab[idx] = acc;
   }
   __syncthreads();
+  CBP_TICK(ph, 1);
   // normal matrix of the scale system
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     const int r = idx / n, c = idx % n;
@@ -689,13 +697,15 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
     Gs[idx] = g;
   }
   __syncthreads();
+  CBP_TICK(ph, 2);
   // Null vector of the scale system by the warp-level tridiagonal solver, one
   // refinement step against the exact operator (FP64 path); the mixed path
   // takes its single-precision T with Newton steps against the double G.
   ScaleApply ap{ab, M};
   const TriWs W = carve_tri(smem + scale_tri_offset(M), n);
-  const TriResult res = tri_smallest<cd, true>(W, Gs, n, 1, 1, 1e300, ap, nullptr, a.mixed != 0);
+  const TriResult res = tri_smallest<cd, true>(W, Gs, n, 1, 1, 1e300, ap, tk, a.mixed != 0);
   __syncthreads();
+  CBP_TICK(ph, 3);
   const cd* xs = W.x;
   // X_k[i][j] = (gamma_j A_k[i][j] + delta_i B_k[i][j]) / 2
   for (int idx = threadIdx.x; idx < 2 * MM; idx += blockDim.x) {
@@ -706,6 +716,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
   __shared__ cd x00[2];
   if (threadIdx.x < 2) x00[threadIdx.x] = X[threadIdx.x * MM];
   __syncthreads();
+  CBP_TICK(ph, 4);
   // inverse DFT, separable: T[i][q] = sum_j X[i][j] w^{-jq};  K[p][q] = sum_i w^{-ip} T[i][q] / M^2
   __shared__ double acc_sq[4];  // re^2, im^2, outside-support, total  (per kernel, reused)
   for (int k = 0; k < 2; ++k) {
@@ -768,6 +779,14 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
     }
     __syncthreads();
   }
+  CBP_TICK(ph, 5);
+#ifdef CBP_PHASE_TIMING
+  if (tk && threadIdx.x == 0)
+    printf("scale f=%d | lift %lld normal %lld tri %lld (reduce %lld bisect %lld invit %lld newton %lld "
+           "theta %lld) combine %lld idft %lld\n", f, ph[1] - ph[0], ph[2] - ph[1], ph[3] - ph[2],
+           tkv[1] - tkv[0], tkv[2] - tkv[1], tkv[3] - tkv[2], tkv[4] - tkv[3], tkv[5] - tkv[4],
+           ph[4] - ph[3], ph[5] - ph[4]);
+#endif
   // aggregate diagnostics
   if (threadIdx.x == 0) {
     double kappa = 0, gap = 1e300, smin = 0;
