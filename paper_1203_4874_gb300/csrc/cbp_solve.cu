@@ -353,9 +353,79 @@ struct SylvesterApply {
   int C, t1, t2, L;
   bool real;        // real sample (z = 1, or z = -1 for even M): real arithmetic
   __device__ void operator()(const cd* x, cd* out) const {
-    if (real) run<true, false>(x, out);
-    else if (F[0]) run<false, true>(x, out);
-    else run<false, false>(x, out);
+    if (real) {
+      if constexpr (BLOCK) {
+        if (F[0]) {
+          run_ff_real(x, out);
+          return;
+        }
+      }
+      run<true, false>(x, out);
+    } else if (F[0]) {
+      run<false, true>(x, out);
+    } else {
+      run<false, false>(x, out);
+    }
+  }
+  // A real sample from float-float samples (mixed path), by the whole CTA:
+  // the same two products in float-float arithmetic on the single-precision
+  // units (each product exact to ~1e-14, rounding terms gathered in the low
+  // part and renormalised per row and per channel), y held as float pairs.
+  // Against the double products the double-precision units (a few per SM)
+  // took, the single-precision ones take ~10 operations per product at 64
+  // times the rate.
+  __device__ void run_ff_real(const cd* x, cd* out) const {
+    __shared__ float2 xf[kMaxN];
+    const int lane = threadIdx.x & 31, nth = blockDim.x;
+    const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int len0 = P.len[0], len1 = P.len[1], n = t1 + t2;
+    float2* yf = reinterpret_cast<float2*>(y);
+    team_sync<BLOCK>();
+    for (int i = threadIdx.x; i < n; i += nth) {
+      const float h = (float)x[i].re;
+      xf[i] = make_float2(h, (float)(x[i].re - (double)h));
+    }
+    team_sync<BLOCK>();
+    for (int idx = threadIdx.x; idx < C * L; idx += nth) {
+      const int ch = idx / L, i = idx - ch * L;
+      const cdf* r0 = F[0] + ch * fstride[0];
+      const cdf* r1 = F[1] + ch * fstride[1];
+      FF acc;
+      const int q0 = max(0, i - len0 + 1), q1 = min(t2 - 1, i);
+      for (int q = q0; q <= q1; ++q) {     // b1 * v
+        const cdf b = r0[i - q];
+        const float2 v = xf[t1 + q];
+        acc.mac(b.rh, b.rl, v.x, v.y);
+      }
+      const int p0 = max(0, i - len1 + 1), p1 = min(t1 - 1, i);
+      for (int p = p0; p <= p1; ++p) {     // - b2 * u
+        const cdf b = r1[i - p];
+        const float2 u = xf[p];
+        acc.mac(-b.rh, -b.rl, u.x, u.y);
+      }
+      acc.add(0.f, 0.f);
+      yf[idx] = make_float2(acc.hi, acc.lo);
+    }
+    team_sync<BLOCK>();
+    for (int o = wid; o < n; o += nw) {
+      const int k = o < t1 ? 1 : 0;       // u rows use b2, v rows use b1
+      const int sh = o < t1 ? o : o - t1;
+      const int lk = k ? len1 : len0;
+      FF acc;
+      for (int ch = 0; ch < C; ++ch) {
+        const cdf* rk = F[k] + ch * fstride[k];
+        const float2* yr = yf + ch * L + sh;
+        for (int m = lane; m < lk; m += 32) {
+          const cdf b = rk[m];
+          const float2 v = yr[m];
+          acc.mac(b.rh, b.rl, v.x, v.y);
+        }
+        acc.add(0.f, 0.f);
+      }
+      const double re = warp_sum(acc.value());
+      if (lane == 0) out[o] = o < t1 ? mk(-re, 0.0) : mk(re, 0.0);
+    }
+    team_sync<BLOCK>();
   }
   template <bool FFS>
   __device__ __forceinline__ cd ld(const void* row, int m) const {
@@ -493,6 +563,12 @@ __global__ void k_sample_solve(SampleArgs a, int nreal) {
     ap.L = a.len[ps][0] + a.t2 - 1;
     ap.y = a.resid + o * a.C * (int64_t)a.Lmax;
     ap.F[0] = ap.F[1] = nullptr;
+    if (a.mixed) {   // the refinement step in float-float arithmetic
+      for (int k = 0; k < 2; ++k) {
+        ap.F[k] = a.pzf[ps][k] + ((int64_t)f * a.C * a.ns + s) * a.len[ps][k];
+        ap.fstride[k] = (int64_t)a.len[ps][k] * a.ns;
+      }
+    }
     ap.real = true;
     res = tri_smallest<double, true>(W, G, n, far, 1, gap, ap, tk);
     if (warp != 0) return;
