@@ -298,7 +298,7 @@ cbp_status copy_stages(const Plan& p, const char* ws, const cbp_stage_out* o, cu
 // streams: the chunks' kernels fill each other's idle
 // SMs and tails (the scale solve, for one, runs one block per pair).  Pairs
 // are independent, so the results do not depend on the split.
-constexpr int kChunks = 3;
+constexpr int kChunks = 4;
 constexpr int kIoChunks = Ctx::kMaxChunks;
 constexpr int kMinChunkPairs = 8;
 

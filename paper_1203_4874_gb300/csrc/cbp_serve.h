@@ -37,7 +37,7 @@ struct Ctx {
   Prof prof;
   // internal streams and fork/join events of chunked synchronous calls
   static constexpr int kMaxChunks = 8;        // chunks of one call
-  static constexpr int kChunkStreams = 3;     // compute streams they rotate over
+  static constexpr int kChunkStreams = 4;     // compute streams they rotate over
   cudaStream_t chunk_st[kChunkStreams] = {};
   cudaStream_t io_st = nullptr;               // host-to-device copies of host-I/O calls, in order
   cudaEvent_t chunk_ev[kMaxChunks + 1] = {};
