@@ -540,7 +540,7 @@ __global__ void k_sample_solve(SampleArgs a, int nreal) {
   const TriWs W = carve_tri(smem + (real ? 0 : (size_t)warp * tri_ws_bytes(n)), n);
   const cd* G = a.G + o * n * n;
 #ifdef CBP_PHASE_TIMING
-  long long tkv[6] = {0, 0, 0, 0, 0, 0};
+  long long tkv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   long long* tk = f == 0 ? tkv : nullptr;
 #else
   long long* tk = nullptr;
@@ -594,8 +594,9 @@ __global__ void k_sample_solve(SampleArgs a, int nreal) {
 #ifdef CBP_PHASE_TIMING
   if (tk && lane == 0)
     printf("tri pass=%d s=%d real=%d near=%d | reduce %lld bisect %lld invit %lld newton %lld "
-           "theta %lld\n", ps, s, (int)real, res.near_degenerate, tkv[1] - tkv[0], tkv[2] - tkv[1],
-           tkv[3] - tkv[2], tkv[4] - tkv[3], tkv[5] - tkv[4]);
+           "(apply %lld) theta %lld\n", ps, s, (int)real, res.near_degenerate, tkv[1] - tkv[0],
+           tkv[2] - tkv[1], tkv[3] - tkv[2], tkv[4] - tkv[3], tkv[6] ? tkv[6] - tkv[3] : 0,
+           tkv[5] - tkv[4]);
 #endif
   for (int i = lane; i < n; i += 32) a.X[o * n + i] = W.x[i];
   if (lane == 0) {
@@ -712,7 +713,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
   const int M = a.M, MM = M * M, t1 = a.t1, t2 = a.t2;
   const int n = 2 * M;
 #ifdef CBP_PHASE_TIMING
-  long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0}, tkv[6] = {0, 0, 0, 0, 0, 0};
+  long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0}, tkv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   long long* tk = f < 2 ? tkv : nullptr;
 #else
   long long* tk = nullptr;

@@ -705,8 +705,10 @@ __device__ int tri_solve_lead(const TriWs& W, const cd* G, int n, int steps_far,
 // gap per step), until the correction stops shrinking or falls below 1e-10.
 // For complex matrices whose two smallest eigenvalues single precision
 // separates by more than 3e-5 lambda_max (contraction <~ 0.1 per step, at
-// most 12 steps); returns false, having changed
-// nothing but the work area, for the others (they take tri_solve_lead).
+// most 12 steps), or separates at all with a gap above 1e-5 lambda_max (at
+// most 24 steps, which must bring the correction below 1e-9); returns false,
+// having changed nothing but the work area, for the others (they take
+// tri_solve_lead).
 __device__ bool tri_solve_lead_sp(const TriWs& W, const cd* G, int n, TriResult& res, double& gs,
                                   double& tnorm, long long* tk) {
   const int lane = threadIdx.x & 31;
@@ -758,8 +760,20 @@ __device__ bool tri_solve_lead_sp(const TriWs& W, const cd* G, int n, TriResult&
   }
   const double lam0 = 0.5 * (br[0].lo + br[0].hi), lam1 = 0.5 * (br[1].lo + br[1].hi);
   const double lamn = 0.5 * (br[2].lo + br[2].hi);
-  // separated beyond the error bounds?
-  if (!((br[1].lo - eb) - (br[0].hi + eb) > 3e-5 * lamn)) return false;
+  // separated beyond the error bounds?  Well beyond (3e-5 lambda_max): at
+  // most 12 Newton steps, contraction <~ 0.1.  Narrowly (apart within the
+  // bounds, gap above 1e-5 lambda_max, contraction <~ 0.3): up to 24 steps,
+  // and the double-precision solve after all unless they converge.
+  const double sep = (br[1].lo - eb) - (br[0].hi + eb);
+  const bool wide = sep > 3e-5 * lamn;
+  if (!wide && !(sep > 0.0 && lam1 - lam0 > 1e-5 * lamn)) {
+#ifdef CBP_PHASE_TIMING
+    if (lane == 0)
+      printf("sp-reject n=%d lam0/lamn %.3e lam1/lamn %.3e eb/lamn %.3e\n", n, lam0 / lamn, lam1 / lamn,
+             eb / lamn);
+#endif
+    return false;
+  }
   if (tk && lane == 0) tk[2] = clock64();
   // inverse iteration in single precision (three steps)
   tri_lu<float>(d, e, u0, u1, u2, lm, W.piv, n, (float)lam0, (float)(1.2e-7 * tnorm));
@@ -816,8 +830,10 @@ __device__ bool tri_solve_lead_sp(const TriWs& W, const cd* G, int n, TriResult&
   cf* yt = (cf*)W.z;          // Q^H x
   cf* yq = yt + n;            // x in single precision
   cf* rq = (cf*)W.r;          // r in single precision, then d~
-  double dprev = 1e300;
-  for (int it = 0; it < 12; ++it) {
+  double dprev = 1e300, dn = 1e300;
+  const int max_it = wide ? 12 : 24;
+  const double stall = wide ? 0.25 : 0.5;
+  for (int it = 0; it < max_it; ++it) {
     cd gx[2];
     cd th = mk(0.0, 0.0);
 #pragma unroll
@@ -881,9 +897,15 @@ __device__ bool tri_solve_lead_sp(const TriWs& W, const cd* G, int n, TriResult&
     const double sc = rsqrt_safe(tri_norm2(W.x, n));
     for (int i = lane; i < n; i += 32) W.x[i] = sc * W.x[i];
     __syncwarp();
-    const double dn = sqrt((double)d2);
-    if (dn < 1e-10 || dn > 0.25 * dprev) break;
+    dn = sqrt((double)d2);
+    if (dn < 1e-10 || dn > stall * dprev) break;
     dprev = dn;
+  }
+  if (!wide && !(dn < 1e-9)) {
+#ifdef CBP_PHASE_TIMING
+    if (lane == 0) printf("sp-narrow-fail n=%d last correction %.3e\n", n, dn);
+#endif
+    return false;
   }
   res.lam_min = gs * lam0;
   res.lam_2 = gs * lam1;
@@ -1023,6 +1045,7 @@ __device__ TriResult tri_smallest(const TriWs& W, const cd* G, int n, int steps_
   for (int it = 0; it < steps; ++it) {
     apply(W.x, W.r);
     team_sync<BLOCK>();
+    if (tk && lead && lane == 0) tk[6] = clock64();   // end of the last step's apply
     if (lead) tri_olsen<E>(W, n, gs, tnorm);
     team_sync<BLOCK>();
   }
