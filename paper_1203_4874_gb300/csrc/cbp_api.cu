@@ -292,8 +292,9 @@ cbp_status copy_stages(const Plan& p, const char* ws, const cbp_stage_out* o, cu
   return CBP_OK;
 }
 
-// A batch is split into up to kChunks chunks (kIoChunks with host I/O) of at
-// least kMinChunkPairs pairs
+// A batch is split into up to kChunks chunks (kIoChunks with host I/O) of
+// about n / chunks pairs, at least kMinChunkPairs (host I/O: the last three
+// smaller)
 // (each with its own plan and workspace region) on the context's internal
 // streams: the chunks' kernels fill each other's idle
 // SMs and tails (the scale solve, for one, runs one block per pair).  Pairs
@@ -368,8 +369,18 @@ cbp_status call_path(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
   size_t off[Ctx::kMaxChunks + 1];
   start[0] = 0;
   off[0] = 0;
+  // Host I/O: the last chunk's compute and read-back follow the last input
+  // copy with the link idle, so the last three chunks shrink (weights 0.73,
+  // 0.45, 0.27 of the others'); otherwise equal chunks.
+  double wt[Ctx::kMaxChunks], wsum = 0.0, wacc = 0.0;
   for (int i = 0; i < nch; ++i) {
-    start[i + 1] = (int)((int64_t)p.n * (i + 1) / nch);
+    const int back = nch - 1 - i;   // 0 for the last chunk
+    wt[i] = (host_io && nch >= 4 && back < 3) ? (back == 0 ? 0.27 : back == 1 ? 0.45 : 0.73) : 1.0;
+    wsum += wt[i];
+  }
+  for (int i = 0; i < nch; ++i) {
+    wacc += wt[i];
+    start[i + 1] = i + 1 == nch ? p.n : (int)std::llround((double)p.n * wacc / wsum);
     f1[i] = frames_slice(b1, start[i], start[i + 1] - start[i]);
     f2[i] = frames_slice(b2, start[i], start[i + 1] - start[i]);
     s = cbp::make_plan(&f1[i], &f2[i], prm, &cp[i]);
