@@ -710,7 +710,7 @@ __device__ int tri_solve_lead(const TriWs& W, const cd* G, int n, int steps_far,
 // having changed nothing but the work area, for the others (they take
 // tri_solve_lead).
 __device__ bool tri_solve_lead_sp(const TriWs& W, const cd* G, int n, TriResult& res, double& gs,
-                                  double& tnorm, long long* tk) {
+                                  double& tnorm, long long* tk, bool prereduced = false) {
   const int lane = threadIdx.x & 31;
   cf* A = (cf*)W.A;
   cf* tau = (cf*)W.tau;
@@ -728,13 +728,15 @@ __device__ bool tri_solve_lead_sp(const TriWs& W, const cd* G, int n, TriResult&
   frexp(gmax, &ex);
   gs = ldexp(1.0, ex);
   const double igs = ldexp(1.0, -ex);
-  const float igsf = (float)igs;
-  for (int idx = lane; idx < n * n; idx += 32)
-    A[idx] = mk((float)G[idx].re * igsf, (float)G[idx].im * igsf);
-  __syncwarp();
-  if (tk && lane == 0) tk[0] = clock64();
-  tri_reduce<cf>(A, tau, (cf*)W.w, d, e, n);
-  if (tk && lane == 0) tk[1] = clock64();
+  if (!prereduced) {   // else the CTA has reduced the same single-precision copy
+    const float igsf = (float)igs;
+    for (int idx = lane; idx < n * n; idx += 32)
+      A[idx] = mk((float)G[idx].re * igsf, (float)G[idx].im * igsf);
+    __syncwarp();
+    if (tk && lane == 0) tk[0] = clock64();
+    tri_reduce<cf>(A, tau, (cf*)W.w, d, e, n);
+    if (tk && lane == 0) tk[1] = clock64();
+  }
   float glo = 1e30f, ghi = -1e30f;
   for (int i = lane; i < n; i += 32) {
     const float rad = (i > 0 ? fabsf(e[i - 1]) : 0.f) + (i + 1 < n ? fabsf(e[i]) : 0.f);
@@ -1031,8 +1033,32 @@ __device__ TriResult tri_smallest(const TriWs& W, const cd* G, int n, int steps_
       pre = true;
     }
   }
+  bool pre_sp = false;
+  if constexpr (BLOCK && sizeof(E) == sizeof(cd)) {
+    if (single && n > 2) {
+      // the CTA reduces the single-precision copy G * 2^-ex together; the
+      // lead warp goes on from T (a double-precision solve, if it follows,
+      // reduces G again on its own)
+      double gmax = 0.0;
+      for (int i = lane; i < n; i += 32) gmax = fmax(gmax, G[(size_t)i * n + i].re);
+      gmax = warp_max(gmax);
+      if (gmax > 0.0) {
+        int ex;
+        frexp(gmax, &ex);
+        const float igsf = (float)ldexp(1.0, -ex);
+        cf* A = (cf*)W.A;
+        for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x)
+          A[idx] = mk((float)G[idx].re * igsf, (float)G[idx].im * igsf);
+        __syncthreads();
+        if (tk && threadIdx.x == 0) tk[0] = clock64();
+        tri_reduce_block<cf>(A, (cf*)W.tau, (cf*)W.w, W.df, (float*)W.e, n, (cf*)W.part);
+        if (tk && threadIdx.x == 0) tk[1] = clock64();
+        pre_sp = true;
+      }
+    }
+  }
   if (lead) {
-    if (single && n > 2 && tri_solve_lead_sp(W, G, n, res, gs, tnorm, tk))
+    if (single && n > 2 && tri_solve_lead_sp(W, G, n, res, gs, tnorm, tk, pre_sp))
       steps = 0;
     else
       steps = tri_solve_lead<E>(W, G, n, steps_far, steps_near, refine_gap, res, gs, tnorm, tk, pre);
