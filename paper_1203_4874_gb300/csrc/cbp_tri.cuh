@@ -995,6 +995,57 @@ __device__ void tri_olsen(const TriWs& W, int n, double gs, double tnorm) {
   __syncwarp();
 }
 
+// The same step for a real sample by a CTA of three or more warps: the two
+// projections onto T's basis and the factorisation of T - theta run on three
+// warps at once, the two solves on two, the rest on the lead warp (the same
+// arithmetic as tri_olsen<double>, in the same order within each chain).
+__device__ void tri_olsen_real_block(const TriWs& W, int n, double gs, double tnorm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const double* A = (const double*)W.A;
+  const double* tau = (const double*)W.tau;
+  const double eps = 2.220446049250313e-16, igs = 1.0 / gs;
+  double* ru = (double*)W.q;        // Q^T r, then u
+  double* yt = ru + n;              // Q^T x
+  double* zt = (double*)W.z;        // z, then the correction
+  double th = 0.0;
+  for (int i = lane; i < n; i += 32) th = fma(W.x[i].re, W.r[i].re, th);
+  const double theta = warp_sum(th);
+  if (warp == 0) {
+    for (int i = lane; i < n; i += 32) ru[i] = W.r[i].re - theta * W.x[i].re;
+    tri_apply_q_r(A, tau, n, ru, false);
+  } else if (warp == 1) {
+    for (int i = lane; i < n; i += 32) yt[i] = W.x[i].re;
+    tri_apply_q_r(A, tau, n, yt, false);
+    for (int i = lane; i < n; i += 32) zt[i] = yt[i];
+    __syncwarp();
+  } else if (warp == 2) {
+    tri_lu(W, n, theta * igs, eps * tnorm);
+  }
+  __syncthreads();
+  if (warp == 0) tri_solve<double, double>(W.u0, W.u1, W.u2, W.lm, W.piv, n, ru);
+  else if (warp == 1) tri_solve<double, double>(W.u0, W.u1, W.u2, W.lm, W.piv, n, zt);
+  __syncthreads();
+  if (warp == 0) {
+    double nu = 0.0, de = 0.0;
+    for (int i = lane; i < n; i += 32) {
+      nu = fma(yt[i], ru[i], nu);
+      de = fma(yt[i], zt[i], de);
+    }
+    nu = warp_sum(nu);
+    de = warp_sum(de);
+    const double ep = de != 0.0 ? nu / de : 0.0;
+    for (int i = lane; i < n; i += 32) zt[i] = igs * (ep * zt[i] - ru[i]);
+    tri_apply_q_r(A, tau, n, zt, true);
+    for (int i = lane; i < n; i += 32) W.x[i] = mk(W.x[i].re + zt[i], 0.0);
+    __syncwarp();
+    const double sc = rsqrt_safe(tri_norm2(W.x, n));
+    for (int i = lane; i < n; i += 32) W.x[i] = sc * W.x[i];
+    __syncwarp();
+  }
+  __syncthreads();
+}
+
+
 // G: the n x n matrix (row-major, global or shared memory).  Result in W.x
 // (unit norm).  Steps of the exact-operator refinement: `steps_far` when the
 // two smallest eigenvalues are more than refine_gap * lam_max apart,
@@ -1057,21 +1108,36 @@ __device__ TriResult tri_smallest(const TriWs& W, const cd* G, int n, int steps_
       }
     }
   }
+  __shared__ double gt[2];   // block mode: the lead's scale and ||T|| for the other warps
   if (lead) {
     if (single && n > 2 && tri_solve_lead_sp(W, G, n, res, gs, tnorm, tk, pre_sp))
       steps = 0;
     else
       steps = tri_solve_lead<E>(W, G, n, steps_far, steps_near, refine_gap, res, gs, tnorm, tk, pre);
-    if (BLOCK && lane == 0) W.iv[0] = steps;
+    if (BLOCK && lane == 0) {
+      W.iv[0] = steps;
+      gt[0] = gs;
+      gt[1] = tnorm;
+    }
   }
   if (BLOCK) {
     __syncthreads();
     steps = W.iv[0];
+    gs = gt[0];
+    tnorm = gt[1];
   }
+  // real samples on a CTA of three or more warps: the step's chains in parallel
+  const bool par = BLOCK && sizeof(E) == sizeof(double) && blockDim.x >= 96;
   for (int it = 0; it < steps; ++it) {
     apply(W.x, W.r);
     team_sync<BLOCK>();
     if (tk && lead && lane == 0) tk[6] = clock64();   // end of the last step's apply
+    if constexpr (BLOCK && sizeof(E) == sizeof(double)) {
+      if (par) {
+        tri_olsen_real_block(W, n, gs, tnorm);
+        continue;
+      }
+    }
     if (lead) tri_olsen<E>(W, n, gs, tnorm);
     team_sync<BLOCK>();
   }
