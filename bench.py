@@ -183,6 +183,33 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ------------------------------------------------------------ multi-rank ---
+SEED_BASE = 1203000
+
+
+def shard_seed(rank: int, n: int) -> int:
+    """First input seed of a rank: rank r deblurs the pairs seeded
+    SEED_BASE + r n ... SEED_BASE + (r + 1) n - 1, so the ranks' batches are
+    disjoint and each rank's work is fixed as ranks are added (weak scaling)."""
+    return SEED_BASE + rank * n
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    """The largest of the ranks' values (gloo all-reduce); x itself on one rank."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, n: int, steps: int, ms: float) -> float:
+    """Whole-job pairs/s: every rank's n pairs per step over the slowest rank's time."""
+    return world * n * steps / (ms / 1e3)
+
+
 # ----------------------------------------------------------------- inputs ---
 def make_inputs(ctx, n: int, seed0: int, device, t1: int = T1, t2: int = T2):
     """Kernels and blob parameters drawn on the host (cbp_synth), latents and
@@ -470,7 +497,7 @@ def main():
     dev = torch.device("cuda", local)
     ctx = cbp.cbp_create(local, 0)
     n = args.pairs
-    b1, b2, _, _ = make_inputs(ctx, n, 1203000 + rank * n, dev)
+    b1, b2, _, _ = make_inputs(ctx, n, shard_seed(rank, n), dev)
     prm = cbp.params(T1, T2, path="mixed", eps=EPS)
     lat = torch.empty((n, C, H, W), dtype=torch.float32, device=dev)
     k1 = torch.empty((n, T1, T1), dtype=torch.float32, device=dev)
@@ -513,12 +540,8 @@ def main():
     torch.cuda.synchronize()
     cbp.cbp_profile(ctx, False)
     stages = cbp.cbp_stage_times(ctx)
-    elapsed_ms = ev[0].elapsed_time(ev[-1])
-    if world > 1:
-        t = torch.tensor([elapsed_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    value = world * n * args.steps / (elapsed_ms / 1e3)
+    elapsed_ms = max_over_ranks(ev[0].elapsed_time(ev[-1]), world)
+    value = job_rate(world, n, args.steps, elapsed_ms)
     mixed_k1, mixed_k2 = k1.clone(), k2.clone()
 
     # ---- plain FP64 path on the same batch (comparison) ----
@@ -531,7 +554,7 @@ def main():
         step(prm64)
     e1.record(stream)
     torch.cuda.synchronize()
-    fp64_ms = e0.elapsed_time(e1) / max(args.fp64_steps, 1)
+    fp64_ms = max_over_ranks(e0.elapsed_time(e1), world) / max(args.fp64_steps, 1)
     rel = lambda a, b: ((a - b).flatten(1).norm(dim=1) / b.flatten(1).norm(dim=1)).max().item()
     kerr = max(rel(mixed_k1.double(), k1.double()), rel(mixed_k2.double(), k2.double()))
 
@@ -553,12 +576,8 @@ def main():
         step_h()
     e1.record(stream)
     torch.cuda.synchronize()
-    e2e_ms = e0.elapsed_time(e1)
-    if world > 1:
-        t = torch.tensor([e2e_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_ms = float(t.item())
-    e2e_value = world * n * args.e2e_steps / (e2e_ms / 1e3)
+    e2e_ms = max_over_ranks(e0.elapsed_time(e1), world)
+    e2e_value = job_rate(world, n, args.e2e_steps, e2e_ms)
     h2d = n * C * (H1 * W1 + H2 * W2) * 4
     d2h = n * C * H * W * 4 + n * (T1 * T1 + T2 * T2) * 4
 
@@ -597,7 +616,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (eval/Gram/FFT) + f64 (solves)",
         "data": "synthetic (device forward model)", "config": config(n),
         "p50_ms": statistics.median(per_step), "p99_ms": sorted(per_step)[int(0.99 * (len(per_step) - 1))],
-        "plain_fp64": {"value": world * n / (fp64_ms / 1e3), "unit": UNIT, "ms_per_step": fp64_ms},
+        "plain_fp64": {"value": job_rate(world, n, 1, fp64_ms), "unit": UNIT, "ms_per_step": fp64_ms},
         "kernel_rel_err_mixed_vs_fp64": kerr,
         "roofline": roof, "stage_ms_per_step": stage_ms,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
