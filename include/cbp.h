@@ -193,17 +193,21 @@ cbp_status cbp_estimate_kernels_stages(cbp_ctx* ctx, const cbp_frames* b1, const
  * The paper has no counterpart: this serves callers that may not allocate
  * device memory -- code under a memory manager that owns every allocation,
  * real-time paths that must not fail on an allocation, deployments that keep
- * a fixed device footprint.  The workspace is a fixed 8 MiB device array in
+ * a fixed device footprint.  The workspace is a fixed 16 MiB device array in
  * the library (held by every GPU that loads it until the process exits);
  * problems whose estimation workspace (cbp_workspace_size without the
  * deconvolution buffers) exceeds it return CBP_ERR_UNSUPPORTED -- one
- * 1080p RGB pair fits on either path.  Inputs and outputs are as in
- * cbp_estimate_kernels (device buffers; CBP_FLAG_HOST_IO and
- * CBP_FLAG_KERNELS_IN are rejected with CBP_ERR_INVALID_ARG).
- * The first call on a device looks up the array's address with that device
- * current: make it before any stream capture.  Every call shares the array and
- * finds the previous call's data in it; calls that overlap on the GPU race on
- * it, so the caller must order them (one stream, or synchronise). */
+ * 1080p RGB pair with 15x15 and 17x17 kernels fits on either path (7.1 MB
+ * FP64, 9.7 MB mixed), three do not.  Inputs and outputs are as in cbp_estimate_kernels (device buffers;
+ * CBP_FLAG_HOST_IO and CBP_FLAG_KERNELS_IN are rejected with
+ * CBP_ERR_INVALID_ARG; the learned path with CBP_ERR_UNSUPPORTED).
+ * The array's address is looked up with the caller's device current on every
+ * call made outside stream capture and remembered per device and context; a
+ * call made while its stream is capturing uses the remembered address, so
+ * make the first call on a device (and the first after a device reset) before
+ * any stream capture.  Every call shares the array and finds the previous
+ * call's data in it; calls that overlap on the GPU race on it, so the caller
+ * must order them (one stream, or synchronise). */
 cbp_status cbp_estimate_kernels_noalloc(const cbp_frames* b1, const cbp_frames* b2,
                                         const cbp_params* params, void* k1, void* k2,
                                         cbp_diag* diag, void* stream);

@@ -96,3 +96,24 @@ def test_create_fails_cleanly_without_device(built_lib):
     ctx = ctypes.c_void_p()
     assert cbp.lib().cbp_create(ctypes.byref(ctx), 0, 0) == cbp.CBP_ERR_CUDA
     assert cbp.lib().cbp_create(None, 0, 0) == cbp.CBP_ERR_INVALID_ARG
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="an accepted call would launch kernels on "
+                    "the placeholder addresses; the size check is pinned where no GPU is present")
+def test_noalloc_size_check_on_the_1080p_rgb_workload(built_lib):
+    """The allocation-free entry point's fixed 16 MiB array holds one 1080p RGB
+    pair (15x15 and 17x17 kernels) on either path -- the call gets past the size
+    check and fails only for want of a device -- and refuses three pairs."""
+    from paper_1203_4874_gb300 import cbp
+    for path in ("fp64", "mixed"):
+        for n, accepted in ((1, True), (3, False)):
+            b1 = _frames(n, 3, 1094, 1934)
+            b2 = _frames(n, 3, 1096, 1936)
+            prm = cbp.params(15, 17, path=path)
+            s = cbp.lib().cbp_estimate_kernels_noalloc(ctypes.byref(b1), ctypes.byref(b2),
+                                                       ctypes.byref(prm), ctypes.c_void_p(0x2000),
+                                                       ctypes.c_void_p(0x3000), None, None)
+            if accepted:
+                assert s == cbp.CBP_ERR_CUDA, (path, n, s)
+            else:
+                assert s == cbp.CBP_ERR_UNSUPPORTED, (path, n, s)
