@@ -41,11 +41,13 @@ M = max(T1, T2)              # unit-circle samples (the default)
 NS = M // 2 + 1              # samples solved per direction
 
 
-def config(pairs):
+def config(pairs, arm="mixed path (CUDA)"):
     return {"workload": f"{WORKLOAD}: {pairs} pairs/step, 1920x1080x3 f32, kernels 15x15 + 17x17 "
-                        f"(Gaussian+motion mixture), noise sigma 1e-3, mixed path, eps 1e-4",
+                        f"(Gaussian+motion mixture), noise sigma 1e-3, {arm}, eps 1e-4",
             "pairs_per_step": pairs, "fft_grid": [PH, PW],
-            "l2": "inputs 3.0 GB per step > L2; no flush between steps"}
+            "l2": f"inputs {pairs * C * (H1 * W1 + H2 * W2) * 4 / 1e9:.2g} GB per step"
+                  + ("; larger than L2, no flush between steps" if pairs * C * (H1 * W1 + H2 * W2) * 4 > 2e8
+                     else "")}
 
 
 # ----------------------------------------------------------- roofline data --
@@ -211,9 +213,11 @@ def job_rate(world: int, n: int, steps: int, ms: float) -> float:
 
 
 # ----------------------------------------------------------------- inputs ---
-def make_inputs(ctx, n: int, seed0: int, device, t1: int = T1, t2: int = T2):
+def make_inputs(ctx, n: int, seed0: int, device, t1: int = T1, t2: int = T2, keep: int = 0,
+                sigma: float = SIGMA):
     """Kernels and blob parameters drawn on the host (cbp_synth), latents and
-    blurred frames synthesised on the device by the library's forward model."""
+    blurred frames synthesised on the device by the library's forward model.
+    keep > 0: also returns the true latents of the first `keep` pairs (host)."""
     import numpy as np
     import torch
     from cbp_synth.generators import _rng, blob_params, draw_kernel_pair
@@ -230,10 +234,13 @@ def make_inputs(ctx, n: int, seed0: int, device, t1: int = T1, t2: int = T2):
     k2 = torch.from_numpy(np.stack(k2s)).to(device)
     bl = torch.from_numpy(np.stack(blobs)).to(device)
     lat = cbp.cbp_synth_latent(ctx, bl, n, C, H, W, torch.float32, 0.05, seed0)
-    b1 = cbp.cbp_forward_blur(ctx, lat, k1, SIGMA, seed0 * 2 + 1)
-    b2 = cbp.cbp_forward_blur(ctx, lat, k2, SIGMA, seed0 * 2 + 2)
+    b1 = cbp.cbp_forward_blur(ctx, lat, k1, sigma, seed0 * 2 + 1)
+    b2 = cbp.cbp_forward_blur(ctx, lat, k2, sigma, seed0 * 2 + 2)
     torch.cuda.synchronize()
+    truth = lat[:keep].cpu() if keep else None
     del lat
+    if keep:
+        return b1, b2, k1, k2, truth
     return b1, b2, k1, k2
 
 
@@ -371,6 +378,13 @@ def learned_bench(ctx, n: int, device, steps: int = 3) -> dict:
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / steps
         out[path] = {"value": n / dt, "ms_per_step": 1e3 * dt}
+        # per-stage times of one unsplit call (stages one after another)
+        cbp.cbp_stage_times(ctx)
+        cbp.cbp_profile(ctx, True)
+        cbp.cbp_deblur_pair(ctx, b1, b2, prm, k1=k1, k2=k2, latent=lat, diag=False)
+        torch.cuda.synchronize()
+        cbp.cbp_profile(ctx, False)
+        out[path]["stage_ms"] = {k: round(v[0], 4) for k, v in cbp.cbp_stage_times(ctx).items() if v[1] > 0}
         if path == "learned":
             rho = [x.rho for x in d]
             out[path]["accepted"] = sum(1 for x in d if x.used_fallback == 0)
@@ -381,41 +395,140 @@ def learned_bench(ctx, n: int, device, steps: int = 3) -> dict:
 
 
 # ------------------------------------------------------- CPU oracle sample --
-def cpu_worker(pairs: int):
-    """Time the FP64 oracle on `pairs` pairs of the workload (host cores)."""
+def _rel(a, b):
     import numpy as np
-    import scipy.signal
+    return float(np.linalg.norm(np.asarray(a, np.float64) - np.asarray(b, np.float64))
+                 / np.linalg.norm(np.asarray(b, np.float64)))
+
+
+def _psnr(x, ref):
+    import numpy as np
+    x, ref = np.asarray(x, np.float64), np.asarray(ref, np.float64)
+    mse = float(np.mean((x - ref) ** 2))
+    return 10.0 * np.log10(float(np.max(np.abs(ref))) ** 2 / mse) if mse > 0 else float("inf")
+
+
+def cpu_worker(folder: str):
+    """Time the FP64 oracle on the frames the GPU deblurred (saved in `folder`
+    by the parent) and state, per pair, the errors of the GPU results against
+    the oracle's and of both against the truth."""
+    import numpy as np
     import oracle
-    from cbp_synth import make_pair_inputs
 
-    total = 0.0
-    for f in range(pairs):
-        inp = make_pair_inputs(WORKLOAD, f)
-        b1 = np.stack([scipy.signal.fftconvolve(ch, inp.k1) for ch in inp.latent]) + inp.noise1
-        b2 = np.stack([scipy.signal.fftconvolve(ch, inp.k2) for ch in inp.latent]) + inp.noise2
-        b1 = b1.astype(np.float32).astype(np.float64)
-        b2 = b2.astype(np.float32).astype(np.float64)
+    d = Path(folder)
+    b1, b2 = np.load(d / "b1.npy", mmap_mode="r"), np.load(d / "b2.npy", mmap_mode="r")
+    k1t, k2t = np.load(d / "k1_true.npy"), np.load(d / "k2_true.npy")
+    lat_t = np.load(d / "latent_true.npy", mmap_mode="r")
+    gk = {p: (np.load(d / f"k1_{p}.npy"), np.load(d / f"k2_{p}.npy")) for p in ("mixed", "fp64")}
+    gl = {p: np.load(d / f"latent_{p}.npy", mmap_mode="r") for p in ("mixed", "fp64")}
+    total, per = 0.0, []
+    for f in range(b1.shape[0]):
+        x1, x2 = np.asarray(b1[f], np.float64), np.asarray(b2[f], np.float64)
         t0 = time.perf_counter()
-        oracle.deblur_pair(b1, b2, T1, T2, eps=EPS)
+        o = oracle.deblur_pair(x1, x2, T1, T2, eps=EPS)
         total += time.perf_counter() - t0
-    print(json.dumps({"pairs": pairs, "seconds": total}))
+        ok = np.concatenate([o["k1"].ravel(), o["k2"].ravel()])
+        tk = np.concatenate([k1t[f].ravel(), k2t[f].ravel()])
+        rec = {"pair": f, "kernel_vs_oracle": {}, "latent_vs_oracle": {}, "kernel_vs_truth": {},
+               "latent_psnr_vs_truth_db": {}}
+        for p in ("mixed", "fp64"):
+            g = np.concatenate([gk[p][0][f].ravel(), gk[p][1][f].ravel()])
+            rec["kernel_vs_oracle"][p] = _rel(g, ok)
+            rec["latent_vs_oracle"][p] = _rel(gl[p][f], o["latent"])
+            rec["kernel_vs_truth"][p] = _rel(g, tk)
+            rec["latent_psnr_vs_truth_db"][p] = _psnr(gl[p][f], lat_t[f])
+        rec["kernel_vs_truth"]["oracle"] = _rel(ok, tk)
+        rec["latent_psnr_vs_truth_db"]["oracle"] = _psnr(o["latent"], lat_t[f])
+        o1 = T1 // 2   # the blur centre: B1 shifted back by half the kernel
+        rec["latent_psnr_vs_truth_db"]["blurred_b1"] = _psnr(np.asarray(b1[f])[:, o1:o1 + H, o1:o1 + W],
+                                                             lat_t[f])
+        per.append(rec)
+    print(json.dumps({"pairs": int(b1.shape[0]), "seconds": total, "per_pair": per}))
 
 
-def cpu_baseline(pairs: int):
+def accuracy_sample(ctx, b1, b2, k1t, k2t, truth, k: int, folder: Path):
+    """Deblur the first k pairs of the batch on both paths with double-precision
+    kernel outputs and save them, the frames and the truth for the oracle leg."""
+    import numpy as np
+    import torch
+    from paper_1203_4874_gb300 import cbp
+
+    np.save(folder / "b1.npy", b1[:k].cpu().numpy())
+    np.save(folder / "b2.npy", b2[:k].cpu().numpy())
+    np.save(folder / "k1_true.npy", k1t[:k].cpu().numpy())
+    np.save(folder / "k2_true.npy", k2t[:k].cpu().numpy())
+    np.save(folder / "latent_true.npy", truth[:k].numpy())
+    for path in ("mixed", "fp64"):
+        prm = cbp.params(T1, T2, path=path, eps=EPS, flags=cbp.CBP_FLAG_KERNELS_F64)
+        lat, g1, g2, _, _ = cbp.cbp_deblur_pair(ctx, b1[:k].contiguous(), b2[:k].contiguous(), prm)
+        torch.cuda.synchronize()
+        np.save(folder / f"k1_{path}.npy", g1.cpu().numpy())
+        np.save(folder / f"k2_{path}.npy", g2.cpu().numpy())
+        np.save(folder / f"latent_{path}.npy", lat.cpu().numpy())
+        del lat
+
+
+def cpu_baseline(folder: Path):
+    """The oracle on the host cores (BLAS threads = core count) in a fresh
+    process, on the pairs saved in `folder`: (cpu_baseline record, accuracy)."""
     cores = os.cpu_count() or 1
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = str(cores)
-    r = subprocess.run([sys.executable, str(Path(__file__).resolve()), "--cpu-worker", str(pairs)],
+    r = subprocess.run([sys.executable, str(Path(__file__).resolve()), "--cpu-worker", str(folder)],
                        capture_output=True, text=True, env=env, timeout=1800)
     line = [l for l in r.stdout.splitlines() if l.startswith("{")]
     if r.returncode != 0 or not line:
-        return {"value": None, "unit": UNIT, "cores": cores, "kind": "oracle",
-                "sample": "failed: " + (r.stderr.strip().splitlines() or ["?"])[-1]}
+        return ({"value": None, "unit": UNIT, "cores": cores, "kind": "oracle",
+                 "sample": "failed: " + (r.stderr.strip().splitlines() or ["?"])[-1]}, None)
     d = json.loads(line[-1])
-    return {"value": d["pairs"] / d["seconds"], "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": f"{d['pairs']} pairs (frames 0..{d['pairs'] - 1}) of {WORKLOAD}, FP64 numpy "
-                      f"oracle, estimation + deconvolution, BLAS threads = {cores}"}
+    base = {"value": d["pairs"] / d["seconds"], "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"the first {d['pairs']} pairs of the GPU's own batch (device-synthesised "
+                      f"{WORKLOAD} frames copied to the host), FP64 numpy oracle, estimation + "
+                      f"deconvolution, BLAS threads = {cores}"}
+    per = d["per_pair"]
+    worst = lambda key, p: max(x[key][p] for x in per)
+    acc = {
+        "pairs": [x["pair"] for x in per],
+        "kernel_rel_err_vs_oracle": {p: worst("kernel_vs_oracle", p) for p in ("mixed", "fp64")},
+        "latent_rel_err_vs_oracle": {p: worst("latent_vs_oracle", p) for p in ("mixed", "fp64")},
+        "kernel_rel_err_vs_truth": {p: worst("kernel_vs_truth", p) for p in ("mixed", "fp64", "oracle")},
+        "bars": {"kernel_vs_oracle": {"mixed": 1e-3, "fp64": 1e-9}, "latent_vs_oracle": 1e-4},
+        "per_pair": per,
+        "note": "max over the sampled pairs; kernels relative L2 over both kernels, latents relative "
+                "L2 over all channels; PSNR against the true latent (peak = its max)",
+    }
+    return base, acc
+
+
+def noise_sweep(ctx, device, sigmas=(0.0, 1e-5, 1e-4, 1e-3), pairs: int = 4) -> dict:
+    """Kernel error against the truth of the mixed path at 1080p RGB as the
+    noise level grows: where the method's output means something."""
+    import torch
+    from paper_1203_4874_gb300 import cbp
+
+    out = []
+    for sg in sigmas:
+        b1, b2, k1t, k2t = make_inputs(ctx, pairs, 1203000, device, sigma=sg)
+        prm = cbp.params(T1, T2, path="mixed", eps=EPS, flags=cbp.CBP_FLAG_KERNELS_F64)
+        k1, k2, d, _ = cbp.cbp_estimate_kernels(ctx, b1, b2, prm)
+        torch.cuda.synchronize()
+        g = torch.cat([k1.flatten(1), k2.flatten(1)], 1)
+        t = torch.cat([k1t.flatten(1), k2t.flatten(1)], 1)
+        e = ((g - t).norm(dim=1) / t.norm(dim=1)).cpu().tolist()
+        out.append({"sigma": sg, "kernel_rel_err_vs_truth": e,
+                    "gap_min": [x.gap_min for x in d]})
+        del b1, b2
+    return {"workload": f"first {pairs} pairs of {WORKLOAD} (seeds 1203000..), mixed path, eps 1e-4",
+            "points": out}
+
+
+def percentile(xs, q):
+    """The q-th percentile of xs, linear interpolation between order statistics
+    (numpy's default); with fewer than 100 samples p99 lies between the two
+    largest."""
+    import numpy as np
+    return float(np.percentile(np.asarray(xs, dtype=np.float64), q))
 
 
 def reference_arm(args):
@@ -450,8 +563,8 @@ def reference_arm(args):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": config(1),
-        "p50_ms": 1e3 * statistics.median(times), "p99_ms": 1e3 * max(times),
+        "data": "synthetic", "config": config(1, "FP64 numpy oracle on the host cores"),
+        "p50_ms": 1e3 * statistics.median(times), "p99_ms": 1e3 * percentile(times, 99),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": f"1 pair per step of {WORKLOAD}, FP64 numpy oracle"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -466,14 +579,17 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="cbp", choices=["cbp", "reference"])
     ap.add_argument("--pairs", type=int, default=60)
-    ap.add_argument("--cpu-pairs", type=int, default=6)
+    ap.add_argument("--cpu-pairs", type=int, default=12,
+                    help="pairs of the GPU's batch the oracle deblurs on the host (timed, and "
+                         "the errors of the GPU results against it)")
+    ap.add_argument("--no-noise-sweep", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-path measurement")
     ap.add_argument("--serve-seconds", type=float, default=6.0,
                     help="seconds of the camera serving trace (0: skip)")
-    ap.add_argument("--cpu-worker", type=int, default=0)
+    ap.add_argument("--cpu-worker", default="")
     args = ap.parse_args()
     if args.cpu_worker:
         cpu_worker(args.cpu_worker)
@@ -497,7 +613,10 @@ def main():
     dev = torch.device("cuda", local)
     ctx = cbp.cbp_create(local, 0)
     n = args.pairs
-    b1, b2, _, _ = make_inputs(ctx, n, shard_seed(rank, n), dev)
+    keep = min(args.cpu_pairs, n) if (rank == 0 and world == 1 and not args.no_cpu_baseline) else 0
+    inputs = make_inputs(ctx, n, shard_seed(rank, n), dev, keep=keep)
+    b1, b2, k1_true, k2_true = inputs[:4]
+    truth = inputs[4] if keep else None
     prm = cbp.params(T1, T2, path="mixed", eps=EPS)
     lat = torch.empty((n, C, H, W), dtype=torch.float32, device=dev)
     k1 = torch.empty((n, T1, T1), dtype=torch.float32, device=dev)
@@ -615,7 +734,7 @@ def main():
         "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32 (eval/Gram/FFT) + f64 (solves)",
         "data": "synthetic (device forward model)", "config": config(n),
-        "p50_ms": statistics.median(per_step), "p99_ms": sorted(per_step)[int(0.99 * (len(per_step) - 1))],
+        "p50_ms": statistics.median(per_step), "p99_ms": percentile(per_step, 99),
         "plain_fp64": {"value": job_rate(world, n, 1, fp64_ms), "unit": UNIT, "ms_per_step": fp64_ms},
         "kernel_rel_err_mixed_vs_fp64": kerr,
         "roofline": roof, "stage_ms_per_step": stage_ms,
@@ -626,8 +745,19 @@ def main():
         result["learned"] = learned_bench(ctx, n, dev)
     if rank == 0 and args.serve_seconds > 0:
         result["serving"] = serving_bench(args.serve_seconds, dev)
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(args.cpu_pairs)
+    if rank == 0 and not args.no_noise_sweep:
+        result["noise_sweep"] = noise_sweep(ctx, dev)
+    if keep:
+        folder = Path(tempfile.mkdtemp(prefix="cbp_bench_"))
+        try:
+            accuracy_sample(ctx, b1, b2, k1_true, k2_true, truth, keep, folder)
+            result["cpu_baseline"], acc = cpu_baseline(folder)
+            if acc is not None:
+                result["accuracy"] = acc
+        finally:
+            for f in folder.glob("*.npy"):
+                f.unlink()
+            folder.rmdir()
     cbp.cbp_destroy(ctx)
     if rank == 0:
         print(json.dumps(result), flush=True)

@@ -61,7 +61,47 @@ def _stage_check(ctx, b1, b2, cfg, path, p_tol, x_tol):
     sv = np.stack([o["sv_z2"][:ns], o["sv_z1"][:ns]])
     assert np.allclose(sd[..., 0], sv[..., 0] ** 2, rtol=1e-5)           # lambda_max
     assert np.allclose(sd[..., 1], sv[..., -2] ** 2, rtol=1e-3)          # second smallest
+    _lifted_check(out["lifted"][0].cpu().numpy(), o, x_tol)
+    _diag_check(out["diag"][0], o, 1e-6 if path == "fp64" else 1e-4)
     return out, o
+
+
+def _phase_free(g, o):
+    """1 - |<g, o>| / (|g| |o|) and the norm ratio |g| / |o|."""
+    ng, no = np.linalg.norm(g), np.linalg.norm(o)
+    return 1 - abs(np.vdot(g, o)) / (ng * no), ng / no
+
+
+def _lifted_check(lifted, o, tol):
+    """A4's lifted spectra against the oracle's a_hat / b_hat.  Each column j of
+    A_k (z2-first order) comes from sample j's cofactor vector, each row i of
+    B_k (z1-first) from sample i's; a vector's phase is arbitrary, its norm
+    (unit cofactors) is not: both kernels' column (row) stacked, compared
+    phase-free, with equal norms."""
+    a, b = lifted[:2], lifted[2:]
+    m = a.shape[1]
+    for j in range(m):
+        d, r = _phase_free(a[:, :, j].ravel(), o["a_hat"][:, :, j].ravel())
+        assert d <= tol and abs(r - 1) <= 1e-6, ("A", j, d, r)
+    for i in range(m):
+        d, r = _phase_free(b[:, i, :].ravel(), o["b_hat"][:, i, :].ravel())
+        assert d <= tol and abs(r - 1) <= 1e-6, ("B", i, d, r)
+
+
+def _diag_check(dg, o, rtol):
+    """Diagnostics against the oracle's: the worst per-sample conditioning
+    1 / (sigma_{n-1} / sigma_1) (the device solves samples j <= M/2, the oracle
+    all M; conjugate samples share singular values) and the scale system's
+    sigma_min / sigma_max, both invariant to the cofactors' phases.  The scale
+    residual's bound: rounding of the 2M-square normal matrix (~1e-16 of its
+    largest eigenvalue) enters sigma_min^2; on the mixed path the cofactors
+    themselves differ from the oracle's by up to ~1e-8, so rtol is wider."""
+    od = o["diag"]
+    assert abs(dg.kappa_max - od["kappa"]) <= 1e-3 * od["kappa"], (dg.kappa_max, od["kappa"])
+    assert abs(dg.gap_min - od["gap_min"]) <= 1e-3 * od["gap_min"], (dg.gap_min, od["gap_min"])
+    assert dg.flagged_samples == 0 or od["flagged_samples"] > 0
+    sr, osr = dg.scale_resid, od["scale_resid"]
+    assert abs(sr * sr - osr * osr) <= 1e-12 + rtol * osr * osr, (sr, osr)
 
 
 def test_stages_match_oracle_fp64(gpu_ctx):
@@ -103,6 +143,8 @@ def test_full_batch_1080p_as_benchmarked(gpu_ctx):
             g = L[f].double().cpu().numpy()
             o = refs[idx[f]]["latent"]
             assert abs(psnr(g, lat[idx[f]]) - psnr(o, lat[idx[f]])) <= 0.05, (path, f)
+            for ch in range(3):
+                assert rel(g[ch], o[ch]) <= 1e-4, (path, f, ch, rel(g[ch], o[ch]))
         del L
 
 
@@ -148,6 +190,8 @@ def test_rgb_1080p_mixed_and_fp64(gpu_ctx):
     g_lat, g_k1, g_k2, diag = run_gpu(gpu_ctx, b1, b2, 15, 17, "mixed", cfg.eps, "f32")
     assert rel(g_k1[0], o["k1"]) <= 1e-3 and rel(g_k2[0], o["k2"]) <= 1e-3
     assert abs(psnr(g_lat[0], lat[0]) - psnr(o["latent"], lat[0])) <= 0.05
+    for ch in range(3):
+        assert rel(g_lat[0][ch], o["latent"][ch]) <= 1e-4, ch
     f_lat, f_k1, f_k2, _ = run_gpu(gpu_ctx, b1, b2, 15, 17, "fp64", cfg.eps, "f32")
     assert rel(f_k1[0], o["k1"]) <= 1e-9 and rel(f_k2[0], o["k2"]) <= 1e-9
     assert rel(f_lat[0], o["latent"]) <= 1e-4
