@@ -211,9 +211,11 @@ cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
     end(CBP_STAGE_SCALE_SOLVE, 1);
   }
   if (deblur) {
-    begin(CBP_STAGE_KERNEL_SPECTRA);
-    launch_kernel_spectra(p, wsp, st);
-    end(CBP_STAGE_KERNEL_SPECTRA, 1);
+    if (!p.col_fused) {
+      begin(CBP_STAGE_KERNEL_SPECTRA);
+      launch_kernel_spectra(p, wsp, st);
+      end(CBP_STAGE_KERNEL_SPECTRA, 1);
+    }
     begin(CBP_STAGE_COL_DECONV);
     launch_col_deconv(p, wsp, st);
     end(CBP_STAGE_COL_DECONV, 1);

@@ -16,6 +16,7 @@
 //   3. inverse rows: complex-to-real inverse FFT, crop to W, scale 1/(Ph Pw).
 // Zero padding is implicit: rows >= H_Bk and columns >= W_Bk are never read.
 #include "cbp_common.cuh"
+#include "cbp_dft.cuh"
 #include "cbp_internal.h"
 #ifdef CBP_PHASE_TIMING
 #include <cstdio>
@@ -25,137 +26,6 @@ namespace cbp {
 namespace {
 
 constexpr int kFftThreads = 256;
-
-// ------------------------------------------------------------- FFT core ---
-// In-register DFTs of size R (Inv: e^{+i...}, unnormalised), float constants
-// for float data.  Radix 8 = 2 x 4 and radix 9 = 3 x 3 with internal twiddles.
-template <typename T, bool Inv>
-__device__ __forceinline__ cpx<T> mul_i(cpx<T> d) {     // (Inv ? +i : -i) * d
-  return Inv ? mk<T>(-d.im, d.re) : mk<T>(d.im, -d.re);
-}
-
-template <typename T, bool Inv>
-__device__ __forceinline__ void dft2(cpx<T>& a, cpx<T>& b) {
-  const cpx<T> t = a - b;
-  a = a + b;
-  b = t;
-}
-
-template <typename T, bool Inv>
-__device__ __forceinline__ void dft3(cpx<T>& a, cpx<T>& b, cpx<T>& c) {
-  const T h = (T)0.86602540378443864676;       // sin(2 pi / 3)
-  const cpx<T> sm = b + c, d = b - c;
-  const cpx<T> t1 = a - (T)0.5 * sm;
-  const cpx<T> t2 = h * mul_i<T, Inv>(d);
-  a = a + sm;
-  b = t1 + t2;
-  c = t1 - t2;
-}
-
-template <typename T, bool Inv>
-__device__ __forceinline__ void dft4(cpx<T>& v0, cpx<T>& v1, cpx<T>& v2, cpx<T>& v3) {
-  const cpx<T> t0 = v0 + v2, t1 = v0 - v2, t2 = v1 + v3;
-  const cpx<T> t3 = mul_i<T, Inv>(v1 - v3);
-  v0 = t0 + t2;
-  v2 = t0 - t2;
-  v1 = t1 + t3;
-  v3 = t1 - t3;
-}
-
-// odd prime radix by symmetric pairs; C, S = cos, sin(2 pi j / R)
-template <typename T, bool Inv, int R>
-__device__ __forceinline__ void dft_odd(cpx<T>* v, const T* C, const T* S) {
-  constexpr int H = (R - 1) / 2;
-  cpx<T> a[H], b[H];
-#pragma unroll
-  for (int m = 1; m <= H; ++m) {
-    a[m - 1] = v[m] + v[R - m];
-    b[m - 1] = v[m] - v[R - m];
-  }
-  const cpx<T> x0 = v[0];
-  cpx<T> s0 = x0;
-#pragma unroll
-  for (int m = 0; m < H; ++m) s0 = s0 + a[m];
-  v[0] = s0;
-#pragma unroll
-  for (int k = 1; k <= H; ++k) {
-    cpx<T> re = x0, im = mk<T>(0, 0);
-#pragma unroll
-    for (int m = 1; m <= H; ++m) {
-      const int j = (k * m) % R;
-      re = re + C[j] * a[m - 1];
-      im = im + S[j] * b[m - 1];
-    }
-    const cpx<T> si = mul_i<T, Inv>(im);   // forward: X[k] = re - i im, X[R-k] = re + i im
-    v[k] = re + si;
-    v[R - k] = re - si;
-  }
-}
-
-template <typename T, bool Inv, int R>
-__device__ __forceinline__ void small_dft(cpx<T>* v) {
-  if constexpr (R == 2) {
-    dft2<T, Inv>(v[0], v[1]);
-  } else if constexpr (R == 3) {
-    dft3<T, Inv>(v[0], v[1], v[2]);
-  } else if constexpr (R == 4) {
-    dft4<T, Inv>(v[0], v[1], v[2], v[3]);
-  } else if constexpr (R == 5) {
-    const T C[5] = {(T)1, (T)0.30901699437494742410, (T)-0.80901699437494742410,
-                    (T)-0.80901699437494742410, (T)0.30901699437494742410};
-    const T S[5] = {(T)0, (T)0.95105651629515357212, (T)0.58778525229247312917,
-                    (T)-0.58778525229247312917, (T)-0.95105651629515357212};
-    dft_odd<T, Inv, 5>(v, C, S);
-  } else if constexpr (R == 7) {
-    const T C[7] = {(T)1, (T)0.62348980185873353053, (T)-0.22252093395631440429,
-                    (T)-0.90096886790241912624, (T)-0.90096886790241912624,
-                    (T)-0.22252093395631440429, (T)0.62348980185873353053};
-    const T S[7] = {(T)0, (T)0.78183148246802980871, (T)0.97492791218182360702,
-                    (T)0.43388373911755812048, (T)-0.43388373911755812048,
-                    (T)-0.97492791218182360702, (T)-0.78183148246802980871};
-    dft_odd<T, Inv, 7>(v, C, S);
-  } else if constexpr (R == 8) {
-    // even / odd halves by radix 4, combined with w8^k
-    dft4<T, Inv>(v[0], v[2], v[4], v[6]);
-    dft4<T, Inv>(v[1], v[3], v[5], v[7]);
-    const T r = (T)0.70710678118654752440;
-    const cpx<T> o1 = r * (v[3] + mul_i<T, Inv>(v[3]));     // w8^1 = r (1 -/+ i)
-    const cpx<T> o2 = mul_i<T, Inv>(v[5]);                   // w8^2 = -/+ i
-    const cpx<T> o3 = r * (mul_i<T, Inv>(v[7]) - v[7]);     // w8^3 = r (-1 -/+ i)
-    const cpx<T> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
-    v[0] = e0 + v[1];
-    v[4] = e0 - v[1];
-    v[1] = e1 + o1;
-    v[5] = e1 - o1;
-    v[2] = e2 + o2;
-    v[6] = e2 - o2;
-    v[3] = e3 + o3;
-    v[7] = e3 - o3;
-  } else {  // R == 9: 3 x 3
-    dft3<T, Inv>(v[0], v[3], v[6]);
-    dft3<T, Inv>(v[1], v[4], v[7]);
-    dft3<T, Inv>(v[2], v[5], v[8]);
-    // twiddles w9^{n2 k1}: (n2, k1) = (1,1) (1,2) (2,1) (2,2) -> w9^1, w9^2, w9^2, w9^4
-    const T c1 = (T)0.76604444311897803520, s1 = (T)0.64278760968653932632;   // 2 pi / 9
-    const T c2 = (T)0.17364817766693034885, s2 = (T)0.98480775301220805936;   // 4 pi / 9
-    const T c4 = (T)-0.93969262078590838405, s4 = (T)0.34202014332566873304;  // 8 pi / 9
-    const T sg = Inv ? (T)1 : (T)-1;
-    v[4] = v[4] * mk<T>(c1, sg * s1);
-    v[7] = v[7] * mk<T>(c2, sg * s2);
-    v[5] = v[5] * mk<T>(c2, sg * s2);
-    v[8] = v[8] * mk<T>(c4, sg * s4);
-    // v[n2 + 3 k1] holds Y_{n2}[k1]; DFT3 over n2 for each k1 -> X[k1 + 3 k2]
-    cpx<T> a0 = v[0], a1 = v[1], a2 = v[2];
-    dft3<T, Inv>(a0, a1, a2);
-    cpx<T> b0 = v[3], b1 = v[4], b2 = v[5];
-    dft3<T, Inv>(b0, b1, b2);
-    cpx<T> d0 = v[6], d1 = v[7], d2 = v[8];
-    dft3<T, Inv>(d0, d1, d2);
-    v[0] = a0; v[3] = a1; v[6] = a2;
-    v[1] = b0; v[4] = b1; v[7] = b2;
-    v[2] = d0; v[5] = d1; v[8] = d2;
-  }
-}
 
 // One Stockham stage of radix R over nb transforms of length N (stride N),
 // in -> out; tw = this stage's twiddles (shared memory).
@@ -1561,7 +1431,8 @@ size_t row_pass_min_smem(const Plan& p) {
 }
 
 void launch_col_deconv(const Plan& p, char* ws, cudaStream_t st) {
-  if (p.fft_f64) run_col_deconv<double, false>(p, ws, st);
+  if (p.col_fused) launch_col_deconv_fused(p, ws, st);
+  else if (p.fft_f64) run_col_deconv<double, false>(p, ws, st);
   else run_col_deconv<float, false>(p, ws, st);
 }
 

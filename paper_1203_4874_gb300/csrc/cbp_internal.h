@@ -67,6 +67,7 @@ struct Plan {
   int pw_half;                 // Pw even: real row FFTs via half-length complex FFTs
   int learned;                 // learned path: proposal + consistency gate first
   int col_strips;              // column strips of the column pass
+  int col_fused;               // column pass computes the kernel spectra itself (no K^ buffer)
   double accept_rho;
   double eps;
   FftPlan fp_h, fp_w, fp_w2;   // plans of Ph, Pw, Pw/2
@@ -85,7 +86,7 @@ struct Plan {
   size_t off_diag;                 // cbp_diag [n]
   size_t off_tw_h, off_tw_w;       // cpx<T_fft> twiddles exp(-2 pi i k / P), k < P
   size_t off_stw_h, off_stw_r;     // cpx<T_fft> stage twiddles of the column and row plans
-  size_t off_khat;                 // cpx<T_fft> [n][2][Ph][Pw2p]
+  size_t off_khat;                 // cpx<T_fft> [n][2][Ph][Pw2p] (learned gate, unfused column pass)
   size_t off_spec[2];              // cpx<T_fft> [n][C][H_Bk][Pw2p]
   size_t off_ihat;                 // cpx<T_fft> [n][C][H][Pw2p]
   size_t off_io_b[2], off_io_k[2], off_io_lat; // device staging for host I/O
@@ -129,6 +130,9 @@ void launch_row_pass(const Plan& p, const FrameDesc& b1, const FrameDesc& b2, ch
 // shared memory of the row pass at one row per group (the planner's limit check)
 size_t row_pass_min_smem(const Plan& p);
 void launch_col_deconv(const Plan& p, char* ws, cudaStream_t st);
+// the fused column pass (cbp_colpass.cu): kernel spectra computed in the pass
+bool col_pass_fused(const Plan& p);
+void launch_col_deconv_fused(const Plan& p, char* ws, cudaStream_t st);
 void launch_row_ifft(const Plan& p, char* ws, void* latent, int out_f64, cudaStream_t st,
                      const uint64_t* lat_tab = nullptr);
 // learned path: consistency residual of the kernels in kd (column pass in

@@ -190,7 +190,8 @@ cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_param
   p.off_tw_w = take(p.Pw * ce);
   p.off_stw_h = take((size_t)p.fp_h.ntw * ce);
   p.off_stw_r = take((size_t)(p.pw_half ? p.fp_w2.ntw : p.fp_w.ntw) * ce);
-  p.off_khat = take(n * 2 * (size_t)p.Ph * p.Pw2p * ce);
+  p.col_fused = col_pass_fused(p) ? 1 : 0;
+  if (!p.col_fused || p.learned) p.off_khat = take(n * 2 * (size_t)p.Ph * p.Pw2p * ce);
   p.off_spec[0] = take(n * C * (size_t)p.H1 * p.Pw2p * ce);
   p.off_spec[1] = take(n * C * (size_t)p.H2 * p.Pw2p * ce);
   p.off_ihat = take(n * C * (size_t)p.H * p.Pw2p * ce);
