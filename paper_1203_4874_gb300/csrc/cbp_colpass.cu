@@ -12,8 +12,9 @@
 // The transforms are the two-factor (Cooley-Tukey) split of a length-N1 N2
 // DFT, with n = n1 + N1 n2 and u = k2 + N2 k1:
 //   X[k2 + N2 k1] = sum_n1 w_N1^(n1 k1) w_Ph^(n1 k2) sum_n2 x[n1 + N1 n2] w_N2^(n2 k2).
-// Step 1: one task per (n1, column) loads its N2 rows from HBM, transforms
-// them in registers, applies the twiddles and leaves them in shared memory.
+// Both frames' strips are staged in shared memory (cp.async) first.
+// Step 1: one task per (n1, column) takes its N2 rows, transforms them in
+// registers, applies the twiddles and puts them back in place.
 // Step 2: one task per (k2, column) reads its N1 values, transforms them in
 // registers, and holds the N1 output rows u = k2 + N2 k1 of that column: both
 // frames' spectra, both kernels' spectra (an N1-point DFT of the t_k nonzero
@@ -29,6 +30,9 @@ namespace cbp {
 namespace {
 
 constexpr int kFcThreads = 160;
+#ifndef CBP_FC_MIN_BLOCKS
+#define CBP_FC_MIN_BLOCKS 3   // resident blocks per SM the register budget is set for
+#endif
 constexpr int kFcCols = 4;          // spectrum columns per strip (one 32-byte sector per row)
 constexpr int kFcMaxT = 32;         // kernel rows the row-transform table holds
 
@@ -42,26 +46,51 @@ struct FusedColArgs {
   float eps;
 };
 
-// Shared memory: two frames' buffers of N2 slot rows of (N1 + 1) slots (the
-// pad spreads step 2's strided reads over the banks), kFcCols columns per
-// slot, and the kernels' row transforms.
+// Shared memory: both frames' column strips (Ph rows of kFcCols columns; row /
+// slot s at physical row fc_phys(s)) and the kernels' row transforms.
 template <int N1, int N2>
 struct FcSmem {
-  static constexpr int kPitch = N1 + 1;
-  static constexpr int kSlots = kPitch * N2;
-  static constexpr size_t kBuf = (size_t)kSlots * kFcCols;          // cf per frame buffer
+  static constexpr size_t kBuf = (size_t)N1 * N2 * kFcCols;          // cf per frame buffer
   static constexpr size_t kBytes = (2 * kBuf + 2 * (size_t)kFcMaxT * kFcCols) * sizeof(cf);
 };
+
+// Logical slot s = j + N1 m (the strip's row index; step 1's task j = n1
+// holds slots j + N1 m, step 2's task m = k2 holds slots j + N1 k2) lives at
+// physical row s ^ (m & 3): step 2's lanes, eight values of m apart by N1
+// rows, then fall on four different groups of eight banks (two wavefronts per
+// 8-byte access, the minimum), and consecutive slots stay in one 4-row group.
+template <int N1>
+__device__ __forceinline__ int fc_phys(int s) {
+  return s ^ ((s / N1) & 3);
+}
 
 __device__ __forceinline__ cf ldg_cf(const cf* p) {
   const float2 v = __ldg((const float2*)p);
   return mk(v.x, v.y);
 }
 
+__device__ __forceinline__ void fc_cp_async16(void* smem_dst, const void* gsrc, int src_bytes) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(gsrc), "r"(src_bytes)
+               : "memory");
+}
+
+// Stage the strip's rows of one row spectrum (rows >= Hk and columns >= the
+// strip's valid count zero-filled) into buf at the swizzled rows.
 template <int N1, int N2>
-__global__ void __launch_bounds__(kFcThreads, 3) k_col_deconv_fused(FusedColArgs a) {
+__device__ __forceinline__ void fc_stage(cf* buf, const cf* src, int Hk, int Pw2p, int nv) {
+  constexpr int Ph = N1 * N2;
+  for (int e = threadIdx.x; e < Ph * 2; e += kFcThreads) {
+    const int row = e >> 1, half = e & 1;
+    const int valid = row < Hk ? max(0, min(2, nv - 2 * half)) * (int)sizeof(cf) : 0;
+    const cf* g = valid ? src + (int64_t)row * Pw2p + 2 * half : src;
+    fc_cp_async16(buf + fc_phys<N1>(row) * kFcCols + 2 * half, g, valid);
+  }
+}
+
+template <int N1, int N2>
+__global__ void __launch_bounds__(kFcThreads, CBP_FC_MIN_BLOCKS) k_col_deconv_fused(FusedColArgs a) {
   using L = FcSmem<N1, N2>;
-  constexpr int P = L::kPitch;
   constexpr int Ph = N1 * N2;
   extern __shared__ __align__(16) char smem[];
   cf* buf0 = (cf*)smem;
@@ -69,7 +98,13 @@ __global__ void __launch_bounds__(kFcThreads, 3) k_col_deconv_fused(FusedColArgs
   cf* rt = buf1 + L::kBuf;                 // [2][kFcMaxT][kFcCols] kernel row transforms
   const int fc = blockIdx.y, f = fc / a.C;
   const int v0 = blockIdx.x * kFcCols;
+  const int nv = min(kFcCols, a.Pw2 - v0);
   const int tid = threadIdx.x;
+
+  // both frames' strips in flight while the kernels' row transforms are made
+  fc_stage<N1, N2>(buf0, a.spec[0] + ((int64_t)fc * a.H1) * a.Pw2p + v0, a.H1, a.Pw2p, nv);
+  fc_stage<N1, N2>(buf1, a.spec[1] + ((int64_t)fc * a.H2) * a.Pw2p + v0, a.H2, a.Pw2p, nv);
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
 
   // kernel row transforms R_k,p(v) for the strip's columns (zero past Pw2)
   const double* K1 = a.kd + (int64_t)f * (a.t1 * a.t1 + a.t2 * a.t2);
@@ -88,27 +123,23 @@ __global__ void __launch_bounds__(kFcThreads, 3) k_col_deconv_fused(FusedColArgs
     }
     rt[e] = acc;
   }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
 
-  // ---- step 1: N2-point DFTs down the columns, twiddled, into shared memory
+  // ---- step 1: N2-point DFTs down the columns, twiddled, in place
   for (int task = tid; task < 2 * N1 * kFcCols; task += kFcThreads) {
     const int fr = task / (N1 * kFcCols), r = task % (N1 * kFcCols);
     const int n1 = r / kFcCols, col = r % kFcCols;
-    const int Hk = fr ? a.H2 : a.H1;
-    const bool cv = v0 + col < a.Pw2;
-    const cf* src = a.spec[fr] + ((int64_t)fc * Hk) * a.Pw2p + v0 + col;
+    cf* b = (fr ? buf1 : buf0) + col;
     cf x[N2];
 #pragma unroll
-    for (int n2 = 0; n2 < N2; ++n2) {
-      const int row = n1 + N1 * n2;
-      x[n2] = (cv && row < Hk) ? ldg_cf(src + (int64_t)row * a.Pw2p) : mk(0.f, 0.f);
-    }
+    for (int n2 = 0; n2 < N2; ++n2) x[n2] = b[fc_phys<N1>(n1 + N1 * n2) * kFcCols];
     reg_dft<false, N2>(x);
-    cf* dst = (fr ? buf1 : buf0) + n1 * kFcCols + col;
 #pragma unroll
     for (int k2 = 0; k2 < N2; ++k2) {
       cf y = x[reg_pos<N2>(k2)];
       if (k2) y = y * ldg_cf(a.tw_h + n1 * k2);      // w_Ph^(n1 k2), n1 k2 < Ph
-      dst[k2 * P * kFcCols] = y;
+      b[fc_phys<N1>(n1 + N1 * k2) * kFcCols] = y;
     }
   }
   __syncthreads();
@@ -116,24 +147,25 @@ __global__ void __launch_bounds__(kFcThreads, 3) k_col_deconv_fused(FusedColArgs
   // ---- step 2: N1-point DFTs across, the formula, the inverse N1-point DFTs
   if (tid < N2 * kFcCols) {
     const int k2 = tid / kFcCols, col = tid % kFcCols;
-    cf* s0 = buf0 + (k2 * P) * kFcCols + col;      // slot (j, k2) at s[j * kFcCols]
-    cf* s1 = buf1 + (k2 * P) * kFcCols + col;
+    cf* s0 = buf0 + col;
+    cf* s1 = buf1 + col;
+    auto at = [&](int j) { return fc_phys<N1>(j + N1 * k2) * kFcCols; };
     // both frames' column spectra at rows u = k2 + N2 k1, back into their slots
     {
       cf x[N1];
 #pragma unroll
-      for (int j = 0; j < N1; ++j) x[j] = s1[j * kFcCols];
+      for (int j = 0; j < N1; ++j) x[j] = s1[at(j)];
       reg_dft<false, N1>(x);
 #pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) s1[k1 * kFcCols] = x[reg_pos<N1>(k1)];
+      for (int k1 = 0; k1 < N1; ++k1) s1[at(k1)] = x[reg_pos<N1>(k1)];
     }
     {
       cf x[N1];
 #pragma unroll
-      for (int j = 0; j < N1; ++j) x[j] = s0[j * kFcCols];
+      for (int j = 0; j < N1; ++j) x[j] = s0[at(j)];
       reg_dft<false, N1>(x);
 #pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) s0[k1 * kFcCols] = x[reg_pos<N1>(k1)];
+      for (int k1 = 0; k1 < N1; ++k1) s0[at(k1)] = x[reg_pos<N1>(k1)];
     }
     // kernel spectra at the same rows: K^(k2 + N2 k1) = DFT_N1 over p of R_p w_Ph^(p k2)
     const cf* r1 = rt + col;
@@ -150,7 +182,7 @@ __global__ void __launch_bounds__(kFcThreads, 3) k_col_deconv_fused(FusedColArgs
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) {
         const cf k = kh[reg_pos<N1>(k1)];
-        s0[k1 * kFcCols] = cmulc(k, s0[k1 * kFcCols]);    // conj(K^1) B^1
+        s0[at(k1)] = cmulc(k, s0[at(k1)]);       // conj(K^1) B^1
         d1[k1] = abs2(k);
       }
     }
@@ -167,7 +199,7 @@ __global__ void __launch_bounds__(kFcThreads, 3) k_col_deconv_fused(FusedColArgs
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) {
         const cf k = kh[reg_pos<N1>(k1)];
-        const cf num = s0[k1 * kFcCols] + cmulc(k, s1[k1 * kFcCols]);
+        const cf num = s0[at(k1)] + cmulc(k, s1[at(k1)]);
         const float den = d1[k1] + abs2(k) + eps;
         iv[k1] = (den != 0.f ? __frcp_rn(den) : 0.f) * num;
       }
@@ -178,7 +210,7 @@ __global__ void __launch_bounds__(kFcThreads, 3) k_col_deconv_fused(FusedColArgs
     for (int n1 = 0; n1 < N1; ++n1) {
       cf z = iv[reg_pos<N1>(n1)];
       if (n1 && k2) z = z * conj(ldg_cf(a.tw_h + n1 * k2));
-      s0[n1 * kFcCols] = z;
+      s0[at(n1)] = z;
     }
   }
   __syncthreads();
@@ -186,12 +218,12 @@ __global__ void __launch_bounds__(kFcThreads, 3) k_col_deconv_fused(FusedColArgs
   // ---- step 3: inverse N2-point DFTs down the columns, rows < H out
   if (tid < N1 * kFcCols) {
     const int n1 = tid / kFcCols, col = tid % kFcCols;
-    const cf* src = buf0 + n1 * kFcCols + col;
+    const cf* src = buf0 + col;
     cf x[N2];
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) x[k2] = src[k2 * P * kFcCols];
+    for (int k2 = 0; k2 < N2; ++k2) x[k2] = src[fc_phys<N1>(n1 + N1 * k2) * kFcCols];
     reg_dft<true, N2>(x);
-    if (v0 + col < a.Pw2) {
+    if (col < nv) {
       cf* dst = a.ihat + ((int64_t)fc * a.H) * a.Pw2p + v0 + col;
 #pragma unroll
       for (int n2 = 0; n2 < N2; ++n2) {
@@ -201,6 +233,7 @@ __global__ void __launch_bounds__(kFcThreads, 3) k_col_deconv_fused(FusedColArgs
     }
   }
   static_assert(N1 <= kFcMaxT, "kernel rows beyond the row-transform table");
+  static_assert(N1 % 4 == 0, "the swizzle permutes rows within groups of four");
   static_assert(Ph == N1 * N2, "");
 }
 
