@@ -88,14 +88,23 @@ __device__ __forceinline__ void fc_stage(cf* buf, const cf* src, int Hk, int Pw2
   }
 }
 
+// 1 / x by the hardware approximation (relative error below 2^-22; the
+// formula's inputs carry single-precision FFT rounding already).
+__device__ __forceinline__ float fc_rcp(float x) {
+  float r;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 template <int N1, int N2>
 __global__ void __launch_bounds__(kFcThreads, CBP_FC_MIN_BLOCKS) k_col_deconv_fused(FusedColArgs a) {
   using L = FcSmem<N1, N2>;
   constexpr int Ph = N1 * N2;
+  constexpr int S = kFcCols;                // slot stride (cf) in a buffer
+  constexpr int B1 = (int)L::kBuf;          // buffer 1 relative to buffer 0 (cf)
   extern __shared__ __align__(16) char smem[];
   cf* buf0 = (cf*)smem;
-  cf* buf1 = buf0 + L::kBuf;
-  cf* rt = buf1 + L::kBuf;                 // [2][kFcMaxT][kFcCols] kernel row transforms
+  cf* rt = buf0 + 2 * L::kBuf;              // [2][kFcMaxT][kFcCols] kernel row transforms
   const int fc = blockIdx.y, f = fc / a.C;
   const int v0 = blockIdx.x * kFcCols;
   const int nv = min(kFcCols, a.Pw2 - v0);
@@ -103,7 +112,7 @@ __global__ void __launch_bounds__(kFcThreads, CBP_FC_MIN_BLOCKS) k_col_deconv_fu
 
   // both frames' strips in flight while the kernels' row transforms are made
   fc_stage<N1, N2>(buf0, a.spec[0] + ((int64_t)fc * a.H1) * a.Pw2p + v0, a.H1, a.Pw2p, nv);
-  fc_stage<N1, N2>(buf1, a.spec[1] + ((int64_t)fc * a.H2) * a.Pw2p + v0, a.H2, a.Pw2p, nv);
+  fc_stage<N1, N2>(buf0 + B1, a.spec[1] + ((int64_t)fc * a.H2) * a.Pw2p + v0, a.H2, a.Pw2p, nv);
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 
   // kernel row transforms R_k,p(v) for the strip's columns (zero past Pw2)
@@ -126,20 +135,28 @@ __global__ void __launch_bounds__(kFcThreads, CBP_FC_MIN_BLOCKS) k_col_deconv_fu
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
 
+  // Slot (j, m) = logical row j + N1 m sits at physical row (j ^ (m & 3)) + N1 m
+  // (fc_phys): with four base pointers per thread every access below is a
+  // base plus an immediate offset.
   // ---- step 1: N2-point DFTs down the columns, twiddled, in place
+#pragma unroll 1
   for (int task = tid; task < 2 * N1 * kFcCols; task += kFcThreads) {
     const int fr = task / (N1 * kFcCols), r = task % (N1 * kFcCols);
     const int n1 = r / kFcCols, col = r % kFcCols;
-    cf* b = (fr ? buf1 : buf0) + col;
+    cf* b = buf0 + (fr ? B1 : 0) + col;
+    cf* q[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) q[c] = b + (n1 ^ c) * S;
     cf x[N2];
 #pragma unroll
-    for (int n2 = 0; n2 < N2; ++n2) x[n2] = b[fc_phys<N1>(n1 + N1 * n2) * kFcCols];
+    for (int m = 0; m < N2; ++m) x[m] = q[m & 3][N1 * m * S];
     reg_dft<false, N2>(x);
+    const cf* tw = a.tw_h + n1;
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) {
-      cf y = x[reg_pos<N2>(k2)];
-      if (k2) y = y * ldg_cf(a.tw_h + n1 * k2);      // w_Ph^(n1 k2), n1 k2 < Ph
-      b[fc_phys<N1>(n1 + N1 * k2) * kFcCols] = y;
+    for (int m = 0; m < N2; ++m) {
+      cf y = x[reg_pos<N2>(m)];
+      if (m) y = y * ldg_cf(tw + (n1 * (m - 1)));    // w_Ph^(n1 m), n1 m < Ph
+      q[m & 3][N1 * m * S] = y;
     }
   }
   __syncthreads();
@@ -147,88 +164,96 @@ __global__ void __launch_bounds__(kFcThreads, CBP_FC_MIN_BLOCKS) k_col_deconv_fu
   // ---- step 2: N1-point DFTs across, the formula, the inverse N1-point DFTs
   if (tid < N2 * kFcCols) {
     const int k2 = tid / kFcCols, col = tid % kFcCols;
-    cf* s0 = buf0 + col;
-    cf* s1 = buf1 + col;
-    auto at = [&](int j) { return fc_phys<N1>(j + N1 * k2) * kFcCols; };
-    // both frames' column spectra at rows u = k2 + N2 k1, back into their slots
+    cf* q[4];
     {
-      cf x[N1];
+      cf* base = buf0 + (N1 * k2) * S + col;
 #pragma unroll
-      for (int j = 0; j < N1; ++j) x[j] = s1[at(j)];
-      reg_dft<false, N1>(x);
-#pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) s1[at(k1)] = x[reg_pos<N1>(k1)];
+      for (int c = 0; c < 4; ++c) q[c] = base + (c ^ (k2 & 3)) * S;
     }
-    {
-      cf x[N1];
-#pragma unroll
-      for (int j = 0; j < N1; ++j) x[j] = s0[at(j)];
-      reg_dft<false, N1>(x);
-#pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) s0[at(k1)] = x[reg_pos<N1>(k1)];
-    }
-    // kernel spectra at the same rows: K^(k2 + N2 k1) = DFT_N1 over p of R_p w_Ph^(p k2)
-    const cf* r1 = rt + col;
-    const cf* r2 = rt + kFcMaxT * kFcCols + col;
+    // element j of this task's slots: q[j & 3][(j & ~3) S] (+ B1 for frame 2)
+#define FC_AT(j) q[(j) & 3][((j) & ~3) * S]
+#define FC_AT1(j) q[(j) & 3][((j) & ~3) * S + B1]
     float d1[N1];
-    {
-      cf kh[N1];
+    cf x[N1];          // the working transform; ends up holding I^ at reg_pos order
+    const float eps = a.eps;
+    // four forward N1-point DFTs through one code path: frame 2's and frame
+    // 1's column spectra (back into their slots), then the two kernels'
+    // spectra K^(k2 + N2 k1) = DFT_N1 over p of R_p w_Ph^(p k2), each consumed
+    // by its part of the formula at once
+#pragma unroll 1
+    for (int it = 0; it < 4; ++it) {
+      if (it == 0) {
 #pragma unroll
-      for (int p = 0; p < N1; ++p) {
-        kh[p] = mk(0.f, 0.f);
-        if (p < a.t1) kh[p] = p ? r1[p * kFcCols] * ldg_cf(a.tw_h + p * k2) : r1[0];
+        for (int j = 0; j < N1; ++j) x[j] = FC_AT1(j);
+      } else if (it == 1) {
+#pragma unroll
+        for (int j = 0; j < N1; ++j) x[j] = FC_AT(j);
+      } else {
+        const cf* r = rt + (it - 2) * kFcMaxT * kFcCols + col;
+        const int t = it == 2 ? a.t1 : a.t2;
+        const cf* tw = a.tw_h;
+#pragma unroll
+        for (int p = 0; p < N1; ++p) {
+          x[p] = mk(0.f, 0.f);
+          if (p < t) x[p] = p ? r[p * kFcCols] * ldg_cf(tw + p * k2) : r[0];
+        }
       }
-      reg_dft<false, N1>(kh);
+      reg_dft<false, N1>(x);
+      if (it == 0) {
 #pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) {
-        const cf k = kh[reg_pos<N1>(k1)];
-        s0[at(k1)] = cmulc(k, s0[at(k1)]);       // conj(K^1) B^1
-        d1[k1] = abs2(k);
-      }
-    }
-    cf iv[N1];
-    {
-      cf kh[N1];
+        for (int k1 = 0; k1 < N1; ++k1) FC_AT1(k1) = x[reg_pos<N1>(k1)];
+      } else if (it == 1) {
 #pragma unroll
-      for (int p = 0; p < N1; ++p) {
-        kh[p] = mk(0.f, 0.f);
-        if (p < a.t2) kh[p] = p ? r2[p * kFcCols] * ldg_cf(a.tw_h + p * k2) : r2[0];
-      }
-      reg_dft<false, N1>(kh);
-      const float eps = a.eps;
+        for (int k1 = 0; k1 < N1; ++k1) FC_AT(k1) = x[reg_pos<N1>(k1)];
+      } else if (it == 2) {
 #pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) {
-        const cf k = kh[reg_pos<N1>(k1)];
-        const cf num = s0[at(k1)] + cmulc(k, s1[at(k1)]);
-        const float den = d1[k1] + abs2(k) + eps;
-        iv[k1] = (den != 0.f ? __frcp_rn(den) : 0.f) * num;
+        for (int k1 = 0; k1 < N1; ++k1) {
+          const cf k = x[reg_pos<N1>(k1)];
+          FC_AT(k1) = cmulc(k, FC_AT(k1));          // conj(K^1) B^1
+          d1[k1] = abs2(k);
+        }
+      } else {
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+          const cf k = x[reg_pos<N1>(k1)];
+          const cf num = FC_AT(k1) + cmulc(k, FC_AT1(k1));
+          const float den = d1[k1] + abs2(k) + eps;
+          x[reg_pos<N1>(k1)] = (den != 0.f ? fc_rcp(den) : 0.f) * num;   // I^(k2 + N2 k1)
+        }
       }
     }
     // inverse over k1, twiddled by w_Ph^(-n1 k2), into this task's slots
+    cf iv[N1];
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) iv[k1] = x[reg_pos<N1>(k1)];
     reg_dft<true, N1>(iv);
 #pragma unroll
     for (int n1 = 0; n1 < N1; ++n1) {
       cf z = iv[reg_pos<N1>(n1)];
-      if (n1 && k2) z = z * conj(ldg_cf(a.tw_h + n1 * k2));
-      s0[at(n1)] = z;
+      if (n1) z = z * conj(ldg_cf(a.tw_h + n1 * k2));
+      FC_AT(n1) = z;
     }
+#undef FC_AT
+#undef FC_AT1
   }
   __syncthreads();
 
   // ---- step 3: inverse N2-point DFTs down the columns, rows < H out
   if (tid < N1 * kFcCols) {
     const int n1 = tid / kFcCols, col = tid % kFcCols;
-    const cf* src = buf0 + col;
+    const cf* q[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) q[c] = buf0 + col + (n1 ^ c) * S;
     cf x[N2];
 #pragma unroll
-    for (int k2 = 0; k2 < N2; ++k2) x[k2] = src[fc_phys<N1>(n1 + N1 * k2) * kFcCols];
+    for (int m = 0; m < N2; ++m) x[m] = q[m & 3][N1 * m * S];
     reg_dft<true, N2>(x);
     if (col < nv) {
-      cf* dst = a.ihat + ((int64_t)fc * a.H) * a.Pw2p + v0 + col;
+      cf* dst = a.ihat + ((int64_t)fc * a.H + n1) * a.Pw2p + v0 + col;
+      const int64_t step = (int64_t)N1 * a.Pw2p;
 #pragma unroll
       for (int n2 = 0; n2 < N2; ++n2) {
-        const int row = n1 + N1 * n2;
-        if (row < a.H) dst[(int64_t)row * a.Pw2p] = x[reg_pos<N2>(n2)];
+        if (n1 + N1 * n2 < a.H) dst[n2 * step] = x[reg_pos<N2>(n2)];
       }
     }
   }
