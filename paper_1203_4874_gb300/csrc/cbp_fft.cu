@@ -719,6 +719,210 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
   }
 }
 
+// ------------------------- row pass with in-register transforms (float rows)
+//
+// The same work as k_row_pass (one read of every row: A1's exact folds and
+// A6's forward real row FFT) for float32 frames whose rows start on 8-byte
+// boundaries and whose half-length transform N = N1 N2 splits into two
+// register-sized factors (the 1080p grid: 972 = 36 x 27).  The half-length
+// complex row z[m] = (x[2m], x[2m+1]) is transformed in place in the staging
+// buffer by the two-factor split n = n1 + N1 n2, k = k2 + N2 k1:
+//   step 1: per (row, n1), an N2-point DFT over n2 in registers, twiddled by
+//           w_N^(n1 k2), back into the same slots n1 + N1 k2;
+//   step 2: per (row, k2), an N1-point DFT over the slots n1 + N1 k2 in
+//           registers: X[k2 + N2 k1] into slot k1 + N1 k2;
+//   then the real-FFT split of X[k] and X[N - k] into the Pw/2 + 1 stored bins.
+// One staging buffer of kIrRows rows: the group's rows arrive by bulk copy,
+// the folds read them, the transforms overwrite them, the next group's copy is
+// issued once the bins are out.  Registers, not shared memory, hold the
+// transform data, so two 288-thread blocks fit per SM.
+constexpr int kIrThreads = 288;
+constexpr int kIrRows = 8;
+
+struct RowIrSmem {
+  size_t raw, rb, rph, mbar, total;
+};
+__host__ __device__ inline RowIrSmem row_ir_layout(int rw) {
+  RowIrSmem L;
+  size_t o = 0;
+  L.raw = o;
+  o += rp_align((size_t)kIrRows * rw * sizeof(float));
+  L.rb = o;
+  o += rp_align((size_t)kIrThreads * 8);
+  L.rph = o;
+  o += rp_align((size_t)kIrRows * sizeof(int));
+  L.mbar = o;
+  o += rp_align(sizeof(uint64_t));
+  L.total = o;
+  return L;
+}
+
+template <int N1, int N2, bool FOLD>
+__global__ void __launch_bounds__(kIrThreads, 2)
+k_row_pass_ir(RowPassArgs a, const cf* tw_w) {
+  constexpr int N = N1 * N2;
+  extern __shared__ __align__(16) char smem[];
+  const FrameDesc& fr = a.fr[blockIdx.z];
+  const int W = fr.w, M = a.M, rw = a.rw;
+  const bool fft = (int)blockIdx.z < a.fft_frames;
+  const RowIrSmem L = row_ir_layout(rw);
+  float* const raw = (float*)(smem + L.raw);
+  TwoSum* rb = (TwoSum*)(smem + L.rb);
+  int* rph = (int*)(smem + L.rph);
+  uint64_t* bar = (uint64_t*)(smem + L.mbar);
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  uint32_t par = 0u;
+  const int fc = blockIdx.y, f = fc / fr.c, ch = fc % fr.c;
+  const int x0 = blockIdx.x, X = gridDim.x;
+  const int nrows = x0 < fr.h ? (fr.h - x0 + X - 1) / X : 0;
+  const int ngroups = (nrows + kIrRows - 1) / kIrRows;
+  const float* fb = (const float*)frame_base(fr, f) + (int64_t)ch * fr.cs;
+  auto row_of = [&](int g, int i) { return x0 + (g * kIrRows + i) * X; };
+  cf* spec = fft ? (cf*)a.spec[blockIdx.z] + (int64_t)fc * fr.h * a.Pw2p : nullptr;
+  // column folds: this thread's column pairs (c, c + 1), c = 2 (tid + kIrThreads j)
+  constexpr int kColPairs = 4;
+  TwoSum creg[2 * kColPairs];
+  Edge<float> en{0.f, -1};
+  if (ngroups > 0)
+    en = stage_rows_bulk<float>(raw, rph, fb, [&](int i) { return (int64_t)row_of(0, i) * fr.rs; },
+                                min(kIrRows, nrows), W, rw, bar);
+  for (int g = 0; g < ngroups; ++g) {
+    const int nr = min(kIrRows, nrows - g * kIrRows);
+    const bool arrived = mbar_wait(bar, par, kWaitLimit);
+    par ^= 1u;
+    if (__syncthreads_or(!arrived)) {
+      // the group's copy did not complete in time (no other copy is in flight)
+      if (tid == 0) atomicOr(a.err, 1);
+      return;
+    }
+    if (en.at >= 0) raw[en.at] = en.v;
+    // zero each row past W up to the transform length (and rows past nr)
+    for (int e = tid; e < nr * (2 * N - W); e += kIrThreads) {
+      const int i = e / (2 * N - W), c = W + e - i * (2 * N - W);
+      raw[i * rw + rph[i] + c] = 0.f;
+    }
+    __syncthreads();
+    if (FOLD) {
+      // column folds (this block's bin), float pairs
+#pragma unroll
+      for (int j = 0; j < kColPairs; ++j) {
+        const int c = 2 * (tid + kIrThreads * j);
+        if (c < W) {
+          for (int i = 0; i < nr; ++i) {
+            const float2 v = *(const float2*)(raw + i * rw + rph[i] + c);
+            creg[2 * j].add(v.x);
+            if (c + 1 < W) creg[2 * j + 1].add(v.y);
+          }
+        }
+      }
+      // row folds: task (i, sg, m) sums columns c = m (mod M) of row i over segment sg
+      const int nseg = max(1, kIrThreads / (nr * M));
+      const int nsteps = (W + M - 1) / M, sps = (nsteps + nseg - 1) / nseg;
+      if (tid < nr * M * nseg) {
+        const int i = tid / (M * nseg), r = tid - i * (M * nseg), sg = r / M, m = r - sg * M;
+        TwoSum acc, acc2;
+        const float* rp = raw + i * rw + rph[i];
+        const int st0 = sg * sps, e = min(nsteps, st0 + sps);
+        int st = st0, c = st0 * M + m;
+        // columns past W read the zeroed tail (up to 2N) or are skipped
+        for (; st + 1 < e && c + M < 2 * N; st += 2, c += 2 * M) {
+          acc.add(rp[c]);
+          acc2.add(rp[c + M]);
+        }
+        for (; st < e; ++st, c += M)
+          if (c < W) acc.add(rp[c]);
+        acc.merge(acc2);
+        rb[tid] = acc;
+      }
+    }
+    __syncthreads();
+    if (FOLD) {
+      const int nseg = max(1, kIrThreads / (nr * M));
+      for (int t = tid; t < nr * M; t += kIrThreads) {
+        const int i = t / M, m = t - i * M;
+        TwoSum v = rb[(i * nseg) * M + m];
+        for (int sg = 1; sg < nseg; ++sg) v.merge(rb[(i * nseg + sg) * M + m]);
+        v.store((char*)a.bins_r[blockIdx.z] + 8 * (((int64_t)fc * M + m) * fr.h + row_of(g, i)));
+      }
+    }
+    if (fft) {
+      // ---- step 1: N2-point DFTs over n2 for each (row, n1), in place
+      if (tid < nr * N1) {
+        const int i = tid / N1, n1 = tid - i * N1;
+        cf* z = (cf*)(raw + i * rw + rph[i]) + n1;
+        cf x[N2];
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) x[n2] = z[N1 * n2];
+        reg_dft<false, N2>(x);
+        const cf* tw = tw_w + 2 * n1;                 // w_N^(n1 k2) = w_Pw^(2 n1 k2)
+#pragma unroll
+        for (int k2 = 0; k2 < N2; ++k2) {
+          cf y = x[reg_pos<N2>(k2)];
+          if (k2) y = y * ldg_cpx(tw + 2 * n1 * (k2 - 1));
+          z[N1 * k2] = y;
+        }
+      }
+      __syncthreads();
+      // ---- step 2: N1-point DFTs over n1 for each (row, k2), in place
+      if (tid < kIrRows * N2) {
+        const int i = tid % kIrRows, k2 = tid / kIrRows;
+        if (i < nr) {
+          cf* z = (cf*)(raw + i * rw + rph[i]) + N1 * k2;
+          cf x[N1];
+#pragma unroll
+          for (int n1 = 0; n1 < N1; ++n1) x[n1] = z[n1];
+          reg_dft<false, N1>(x);
+#pragma unroll
+          for (int k1 = 0; k1 < N1; ++k1) z[k1] = x[reg_pos<N1>(k1)];   // X[k2 + N2 k1]
+        }
+      }
+      __syncthreads();
+      // ---- the real-FFT split: bins k <= N from X[k] and X[N - k]
+      for (int e = tid; e < nr * a.Pw2; e += kIrThreads) {
+        const int i = e / a.Pw2, k = e - i * a.Pw2;
+        const cf* z = (const cf*)(raw + i * rw + rph[i]);
+        const int ka = k < N ? k : 0, kb = k > 0 ? N - k : 0;
+        const cf zk = z[(ka / N2) + N1 * (ka % N2)];
+        const cf zc = conj(z[(kb / N2) + N1 * (kb % N2)]);
+        const cf ev = 0.5f * (zk + zc), d = 0.5f * (zk - zc);
+        const cf wd = ldg_cpx(tw_w + k) * d;          // X = e - i w d, w = w_Pw^k
+        spec[(int64_t)row_of(g, i) * a.Pw2p + k] = mk(ev.re + wd.im, ev.im - wd.re);
+      }
+    }
+    // the buffer is rewritten by the next bulk copy: order its generic-proxy
+    // accesses first
+    fence_proxy_async();
+    __syncthreads();
+    if (g + 1 < ngroups) {
+      const int g1 = g + 1;
+      en = stage_rows_bulk<float>(raw, rph, fb, [&](int i) { return (int64_t)row_of(g1, i) * fr.rs; },
+                                  min(kIrRows, nrows - g1 * kIrRows), W, rw, bar);
+    }
+  }
+  if (FOLD) {
+    bool finite = true;
+    char* dst = (char*)a.bins_c[blockIdx.z] + 8 * (((int64_t)fc * M + x0) * W);
+#pragma unroll
+    for (int j = 0; j < kColPairs; ++j) {
+      const int c = 2 * (tid + kIrThreads * j);
+      if (c < W) {
+        finite = finite && creg[2 * j].finite();
+        creg[2 * j].store(dst + 8 * (size_t)c);
+      }
+      if (c + 1 < W) {
+        finite = finite && creg[2 * j + 1].finite();
+        creg[2 * j + 1].store(dst + 8 * (size_t)(c + 1));
+      }
+    }
+    if (__syncthreads_or(!finite) && tid == 0) atomicOr(a.bad + f, 1);
+  }
+}
+
 constexpr int kColThreads = 512;
 
 struct ColArgs {
@@ -1248,6 +1452,17 @@ void run_row_pass_t(const Plan& p, const RowPassArgs& a, int gx, int gz, char* w
       a, (const cpx<T>*)(ws + p.off_tw_w), (const cpx<T>*)(ws + p.off_stw_r));
 }
 
+// The in-register row pass applies: float rows starting on 8-byte boundaries
+// (strided batches; tables of per-pair addresses take the general kernel) and
+// a half-length transform of 972 = 36 x 27 points.
+static bool row_pass_ir_ok(const Plan& p, const FrameDesc& b1, const FrameDesc& b2, bool fft) {
+  if (!fft || p.fft_f64 || b1.f64 || !p.pw_half || p.fp_w2.n != 972 || p.M > 32) return false;
+  for (const FrameDesc* b : {&b1, &b2}) {
+    if (b->tab || ((uintptr_t)b->data & 7) || (b->rs & 1) || (b->cs & 1) || (b->fs & 1)) return false;
+  }
+  return true;
+}
+
 template <typename T, typename In>
 void run_row_pass(const Plan& p, const FrameDesc& b1, const FrameDesc& b2, char* ws,
                   cudaStream_t st, bool fold, bool fft) {
@@ -1285,6 +1500,16 @@ void run_row_pass(const Plan& p, const FrameDesc& b1, const FrameDesc& b2, char*
   const int hmax = p.H1 > p.H2 ? p.H1 : p.H2;
   const int gx = fold ? p.M : (hmax + 31) / 32;
   const int gz = fold ? 2 : a.fft_frames;
+  if constexpr (sizeof(T) == 4 && sizeof(In) == 4) {
+    if (row_pass_ir_ok(p, b1, b2, fft)) {
+      a.rw = ((2 * a.pl.n + 4 + 3) / 4) * 4;       // transform length + the 16-byte phase
+      const RowIrSmem L = row_ir_layout(a.rw);
+      auto kern = fold ? k_row_pass_ir<36, 27, true> : k_row_pass_ir<36, 27, false>;
+      cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+      kern<<<dim3(gx, p.n * p.C, gz), kIrThreads, L.total, st>>>(a, (const cf*)(ws + p.off_tw_w));
+      return;
+    }
+  }
   if (fold && fft) run_row_pass_t<T, In, true, true>(p, a, gx, gz, ws, st);
   else if (fft) run_row_pass_t<T, In, false, true>(p, a, gx, gz, ws, st);
   else run_row_pass_t<float, In, true, false>(p, a, gx, gz, ws, st);
