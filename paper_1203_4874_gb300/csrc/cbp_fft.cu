@@ -740,13 +740,15 @@ constexpr int kIrThreads = 288;
 constexpr int kIrRows = 8;
 
 struct RowIrSmem {
-  size_t raw, rb, rph, mbar, total;
+  size_t raw, colacc, rb, rph, mbar, total;
 };
 __host__ __device__ inline RowIrSmem row_ir_layout(int rw) {
   RowIrSmem L;
   size_t o = 0;
   L.raw = o;
   o += rp_align((size_t)kIrRows * rw * sizeof(float));
+  L.colacc = o;                                   // column-fold (hi, lo) per column, W <= rw
+  o += rp_align((size_t)rw * sizeof(TwoSum));
   L.rb = o;
   o += rp_align((size_t)kIrThreads * 8);
   L.rph = o;
@@ -758,7 +760,7 @@ __host__ __device__ inline RowIrSmem row_ir_layout(int rw) {
 }
 
 template <int N1, int N2, bool FOLD>
-__global__ void __launch_bounds__(kIrThreads, 2)
+__global__ void __maxnreg__(112)
 k_row_pass_ir(RowPassArgs a, const cf* tw_w) {
   constexpr int N = N1 * N2;
   extern __shared__ __align__(16) char smem[];
@@ -784,9 +786,12 @@ k_row_pass_ir(RowPassArgs a, const cf* tw_w) {
   const float* fb = (const float*)frame_base(fr, f) + (int64_t)ch * fr.cs;
   auto row_of = [&](int g, int i) { return x0 + (g * kIrRows + i) * X; };
   cf* spec = fft ? (cf*)a.spec[blockIdx.z] + (int64_t)fc * fr.h * a.Pw2p : nullptr;
-  // column folds: this thread's column pairs (c, c + 1), c = 2 (tid + kIrThreads j)
+  // column folds: this thread's column pairs (c, c + 1), c = 2 (tid + kIrThreads j),
+  // accumulated in shared memory across the groups
   constexpr int kColPairs = 4;
-  TwoSum creg[2 * kColPairs];
+  TwoSum* colacc = (TwoSum*)(smem + L.colacc);
+  if (FOLD)
+    for (int c = tid; c < W; c += kIrThreads) colacc[c] = TwoSum();
   Edge<float> en{0.f, -1};
   if (ngroups > 0)
     en = stage_rows_bulk<float>(raw, rph, fb, [&](int i) { return (int64_t)row_of(0, i) * fr.rs; },
@@ -813,29 +818,40 @@ k_row_pass_ir(RowPassArgs a, const cf* tw_w) {
       for (int j = 0; j < kColPairs; ++j) {
         const int c = 2 * (tid + kIrThreads * j);
         if (c < W) {
+          const float4 h = *(const float4*)(colacc + c);    // (hi, lo) of c and c + 1
+          TwoSum s0, s1;
+          s0.hi = h.x;
+          s0.lo = h.y;
+          s1.hi = h.z;
+          s1.lo = h.w;
           for (int i = 0; i < nr; ++i) {
             const float2 v = *(const float2*)(raw + i * rw + rph[i] + c);
-            creg[2 * j].add(v.x);
-            if (c + 1 < W) creg[2 * j + 1].add(v.y);
+            s0.add(v.x);
+            s1.add(v.y);                     // column W (odd W) reads the zeroed tail
           }
+          *(float4*)(colacc + c) = make_float4(s0.hi, s0.lo, s1.hi, s1.lo);
         }
       }
-      // row folds: task (i, sg, m) sums columns c = m (mod M) of row i over segment sg
+      // row folds: task (i, sg, m) sums columns c = m (mod M) of row i over
+      // segment sg; columns W..2N-1 read the zeroed tail
       const int nseg = max(1, kIrThreads / (nr * M));
       const int nsteps = (W + M - 1) / M, sps = (nsteps + nseg - 1) / nseg;
       if (tid < nr * M * nseg) {
         const int i = tid / (M * nseg), r = tid - i * (M * nseg), sg = r / M, m = r - sg * M;
         TwoSum acc, acc2;
-        const float* rp = raw + i * rw + rph[i];
         const int st0 = sg * sps, e = min(nsteps, st0 + sps);
-        int st = st0, c = st0 * M + m;
-        // columns past W read the zeroed tail (up to 2N) or are skipped
-        for (; st + 1 < e && c + M < 2 * N; st += 2, c += 2 * M) {
-          acc.add(rp[c]);
-          acc2.add(rp[c + M]);
+        const float* rp = raw + i * rw + rph[i] + st0 * M + m;
+        int n = e - st0;                                   // terms of this task
+        const int last = st0 * M + m + (n - 1) * M;        // column of the last term
+        if (n > 0 && last >= 2 * N) --n;                   // past the zeroed tail: beyond W
+        int k = 0;
+        for (; k + 3 < n; k += 4, rp += 4 * M) {
+          acc.add(rp[0]);
+          acc2.add(rp[M]);
+          acc.add(rp[2 * M]);
+          acc2.add(rp[3 * M]);
         }
-        for (; st < e; ++st, c += M)
-          if (c < W) acc.add(rp[c]);
+        for (; k < n; ++k, rp += M) acc.add(rp[0]);
         acc.merge(acc2);
         rb[tid] = acc;
       }
@@ -851,47 +867,72 @@ k_row_pass_ir(RowPassArgs a, const cf* tw_w) {
       }
     }
     if (fft) {
-      // ---- step 1: N2-point DFTs over n2 for each (row, n1), in place
-      if (tid < nr * N1) {
-        const int i = tid / N1, n1 = tid - i * N1;
-        cf* z = (cf*)(raw + i * rw + rph[i]) + n1;
-        cf x[N2];
+      // ---- step 1: N2-point DFTs over n2 for each (row, n1); the results go
+      // to slot (n1 ^ sw(k2)) + N1 k2 of the row, sw(k2) = (k2 >> 2) & 3, so
+      // that step 2's lanes (consecutive k2) fall on distinct banks.  Every
+      // task reads before any writes (a barrier between).
+      const bool t1 = tid < nr * N1;
+      const int i1 = tid / N1, n1 = tid - i1 * N1;
+      cf x1[N2];
+      if (t1) {
+        const cf* z = (const cf*)(raw + i1 * rw + rph[i1]) + n1;
 #pragma unroll
-        for (int n2 = 0; n2 < N2; ++n2) x[n2] = z[N1 * n2];
-        reg_dft<false, N2>(x);
+        for (int n2 = 0; n2 < N2; ++n2) x1[n2] = z[N1 * n2];
+        reg_dft<false, N2>(x1);
+      }
+      __syncthreads();
+      if (t1) {
+        cf* z = (cf*)(raw + i1 * rw + rph[i1]);
+        cf* q[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) q[c] = z + (n1 ^ c);
         const cf* tw = tw_w + 2 * n1;                 // w_N^(n1 k2) = w_Pw^(2 n1 k2)
 #pragma unroll
         for (int k2 = 0; k2 < N2; ++k2) {
-          cf y = x[reg_pos<N2>(k2)];
+          cf y = x1[reg_pos<N2>(k2)];
           if (k2) y = y * ldg_cpx(tw + 2 * n1 * (k2 - 1));
-          z[N1 * k2] = y;
+          q[(k2 >> 2) & 3][N1 * k2] = y;
         }
       }
       __syncthreads();
-      // ---- step 2: N1-point DFTs over n1 for each (row, k2), in place
-      if (tid < kIrRows * N2) {
-        const int i = tid % kIrRows, k2 = tid / kIrRows;
-        if (i < nr) {
-          cf* z = (cf*)(raw + i * rw + rph[i]) + N1 * k2;
-          cf x[N1];
+      // ---- step 2: one warp per row, lane k2: an N1-point DFT over n1 gives
+      // X[k2 + N2 k1] in registers; the real-FFT split pairs X[k] with
+      // X[N - k], held by lane N2 - k2 at k1' = N1 - 1 - k1 (lane 0: by
+      // itself at (N1 - k1) mod N1), fetched by shuffle; bins go straight out.
+      const int warp = tid >> 5, lane = tid & 31;
+      static_assert(N2 <= 32, "one lane per k2");
+      if (warp < nr && lane < N2) {
+        const int i = warp, k2 = lane;
+        const cf* z = (const cf*)(raw + i * rw + rph[i]) + N1 * k2;
+        const int sw = (k2 >> 2) & 3;
+        const cf* q[4];
 #pragma unroll
-          for (int n1 = 0; n1 < N1; ++n1) x[n1] = z[n1];
-          reg_dft<false, N1>(x);
+        for (int c = 0; c < 4; ++c) q[c] = z + (c ^ sw);
+        cf x[N1];
 #pragma unroll
-          for (int k1 = 0; k1 < N1; ++k1) z[k1] = x[reg_pos<N1>(k1)];   // X[k2 + N2 k1]
+        for (int n = 0; n < N1; ++n) x[n] = q[n & 3][n & ~3];
+        reg_dft<false, N1>(x);
+        constexpr unsigned kMask = (N2 == 32) ? 0xffffffffu : ((1u << N2) - 1u);
+        const int src = k2 ? N2 - k2 : 0;
+        cf* out = spec + (int64_t)row_of(g, i) * a.Pw2p;
+        const cf* tw = tw_w + k2;
+#pragma unroll
+        for (int k1 = 0; k1 < N1; ++k1) {
+          const cf send = x[reg_pos<N1>(N1 - 1 - k1)];
+          const float pr = __shfl_sync(kMask, send.re, src);
+          const float pi = __shfl_sync(kMask, send.im, src);
+          const cf zk = x[reg_pos<N1>(k1)];
+          const cf own = x[reg_pos<N1>((N1 - k1) % N1)];
+          const cf zc = k2 ? mk(pr, -pi) : conj(own);
+          const cf ev = 0.5f * (zk + zc), d = 0.5f * (zk - zc);
+          const cf wd = ldg_cpx(tw + N2 * k1) * d;     // X = e - i w d, w = w_Pw^k
+          out[k2 + N2 * k1] = mk(ev.re + wd.im, ev.im - wd.re);
         }
-      }
-      __syncthreads();
-      // ---- the real-FFT split: bins k <= N from X[k] and X[N - k]
-      for (int e = tid; e < nr * a.Pw2; e += kIrThreads) {
-        const int i = e / a.Pw2, k = e - i * a.Pw2;
-        const cf* z = (const cf*)(raw + i * rw + rph[i]);
-        const int ka = k < N ? k : 0, kb = k > 0 ? N - k : 0;
-        const cf zk = z[(ka / N2) + N1 * (ka % N2)];
-        const cf zc = conj(z[(kb / N2) + N1 * (kb % N2)]);
-        const cf ev = 0.5f * (zk + zc), d = 0.5f * (zk - zc);
-        const cf wd = ldg_cpx(tw_w + k) * d;          // X = e - i w d, w = w_Pw^k
-        spec[(int64_t)row_of(g, i) * a.Pw2p + k] = mk(ev.re + wd.im, ev.im - wd.re);
+        if (k2 == 0) {                                 // bin N from X[0]
+          const cf z0 = x[reg_pos<N1>(0)];
+          const cf wd = ldg_cpx(tw_w + N) * mk(0.f, z0.im);    // d = i Im X[0]
+          out[N] = mk(z0.re + wd.im, -wd.re);
+        }
       }
     }
     // the buffer is rewritten by the next bulk copy: order its generic-proxy
@@ -907,17 +948,10 @@ k_row_pass_ir(RowPassArgs a, const cf* tw_w) {
   if (FOLD) {
     bool finite = true;
     char* dst = (char*)a.bins_c[blockIdx.z] + 8 * (((int64_t)fc * M + x0) * W);
-#pragma unroll
-    for (int j = 0; j < kColPairs; ++j) {
-      const int c = 2 * (tid + kIrThreads * j);
-      if (c < W) {
-        finite = finite && creg[2 * j].finite();
-        creg[2 * j].store(dst + 8 * (size_t)c);
-      }
-      if (c + 1 < W) {
-        finite = finite && creg[2 * j + 1].finite();
-        creg[2 * j + 1].store(dst + 8 * (size_t)(c + 1));
-      }
+    __syncthreads();
+    for (int c = tid; c < W; c += kIrThreads) {
+      finite = finite && colacc[c].finite();
+      colacc[c].store(dst + 8 * (size_t)c);
     }
     if (__syncthreads_or(!finite) && tid == 0) atomicOr(a.bad + f, 1);
   }
