@@ -735,9 +735,9 @@ k_row_pass(RowPassArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
 // One staging buffer of kIrRows rows: the group's rows arrive by bulk copy,
 // the folds read them, the transforms overwrite them, the next group's copy is
 // issued once the bins are out.  Registers, not shared memory, hold the
-// transform data, so two 288-thread blocks fit per SM.
-constexpr int kIrThreads = 288;
-constexpr int kIrRows = 8;
+// transform data; two 256-thread blocks per SM.
+constexpr int kIrThreads = 256;      // eight warps: two blocks keep four warps per scheduler
+constexpr int kIrRows = 7;           // rows per group: 7 x 36 step-1 tasks, one warp per row in step 2
 
 struct RowIrSmem {
   size_t raw, colacc, rb, rph, mbar, total;
@@ -760,7 +760,7 @@ __host__ __device__ inline RowIrSmem row_ir_layout(int rw) {
 }
 
 template <int N1, int N2, bool FOLD>
-__global__ void __maxnreg__(112)
+__global__ void __launch_bounds__(kIrThreads, 2)
 k_row_pass_ir(RowPassArgs a, const cf* tw_w) {
   constexpr int N = N1 * N2;
   extern __shared__ __align__(16) char smem[];
@@ -1540,6 +1540,7 @@ void run_row_pass(const Plan& p, const FrameDesc& b1, const FrameDesc& b2, char*
       const RowIrSmem L = row_ir_layout(a.rw);
       auto kern = fold ? k_row_pass_ir<36, 27, true> : k_row_pass_ir<36, 27, false>;
       cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.total);
+      cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
       kern<<<dim3(gx, p.n * p.C, gz), kIrThreads, L.total, st>>>(a, (const cf*)(ws + p.off_tw_w));
       return;
     }
