@@ -740,11 +740,13 @@ constexpr int kIrThreads = 256;      // eight warps: two blocks keep four warps 
 constexpr int kIrRows = 7;           // rows per group: 7 x 36 step-1 tasks, one warp per row in step 2
 
 struct RowIrSmem {
-  size_t raw, colacc, rb, rph, mbar, total;
+  size_t tw, raw, colacc, rb, rph, mbar, total;
 };
 __host__ __device__ inline RowIrSmem row_ir_layout(int rw) {
   RowIrSmem L;
   size_t o = 0;
+  L.tw = o;                                       // w_Pw^k, k < Pw = rw - 4
+  o += rp_align((size_t)(rw - 4) * sizeof(cf));
   L.raw = o;
   o += rp_align((size_t)kIrRows * rw * sizeof(float));
   L.colacc = o;                                   // column-fold (hi, lo) per column, W <= rw
@@ -772,11 +774,14 @@ k_row_pass_ir(RowPassArgs a, const cf* tw_w) {
   TwoSum* rb = (TwoSum*)(smem + L.rb);
   int* rph = (int*)(smem + L.rph);
   uint64_t* bar = (uint64_t*)(smem + L.mbar);
+  cf* tws = (cf*)(smem + L.tw);
   const int tid = threadIdx.x;
   if (tid == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
   }
+  if (fft)
+    for (int k = tid; k < 2 * N; k += kIrThreads) tws[k] = ldg_cpx(tw_w + k);
   __syncthreads();
   uint32_t par = 0u;
   const int fc = blockIdx.y, f = fc / fr.c, ch = fc % fr.c;
@@ -879,6 +884,9 @@ k_row_pass_ir(RowPassArgs a, const cf* tw_w) {
 #pragma unroll
         for (int n2 = 0; n2 < N2; ++n2) x1[n2] = z[N1 * n2];
         reg_dft<false, N2>(x1);
+        const cf* tw = tws + 2 * n1;                  // w_N^(n1 k2) = w_Pw^(2 n1 k2)
+#pragma unroll
+        for (int k2 = 1; k2 < N2; ++k2) x1[reg_pos<N2>(k2)] = x1[reg_pos<N2>(k2)] * tw[2 * n1 * (k2 - 1)];
       }
       __syncthreads();
       if (t1) {
@@ -886,13 +894,8 @@ k_row_pass_ir(RowPassArgs a, const cf* tw_w) {
         cf* q[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c) q[c] = z + (n1 ^ c);
-        const cf* tw = tw_w + 2 * n1;                 // w_N^(n1 k2) = w_Pw^(2 n1 k2)
 #pragma unroll
-        for (int k2 = 0; k2 < N2; ++k2) {
-          cf y = x1[reg_pos<N2>(k2)];
-          if (k2) y = y * ldg_cpx(tw + 2 * n1 * (k2 - 1));
-          q[(k2 >> 2) & 3][N1 * k2] = y;
-        }
+        for (int k2 = 0; k2 < N2; ++k2) q[(k2 >> 2) & 3][N1 * k2] = x1[reg_pos<N2>(k2)];
       }
       __syncthreads();
       // ---- step 2: one warp per row, lane k2: an N1-point DFT over n1 gives
@@ -915,7 +918,7 @@ k_row_pass_ir(RowPassArgs a, const cf* tw_w) {
         constexpr unsigned kMask = (N2 == 32) ? 0xffffffffu : ((1u << N2) - 1u);
         const int src = k2 ? N2 - k2 : 0;
         cf* out = spec + (int64_t)row_of(g, i) * a.Pw2p;
-        const cf* tw = tw_w + k2;
+        const cf* tw = tws + k2;
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) {
           const cf send = x[reg_pos<N1>(N1 - 1 - k1)];
@@ -925,12 +928,12 @@ k_row_pass_ir(RowPassArgs a, const cf* tw_w) {
           const cf own = x[reg_pos<N1>((N1 - k1) % N1)];
           const cf zc = k2 ? mk(pr, -pi) : conj(own);
           const cf ev = 0.5f * (zk + zc), d = 0.5f * (zk - zc);
-          const cf wd = ldg_cpx(tw + N2 * k1) * d;     // X = e - i w d, w = w_Pw^k
+          const cf wd = tw[N2 * k1] * d;               // X = e - i w d, w = w_Pw^k
           out[k2 + N2 * k1] = mk(ev.re + wd.im, ev.im - wd.re);
         }
         if (k2 == 0) {                                 // bin N from X[0]
           const cf z0 = x[reg_pos<N1>(0)];
-          const cf wd = ldg_cpx(tw_w + N) * mk(0.f, z0.im);    // d = i Im X[0]
+          const cf wd = tws[N] * mk(0.f, z0.im);       // d = i Im X[0]
           out[N] = mk(z0.re + wd.im, -wd.re);
         }
       }
