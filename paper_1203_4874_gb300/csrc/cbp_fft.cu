@@ -1463,6 +1463,127 @@ k_row_ifft(IRowArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
 }
 
 
+// ---------------- inverse row pass with in-register transforms (float)
+//
+// The inverse of k_row_pass_ir for float output rows starting on 8-byte
+// boundaries: per spectrum row, the half-length sequence
+//   Z[k] = E + i O,  E = (X[k] + conj X[N-k]) / 2,  O = w_Pw^-k (X[k] - conj X[N-k]) / 2,
+// its inverse N-point DFT z by the two-factor split (step A: per (row, k2)
+// an N1-point inverse DFT over k1, twiddled by w_N^-(n1 k2); step B: per
+// (row, n1) an N2-point inverse DFT over k2), then x[2m] = Re z[m],
+// x[2m+1] = Im z[m], scaled by 2 / (Ph Pw) and cropped to W.  The staged
+// spectrum rows are overwritten in place; one buffer of kIrRows rows.
+struct IRowIrSmem {
+  size_t tw, raw, mbar, total;
+};
+__host__ __device__ inline IRowIrSmem irow_ir_layout(int N, int Pw2p) {
+  IRowIrSmem L;
+  size_t o = 0;
+  L.tw = o;
+  o += rp_align((size_t)2 * N * sizeof(cf));
+  L.raw = o;
+  o += rp_align((size_t)kIrRows * Pw2p * sizeof(cf));
+  L.mbar = o;
+  o += rp_align(sizeof(uint64_t));
+  L.total = o;
+  return L;
+}
+
+template <int N1, int N2>
+__global__ void __launch_bounds__(kIrThreads, 2) k_row_ifft_ir(IRowArgs a, const cf* tw_w) {
+  constexpr int N = N1 * N2;
+  extern __shared__ __align__(16) char smem[];
+  const IRowIrSmem L = irow_ir_layout(N, a.Pw2p);
+  cf* tws = (cf*)(smem + L.tw);
+  cf* const raw = (cf*)(smem + L.raw);
+  uint64_t* bar = (uint64_t*)(smem + L.mbar);
+  const int tid = threadIdx.x;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  for (int k = tid; k < 2 * N; k += kIrThreads) tws[k] = ldg_cpx(tw_w + k);
+  __syncthreads();
+  uint32_t par = 0u;
+  const int fc = blockIdx.y;
+  const int x0 = blockIdx.x, X = gridDim.x;
+  const int nrows = x0 < a.H ? (a.H - x0 + X - 1) / X : 0;
+  const int ngroups = (nrows + kIrRows - 1) / kIrRows;
+  auto row_of = [&](int g, int i) { return x0 + (g * kIrRows + i) * X; };
+  const cf* src = (const cf*)a.ihat + (int64_t)fc * a.H * a.Pw2p;
+  float* outp = (float*)a.latent + (int64_t)fc * a.H * a.W;
+  const float sc2 = (float)(2.0 * a.scale);
+  if (ngroups > 0)
+    stage_spec_rows_bulk<float>(raw, [&](int i) { return src + (int64_t)row_of(0, i) * a.Pw2p; },
+                                min(kIrRows, nrows), a.Pw2p, bar);
+  const int warp = tid >> 5, lane = tid & 31;
+  for (int g = 0; g < ngroups; ++g) {
+    const int nr = min(kIrRows, nrows - g * kIrRows);
+    const bool arrived = mbar_wait(bar, par, kWaitLimit);
+    par ^= 1u;
+    if (__syncthreads_or(!arrived)) {
+      if (tid == 0) atomicOr(a.err, 1);
+      return;
+    }
+    // ---- step A: one warp per row, lane k2
+    const bool ta = warp < nr && lane < N2;
+    const int k2 = lane;
+    cf x[N1];
+    if (ta) {
+      const cf* X_ = raw + warp * a.Pw2p;
+      const cf* tw = tws + k2;
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) {
+        const int k = k2 + N2 * k1;                 // < N
+        const cf xk = X_[k], xc = conj(X_[N - k]);
+        const cf e = 0.5f * (xk + xc), d = 0.5f * (xk - xc);
+        const cf o = conj(tw[N2 * k1]) * d;        // w_Pw^-k d
+        x[k1] = mk(e.re - o.im, e.im + o.re);       // E + i O
+      }
+      static_assert(N2 <= 32, "one lane per k2");
+      reg_dft<true, N1>(x);
+      const cf* tn = tws + 2 * k2;                  // w_N^(n1 k2) = w_Pw^(2 n1 k2)
+#pragma unroll
+      for (int n1 = 1; n1 < N1; ++n1) x[reg_pos<N1>(n1)] = x[reg_pos<N1>(n1)] * conj(tn[2 * k2 * (n1 - 1)]);
+    }
+    __syncthreads();
+    if (ta) {
+      cf* z = raw + warp * a.Pw2p + N1 * k2;
+      const int sw = (k2 >> 2) & 3;
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1) z[n1 ^ sw] = x[reg_pos<N1>(n1)];
+    }
+    __syncthreads();
+    // ---- step B: per (row, n1), the N2-point inverse DFT over k2, rows out
+    if (tid < nr * N1) {
+      const int i = tid / N1, n1 = tid - i * N1;
+      const cf* z = raw + i * a.Pw2p;
+      const cf* q[4];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) q[c] = z + (n1 ^ c);
+      cf y[N2];
+#pragma unroll
+      for (int kk = 0; kk < N2; ++kk) y[kk] = q[(kk >> 2) & 3][N1 * kk];
+      reg_dft<true, N2>(y);
+      float* o = outp + (int64_t)row_of(g, i) * a.W;
+#pragma unroll
+      for (int n2 = 0; n2 < N2; ++n2) {
+        const int c = 2 * (n1 + N1 * n2);
+        const cf v = y[reg_pos<N2>(n2)];
+        if (c + 1 < a.W) *(float2*)(o + c) = make_float2(sc2 * v.re, sc2 * v.im);
+        else if (c < a.W) o[c] = sc2 * v.re;
+      }
+    }
+    fence_proxy_async();
+    __syncthreads();
+    if (g + 1 < ngroups) {
+      const int g1 = g + 1;
+      stage_spec_rows_bulk<float>(raw, [&](int i) { return src + (int64_t)row_of(g1, i) * a.Pw2p; },
+                                  min(kIrRows, nrows - g1 * kIrRows), a.Pw2p, bar);
+    }
+  }
+}
+
 template <typename T>
 void run_kernel_spectra(const Plan& p, char* ws, cudaStream_t st) {
   const cpx<T>* tw_h = (const cpx<T>*)(ws + p.off_tw_h);
@@ -1643,8 +1764,19 @@ void run_row_ifft(const Plan& p, char* ws, void* latent, int out_f64, cudaStream
       break;
     }
   }
-  const size_t sm = irow_layout(plw.n, plw.ntw, p.Pw2p, a.nbr, sizeof(cpx<T>)).total;
   dim3 g((p.H + 31) / 32, p.n * p.C);
+  if constexpr (sizeof(T) == 4) {
+    // in-register transforms: float output rows on 8-byte boundaries, 972 = 36 x 27
+    if (p.pw_half && plw.n == 972 && !out_f64 && !lat_tab && (p.W % 2) == 0 &&
+        ((uintptr_t)latent & 7) == 0) {
+      const size_t smi = irow_ir_layout(plw.n, p.Pw2p).total;
+      cudaFuncSetAttribute(k_row_ifft_ir<36, 27>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smi);
+      cudaFuncSetAttribute(k_row_ifft_ir<36, 27>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+      k_row_ifft_ir<36, 27><<<g, kIrThreads, smi, st>>>(a, (const cf*)(ws + p.off_tw_w));
+      return;
+    }
+  }
+  const size_t sm = irow_layout(plw.n, plw.ntw, p.Pw2p, a.nbr, sizeof(cpx<T>)).total;
   cudaFuncSetAttribute(k_row_ifft<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_row_ifft<T><<<g, kRowPassThreads, sm, st>>>(a, (const cpx<T>*)(ws + p.off_tw_w),
                                                 (const cpx<T>*)(ws + p.off_stw_r));
