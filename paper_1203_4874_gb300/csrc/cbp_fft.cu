@@ -1472,19 +1472,20 @@ k_row_ifft(IRowArgs a, const cpx<T>* tw_w, const cpx<T>* stw) {
 // an N1-point inverse DFT over k1, twiddled by w_N^-(n1 k2); step B: per
 // (row, n1) an N2-point inverse DFT over k2), then x[2m] = Re z[m],
 // x[2m+1] = Im z[m], scaled by 2 / (Ph Pw) and cropped to W.  The staged
-// spectrum rows are overwritten in place; one buffer of kIrRows rows.
+// spectrum rows are overwritten in place; two buffers of kIrRows rows, the
+// next group's copy in flight while one is transformed.
 struct IRowIrSmem {
-  size_t tw, raw, mbar, total;
+  size_t raw0, raw1, mbar, total;
 };
-__host__ __device__ inline IRowIrSmem irow_ir_layout(int N, int Pw2p) {
+__host__ __device__ inline IRowIrSmem irow_ir_layout(int Pw2p) {
   IRowIrSmem L;
   size_t o = 0;
-  L.tw = o;
-  o += rp_align((size_t)2 * N * sizeof(cf));
-  L.raw = o;
+  L.raw0 = o;
+  o += rp_align((size_t)kIrRows * Pw2p * sizeof(cf));
+  L.raw1 = o;
   o += rp_align((size_t)kIrRows * Pw2p * sizeof(cf));
   L.mbar = o;
-  o += rp_align(sizeof(uint64_t));
+  o += rp_align(2 * sizeof(uint64_t));
   L.total = o;
   return L;
 }
@@ -1493,18 +1494,18 @@ template <int N1, int N2>
 __global__ void __launch_bounds__(kIrThreads, 2) k_row_ifft_ir(IRowArgs a, const cf* tw_w) {
   constexpr int N = N1 * N2;
   extern __shared__ __align__(16) char smem[];
-  const IRowIrSmem L = irow_ir_layout(N, a.Pw2p);
-  cf* tws = (cf*)(smem + L.tw);
-  cf* const raw = (cf*)(smem + L.raw);
-  uint64_t* bar = (uint64_t*)(smem + L.mbar);
+  const IRowIrSmem L = irow_ir_layout(a.Pw2p);
+  cf* const raw0 = (cf*)(smem + L.raw0);
+  cf* const raw1 = (cf*)(smem + L.raw1);
+  uint64_t* bars = (uint64_t*)(smem + L.mbar);   // one per staging buffer
   const int tid = threadIdx.x;
   if (tid == 0) {
-    mbar_init(bar, 1);
+    mbar_init(&bars[0], 1);
+    mbar_init(&bars[1], 1);
     fence_mbar_init();
   }
-  for (int k = tid; k < 2 * N; k += kIrThreads) tws[k] = ldg_cpx(tw_w + k);
   __syncthreads();
-  uint32_t par = 0u;
+  uint32_t par = 0u;   // bit b: phase parity of buffer b's next completion
   const int fc = blockIdx.y;
   const int x0 = blockIdx.x, X = gridDim.x;
   const int nrows = x0 < a.H ? (a.H - x0 + X - 1) / X : 0;
@@ -1514,15 +1515,25 @@ __global__ void __launch_bounds__(kIrThreads, 2) k_row_ifft_ir(IRowArgs a, const
   float* outp = (float*)a.latent + (int64_t)fc * a.H * a.W;
   const float sc2 = (float)(2.0 * a.scale);
   if (ngroups > 0)
-    stage_spec_rows_bulk<float>(raw, [&](int i) { return src + (int64_t)row_of(0, i) * a.Pw2p; },
-                                min(kIrRows, nrows), a.Pw2p, bar);
+    stage_spec_rows_bulk<float>(raw0, [&](int i) { return src + (int64_t)row_of(0, i) * a.Pw2p; },
+                                min(kIrRows, nrows), a.Pw2p, &bars[0]);
   const int warp = tid >> 5, lane = tid & 31;
   for (int g = 0; g < ngroups; ++g) {
     const int nr = min(kIrRows, nrows - g * kIrRows);
-    const bool arrived = mbar_wait(bar, par, kWaitLimit);
-    par ^= 1u;
+    cf* const raw = (g & 1) ? raw1 : raw0;
+    if (g + 1 < ngroups) {
+      const int g1 = g + 1;
+      stage_spec_rows_bulk<float>((g1 & 1) ? raw1 : raw0,
+                                  [&](int i) { return src + (int64_t)row_of(g1, i) * a.Pw2p; },
+                                  min(kIrRows, nrows - g1 * kIrRows), a.Pw2p, &bars[g1 & 1]);
+    }
+    const bool arrived = mbar_wait(&bars[g & 1], (par >> (g & 1)) & 1u, kWaitLimit);
+    par ^= 1u << (g & 1);
     if (__syncthreads_or(!arrived)) {
+      // a copy did not complete in time: report it, wait (bounded) for the
+      // other buffer's copy still in flight, and leave
       if (tid == 0) atomicOr(a.err, 1);
+      if (g + 1 < ngroups) mbar_wait(&bars[(g + 1) & 1], (par >> ((g + 1) & 1)) & 1u, kWaitLimit);
       return;
     }
     // ---- step A: one warp per row, lane k2
@@ -1531,20 +1542,21 @@ __global__ void __launch_bounds__(kIrThreads, 2) k_row_ifft_ir(IRowArgs a, const
     cf x[N1];
     if (ta) {
       const cf* X_ = raw + warp * a.Pw2p;
-      const cf* tw = tws + k2;
+      const cf* tw = tw_w + k2;
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) {
         const int k = k2 + N2 * k1;                 // < N
         const cf xk = X_[k], xc = conj(X_[N - k]);
         const cf e = 0.5f * (xk + xc), d = 0.5f * (xk - xc);
-        const cf o = conj(tw[N2 * k1]) * d;        // w_Pw^-k d
+        const cf o = conj(ldg_cpx(tw + N2 * k1)) * d;   // w_Pw^-k d
         x[k1] = mk(e.re - o.im, e.im + o.re);       // E + i O
       }
       static_assert(N2 <= 32, "one lane per k2");
       reg_dft<true, N1>(x);
-      const cf* tn = tws + 2 * k2;                  // w_N^(n1 k2) = w_Pw^(2 n1 k2)
+      const cf* tn = tw_w + 2 * k2;                 // w_N^(n1 k2) = w_Pw^(2 n1 k2)
 #pragma unroll
-      for (int n1 = 1; n1 < N1; ++n1) x[reg_pos<N1>(n1)] = x[reg_pos<N1>(n1)] * conj(tn[2 * k2 * (n1 - 1)]);
+      for (int n1 = 1; n1 < N1; ++n1)
+        x[reg_pos<N1>(n1)] = x[reg_pos<N1>(n1)] * conj(ldg_cpx(tn + 2 * k2 * (n1 - 1)));
     }
     __syncthreads();
     if (ta) {
@@ -1574,13 +1586,10 @@ __global__ void __launch_bounds__(kIrThreads, 2) k_row_ifft_ir(IRowArgs a, const
         else if (c < a.W) o[c] = sc2 * v.re;
       }
     }
+    // this buffer is rewritten by the copy issued two groups on: order its
+    // generic-proxy accesses first
     fence_proxy_async();
     __syncthreads();
-    if (g + 1 < ngroups) {
-      const int g1 = g + 1;
-      stage_spec_rows_bulk<float>(raw, [&](int i) { return src + (int64_t)row_of(g1, i) * a.Pw2p; },
-                                  min(kIrRows, nrows - g1 * kIrRows), a.Pw2p, bar);
-    }
   }
 }
 
@@ -1769,7 +1778,7 @@ void run_row_ifft(const Plan& p, char* ws, void* latent, int out_f64, cudaStream
     // in-register transforms: float output rows on 8-byte boundaries, 972 = 36 x 27
     if (p.pw_half && plw.n == 972 && !out_f64 && !lat_tab && (p.W % 2) == 0 &&
         ((uintptr_t)latent & 7) == 0) {
-      const size_t smi = irow_ir_layout(plw.n, p.Pw2p).total;
+      const size_t smi = irow_ir_layout(p.Pw2p).total;
       cudaFuncSetAttribute(k_row_ifft_ir<36, 27>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smi);
       cudaFuncSetAttribute(k_row_ifft_ir<36, 27>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
       k_row_ifft_ir<36, 27><<<g, kIrThreads, smi, st>>>(a, (const cf*)(ws + p.off_tw_w));
