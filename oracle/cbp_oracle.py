@@ -287,3 +287,58 @@ def deblur_pair(b1, b2, t1: int, t2: int, m: int | None = None, eps: float = 1e-
     w = b1.shape[2] - t1 + 1
     out["latent"] = deconvolve_dual(b1, b2, k1, k2, h, w, eps, ph, pw)
     return out
+
+
+# ------------------------------------------------------- kernel-size estimation
+def plane_sums(b: np.ndarray):
+    """The z = 1 samples of both evaluation orders (Eq. 3 at z2 = 1 and z1 = 1):
+    row sums (C, H_B) and column sums (C, W_B) of a frame."""
+    b = np.asarray(b, dtype=np.float64)
+    return b.sum(axis=2), b.sum(axis=1)
+
+
+def size_ratios(b1: np.ndarray, b2: np.ndarray, t_min: int, t_max: int):
+    """Singularity test of the kernel-degree step (Section 4: the degree is read
+    from the singularity of the cofactor system; Section 5: square candidates in
+    a fixed range).  Under full convolution the blurred sizes fix d = t1 - t2;
+    for each candidate t1' in [t_min, t_max] (t2' = t1' - d) the Sylvester
+    system of the z = 1 samples is built for both evaluation orders and its
+    sigma_min / sigma_max taken by SVD.  The system has a null vector exactly
+    when t1' >= t1 (then u = k1 s, v = k2 s for any s of degree t1' - t1), so
+    the ratio drops to the noise floor at the true size.  Returns
+    (d, {t1': max over the two orders of sigma_min / sigma_max})."""
+    b1 = np.asarray(b1, dtype=np.float64)
+    b2 = np.asarray(b2, dtype=np.float64)
+    if b1.ndim == 2:
+        b1, b2 = b1[None], b2[None]
+    d = b1.shape[1] - b2.shape[1]
+    if b1.shape[2] - b2.shape[2] != d:
+        raise ValueError("blurred sizes disagree on t1 - t2")
+    r1, c1 = plane_sums(b1)
+    r2, c2 = plane_sums(b2)
+    out = {}
+    for t1 in range(t_min, t_max + 1):
+        t2 = t1 - d
+        if t2 < 1 or t1 < 1:
+            continue
+        worst = 0.0
+        for p1, p2 in ((r1, r2), (c1, c2)):
+            sv = np.linalg.svd(sylvester_system(p1, p2, t1, t2), compute_uv=False)
+            worst = max(worst, sv[-1] / sv[0])
+        out[t1] = worst
+    return d, out
+
+
+def estimate_size(b1, b2, t_min: int = 1, t_max: int = 32, tol: float = 1e-6):
+    """Kernel degree (Section 4, Section 5): the smallest candidate whose system
+    is numerically singular (sigma_min / sigma_max <= tol); when none is, the
+    largest candidate (Section 5 falls back to its largest size).  Returns
+    (t1, t2, found, ratios)."""
+    d, ratios = size_ratios(b1, b2, t_min, t_max)
+    if not ratios:
+        raise ValueError("no valid candidate size")
+    for t1 in sorted(ratios):
+        if ratios[t1] <= tol:
+            return t1, t1 - d, True, ratios
+    t1 = max(ratios)
+    return t1, t1 - d, False, ratios
