@@ -100,6 +100,15 @@ typedef struct cbp_params {
   int32_t reserved;
 } cbp_params;
 
+/* Candidate range and tolerance of the kernel-size scan (cbp_estimate_size). */
+typedef struct cbp_size_params {
+  int32_t t_min;      /* smallest candidate t1; 0 => 1                            */
+  int32_t t_max;      /* largest candidate t1; 0 => 32 (capped by t1 + t2 <= 64 and
+                         the frame size)                                           */
+  double tol;         /* a candidate is singular when sigma_min / sigma_max <= tol;
+                         0 => 1e-6                                                 */
+} cbp_size_params;
+
 /* Per-pair diagnostics, computed on the device (one entry per batch entry). */
 typedef struct cbp_diag {
   double kappa_max;     /* max over samples of sigma_1 / sigma_{n-1}               */
@@ -135,6 +144,30 @@ const char* cbp_status_string(cbp_status s);
  * arguments needs (bytes, written to *bytes).  No device work. */
 cbp_status cbp_workspace_size(const cbp_frames* b1, const cbp_frames* b2,
                               const cbp_params* params, size_t* bytes);
+
+/* Kernel-size estimation for a batch of frame pairs (Section 4: the degree
+ * of the blur kernels comes first, from the singularity of the cofactor
+ * system; Section 5: a scan over square candidate sizes that falls back to
+ * the largest when no candidate is singular).  Under full convolution the
+ * blurred sizes fix d = t1 - t2 = H_B1 - H_B2 = W_B1 - W_B2 (else
+ * CBP_ERR_SIZE_MISMATCH).  For every candidate t1' (t2' = t1' - d) the
+ * Sylvester system of the z = 1 samples (row sums for the z2-first order,
+ * column sums for the z1-first order; channels' rows stacked) is formed and
+ * ratio(t1') = sigma_min / sigma_max taken, the larger of the two orders'; the
+ * system has a null vector exactly when t1' >= t1.  The estimate is the
+ * smallest candidate with ratio <= tol, else the largest candidate.
+ * params: NULL or the candidate range and tolerance.
+ * t1_out, t2_out: host arrays of n entries; found: NULL or host array of n
+ * (1: a singular candidate was found, 0: the fallback); ratios: NULL or host
+ * array [n][ncand] with ncand = t_max - t_min + 1 after the caps (-1 marks a
+ * candidate the caps exclude) -- all filled by asynchronous copies on the
+ * stream, valid after it is synchronised (pinned memory recommended).
+ * *ncand_out: NULL or the number of candidates (set before returning).
+ * Errors: CBP_ERR_INVALID_ARG, CBP_ERR_SIZE_MISMATCH, CBP_ERR_BUDGET,
+ * CBP_ERR_OOM, CBP_ERR_CUDA. */
+cbp_status cbp_estimate_size(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
+                             const cbp_size_params* params, int32_t* t1_out, int32_t* t2_out,
+                             int32_t* found, double* ratios, int32_t* ncand_out, void* stream);
 
 /* Blind kernel estimation for a batch of frame pairs (Sections 4-5):
  *   1. evaluation of both frames' z-polynomials at the m-th roots of unity in

@@ -29,10 +29,14 @@ EXPORTED = [
     "cbp_estimate_kernels", "cbp_deblur_pair", "cbp_forward_blur", "cbp_synth_latent",
     "cbp_stream_submit", "cbp_stream_poll", "cbp_stream_stats", "cbp_profile", "cbp_stage_times",
     "cbp_estimate_kernels_stages", "cbp_estimate_kernels_noalloc", "cbp_cnn_param_count",
-    "cbp_cnn_forward", "cbp_cnn_train_step", "cbp_learned_load",
+    "cbp_cnn_forward", "cbp_cnn_train_step", "cbp_learned_load", "cbp_estimate_size",
 ]
 STAGES = ["eval", "sample_solve", "scale_solve", "kernel_spectra", "row_fft", "col_deconv",
           "row_ifft", "h2d", "d2h", "proposal", "gate"]
+
+
+class cbp_size_params(ctypes.Structure):
+    _fields_ = [("t_min", c_int32), ("t_max", c_int32), ("tol", c_double)]
 
 
 class cbp_frames(ctypes.Structure):
@@ -110,6 +114,9 @@ def lib() -> ctypes.CDLL:
             "cbp_cnn_train_step": ([c_void_p, fr, fr, c_void_p, c_void_p, c_void_p, c_void_p,
                                     POINTER(cbp_adamw), c_void_p, POINTER(cbp_cnn_trace), c_void_p], c_int),
             "cbp_learned_load": ([c_void_p, ctypes.c_char_p], c_int),
+            "cbp_estimate_size": ([c_void_p, fr, fr, POINTER(cbp_size_params), POINTER(c_int32),
+                                   POINTER(c_int32), POINTER(c_int32), POINTER(c_double),
+                                   POINTER(c_int32), c_void_p], c_int),
         }
         for name, (args, res) in sig.items():
             f = getattr(L, name)
@@ -319,6 +326,30 @@ def cbp_estimate_kernels_stages(ctx, b1: torch.Tensor, b2: torch.Tensor, prm: cb
     _check(st, "cbp_estimate_kernels_stages")
     out["k1"], out["k2"], out["diag"] = k1, k2, d
     return out
+
+
+def cbp_estimate_size(ctx, b1: torch.Tensor, b2: torch.Tensor, t_min: int = 0, t_max: int = 0,
+                      tol: float = 0.0, stream=None):
+    """Kernel-size scan of a batch on the device.  Synchronises the stream and
+    returns (t1 list, t2 list, found list, ratios as an (n, ncand) float64
+    tensor over the candidates t_min.. after the library's caps, -1 marking
+    excluded ones)."""
+    n = _batch(b1)
+    sp = cbp_size_params(t_min, t_max, tol)
+    nc = c_int32()
+    cap = 64                      # candidates never exceed t1 + t2 <= 64
+    t1 = (c_int32 * n)()
+    t2 = (c_int32 * n)()
+    fd = (c_int32 * n)()
+    ratios = torch.empty((n, cap), dtype=torch.float64).pin_memory() if torch.cuda.is_available() \
+        else torch.empty((n, cap), dtype=torch.float64)
+    rp = ctypes.cast(ratios.data_ptr(), POINTER(c_double))
+    _check(lib().cbp_estimate_size(ctx, byref(frames(b1)), byref(frames(b2)), byref(sp), t1, t2, fd,
+                                   rp, byref(nc), _stream_ptr(stream)), "cbp_estimate_size")
+    torch.cuda.synchronize()
+    k = nc.value
+    r = ratios.flatten()[:n * k].reshape(n, k).clone()
+    return list(t1), list(t2), [bool(x) for x in fd], r
 
 
 def cbp_estimate_kernels_noalloc(b1: torch.Tensor, b2: torch.Tensor, prm: cbp_params, k1: torch.Tensor,

@@ -328,6 +328,38 @@ cbp_frames frames_slice(const cbp_frames* f, int start, int count) {
   return s;
 }
 
+// Kernel-size scan of a batch on the device, results copied to the host.
+cbp_status size_scan(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
+                     const cbp_size_params* sprm, int32_t* t1_out, int32_t* t2_out,
+                     int32_t* found, double* ratios, int32_t* ncand_out, void* stream) {
+  if (!ctx || !t1_out || !t2_out) return CBP_ERR_INVALID_ARG;
+  Ctx* c = reinterpret_cast<Ctx*>(ctx);
+  cbp::SizePlan sp;
+  cbp_status s = cbp::make_size_plan(b1, b2, sprm, &sp);
+  if (s != CBP_OK) return s;
+  if (ncand_out) *ncand_out = sp.ncand;
+  DeviceGuard g(c->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lk(c->api_mu);
+  s = c->ensure_ws(sp.total, st);
+  if (s != CBP_OK) return s;
+  const cbp::FrameDesc d1 = cbp::frame_desc(b1, nullptr), d2 = cbp::frame_desc(b2, nullptr);
+  cbp::launch_size_scan(sp, d1, d2, c->ws, st);
+  if (cudaGetLastError() != cudaSuccess) return CBP_ERR_CUDA;
+  // t out as [n][3] ints on the device: t1, t2, found
+  const int* tdev = (const int*)(c->ws + sp.off_t);
+  for (int k = 0; k < 3; ++k) {
+    int32_t* dst = k == 0 ? t1_out : k == 1 ? t2_out : found;
+    if (dst && cudaMemcpy2DAsync(dst, sizeof(int32_t), tdev + k, 3 * sizeof(int), sizeof(int32_t),
+                                 sp.n, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+      return CBP_ERR_CUDA;
+  }
+  if (ratios && cudaMemcpyAsync(ratios, c->ws + sp.off_rmax, (size_t)sp.n * sp.ncand * sizeof(double),
+                                cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    return CBP_ERR_CUDA;
+  return CBP_OK;
+}
+
 cbp_status call_path(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
                      const cbp_params* prm, void* k1, void* k2, void* latent, cbp_diag* diag,
                      void* stream, bool deblur, const cbp_stage_out* stages = nullptr) {
@@ -632,6 +664,12 @@ cbp_status cbp_stage_times(cbp_ctx* ctx, double* ms, int64_t* launches) {
     P.launches[i] = 0;
   }
   return st;
+}
+
+cbp_status cbp_estimate_size(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
+                             const cbp_size_params* params, int32_t* t1_out, int32_t* t2_out,
+                             int32_t* found, double* ratios, int32_t* ncand_out, void* stream) {
+  return size_scan(ctx, b1, b2, params, t1_out, t2_out, found, ratios, ncand_out, stream);
 }
 
 }  // extern "C"

@@ -97,11 +97,25 @@ struct Plan {
   size_t total;
 };
 
+// Kernel-size scan of a batch (cbp_estimate_size): candidates t1' in
+// [t_min, t_min + ncand), t2' = t1' - d; workspace layout.
+struct SizePlan {
+  int n, C, d, t_min, ncand;
+  double tol;
+  size_t off_rows[2], off_cols[2];   // cd [n][C][H_k] row sums, [n][C][W_k] column sums
+  size_t off_ratio;                  // double [n][2][ncand] per order
+  size_t off_rmax;                   // double [n][ncand] the larger of the two (-1: excluded)
+  size_t off_t;                      // int [n][3]: t1, t2, found
+  size_t total;
+};
+
 // ---- planning (cbp_plan.cpp) ----
 int next_7_smooth(int n);
 bool make_fft_plan(int n, FftPlan* p);
 cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_params* prm,
                      Plan* plan);
+cbp_status make_size_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_size_params* sp,
+                          SizePlan* plan);
 FrameDesc frame_desc(const cbp_frames* f, const void* data_override);
 
 // ---- launchers (one per .cu file) ----
@@ -154,6 +168,10 @@ void launch_forward_blur(const void* latent, int n, int c, int h, int w, int f64
 void launch_synth_latent(const double* blobs, int nblobs, int n, int c, int h, int w, int f64,
                          double floor_amp, uint64_t seed, void* out, cudaStream_t st);
 size_t sample_solve_smem(int nn);
+// kernel-size scan (cbp_solve.cu): plane sums, per-candidate ratios, the pick
+void launch_size_scan(const SizePlan& sp, const FrameDesc& b1, const FrameDesc& b2, char* ws,
+                      cudaStream_t st);
+size_t size_scan_smem();
 size_t scale_solve_smem(int M);
 
 }  // namespace cbp

@@ -215,4 +215,43 @@ cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_param
   return CBP_OK;
 }
 
+cbp_status make_size_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_size_params* sp,
+                          SizePlan* P) {
+  if (!valid_frames(b1) || !valid_frames(b2)) return CBP_ERR_INVALID_ARG;
+  if (b1->n != b2->n || b1->c != b2->c || b1->dtype != b2->dtype) return CBP_ERR_INVALID_ARG;
+  // full convolution: both blurred sizes differ by t1 - t2
+  const int d = b1->h - b2->h;
+  if (b1->w - b2->w != d) return CBP_ERR_SIZE_MISMATCH;
+  SizePlan p = {};
+  p.n = b1->n;
+  p.C = b1->c;
+  p.d = d;
+  const int lo_valid = std::max(1, d + 1);                 // t2' = t1' - d >= 1
+  int hi_valid = std::min(b1->h, b1->w);                   // a latent of at least one pixel
+  hi_valid = std::min(hi_valid, (kMaxN + d) / 2);          // t1' + t2' <= kMaxN
+  p.t_min = std::max(sp && sp->t_min > 0 ? sp->t_min : 1, lo_valid);
+  const int t_max = std::min(sp && sp->t_max > 0 ? sp->t_max : 32, hi_valid);
+  if (t_max < p.t_min) return CBP_ERR_INVALID_ARG;
+  p.ncand = t_max - p.t_min + 1;
+  p.tol = sp && sp->tol > 0.0 ? sp->tol : 1e-6;
+  if (!std::isfinite(p.tol)) return CBP_ERR_INVALID_ARG;
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off += align_up(bytes);
+    return o;
+  };
+  const size_t n = p.n, C = p.C;
+  p.off_rows[0] = take(n * C * (size_t)b1->h * 16);
+  p.off_rows[1] = take(n * C * (size_t)b2->h * 16);
+  p.off_cols[0] = take(n * C * (size_t)b1->w * 16);
+  p.off_cols[1] = take(n * C * (size_t)b2->w * 16);
+  p.off_ratio = take(n * 2 * (size_t)p.ncand * 8);
+  p.off_rmax = take(n * (size_t)p.ncand * 8);
+  p.off_t = take(n * 3 * sizeof(int));
+  p.total = off;
+  *P = p;
+  return CBP_OK;
+}
+
 }  // namespace cbp

@@ -25,6 +25,7 @@
 // eigen-solver on its 2M x 2M normal matrix, one exact-residual step on the
 // FP64 path), average,
 // normalise to unit kernel sum, inverse M x M DFT (Section 5).
+#include <algorithm>
 #include "cbp_common.cuh"
 #include "cbp_internal.h"
 #ifdef CBP_PHASE_TIMING
@@ -925,6 +926,91 @@ __global__ void k_kernels_in(const void* k1, const void* k2, int in_f64, int n, 
   }
 }
 
+// ------------------------------------------------- kernel-size estimation ---
+// The kernel degree (Section 4: read from the singularity of the cofactor
+// system; Section 5: a scan of candidate sizes with a fallback to the
+// largest).  Under full convolution the blurred sizes fix d = t1 - t2; for
+// candidate t1' (t2' = t1' - d) the Sylvester system of the z = 1 samples
+// (row sums, column sums) has a null vector exactly when t1' >= t1.  One CTA
+// per (candidate, order, pair) forms the real normal matrix from the
+// correlations and takes its extreme eigenvalues with the tridiagonal solver
+// (no refinement steps): ratio = sqrt(lambda_min / lambda_max).
+
+// z = 1 samples of a frame batch: row sums [n][C][h] and column sums
+// [n][C][w] (imaginary parts zero), accumulated in double.
+__global__ void k_plane_sums(FrameDesc fr, cd* rows, cd* cols) {
+  const int fc = blockIdx.y, f = fc / fr.c, ch = fc % fr.c;
+  const char* base = (const char*)frame_base(fr, f) + (int64_t)ch * fr.cs * (fr.f64 ? 8 : 4);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (blockIdx.z == 0) {
+    for (int r = blockIdx.x * nw + warp; r < fr.h; r += gridDim.x * nw) {
+      double acc = 0.0;
+      for (int c = lane; c < fr.w; c += 32) acc += ld_frame<double>(base, (int64_t)r * fr.rs + c, fr.f64);
+      acc = warp_sum(acc);
+      if (lane == 0) rows[(int64_t)fc * fr.h + r] = mk(acc, 0.0);
+    }
+  } else {
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < fr.w; c += gridDim.x * blockDim.x) {
+      double acc = 0.0;
+      for (int r = 0; r < fr.h; ++r) acc += ld_frame<double>(base, (int64_t)r * fr.rs + c, fr.f64);
+      cols[(int64_t)fc * fr.w + c] = mk(acc, 0.0);
+    }
+  }
+}
+
+struct SizeScanArgs {
+  const cd* pz[2][2];   // [order][frame]: z = 1 samples [n][C][len]
+  int len[2][2];
+  int C, t_min, d, ncand;
+  double* ratio;        // [n][2][ncand]; -1 for an invalid candidate
+};
+
+// The refinement steps are off in the scan: an operator that is never applied.
+struct NoApply {
+  __device__ void operator()(const cd*, cd*) const {}
+};
+
+__global__ void __launch_bounds__(kSolveThreads) k_size_scan(SizeScanArgs a) {
+  extern __shared__ __align__(16) char smem[];
+  const int cand = blockIdx.x, ps = blockIdx.y, f = blockIdx.z;
+  const int t1 = a.t_min + cand, t2 = t1 - a.d, n = t1 + t2;
+  double* out = a.ratio + ((int64_t)f * 2 + ps) * a.ncand + cand;
+  if (t1 < 1 || t2 < 1 || n > kMaxN || n < 2) {
+    if (threadIdx.x == 0) *out = -1.0;
+    return;
+  }
+  cd* G = (cd*)smem;                                    // [n][n]
+  cd* rho = G + kMaxN * kMaxN;                          // [2 n - 1]
+  const TriWs W = carve_tri(smem + sizeof(cd) * (kMaxN * kMaxN + 2 * kMaxN), n);
+  const SamplePolys<double, double> P = sample_polys<double, double>(a.pz[ps], a.len[ps], f, a.C, 1, 0);
+  correlations_real(P, a.C, t1, t2, rho);
+  gram_from_rho(rho, t1, t2, G);
+  const TriResult res = tri_smallest<double, true>(W, G, n, 0, 0, 1e300, NoApply{});
+  if (threadIdx.x == 0) *out = res.lam_max > 0.0 ? sqrt(fmax(res.lam_min, 0.0) / res.lam_max) : 0.0;
+}
+
+// Per pair: the smallest candidate whose ratio (the larger of the two
+// orders') is at most tol, else the largest valid candidate.
+__global__ void k_size_pick(const double* ratio, int n, int ncand, int t_min, int d, double tol,
+                            int* t_out /* [n][3]: t1, t2, found */, double* rmax /* [n][ncand] */) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n) return;
+  int best = -1, last = -1;
+  for (int c = 0; c < ncand; ++c) {
+    const double r0 = ratio[((int64_t)f * 2 + 0) * ncand + c];
+    const double r1 = ratio[((int64_t)f * 2 + 1) * ncand + c];
+    const bool valid = r0 >= 0.0 && r1 >= 0.0;
+    rmax[(int64_t)f * ncand + c] = valid ? fmax(r0, r1) : -1.0;
+    if (!valid) continue;
+    last = c;
+    if (best < 0 && fmax(r0, r1) <= tol) best = c;
+  }
+  const int c = best >= 0 ? best : last;
+  t_out[3 * f + 0] = c >= 0 ? t_min + c : 0;
+  t_out[3 * f + 1] = c >= 0 ? t_min + c - d : 0;
+  t_out[3 * f + 2] = best >= 0 ? 1 : 0;
+}
+
 }  // namespace
 
 size_t sample_solve_smem(int nn) { return tri_ws_bytes(nn); }
@@ -1006,6 +1092,38 @@ void launch_kernels_in(const Plan& p, char* ws, const void* k1, const void* k2, 
   k_kernels_in<<<blocks, 256, 0, st>>>(k1, k2, in_f64, p.n, p.t1, p.t2, (double*)(ws + p.off_kd),
                                        (cbp_diag*)(ws + p.off_diag), p.Ph, p.Pw,
                                        (const int*)(ws + p.off_bad), k1_tab, k2_tab);
+}
+
+size_t size_scan_smem() {
+  return sizeof(cd) * (kMaxN * kMaxN + 2 * kMaxN) + tri_ws_bytes(kMaxN);
+}
+
+void launch_size_scan(const SizePlan& sp, const FrameDesc& b1, const FrameDesc& b2, char* ws,
+                      cudaStream_t st) {
+  const FrameDesc* fr[2] = {&b1, &b2};
+  for (int k = 0; k < 2; ++k) {
+    dim3 g(std::max(1, std::min(64, (std::max(fr[k]->h, fr[k]->w) + 255) / 256)), sp.n * sp.C, 2);
+    k_plane_sums<<<g, 256, 0, st>>>(*fr[k], (cd*)(ws + sp.off_rows[k]), (cd*)(ws + sp.off_cols[k]));
+  }
+  SizeScanArgs a;
+  for (int k = 0; k < 2; ++k) {
+    a.pz[0][k] = (const cd*)(ws + sp.off_rows[k]);
+    a.pz[1][k] = (const cd*)(ws + sp.off_cols[k]);
+  }
+  a.len[0][0] = b1.h;
+  a.len[0][1] = b2.h;
+  a.len[1][0] = b1.w;
+  a.len[1][1] = b2.w;
+  a.C = sp.C;
+  a.t_min = sp.t_min;
+  a.d = sp.d;
+  a.ncand = sp.ncand;
+  a.ratio = (double*)(ws + sp.off_ratio);
+  const size_t sm = size_scan_smem();
+  cudaFuncSetAttribute(k_size_scan, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_size_scan<<<dim3(sp.ncand, 2, sp.n), kSolveThreads, sm, st>>>(a);
+  k_size_pick<<<(sp.n + 127) / 128, 128, 0, st>>>(a.ratio, sp.n, sp.ncand, sp.t_min, sp.d, sp.tol,
+                                                 (int*)(ws + sp.off_t), (double*)(ws + sp.off_rmax));
 }
 
 }  // namespace cbp
