@@ -934,7 +934,8 @@ __global__ void k_kernels_in(const void* k1, const void* k2, int in_f64, int n, 
 // (row sums, column sums) has a null vector exactly when t1' >= t1.  One CTA
 // per (candidate, order, pair) forms the real normal matrix from the
 // correlations and takes its extreme eigenvalues with the tridiagonal solver
-// (no refinement steps): ratio = sqrt(lambda_min / lambda_max).
+// (no refinement steps): ratio = sqrt(theta / lambda_max), theta the
+// Rayleigh quotient of the smallest eigenvector.
 
 // z = 1 samples of a frame batch: row sums [n][C][h] and column sums
 // [n][C][w] (imaginary parts zero), accumulated in double.
@@ -986,7 +987,9 @@ __global__ void __launch_bounds__(kSolveThreads) k_size_scan(SizeScanArgs a) {
   correlations_real(P, a.C, t1, t2, rho);
   gram_from_rho(rho, t1, t2, G);
   const TriResult res = tri_smallest<double, true>(W, G, n, 0, 0, 1e300, NoApply{});
-  if (threadIdx.x == 0) *out = res.lam_max > 0.0 ? sqrt(fmax(res.lam_min, 0.0) / res.lam_max) : 0.0;
+  // the Rayleigh quotient of the converged vector (the multisection bracket
+  // is only narrowed as far as the eigenvector needs)
+  if (threadIdx.x == 0) *out = res.lam_max > 0.0 ? sqrt(fmax(res.theta, 0.0) / res.lam_max) : 0.0;
 }
 
 // Per pair: the smallest candidate whose ratio (the larger of the two
