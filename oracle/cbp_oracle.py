@@ -342,3 +342,19 @@ def estimate_size(b1, b2, t_min: int = 1, t_max: int = 32, tol: float = 1e-6):
             return t1, t1 - d, True, ratios
     t1 = max(ratios)
     return t1, t1 - d, False, ratios
+
+
+# ------------------------------------------------------ multi-level security
+def truncate_lsb(b: np.ndarray, bits: int, drop: int) -> np.ndarray:
+    """Multi-level access to the private stream (Section 3, "Multi-level
+    Security"): a lower clearance level receives the blurred frames with the
+    least significant bits removed.  Reading: intensities in [0, 1] are coded
+    as unsigned integers of `bits` bits, code = rint(x (2^bits - 1)) clamped to
+    [0, 2^bits - 1]; level `drop` clears the code's `drop` lowest bits; the
+    value it sees is code / (2^bits - 1).  Computed in double precision."""
+    if not (1 <= bits <= 30 and 0 <= drop < bits):
+        raise ValueError("need 1 <= bits <= 30 and 0 <= drop < bits")
+    top = float((1 << bits) - 1)
+    code = np.clip(np.rint(np.asarray(b, dtype=np.float64) * top), 0.0, top).astype(np.int64)
+    code &= ~np.int64((1 << drop) - 1)
+    return code.astype(np.float64) / top
