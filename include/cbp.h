@@ -270,6 +270,18 @@ cbp_status cbp_forward_blur(cbp_ctx* ctx, const void* latent, int32_t n, int32_t
                             int32_t h, int32_t w, cbp_dtype dtype, const double* kernel,
                             int32_t t, double sigma, uint64_t seed, void* out, void* stream);
 
+/* Multi-level security (Section 3): the private stream as a lower clearance
+ * level receives it, with the least significant bits of its pixel codes
+ * removed.  Each of the `count` elements x (intensities nominally in [0, 1])
+ * is coded as code = rint(x (2^bits - 1)) clamped to [0, 2^bits - 1]; the
+ * `drop` lowest bits of the code are cleared and the value
+ * code / (2^bits - 1) written to out (same dtype; out may equal in).  The
+ * arithmetic is double precision for either dtype.  in, out: device buffers.
+ * Errors: CBP_ERR_INVALID_ARG (1 <= bits <= 30, 0 <= drop < bits),
+ * CBP_ERR_CUDA. */
+cbp_status cbp_truncate_lsb(cbp_ctx* ctx, const void* in, cbp_dtype dtype, int64_t count,
+                            int32_t bits, int32_t drop, void* out, void* stream);
+
 /* Synthetic latent frames for benchmarks (stand-in for the paper's camera
  * video, Section 6): for every channel, sum of Gaussian blobs
  * a * exp(-((x-cx)^2 + (y-cy)^2) / (2 s^2)) plus a uniform floor U[0, floor_amp]

@@ -30,6 +30,7 @@ EXPORTED = [
     "cbp_stream_submit", "cbp_stream_poll", "cbp_stream_stats", "cbp_profile", "cbp_stage_times",
     "cbp_estimate_kernels_stages", "cbp_estimate_kernels_noalloc", "cbp_cnn_param_count",
     "cbp_cnn_forward", "cbp_cnn_train_step", "cbp_learned_load", "cbp_estimate_size",
+    "cbp_truncate_lsb",
 ]
 STAGES = ["eval", "sample_solve", "scale_solve", "kernel_spectra", "row_fft", "col_deconv",
           "row_ifft", "h2d", "d2h", "proposal", "gate"]
@@ -114,6 +115,8 @@ def lib() -> ctypes.CDLL:
             "cbp_cnn_train_step": ([c_void_p, fr, fr, c_void_p, c_void_p, c_void_p, c_void_p,
                                     POINTER(cbp_adamw), c_void_p, POINTER(cbp_cnn_trace), c_void_p], c_int),
             "cbp_learned_load": ([c_void_p, ctypes.c_char_p], c_int),
+            "cbp_truncate_lsb": ([c_void_p, c_void_p, c_int, c_int64, c_int32, c_int32, c_void_p,
+                                  c_void_p], c_int),
             "cbp_estimate_size": ([c_void_p, fr, fr, POINTER(cbp_size_params), POINTER(c_int32),
                                    POINTER(c_int32), POINTER(c_int32), POINTER(c_double),
                                    POINTER(c_int32), c_void_p], c_int),
@@ -325,6 +328,19 @@ def cbp_estimate_kernels_stages(ctx, b1: torch.Tensor, b2: torch.Tensor, prm: cb
                                            _stream_ptr(stream))
     _check(st, "cbp_estimate_kernels_stages")
     out["k1"], out["k2"], out["diag"] = k1, k2, d
+    return out
+
+
+def cbp_truncate_lsb(ctx, x: torch.Tensor, bits: int, drop: int, out: torch.Tensor | None = None,
+                     stream=None) -> torch.Tensor:
+    """The frames `x` (device, float32/float64, contiguous) with the `drop`
+    least significant bits of their `bits`-bit codes removed (Section 3)."""
+    if not x.is_contiguous():
+        raise ValueError("contiguous frames expected")
+    out = torch.empty_like(x) if out is None else out
+    dt = CBP_F64 if x.dtype == torch.float64 else CBP_F32
+    _check(lib().cbp_truncate_lsb(ctx, x.data_ptr(), dt, x.numel(), bits, drop, out.data_ptr(),
+                                  _stream_ptr(stream)), "cbp_truncate_lsb")
     return out
 
 

@@ -622,6 +622,18 @@ cbp_status cbp_forward_blur(cbp_ctx* ctx, const void* latent, int32_t n, int32_t
   return cudaGetLastError() == cudaSuccess ? CBP_OK : CBP_ERR_CUDA;
 }
 
+cbp_status cbp_truncate_lsb(cbp_ctx* ctx, const void* in, cbp_dtype dtype, int64_t count,
+                            int32_t bits, int32_t drop, void* out, void* stream) {
+  if (!ctx || !in || !out || count < 0 || bits < 1 || bits > 30 || drop < 0 || drop >= bits ||
+      (dtype != CBP_F32 && dtype != CBP_F64))
+    return CBP_ERR_INVALID_ARG;
+  if (count == 0) return CBP_OK;
+  Ctx* cx = reinterpret_cast<Ctx*>(ctx);
+  DeviceGuard g(cx->device);
+  cbp::launch_truncate_lsb(in, dtype == CBP_F64, count, bits, drop, out, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? CBP_OK : CBP_ERR_CUDA;
+}
+
 cbp_status cbp_synth_latent(cbp_ctx* ctx, const double* blobs, int32_t nblobs, int32_t n,
                             int32_t c, int32_t h, int32_t w, cbp_dtype dtype, double floor_amp,
                             uint64_t seed, void* out, void* stream) {

@@ -122,7 +122,31 @@ __global__ void k_synth_latent(const double* blobs, int nblobs, int c, int h, in
   out[oi] = v;
 }
 
+// Multi-level security (Section 3): the private stream at a lower clearance
+// level, its least significant bits removed.  code = rint(x (2^bits - 1))
+// clamped to [0, 2^bits - 1], the `drop` low bits cleared, value
+// code / (2^bits - 1); in double precision whatever the element type.
+template <typename T>
+__global__ void k_truncate_lsb(const T* in, int64_t count, int bits, int drop, T* out) {
+  const double top = (double)((1ll << bits) - 1);
+  const long long mask = ~((1ll << drop) - 1);
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double c = fmin(fmax(rint((double)in[i] * top), 0.0), top);
+    const long long code = (long long)c & mask;
+    out[i] = (T)((double)code / top);
+  }
+}
+
 }  // namespace
+
+void launch_truncate_lsb(const void* in, int f64, int64_t count, int bits, int drop, void* out,
+                         cudaStream_t st) {
+  const int64_t blocks64 = (count + 255) / 256;
+  const int blocks = (int)(blocks64 < 152 * 32 ? (blocks64 > 0 ? blocks64 : 1) : 152 * 32);
+  if (f64) k_truncate_lsb<double><<<blocks, 256, 0, st>>>((const double*)in, count, bits, drop, (double*)out);
+  else k_truncate_lsb<float><<<blocks, 256, 0, st>>>((const float*)in, count, bits, drop, (float*)out);
+}
 
 void launch_forward_blur(const void* latent, int n, int c, int h, int w, int f64,
                          const double* kernel, int t, double sigma, uint64_t seed, void* out,

@@ -167,6 +167,9 @@ void launch_forward_blur(const void* latent, int n, int c, int h, int w, int f64
                          cudaStream_t st);
 void launch_synth_latent(const double* blobs, int nblobs, int n, int c, int h, int w, int f64,
                          double floor_amp, uint64_t seed, void* out, cudaStream_t st);
+// Section 3 multi-level security: LSB truncation of a frame buffer (cbp_forward.cu)
+void launch_truncate_lsb(const void* in, int f64, int64_t count, int bits, int drop, void* out,
+                         cudaStream_t st);
 size_t sample_solve_smem(int nn);
 // kernel-size scan (cbp_solve.cu): plane sums, per-candidate ratios, the pick
 void launch_size_scan(const SizePlan& sp, const FrameDesc& b1, const FrameDesc& b2, char* ws,
