@@ -20,3 +20,4 @@ from .cbp_oracle import (  # noqa: F401
     plane_sums, size_ratios, estimate_size, truncate_lsb,
 )
 from .coprime import resultant_nonzero  # noqa: F401
+from . import camera  # noqa: F401
