@@ -270,6 +270,48 @@ cbp_status cbp_forward_blur(cbp_ctx* ctx, const void* latent, int32_t n, int32_t
                             int32_t h, int32_t w, cbp_dtype dtype, const double* kernel,
                             int32_t t, double sigma, uint64_t seed, void* out, void* stream);
 
+/* Camera side of the scheme (Section 3, "Blur Kernel Selection" and the
+ * cascaded pair). */
+typedef struct cbp_encrypt_params {
+  int32_t t1, t2;       /* sizes of the pair's kernels (public K1, private K2), 1..32    */
+  int32_t t3, t4;       /* sizes of the cascade's pair (0, 0: no cascade)                */
+  int32_t m;            /* samples per direction of the coprimality test; 0 => max of
+                           the pair's sizes (the deblurring's default M), <= 32         */
+  int32_t max_attempts; /* draws per frame and pair before giving up; 0 => 8           */
+  double tol;           /* coprime when every sample's sigma_min / sigma_max > tol;
+                           0 => 1e-7                                                     */
+  double sigma;         /* sensor noise N(0, sigma^2) on both streams (not the cascade)  */
+  uint64_t seed;        /* key of the generator                                          */
+  int32_t frame0;       /* frame index of the batch's first frame (generator counter)    */
+  int32_t reserved;
+} cbp_encrypt_params;
+
+/* Encrypt a batch of latent frames on the device (Section 3): for every frame
+ * f a new pair of random square kernels -- entries uniform in (0, 1] from
+ * Philox-4x32-10 (entry e of kernel `kind` at redraw a: word e mod 4 of
+ * Philox(counter = (e / 4, frame0 + f, 256 kind + a, 0), key = seed), value
+ * (word + 1) 2^-32), normalised to unit sum -- redrawn until the pair passes
+ * the coprimality test: at every sample w^j (w = exp(-2 pi i / m)) of both
+ * evaluation orders the univariate kernel polynomials share no root
+ * (sigma_min / sigma_max of their Sylvester matrix > tol) and one keeps full
+ * degree.  Then B1 = L (x) K1 + N1 (public stream) and B2 = L (x) K2 + N2
+ * (private stream), full 2D convolution per channel (Eq. 1).  With a cascade
+ * (t3, t4 > 0), a second coprime pair (kinds 2, 3) blurs the public stream
+ * again: C1 = B1 (x) K3, C2 = B1 (x) K4, the pair distributed where the
+ * first pair's private stream may not go.
+ * latent: device, n x c x h x w of dtype.  k1, k2 (k3, k4): device, n t_k^2
+ * doubles.  b1, b2: device, n x c x (h + t_k - 1) x (w + t_k - 1) of dtype.
+ * c1, c2: NULL without a cascade, else n x c x (h + t1 + t3 - 2) x
+ * (w + t1 + t3 - 2) and (... t4 ...).  attempts: NULL or host array of n
+ * (2 n with a cascade: the cascade's after the pair's) accepted draw indices,
+ * -1 where every draw failed (the last draw is used).  The draws synchronise
+ * the stream once per redraw round (usually one round).
+ * Errors: CBP_ERR_INVALID_ARG, CBP_ERR_BUDGET, CBP_ERR_OOM, CBP_ERR_CUDA. */
+cbp_status cbp_encrypt(cbp_ctx* ctx, const void* latent, int32_t n, int32_t c, int32_t h, int32_t w,
+                       cbp_dtype dtype, const cbp_encrypt_params* params, double* k1, double* k2,
+                       void* b1, void* b2, double* k3, double* k4, void* c1, void* c2,
+                       int32_t* attempts, void* stream);
+
 /* Multi-level security (Section 3): the private stream as a lower clearance
  * level receives it, with the least significant bits of its pixel codes
  * removed.  Each of the `count` elements x (intensities nominally in [0, 1])

@@ -30,10 +30,16 @@ EXPORTED = [
     "cbp_stream_submit", "cbp_stream_poll", "cbp_stream_stats", "cbp_profile", "cbp_stage_times",
     "cbp_estimate_kernels_stages", "cbp_estimate_kernels_noalloc", "cbp_cnn_param_count",
     "cbp_cnn_forward", "cbp_cnn_train_step", "cbp_learned_load", "cbp_estimate_size",
-    "cbp_truncate_lsb",
+    "cbp_truncate_lsb", "cbp_encrypt",
 ]
 STAGES = ["eval", "sample_solve", "scale_solve", "kernel_spectra", "row_fft", "col_deconv",
           "row_ifft", "h2d", "d2h", "proposal", "gate"]
+
+
+class cbp_encrypt_params(ctypes.Structure):
+    _fields_ = [("t1", c_int32), ("t2", c_int32), ("t3", c_int32), ("t4", c_int32), ("m", c_int32),
+                ("max_attempts", c_int32), ("tol", c_double), ("sigma", c_double), ("seed", c_uint64),
+                ("frame0", c_int32), ("reserved", c_int32)]
 
 
 class cbp_size_params(ctypes.Structure):
@@ -117,6 +123,9 @@ def lib() -> ctypes.CDLL:
             "cbp_learned_load": ([c_void_p, ctypes.c_char_p], c_int),
             "cbp_truncate_lsb": ([c_void_p, c_void_p, c_int, c_int64, c_int32, c_int32, c_void_p,
                                   c_void_p], c_int),
+            "cbp_encrypt": ([c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int,
+                             POINTER(cbp_encrypt_params), c_void_p, c_void_p, c_void_p, c_void_p,
+                             c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_int32), c_void_p], c_int),
             "cbp_estimate_size": ([c_void_p, fr, fr, POINTER(cbp_size_params), POINTER(c_int32),
                                    POINTER(c_int32), POINTER(c_int32), POINTER(c_double),
                                    POINTER(c_int32), c_void_p], c_int),
@@ -328,6 +337,39 @@ def cbp_estimate_kernels_stages(ctx, b1: torch.Tensor, b2: torch.Tensor, prm: cb
                                            _stream_ptr(stream))
     _check(st, "cbp_estimate_kernels_stages")
     out["k1"], out["k2"], out["diag"] = k1, k2, d
+    return out
+
+
+def cbp_encrypt(ctx, latent: torch.Tensor, t1: int, t2: int, seed: int, frame0: int = 0,
+                sigma: float = 0.0, cascade: tuple | None = None, m: int = 0, max_attempts: int = 0,
+                tol: float = 0.0, stream=None) -> dict:
+    """Camera side on the device (Section 3): per-frame coprime kernel pairs,
+    the public/private blurred streams and, with cascade = (t3, t4), the
+    cascaded pair.  latent: (n, c, h, w) contiguous device tensor.  Returns a
+    dict of tensors (k1, k2, b1, b2[, k3, k4, c1, c2]) and `attempts` (list)."""
+    if not latent.is_contiguous() or latent.dim() != 4:
+        raise ValueError("(n, c, h, w) contiguous latent expected")
+    n, c, h, w = latent.shape
+    dev, dt = latent.device, latent.dtype
+    t3, t4 = cascade if cascade else (0, 0)
+    prm = cbp_encrypt_params(t1, t2, t3, t4, m, max_attempts, tol, sigma, seed, frame0, 0)
+    out = {"k1": torch.empty((n, t1, t1), dtype=torch.float64, device=dev),
+           "k2": torch.empty((n, t2, t2), dtype=torch.float64, device=dev),
+           "b1": torch.empty((n, c, h + t1 - 1, w + t1 - 1), dtype=dt, device=dev),
+           "b2": torch.empty((n, c, h + t2 - 1, w + t2 - 1), dtype=dt, device=dev)}
+    if cascade:
+        out["k3"] = torch.empty((n, t3, t3), dtype=torch.float64, device=dev)
+        out["k4"] = torch.empty((n, t4, t4), dtype=torch.float64, device=dev)
+        out["c1"] = torch.empty((n, c, h + t1 + t3 - 2, w + t1 + t3 - 2), dtype=dt, device=dev)
+        out["c2"] = torch.empty((n, c, h + t1 + t4 - 2, w + t1 + t4 - 2), dtype=dt, device=dev)
+    att = (c_int32 * (2 * n if cascade else n))()
+    ptr = lambda k: out[k].data_ptr() if k in out else None
+    _check(lib().cbp_encrypt(ctx, latent.data_ptr(), n, c, h, w,
+                             CBP_F64 if dt == torch.float64 else CBP_F32, byref(prm), ptr("k1"), ptr("k2"),
+                             ptr("b1"), ptr("b2"), ptr("k3"), ptr("k4"), ptr("c1"), ptr("c2"), att,
+                             _stream_ptr(stream)), "cbp_encrypt")
+    torch.cuda.synchronize()
+    out["attempts"] = list(att)
     return out
 
 

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <mutex>
 #include <new>
+#include <vector>
 #include "cbp.h"
 #include "cbp_internal.h"
 #if defined(CBP_DEBUG_ERRORS) || defined(CBP_TIMELINE)
@@ -360,6 +361,90 @@ cbp_status size_scan(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
   return CBP_OK;
 }
 
+// Draw coprime kernel pairs (kinds ka, kb) for every frame of a batch on the
+// device, redrawing in rounds; attempts (device int[n]) ends with the accepted
+// draw or -1.
+cbp_status draw_coprime_pairs(int n, int ta, int tb, int kind_a, int kind_b, int M, double tol,
+                              int max_attempts, int frame0, uint64_t seed, double* ka, double* kb,
+                              char* ws, cudaStream_t st) {
+  int* active = (int*)ws;
+  int* attempt = active + n;
+  int* any = attempt + n;
+  int* pass = any + 4;
+  std::vector<int> ones((size_t)n, 1);
+  if (cudaMemcpyAsync(active, ones.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, st) !=
+          cudaSuccess ||
+      cudaMemsetAsync(attempt, 0, (size_t)n * sizeof(int), st) != cudaSuccess)
+    return CBP_ERR_CUDA;
+  for (int r = 0; r < max_attempts; ++r) {
+    cbp::launch_draw_kernels(n, ta, kind_a, frame0, seed, active, attempt, ka, st);
+    cbp::launch_draw_kernels(n, tb, kind_b, frame0, seed, active, attempt, kb, st);
+    int h_any = 0;
+    if (cudaMemsetAsync(any, 0, sizeof(int), st) != cudaSuccess) return CBP_ERR_CUDA;
+    cbp::launch_coprime_round(ka, kb, n, ta, tb, M, tol, max_attempts, active, attempt, pass, any, st);
+    if (cudaMemcpyAsync(&h_any, any, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return CBP_ERR_CUDA;
+    if (!h_any) break;
+  }
+  return cudaGetLastError() == cudaSuccess ? CBP_OK : CBP_ERR_CUDA;
+}
+
+cbp_status encrypt_frames(cbp_ctx* ctx, const void* latent, int32_t n, int32_t c, int32_t h,
+                          int32_t w, cbp_dtype dtype, const cbp_encrypt_params* prm, double* k1,
+                          double* k2, void* b1, void* b2, double* k3, double* k4, void* c1, void* c2,
+                          int32_t* attempts, void* stream) {
+  if (!ctx || !latent || !prm || !k1 || !k2 || !b1 || !b2 || n < 1 || c < 1 || h < 1 || w < 1 ||
+      (dtype != CBP_F32 && dtype != CBP_F64) || !(prm->sigma >= 0.0))
+    return CBP_ERR_INVALID_ARG;
+  const bool cascade = prm->t3 > 0 || prm->t4 > 0;
+  const int ts[4] = {prm->t1, prm->t2, prm->t3, prm->t4};
+  for (int i = 0; i < (cascade ? 4 : 2); ++i)
+    if (ts[i] < 1 || ts[i] > 32) return CBP_ERR_INVALID_ARG;
+  if (cascade && (!k3 || !k4 || !c1 || !c2)) return CBP_ERR_INVALID_ARG;
+  const int M1 = prm->m ? prm->m : std::max(prm->t1, prm->t2);
+  const int M2 = prm->m ? prm->m : std::max(prm->t3, prm->t4);
+  if (M1 < 1 || M1 > cbp::kMaxM || (cascade && (M2 < 1 || M2 > cbp::kMaxM))) return CBP_ERR_INVALID_ARG;
+  const int maxa = prm->max_attempts > 0 ? prm->max_attempts : 8;
+  const double tol = prm->tol > 0.0 ? prm->tol : 1e-7;
+  if (!std::isfinite(tol) || maxa > 255) return CBP_ERR_INVALID_ARG;
+  Ctx* cx = reinterpret_cast<Ctx*>(ctx);
+  DeviceGuard g(cx->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  std::lock_guard<std::mutex> lk(cx->api_mu);
+  const int Mmax = std::max(M1, cascade ? M2 : 1);
+  const size_t per = (size_t)(2 * n + 4 + n * 2 * (Mmax / 2 + 1)) * sizeof(int);
+  cbp_status s = cx->ensure_ws(2 * ((per + 255) & ~size_t(255)), st);
+  if (s != CBP_OK) return s;
+  char* wa = cx->ws;
+  char* wb = cx->ws + ((per + 255) & ~size_t(255));
+  s = draw_coprime_pairs(n, prm->t1, prm->t2, 0, 1, M1, tol, maxa, prm->frame0, prm->seed, k1, k2, wa, st);
+  if (s != CBP_OK) return s;
+  if (cascade) {
+    s = draw_coprime_pairs(n, prm->t3, prm->t4, 2, 3, M2, tol, maxa, prm->frame0, prm->seed, k3, k4, wb,
+                           st);
+    if (s != CBP_OK) return s;
+  }
+  // noise keys per batch and stream
+  const uint64_t nkey = prm->seed + 0x100000000ull * (uint64_t)(prm->frame0 + 1);
+  const int f64 = dtype == CBP_F64;
+  cbp::launch_forward_blur(latent, n, c, h, w, f64, k1, prm->t1, prm->sigma, nkey + 1, b1, st);
+  cbp::launch_forward_blur(latent, n, c, h, w, f64, k2, prm->t2, prm->sigma, nkey + 2, b2, st);
+  if (cascade) {
+    const int hb = h + prm->t1 - 1, wb1 = w + prm->t1 - 1;
+    cbp::launch_forward_blur(b1, n, c, hb, wb1, f64, k3, prm->t3, 0.0, 0, c1, st);
+    cbp::launch_forward_blur(b1, n, c, hb, wb1, f64, k4, prm->t4, 0.0, 0, c2, st);
+  }
+  if (attempts) {
+    if (cudaMemcpyAsync(attempts, (int*)wa + n, (size_t)n * sizeof(int), cudaMemcpyDeviceToHost, st) !=
+            cudaSuccess ||
+        (cascade && cudaMemcpyAsync(attempts + n, (int*)wb + n, (size_t)n * sizeof(int),
+                                    cudaMemcpyDeviceToHost, st) != cudaSuccess))
+      return CBP_ERR_CUDA;
+  }
+  return cudaGetLastError() == cudaSuccess ? CBP_OK : CBP_ERR_CUDA;
+}
+
 cbp_status call_path(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
                      const cbp_params* prm, void* k1, void* k2, void* latent, cbp_diag* diag,
                      void* stream, bool deblur, const cbp_stage_out* stages = nullptr) {
@@ -682,6 +767,18 @@ cbp_status cbp_estimate_size(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frame
                              const cbp_size_params* params, int32_t* t1_out, int32_t* t2_out,
                              int32_t* found, double* ratios, int32_t* ncand_out, void* stream) {
   return size_scan(ctx, b1, b2, params, t1_out, t2_out, found, ratios, ncand_out, stream);
+}
+
+cbp_status cbp_encrypt(cbp_ctx* ctx, const void* latent, int32_t n, int32_t c, int32_t h, int32_t w,
+                       cbp_dtype dtype, const cbp_encrypt_params* params, double* k1, double* k2,
+                       void* b1, void* b2, double* k3, double* k4, void* c1, void* c2,
+                       int32_t* attempts, void* stream) {
+  try {
+    return encrypt_frames(ctx, latent, n, c, h, w, dtype, params, k1, k2, b1, b2, k3, k4, c1, c2,
+                          attempts, stream);
+  } catch (...) {
+    return CBP_ERR_OOM;
+  }
 }
 
 }  // extern "C"

@@ -5,29 +5,10 @@
 // counter = (element index lo, element index hi, stream, 0), key = seed.
 #include "cbp_common.cuh"
 #include "cbp_internal.h"
+#include "cbp_philox.cuh"
 
 namespace cbp {
 namespace {
-
-struct U4 { uint32_t x, y, z, w; };
-
-__device__ __forceinline__ U4 philox_round(U4 c, uint32_t k0, uint32_t k1) {
-  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
-  uint32_t hi0 = __umulhi(M0, c.x), lo0 = M0 * c.x;
-  uint32_t hi1 = __umulhi(M1, c.z), lo1 = M1 * c.z;
-  return {hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0};
-}
-
-__device__ __forceinline__ U4 philox4x32_10(U4 c, uint32_t k0, uint32_t k1) {
-  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
-#pragma unroll
-  for (int i = 0; i < 10; ++i) {
-    c = philox_round(c, k0, k1);
-    k0 += W0;
-    k1 += W1;
-  }
-  return c;
-}
 
 // Uniform in (0, 1] from 32 bits.
 __device__ __forceinline__ double u01(uint32_t v) { return ((double)v + 1.0) * 2.3283064365386963e-10; }
@@ -138,7 +119,39 @@ __global__ void k_truncate_lsb(const T* in, int64_t count, int bits, int drop, T
   }
 }
 
+// Camera side (Section 3, "Blur Kernel Selection": new random kernels for
+// every frame): kernel `kind` of frame frame0 + f at redraw attempt[f],
+// entries (Philox word + 1) 2^-32, uniform in (0, 1], normalised to unit sum
+// in entry order.  Entry e is word e mod 4 of Philox(counter = (e / 4, frame,
+// kind * 256 + attempt, 0), key = seed).  One thread per kernel; pairs whose
+// active flag is clear keep their kernels.
+__global__ void k_draw_kernels(int n, int t, int kind, int frame0, uint64_t seed, const int* active,
+                               const int* attempt, double* kd) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n || !active[f]) return;
+  double* K = kd + (int64_t)f * t * t;
+  const uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  const int nn = t * t;
+  double sum = 0.0;
+  for (int b = 0; 4 * b < nn; ++b) {
+    const U4 r = philox4x32_10({(uint32_t)b, (uint32_t)(frame0 + f), (uint32_t)(kind * 256 + attempt[f]), 0u},
+                               k0, k1);
+    const uint32_t w[4] = {r.x, r.y, r.z, r.w};
+    for (int i = 0; i < 4 && 4 * b + i < nn; ++i) {
+      const double u = u01(w[i]);
+      K[4 * b + i] = u;
+      sum += u;
+    }
+  }
+  for (int e = 0; e < nn; ++e) K[e] = K[e] / sum;
+}
+
 }  // namespace
+
+void launch_draw_kernels(int n, int t, int kind, int frame0, uint64_t seed, const int* active,
+                         const int* attempt, double* kd, cudaStream_t st) {
+  k_draw_kernels<<<(n + 127) / 128, 128, 0, st>>>(n, t, kind, frame0, seed, active, attempt, kd);
+}
 
 void launch_truncate_lsb(const void* in, int f64, int64_t count, int bits, int drop, void* out,
                          cudaStream_t st) {

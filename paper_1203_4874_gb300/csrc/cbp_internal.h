@@ -170,6 +170,13 @@ void launch_synth_latent(const double* blobs, int nblobs, int n, int c, int h, i
 // Section 3 multi-level security: LSB truncation of a frame buffer (cbp_forward.cu)
 void launch_truncate_lsb(const void* in, int f64, int64_t count, int bits, int drop, void* out,
                          cudaStream_t st);
+// camera side (Section 3): per-frame kernel draws (cbp_forward.cu) and one
+// round of the coprimality test with the redraw decision (cbp_solve.cu)
+void launch_draw_kernels(int n, int t, int kind, int frame0, uint64_t seed, const int* active,
+                         const int* attempt, double* kd, cudaStream_t st);
+void launch_coprime_round(const double* ka, const double* kb, int n, int ta, int tb, int M,
+                          double tol, int max_attempts, int* active, int* attempt, int* pass,
+                          int* any, cudaStream_t st);
 size_t sample_solve_smem(int nn);
 // kernel-size scan (cbp_solve.cu): plane sums, per-candidate ratios, the pick
 void launch_size_scan(const SizePlan& sp, const FrameDesc& b1, const FrameDesc& b2, char* ws,

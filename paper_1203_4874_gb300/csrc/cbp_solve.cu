@@ -1014,6 +1014,94 @@ __global__ void k_size_pick(const double* ratio, int n, int ncand, int t_min, in
   t_out[3 * f + 2] = best >= 0 ? 1 : 0;
 }
 
+// ------------------------------------------- coprimality of kernel pairs ---
+// The camera side's test (Section 3: the pair must be coprime as bivariate
+// polynomials): at every solved sample w^j (j <= M/2; sample M - j is the
+// conjugate) of both evaluation orders, the univariate polynomials
+// a = K1(., w^j), b = K2(., w^j) share no root -- sigma_min / sigma_max of
+// their square Sylvester matrix (the cofactor system at t1 - 1, t2 - 1)
+// above tol, from its normal matrix's extreme eigenvalues -- and one of them
+// keeps full degree (|leading coefficient| > 1e-12 of its norm).
+struct CoprimeArgs {
+  const double* ka;     // [n][ta ta]
+  const double* kb;     // [n][tb tb]
+  int ta, tb, M, ns;
+  const int* active;    // [n] pairs under test
+  double tol;
+  int* pass;            // [n][2][ns]
+};
+
+__global__ void __launch_bounds__(kSolveThreads) k_coprime_test(CoprimeArgs a) {
+  extern __shared__ __align__(16) char smem[];
+  const int j = blockIdx.x, order = blockIdx.y, f = blockIdx.z;
+  if (!a.active[f]) return;
+  const int ta = a.ta, tb = a.tb, n = ta + tb - 2;
+  cd* pa = (cd*)smem;                                  // [ta]
+  cd* pb = pa + kMaxN;                                 // [tb]
+  cd* G = pb + kMaxN;                                  // [n][n]
+  cd* rho = G + kMaxN * kMaxN;                         // [2 n - 1]
+  __shared__ int full;
+  const double* K1 = a.ka + (int64_t)f * ta * ta;
+  const double* K2 = a.kb + (int64_t)f * tb * tb;
+  // a[p] = sum_q K1[p][q] w^(j q) (order 0) or a[q] = sum_p K1[p][q] w^(j p)
+  for (int e = threadIdx.x; e < ta + tb; e += blockDim.x) {
+    const bool second = e >= ta;
+    const int t = second ? tb : ta, i = second ? e - ta : e;
+    const double* K = second ? K2 : K1;
+    cd acc = mk(0.0, 0.0);
+    for (int k = 0; k < t; ++k) {
+      double sn, cs;
+      sincospi(-2.0 * (double)((j * k) % a.M) / (double)a.M, &sn, &cs);
+      const double v = order == 0 ? K[i * t + k] : K[k * t + i];
+      acc = acc + v * mk(cs, sn);
+    }
+    (second ? pb : pa)[i] = acc;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double na = 0.0, nb = 0.0;
+    for (int i = 0; i < ta; ++i) na += abs2(pa[i]);
+    for (int i = 0; i < tb; ++i) nb += abs2(pb[i]);
+    full = (abs2(pa[ta - 1]) > 1e-24 * na) || (abs2(pb[tb - 1]) > 1e-24 * nb);
+  }
+  __syncthreads();
+  double ratio = 1.0;
+  if (ta > 1 && tb > 1) {
+    SamplePolys<double, double> P;
+    P.c[0] = pa;
+    P.c[1] = pb;
+    P.cstride[0] = P.cstride[1] = 0;
+    P.len[0] = ta;
+    P.len[1] = tb;
+    correlations(P, 1, ta - 1, tb - 1, rho);
+    gram_from_rho(rho, ta - 1, tb - 1, G);
+    const TriWs W = carve_tri(smem + sizeof(cd) * (2 * kMaxN + kMaxN * kMaxN + 2 * kMaxN), n);
+    const TriResult res = tri_smallest<cd, true>(W, G, n, 0, 0, 1e300, NoApply{});
+    ratio = res.lam_max > 0.0 ? sqrt(fmax(res.theta, 0.0) / res.lam_max) : 0.0;
+  }
+  if (threadIdx.x == 0) a.pass[((int64_t)f * 2 + order) * a.ns + j] = (full && ratio > a.tol) ? 1 : 0;
+}
+
+// Per pair under test: accepted when every sample passed; else the next
+// attempt, or -1 once max_attempts draws have failed.  *any: some pair is
+// still under test.
+__global__ void k_coprime_pick(int n, int ns, const int* pass, int* active, int* attempt,
+                               int max_attempts, int* any) {
+  const int f = blockIdx.x * blockDim.x + threadIdx.x;
+  if (f >= n || !active[f]) return;
+  bool ok = true;
+  for (int i = 0; i < 2 * ns; ++i) ok = ok && pass[(int64_t)f * 2 * ns + i];
+  if (ok) {
+    active[f] = 0;
+  } else if (attempt[f] + 1 < max_attempts) {
+    attempt[f] += 1;
+    atomicOr(any, 1);
+  } else {
+    active[f] = 0;
+    attempt[f] = -1;
+  }
+}
+
 }  // namespace
 
 size_t sample_solve_smem(int nn) { return tri_ws_bytes(nn); }
@@ -1127,6 +1215,29 @@ void launch_size_scan(const SizePlan& sp, const FrameDesc& b1, const FrameDesc& 
   k_size_scan<<<dim3(sp.ncand, 2, sp.n), kSolveThreads, sm, st>>>(a);
   k_size_pick<<<(sp.n + 127) / 128, 128, 0, st>>>(a.ratio, sp.n, sp.ncand, sp.t_min, sp.d, sp.tol,
                                                  (int*)(ws + sp.off_t), (double*)(ws + sp.off_rmax));
+}
+
+size_t coprime_test_smem() {
+  return sizeof(cd) * (2 * kMaxN + kMaxN * kMaxN + 2 * kMaxN) + tri_ws_bytes(kMaxN);
+}
+
+void launch_coprime_round(const double* ka, const double* kb, int n, int ta, int tb, int M,
+                          double tol, int max_attempts, int* active, int* attempt, int* pass,
+                          int* any, cudaStream_t st) {
+  CoprimeArgs a;
+  a.ka = ka;
+  a.kb = kb;
+  a.ta = ta;
+  a.tb = tb;
+  a.M = M;
+  a.ns = M / 2 + 1;
+  a.active = active;
+  a.tol = tol;
+  a.pass = pass;
+  const size_t sm = coprime_test_smem();
+  cudaFuncSetAttribute(k_coprime_test, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_coprime_test<<<dim3(a.ns, 2, n), kSolveThreads, sm, st>>>(a);
+  k_coprime_pick<<<(n + 127) / 128, 128, 0, st>>>(n, a.ns, pass, active, attempt, max_attempts, any);
 }
 
 }  // namespace cbp
