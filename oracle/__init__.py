@@ -17,7 +17,8 @@ from .cbp_oracle import (  # noqa: F401
     convolution_matrix, sylvester_system, null_vector, cofactors_pass,
     lift, scale_least_squares, kernel_spectra, kernels_from_spectra,
     fft_grid_size, deconvolve_dual, estimate_kernels, deblur_pair,
-    plane_sums, size_ratios, estimate_size, truncate_lsb,
+    plane_sums, size_ratios, estimate_size, truncate_lsb, scale_least_squares_k1,
+    scale_support, kernel_spectra_support,
 )
 from .coprime import resultant_nonzero  # noqa: F401
 from . import camera  # noqa: F401

@@ -161,7 +161,7 @@ def scale_least_squares(a: np.ndarray, b: np.ndarray):
     """
     m = a.shape[1]
     rows = []
-    for k in range(2):
+    for k in range(a.shape[0]):                      # the kernels whose equations enter
         for i in range(m):
             for j in range(m):
                 row = np.zeros(2 * m, dtype=np.complex128)
@@ -170,6 +170,41 @@ def scale_least_squares(a: np.ndarray, b: np.ndarray):
                 rows.append(row)
     theta, sv = null_vector(np.array(rows))
     return theta[:m], theta[m:], sv
+
+
+def scale_least_squares_k1(a: np.ndarray, b: np.ndarray):
+    """The paper's k1-only pipeline (Section 4 recovers the cofactor k1 and
+    divides B1 by K1): the scale fix of `scale_least_squares` with kernel 1's
+    equations only, gamma_j A_1[i][j] - delta_i B_1[i][j] = 0 (M^2 equations).
+    Returns (gamma, delta, singular values)."""
+    return scale_least_squares(a[:1], b[:1])
+
+
+def scale_support(a: np.ndarray, t1: int, t2: int):
+    """Single-pass scale fix from the kernels' support (a reading of Section
+    5's remark that the M x M estimates hold kernels of size t < M): with the
+    z2-first lift A_k[i][j] = c_j K_k^[i][j] only, the inverse DFT along j of
+    gamma_j A_k[i][j] must vanish at the columns q >= t_k the kernel does not
+    occupy:  sum_j gamma_j A_k[i][j] omega^(-j q) = 0  for k = 1, 2, every i and
+    t_k <= q < M.  gamma is the null vector of this 2 M (M - t) x M system (by
+    SVD); needs M > max(t1, t2).  Returns (gamma, singular values)."""
+    m = a.shape[1]
+    if m <= max(t1, t2):
+        raise ValueError("the support constraint needs M > max(t1, t2)")
+    v = root_powers(m, m, sign=+1)                   # v[j][q] = omega^(-jq)
+    rows = []
+    for k, t in ((0, t1), (1, t2)):
+        for i in range(m):
+            for q in range(t, m):
+                rows.append(a[k, i, :] * v[:, q])
+    gamma, sv = null_vector(np.array(rows))
+    return gamma, sv
+
+
+def kernel_spectra_support(a: np.ndarray, gamma: np.ndarray):
+    """X_k[i][j] = gamma_j A_k[i][j], normalised so that X_k[0][0] = 1."""
+    x = gamma[None, None, :] * a
+    return x / x[:, :1, :1]
 
 
 def kernel_spectra(a: np.ndarray, b: np.ndarray, gamma: np.ndarray, delta: np.ndarray):
@@ -235,7 +270,8 @@ def deconvolve_dual(b1: np.ndarray, b2: np.ndarray, k1: np.ndarray, k2: np.ndarr
 
 
 # --------------------------------------------------------------- pipelines ---
-def estimate_kernels(b1: np.ndarray, b2: np.ndarray, t1: int, t2: int, m: int | None = None):
+def estimate_kernels(b1: np.ndarray, b2: np.ndarray, t1: int, t2: int, m: int | None = None,
+                     scale: str = "ls"):
     """Blind recovery of (K1, K2) from a coprime blurred pair, in the paper's order.
 
     b1, b2: (C, H_B1, W_B1) and (C, H_B2, W_B2).  Returns a dict of every
@@ -255,10 +291,22 @@ def estimate_kernels(b1: np.ndarray, b2: np.ndarray, t1: int, t2: int, m: int | 
     out["x_z2"], out["sv_z2"] = cofactors_pass(out["p_z2_1"], out["p_z2_2"], t1, t2)
     out["x_z1"], out["sv_z1"] = cofactors_pass(out["p_z1_1"], out["p_z1_2"], t1, t2)
     out["a_hat"], out["b_hat"] = lift(out["x_z2"], out["x_z1"], t1, t2, m)
-    out["gamma"], out["delta"], out["sv_scale"] = scale_least_squares(out["a_hat"], out["b_hat"])
-    out["x_k"] = kernel_spectra(out["a_hat"], out["b_hat"], out["gamma"], out["delta"])
+    if scale == "support":
+        # single pass: the z2-first lift and the support constraint only
+        out["gamma"], out["sv_scale"] = scale_support(out["a_hat"], t1, t2)
+        out["x_k"] = kernel_spectra_support(out["a_hat"], out["gamma"])
+    elif scale == "k1":
+        out["gamma"], out["delta"], out["sv_scale"] = scale_least_squares_k1(out["a_hat"], out["b_hat"])
+        x1 = kernel_spectra(out["a_hat"][:1], out["b_hat"][:1], out["gamma"], out["delta"])
+        out["x_k"] = np.concatenate([x1, np.full_like(x1, np.nan)])
+    else:
+        out["gamma"], out["delta"], out["sv_scale"] = scale_least_squares(out["a_hat"], out["b_hat"])
+        out["x_k"] = kernel_spectra(out["a_hat"], out["b_hat"], out["gamma"], out["delta"])
     out["k1"], out["k1_full"] = kernels_from_spectra(out["x_k"][0], t1)
-    out["k2"], out["k2_full"] = kernels_from_spectra(out["x_k"][1], t2)
+    if scale == "k1":
+        out["k2"] = out["k2_full"] = None
+    else:
+        out["k2"], out["k2_full"] = kernels_from_spectra(out["x_k"][1], t2)
     sv = np.concatenate([out["sv_z2"], out["sv_z1"]])
     gap = sv[:, -2] / sv[:, 0]
     out["diag"] = {
@@ -273,18 +321,23 @@ def estimate_kernels(b1: np.ndarray, b2: np.ndarray, t1: int, t2: int, m: int | 
 
 
 def deblur_pair(b1, b2, t1: int, t2: int, m: int | None = None, eps: float = 1e-4,
-                k1=None, k2=None, ph: int | None = None, pw: int | None = None):
-    """Kernels (estimated unless given) and the latent frame of one pair (Sections 4-5)."""
+                k1=None, k2=None, ph: int | None = None, pw: int | None = None, scale: str = "ls"):
+    """Kernels (estimated unless given) and the latent frame of one pair (Sections 4-5).
+    scale: "ls" (both kernels' two-order least squares, dual-kernel division),
+    "support" (single-pass support-constrained scale fix), "k1" (the paper's
+    k1-only pipeline: kernel 1's scale fix, B1 divided by K1)."""
     b1 = np.asarray(b1, dtype=np.float64)
     b2 = np.asarray(b2, dtype=np.float64)
     if b1.ndim == 2:
         b1, b2 = b1[None], b2[None]
     out = {}
-    if k1 is None or k2 is None:
-        out = estimate_kernels(b1, b2, t1, t2, m)
+    if k1 is None or (k2 is None and scale != "k1"):
+        out = estimate_kernels(b1, b2, t1, t2, m, scale)
         k1, k2 = out["k1"], out["k2"]
     h = b1.shape[1] - t1 + 1
     w = b1.shape[2] - t1 + 1
+    if scale == "k1":
+        k2 = np.zeros((t2, t2))                      # single-kernel form: B1 / K1
     out["latent"] = deconvolve_dual(b1, b2, k1, k2, h, w, eps, ph, pw)
     return out
 
