@@ -87,6 +87,16 @@ typedef struct cbp_frames {
                                     the dual-kernel formula                         */
 #define CBP_FLAG_KERNELS_F64 8u  /* k1, k2 buffers hold doubles whatever the frames'
                                     dtype (the FP64 path's full accuracy)           */
+#define CBP_FLAG_K1_ONLY    16u  /* the paper's k1-only pipeline (Section 4: the
+                                    cofactor k1, then B1 divided by K1): the scale
+                                    fix from kernel 1's equations only, the
+                                    single-kernel deconvolution; k2 is not written  */
+#define CBP_FLAG_SCALE_SUPPORT 32u /* single-pass scale fix from the kernels'
+                                    support: with m > max(t1, t2) the z2-first
+                                    estimates' inverse DFT must vanish at columns
+                                    q >= t_k; gamma_j is the null vector of those
+                                    equations (the z1-first pass is not used).
+                                    Needs m > max(t1, t2); excludes K1_ONLY        */
 
 typedef struct cbp_params {
   int32_t t1, t2;     /* kernel sizes (square kernels), 1 <= t_k, t1 + t2 <= 64  */

@@ -21,6 +21,7 @@ CBP_ERR_BUDGET, CBP_ERR_UNSUPPORTED = -8, -9
 CBP_F32, CBP_F64 = 0, 1
 CBP_PATH_FP64, CBP_PATH_MIXED, CBP_PATH_LEARNED = 0, 1, 2
 CBP_FLAG_HOST_IO, CBP_FLAG_KERNELS_IN, CBP_FLAG_SINGLE_KERNEL, CBP_FLAG_KERNELS_F64 = 1, 2, 4, 8
+CBP_FLAG_K1_ONLY, CBP_FLAG_SCALE_SUPPORT = 16, 32
 PATHS = {"fp64": CBP_PATH_FP64, "mixed": CBP_PATH_MIXED, "learned": CBP_PATH_LEARNED}
 
 # Every symbol include/cbp.h declares (checked by the CPU tests).

@@ -68,6 +68,7 @@ struct Plan {
   int learned;                 // learned path: proposal + consistency gate first
   int col_strips;              // column strips of the column pass
   int col_fused;               // column pass computes the kernel spectra itself (no K^ buffer)
+  int scale_mode;              // 0: two-order least squares, 1: k1-only, 2: support constraint
   double accept_rho;
   double eps;
   FftPlan fp_h, fp_w, fp_w2;   // plans of Ph, Pw, Pw/2

@@ -135,6 +135,12 @@ cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_param
   p.fft_f64 = (frame_f64 && !p.mixed) ? 1 : 0;
   p.frames_f64 = frame_f64;
   p.single_kernel = (prm->flags & CBP_FLAG_SINGLE_KERNEL) ? 1 : 0;
+  const bool k1_only = (prm->flags & CBP_FLAG_K1_ONLY) != 0;
+  const bool support = (prm->flags & CBP_FLAG_SCALE_SUPPORT) != 0;
+  if (k1_only && support) return CBP_ERR_INVALID_ARG;
+  if (support && p.M <= std::max(t1, t2)) return CBP_ERR_INVALID_ARG;   // needs M > t
+  p.scale_mode = k1_only ? 1 : support ? 2 : 0;
+  if (k1_only) p.single_kernel = 1;            // the paper's division of B1 by K1
   p.learned = prm->path == CBP_PATH_LEARNED ? 1 : 0;
   if (p.learned && (t1 != kCnnT || t2 != kCnnT)) return CBP_ERR_UNSUPPORTED;  // network output size
   if (p.learned && !(prm->accept_rho >= 0.0)) return CBP_ERR_INVALID_ARG;

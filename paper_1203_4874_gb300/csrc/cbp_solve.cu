@@ -625,7 +625,12 @@ struct ScaleArgs {
   const int* accepted;  // learned path: proposal passed the gate (kernels already in kd)
   const double* rho;    // learned path: consistency residual of the proposal
   int M, ns, t1, t2, nn, mixed, Ph, Pw;
+  int mode;             // kScaleLS, kScaleK1, kScaleSupport
 };
+
+// Scale fixes: both kernels' two-order least squares; kernel 1's equations
+// only (the paper's k1-only pipeline); the single-pass support constraint.
+constexpr int kScaleLS = 0, kScaleK1 = 1, kScaleSupport = 2;
 
 // w^k (sign -1) or w^-k (sign +1), w = exp(-2 pi i / M), from a table of w^j, j < M.
 __device__ __forceinline__ cd root(const cd* wt, int k, int M, double sign) {
@@ -646,11 +651,12 @@ __device__ __forceinline__ cd cofactor(const ScaleArgs& a, int f, int ps, int s,
 struct ScaleApply {
   const cd* ab;
   int M;
+  int nk;               // kernels whose equations enter (2, or 1 for the k1-only fix)
   __device__ void operator()(const cd* th, cd* out) const {
     const int MM = M * M;
     for (int u = threadIdx.x; u < 2 * M; u += blockDim.x) {
       cd acc = mk(0.0, 0.0);
-      for (int k = 0; k < 2; ++k) {
+      for (int k = 0; k < nk; ++k) {
         const cd* A = ab + k * MM;
         const cd* B = ab + (2 + k) * MM;
         for (int t = 0; t < M; ++t) {
@@ -666,6 +672,35 @@ struct ScaleApply {
         }
       }
       out[u] = acc;
+    }
+    __syncthreads();
+  }
+};
+
+// Exact operator of the support-constrained system (rows r_j = A_k[i][j] w^(-j q),
+// k = 1, 2, every i, t_k <= q < M): out = S^H (S theta), S theta staged in s.
+struct SupportApply {
+  const cd* ab;
+  const cd* wt;
+  cd* s;                // [2][M][M] scratch (k, i, q)
+  int M, t1, t2;
+  __device__ void operator()(const cd* th, cd* out) const {
+    const int MM = M * M;
+    for (int e = threadIdx.x; e < 2 * MM; e += blockDim.x) {
+      const int k = e / MM, i = (e % MM) / M, q = e % M;
+      cd acc = mk(0.0, 0.0);
+      if (q >= (k ? t2 : t1))
+        for (int j = 0; j < M; ++j) cfma(acc, ab[k * MM + i * M + j] * root(wt, j * q, M, 1.0), th[j]);
+      s[e] = acc;
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < M; j += blockDim.x) {
+      cd acc = mk(0.0, 0.0);
+      for (int k = 0; k < 2; ++k)
+        for (int i = 0; i < M; ++i)
+          for (int q = k ? t2 : t1; q < M; ++q)
+            cfmac(acc, ab[k * MM + i * M + j] * root(wt, j * q, M, 1.0), s[k * MM + i * M + q]);
+      out[j] = acc;
     }
     __syncthreads();
   }
@@ -712,7 +747,9 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
     return;
   }
   const int M = a.M, MM = M * M, t1 = a.t1, t2 = a.t2;
-  const int n = 2 * M;
+  const int mode = a.mode;
+  const int n = mode == kScaleSupport ? M : 2 * M;   // unknowns: gamma (support) or (gamma, delta)
+  const int nk = mode == kScaleK1 ? 1 : 2;            // kernels estimated
 #ifdef CBP_PHASE_TIMING
   long long ph[8] = {0, 0, 0, 0, 0, 0, 0, 0}, tkv[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   long long* tk = f < 2 ? tkv : nullptr;
@@ -751,23 +788,32 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
   for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
     const int r = idx / n, c = idx % n;
     cd g = mk(0.0, 0.0);
-    if (r < M && c < M) {
+    if (mode == kScaleSupport) {
+      // sum over rows (k, i, q >= t_k) of conj(A_k[i][r] w^-rq) A_k[i][c] w^-cq
+      for (int k = 0; k < 2; ++k) {
+        cd e = mk(0.0, 0.0);                   // sum_q w^((r - c) q), q = t_k .. M-1
+        for (int q = k ? t2 : t1; q < M; ++q) e = e + root(wt, ((r - c + M) % M) * q, M, -1.0);
+        cd h = mk(0.0, 0.0);
+        for (int i = 0; i < M; ++i) cfmac(h, ab[k * MM + i * M + r], ab[k * MM + i * M + c]);
+        g = g + h * e;
+      }
+    } else if (r < M && c < M) {
       if (r == c)
-        for (int k = 0; k < 2; ++k)
+        for (int k = 0; k < nk; ++k)
           for (int i = 0; i < M; ++i) g.re += abs2(ab[k * MM + i * M + r]);
     } else if (r >= M && c >= M) {
       if (r == c)
-        for (int k = 0; k < 2; ++k)
+        for (int k = 0; k < nk; ++k)
           for (int j = 0; j < M; ++j) g.re += abs2(ab[(2 + k) * MM + (r - M) * M + j]);
     } else if (r < M) {   // (gamma_j, delta_i) = -sum_k conj(A_k[i][j]) B_k[i][j]
       const int j = r, i = c - M;
-      for (int k = 0; k < 2; ++k) {
+      for (int k = 0; k < nk; ++k) {
         cd v = cmulc(ab[k * MM + i * M + j], ab[(2 + k) * MM + i * M + j]);
         g = g - v;
       }
     } else {
       const int j = c, i = r - M;
-      for (int k = 0; k < 2; ++k) {
+      for (int k = 0; k < nk; ++k) {
         cd v = cmulc(ab[(2 + k) * MM + i * M + j], ab[k * MM + i * M + j]);
         g = g - v;
       }
@@ -779,16 +825,25 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
   // Null vector of the scale system by the warp-level tridiagonal solver, one
   // refinement step against the exact operator (FP64 path); the mixed path
   // takes its single-precision T with Newton steps against the double G.
-  ScaleApply ap{ab, M};
   const TriWs W = carve_tri(smem + scale_tri_offset(M), n);
-  const TriResult res = tri_smallest<cd, true>(W, Gs, n, 1, 1, 1e300, ap, tk, a.mixed != 0);
+  TriResult res;
+  if (mode == kScaleSupport) {
+    SupportApply ap{ab, wt, X, M, t1, t2};      // X is free until the combination below
+    res = tri_smallest<cd, true>(W, Gs, n, 1, 1, 1e300, ap, tk, a.mixed != 0);
+  } else {
+    ScaleApply ap{ab, M, nk};
+    res = tri_smallest<cd, true>(W, Gs, n, 1, 1, 1e300, ap, tk, a.mixed != 0);
+  }
   __syncthreads();
   CBP_TICK(ph, 3);
   const cd* xs = W.x;
-  // X_k[i][j] = (gamma_j A_k[i][j] + delta_i B_k[i][j]) / 2
+  // X_k[i][j] = (gamma_j A_k[i][j] + delta_i B_k[i][j]) / 2, or gamma_j A_k[i][j]
+  // (support); the k1-only fix leaves kernel 2's spectrum zero
   for (int idx = threadIdx.x; idx < 2 * MM; idx += blockDim.x) {
     const int k = idx / MM, i = (idx % MM) / M, j = idx % M;
-    X[idx] = 0.5 * (xs[j] * ab[k * MM + i * M + j] + xs[M + i] * ab[(2 + k) * MM + i * M + j]);
+    if (k >= nk) X[idx] = mk(0.0, 0.0);
+    else if (mode == kScaleSupport) X[idx] = xs[j] * ab[k * MM + i * M + j];
+    else X[idx] = 0.5 * (xs[j] * ab[k * MM + i * M + j] + xs[M + i] * ab[(2 + k) * MM + i * M + j]);
   }
   __syncthreads();
   __shared__ cd x00[2];
@@ -798,6 +853,12 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
   // inverse DFT, separable: T[i][q] = sum_j X[i][j] w^{-jq};  K[p][q] = sum_i w^{-ip} T[i][q] / M^2
   __shared__ double acc_sq[4];  // re^2, im^2, outside-support, total  (per kernel, reused)
   for (int k = 0; k < 2; ++k) {
+    if (k >= nk) {
+      // k1-only: no kernel 2 (its internal copy zeroed, the caller's buffer untouched)
+      double* kd2 = a.kd + (int64_t)f * (t1 * t1 + t2 * t2) + t1 * t1;
+      for (int e = threadIdx.x; e < t2 * t2; e += blockDim.x) kd2[e] = 0.0;
+      continue;
+    }
     cd* Xk = X + k * MM;
     const cd inv00 = [&] {
       cd z = x00[k];
@@ -893,7 +954,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
     int st = CBP_OK;
     if (*a.err) st = CBP_ERR_TIMEOUT;
     else if (a.bad[f]) st = CBP_ERR_INVALID_ARG;
-    else if (!(x00[0].re != 0.0 || x00[0].im != 0.0) || !(x00[1].re != 0.0 || x00[1].im != 0.0))
+    else if (!(x00[0].re != 0.0 || x00[0].im != 0.0) ||
+             (nk > 1 && !(x00[1].re != 0.0 || x00[1].im != 0.0)))
       st = CBP_ERR_NOT_COPRIME;
     else if (gap < 1e-13) st = CBP_ERR_NOT_COPRIME;
     else if (flagged) st = CBP_WARN_ILL_CONDITIONED;
@@ -1170,6 +1232,7 @@ void launch_scale_solve(const Plan& p, char* ws, void* k1_out, void* k2_out, int
   a.Pw = p.Pw;
   a.accepted = p.learned ? (const int*)(ws + p.off_acc) : nullptr;
   a.rho = p.learned ? (const double*)(ws + p.off_rho) : nullptr;
+  a.mode = p.scale_mode;
   const size_t sm = scale_solve_smem(p.M);
   cudaFuncSetAttribute(k_scale_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_scale_solve<<<p.n, kSolveThreads, sm, st>>>(a);

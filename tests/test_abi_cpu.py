@@ -117,3 +117,32 @@ def test_noalloc_size_check_on_the_1080p_rgb_workload(built_lib):
                 assert s == cbp.CBP_ERR_CUDA, (path, n, s)
             else:
                 assert s == cbp.CBP_ERR_UNSUPPORTED, (path, n, s)
+
+
+def test_scale_variant_flags_validated(built_lib):
+    from paper_1203_4874_gb300 import cbp
+    f1, f2 = _frames(1, 1, 68, 68), _frames(1, 1, 68, 68)
+    assert _ws(f1, f2, cbp.params(5, 5, m=7, flags=cbp.CBP_FLAG_SCALE_SUPPORT))[0] == cbp.CBP_OK
+    assert _ws(f1, f2, cbp.params(5, 5, flags=cbp.CBP_FLAG_SCALE_SUPPORT))[0] == cbp.CBP_ERR_INVALID_ARG
+    both = cbp.CBP_FLAG_SCALE_SUPPORT | cbp.CBP_FLAG_K1_ONLY
+    assert _ws(f1, f2, cbp.params(5, 5, m=7, flags=both))[0] == cbp.CBP_ERR_INVALID_ARG
+    assert _ws(f1, f2, cbp.params(5, 5, flags=cbp.CBP_FLAG_K1_ONLY))[0] == cbp.CBP_OK
+
+
+def test_size_and_encrypt_validation(built_lib):
+    from paper_1203_4874_gb300 import cbp
+    import ctypes
+    L = cbp.lib()
+    t1 = (ctypes.c_int32 * 1)()
+    t2 = (ctypes.c_int32 * 1)()
+    # blurred sizes that disagree on t1 - t2
+    s = L.cbp_estimate_size(ctypes.c_void_p(1), ctypes.byref(_frames(1, 1, 70, 68)),
+                            ctypes.byref(_frames(1, 1, 68, 68)), None, t1, t2, None, None, None, None)
+    assert s == cbp.CBP_ERR_SIZE_MISMATCH
+    prm = cbp.cbp_encrypt_params(0, 5, 0, 0, 0, 0, 0.0, 0.0, 1, 0, 0)
+    s = L.cbp_encrypt(ctypes.c_void_p(1), ctypes.c_void_p(0x1000), 1, 1, 8, 8, cbp.CBP_F32, ctypes.byref(prm),
+                      ctypes.c_void_p(0x2000), ctypes.c_void_p(0x3000), ctypes.c_void_p(0x4000),
+                      ctypes.c_void_p(0x5000), None, None, None, None, None, None)
+    assert s == cbp.CBP_ERR_INVALID_ARG
+    assert L.cbp_truncate_lsb(ctypes.c_void_p(1), ctypes.c_void_p(0x1000), cbp.CBP_F32, 10, 16, 16,
+                              ctypes.c_void_p(0x1000), None) == cbp.CBP_ERR_INVALID_ARG
