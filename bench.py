@@ -214,7 +214,7 @@ def job_rate(world: int, n: int, steps: int, ms: float) -> float:
 
 # ----------------------------------------------------------------- inputs ---
 def make_inputs(ctx, n: int, seed0: int, device, t1: int = T1, t2: int = T2, keep: int = 0,
-                sigma: float = SIGMA):
+                sigma: float = SIGMA, h: int = H, w: int = W, c: int = C, family: str = "mixture"):
     """Kernels and blob parameters drawn on the host (cbp_synth), latents and
     blurred frames synthesised on the device by the library's forward model.
     keep > 0: also returns the true latents of the first `keep` pairs (host)."""
@@ -226,14 +226,14 @@ def make_inputs(ctx, n: int, seed0: int, device, t1: int = T1, t2: int = T2, kee
     k1s, k2s, blobs = [], [], []
     for f in range(n):
         rng = _rng(seed0 + f)
-        blobs.append(np.stack([blob_params(rng, H, W) for _ in range(C)]))
-        a, b = draw_kernel_pair(rng, t1, t2, max(t1, t2), "mixture")
+        blobs.append(np.stack([blob_params(rng, h, w) for _ in range(c)]))
+        a, b = draw_kernel_pair(rng, t1, t2, max(t1, t2), family)
         k1s.append(a)
         k2s.append(b)
     k1 = torch.from_numpy(np.stack(k1s)).to(device)
     k2 = torch.from_numpy(np.stack(k2s)).to(device)
     bl = torch.from_numpy(np.stack(blobs)).to(device)
-    lat = cbp.cbp_synth_latent(ctx, bl, n, C, H, W, torch.float32, 0.05, seed0)
+    lat = cbp.cbp_synth_latent(ctx, bl, n, c, h, w, torch.float32, 0.05, seed0)
     b1 = cbp.cbp_forward_blur(ctx, lat, k1, sigma, seed0 * 2 + 1)
     b2 = cbp.cbp_forward_blur(ctx, lat, k2, sigma, seed0 * 2 + 2)
     torch.cuda.synchronize()
@@ -392,6 +392,116 @@ def learned_bench(ctx, n: int, device, steps: int = 3) -> dict:
     return {"workload": f"{n} pairs/step, 1920x1080x3 f32, both kernels 15x15 (mixture), noise sigma 1e-3, "
                         "accept_rho 1e-3, trained weights (200k pairs)", "unit": UNIT,
             "learned": out["learned"], "mixed": out["mixed"]}
+
+
+# ------------------------------------------------- the paper's other rows --
+def _kerr(k1, k2, k1t, k2t):
+    """Per-pair relative L2 error of both kernels against the truth."""
+    import torch
+    g = torch.cat([k1.flatten(1).double(), k2.flatten(1).double()], 1)
+    t = torch.cat([k1t.flatten(1).double(), k2t.flatten(1).double()], 1)
+    return ((g - t).norm(dim=1) / t.norm(dim=1)).cpu().tolist()
+
+
+def _psnr_t(x, ref):
+    import torch
+    mse = ((x.double() - ref.double()) ** 2).flatten(1).mean(1)
+    peak = ref.double().flatten(1).abs().max(1).values
+    return (10 * torch.log10(peak * peak / mse)).cpu().tolist()
+
+
+def _timed(fn, reps=3):
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        fn()
+    torch.cuda.synchronize()
+    return 1e3 * (time.perf_counter() - t0) / reps
+
+
+def size_estimation_bench(ctx, device, pairs: int = 4) -> dict:
+    """Kernel-size estimation (Section 4-5's degree step) on the first pairs
+    of the 1080p RGB workload, noise-free and at sigma 1e-3."""
+    from paper_1203_4874_gb300 import cbp
+    out = []
+    for sg in (0.0, SIGMA):
+        b1, b2, _, _ = make_inputs(ctx, pairs, 1203000, device, sigma=sg)
+        res = {}
+        ms = _timed(lambda: res.update(r=cbp.cbp_estimate_size(ctx, b1, b2, 5, 21)), reps=2)
+        t1, t2, found, _ = res["r"]
+        out.append({"sigma": sg, "t1": t1, "t2": t2, "found": found,
+                    "recovered": sum(1 for a, b in zip(t1, t2) if (a, b) == (T1, T2)), "ms_per_call": ms})
+        del b1, b2
+    return {"workload": f"{pairs} pairs of {WORKLOAD}, true sizes {T1}/{T2}, candidates 5..21, tol 1e-6",
+            "points": out}
+
+
+def multilevel_bench(ctx, device, pairs: int = 4) -> dict:
+    """Multi-level security (Section 3): the private stream with its `drop`
+    least significant bits (of 16) removed, deblurred on the mixed path;
+    480p grayscale, kernels 9 / 11, noise-free latents."""
+    from paper_1203_4874_gb300 import cbp
+    b1, b2, k1t, k2t, truth = make_inputs(ctx, pairs, 4874, device, 9, 11, keep=pairs, sigma=0.0,
+                                          h=480, w=640, c=1, family="uniform")
+    truth = truth.to(device)
+    out = []
+    for drop in (0, 2, 4, 6, 8):
+        b2t = cbp.cbp_truncate_lsb(ctx, b2, 16, drop)
+        b1q = cbp.cbp_truncate_lsb(ctx, b1, 16, 0)          # the public stream at full resolution
+        prm = cbp.params(9, 11, path="mixed", eps=EPS, flags=cbp.CBP_FLAG_KERNELS_F64)
+        lat, k1, k2, _, _ = cbp.cbp_deblur_pair(ctx, b1q, b2t, prm)
+        out.append({"drop_bits": drop, "kernel_rel_err_vs_truth": _kerr(k1, k2, k1t, k2t),
+                    "latent_psnr_db": _psnr_t(lat, truth)})
+    return {"workload": f"{pairs} pairs, 480x640 grayscale f32, kernels 9x9 + 11x11 (U[0,1]), noise-free, "
+                        "16-bit codes, private stream truncated, mixed path", "points": out}
+
+
+def camera_bench(ctx, device, n: int = 60, reps: int = 3) -> dict:
+    """Encryption at camera rate (Section 3): per-frame coprime kernel pairs
+    drawn and tested on the device, both streams blurred; then with the
+    cascaded pair.  1080p RGB f32 latents resident on the device."""
+    import torch
+    from paper_1203_4874_gb300 import cbp
+    lat = torch.rand((n, C, H, W), dtype=torch.float32, device=device)
+    res = {}
+    ms = _timed(lambda: res.update(o=cbp.cbp_encrypt(ctx, lat, T1, T2, seed=1, sigma=SIGMA)), reps)
+    att = res["o"]["attempts"]
+    del res["o"]
+    ms_c = _timed(lambda: res.update(o=cbp.cbp_encrypt(ctx, lat, T1, T2, seed=1, sigma=SIGMA, cascade=(9, 11))),
+                  reps)
+    del res["o"]
+    return {"workload": f"{n} frames 1920x1080x3 f32 per call, kernels {T1}x{T1} + {T2}x{T2} (U[0,1], "
+                        "redrawn until coprime at every sample), sigma 1e-3; cascade 9x9 + 11x11",
+            "unit": "frames/s", "pair": {"value": n / (ms / 1e3), "ms_per_call": ms},
+            "pair_and_cascade": {"value": n / (ms_c / 1e3), "ms_per_call": ms_c},
+            "redraws": sum(1 for a in att if a > 0), "failed": sum(1 for a in att if a < 0)}
+
+
+def scale_variants_bench(ctx, device, pairs: int = 8) -> dict:
+    """The scale fixes compared (Sections 4-5): two-order least squares with
+    both kernels (the default), the paper's k1-only pipeline, and the
+    single-pass support constraint (m = 13 > 11); 480p grayscale 9 / 11."""
+    from paper_1203_4874_gb300 import cbp
+    out = []
+    for sg in (0.0, SIGMA):
+        b1, b2, k1t, k2t = make_inputs(ctx, pairs, 4874, device, 9, 11, sigma=sg, h=480, w=640, c=1,
+                                       family="uniform")
+        row = {"sigma": sg}
+        for name, m, flags in (("least_squares", 0, 0), ("k1_only", 0, cbp.CBP_FLAG_K1_ONLY),
+                               ("support", 13, cbp.CBP_FLAG_SCALE_SUPPORT)):
+            prm = cbp.params(9, 11, m=m, path="fp64", eps=EPS, flags=flags | cbp.CBP_FLAG_KERNELS_F64)
+            res = {}
+            ms = _timed(lambda: res.update(r=cbp.cbp_estimate_kernels(ctx, b1, b2, prm)), reps=2)
+            k1, k2 = res["r"][0], res["r"][1]
+            e1 = ((k1.flatten(1) - k1t.flatten(1)).norm(dim=1) / k1t.flatten(1).norm(dim=1)).cpu().tolist()
+            row[name] = {"k1_rel_err_vs_truth": e1, "ms_per_call": ms}
+            if name != "k1_only":
+                row[name]["kernel_rel_err_vs_truth"] = _kerr(k1, k2, k1t, k2t)
+        out.append(row)
+    return {"workload": f"{pairs} pairs, 480x640 grayscale f32, kernels 9x9 + 11x11 (U[0,1]), FP64 path",
+            "points": out}
 
 
 # ------------------------------------------------------- CPU oracle sample --
@@ -583,6 +693,8 @@ def main():
                     help="pairs of the GPU's batch the oracle deblurs on the host (timed, and "
                          "the errors of the GPU results against it)")
     ap.add_argument("--no-noise-sweep", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the size-estimation, multi-level, camera-side and scale-fix sections")
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -747,6 +859,11 @@ def main():
         result["serving"] = serving_bench(args.serve_seconds, dev)
     if rank == 0 and not args.no_noise_sweep:
         result["noise_sweep"] = noise_sweep(ctx, dev)
+    if rank == 0 and not args.no_extras:
+        result["size_estimation"] = size_estimation_bench(ctx, dev)
+        result["multilevel_security"] = multilevel_bench(ctx, dev)
+        result["camera_side"] = camera_bench(ctx, dev)
+        result["scale_variants"] = scale_variants_bench(ctx, dev)
     if keep:
         folder = Path(tempfile.mkdtemp(prefix="cbp_bench_"))
         try:

@@ -134,6 +134,9 @@ typedef struct cbp_diag {
   int32_t status;          /* cbp_status derived from the fields above             */
   int32_t hard_samples;    /* samples whose two smallest normal-matrix eigenvalues
                               are within 1e-4 of the largest (near-degenerate)  */
+  double gpu_start_ms;     /* serving: the request's batch began / ended on the   */
+  double gpu_end_ms;       /* device, ms after the engine started (CUDA events);
+                              0 for the synchronous calls                          */
 } cbp_diag;
 
 typedef struct cbp_ctx cbp_ctx;

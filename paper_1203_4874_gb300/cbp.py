@@ -78,7 +78,7 @@ class cbp_diag(ctypes.Structure):
                 ("scale_resid", c_double), ("imag_ratio", c_double), ("support_ratio", c_double),
                 ("rho", c_double), ("flagged_samples", c_int32), ("used_fallback", c_int32),
                 ("pad_h", c_int32), ("pad_w", c_int32), ("status", c_int32),
-                ("hard_samples", c_int32)]
+                ("hard_samples", c_int32), ("gpu_start_ms", c_double), ("gpu_end_ms", c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

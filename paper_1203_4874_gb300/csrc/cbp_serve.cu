@@ -104,6 +104,7 @@ struct Entry {
 struct Slot {
   cudaStream_t st = nullptr;
   cudaEvent_t ev = nullptr;
+  cudaEvent_t t0 = nullptr, t1 = nullptr;   // timing: the batch's start and end on the device
   uint64_t* tab_host = nullptr;   // pinned [kTables][kMaxBatch]
   cbp_diag* diag_host = nullptr;  // pinned [kMaxBatch]
   std::vector<Request*> batch;
@@ -132,6 +133,7 @@ struct ServeState {
   std::vector<double> lat_ms;
   uint64_t completed = 0;
   std::thread th;
+  cudaEvent_t ref = nullptr;        // the engine's start on the device (batch timestamps)
 
   void finish(Request* r, cbp_status s, const cbp_diag* d, Clock::time_point now) {
     r->status = s;
@@ -257,9 +259,11 @@ struct ServeState {
       s.tab_host[3 * B + i] = (uint64_t)r->k2;
       s.tab_host[4 * B + i] = (uint64_t)r->lat;
     }
-    bool ok = cudaMemcpyAsync(e->tab, s.tab_host, (size_t)kTables * B * sizeof(uint64_t),
-                              cudaMemcpyHostToDevice, s.st) == cudaSuccess;
+    bool ok = cudaEventRecord(s.t0, s.st) == cudaSuccess;
+    ok = ok && cudaMemcpyAsync(e->tab, s.tab_host, (size_t)kTables * B * sizeof(uint64_t),
+                               cudaMemcpyHostToDevice, s.st) == cudaSuccess;
     ok = ok && cudaGraphLaunch(e->exec, s.st) == cudaSuccess;
+    ok = ok && cudaEventRecord(s.t1, s.st) == cudaSuccess;
     ok = ok && cudaMemcpyAsync(s.diag_host, e->mem + e->plan.off_diag, (size_t)B * sizeof(cbp_diag),
                                cudaMemcpyDeviceToHost, s.st) == cudaSuccess;
     ok = ok && cudaEventRecord(s.ev, s.st) == cudaSuccess;
@@ -333,8 +337,16 @@ struct ServeState {
       if (q == cudaErrorNotReady) continue;
       const auto now = Clock::now();
       if (q != cudaSuccess) cudaGetLastError();
+      float a_ms = 0.f, b_ms = 0.f;
+      if (q == cudaSuccess && (cudaEventElapsedTime(&a_ms, ref, s.t0) != cudaSuccess ||
+                               cudaEventElapsedTime(&b_ms, ref, s.t1) != cudaSuccess)) {
+        cudaGetLastError();
+        a_ms = b_ms = 0.f;
+      }
       for (size_t i = 0; i < s.batch.size(); ++i) {
-        const cbp_diag& d = s.diag_host[i];
+        cbp_diag d = s.diag_host[i];
+        d.gpu_start_ms = a_ms;
+        d.gpu_end_ms = b_ms;
         finish(s.batch[i], q == cudaSuccess ? (cbp_status)d.status : CBP_ERR_CUDA, &d, now);
       }
       s.batch.clear();
@@ -349,10 +361,14 @@ struct ServeState {
     for (Slot& s : slots) {
       if (cudaStreamCreateWithFlags(&s.st, cudaStreamNonBlocking) != cudaSuccess ||
           cudaEventCreateWithFlags(&s.ev, cudaEventDisableTiming) != cudaSuccess ||
+          cudaEventCreate(&s.t0) != cudaSuccess || cudaEventCreate(&s.t1) != cudaSuccess ||
           cudaMallocHost((void**)&s.tab_host, sizeof(uint64_t) * kTables * kMaxBatch) != cudaSuccess ||
           cudaMallocHost((void**)&s.diag_host, sizeof(cbp_diag) * kMaxBatch) != cudaSuccess)
         is = CBP_ERR_CUDA;
     }
+    if (is == CBP_OK && (cudaEventCreate(&ref) != cudaSuccess || cudaEventRecord(ref, slots[0].st) != cudaSuccess ||
+                         cudaEventSynchronize(ref) != cudaSuccess))
+      is = CBP_ERR_CUDA;
     std::unique_lock<std::mutex> lk(mu);
     init_status = is;
     ready = true;
@@ -372,10 +388,13 @@ struct ServeState {
       s.cache.clear();
       if (s.st) cudaStreamSynchronize(s.st);
       if (s.ev) cudaEventDestroy(s.ev);
+      if (s.t0) cudaEventDestroy(s.t0);
+      if (s.t1) cudaEventDestroy(s.t1);
       if (s.st) cudaStreamDestroy(s.st);
       if (s.tab_host) cudaFreeHost(s.tab_host);
       if (s.diag_host) cudaFreeHost(s.diag_host);
     }
+    if (ref) cudaEventDestroy(ref);
   }
 };
 

@@ -32,12 +32,12 @@ def _outputs(cbp, b1, cfg, prm, deblur=True):
     return k1, k2, lat
 
 
-def _prm(cbp, cfg):
-    return cbp.params(cfg.t1, cfg.t2, path=cfg.path, eps=cfg.eps)
+def _prm(cbp, cfg, path=None):
+    return cbp.params(cfg.t1, cfg.t2, path=path or cfg.path, eps=cfg.eps)
 
 
-def _submit(cbp, ctx, b1, b2, cfg, deblur=True):
-    prm = _prm(cbp, cfg)
+def _submit(cbp, ctx, b1, b2, cfg, deblur=True, path=None):
+    prm = _prm(cbp, cfg, path)
     k1, k2, lat = _outputs(cbp, b1, cfg, prm, deblur)
     t = cbp.cbp_stream_submit(ctx, b1, b2, prm, k1, k2, lat)
     return t, (k1, k2, lat)
@@ -49,26 +49,30 @@ def _wait(cbp, ctx, t):
     return s, d
 
 
-def test_identical_alone_in_mix_and_sync(gpu_ctx):
+@pytest.mark.parametrize("path", [None, "mixed"])
+def test_identical_alone_in_mix_and_sync(gpu_ctx, path):
+    """Alone, in a mix of buckets, and from the synchronous call: the same
+    result, bit for bit -- on each workload's own path and on the mixed path
+    the serving benchmark runs."""
     from paper_1203_4874_gb300 import cbp
     a1, a2, cfg = _pair("video_480p", 0, 60, 80)
     b1, b2, _ = _pair("video_480p", 1, 60, 80)
     c1, c2, _ = _pair("video_480p", 2, 48, 64)       # another bucket
     d1, d2, _ = _pair("video_480p", 3, 60, 80)
     e1, e2, cfg64 = _pair("single_64", 0, None, None)  # float64 frames, another bucket
-    ta, outa = _submit(cbp, gpu_ctx, a1, a2, cfg)
+    ta, outa = _submit(cbp, gpu_ctx, a1, a2, cfg, path=path)
     _wait(cbp, gpu_ctx, ta)
     # the same request again, in a mix of buckets
     tickets = []
     for x1, x2, cf in ((b1, b2, cfg), (c1, c2, cfg), (a1, a2, cfg), (e1, e2, cfg64), (d1, d2, cfg)):
-        tickets.append(_submit(cbp, gpu_ctx, x1, x2, cf))
+        tickets.append(_submit(cbp, gpu_ctx, x1, x2, cf, path=path))
     for t, _ in tickets:
         _wait(cbp, gpu_ctx, t)
     outa2 = tickets[2][1]
     for x, y in zip(outa, outa2):
         assert torch.equal(x, y)
     # and the synchronous call on the same pair
-    lat, k1, k2, _, st = cbp.cbp_deblur_pair(gpu_ctx, a1, a2, _prm(cbp, cfg))
+    lat, k1, k2, _, st = cbp.cbp_deblur_pair(gpu_ctx, a1, a2, _prm(cbp, cfg, path))
     torch.cuda.synchronize()
     assert st >= 0
     assert torch.equal(k1, outa[0]) and torch.equal(k2, outa[1]) and torch.equal(lat, outa[2])
@@ -165,3 +169,26 @@ def test_small_budget_admission(built_lib):
         assert cbp.cbp_stream_stats(ctx)["completed"] == 6
     finally:
         cbp.cbp_destroy(ctx)
+
+
+def test_two_buckets_overlap_on_the_device(gpu_ctx):
+    """Requests of two buckets submitted together run as two batches on two
+    slot streams at once: their device intervals (CUDA events around each
+    batch) overlap."""
+    from paper_1203_4874_gb300 import cbp
+    a1, a2, cfg = _pair("rgb_1080p", 0, 720, 1280)
+    b1, b2, _ = _pair("rgb_1080p", 1, 540, 960)           # another bucket
+    prm_a = cbp.params(cfg.t1, cfg.t2, path="mixed", eps=cfg.eps)
+    # warm the engine (graph captures) so that both batches launch at once
+    for x1, x2 in ((a1, a2), (b1, b2)):
+        k1, k2, lat = _outputs(cbp, x1, cfg, prm_a)
+        _wait(cbp, gpu_ctx, cbp.cbp_stream_submit(gpu_ctx, x1, x2, prm_a, k1, k2, lat))
+    outs, tickets = [], []
+    for x1, x2 in ((a1, a2), (b1, b2)):
+        k1, k2, lat = _outputs(cbp, x1, cfg, prm_a)
+        outs.append((k1, k2, lat))
+        tickets.append(cbp.cbp_stream_submit(gpu_ctx, x1, x2, prm_a, k1, k2, lat))
+    (_, da), (_, db) = (_wait(cbp, gpu_ctx, t) for t in tickets)
+    assert 0 < da.gpu_start_ms < da.gpu_end_ms and 0 < db.gpu_start_ms < db.gpu_end_ms
+    overlap = min(da.gpu_end_ms, db.gpu_end_ms) - max(da.gpu_start_ms, db.gpu_start_ms)
+    assert overlap > 0, (da.gpu_start_ms, da.gpu_end_ms, db.gpu_start_ms, db.gpu_end_ms)
