@@ -83,6 +83,71 @@ k_forward_blur(const T* lat, int c, int h, int w, const double* kern, int t, dou
   }
 }
 
+// The same convolution for float frames with the kernel size fixed at compile
+// time (T <= 17): a block makes 64 rows x 32 columns of output; a thread keeps
+// eight consecutive output rows of one column and, for each kernel column q,
+// the T + 7 input values they need in registers, so each shared-memory load
+// feeds about four multiply-adds.  Sums in float, in the order p = T-1 .. 0
+// for every q (as the general kernel's per-output order differs, results
+// agree to float rounding, not bitwise).
+constexpr int kBlurRows = 8;          // output rows per thread
+constexpr int kBlurTileR = 8 * kBlurRows;
+template <int T>
+__global__ void __launch_bounds__(256)
+k_forward_blur_rb(const float* lat, int c, int h, int w, const double* kern, double sigma,
+                  uint64_t seed, float* out) {
+  __shared__ float K[T * T];
+  __shared__ float tile[(kBlurTileR + T - 1) * (32 + T - 1)];
+  constexpr int TW = 32 + T - 1, TH = kBlurTileR + T - 1;
+  const int hb = h + T - 1, wb = w + T - 1;
+  const int fc = blockIdx.z, f = fc / c;
+  const int r0 = blockIdx.y * kBlurTileR, c0 = blockIdx.x * 32;
+  for (int i = threadIdx.x; i < T * T; i += blockDim.x) K[i] = (float)kern[(int64_t)f * T * T + i];
+  const float* L = lat + (int64_t)fc * h * w;
+  for (int i = threadIdx.x; i < TH * TW; i += blockDim.x) {
+    const int y = i / TW, x = i - y * TW;
+    const int ly = r0 - (T - 1) + y, lx = c0 - (T - 1) + x;
+    tile[i] = (ly >= 0 && ly < h && lx >= 0 && lx < w) ? L[(int64_t)ly * w + lx] : 0.f;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  float acc[kBlurRows];
+#pragma unroll
+  for (int i = 0; i < kBlurRows; ++i) acc[i] = 0.f;
+  // out[r][col] = sum_{p,q} K[p][q] tile[(r - r0) + T-1-p][(col - c0) + T-1-q]
+  for (int q = 0; q < T; ++q) {
+    float v[kBlurRows + T - 1];
+    const float* col = tile + (ty * kBlurRows) * TW + tx + T - 1 - q;
+#pragma unroll
+    for (int j = 0; j < kBlurRows + T - 1; ++j) v[j] = col[j * TW];
+#pragma unroll
+    for (int p = 0; p < T; ++p) {
+      const float kv = K[p * T + q];
+#pragma unroll
+      for (int i = 0; i < kBlurRows; ++i) acc[i] = fmaf(kv, v[i + T - 1 - p], acc[i]);
+    }
+  }
+  const int colo = c0 + tx;
+  if (colo >= wb) return;
+#pragma unroll
+  for (int i = 0; i < kBlurRows; ++i) {
+    const int r = r0 + ty * kBlurRows + i;
+    if (r >= hb) break;
+    const int64_t oi = ((int64_t)fc * hb + r) * wb + colo;
+    float a = acc[i];
+    if (sigma > 0) a += (float)sigma * normal_at_f(seed, (uint64_t)oi, 1u);
+    out[oi] = a;
+  }
+}
+
+template <int T>
+void launch_blur_rb(const float* lat, int n, int c, int h, int w, const double* kern, double sigma,
+                    uint64_t seed, float* out, cudaStream_t st) {
+  const int hb = h + T - 1, wb = w + T - 1;
+  dim3 g((wb + 31) / 32, (hb + kBlurTileR - 1) / kBlurTileR, n * c);
+  k_forward_blur_rb<T><<<g, 256, 0, st>>>(lat, c, h, w, kern, sigma, seed, out);
+}
+
 // Blob latent: L = sum_k a_k exp(-((x-cx)^2 + (y-cy)^2) / (2 s^2)) + U[0, floor].
 template <typename T>
 __global__ void k_synth_latent(const double* blobs, int nblobs, int c, int h, int w,
@@ -172,6 +237,18 @@ void launch_forward_blur(const void* latent, int n, int c, int h, int w, int f64
     cudaFuncSetAttribute(k_forward_blur<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_forward_blur<double><<<g, kTile * 8, sm, st>>>((const double*)latent, c, h, w, kernel, t,
                                                       sigma, seed, (double*)out);
+  } else if (t <= 17) {
+    const float* L = (const float*)latent;
+    float* o = (float*)out;
+    switch (t) {
+#define CBP_BLUR_CASE(T) \
+  case T: launch_blur_rb<T>(L, n, c, h, w, kernel, sigma, seed, o, st); break;
+      CBP_BLUR_CASE(1) CBP_BLUR_CASE(2) CBP_BLUR_CASE(3) CBP_BLUR_CASE(4) CBP_BLUR_CASE(5)
+      CBP_BLUR_CASE(6) CBP_BLUR_CASE(7) CBP_BLUR_CASE(8) CBP_BLUR_CASE(9) CBP_BLUR_CASE(10)
+      CBP_BLUR_CASE(11) CBP_BLUR_CASE(12) CBP_BLUR_CASE(13) CBP_BLUR_CASE(14) CBP_BLUR_CASE(15)
+      CBP_BLUR_CASE(16) default: CBP_BLUR_CASE(17)
+#undef CBP_BLUR_CASE
+    }
   } else {
     cudaFuncSetAttribute(k_forward_blur<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_forward_blur<float><<<g, kTile * 8, sm, st>>>((const float*)latent, c, h, w, kernel, t,
