@@ -337,6 +337,15 @@ cbp_status cbp_encrypt(cbp_ctx* ctx, const void* latent, int32_t n, int32_t c, i
 cbp_status cbp_truncate_lsb(cbp_ctx* ctx, const void* in, cbp_dtype dtype, int64_t count,
                             int32_t bits, int32_t drop, void* out, void* stream);
 
+/* Verification of the solver's double-precision reciprocal and reciprocal
+ * square root (the paper has no counterpart): the Newton-Raphson iteration
+ * from a single-precision seed, two steps, used inside the eigen-solver for
+ * 1e-30 < |x| < 1e30 (plain division and sqrt outside).  For each of the n
+ * device doubles x: rcp = 1 / x, rsqrt = 1 / sqrt(x) (0 where x <= 0), as the
+ * solver computes them.  Device buffers; no context.
+ * Errors: CBP_ERR_INVALID_ARG, CBP_ERR_CUDA. */
+cbp_status cbp_check_recip(const double* x, int64_t n, double* rcp, double* rsqrt, void* stream);
+
 /* Synthetic latent frames for benchmarks (stand-in for the paper's camera
  * video, Section 6): for every channel, sum of Gaussian blobs
  * a * exp(-((x-cx)^2 + (y-cy)^2) / (2 s^2)) plus a uniform floor U[0, floor_amp]

@@ -31,7 +31,7 @@ EXPORTED = [
     "cbp_stream_submit", "cbp_stream_poll", "cbp_stream_stats", "cbp_profile", "cbp_stage_times",
     "cbp_estimate_kernels_stages", "cbp_estimate_kernels_noalloc", "cbp_cnn_param_count",
     "cbp_cnn_forward", "cbp_cnn_train_step", "cbp_learned_load", "cbp_estimate_size",
-    "cbp_truncate_lsb", "cbp_encrypt",
+    "cbp_truncate_lsb", "cbp_encrypt", "cbp_check_recip",
 ]
 STAGES = ["eval", "sample_solve", "scale_solve", "kernel_spectra", "row_fft", "col_deconv",
           "row_ifft", "h2d", "d2h", "proposal", "gate"]
@@ -124,6 +124,7 @@ def lib() -> ctypes.CDLL:
             "cbp_learned_load": ([c_void_p, ctypes.c_char_p], c_int),
             "cbp_truncate_lsb": ([c_void_p, c_void_p, c_int, c_int64, c_int32, c_int32, c_void_p,
                                   c_void_p], c_int),
+            "cbp_check_recip": ([c_void_p, c_int64, c_void_p, c_void_p, c_void_p], c_int),
             "cbp_encrypt": ([c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int,
                              POINTER(cbp_encrypt_params), c_void_p, c_void_p, c_void_p, c_void_p,
                              c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_int32), c_void_p], c_int),

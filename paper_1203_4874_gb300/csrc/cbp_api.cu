@@ -781,4 +781,11 @@ cbp_status cbp_encrypt(cbp_ctx* ctx, const void* latent, int32_t n, int32_t c, i
   }
 }
 
+cbp_status cbp_check_recip(const double* x, int64_t n, double* rcp, double* rsqrt, void* stream) {
+  if (!x || !rcp || !rsqrt || n < 0) return CBP_ERR_INVALID_ARG;
+  if (n == 0) return CBP_OK;
+  cbp::launch_check_recip(x, n, rcp, rsqrt, (cudaStream_t)stream);
+  return cudaGetLastError() == cudaSuccess ? CBP_OK : CBP_ERR_CUDA;
+}
+
 }  // extern "C"

@@ -178,6 +178,8 @@ void launch_draw_kernels(int n, int t, int kind, int frame0, uint64_t seed, cons
 void launch_coprime_round(const double* ka, const double* kb, int n, int ta, int tb, int M,
                           double tol, int max_attempts, int* active, int* attempt, int* pass,
                           int* any, cudaStream_t st);
+// the solver's reciprocal routines, elementwise (verification)
+void launch_check_recip(const double* x, int64_t n, double* r, double* q, cudaStream_t st);
 size_t sample_solve_smem(int nn);
 // kernel-size scan (cbp_solve.cu): plane sums, per-candidate ratios, the pick
 void launch_size_scan(const SizePlan& sp, const FrameDesc& b1, const FrameDesc& b2, char* ws,

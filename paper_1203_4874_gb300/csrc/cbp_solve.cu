@@ -89,9 +89,13 @@ template <typename T> struct Ops<cpx<T>> {
   static __device__ bool nz(cpx<T> x) { return x.re != (T)0 || x.im != (T)0; }
 };
 
-// Reciprocal and reciprocal square root in double precision from a float seed
-// refined by two Newton steps (y <- y (2 - x y), y <- y (3 - x y^2) / 2); valid
-// for x within the float range.  Cheap on a GPU whose double pipe is slow.
+// Reciprocal and reciprocal square root in double precision by the
+// Newton-Raphson iteration: a single-precision seed (relative error below
+// 2^-23) refined by two Newton steps for f(y) = 1/y - x, y <- y (2 - x y), and
+// for f(y) = 1/y^2 - x, y <- y (3 - x y^2) / 2; each step squares the
+// relative error, so two take it below double rounding.  Valid for x within
+// the float range (callers guard 1e-30 < |x| < 1e30).  Cheap on a GPU whose
+// double pipe is slow; cbp_check_recip exposes them for verification.
 __device__ __forceinline__ double rcp_d(double x) {
   double y = (double)(1.0f / (float)x);
   y = y * fma(-x, y, 2.0);
@@ -1164,6 +1168,15 @@ __global__ void k_coprime_pick(int n, int ns, const int* pass, int* active, int*
   }
 }
 
+// The solver's guarded reciprocal and reciprocal square root, elementwise.
+__global__ void k_check_recip(const double* x, int64_t n, double* r, double* q) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    r[i] = rcp_safe(x[i]);
+    q[i] = x[i] > 0.0 ? rsqrt_safe(x[i]) : 0.0;
+  }
+}
+
 }  // namespace
 
 size_t sample_solve_smem(int nn) { return tri_ws_bytes(nn); }
@@ -1301,6 +1314,11 @@ void launch_coprime_round(const double* ka, const double* kb, int n, int ta, int
   cudaFuncSetAttribute(k_coprime_test, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_coprime_test<<<dim3(a.ns, 2, n), kSolveThreads, sm, st>>>(a);
   k_coprime_pick<<<(n + 127) / 128, 128, 0, st>>>(n, a.ns, pass, active, attempt, max_attempts, any);
+}
+
+void launch_check_recip(const double* x, int64_t n, double* r, double* q, cudaStream_t st) {
+  const int64_t b = (n + 255) / 256;
+  k_check_recip<<<(int)std::min<int64_t>(std::max<int64_t>(b, 1), 4096), 256, 0, st>>>(x, n, r, q);
 }
 
 }  // namespace cbp
