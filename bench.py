@@ -836,9 +836,9 @@ def main():
                 "frac": None, "ms_per_launch": dom_ms, "traffic": None}
     stage_ms = {s: round(stages[s][0] / prof_steps, 4) for s in stages if stages[s][1] > 0}
     # launches per step of the profiled (unsplit) call, times the library's
-    # split of a call into up to 4 chunks of at least 8 pairs (each launches
+    # split of a call into up to 3 chunks of at least 8 pairs (each launches
     # the whole sequence)
-    chunks = max(1, min(4, n // 8))
+    chunks = max(1, min(3, n // 8))
     launches = int(sum(v[1] for v in stages.values()) / prof_steps) * chunks * args.steps
 
     result = {
