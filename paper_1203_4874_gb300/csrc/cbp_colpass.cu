@@ -41,6 +41,8 @@ struct FusedColArgs {
   cf* ihat;            // [n][C][H][Pw2p] deconvolved spectrum (column-inverse done)
   const double* kd;    // [n][t1 t1 + t2 t2] kernels
   const cf* tw_h;      // w_Ph^k, k < Ph
+  const cf* tw1;       // w_Ph^(n1 m) at [m][n1] (step 1)
+  const cf* tw2;       // w_Ph^(p k2) at [p][k2] (step 2: kernel spectra, inverse)
   const cf* tw_w;      // w_Pw^k, k < Pw
   int H1, H2, H, C, t1, t2, Pw, Pw2, Pw2p;
   float eps;
@@ -151,11 +153,11 @@ __global__ void __launch_bounds__(kFcThreads, CBP_FC_MIN_BLOCKS) k_col_deconv_fu
 #pragma unroll
     for (int m = 0; m < N2; ++m) x[m] = q[m & 3][N1 * m * S];
     reg_dft<false, N2>(x);
-    const cf* tw = a.tw_h + n1;
+    const cf* tw = a.tw1 + n1;                        // w_Ph^(n1 m) at [m][n1]
 #pragma unroll
     for (int m = 0; m < N2; ++m) {
       cf y = x[reg_pos<N2>(m)];
-      if (m) y = y * ldg_cf(tw + (n1 * (m - 1)));    // w_Ph^(n1 m), n1 m < Ph
+      if (m) y = y * ldg_cf(tw + N1 * m);
       q[m & 3][N1 * m * S] = y;
     }
   }
@@ -191,11 +193,11 @@ __global__ void __launch_bounds__(kFcThreads, CBP_FC_MIN_BLOCKS) k_col_deconv_fu
       } else {
         const cf* r = rt + (it - 2) * kFcMaxT * kFcCols + col;
         const int t = it == 2 ? a.t1 : a.t2;
-        const cf* tw = a.tw_h;
+        const cf* tw = a.tw2 + k2;                    // w_Ph^(p k2) at [p][k2]
 #pragma unroll
         for (int p = 0; p < N1; ++p) {
           x[p] = mk(0.f, 0.f);
-          if (p < t) x[p] = p ? r[p * kFcCols] * ldg_cf(tw + p * k2) : r[0];
+          if (p < t) x[p] = p ? r[p * kFcCols] * ldg_cf(tw + N2 * p) : r[0];
         }
       }
       reg_dft<false, N1>(x);
@@ -230,7 +232,7 @@ __global__ void __launch_bounds__(kFcThreads, CBP_FC_MIN_BLOCKS) k_col_deconv_fu
 #pragma unroll
     for (int n1 = 0; n1 < N1; ++n1) {
       cf z = iv[reg_pos<N1>(n1)];
-      if (n1) z = z * conj(ldg_cf(a.tw_h + n1 * k2));
+      if (n1) z = z * conj(ldg_cf(a.tw2 + N2 * n1 + k2));
       FC_AT(n1) = z;
     }
 #undef FC_AT
@@ -271,6 +273,8 @@ void run_fused(const Plan& p, char* ws, cudaStream_t st) {
   a.kd = (const double*)(ws + p.off_kd);
   a.tw_h = (const cf*)(ws + p.off_tw_h);
   a.tw_w = (const cf*)(ws + p.off_tw_w);
+  a.tw1 = (const cf*)(ws + p.off_tw2c);
+  a.tw2 = a.tw1 + N1 * N2;
   a.H1 = p.H1;
   a.H2 = p.H2;
   a.H = p.H;

@@ -321,6 +321,7 @@ __device__ __forceinline__ cd ldg_cpx(const cd* p) {
 // group, the next group in flight while the current one is folded and
 // transformed.
 struct RowPassArgs {
+  const cf* tw2;       // in-register row pass: w_N^(n1 k2) at [k2][n1]
   FrameDesc fr[2];
   void* spec[2];       // cpx<T> [n][C][H_Bk][Pw2p] (FFT)
   void* bins_r[2];     // [n C][M][H_Bk] row-fold bins, 8 bytes each (FOLD)
@@ -884,9 +885,9 @@ k_row_pass_ir(RowPassArgs a, const cf* tw_w) {
 #pragma unroll
         for (int n2 = 0; n2 < N2; ++n2) x1[n2] = z[N1 * n2];
         reg_dft<false, N2>(x1);
-        const cf* tw = tws + 2 * n1;                  // w_N^(n1 k2) = w_Pw^(2 n1 k2)
+        const cf* tw = a.tw2 + n1;                    // w_N^(n1 k2) at [k2][n1]: lanes read in a row
 #pragma unroll
-        for (int k2 = 1; k2 < N2; ++k2) x1[reg_pos<N2>(k2)] = x1[reg_pos<N2>(k2)] * tw[2 * n1 * (k2 - 1)];
+        for (int k2 = 1; k2 < N2; ++k2) x1[reg_pos<N2>(k2)] = x1[reg_pos<N2>(k2)] * ldg_cpx(tw + N1 * k2);
       }
       __syncthreads();
       if (t1) {
@@ -1269,6 +1270,7 @@ k_col_deconv(ColArgs a) {
 }
 
 struct IRowArgs {
+  const cf* tw2;     // in-register inverse: w_N^(n1 k2) at [n1][k2]
   const void* ihat;  // cpx<T> [n][C][H][Pw2]
   void* latent;      // TO [n][C][H][W]
   const uint64_t* lat_tab;  // optional per-pair latent addresses ([C][H][W] each)
@@ -1553,10 +1555,9 @@ __global__ void __launch_bounds__(kIrThreads, 2) k_row_ifft_ir(IRowArgs a, const
       }
       static_assert(N2 <= 32, "one lane per k2");
       reg_dft<true, N1>(x);
-      const cf* tn = tw_w + 2 * k2;                 // w_N^(n1 k2) = w_Pw^(2 n1 k2)
+      const cf* tn = a.tw2 + k2;                    // w_N^(n1 k2) at [n1][k2]: lanes read in a row
 #pragma unroll
-      for (int n1 = 1; n1 < N1; ++n1)
-        x[reg_pos<N1>(n1)] = x[reg_pos<N1>(n1)] * conj(ldg_cpx(tn + 2 * k2 * (n1 - 1)));
+      for (int n1 = 1; n1 < N1; ++n1) x[reg_pos<N1>(n1)] = x[reg_pos<N1>(n1)] * conj(ldg_cpx(tn + N2 * n1));
     }
     __syncthreads();
     if (ta) {
@@ -1623,7 +1624,8 @@ void run_row_pass_t(const Plan& p, const RowPassArgs& a, int gx, int gz, char* w
 // (strided batches; tables of per-pair addresses take the general kernel) and
 // a half-length transform of 972 = 36 x 27 points.
 static bool row_pass_ir_ok(const Plan& p, const FrameDesc& b1, const FrameDesc& b2, bool fft) {
-  if (!fft || p.fft_f64 || b1.f64 || !p.pw_half || p.fp_w2.n != 972 || p.M > 32) return false;
+  if (!fft || p.fft_f64 || b1.f64 || !p.pw_half || p.fp_w2.n != 972 || p.M > 32 || !p.off_tw2r)
+    return false;
   for (const FrameDesc* b : {&b1, &b2}) {
     if (b->tab || ((uintptr_t)b->data & 7) || (b->rs & 1) || (b->cs & 1) || (b->fs & 1)) return false;
   }
@@ -1634,6 +1636,7 @@ template <typename T, typename In>
 void run_row_pass(const Plan& p, const FrameDesc& b1, const FrameDesc& b2, char* ws,
                   cudaStream_t st, bool fold, bool fft) {
   RowPassArgs a;
+  a.tw2 = p.off_tw2r ? (const cf*)(ws + p.off_tw2r) : nullptr;
   a.fr[0] = b1;
   a.fr[1] = b2;
   a.spec[0] = ws + p.off_spec[0];
@@ -1751,6 +1754,7 @@ void run_row_ifft(const Plan& p, char* ws, void* latent, int out_f64, cudaStream
                   const uint64_t* lat_tab) {
   const FftPlan& plw = p.pw_half ? p.fp_w2 : p.fp_w;
   IRowArgs a;
+  a.tw2 = p.off_tw2r ? (const cf*)(ws + p.off_tw2r) + 972 : nullptr;
   a.ihat = ws + p.off_ihat;
   a.latent = latent;
   a.lat_tab = lat_tab;
@@ -1777,7 +1781,7 @@ void run_row_ifft(const Plan& p, char* ws, void* latent, int out_f64, cudaStream
   if constexpr (sizeof(T) == 4) {
     // in-register transforms: float output rows on 8-byte boundaries, 972 = 36 x 27
     if (p.pw_half && plw.n == 972 && !out_f64 && !lat_tab && (p.W % 2) == 0 &&
-        ((uintptr_t)latent & 7) == 0) {
+        ((uintptr_t)latent & 7) == 0 && p.off_tw2r) {
       const size_t smi = irow_ir_layout(p.Pw2p).total;
       cudaFuncSetAttribute(k_row_ifft_ir<36, 27>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smi);
       cudaFuncSetAttribute(k_row_ifft_ir<36, 27>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -1793,8 +1797,24 @@ void run_row_ifft(const Plan& p, char* ws, void* latent, int out_f64, cudaStream
 
 }  // namespace
 
+// Transposed twiddle tables of a two-factor split N = A B:
+// out[b A + a] = w_N^(a b) and out[A B + a B + b] = w_N^(a b), a < A, b < B.
+__global__ void k_twiddles_2f(cf* out, int A, int B) {
+  const int N = A * B;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < N; e += gridDim.x * blockDim.x) {
+    const int b = e / A, a = e % A;
+    double sn, cs;
+    sincospi(-2.0 * (double)((a * b) % N) / (double)N, &sn, &cs);
+    const cf w = mk((float)cs, (float)sn);
+    out[b * A + a] = w;
+    out[N + a * B + b] = w;
+  }
+}
+
 template <typename T>
 void run_twiddles(const Plan& p, char* ws, cudaStream_t st) {
+  if (p.off_tw2r) k_twiddles_2f<<<4, 256, 0, st>>>((cf*)(ws + p.off_tw2r), 36, 27);
+  if (p.off_tw2c) k_twiddles_2f<<<5, 256, 0, st>>>((cf*)(ws + p.off_tw2c), 32, 35);
   k_twiddles<T><<<(p.Ph + 255) / 256, 256, 0, st>>>((cpx<T>*)(ws + p.off_tw_h), p.Ph);
   k_twiddles<T><<<(p.Pw + 255) / 256, 256, 0, st>>>((cpx<T>*)(ws + p.off_tw_w), p.Pw);
   const FftPlan& plw = p.pw_half ? p.fp_w2 : p.fp_w;
