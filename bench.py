@@ -64,7 +64,9 @@ def algorithmic_bytes(stage: str, n: int) -> float | None:
     return {
         "eval": bins + samples,                    # fold bins -> samples
         "row_fft": fr + spec + bins,               # one read of the frames: folds + row FFTs
-        "col_deconv": spec + khat + ihat,
+        # the fused column pass of this grid computes the kernel spectra itself:
+        # row spectra in, deconvolved spectrum out (khat: the unfused pass's extra)
+        "col_deconv": spec + ihat,
         "row_ifft": ihat + lat,
     }.get(stage)
 
@@ -91,7 +93,7 @@ def fp32_peak_tflops(sm_mhz: float) -> float:
 
 
 STAGE_FILES = {"eval": "cbp_eval.cu", "sample_solve": "cbp_solve.cu", "scale_solve": "cbp_solve.cu",
-               "kernel_spectra": "cbp_fft.cu", "row_fft": "cbp_fft.cu", "col_deconv": "cbp_fft.cu",
+               "kernel_spectra": "cbp_fft.cu", "row_fft": "cbp_fft.cu", "col_deconv": "cbp_colpass.cu",
                "row_ifft": "cbp_fft.cu"}
 
 
