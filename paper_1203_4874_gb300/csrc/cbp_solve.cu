@@ -28,7 +28,7 @@
 #include <algorithm>
 #include "cbp_common.cuh"
 #include "cbp_internal.h"
-#ifdef CBP_PHASE_TIMING
+#if defined(CBP_PHASE_TIMING) || defined(CBP_SCHED_TRACE)
 #include <cstdio>
 #endif
 
@@ -36,6 +36,9 @@ namespace cbp {
 namespace {
 
 constexpr int kSolveThreads = 256;
+#ifndef CBP_SOLVE_WPC
+#define CBP_SOLVE_WPC 4
+#endif
 
 // Optional per-phase cycle counts (build with -DCBP_PHASE_TIMING): thread 0 of
 // a few blocks prints the clock64 deltas between the solver's phases.
@@ -357,6 +360,12 @@ struct SylvesterApply {
   cd* y;            // [C][L]
   int C, t1, t2, L;
   bool real;        // real sample (z = 1, or z = -1 for even M): real arithmetic
+  // float-float real samples: shared scratch of ys_cap float pairs (a
+  // channel's S x and both polynomials when they fit, else y and the samples
+  // are used in place), the warps' partial sums of S^H y in part[nw][n]
+  float2* ys = nullptr;
+  int ys_cap = 0;
+  float2* part = nullptr;
   __device__ void operator()(const cd* x, cd* out) const {
     if (real) {
       if constexpr (BLOCK) {
@@ -375,60 +384,142 @@ struct SylvesterApply {
   // A real sample from float-float samples (mixed path), by the whole CTA:
   // the same two products in float-float arithmetic on the single-precision
   // units (each product exact to ~1e-14, rounding terms gathered in the low
-  // part and renormalised per row and per channel), y held as float pairs.
+  // part and renormalised at most every 32 terms), y held as float pairs.
   // Against the double products the double-precision units (a few per SM)
   // took, the single-precision ones take ~10 operations per product at 64
-  // times the rate.
+  // times the rate.  One channel at a time, its two polynomials staged in
+  // shared memory; both products keep several independent sums per thread
+  // (eight outputs of S x, four slices of each output of S^H y), so the
+  // chains' latencies overlap instead of adding up.
   __device__ void run_ff_real(const cd* x, cd* out) const {
     __shared__ float2 xf[kMaxN];
+    constexpr int R = 8;                       // outputs of S x per thread and pass
     const int lane = threadIdx.x & 31, nth = blockDim.x;
     const int wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int len0 = P.len[0], len1 = P.len[1], n = t1 + t2;
-    float2* yf = reinterpret_cast<float2*>(y);
+    // one channel at a time: both polynomials (hi, lo) and that channel's S x
+    // in shared memory when they fit, else read and written in place
+    const bool stage = ys && ys_cap >= L + len0 + len1;
     team_sync<BLOCK>();
     for (int i = threadIdx.x; i < n; i += nth) {
       const float h = (float)x[i].re;
       xf[i] = make_float2(h, (float)(x[i].re - (double)h));
     }
-    team_sync<BLOCK>();
-    for (int idx = threadIdx.x; idx < C * L; idx += nth) {
-      const int ch = idx / L, i = idx - ch * L;
-      const cdf* r0 = F[0] + ch * fstride[0];
-      const cdf* r1 = F[1] + ch * fstride[1];
-      FF acc;
-      const int q0 = max(0, i - len0 + 1), q1 = min(t2 - 1, i);
-      for (int q = q0; q <= q1; ++q) {     // b1 * v
-        const cdf b = r0[i - q];
-        const float2 v = xf[t1 + q];
-        acc.mac(b.rh, b.rl, v.x, v.y);
+    const int mmax = max(len0, len1), chunk = (mmax + nw - 1) / nw;
+    const int nblk = (L + R - 1) / R;
+    FF tot[2];                                 // this lane's outputs o = lane, lane + 32
+    for (int ch = 0; ch < C; ++ch) {
+      const float2* g0 = reinterpret_cast<const float2*>(F[0] + ch * fstride[0]);   // b1
+      const float2* g1 = reinterpret_cast<const float2*>(F[1] + ch * fstride[1]);   // b2
+      const float2* pb[2] = {g0, g1};
+      int bs = 2;                              // float2 per coefficient
+      float2* yc = reinterpret_cast<float2*>(y) + ch * L;
+      team_sync<BLOCK>();                      // the last channel's reads are done
+      if (stage) {
+        float2* s0 = ys + L;
+        float2* s1 = s0 + len0;
+        // asynchronous copies: every thread's loads in flight at once
+        for (int i = threadIdx.x; i < len0 + len1; i += nth) {
+          const float2* src = i < len0 ? g0 + 2 * i : g1 + 2 * (i - len0);
+          const unsigned dst = (unsigned)__cvta_generic_to_shared(s0 + i);
+          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+        }
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+        pb[0] = s0;
+        pb[1] = s1;
+        bs = 1;
+        yc = ys;
+        team_sync<BLOCK>();
       }
-      const int p0 = max(0, i - len1 + 1), p1 = min(t1 - 1, i);
-      for (int p = p0; p <= p1; ++p) {     // - b2 * u
-        const cdf b = r1[i - p];
-        const float2 u = xf[p];
-        acc.mac(-b.rh, -b.rl, u.x, u.y);
+      // y = S x: each thread R consecutive outputs, the coefficient window slid
+      // by one per term (R independent sums)
+      for (int bi = threadIdx.x; bi < nblk; bi += nth) {
+        const int i0 = bi * R;
+        FF acc[R];
+        for (int k = 0; k < 2; ++k) {          // k = 0: b1 * v (t2 terms); k = 1: -b2 * u (t1 terms)
+          const float2* r = pb[k];
+          const int lk = k ? len1 : len0, nt = k ? t1 : t2, x0 = k ? 0 : t1;
+          const float sg = k ? -1.f : 1.f;
+          float2 w[R];                         // w[j] = b[i0 + j - q]
+#pragma unroll
+          for (int j = 0; j < R; ++j) {
+            const int m = i0 + j;
+            w[j] = (m < lk) ? r[bs * m] : make_float2(0.f, 0.f);
+          }
+          for (int q = 0; q < nt; ++q) {
+            const float2 c = xf[x0 + q];
+#pragma unroll
+            for (int j = 0; j < R; ++j) acc[j].mac(sg * w[j].x, sg * w[j].y, c.x, c.y);
+#pragma unroll
+            for (int j = R - 1; j > 0; --j) w[j] = w[j - 1];
+            const int m = i0 - q - 1;
+            w[0] = (m >= 0 && m < lk) ? r[bs * m] : make_float2(0.f, 0.f);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+          if (i0 + j < L) {
+            acc[j].add(0.f, 0.f);
+            yc[i0 + j] = make_float2(acc[j].hi, acc[j].lo);
+          }
+        }
       }
-      acc.add(0.f, 0.f);
-      yf[idx] = make_float2(acc.hi, acc.lo);
+      team_sync<BLOCK>();
+      // S^H y, this channel's terms: lane <-> output o, warp <-> a slice of
+      // the terms; four sums per lane (renormalised every 16 terms)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        if (32 * c >= n) break;
+        const int o = 32 * c + lane;
+        const bool act = o < n;
+        const int k = o < t1 ? 1 : 0;          // u rows use b2, v rows use b1
+        const int sh = o < t1 ? o : o - t1;
+        const int lk = act ? (k ? len1 : len0) : 0;
+        const float2* rk = pb[k];
+        const float2* yr = yc + sh;
+        FF a0, a1, a2, a3;
+        const int mb = wid * chunk, me = min(mb + chunk, lk);
+        int m = mb;
+        while (m + 4 <= me) {
+          const int stop = min(me, m + 64);
+          for (; m + 4 <= stop; m += 4) {
+            const float2 b0 = rk[bs * m], b1 = rk[bs * (m + 1)], b2 = rk[bs * (m + 2)],
+                         b3 = rk[bs * (m + 3)];
+            const float2 y0 = yr[m], y1 = yr[m + 1], y2 = yr[m + 2], y3 = yr[m + 3];
+            a0.mac(b0.x, b0.y, y0.x, y0.y);
+            a1.mac(b1.x, b1.y, y1.x, y1.y);
+            a2.mac(b2.x, b2.y, y2.x, y2.y);
+            a3.mac(b3.x, b3.y, y3.x, y3.y);
+          }
+          a0.add(0.f, 0.f);
+          a1.add(0.f, 0.f);
+          a2.add(0.f, 0.f);
+          a3.add(0.f, 0.f);
+        }
+        for (; m < me; ++m) {
+          const float2 b = rk[bs * m], v = yr[m];
+          a0.mac(b.x, b.y, v.x, v.y);
+        }
+        a0.add(0.f, 0.f);
+        a0.add(a1.hi, a1.lo);
+        a0.add(a2.hi, a2.lo);
+        a0.add(a3.hi, a3.lo);
+        tot[c].add(a0.hi, a0.lo);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const int o = 32 * c + lane;
+      if (o < n) part[wid * n + o] = make_float2(tot[c].hi, tot[c].lo);
     }
     team_sync<BLOCK>();
-    for (int o = wid; o < n; o += nw) {
-      const int k = o < t1 ? 1 : 0;       // u rows use b2, v rows use b1
-      const int sh = o < t1 ? o : o - t1;
-      const int lk = k ? len1 : len0;
-      FF acc;
-      for (int ch = 0; ch < C; ++ch) {
-        const cdf* rk = F[k] + ch * fstride[k];
-        const float2* yr = yf + ch * L + sh;
-        for (int m = lane; m < lk; m += 32) {
-          const cdf b = rk[m];
-          const float2 v = yr[m];
-          acc.mac(b.rh, b.rl, v.x, v.y);
-        }
-        acc.add(0.f, 0.f);
+    for (int o = threadIdx.x; o < n; o += nth) {
+      double s = 0.0;
+      for (int w = 0; w < nw; ++w) {
+        const float2 v = part[w * n + o];
+        s += (double)v.x + (double)v.y;
       }
-      const double re = warp_sum(acc.value());
-      if (lane == 0) out[o] = o < t1 ? mk(-re, 0.0) : mk(re, 0.0);
+      out[o] = o < t1 ? mk(-s, 0.0) : mk(s, 0.0);
     }
     team_sync<BLOCK>();
   }
@@ -523,6 +614,10 @@ __global__ void __launch_bounds__(kSolveThreads) k_sample_gram(SampleArgs a) {
 // on the whole CTA); the others take one complex sample per warp.
 __global__ void k_sample_solve(SampleArgs a, int nreal) {
   extern __shared__ __align__(16) char smem[];
+#ifdef CBP_SCHED_TRACE
+  unsigned long long t_start;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_start));
+#endif
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, wpc = blockDim.x >> 5;
   const int n = a.nn;
   const int nrs = (a.M % 2 == 0) ? 2 : 1, ncs = a.ns - nrs;   // real / complex samples per pass
@@ -575,6 +670,16 @@ __global__ void k_sample_solve(SampleArgs a, int nreal) {
       }
     }
     ap.real = true;
+    ap.part = reinterpret_cast<float2*>(W.part);   // free once the reduction is done
+    {
+      unsigned dsm;
+      asm("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dsm));
+      const size_t per = tri_ws_bytes(n);          // this CTA's other sample slots hold S x
+      if (dsm > per) {
+        ap.ys = reinterpret_cast<float2*>(smem + per);
+        ap.ys_cap = (int)((dsm - per) / sizeof(float2));
+      }
+    }
     res = tri_smallest<double, true>(W, G, n, far, 1, gap, ap, tk);
     if (warp != 0) return;
   } else {
@@ -604,6 +709,16 @@ __global__ void k_sample_solve(SampleArgs a, int nreal) {
            tkv[5] - tkv[4]);
 #endif
   for (int i = lane; i < n; i += 32) a.X[o * n + i] = W.x[i];
+#ifdef CBP_SCHED_TRACE
+  if (lane == 0) {
+    unsigned long long t_end;
+    unsigned smid;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t_end));
+    asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+    printf("SCHED %d %d %d %d %u %llu %llu %d\n", (int)real, f, ps, s, smid, t_start, t_end,
+           (int)res.near_degenerate);
+  }
+#endif
   if (lane == 0) {
     a.sdiag[o * 4 + 0] = res.lam_max;
     a.sdiag[o * 4 + 1] = res.lam_2;
@@ -1209,11 +1324,11 @@ void launch_sample_solve(const Plan& p, char* ws, cudaStream_t st) {
   a.G = (cd*)(ws + p.off_gall);
   dim3 grid(p.n, 2, p.ns);
   k_sample_gram<<<grid, kSolveThreads, 0, st>>>(a);
-  // warps (samples) per CTA: up to 4 within ~110 KB of shared memory
+  // warps (samples) per CTA: up to CBP_SOLVE_WPC within ~110 KB of shared memory
   const int nrs = (p.M % 2 == 0) ? 2 : 1, ncs = p.ns - nrs;
   const int nreal = p.n * 2 * nrs, ncomplex = p.n * 2 * ncs;
   const size_t per = tri_ws_bytes(p.nn);
-  const int wpc = (int)std::max<size_t>(1, std::min<size_t>(4, (110u << 10) / per));
+  const int wpc = (int)std::max<size_t>(1, std::min<size_t>(CBP_SOLVE_WPC, (110u << 10) / per));
   const size_t sm = per * wpc;
   a.nfr = p.n;
   cudaFuncSetAttribute(k_sample_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
