@@ -65,6 +65,7 @@ cbp_status Ctx::ensure_ws(size_t bytes, cudaStream_t st) {
   }
   ws = (char*)p;
   ws_size = bytes;
+  ++ws_gen;
   return CBP_OK;
 }
 
@@ -74,6 +75,15 @@ cbp_status Ctx::ensure_chunk_streams() {
     if (cudaStreamCreateWithFlags(&chunk_st[i], cudaStreamNonBlocking) != cudaSuccess)
       return CBP_ERR_CUDA;
   if (cudaStreamCreateWithFlags(&io_st, cudaStreamNonBlocking) != cudaSuccess) return CBP_ERR_CUDA;
+  int prio_lo = 0, prio_hi = 0;
+  if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) return CBP_ERR_CUDA;
+  for (int i = 0; i < kChunkStreams; ++i)
+    if (cudaStreamCreateWithPriority(&solve_st[i], cudaStreamNonBlocking, prio_hi) != cudaSuccess)
+      return CBP_ERR_CUDA;
+  for (int i = 0; i < kMaxChunks; ++i)
+    if (cudaEventCreateWithFlags(&fork_ev[i], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&join_ev[i], cudaEventDisableTiming) != cudaSuccess)
+      return CBP_ERR_CUDA;
   for (int i = 0; i <= kMaxChunks; ++i)
     if (cudaEventCreateWithFlags(&chunk_ev[i], cudaEventDisableTiming) != cudaSuccess)
       return CBP_ERR_CUDA;
@@ -108,13 +118,15 @@ cbp_status Ctx::ensure_cnn_ws(size_t bytes, cudaStream_t st) {
 cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
                     const cbp_params* prm, void* k1, void* k2, void* latent, bool deblur,
                     char* wsp, cudaStream_t st, Prof* prof, const PtrTables* tabs,
-                    const float* cnn_w, bool h2d_done, cudaEvent_t after_read) {
+                    const float* cnn_w, bool h2d_done, cudaEvent_t after_read,
+                    cudaStream_t solve, cudaEvent_t fork, cudaEvent_t join, bool tw_ready) {
   cudaEvent_t ev = nullptr;
+  cudaStream_t cur = st;   // the stream stages are timed on
   auto begin = [&](int stage) {
-    if (prof) prof->begin(stage, st, &ev);
+    if (prof) prof->begin(stage, cur, &ev);
   };
   auto end = [&](int stage, int nk) {
-    if (prof) prof->end(stage, st, ev, nk);
+    if (prof) prof->end(stage, cur, ev, nk);
   };
   const bool host_io = prm->flags & CBP_FLAG_HOST_IO;
   const bool kin = deblur && (prm->flags & CBP_FLAG_KERNELS_IN);
@@ -182,9 +194,11 @@ cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
     end(CBP_STAGE_PROPOSAL, 7);
   }
   if (fft) {
-    begin(CBP_STAGE_KERNEL_SPECTRA);   // FFT twiddle tables
-    init_twiddles(p, wsp, st);
-    end(CBP_STAGE_KERNEL_SPECTRA, 4);
+    if (!tw_ready) {
+      begin(CBP_STAGE_KERNEL_SPECTRA);   // FFT twiddle tables
+      init_twiddles(p, wsp, st);
+      end(CBP_STAGE_KERNEL_SPECTRA, 4);
+    }
     // one read of the frames: A1 folds and the A6 forward row FFTs together
     begin(CBP_STAGE_ROW_FFT);
     launch_row_pass(p, d1, d2, wsp, st, !kin, true);
@@ -199,17 +213,28 @@ cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
     end(CBP_STAGE_GATE, 3);
   }
   if (!kin) {
+    // the latency-bound estimation, on the high-priority stream when given
+    const bool forked = solve && fork && join;
+    if (forked && (cudaEventRecord(fork, st) != cudaSuccess ||
+                   cudaStreamWaitEvent(solve, fork, 0) != cudaSuccess))
+      return CBP_ERR_CUDA;
+    cudaStream_t es = forked ? solve : st;
+    cur = es;
     begin(CBP_STAGE_EVAL);
-    if (fft) launch_fold_dft(p, wsp, st);
-    else launch_eval(p, d1, d2, wsp, st);
+    if (fft) launch_fold_dft(p, wsp, es);
+    else launch_eval(p, d1, d2, wsp, es);
     end(CBP_STAGE_EVAL, fft ? 1 : 2);
     begin(CBP_STAGE_SAMPLE_SOLVE);
-    launch_sample_solve(p, wsp, st);
+    launch_sample_solve(p, wsp, es);
     end(CBP_STAGE_SAMPLE_SOLVE, 1);
     begin(CBP_STAGE_SCALE_SOLVE);
-    launch_scale_solve(p, wsp, k1d, k2d, kf64, st, tabs ? tabs->k1 : nullptr,
+    launch_scale_solve(p, wsp, k1d, k2d, kf64, es, tabs ? tabs->k1 : nullptr,
                        tabs ? tabs->k2 : nullptr);
     end(CBP_STAGE_SCALE_SOLVE, 1);
+    cur = st;
+    if (forked && (cudaEventRecord(join, solve) != cudaSuccess ||
+                   cudaStreamWaitEvent(st, join, 0) != cudaSuccess))
+      return CBP_ERR_CUDA;
   }
   if (deblur) {
     if (!p.col_fused) {
@@ -345,6 +370,7 @@ cbp_status size_scan(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
   DeviceGuard g(c->device);
   cudaStream_t st = (cudaStream_t)stream;
   std::lock_guard<std::mutex> lk(c->api_mu);
+  c->tw_key = 0;   // the workspace is laid out differently
   s = c->ensure_ws(sp.total, st);
   if (s != CBP_OK) return s;
   const cbp::FrameDesc d1 = cbp::frame_desc(b1, nullptr), d2 = cbp::frame_desc(b2, nullptr);
@@ -417,6 +443,7 @@ cbp_status encrypt_frames(cbp_ctx* ctx, const void* latent, int32_t n, int32_t c
   std::lock_guard<std::mutex> lk(cx->api_mu);
   const int Mmax = std::max(M1, cascade ? M2 : 1);
   const size_t per = (size_t)(2 * n + 4 + n * 2 * (Mmax / 2 + 1)) * sizeof(int);
+  cx->tw_key = 0;   // the workspace is laid out differently
   cbp_status s = cx->ensure_ws(2 * ((per + 255) & ~size_t(255)), st);
   if (s != CBP_OK) return s;
   char* wa = cx->ws;
@@ -464,6 +491,10 @@ cbp_status call_path(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
   cudaStream_t st = (cudaStream_t)stream;
   std::lock_guard<std::mutex> lk(c->api_mu);
   const bool host_io = (prm->flags & CBP_FLAG_HOST_IO) != 0;
+  // twiddle tables of the last chunked call, valid while this call's chunk
+  // layout and workspace are the same (they depend on nothing else)
+  const uint64_t tw_prev = c->tw_key;
+  c->tw_key = 0;
   if (host_io && (!contiguous(b1) || !contiguous(b2))) return CBP_ERR_INVALID_ARG;
   const int nch = (c->profiling || stages)
                       ? 1
@@ -511,6 +542,28 @@ cbp_status call_path(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
   }
   s = c->ensure_ws(off[nch], st);
   if (s != CBP_OK) return s;
+  // key of the tables' layout: workspace generation, chunk regions and the
+  // offsets and sizes the tables are built for (FNV-1a)
+  uint64_t key = 1469598103934665603ull;
+  auto mix = [&](uint64_t v) {
+    for (int b = 0; b < 8; ++b) {
+      key ^= (v >> (8 * b)) & 0xff;
+      key *= 1099511628211ull;
+    }
+  };
+  mix(c->ws_gen);
+  mix((uint64_t)(uintptr_t)c->ws);
+  mix((uint64_t)nch);
+  for (int i = 0; i < nch; ++i) {
+    const Plan& q = cp[i];
+    const uint64_t v[] = {off[i], (uint64_t)q.fft_f64, (uint64_t)q.Ph, (uint64_t)q.Pw,
+                          (uint64_t)q.pw_half, (uint64_t)q.fp_h.n, (uint64_t)q.fp_w.n,
+                          (uint64_t)q.fp_w2.n, q.off_tw_h, q.off_tw_w, q.off_stw_h, q.off_stw_r,
+                          q.off_tw2r, q.off_tw2c};
+    for (uint64_t x : v) mix(x);
+  }
+  if (key == 0) key = 1;
+  const bool tw_ready = key == tw_prev;
 #ifdef CBP_TIMELINE
   // Diagnostic build: per-chunk stage events against a start event, printed
   // once the call completes (the call becomes synchronous).
@@ -566,7 +619,9 @@ cbp_status call_path(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
     cbp::Prof* tlp = nullptr;
 #endif
     s = cbp::run_plan(cp[i], &f1[i], &f2[i], prm, ck1, ck2, clat, deblur, w, cs, tlp, nullptr,
-                      c->cnn_w, host_io, host_io ? nullptr : c->read_ev[i]);
+                      c->cnn_w, host_io, host_io ? nullptr : c->read_ev[i],
+                      c->solve_st[i % Ctx::kChunkStreams], c->fork_ev[i], c->join_ev[i],
+                      tw_ready);
     if (s != CBP_OK) return s;
     if (diag && cudaMemcpyAsync(diag + a, w + cp[i].off_diag, (size_t)cp[i].n * sizeof(cbp_diag),
                                 cudaMemcpyDeviceToHost, cs) != cudaSuccess)
@@ -575,6 +630,7 @@ cbp_status call_path(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
         cudaStreamWaitEvent(st, c->chunk_ev[i], 0) != cudaSuccess)
       return CBP_ERR_CUDA;
   }
+  if (deblur || cp[0].learned) c->tw_key = key;   // every chunk has its tables now
 #ifdef CBP_TIMELINE
   cudaStreamSynchronize(st);
   for (int i = 0; i < nch; ++i) {
@@ -627,11 +683,15 @@ cbp_status cbp_destroy(cbp_ctx* ctx) {
   for (int i = 0; i < Ctx::kChunkStreams; ++i)
     if (c->chunk_st[i]) cudaStreamDestroy(c->chunk_st[i]);
   if (c->io_st) cudaStreamDestroy(c->io_st);
+  for (int i = 0; i < Ctx::kChunkStreams; ++i)
+    if (c->solve_st[i]) cudaStreamDestroy(c->solve_st[i]);
   for (int i = 0; i <= Ctx::kMaxChunks; ++i)
     if (c->chunk_ev[i]) cudaEventDestroy(c->chunk_ev[i]);
   for (int i = 0; i < Ctx::kMaxChunks; ++i) {
     if (c->io_ev[i]) cudaEventDestroy(c->io_ev[i]);
     if (c->read_ev[i]) cudaEventDestroy(c->read_ev[i]);
+    if (c->fork_ev[i]) cudaEventDestroy(c->fork_ev[i]);
+    if (c->join_ev[i]) cudaEventDestroy(c->join_ev[i]);
   }
   if (c->cnn_ws) cudaFree(c->cnn_ws);
   if (c->cnn_w) cudaFree(c->cnn_w);

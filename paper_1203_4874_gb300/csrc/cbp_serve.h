@@ -32,6 +32,10 @@ struct Ctx {
   std::mutex api_mu;          // serialises the synchronous API's workspace use
   char* ws = nullptr;         // synchronous-API workspace
   size_t ws_size = 0;
+  uint64_t ws_gen = 0;        // bumped whenever `ws` is replaced
+  // FFT twiddle tables left in `ws` by the last chunked call: a key of the
+  // workspace and the chunks' table layout (0: none valid)
+  uint64_t tw_key = 0;
   ServeState* serve = nullptr;
   bool profiling = false;
   Prof prof;
@@ -43,6 +47,11 @@ struct Ctx {
   cudaEvent_t chunk_ev[kMaxChunks + 1] = {};
   cudaEvent_t io_ev[kMaxChunks] = {};
   cudaEvent_t read_ev[kMaxChunks] = {};      // chunk i has read its frames (row pass done)
+  // high-priority streams of the chunks' latency-bound solves: their blocks
+  // are placed before the pending FFT blocks of the other chunks
+  cudaStream_t solve_st[kChunkStreams] = {};
+  cudaEvent_t fork_ev[kMaxChunks] = {};
+  cudaEvent_t join_ev[kMaxChunks] = {};
   bool chunk_ready = false;
   cbp_status ensure_chunk_streams();
   std::mutex serve_mu;        // guards creation of `serve`
@@ -61,7 +70,12 @@ cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
                     char* wsp, cudaStream_t st, Prof* prof = nullptr,
                     const PtrTables* tabs = nullptr, const float* cnn_w = nullptr,
                     bool h2d_done = false,    // host I/O: inputs already copied by the caller
-                    cudaEvent_t after_read = nullptr);  // recorded once the frames are read
+                    cudaEvent_t after_read = nullptr,   // recorded once the frames are read
+                    // estimation kernels on `solve` (forked from and joined to st by
+                    // the two events) when given
+                    cudaStream_t solve = nullptr, cudaEvent_t fork = nullptr,
+                    cudaEvent_t join = nullptr,
+                    bool tw_ready = false);   // the twiddle tables are already in wsp
 void serve_shutdown(Ctx* c);
 
 }  // namespace cbp
