@@ -244,7 +244,7 @@ cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
     }
     begin(CBP_STAGE_COL_DECONV);
     launch_col_deconv(p, wsp, st);
-    end(CBP_STAGE_COL_DECONV, 1);
+    end(CBP_STAGE_COL_DECONV, p.col_fused ? 2 : 1);   // fused: the kernels' row transforms first
     begin(CBP_STAGE_ROW_IFFT);
     launch_row_ifft(p, wsp, latd, f64, st, tabs ? tabs->lat : nullptr);
     end(CBP_STAGE_ROW_IFFT, 1);

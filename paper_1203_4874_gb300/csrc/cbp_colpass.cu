@@ -6,13 +6,15 @@
 // For one strip of four spectrum columns v of one frame channel:
 //   B^_k(., v)  column DFTs of both frames' row spectra (rows >= H_k are zero),
 //   K^_k(., v)  the kernels' spectra, from their row transforms
-//               R_k,p(v) = sum_q K_k[p][q] w_Pw^(q v)  (p < t_k),
+//               R_k,p(v) = sum_q K_k[p][q] w_Pw^(q v)  (p < t_k; made once per
+//               pair by k_kernel_rows and shared by the pair's channels),
 //   I^ = (conj(K^1) B^1 + conj(K^2) B^2) / (|K^1|^2 + |K^2|^2 + eps),
 //   inverse column DFT of I^, rows < H written out.
 // The transforms are the two-factor (Cooley-Tukey) split of a length-N1 N2
 // DFT, with n = n1 + N1 n2 and u = k2 + N2 k1:
 //   X[k2 + N2 k1] = sum_n1 w_N1^(n1 k1) w_Ph^(n1 k2) sum_n2 x[n1 + N1 n2] w_N2^(n2 k2).
-// Both frames' strips are staged in shared memory (cp.async) first.
+// Both frames' strips and the strip's row transforms are staged in shared
+// memory (cp.async) first.
 // Step 1: one task per (n1, column) takes its N2 rows, transforms them in
 // registers, applies the twiddles and puts them back in place.
 // Step 2: one task per (k2, column) reads its N1 values, transforms them in
@@ -22,9 +24,21 @@
 // transform all happen there; step 3 (one task per (n1, column)) finishes the
 // inverse and writes the rows < H.  Two block barriers per channel strip; the
 // kernel spectra never touch HBM.
+#include <algorithm>
 #include "cbp_common.cuh"
 #include "cbp_dft.cuh"
 #include "cbp_internal.h"
+#ifdef CBP_PHASE_TIMING
+#include <cstdio>
+#define FC_TICK(i) \
+  do {             \
+    if (threadIdx.x == 0) tck[i] = clock64(); \
+  } while (0)
+#else
+#define FC_TICK(i) \
+  do {             \
+  } while (0)
+#endif
 
 namespace cbp {
 namespace {
@@ -39,12 +53,10 @@ constexpr int kFcMaxT = 32;         // kernel rows the row-transform table holds
 struct FusedColArgs {
   const cf* spec[2];   // [n][C][H_k][Pw2p] row spectra of B1, B2
   cf* ihat;            // [n][C][H][Pw2p] deconvolved spectrum (column-inverse done)
-  const double* kd;    // [n][t1 t1 + t2 t2] kernels
-  const cf* tw_h;      // w_Ph^k, k < Ph
+  const cf* krow;      // [n][2][max(t1, t2)][Pw2p] kernels' row transforms (k_kernel_rows)
   const cf* tw1;       // w_Ph^(n1 m) at [m][n1] (step 1)
   const cf* tw2;       // w_Ph^(p k2) at [p][k2] (step 2: kernel spectra, inverse)
-  const cf* tw_w;      // w_Pw^k, k < Pw
-  int H1, H2, H, C, t1, t2, Pw, Pw2, Pw2p;
+  int H1, H2, H, C, t1, t2, Pw2, Pw2p;
   float eps;
 };
 
@@ -98,6 +110,30 @@ __device__ __forceinline__ float fc_rcp(float x) {
   return r;
 }
 
+// The kernels' row transforms R_k,p(v) = sum_q K_k[p][q] w_Pw^(q v) of the
+// half-spectrum columns v < Pw2 (zero on the padding up to Pw2p), once per
+// pair: the column pass of each of its channels copies in the rows it needs.
+constexpr int kKrThreads = 128;
+__global__ void __launch_bounds__(kKrThreads) k_kernel_rows(const double* kd, const cf* tw_w, cf* krow,
+                                                            int t1, int t2, int Pw, int Pw2,
+                                                            int Pw2p) {
+  const int v = blockIdx.x * kKrThreads + threadIdx.x;
+  const int p = blockIdx.y, f = blockIdx.z >> 1, k = blockIdx.z & 1;
+  const int t = k ? t2 : t1, tm = max(t1, t2);
+  if (p >= t || v >= Pw2p) return;
+  const double* K = kd + (int64_t)f * (t1 * t1 + t2 * t2) + (k ? t1 * t1 : 0) + p * t;
+  cf acc = mk(0.f, 0.f);
+  if (v < Pw2) {
+    int w = 0;                                   // (q v) mod Pw, incrementally
+    for (int q = 0; q < t; ++q) {
+      acc = acc + (float)K[q] * ldg_cf(tw_w + w);
+      w += v;
+      if (w >= Pw) w -= Pw;
+    }
+  }
+  krow[(((int64_t)f * 2 + k) * tm + p) * Pw2p + v] = acc;
+}
+
 template <int N1, int N2>
 __global__ void __launch_bounds__(kFcThreads, CBP_FC_MIN_BLOCKS) k_col_deconv_fused(FusedColArgs a) {
   using L = FcSmem<N1, N2>;
@@ -111,31 +147,33 @@ __global__ void __launch_bounds__(kFcThreads, CBP_FC_MIN_BLOCKS) k_col_deconv_fu
   const int v0 = blockIdx.x * kFcCols;
   const int nv = min(kFcCols, a.Pw2 - v0);
   const int tid = threadIdx.x;
+#ifdef CBP_PHASE_TIMING
+  long long tck[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+#endif
+  FC_TICK(0);
 
   // both frames' strips in flight while the kernels' row transforms are made
   fc_stage<N1, N2>(buf0, a.spec[0] + ((int64_t)fc * a.H1) * a.Pw2p + v0, a.H1, a.Pw2p, nv);
   fc_stage<N1, N2>(buf0 + B1, a.spec[1] + ((int64_t)fc * a.H2) * a.Pw2p + v0, a.H2, a.Pw2p, nv);
   asm volatile("cp.async.commit_group;\n" ::: "memory");
 
-  // kernel row transforms R_k,p(v) for the strip's columns (zero past Pw2)
-  const double* K1 = a.kd + (int64_t)f * (a.t1 * a.t1 + a.t2 * a.t2);
-  for (int e = tid; e < 2 * kFcMaxT * kFcCols; e += kFcThreads) {
-    const int k = e / (kFcMaxT * kFcCols), p = (e / kFcCols) % kFcMaxT, col = e % kFcCols;
-    const int t = k ? a.t2 : a.t1, v = v0 + col;
-    const double* K = K1 + (k ? a.t1 * a.t1 : 0) + p * t;
-    cf acc = mk(0.f, 0.f);
-    if (p < t && v < a.Pw2) {
-      int w = 0;                                   // (q v) mod Pw, incrementally
-      for (int q = 0; q < t; ++q) {
-        acc = acc + (float)K[q] * ldg_cf(a.tw_w + w);
-        w += v;
-        if (w >= a.Pw) w -= a.Pw;
-      }
+  // the kernels' row transforms R_k,p(v) of the strip's columns (rows p < t_k;
+  // made once per pair by k_kernel_rows), copied in with the strips
+  {
+    const int tm = max(a.t1, a.t2);
+    const cf* KR = a.krow + (int64_t)f * 2 * tm * a.Pw2p + v0;
+    for (int e = tid; e < 2 * tm * 2; e += kFcThreads) {
+      const int half = e & 1, kp = e >> 1, k = kp / tm, p = kp - k * tm;
+      if (p < (k ? a.t2 : a.t1))
+        fc_cp_async16(rt + (k * kFcMaxT + p) * kFcCols + 2 * half,
+                      KR + ((int64_t)k * tm + p) * a.Pw2p + 2 * half, 16);
     }
-    rt[e] = acc;
   }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  FC_TICK(1);
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
+  FC_TICK(2);
 
   // Slot (j, m) = logical row j + N1 m sits at physical row (j ^ (m & 3)) + N1 m
   // (fc_phys): with four base pointers per thread every access below is a
@@ -162,6 +200,7 @@ __global__ void __launch_bounds__(kFcThreads, CBP_FC_MIN_BLOCKS) k_col_deconv_fu
     }
   }
   __syncthreads();
+  FC_TICK(3);
 
   // ---- step 2: N1-point DFTs across, the formula, the inverse N1-point DFTs
   if (tid < N2 * kFcCols) {
@@ -239,6 +278,7 @@ __global__ void __launch_bounds__(kFcThreads, CBP_FC_MIN_BLOCKS) k_col_deconv_fu
 #undef FC_AT1
   }
   __syncthreads();
+  FC_TICK(4);
 
   // ---- step 3: inverse N2-point DFTs down the columns, rows < H out
   if (tid < N1 * kFcCols) {
@@ -259,6 +299,14 @@ __global__ void __launch_bounds__(kFcThreads, CBP_FC_MIN_BLOCKS) k_col_deconv_fu
       }
     }
   }
+#ifdef CBP_PHASE_TIMING
+  __syncthreads();
+  FC_TICK(5);
+  if (tid == 0 && blockIdx.x % 61 == 0 && blockIdx.y % 23 == 0)
+    printf("colpass blk=%d,%d | rt %lld wait %lld step1 %lld step2 %lld step3 %lld\n", blockIdx.x,
+           blockIdx.y, tck[1] - tck[0], tck[2] - tck[1], tck[3] - tck[2], tck[4] - tck[3],
+           tck[5] - tck[4]);
+#endif
   static_assert(N1 <= kFcMaxT, "kernel rows beyond the row-transform table");
   static_assert(N1 % 4 == 0, "the swizzle permutes rows within groups of four");
   static_assert(Ph == N1 * N2, "");
@@ -270,9 +318,7 @@ void run_fused(const Plan& p, char* ws, cudaStream_t st) {
   a.spec[0] = (const cf*)(ws + p.off_spec[0]);
   a.spec[1] = (const cf*)(ws + p.off_spec[1]);
   a.ihat = (cf*)(ws + p.off_ihat);
-  a.kd = (const double*)(ws + p.off_kd);
-  a.tw_h = (const cf*)(ws + p.off_tw_h);
-  a.tw_w = (const cf*)(ws + p.off_tw_w);
+  a.krow = (const cf*)(ws + p.off_krow);
   a.tw1 = (const cf*)(ws + p.off_tw2c);
   a.tw2 = a.tw1 + N1 * N2;
   a.H1 = p.H1;
@@ -281,10 +327,13 @@ void run_fused(const Plan& p, char* ws, cudaStream_t st) {
   a.C = p.C;
   a.t1 = p.t1;
   a.t2 = p.t2;
-  a.Pw = p.Pw;
   a.Pw2 = p.Pw2;
   a.Pw2p = p.Pw2p;
   a.eps = (float)p.eps;
+  const int tm = std::max(p.t1, p.t2);
+  k_kernel_rows<<<dim3((p.Pw2p + kKrThreads - 1) / kKrThreads, tm, p.n * 2), kKrThreads, 0, st>>>(
+      (const double*)(ws + p.off_kd), (const cf*)(ws + p.off_tw_w), (cf*)(ws + p.off_krow), p.t1,
+      p.t2, p.Pw, p.Pw2, p.Pw2p);
   const size_t sm = FcSmem<N1, N2>::kBytes;
   cudaFuncSetAttribute(k_col_deconv_fused<N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   cudaFuncSetAttribute(k_col_deconv_fused<N1, N2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
@@ -297,7 +346,7 @@ void run_fused(const Plan& p, char* ws, cudaStream_t st) {
 bool col_pass_fused(const Plan& p) {
   if (p.fft_f64 || p.single_kernel) return false;
   if (p.t1 > kFcMaxT || p.t2 > kFcMaxT) return false;
-  return p.Ph == 1120 && p.t1 <= 32 && p.t2 <= 32;
+  return p.Ph == 1120 && p.Pw2p % 4 == 0;
 }
 
 void launch_col_deconv_fused(const Plan& p, char* ws, cudaStream_t st) {

@@ -89,6 +89,8 @@ struct Plan {
   size_t off_stw_h, off_stw_r;     // cpx<T_fft> stage twiddles of the column and row plans
   size_t off_tw2r, off_tw2c;       // float twiddles w_N^(a b) of the in-register passes, laid out
                                    // so a warp's lanes read consecutive entries (0: not used)
+  size_t off_krow;                 // fused column pass: the kernels' row transforms R_k,p(v), float
+                                   // complex [n][2][max(t1, t2)][Pw2p] (0: not used)
   size_t off_khat;                 // cpx<T_fft> [n][2][Ph][Pw2p] (learned gate, unfused column pass)
   size_t off_spec[2];              // cpx<T_fft> [n][C][H_Bk][Pw2p]
   size_t off_ihat;                 // cpx<T_fft> [n][C][H][Pw2p]

@@ -200,6 +200,7 @@ cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_param
   // [k2][n1] and [n1][k2] of w_972^(n1 k2) (row passes); [m][n1] and [p][k2] of w_1120 (column pass)
   p.off_tw2r = (!p.fft_f64 && p.pw_half && p.fp_w2.n == 972) ? take(2 * 972 * 8) : 0;
   p.off_tw2c = p.col_fused ? take(2 * 1120 * 8) : 0;
+  p.off_krow = p.col_fused ? take(n * 2 * (size_t)std::max(t1, t2) * p.Pw2p * 8) : 0;
   if (!p.col_fused || p.learned) p.off_khat = take(n * 2 * (size_t)p.Ph * p.Pw2p * ce);
   p.off_spec[0] = take(n * C * (size_t)p.H1 * p.Pw2p * ce);
   p.off_spec[1] = take(n * C * (size_t)p.H2 * p.Pw2p * ce);
