@@ -208,8 +208,14 @@ cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
   if (p.learned) {
     // consistency residual of the proposal; accepted pairs skip the solves
     begin(CBP_STAGE_GATE);
-    launch_kernel_spectra(p, wsp, st);
-    launch_residual_gate(p, wsp, st);
+    if (p.col_fused) {
+      // the proposal's deconvolution with the residual sums (its spectrum stands
+      // for accepted pairs; the column pass below redoes the rejected ones)
+      launch_col_gate_fused(p, wsp, st);
+    } else {
+      launch_kernel_spectra(p, wsp, st);
+      launch_residual_gate(p, wsp, st);
+    }
     end(CBP_STAGE_GATE, 3);
   }
   if (!kin) {

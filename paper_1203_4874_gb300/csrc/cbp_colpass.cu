@@ -56,7 +56,9 @@ struct FusedColArgs {
   const cf* krow;      // [n][2][max(t1, t2)][Pw2p] kernels' row transforms (k_kernel_rows)
   const cf* tw1;       // w_Ph^(n1 m) at [m][n1] (step 1)
   const cf* tw2;       // w_Ph^(p k2) at [p][k2] (step 2: kernel spectra, inverse)
-  int H1, H2, H, C, t1, t2, Pw2, Pw2p;
+  const int* accepted; // learned path: pairs whose proposal passed the gate (or null)
+  double* rpart;       // RESID: [n C][strips][2] residual sums
+  int H1, H2, H, C, t1, t2, Pw, Pw2, Pw2p;
   float eps;
 };
 
@@ -134,8 +136,43 @@ __global__ void __launch_bounds__(kKrThreads) k_kernel_rows(const double* kd, co
   krow[(((int64_t)f * 2 + k) * tm + p) * Pw2p + v] = acc;
 }
 
+// Inputs of an N1-point DFT giving a kernel's column spectrum K^(k2 + N2 k1):
+// R_p w_Ph^(p k2) for its t nonzero rows p (r: the strip's row transforms of
+// this column, stride kFcCols; tw: w_Ph^(p k2) at [p][k2], already offset by k2).
 template <int N1, int N2>
-__global__ void __launch_bounds__(kFcThreads, CBP_FC_MIN_BLOCKS) k_col_deconv_fused(FusedColArgs a) {
+__device__ __forceinline__ void fc_kspec_in(cf* v, const cf* r, int t, const cf* tw) {
+#pragma unroll
+  for (int p = 0; p < N1; ++p) {
+    v[p] = mk(0.f, 0.f);
+    if (p < t) v[p] = p ? r[p * kFcCols] * ldg_cf(tw + N2 * p) : r[0];
+  }
+}
+
+// The formula's arithmetic spelled out with explicit rounding (no contraction
+// left to the compiler), so that both variants of the pass round alike.
+__device__ __forceinline__ cf fc_cmulc(cf k, cf b) {   // conj(k) b
+  return mk(__fmaf_rn(k.re, b.re, __fmul_rn(k.im, b.im)), __fmaf_rn(k.re, b.im, -__fmul_rn(k.im, b.re)));
+}
+__device__ __forceinline__ float fc_abs2(cf k) { return __fmaf_rn(k.re, k.re, __fmul_rn(k.im, k.im)); }
+// I^ = (t1 + conj(K2) B2) / (d1 + |K2|^2 + eps), t1 = conj(K1) B1, d1 = |K1|^2
+__device__ __forceinline__ cf fc_formula(cf t1, float d1, cf k2, cf b2, float eps) {
+  const cf t2 = fc_cmulc(k2, b2);
+  const cf num = mk(__fadd_rn(t1.re, t2.re), __fadd_rn(t1.im, t2.im));
+  const float den = __fadd_rn(__fadd_rn(d1, fc_abs2(k2)), eps);
+  const float r = den != 0.f ? fc_rcp(den) : 0.f;
+  return mk(__fmul_rn(r, num.re), __fmul_rn(r, num.im));
+}
+
+// RESID (learned path): the same pass with the proposal's kernels, and besides
+// the deconvolved spectrum the strip's part of the consistency residual,
+//   sum |K2^ B1^ - K1^ B2^|^2 and sum |B1^|^2 over the strip's (u, v),
+// each half-spectrum column counted twice except v = 0 and v = Pw/2 (its own
+// mirror): by Parseval their ratio is rho^2 of the circular convolutions.  Both
+// kernels' spectra are held in registers at once (two blocks per SM).
+// Without RESID, pairs whose proposal was accepted are skipped.
+template <int N1, int N2, bool RESID>
+__global__ void __launch_bounds__(kFcThreads, RESID ? 2 : CBP_FC_MIN_BLOCKS)
+k_col_deconv_fused(FusedColArgs a) {
   using L = FcSmem<N1, N2>;
   constexpr int Ph = N1 * N2;
   constexpr int S = kFcCols;                // slot stride (cf) in a buffer
@@ -144,6 +181,7 @@ __global__ void __launch_bounds__(kFcThreads, CBP_FC_MIN_BLOCKS) k_col_deconv_fu
   cf* buf0 = (cf*)smem;
   cf* rt = buf0 + 2 * L::kBuf;              // [2][kFcMaxT][kFcCols] kernel row transforms
   const int fc = blockIdx.y, f = fc / a.C;
+  if (!RESID && a.accepted && a.accepted[f]) return;   // the proposal's pass stands
   const int v0 = blockIdx.x * kFcCols;
   const int nv = min(kFcCols, a.Pw2 - v0);
   const int tid = threadIdx.x;
@@ -203,6 +241,7 @@ __global__ void __launch_bounds__(kFcThreads, CBP_FC_MIN_BLOCKS) k_col_deconv_fu
   FC_TICK(3);
 
   // ---- step 2: N1-point DFTs across, the formula, the inverse N1-point DFTs
+  float rn = 0.f, rd = 0.f;   // RESID: this task's residual sums
   if (tid < N2 * kFcCols) {
     const int k2 = tid / kFcCols, col = tid % kFcCols;
     cf* q[4];
@@ -216,13 +255,14 @@ __global__ void __launch_bounds__(kFcThreads, CBP_FC_MIN_BLOCKS) k_col_deconv_fu
 #define FC_AT1(j) q[(j) & 3][((j) & ~3) * S + B1]
     float d1[N1];
     cf x[N1];          // the working transform; ends up holding I^ at reg_pos order
+    cf y[N1];          // RESID: K^1 while K^2 is made
     const float eps = a.eps;
     // four forward N1-point DFTs through one code path: frame 2's and frame
     // 1's column spectra (back into their slots), then the two kernels'
     // spectra K^(k2 + N2 k1) = DFT_N1 over p of R_p w_Ph^(p k2), each consumed
     // by its part of the formula at once
 #pragma unroll 1
-    for (int it = 0; it < 4; ++it) {
+    for (int it = 0; it < (RESID ? 2 : 4); ++it) {
       if (it == 0) {
 #pragma unroll
         for (int j = 0; j < N1; ++j) x[j] = FC_AT1(j);
@@ -230,14 +270,8 @@ __global__ void __launch_bounds__(kFcThreads, CBP_FC_MIN_BLOCKS) k_col_deconv_fu
 #pragma unroll
         for (int j = 0; j < N1; ++j) x[j] = FC_AT(j);
       } else {
-        const cf* r = rt + (it - 2) * kFcMaxT * kFcCols + col;
-        const int t = it == 2 ? a.t1 : a.t2;
-        const cf* tw = a.tw2 + k2;                    // w_Ph^(p k2) at [p][k2]
-#pragma unroll
-        for (int p = 0; p < N1; ++p) {
-          x[p] = mk(0.f, 0.f);
-          if (p < t) x[p] = p ? r[p * kFcCols] * ldg_cf(tw + N2 * p) : r[0];
-        }
+        fc_kspec_in<N1, N2>(x, rt + (it - 2) * kFcMaxT * kFcCols + col, it == 2 ? a.t1 : a.t2,
+                            a.tw2 + k2);
       }
       reg_dft<false, N1>(x);
       if (it == 0) {
@@ -250,17 +284,32 @@ __global__ void __launch_bounds__(kFcThreads, CBP_FC_MIN_BLOCKS) k_col_deconv_fu
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) {
           const cf k = x[reg_pos<N1>(k1)];
-          FC_AT(k1) = cmulc(k, FC_AT(k1));          // conj(K^1) B^1
-          d1[k1] = abs2(k);
+          FC_AT(k1) = fc_cmulc(k, FC_AT(k1));       // conj(K^1) B^1
+          d1[k1] = fc_abs2(k);
         }
       } else {
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) {
           const cf k = x[reg_pos<N1>(k1)];
-          const cf num = FC_AT(k1) + cmulc(k, FC_AT1(k1));
-          const float den = d1[k1] + abs2(k) + eps;
-          x[reg_pos<N1>(k1)] = (den != 0.f ? fc_rcp(den) : 0.f) * num;   // I^(k2 + N2 k1)
+          x[reg_pos<N1>(k1)] = fc_formula(FC_AT(k1), d1[k1], k, FC_AT1(k1), eps);   // I^(k2 + N2 k1)
         }
+      }
+    }
+    if constexpr (RESID) {
+      // both kernels' spectra at once (K^1 in y, K^2 in x), the residual sums
+      // and the formula
+      fc_kspec_in<N1, N2>(y, rt + col, a.t1, a.tw2 + k2);
+      reg_dft<false, N1>(y);
+      fc_kspec_in<N1, N2>(x, rt + kFcMaxT * kFcCols + col, a.t2, a.tw2 + k2);
+      reg_dft<false, N1>(x);
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) {
+        const cf kk1 = y[reg_pos<N1>(k1)], kk2 = x[reg_pos<N1>(k1)];
+        const cf b1 = FC_AT(k1), b2 = FC_AT1(k1);
+        const cf r = kk2 * b1 - kk1 * b2;
+        rn += abs2(r);
+        rd += abs2(b1);
+        x[reg_pos<N1>(k1)] = fc_formula(fc_cmulc(kk1, b1), fc_abs2(kk1), kk2, b2, eps);
       }
     }
     // inverse over k1, twiddled by w_Ph^(-n1 k2), into this task's slots
@@ -276,6 +325,27 @@ __global__ void __launch_bounds__(kFcThreads, CBP_FC_MIN_BLOCKS) k_col_deconv_fu
     }
 #undef FC_AT
 #undef FC_AT1
+  }
+  if constexpr (RESID) {
+    __shared__ double red[2][kFcThreads / 32];
+    const int v = v0 + tid % kFcCols;
+    const double wv = (v == 0 || 2 * v == a.Pw) ? 1.0 : 2.0;
+    const double sn = warp_sum(wv * (double)rn), sd = warp_sum(wv * (double)rd);
+    if ((tid & 31) == 0) {
+      red[0][tid >> 5] = sn;
+      red[1][tid >> 5] = sd;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double tn = 0.0, td = 0.0;
+      for (int w = 0; w < kFcThreads / 32; ++w) {
+        tn += red[0][w];
+        td += red[1][w];
+      }
+      double* o = a.rpart + ((int64_t)fc * gridDim.x + blockIdx.x) * 2;
+      o[0] = tn;
+      o[1] = td;
+    }
   }
   __syncthreads();
   FC_TICK(4);
@@ -312,7 +382,7 @@ __global__ void __launch_bounds__(kFcThreads, CBP_FC_MIN_BLOCKS) k_col_deconv_fu
   static_assert(Ph == N1 * N2, "");
 }
 
-template <int N1, int N2>
+template <int N1, int N2, bool RESID>
 void run_fused(const Plan& p, char* ws, cudaStream_t st) {
   FusedColArgs a;
   a.spec[0] = (const cf*)(ws + p.off_spec[0]);
@@ -321,12 +391,15 @@ void run_fused(const Plan& p, char* ws, cudaStream_t st) {
   a.krow = (const cf*)(ws + p.off_krow);
   a.tw1 = (const cf*)(ws + p.off_tw2c);
   a.tw2 = a.tw1 + N1 * N2;
+  a.accepted = (!RESID && p.learned) ? (const int*)(ws + p.off_acc) : nullptr;
+  a.rpart = RESID ? (double*)(ws + p.off_rpart) : nullptr;
   a.H1 = p.H1;
   a.H2 = p.H2;
   a.H = p.H;
   a.C = p.C;
   a.t1 = p.t1;
   a.t2 = p.t2;
+  a.Pw = p.Pw;
   a.Pw2 = p.Pw2;
   a.Pw2p = p.Pw2p;
   a.eps = (float)p.eps;
@@ -335,10 +408,10 @@ void run_fused(const Plan& p, char* ws, cudaStream_t st) {
       (const double*)(ws + p.off_kd), (const cf*)(ws + p.off_tw_w), (cf*)(ws + p.off_krow), p.t1,
       p.t2, p.Pw, p.Pw2, p.Pw2p);
   const size_t sm = FcSmem<N1, N2>::kBytes;
-  cudaFuncSetAttribute(k_col_deconv_fused<N1, N2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  cudaFuncSetAttribute(k_col_deconv_fused<N1, N2>, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-  dim3 g((p.Pw2 + kFcCols - 1) / kFcCols, p.n * p.C);
-  k_col_deconv_fused<N1, N2><<<g, kFcThreads, sm, st>>>(a);
+  auto kern = k_col_deconv_fused<N1, N2, RESID>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+  kern<<<dim3(fused_strips(p), p.n * p.C), kFcThreads, sm, st>>>(a);
 }
 
 }  // namespace
@@ -349,8 +422,15 @@ bool col_pass_fused(const Plan& p) {
   return p.Ph == 1120 && p.Pw2p % 4 == 0;
 }
 
+int fused_strips(const Plan& p) { return (p.Pw2 + kFcCols - 1) / kFcCols; }
+
 void launch_col_deconv_fused(const Plan& p, char* ws, cudaStream_t st) {
-  run_fused<32, 35>(p, ws, st);
+  run_fused<32, 35, false>(p, ws, st);
+}
+
+void launch_col_gate_fused(const Plan& p, char* ws, cudaStream_t st) {
+  run_fused<32, 35, true>(p, ws, st);
+  launch_gate(p, ws, st, fused_strips(p));
 }
 
 }  // namespace cbp

@@ -37,6 +37,8 @@ struct FoldDftArgs {
   int len[4];
   int M, ns;
   int pz_all;              // float-float kernel: double copies of every sample, not only the real ones
+  const int* accepted;     // learned path: pairs whose proposal passed the gate (skipped), or null
+  int C;
 };
 
 // 8-byte bin m of a position: (hi, lo) floats (F32) or a double.
@@ -60,7 +62,7 @@ __global__ void __launch_bounds__(kDftThreads) k_fold_dft(FoldDftArgs a) {
   __syncthreads();
   const int z = blockIdx.z, fc = blockIdx.y, M = a.M, len = a.len[z];
   const int pos = blockIdx.x * blockDim.x + threadIdx.x;
-  if (pos >= len) return;
+  if (pos >= len || (a.accepted && a.accepted[fc / a.C])) return;
   const int64_t b = (int64_t)fc * M * len + pos;
   const void* bb = a.bins[z];
   const int h = (M - 1) / 2;
@@ -133,7 +135,7 @@ __global__ void __launch_bounds__(kDftThreads) k_fold_dft_ff(FoldDftArgs a) {
   __syncthreads();
   const int z = blockIdx.z, fc = blockIdx.y, M = a.M, len = a.len[z];
   const int pos = blockIdx.x * blockDim.x + threadIdx.x;
-  if (pos >= len) return;
+  if (pos >= len || (a.accepted && a.accepted[fc / a.C])) return;
   const float2* bb = (const float2*)a.bins[z] + (int64_t)fc * M * len + pos;
   auto bin = [&](int m) {
     const float2 v = bb[(int64_t)m * len];
@@ -192,6 +194,8 @@ void launch_fold_dft(const Plan& p, char* ws, cudaStream_t st) {
   a.M = p.M;
   a.ns = p.ns;
   a.pz_all = p.pz_all;
+  a.accepted = p.learned ? (const int*)(ws + p.off_acc) : nullptr;
+  a.C = p.C;
   dim3 g((maxlen + kDftThreads - 1) / kDftThreads, p.n * p.C, 4);
   // bins of float32 frames are (hi, lo) pairs; the mixed path of float32
   // frames takes the float-float kernel

@@ -1866,12 +1866,16 @@ void launch_row_ifft(const Plan& p, char* ws, void* latent, int out_f64, cudaStr
   else run_row_ifft<float>(p, ws, latent, out_f64, st, lat_tab);
 }
 
+void launch_gate(const Plan& p, char* ws, cudaStream_t st, int strips) {
+  k_gate<<<p.n, kGateThreads, 0, st>>>((const double*)(ws + p.off_rpart), p.n, p.C, strips,
+                                            p.accept_rho, (int*)(ws + p.off_acc),
+                                            (double*)(ws + p.off_rho));
+}
+
 void launch_residual_gate(const Plan& p, char* ws, cudaStream_t st) {
   if (p.fft_f64) run_col_deconv<double, true>(p, ws, st);
   else run_col_deconv<float, true>(p, ws, st);
-  k_gate<<<p.n, kGateThreads, 0, st>>>((const double*)(ws + p.off_rpart), p.n, p.C, p.col_strips,
-                                            p.accept_rho, (int*)(ws + p.off_acc),
-                                            (double*)(ws + p.off_rho));
+  launch_gate(p, ws, st, p.col_strips);
 }
 
 }  // namespace cbp

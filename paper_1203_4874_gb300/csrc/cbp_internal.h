@@ -152,6 +152,12 @@ void launch_col_deconv(const Plan& p, char* ws, cudaStream_t st);
 // the fused column pass (cbp_colpass.cu): kernel spectra computed in the pass
 bool col_pass_fused(const Plan& p);
 void launch_col_deconv_fused(const Plan& p, char* ws, cudaStream_t st);
+int fused_strips(const Plan& p);   // column strips of the fused column pass
+// learned path, fused column pass: the proposal's deconvolution with the
+// residual sums, then the per-pair decision
+void launch_col_gate_fused(const Plan& p, char* ws, cudaStream_t st);
+// per-pair consistency residual from `strips` partial sums per channel, and the decision
+void launch_gate(const Plan& p, char* ws, cudaStream_t st, int strips);
 void launch_row_ifft(const Plan& p, char* ws, void* latent, int out_f64, cudaStream_t st,
                      const uint64_t* lat_tab = nullptr);
 // learned path: consistency residual of the kernels in kd (column pass in

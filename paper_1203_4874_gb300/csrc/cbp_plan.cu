@@ -201,7 +201,7 @@ cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_param
   p.off_tw2r = (!p.fft_f64 && p.pw_half && p.fp_w2.n == 972) ? take(2 * 972 * 8) : 0;
   p.off_tw2c = p.col_fused ? take(2 * 1120 * 8) : 0;
   p.off_krow = p.col_fused ? take(n * 2 * (size_t)std::max(t1, t2) * p.Pw2p * 8) : 0;
-  if (!p.col_fused || p.learned) p.off_khat = take(n * 2 * (size_t)p.Ph * p.Pw2p * ce);
+  if (!p.col_fused) p.off_khat = take(n * 2 * (size_t)p.Ph * p.Pw2p * ce);
   p.off_spec[0] = take(n * C * (size_t)p.H1 * p.Pw2p * ce);
   p.off_spec[1] = take(n * C * (size_t)p.H2 * p.Pw2p * ce);
   p.off_ihat = take(n * C * (size_t)p.H * p.Pw2p * ce);
@@ -210,7 +210,8 @@ cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_param
     p.off_cnn = take(cnn_workspace(p.n, false));
     p.off_acc = take(n * 4);
     p.off_rho = take(n * 8);
-    p.off_rpart = take(n * C * (size_t)p.col_strips * 2 * 8);
+    const int strips = p.col_fused ? fused_strips(p) : p.col_strips;
+    p.off_rpart = take(n * C * (size_t)strips * 2 * 8);
   }
   if (prm->flags & CBP_FLAG_HOST_IO) {
     const size_t es = frame_f64 ? 8 : 4;
