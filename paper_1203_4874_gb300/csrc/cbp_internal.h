@@ -195,6 +195,6 @@ size_t sample_solve_smem(int nn);
 void launch_size_scan(const SizePlan& sp, const FrameDesc& b1, const FrameDesc& b2, char* ws,
                       cudaStream_t st);
 size_t size_scan_smem();
-size_t scale_solve_smem(int M);
+size_t scale_solve_smem(int M, int nn);
 
 }  // namespace cbp

@@ -156,7 +156,7 @@ cbp_status make_plan(const cbp_frames* b1, const cbp_frames* b2, const cbp_param
   // row pass at one row per group; exact magic division needs rows * N < 2^16
   if (row_pass_min_smem(p) > smem_max || nrow > 16384) return CBP_ERR_UNSUPPORTED;
   if (3 * cw * ce * p.Ph > smem_max || cw * p.Ph > 65536) return CBP_ERR_UNSUPPORTED;
-  if (sample_solve_smem(p.nn) > smem_max || scale_solve_smem(p.M) > smem_max)
+  if (sample_solve_smem(p.nn) > smem_max || scale_solve_smem(p.M, p.nn) > smem_max)
     return CBP_ERR_UNSUPPORTED;
 
   // workspace layout

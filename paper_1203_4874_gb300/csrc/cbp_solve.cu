@@ -27,6 +27,7 @@
 // normalise to unit kernel sum, inverse M x M DFT (Section 5).
 #include <algorithm>
 #include "cbp_common.cuh"
+#include "cbp_ff.cuh"
 #include "cbp_internal.h"
 #if defined(CBP_PHASE_TIMING) || defined(CBP_SCHED_TRACE)
 #include <cstdio>
@@ -745,6 +746,7 @@ struct ScaleArgs {
   const double* rho;    // learned path: consistency residual of the proposal
   int M, ns, t1, t2, nn, mixed, Ph, Pw;
   int mode;             // kScaleLS, kScaleK1, kScaleSupport
+  int ffx;              // mixed path with room for the float-float stage (scale_ff_offset)
 };
 
 // Scale fixes: both kernels' two-order least squares; kernel 1's equations
@@ -832,6 +834,13 @@ __host__ __device__ inline size_t scale_tri_offset(int M) {
   return (sizeof(cd) * 4 * M * M + 32 * sizeof(double) + sizeof(cd) * 3 * M * M + 127) &
          ~size_t(127);
 }
+// then the mixed path's float-float cofactors [2][M][nn] and lifted spectra [4][M][M]
+__host__ __device__ inline size_t scale_ff_offset(int M, int nn) {
+  return (scale_tri_offset(M) + tri_ws_bytes(2 * M) + 127) & ~size_t(127);
+}
+__host__ __device__ inline size_t scale_ff_bytes(int M, int nn) {
+  return sizeof(cfx) * (2 * (size_t)M * nn + 4 * (size_t)M * M);
+}
 
 __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
   extern __shared__ __align__(16) char smem[];
@@ -882,15 +891,42 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
   cd* X = (cd*)p;                 // [2][M][M] kernel spectra, then full inverse DFTs
   cd* T = X + 2 * MM;             // [M][M] temporary
   __shared__ cd wt[kMaxM];
+  __shared__ cfx wtx[kMaxM];
   for (int k = threadIdx.x; k < M; k += blockDim.x) {
     double sn, cs;
     sincospi(-2.0 * (double)k / (double)M, &sn, &cs);
     wt[k] = mk(cs, sn);
+    wtx[k] = cfx_of(wt[k]);
   }
   __syncthreads();
   cd* ab = a.ab + (int64_t)f * 4 * MM;
+  // Mixed path (two-order and k1-only fixes): the lift, the normal matrix and
+  // the inverse DFT in float-float arithmetic (~1e-14) on the single-precision
+  // units, the cofactors and lifted spectra staged in shared memory.
+  const bool ffx = a.ffx && mode != kScaleSupport;
+  cfx* cof = (cfx*)(smem + scale_ff_offset(M, a.nn));   // [2][M][nn] cofactors, conjugates expanded
+  cfx* abx = cof + 2 * M * a.nn;                         // [4][M][M] A_1, A_2, B_1, B_2
+  if (ffx) {
+    for (int idx = threadIdx.x; idx < 2 * M * a.nn; idx += blockDim.x) {
+      const int ps = idx / (M * a.nn), sm = (idx / a.nn) % M, e = idx % a.nn;
+      cof[idx] = cfx_of(cofactor(a, f, ps, sm, e));
+    }
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < 4 * MM; idx += blockDim.x) {
+      const int which = idx / MM, i = (idx % MM) / M, j = idx % M;
+      const int kk = which & 1, isB = which >> 1;
+      const int t = kk ? t2 : t1, lo = kk ? t1 : 0;
+      const cfx* u = cof + ((isB ? M : 0) + (isB ? i : j)) * a.nn + lo;
+      const int mult = isB ? j : i;
+      cfx_acc acc;
+      for (int q = 0; q < t; ++q) acc.mac(u[q], wtx[(mult * q) % M]);
+      const cfx v = acc.value();
+      abx[idx] = v;
+      ab[idx] = cfx_val(v);
+    }
+  }
   // lift: A_k[i][j] = sum_p u^{Z2}_{k,j}[p] w^{ip};  B_k[i][j] = sum_q u^{Z1}_{k,i}[q] w^{jq}
-  for (int idx = threadIdx.x; idx < 4 * MM; idx += blockDim.x) {
+  for (int idx = threadIdx.x; !ffx && idx < 4 * MM; idx += blockDim.x) {
     const int which = idx / MM, i = (idx % MM) / M, j = idx % M;
     const int kk = which & 1, isB = which >> 1;
     const int t = kk ? t2 : t1, lo = kk ? t1 : 0;
@@ -904,7 +940,36 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
   __syncthreads();
   CBP_TICK(ph, 1);
   // normal matrix of the scale system
-  for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+  if (ffx) {
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) {
+      const int r = idx / n, c = idx % n;
+      cfx_acc g;
+      if (r < M && c < M) {
+        if (r == c)
+          for (int k = 0; k < nk; ++k)
+            for (int i = 0; i < M; ++i) g.macc(abx[k * MM + i * M + r], abx[k * MM + i * M + r]);
+      } else if (r >= M && c >= M) {
+        if (r == c)
+          for (int k = 0; k < nk; ++k)
+            for (int j = 0; j < M; ++j)
+              g.macc(abx[(2 + k) * MM + (r - M) * M + j], abx[(2 + k) * MM + (r - M) * M + j]);
+      } else if (r < M) {   // (gamma_j, delta_i) = -sum_k conj(A_k[i][j]) B_k[i][j]
+        const int j = r, i = c - M;
+        for (int k = 0; k < nk; ++k) {
+          const cfx av = abx[k * MM + i * M + j];
+          g.macc({fx_neg(av.re), fx_neg(av.im)}, abx[(2 + k) * MM + i * M + j]);
+        }
+      } else {
+        const int j = c, i = r - M;
+        for (int k = 0; k < nk; ++k) {
+          const cfx bv = abx[(2 + k) * MM + i * M + j];
+          g.macc({fx_neg(bv.re), fx_neg(bv.im)}, abx[k * MM + i * M + j]);
+        }
+      }
+      Gs[idx] = cfx_val(g.value());
+    }
+  }
+  for (int idx = threadIdx.x; !ffx && idx < n * n; idx += blockDim.x) {
     const int r = idx / n, c = idx % n;
     cd g = mk(0.0, 0.0);
     if (mode == kScaleSupport) {
@@ -984,7 +1049,23 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
       double d = abs2(z);
       return d > 0 ? mk(z.re / d, -z.im / d) : mk(0.0, 0.0);
     }();
-    for (int idx = threadIdx.x; idx < MM; idx += blockDim.x) {
+    cfx* Yx = (cfx*)Xk;   // float-float: Xk inv00 in place, then the stages on Tx
+    cfx* Tx = (cfx*)T;
+    if (ffx) {
+      const cfx inv = cfx_of(inv00);
+      for (int idx = threadIdx.x; idx < MM; idx += blockDim.x) Yx[idx] = cfx_mul(cfx_of(Xk[idx]), inv);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < MM; idx += blockDim.x) {
+        const int i = idx / M, q = idx % M;
+        cfx_acc acc;
+        for (int j = 0; j < M; ++j) {
+          const cfx w = wtx[(j * q) % M];
+          acc.mac(Yx[i * M + j], {w.re, fx_neg(w.im)});
+        }
+        Tx[idx] = acc.value();
+      }
+    }
+    for (int idx = threadIdx.x; !ffx && idx < MM; idx += blockDim.x) {
       const int i = idx / M, q = idx % M;
       cd acc = mk(0.0, 0.0);
       for (int j = 0; j < M; ++j) cfma(acc, Xk[i * M + j] * inv00, root(wt, j * q, M, 1.0));
@@ -999,7 +1080,16 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
     for (int idx = threadIdx.x; idx < MM; idx += blockDim.x) {
       const int pp = idx / M, q = idx % M;
       cd acc = mk(0.0, 0.0);
-      for (int i = 0; i < M; ++i) cfma(acc, root(wt, i * pp, M, 1.0), T[i * M + q]);
+      if (ffx) {
+        cfx_acc ax;
+        for (int i = 0; i < M; ++i) {
+          const cfx w = wtx[(i * pp) % M];
+          ax.mac({w.re, fx_neg(w.im)}, Tx[i * M + q]);
+        }
+        acc = cfx_val(ax.value());
+      } else {
+        for (int i = 0; i < M; ++i) cfma(acc, root(wt, i * pp, M, 1.0), T[i * M + q]);
+      }
       acc = (1.0 / (double)MM) * acc;
       l_re += acc.re * acc.re;
       l_im += acc.im * acc.im;
@@ -1295,7 +1385,7 @@ __global__ void k_check_recip(const double* x, int64_t n, double* r, double* q) 
 }  // namespace
 
 size_t sample_solve_smem(int nn) { return tri_ws_bytes(nn); }
-size_t scale_solve_smem(int M) { return scale_tri_offset(M) + tri_ws_bytes(2 * M); }
+size_t scale_solve_smem(int M, int nn) { return scale_tri_offset(M) + tri_ws_bytes(2 * M); }
 
 void launch_sample_solve(const Plan& p, char* ws, cudaStream_t st) {
   SampleArgs a;
@@ -1361,7 +1451,13 @@ void launch_scale_solve(const Plan& p, char* ws, void* k1_out, void* k2_out, int
   a.accepted = p.learned ? (const int*)(ws + p.off_acc) : nullptr;
   a.rho = p.learned ? (const double*)(ws + p.off_rho) : nullptr;
   a.mode = p.scale_mode;
-  const size_t sm = scale_solve_smem(p.M);
+  // the mixed path's float-float stage where its shared memory fits
+  const size_t ff_end = scale_ff_offset(p.M, p.nn) + scale_ff_bytes(p.M, p.nn);
+  int dev = 0, smem_max = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&smem_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  a.ffx = p.mixed && p.scale_mode != kScaleSupport && ff_end <= (size_t)smem_max;
+  const size_t sm = a.ffx ? ff_end : scale_solve_smem(p.M, p.nn);
   cudaFuncSetAttribute(k_scale_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   k_scale_solve<<<p.n, kSolveThreads, sm, st>>>(a);
 }
