@@ -1010,13 +1010,20 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
   // refinement step against the exact operator (FP64 path); the mixed path
   // takes its single-precision T with Newton steps against the double G.
   const TriWs W = carve_tri(smem + scale_tri_offset(M), n);
+  cfx* Gx = nullptr;   // float-float copy of the normal matrix (the cofactors' space is free)
+  if (ffx) {
+    Gx = cof;
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < n * n; idx += blockDim.x) Gx[idx] = cfx_of(Gs[idx]);
+    __syncthreads();
+  }
   TriResult res;
   if (mode == kScaleSupport) {
     SupportApply ap{ab, wt, X, M, t1, t2};      // X is free until the combination below
     res = tri_smallest<cd, true>(W, Gs, n, 1, 1, 1e300, ap, tk, a.mixed != 0);
   } else {
     ScaleApply ap{ab, M, nk};
-    res = tri_smallest<cd, true>(W, Gs, n, 1, 1, 1e300, ap, tk, a.mixed != 0);
+    res = tri_smallest<cd, true>(W, Gs, n, 1, 1, 1e300, ap, tk, a.mixed != 0, Gx);
   }
   __syncthreads();
   CBP_TICK(ph, 3);

@@ -709,8 +709,11 @@ __device__ int tri_solve_lead(const TriWs& W, const cd* G, int n, int steps_far,
 // most 24 steps, which must bring the correction below 1e-9); returns false,
 // having changed nothing but the work area, for the others (they take
 // tri_solve_lead).
+// Gx: a float-float copy of G (or null): the Newton steps' residual G x is
+// then formed on the single-precision units (~1e-14) instead of in double.
 __device__ bool tri_solve_lead_sp(const TriWs& W, const cd* G, int n, TriResult& res, double& gs,
-                                  double& tnorm, long long* tk, bool prereduced = false) {
+                                  double& tnorm, long long* tk, bool prereduced = false,
+                                  const cfx* Gx = nullptr) {
   const int lane = threadIdx.x & 31;
   cf* A = (cf*)W.A;
   cf* tau = (cf*)W.tau;
@@ -838,13 +841,31 @@ __device__ bool tri_solve_lead_sp(const TriWs& W, const cd* G, int n, TriResult&
   for (int it = 0; it < max_it; ++it) {
     cd gx[2];
     cd th = mk(0.0, 0.0);
+    if (Gx) {
+      cfx* xx = (cfx*)W.part;   // x in float-float (the reduction's scratch is free)
+      for (int i = lane; i < n; i += 32) xx[i] = cfx_of(W.x[i]);
+      __syncwarp();
 #pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const int i = lane + 32 * c;
-      gx[c] = mk(0.0, 0.0);
-      if (i < n) {
-        for (int j = 0; j < n; ++j) cfmac(gx[c], G[(size_t)j * n + i], W.x[j]);   // (G x)_i
-        cfmac(th, W.x[i], gx[c]);
+      for (int c = 0; c < 2; ++c) {
+        const int i = lane + 32 * c;
+        gx[c] = mk(0.0, 0.0);
+        if (i < n) {
+          cfx_acc acc;
+          for (int j = 0; j < n; ++j) acc.macc(Gx[(size_t)j * n + i], xx[j]);   // (G x)_i
+          gx[c] = cfx_val(acc.value());
+          cfmac(th, W.x[i], gx[c]);
+        }
+      }
+      __syncwarp();
+    } else {
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        const int i = lane + 32 * c;
+        gx[c] = mk(0.0, 0.0);
+        if (i < n) {
+          for (int j = 0; j < n; ++j) cfmac(gx[c], G[(size_t)j * n + i], W.x[j]);   // (G x)_i
+          cfmac(th, W.x[i], gx[c]);
+        }
       }
     }
     const double theta = warp_sum(th.re);
@@ -1056,7 +1077,8 @@ __device__ void tri_olsen_real_block(const TriWs& W, int n, double gs, double tn
 template <typename E, bool BLOCK, class Apply>
 __device__ TriResult tri_smallest(const TriWs& W, const cd* G, int n, int steps_far,
                                   int steps_near, double refine_gap, const Apply& apply,
-                                  long long* tk = nullptr, bool single = false) {
+                                  long long* tk = nullptr, bool single = false,
+                                  const cfx* Gx = nullptr) {
   const int lane = threadIdx.x & 31;
   const bool lead = !BLOCK || threadIdx.x < 32;
   TriResult res = {};
@@ -1110,7 +1132,7 @@ __device__ TriResult tri_smallest(const TriWs& W, const cd* G, int n, int steps_
   }
   __shared__ double gt[2];   // block mode: the lead's scale and ||T|| for the other warps
   if (lead) {
-    if (single && n > 2 && tri_solve_lead_sp(W, G, n, res, gs, tnorm, tk, pre_sp))
+    if (single && n > 2 && tri_solve_lead_sp(W, G, n, res, gs, tnorm, tk, pre_sp, Gx))
       steps = 0;
     else
       steps = tri_solve_lead<E>(W, G, n, steps_far, steps_near, refine_gap, res, gs, tnorm, tk, pre);
@@ -1145,12 +1167,23 @@ __device__ TriResult tri_smallest(const TriWs& W, const cd* G, int n, int steps_
   if (lead) {
     // theta = x^H G x
     cd th = mk(0.0, 0.0);
+    cfx* xx = (cfx*)W.part;
+    if (Gx) {
+      for (int i = lane; i < n; i += 32) xx[i] = cfx_of(W.x[i]);
+      __syncwarp();
+    }
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       const int i = lane + 32 * c;
       if (i < n) {
         cd gx = mk(0.0, 0.0);
-        for (int j = 0; j < n; ++j) cfmac(gx, G[(size_t)j * n + i], W.x[j]);   // (G x)_i
+        if (Gx) {
+          cfx_acc acc;
+          for (int j = 0; j < n; ++j) acc.macc(Gx[(size_t)j * n + i], xx[j]);
+          gx = cfx_val(acc.value());
+        } else {
+          for (int j = 0; j < n; ++j) cfmac(gx, G[(size_t)j * n + i], W.x[j]);   // (G x)_i
+        }
         cfmac(th, W.x[i], gx);
       }
     }
