@@ -44,6 +44,20 @@ __device__ __forceinline__ fx fx_scale(fx a, float s) {   // a * s, s a single-p
   const float p = a.hi * s;
   return fx_norm(p, fmaf(a.hi, s, -p) + a.lo * s);
 }
+__device__ __forceinline__ fx fx_sub(fx a, fx b) { return fx_add(a, fx_neg(b)); }
+// a / b: a single-precision quotient, corrected once by the exactly formed
+// remainder a - q b (long division with two digits)
+__device__ __forceinline__ fx fx_div(fx a, fx b) {
+  const float q1 = __fdividef(a.hi, b.hi);
+  const float p = q1 * b.hi;
+  const float pe = fmaf(q1, b.hi, -p);                      // q1 b.hi = p + pe exactly
+  const float r = (((a.hi - p) - pe) + a.lo) - q1 * b.lo;   // a - q1 b
+  return fx_norm(q1, __fdividef(r, b.hi));
+}
+__device__ __forceinline__ fx fx_ldexp(fx a, int e) { return {ldexpf(a.hi, e), ldexpf(a.lo, e)}; }
+__device__ __forceinline__ float fx_abs_hi(fx a) { return fabsf(a.hi); }
+__device__ __forceinline__ bool fx_neg_sign(fx a) { return a.hi < 0.f || (a.hi == 0.f && a.lo < 0.f); }
+__device__ __forceinline__ bool fx_is_zero(fx a) { return a.hi == 0.f && a.lo == 0.f; }
 
 // Accumulator for sums of products: the products' high parts are added by
 // two-sum, every rounding term gathered in lo without renormalising (a few

@@ -681,7 +681,9 @@ __global__ void k_sample_solve(SampleArgs a, int nreal) {
         ap.ys_cap = (int)((dsm - per) / sizeof(float2));
       }
     }
-    res = tri_smallest<double, true>(W, G, n, far, 1, gap, ap, tk);
+    // mixed path with a CTA of three or more warps: float-float steps 2-5
+    res = tri_smallest<double, true>(W, G, n, far, 1, gap, ap, tk, false, nullptr,
+                                     a.mixed && blockDim.x >= 96);
     if (warp != 0) return;
   } else {
     SylvesterApply<false> ap;

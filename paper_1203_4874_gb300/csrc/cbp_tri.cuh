@@ -1066,6 +1066,343 @@ __device__ void tri_olsen_real_block(const TriWs& W, int n, double gs, double tn
   __syncthreads();
 }
 
+// ------------------------------------------------------------------------
+// Float-float forms of the real samples' steps 2-5 (mixed path): on this GPU
+// a double-precision instruction holds a scheduler's double unit for ~64
+// cycles, and these steps are chains of them on one lane or one warp.  The
+// same algorithms with float-float values (~48 bits) on the single-precision
+// units; T's eigenvalues come out to ~1e-13 ||T||, the vector from inverse
+// iteration and the Olsen step as before.
+
+// Sturm count of T - sig I from the leading minors p_i (product form),
+// rescaled by powers of two when they leave [2^-60, 2^60].
+__device__ __forceinline__ int sturm_count_x(const fx* d, const fx* e2, int n, fx sig) {
+  fx pm = {1.f, 0.f}, p = fx_sub(d[0], sig);
+  bool negp = fx_neg_sign(p) || fx_is_zero(p);
+  int cnt = negp ? 1 : 0;
+  for (int i = 1; i < n; ++i) {
+    const fx pn = fx_sub(fx_mul(fx_sub(d[i], sig), p), fx_mul(e2[i - 1], pm));
+    pm = p;
+    p = pn;
+    const bool neg = fx_is_zero(p) ? !negp : fx_neg_sign(p);
+    cnt += neg != negp;
+    negp = neg;
+    const float a = fmaxf(fabsf(p.hi), fabsf(pm.hi));
+    if (a > 0x1p60f) {
+      p = fx_ldexp(p, -60);
+      pm = fx_ldexp(pm, -60);
+    } else if (a < 0x1p-60f && a > 0.f) {
+      p = fx_ldexp(p, 60);
+      pm = fx_ldexp(pm, 60);
+    }
+  }
+  return cnt;
+}
+
+__device__ void multisect_x(const fx* d, const fx* e2, int n, int t, Bracket* br, int nb,
+                            const int* which) {
+  const int lane = threadIdx.x & 31;
+  const double h = (br[t].hi - br[t].lo) * (1.0 / 33.0);
+  const double sig = fma(h, (double)(lane + 1), br[t].lo);
+  const int c = sturm_count_x(d, e2, n, fx_of(sig));
+  for (int m = 0; m < nb; ++m) {
+    const unsigned above = __ballot_sync(0xffffffffu, c > which[m]);
+    shrink(br[m], above, sig);
+  }
+}
+
+__device__ __forceinline__ fx fx_clamp_pivot(fx x, float tiny) {
+  return fabsf(x.hi) >= tiny ? x : fx{fx_neg_sign(x) ? -tiny : tiny, 0.f};
+}
+// LU of T - sig I with row interchanges (lane 0), as tri_lu
+__device__ void tri_lu_x(const fx* d, const fx* e, fx* u0, fx* u1, fx* u2, fx* lm, int* pv, int n,
+                         fx sig, float tiny) {
+  if ((threadIdx.x & 31) != 0) return;
+  const fx one = {1.f, 0.f}, zero = {0.f, 0.f};
+  for (int i = 0; i < n; ++i) {
+    u0[i] = fx_sub(d[i], sig);
+    u1[i] = i + 1 < n ? e[i] : zero;
+    u2[i] = zero;
+  }
+  for (int i = 0; i + 1 < n; ++i) {
+    const fx sub = e[i];
+    const fx piv = u0[i];
+    if (fabsf(piv.hi) >= fabsf(sub.hi)) {
+      const fx r = fx_div(one, fx_clamp_pivot(piv, tiny));
+      const fx m = fx_mul(sub, r);
+      lm[i] = m;
+      pv[i] = 0;
+      u0[i] = r;
+      u0[i + 1] = fx_sub(u0[i + 1], fx_mul(m, u1[i]));
+    } else {
+      const fx r = fx_div(one, sub);
+      const fx m = fx_mul(piv, r);
+      const fx a1 = u0[i + 1], b1 = u1[i + 1];
+      lm[i] = m;
+      pv[i] = 1;
+      u0[i] = r;
+      u0[i + 1] = fx_sub(u1[i], fx_mul(m, a1));
+      u1[i + 1] = fx_neg(fx_mul(m, b1));
+      u1[i] = a1;
+      u2[i] = b1;
+    }
+  }
+  u0[n - 1] = fx_div(one, fx_clamp_pivot(u0[n - 1], tiny));
+}
+__device__ void tri_solve_x(const fx* u0, const fx* u1, const fx* u2, const fx* lm, const int* pv,
+                            int n, fx* b) {
+  if ((threadIdx.x & 31) != 0) return;
+  for (int i = 0; i + 1 < n; ++i) {
+    if (pv[i]) {
+      const fx t = b[i];
+      b[i] = b[i + 1];
+      b[i + 1] = t;
+    }
+    b[i + 1] = fx_sub(b[i + 1], fx_mul(lm[i], b[i]));
+  }
+  for (int i = n - 1; i >= 0; --i) {
+    fx v = b[i];
+    if (i + 1 < n) v = fx_sub(v, fx_mul(u1[i], b[i + 1]));
+    if (i + 2 < n) v = fx_sub(v, fx_mul(u2[i], b[i + 2]));
+    b[i] = fx_mul(u0[i], v);
+  }
+}
+__device__ __forceinline__ fx warp_sum_x(fx v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const fx w = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    v = fx_add(v, w);
+  }
+  return v;
+}
+// Real reflectors (float-float copies) on a float-float vector, as tri_apply_q_r.
+__device__ void tri_apply_q_rx(const fx* A, const fx* tau, int n, fx* b, bool back) {
+  const int lane = threadIdx.x & 31;
+  __syncwarp();
+  for (int s = 0; s + 1 < n; ++s) {
+    const int k = back ? n - 2 - s : s;
+    const fx tk = tau[k];
+    if (fx_is_zero(tk)) continue;
+    const fx* vk = A + (size_t)k * n;
+    fx_acc acc;
+    for (int i = lane; i < n; i += 32)
+      if (i > k) acc.mac(vk[i], b[i]);
+    const fx f = fx_mul(tk, warp_sum_x(acc.value()));
+    __syncwarp();
+    for (int i = lane; i < n; i += 32)
+      if (i > k) b[i] = fx_sub(b[i], fx_mul(f, vk[i]));
+    __syncwarp();
+  }
+}
+// 1 / ||b|| in single precision (a scale for normalising)
+__device__ __forceinline__ float inv_norm_x(const fx* b, int n) {
+  const int lane = threadIdx.x & 31;
+  float s = 0.f;
+  for (int i = lane; i < n; i += 32) s = fmaf(b[i].hi, b[i].hi, s);
+  s = warp_sum(s);
+  return s > 0.f ? rsqrtf(s) : 1.f;
+}
+
+// Steps 2-4 for a real sample whose T the CTA has reduced in double precision
+// (W.d, W.e; reflectors in W.A, W.tau): the brackets' single-precision rounds
+// as in tri_solve_lead, then T, the reflectors and everything after them in
+// float-float (overwriting the double copies in place).  Returns the number of
+// refinement steps (steps_far or steps_near, as tri_solve_lead).
+__device__ int tri_solve_lead_rx(const TriWs& W, const cd* G, int n, int steps_far, int steps_near,
+                                 double refine_gap, TriResult& res, double& gs, double& tnorm,
+                                 long long* tk) {
+  const int lane = threadIdx.x & 31;
+  double gmax = 0.0;
+  for (int i = lane; i < n; i += 32) gmax = fmax(gmax, G[(size_t)i * n + i].re);
+  gmax = warp_max(gmax);
+  if (!(gmax > 0.0)) {
+    for (int i = lane; i < n; i += 32) W.x[i] = mk(i == 0 ? 1.0 : 0.0, 0.0);
+    __syncwarp();
+    res.lam_min = res.lam_2 = res.lam_max = 0.0;
+    res.near_degenerate = 1;
+    gs = 1.0;
+    tnorm = 0.0;
+    return 0;
+  }
+  int ex;
+  frexp(gmax, &ex);
+  gs = ldexp(1.0, ex);
+  double glo = 1e300, ghi = -1e300;
+  for (int i = lane; i < n; i += 32) {
+    const double rad = (i > 0 ? fabs(W.e[i - 1]) : 0.0) + (i + 1 < n ? fabs(W.e[i]) : 0.0);
+    glo = fmin(glo, W.d[i] - rad);
+    ghi = fmax(ghi, W.d[i] + rad);
+    const double e2 = i + 1 < n ? W.e[i] * W.e[i] : 0.0;
+    W.e2[i] = e2;
+    W.df[i] = (float)W.d[i];
+    W.e2f[i] = (float)e2;
+  }
+  glo = -warp_max(-glo);
+  ghi = warp_max(ghi);
+  tnorm = fmax(fabs(glo), fabs(ghi));
+  glo -= 4e-13 * tnorm + 1e-300;
+  ghi += 4e-13 * tnorm + 1e-300;
+  __syncwarp();
+  const int which[3] = {0, n > 1 ? 1 : 0, n - 1};
+  Bracket br[3] = {{glo, ghi}, {glo, ghi}, {glo, ghi}};
+  const double fl = 1e-5 * tnorm;
+  const float tiny_f = (float)(1e-30 * fmax(tnorm, 1e-8));
+  for (int round = 0; round < 12; ++round) {
+    int t = -1;
+    for (int m = 2; m >= 0; --m)
+      if (br[m].hi - br[m].lo > fl) t = m;
+    if (t < 0) break;
+    multisect<true>(W, n, t, br, 3, which, tiny_f);
+  }
+  for (int m = 0; m < 3; ++m) {
+    br[m].lo = fmax(glo, br[m].lo - 4e-6 * tnorm);
+    br[m].hi = fmin(ghi, br[m].hi + 4e-6 * tnorm);
+  }
+  // T in float-float, in place of its double copies
+  fx* dx = (fx*)W.d;
+  fx* ex_ = (fx*)W.e;
+  fx* e2x = (fx*)W.e2;
+  for (int i = lane; i < n; i += 32) {
+    const double d = W.d[i], e = W.e[i], e2 = W.e2[i];
+    dx[i] = fx_of(d);
+    ex_[i] = fx_of(e);
+    e2x[i] = fx_of(e2);
+  }
+  __syncwarp();
+  {
+    const int m = lane % 3, end = (lane / 3) & 1;
+    const double sig = end ? br[m].hi : br[m].lo;
+    const int c = lane < 6 ? sturm_count_x(dx, e2x, n, fx_of(sig)) : 0;
+    const bool bad = lane < 6 && (end ? c <= which[m] : c > which[m]);
+    const unsigned badm = __ballot_sync(0xffffffffu, bad);
+    for (int m2 = 0; m2 < 3; ++m2)
+      if (badm & (0x9u << m2)) br[m2] = Bracket{glo, ghi};
+  }
+  const double tol_abs = 1e-13 * tnorm;
+  for (int round = 0; round < 40; ++round) {
+    const double w0 = br[0].hi - br[0].lo;
+    if (w0 <= tol_abs || (n > 1 && br[1].lo > br[0].hi && w0 <= 1e-4 * (br[1].lo - br[0].hi)))
+      break;
+    multisect_x(dx, e2x, n, 0, br, 3, which);
+  }
+  if (n > 1) {
+    for (int round = 0; round < 40; ++round) {
+      const double w1 = br[1].hi - br[1].lo;
+      if (w1 <= fmax(tol_abs, 1e-5 * fabs(br[1].hi))) break;
+      multisect_x(dx, e2x, n, 1, br, 3, which);
+    }
+  }
+  for (int round = 0; round < 40; ++round) {
+    const double w2 = br[2].hi - br[2].lo;
+    if (w2 <= fmax(tol_abs, 1e-7 * fabs(br[2].hi))) break;
+    multisect_x(dx, e2x, n, 2, br, 3, which);
+  }
+  if (tk && lane == 0) tk[2] = clock64();
+  const double lam0 = 0.5 * (br[0].lo + br[0].hi);
+  const double lam1 = n > 1 ? 0.5 * (br[1].lo + br[1].hi) : lam0;
+  const double lamn = 0.5 * (br[2].lo + br[2].hi);
+  // the reflectors in float-float, in place (rows k, entries i > k)
+  fx* Ax = (fx*)W.A;
+  fx* taux = (fx*)W.tau;
+  {
+    const double* A = (const double*)W.A;
+    const double* tau = (const double*)W.tau;
+    for (int idx = lane; idx < n * n; idx += 32) {
+      const double v = A[idx];
+      if (idx % n > idx / n) Ax[idx] = fx_of(v);
+    }
+    for (int i = lane; i < n; i += 32) {
+      const double v = tau[i];
+      taux[i] = fx_of(v);
+    }
+    __syncwarp();
+  }
+  // 3. inverse iteration (three steps) from a fixed start vector; 4. x = Q y
+  fx* u0 = (fx*)W.u0;
+  fx* u1 = (fx*)W.u1;
+  fx* u2 = (fx*)W.u2;
+  fx* lm = (fx*)W.lm;
+  tri_lu_x(dx, ex_, u0, u1, u2, lm, W.piv, n, fx_of(lam0), (float)(1e-14 * tnorm));
+  fx* y = (fx*)W.z;
+  for (int i = lane; i < n; i += 32) y[i] = fx{1.0f + 0.25f * (float)((i * 7) % 5), 0.f};
+  __syncwarp();
+  for (int it = 0; it < 3; ++it) {
+    tri_solve_x(u0, u1, u2, lm, W.piv, n, y);
+    __syncwarp();
+    const float sc = inv_norm_x(y, n);
+    for (int i = lane; i < n; i += 32) y[i] = fx_scale(y[i], sc);
+    __syncwarp();
+  }
+  tri_apply_q_rx(Ax, taux, n, y, true);
+  for (int i = lane; i < n; i += 32) W.x[i] = mk(fx_val(y[i]), 0.0);
+  __syncwarp();
+  const double sc = rsqrt_safe(tri_norm2(W.x, n));
+  for (int i = lane; i < n; i += 32) W.x[i] = sc * W.x[i];
+  __syncwarp();
+  if (tk && lane == 0) tk[3] = clock64();
+  res.lam_min = gs * lam0;
+  res.lam_2 = gs * lam1;
+  res.lam_max = gs * lamn;
+  res.near_degenerate = n > 1 && (lam1 - lam0) <= 1e-4 * lamn ? 1 : 0;
+  const bool near = n > 1 && (lam1 - lam0) <= refine_gap * lamn;
+  return near ? steps_near : steps_far;
+}
+
+// The Olsen step of tri_olsen_real_block with tri_solve_lead_rx's float-float
+// T and reflectors (three warps: Q^T r, Q^T x with the factorisation, then
+// the two solves; warp 0 finishes).
+__device__ void tri_olsen_real_block_x(const TriWs& W, int n, double gs, double tnorm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const fx* Ax = (const fx*)W.A;
+  const fx* taux = (const fx*)W.tau;
+  const fx* dx = (const fx*)W.d;
+  const fx* ex_ = (const fx*)W.e;
+  fx* u0 = (fx*)W.u0;
+  fx* u1 = (fx*)W.u1;
+  fx* u2 = (fx*)W.u2;
+  fx* lm = (fx*)W.lm;
+  const double igs = 1.0 / gs;
+  fx* ru = (fx*)W.q;        // Q^T r, then u
+  fx* yt = ru + n;          // Q^T x
+  fx* zt = (fx*)W.z;        // z, then the correction
+  double th = 0.0;
+  for (int i = lane; i < n; i += 32) th = fma(W.x[i].re, W.r[i].re, th);
+  const double theta = warp_sum(th);
+  if (warp == 0) {
+    for (int i = lane; i < n; i += 32) ru[i] = fx_of(W.r[i].re - theta * W.x[i].re);
+    tri_apply_q_rx(Ax, taux, n, ru, false);
+  } else if (warp == 1) {
+    for (int i = lane; i < n; i += 32) yt[i] = fx_of(W.x[i].re);
+    tri_apply_q_rx(Ax, taux, n, yt, false);
+    for (int i = lane; i < n; i += 32) zt[i] = yt[i];
+    __syncwarp();
+  } else if (warp == 2) {
+    tri_lu_x(dx, ex_, u0, u1, u2, lm, W.piv, n, fx_of(theta * igs), (float)(1e-14 * tnorm));
+  }
+  __syncthreads();
+  if (warp == 0) tri_solve_x(u0, u1, u2, lm, W.piv, n, ru);
+  else if (warp == 1) tri_solve_x(u0, u1, u2, lm, W.piv, n, zt);
+  __syncthreads();
+  if (warp == 0) {
+    fx_acc nu, de;
+    for (int i = lane; i < n; i += 32) {
+      nu.mac(yt[i], ru[i]);
+      de.mac(yt[i], zt[i]);
+    }
+    const fx nuv = warp_sum_x(nu.value()), dev = warp_sum_x(de.value());
+    const fx ep = fx_is_zero(dev) ? fx{0.f, 0.f} : fx_div(nuv, dev);
+    const float ig = (float)igs;   // a power of two: exact
+    for (int i = lane; i < n; i += 32) zt[i] = fx_scale(fx_sub(fx_mul(ep, zt[i]), ru[i]), ig);
+    tri_apply_q_rx(Ax, taux, n, zt, true);
+    for (int i = lane; i < n; i += 32) W.x[i] = mk(W.x[i].re + fx_val(zt[i]), 0.0);
+    __syncwarp();
+    const double sc = rsqrt_safe(tri_norm2(W.x, n));
+    for (int i = lane; i < n; i += 32) W.x[i] = sc * W.x[i];
+    __syncwarp();
+  }
+  __syncthreads();
+}
+
 
 // G: the n x n matrix (row-major, global or shared memory).  Result in W.x
 // (unit norm).  Steps of the exact-operator refinement: `steps_far` when the
@@ -1078,7 +1415,7 @@ template <typename E, bool BLOCK, class Apply>
 __device__ TriResult tri_smallest(const TriWs& W, const cd* G, int n, int steps_far,
                                   int steps_near, double refine_gap, const Apply& apply,
                                   long long* tk = nullptr, bool single = false,
-                                  const cfx* Gx = nullptr) {
+                                  const cfx* Gx = nullptr, bool ffr = false) {
   const int lane = threadIdx.x & 31;
   const bool lead = !BLOCK || threadIdx.x < 32;
   TriResult res = {};
@@ -1134,6 +1471,8 @@ __device__ TriResult tri_smallest(const TriWs& W, const cd* G, int n, int steps_
   if (lead) {
     if (single && n > 2 && tri_solve_lead_sp(W, G, n, res, gs, tnorm, tk, pre_sp, Gx))
       steps = 0;
+    else if (ffr && pre)   // real sample, mixed path: float-float steps 2-5
+      steps = tri_solve_lead_rx(W, G, n, steps_far, steps_near, refine_gap, res, gs, tnorm, tk);
     else
       steps = tri_solve_lead<E>(W, G, n, steps_far, steps_near, refine_gap, res, gs, tnorm, tk, pre);
     if (BLOCK && lane == 0) {
@@ -1156,7 +1495,8 @@ __device__ TriResult tri_smallest(const TriWs& W, const cd* G, int n, int steps_
     if (tk && lead && lane == 0) tk[6] = clock64();   // end of the last step's apply
     if constexpr (BLOCK && sizeof(E) == sizeof(double)) {
       if (par) {
-        tri_olsen_real_block(W, n, gs, tnorm);
+        if (ffr && pre) tri_olsen_real_block_x(W, n, gs, tnorm);
+        else tri_olsen_real_block(W, n, gs, tnorm);
         continue;
       }
     }
