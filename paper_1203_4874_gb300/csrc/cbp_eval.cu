@@ -57,12 +57,13 @@ __device__ __forceinline__ double bin_at(const void* b, int64_t i) {
 //         [+ (-1)^s b_(M/2) when M is even].
 template <bool F32>
 __global__ void __launch_bounds__(kDftThreads) k_fold_dft(FoldDftArgs a) {
+  if (a.accepted && a.accepted[blockIdx.y / a.C]) return;   // the proposal stands (whole block)
   __shared__ double cs[kMaxM], sn[kMaxM];
   for (int k = threadIdx.x; k < a.M; k += blockDim.x) sincospi(2.0 * (double)k / (double)a.M, &sn[k], &cs[k]);
   __syncthreads();
   const int z = blockIdx.z, fc = blockIdx.y, M = a.M, len = a.len[z];
   const int pos = blockIdx.x * blockDim.x + threadIdx.x;
-  if (pos >= len || (a.accepted && a.accepted[fc / a.C])) return;
+  if (pos >= len) return;
   const int64_t b = (int64_t)fc * M * len + pos;
   const void* bb = a.bins[z];
   const int h = (M - 1) / 2;
@@ -123,7 +124,8 @@ __device__ __forceinline__ F2 f2_norm(F2 a) {
 
 // The same DFT in float-float arithmetic from (hi, lo) bins of float32 frames:
 // ~1e-14 of the terms' magnitudes, like the bins themselves.
-__global__ void __launch_bounds__(kDftThreads) k_fold_dft_ff(FoldDftArgs a) {
+__global__ void __launch_bounds__(kDftThreads, 4) k_fold_dft_ff(FoldDftArgs a) {
+  if (a.accepted && a.accepted[blockIdx.y / a.C]) return;   // the proposal stands (whole block)
   __shared__ F2 cs[kMaxM], sn[kMaxM];
   for (int k = threadIdx.x; k < a.M; k += blockDim.x) {
     double s, c;
@@ -135,7 +137,7 @@ __global__ void __launch_bounds__(kDftThreads) k_fold_dft_ff(FoldDftArgs a) {
   __syncthreads();
   const int z = blockIdx.z, fc = blockIdx.y, M = a.M, len = a.len[z];
   const int pos = blockIdx.x * blockDim.x + threadIdx.x;
-  if (pos >= len || (a.accepted && a.accepted[fc / a.C])) return;
+  if (pos >= len) return;
   const float2* bb = (const float2*)a.bins[z] + (int64_t)fc * M * len + pos;
   auto bin = [&](int m) {
     const float2 v = bb[(int64_t)m * len];
