@@ -626,8 +626,10 @@ cbp_status call_path(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
 #endif
     s = cbp::run_plan(cp[i], &f1[i], &f2[i], prm, ck1, ck2, clat, deblur, w, cs, tlp, nullptr,
                       c->cnn_w, host_io, host_io ? nullptr : c->read_ev[i],
-                      c->solve_st[i % Ctx::kChunkStreams], c->fork_ev[i], c->join_ev[i],
-                      tw_ready);
+                      // device-resident calls only: with host I/O's copy stream the
+                      // extra streams would share the GPU's hardware queues with it
+                      host_io ? nullptr : c->solve_st[i % Ctx::kChunkStreams], c->fork_ev[i],
+                      c->join_ev[i], tw_ready);
     if (s != CBP_OK) return s;
     if (diag && cudaMemcpyAsync(diag + a, w + cp[i].off_diag, (size_t)cp[i].n * sizeof(cbp_diag),
                                 cudaMemcpyDeviceToHost, cs) != cudaSuccess)
