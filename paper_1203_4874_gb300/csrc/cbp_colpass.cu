@@ -216,156 +216,158 @@ k_col_deconv_fused(FusedColArgs a) {
   // Slot (j, m) = logical row j + N1 m sits at physical row (j ^ (m & 3)) + N1 m
   // (fc_phys): with four base pointers per thread every access below is a
   // base plus an immediate offset.
-  // ---- step 1: N2-point DFTs down the columns, twiddled, in place
+  // Steps 1 and 3 share one code path (phase 0: forward N2-point DFTs of both
+  // frames, twiddled, in place; phase 1: the inverse as conj(DFT(conj(.))), rows
+  // < H out), with step 2 between them: one copy of each transform's code.
+  // ---- step 1 (phase 0), step 2, step 3 (phase 1)
 #pragma unroll 1
-  for (int task = tid; task < 2 * N1 * kFcCols; task += kFcThreads) {
-    const int fr = task / (N1 * kFcCols), r = task % (N1 * kFcCols);
-    const int n1 = r / kFcCols, col = r % kFcCols;
-    cf* b = buf0 + (fr ? B1 : 0) + col;
-    cf* q[4];
+  for (int ph = 0; ph < 2; ++ph) {
+    if (ph == 1) {
+      __syncthreads();
+      FC_TICK(3);
+      // ---- step 2: N1-point DFTs across, the formula, the inverse N1-point DFTs
+      float rn = 0.f, rd = 0.f;   // RESID: this task's residual sums
+      if (tid < N2 * kFcCols) {
+        const int k2 = tid / kFcCols, col = tid % kFcCols;
+        cf* q[4];
+        {
+          cf* base = buf0 + (N1 * k2) * S + col;
 #pragma unroll
-    for (int c = 0; c < 4; ++c) q[c] = b + (n1 ^ c) * S;
-    cf x[N2];
-#pragma unroll
-    for (int m = 0; m < N2; ++m) x[m] = q[m & 3][N1 * m * S];
-    reg_dft<false, N2>(x);
-    const cf* tw = a.tw1 + n1;                        // w_Ph^(n1 m) at [m][n1]
-#pragma unroll
-    for (int m = 0; m < N2; ++m) {
-      cf y = x[reg_pos<N2>(m)];
-      if (m) y = y * ldg_cf(tw + N1 * m);
-      q[m & 3][N1 * m * S] = y;
-    }
-  }
-  __syncthreads();
-  FC_TICK(3);
-
-  // ---- step 2: N1-point DFTs across, the formula, the inverse N1-point DFTs
-  float rn = 0.f, rd = 0.f;   // RESID: this task's residual sums
-  if (tid < N2 * kFcCols) {
-    const int k2 = tid / kFcCols, col = tid % kFcCols;
-    cf* q[4];
-    {
-      cf* base = buf0 + (N1 * k2) * S + col;
-#pragma unroll
-      for (int c = 0; c < 4; ++c) q[c] = base + (c ^ (k2 & 3)) * S;
-    }
-    // element j of this task's slots: q[j & 3][(j & ~3) S] (+ B1 for frame 2)
+          for (int c = 0; c < 4; ++c) q[c] = base + (c ^ (k2 & 3)) * S;
+        }
+        // element j of this task's slots: q[j & 3][(j & ~3) S] (+ B1 for frame 2)
 #define FC_AT(j) q[(j) & 3][((j) & ~3) * S]
 #define FC_AT1(j) q[(j) & 3][((j) & ~3) * S + B1]
-    float d1[N1];
-    cf x[N1];          // the working transform; ends up holding I^ at reg_pos order
-    cf y[N1];          // RESID: K^1 while K^2 is made
-    const float eps = a.eps;
-    // four forward N1-point DFTs through one code path: frame 2's and frame
-    // 1's column spectra (back into their slots), then the two kernels'
-    // spectra K^(k2 + N2 k1) = DFT_N1 over p of R_p w_Ph^(p k2), each consumed
-    // by its part of the formula at once
+        float d1[N1];
+        cf x[N1];          // the working transform; ends up holding I^ at reg_pos order
+        cf y[N1];          // RESID: K^1 while K^2 is made
+        const float eps = a.eps;
+        // four forward N1-point DFTs through one code path: frame 2's and frame
+        // 1's column spectra (back into their slots), then the two kernels'
+        // spectra K^(k2 + N2 k1) = DFT_N1 over p of R_p w_Ph^(p k2), each consumed
+        // by its part of the formula at once
 #pragma unroll 1
-    for (int it = 0; it < (RESID ? 2 : 4); ++it) {
-      if (it == 0) {
+        for (int it = 0; it < (RESID ? 2 : 4); ++it) {
+          if (it == 0) {
 #pragma unroll
-        for (int j = 0; j < N1; ++j) x[j] = FC_AT1(j);
-      } else if (it == 1) {
+            for (int j = 0; j < N1; ++j) x[j] = FC_AT1(j);
+          } else if (it == 1) {
 #pragma unroll
-        for (int j = 0; j < N1; ++j) x[j] = FC_AT(j);
-      } else {
-        fc_kspec_in<N1, N2>(x, rt + (it - 2) * kFcMaxT * kFcCols + col, it == 2 ? a.t1 : a.t2,
-                            a.tw2 + k2);
-      }
-      reg_dft<false, N1>(x);
-      if (it == 0) {
+            for (int j = 0; j < N1; ++j) x[j] = FC_AT(j);
+          } else {
+            fc_kspec_in<N1, N2>(x, rt + (it - 2) * kFcMaxT * kFcCols + col, it == 2 ? a.t1 : a.t2,
+                                a.tw2 + k2);
+          }
+          reg_dft<false, N1>(x);
+          if (it == 0) {
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) FC_AT1(k1) = x[reg_pos<N1>(k1)];
-      } else if (it == 1) {
+            for (int k1 = 0; k1 < N1; ++k1) FC_AT1(k1) = x[reg_pos<N1>(k1)];
+          } else if (it == 1) {
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) FC_AT(k1) = x[reg_pos<N1>(k1)];
-      } else if (it == 2) {
+            for (int k1 = 0; k1 < N1; ++k1) FC_AT(k1) = x[reg_pos<N1>(k1)];
+          } else if (it == 2) {
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) {
-          const cf k = x[reg_pos<N1>(k1)];
-          FC_AT(k1) = fc_cmulc(k, FC_AT(k1));       // conj(K^1) B^1
-          d1[k1] = fc_abs2(k);
+            for (int k1 = 0; k1 < N1; ++k1) {
+              const cf k = x[reg_pos<N1>(k1)];
+              FC_AT(k1) = fc_cmulc(k, FC_AT(k1));       // conj(K^1) B^1
+              d1[k1] = fc_abs2(k);
+            }
+          } else {
+#pragma unroll
+            for (int k1 = 0; k1 < N1; ++k1) {
+              const cf k = x[reg_pos<N1>(k1)];
+              x[reg_pos<N1>(k1)] = fc_formula(FC_AT(k1), d1[k1], k, FC_AT1(k1), eps);   // I^(k2 + N2 k1)
+            }
+          }
         }
-      } else {
+        if constexpr (RESID) {
+          // both kernels' spectra at once (K^1 in y, K^2 in x), the residual sums
+          // and the formula
+          fc_kspec_in<N1, N2>(y, rt + col, a.t1, a.tw2 + k2);
+          reg_dft<false, N1>(y);
+          fc_kspec_in<N1, N2>(x, rt + kFcMaxT * kFcCols + col, a.t2, a.tw2 + k2);
+          reg_dft<false, N1>(x);
 #pragma unroll
-        for (int k1 = 0; k1 < N1; ++k1) {
-          const cf k = x[reg_pos<N1>(k1)];
-          x[reg_pos<N1>(k1)] = fc_formula(FC_AT(k1), d1[k1], k, FC_AT1(k1), eps);   // I^(k2 + N2 k1)
+          for (int k1 = 0; k1 < N1; ++k1) {
+            const cf kk1 = y[reg_pos<N1>(k1)], kk2 = x[reg_pos<N1>(k1)];
+            const cf b1 = FC_AT(k1), b2 = FC_AT1(k1);
+            const cf r = kk2 * b1 - kk1 * b2;
+            rn += abs2(r);
+            rd += abs2(b1);
+            x[reg_pos<N1>(k1)] = fc_formula(fc_cmulc(kk1, b1), fc_abs2(kk1), kk2, b2, eps);
+          }
         }
-      }
-    }
-    if constexpr (RESID) {
-      // both kernels' spectra at once (K^1 in y, K^2 in x), the residual sums
-      // and the formula
-      fc_kspec_in<N1, N2>(y, rt + col, a.t1, a.tw2 + k2);
-      reg_dft<false, N1>(y);
-      fc_kspec_in<N1, N2>(x, rt + kFcMaxT * kFcCols + col, a.t2, a.tw2 + k2);
-      reg_dft<false, N1>(x);
+        {
+          // inverse over k1, twiddled by w_Ph^(-n1 k2), into this task's slots
+          cf iv[N1];
 #pragma unroll
-      for (int k1 = 0; k1 < N1; ++k1) {
-        const cf kk1 = y[reg_pos<N1>(k1)], kk2 = x[reg_pos<N1>(k1)];
-        const cf b1 = FC_AT(k1), b2 = FC_AT1(k1);
-        const cf r = kk2 * b1 - kk1 * b2;
-        rn += abs2(r);
-        rd += abs2(b1);
-        x[reg_pos<N1>(k1)] = fc_formula(fc_cmulc(kk1, b1), fc_abs2(kk1), kk2, b2, eps);
-      }
-    }
-    // inverse over k1, twiddled by w_Ph^(-n1 k2), into this task's slots
-    cf iv[N1];
+          for (int k1 = 0; k1 < N1; ++k1) iv[k1] = x[reg_pos<N1>(k1)];
+          reg_dft<true, N1>(iv);
 #pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) iv[k1] = x[reg_pos<N1>(k1)];
-    reg_dft<true, N1>(iv);
-#pragma unroll
-    for (int n1 = 0; n1 < N1; ++n1) {
-      cf z = iv[reg_pos<N1>(n1)];
-      if (n1) z = z * conj(ldg_cf(a.tw2 + N2 * n1 + k2));
-      FC_AT(n1) = z;
-    }
+          for (int n1 = 0; n1 < N1; ++n1) {
+            cf z = iv[reg_pos<N1>(n1)];
+            if (n1) z = z * conj(ldg_cf(a.tw2 + N2 * n1 + k2));
+            FC_AT(n1) = z;
+          }
+        }
 #undef FC_AT
 #undef FC_AT1
-  }
-  if constexpr (RESID) {
-    __shared__ double red[2][kFcThreads / 32];
-    const int v = v0 + tid % kFcCols;
-    const double wv = (v == 0 || 2 * v == a.Pw) ? 1.0 : 2.0;
-    const double sn = warp_sum(wv * (double)rn), sd = warp_sum(wv * (double)rd);
-    if ((tid & 31) == 0) {
-      red[0][tid >> 5] = sn;
-      red[1][tid >> 5] = sd;
-    }
-    __syncthreads();
-    if (tid == 0) {
-      double tn = 0.0, td = 0.0;
-      for (int w = 0; w < kFcThreads / 32; ++w) {
-        tn += red[0][w];
-        td += red[1][w];
       }
-      double* o = a.rpart + ((int64_t)fc * gridDim.x + blockIdx.x) * 2;
-      o[0] = tn;
-      o[1] = td;
+      if constexpr (RESID) {
+        __shared__ double red[2][kFcThreads / 32];
+        const int v = v0 + tid % kFcCols;
+        const double wv = (v == 0 || 2 * v == a.Pw) ? 1.0 : 2.0;
+        const double sn = warp_sum(wv * (double)rn), sd = warp_sum(wv * (double)rd);
+        if ((tid & 31) == 0) {
+          red[0][tid >> 5] = sn;
+          red[1][tid >> 5] = sd;
+        }
+        __syncthreads();
+        if (tid == 0) {
+          double tn = 0.0, td = 0.0;
+          for (int w = 0; w < kFcThreads / 32; ++w) {
+            tn += red[0][w];
+            td += red[1][w];
+          }
+          double* o = a.rpart + ((int64_t)fc * gridDim.x + blockIdx.x) * 2;
+          o[0] = tn;
+          o[1] = td;
+        }
+      }
+      __syncthreads();
+      FC_TICK(4);
     }
-  }
-  __syncthreads();
-  FC_TICK(4);
-
-  // ---- step 3: inverse N2-point DFTs down the columns, rows < H out
-  if (tid < N1 * kFcCols) {
-    const int n1 = tid / kFcCols, col = tid % kFcCols;
-    const cf* q[4];
+    const int ntask = ph ? N1 * kFcCols : 2 * N1 * kFcCols;
+#pragma unroll 1
+    for (int task = tid; task < ntask; task += kFcThreads) {
+      const int fr = task / (N1 * kFcCols), r = task % (N1 * kFcCols);
+      const int n1 = r / kFcCols, col = r % kFcCols;
+      cf* b = buf0 + (fr ? B1 : 0) + col;
+      cf* q[4];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) q[c] = buf0 + col + (n1 ^ c) * S;
-    cf x[N2];
+      for (int c = 0; c < 4; ++c) q[c] = b + (n1 ^ c) * S;
+      cf x[N2];
 #pragma unroll
-    for (int m = 0; m < N2; ++m) x[m] = q[m & 3][N1 * m * S];
-    reg_dft<true, N2>(x);
-    if (col < nv) {
-      cf* dst = a.ihat + ((int64_t)fc * a.H + n1) * a.Pw2p + v0 + col;
-      const int64_t step = (int64_t)N1 * a.Pw2p;
+      for (int m = 0; m < N2; ++m) {
+        const cf v = q[m & 3][N1 * m * S];
+        x[m] = ph ? conj(v) : v;
+      }
+      reg_dft<false, N2>(x);
+      if (ph == 0) {
+        const cf* tw = a.tw1 + n1;                    // w_Ph^(n1 m) at [m][n1]
 #pragma unroll
-      for (int n2 = 0; n2 < N2; ++n2) {
-        if (n1 + N1 * n2 < a.H) dst[n2 * step] = x[reg_pos<N2>(n2)];
+        for (int m = 0; m < N2; ++m) {
+          cf y = x[reg_pos<N2>(m)];
+          if (m) y = y * ldg_cf(tw + N1 * m);
+          q[m & 3][N1 * m * S] = y;
+        }
+      } else if (col < nv) {
+        cf* dst = a.ihat + ((int64_t)fc * a.H + n1) * a.Pw2p + v0 + col;
+        const int64_t step = (int64_t)N1 * a.Pw2p;
+#pragma unroll
+        for (int n2 = 0; n2 < N2; ++n2) {
+          if (n1 + N1 * n2 < a.H) dst[n2 * step] = conj(x[reg_pos<N2>(n2)]);
+        }
       }
     }
   }
