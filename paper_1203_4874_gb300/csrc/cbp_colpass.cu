@@ -242,16 +242,16 @@ k_col_deconv_fused(FusedColArgs a) {
         cf x[N1];          // the working transform; ends up holding I^ at reg_pos order
         cf y[N1];          // RESID: K^1 while K^2 is made
         const float eps = a.eps;
-        // four forward N1-point DFTs through one code path: frame 2's and frame
-        // 1's column spectra (back into their slots), then the two kernels'
-        // spectra K^(k2 + N2 k1) = DFT_N1 over p of R_p w_Ph^(p k2), each consumed
-        // by its part of the formula at once
+        // five N1-point DFTs through one code path: frame 2's and frame 1's
+        // column spectra (back into their slots), the two kernels' spectra
+        // K^(k2 + N2 k1) = DFT_N1 over p of R_p w_Ph^(p k2), each consumed by its
+        // part of the formula at once, and the inverse (conjugated in and out)
 #pragma unroll 1
-        for (int it = 0; it < (RESID ? 2 : 4); ++it) {
+        for (int it = 0; it < (RESID ? 2 : 5); ++it) {
           if (it == 0) {
 #pragma unroll
             for (int j = 0; j < N1; ++j) x[j] = FC_AT1(j);
-          } else if (it == 1) {
+          } else if (it == 1 || it == 4) {
 #pragma unroll
             for (int j = 0; j < N1; ++j) x[j] = FC_AT(j);
           } else {
@@ -272,11 +272,21 @@ k_col_deconv_fused(FusedColArgs a) {
               FC_AT(k1) = fc_cmulc(k, FC_AT(k1));       // conj(K^1) B^1
               d1[k1] = fc_abs2(k);
             }
-          } else {
+          } else if (it == 3) {
+            // I^(k2 + N2 k1), conjugated, into this task's slots in natural
+            // order: the inverse runs as conj(DFT(conj(.))) on the next pass
 #pragma unroll
             for (int k1 = 0; k1 < N1; ++k1) {
               const cf k = x[reg_pos<N1>(k1)];
-              x[reg_pos<N1>(k1)] = fc_formula(FC_AT(k1), d1[k1], k, FC_AT1(k1), eps);   // I^(k2 + N2 k1)
+              FC_AT(k1) = conj(fc_formula(FC_AT(k1), d1[k1], k, FC_AT1(k1), eps));
+            }
+          } else {
+            // the inverse over k1, twiddled by w_Ph^(-n1 k2), into this task's slots
+#pragma unroll
+            for (int n1 = 0; n1 < N1; ++n1) {
+              cf z = conj(x[reg_pos<N1>(n1)]);
+              if (n1) z = z * conj(ldg_cf(a.tw2 + N2 * n1 + k2));
+              FC_AT(n1) = z;
             }
           }
         }
@@ -297,7 +307,7 @@ k_col_deconv_fused(FusedColArgs a) {
             x[reg_pos<N1>(k1)] = fc_formula(fc_cmulc(kk1, b1), fc_abs2(kk1), kk2, b2, eps);
           }
         }
-        {
+        if constexpr (RESID) {
           // inverse over k1, twiddled by w_Ph^(-n1 k2), into this task's slots
           cf iv[N1];
 #pragma unroll
