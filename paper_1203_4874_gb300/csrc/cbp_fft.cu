@@ -741,13 +741,15 @@ constexpr int kIrThreads = 256;      // eight warps: two blocks keep four warps 
 constexpr int kIrRows = 7;           // rows per group: 7 x 36 step-1 tasks, one warp per row in step 2
 
 struct RowIrSmem {
-  size_t tw, raw, colacc, rb, rph, mbar, total;
+  size_t tw, tw2, raw, colacc, rb, rph, mbar, total;
 };
 __host__ __device__ inline RowIrSmem row_ir_layout(int rw) {
   RowIrSmem L;
   size_t o = 0;
   L.tw = o;                                       // w_Pw^k, k < Pw = rw - 4
   o += rp_align((size_t)(rw - 4) * sizeof(cf));
+  L.tw2 = o;                                      // step 1's w_N^(n1 k2) at [k2][n1], N = Pw / 2
+  o += rp_align((size_t)(rw - 4) / 2 * sizeof(cf));
   L.raw = o;
   o += rp_align((size_t)kIrRows * rw * sizeof(float));
   L.colacc = o;                                   // column-fold (hi, lo) per column, W <= rw
@@ -776,13 +778,17 @@ k_row_pass_ir(RowPassArgs a, const cf* tw_w) {
   int* rph = (int*)(smem + L.rph);
   uint64_t* bar = (uint64_t*)(smem + L.mbar);
   cf* tws = (cf*)(smem + L.tw);
+  cf* tw2s = (cf*)(smem + L.tw2);
   const int tid = threadIdx.x;
   if (tid == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
   }
   if (fft)
-    for (int k = tid; k < 2 * N; k += kIrThreads) tws[k] = ldg_cpx(tw_w + k);
+    for (int k = tid; k < 2 * N; k += kIrThreads) {
+      tws[k] = ldg_cpx(tw_w + k);
+      if (k < N) tw2s[k] = ldg_cpx(a.tw2 + k);
+    }
   __syncthreads();
   uint32_t par = 0u;
   const int fc = blockIdx.y, f = fc / fr.c, ch = fc % fr.c;
@@ -885,9 +891,9 @@ k_row_pass_ir(RowPassArgs a, const cf* tw_w) {
 #pragma unroll
         for (int n2 = 0; n2 < N2; ++n2) x1[n2] = z[N1 * n2];
         reg_dft<false, N2>(x1);
-        const cf* tw = a.tw2 + n1;                    // w_N^(n1 k2) at [k2][n1]: lanes read in a row
+        const cf* tw = tw2s + n1;                     // w_N^(n1 k2) at [k2][n1]: lanes read in a row
 #pragma unroll
-        for (int k2 = 1; k2 < N2; ++k2) x1[reg_pos<N2>(k2)] = x1[reg_pos<N2>(k2)] * ldg_cpx(tw + N1 * k2);
+        for (int k2 = 1; k2 < N2; ++k2) x1[reg_pos<N2>(k2)] = x1[reg_pos<N2>(k2)] * tw[N1 * k2];
       }
       __syncthreads();
       if (t1) {
