@@ -189,9 +189,9 @@ cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
   if (p.learned) {
     // learned path: the network's proposal, written where the estimate goes
     begin(CBP_STAGE_PROPOSAL);
-    cnn_forward(d1, d2, p.n, cnn_w, wsp + p.off_cnn, st);
+    cnn_forward(d1, d2, p.n, cnn_w, wsp + p.off_cnn, st, nullptr, (int*)(wsp + p.off_err));
     cnn_to_kd(wsp + p.off_cnn, p.n, (double*)(wsp + p.off_kd), st);
-    end(CBP_STAGE_PROPOSAL, 7);
+    end(CBP_STAGE_PROPOSAL, 8);
   }
   if (fft) {
     if (!tw_ready) {

@@ -5,11 +5,12 @@
 //   conv 3x3 s2 p1 (2 -> 32) + ReLU, conv 3x3 s2 p1 (32 -> 32) + ReLU,
 //   conv 3x3 s4 p1 (32 -> 32) + ReLU, conv 2x2 s1 p0 (32 -> 2),
 //   softmax over each output channel's 15 x 15 logits -> K1, K2.
-// Activations are stored as bfloat16, weights are float32 master copies,
-// every product is accumulated in float32.  The whole network is ~50 M
-// multiply-adds per pair, a few percent of the pair's deconvolution work, so
-// these are direct convolutions on the FP32 units (thread per output, the
-// layer's weights in shared memory); weight gradients reduce in a fixed order
+// Activations are stored as bfloat16 and weights kept as float32 master
+// copies.  The forward convolutions run on the tensor cores (tcgen05, BF16
+// operands with the weights rounded to BF16, FP32 accumulation in tensor
+// memory) as implicit GEMMs over 128 output positions per CTA; the backward
+// pass (training only) stays on the FP32 units with the float32 weights, a
+// thread per output and weight gradients reduced in a fixed order
 // (deterministic).  Training minimises the mean squared error of both
 // kernels with AdamW (decoupled weight decay).
 #include <cuda_bf16.h>
@@ -19,6 +20,7 @@
 #include "cbp_common.cuh"
 #include "cbp_internal.h"
 #include "cbp_serve.h"
+#include "cbp_tc.cuh"
 
 namespace cbp {
 
@@ -42,9 +44,34 @@ __host__ __device__ inline Layer cnn_layer(int i) {
 constexpr int kCnnThreads = 256;
 constexpr int kT2 = kCnnT * kCnnT;
 
+constexpr int kTcThreads = 256;
+constexpr int kTcM = 128;
+constexpr uint32_t kTcCols = 32;   // tensor-memory columns per CTA (>= N, a power of two >= 32)
+template <int CIN, int KS, int N>
+struct ConvTc {
+  static constexpr int kK = KS * KS * CIN;
+  static constexpr int kKpad = (kK + 15) / 16 * 16;
+  static constexpr int kGroups = kKpad / 8;                 // K-groups of 8
+  static constexpr uint32_t kAGroup = kTcM * 16;            // bytes per K-group of A
+  static constexpr uint32_t kBGroup = N * 16;               // bytes per K-group of B
+  static constexpr int kBBytes = kKpad * N * 2;
+  static constexpr int kABytes = kKpad * kTcM * 2;
+  static constexpr int kSmem = kBBytes + kABytes;
+};
+// The four layers' shapes: (CIN, KS, N).
+using Tc0 = ConvTc<2, 3, 32>;
+using Tc1 = ConvTc<32, 3, 32>;
+using Tc2 = ConvTc<32, 3, 32>;
+using Tc3 = ConvTc<32, 2, 16>;
+// Byte offsets of the layers' B images in the weight-image buffer.
+__host__ __device__ constexpr int tc_img_offset(int li) {
+  return (li > 0 ? Tc0::kBBytes : 0) + (li > 1 ? Tc1::kBBytes : 0) + (li > 2 ? Tc2::kBBytes : 0) +
+         (li > 3 ? Tc3::kBBytes : 0);
+}
+
 // Workspace layout (byte offsets) for n pairs.
 struct CnnWs {
-  size_t x0, a1, a2, a3, z4, k, dz4, dz3, dz2, dz1, grad, lossp, total;
+  size_t x0, a1, a2, a3, z4, k, wimg, dz4, dz3, dz2, dz1, grad, lossp, total;
 };
 size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 CnnWs cnn_ws_layout(int n, bool train) {
@@ -62,6 +89,7 @@ CnnWs cnn_ws_layout(int n, bool train) {
   L.a3 = take(N * 32 * (kCnnSide / 16) * (kCnnSide / 16) * sizeof(bf16));
   L.z4 = take(N * 2 * kT2 * 4);
   L.k = take(N * 2 * kT2 * 4);
+  L.wimg = take(tc_img_offset(4));
   if (train) {
     L.dz4 = take(N * 2 * kT2 * 4);
     L.dz3 = take(N * 32 * (kCnnSide / 16) * (kCnnSide / 16) * 4);
@@ -188,107 +216,160 @@ template <typename TO> __device__ __forceinline__ TO to_out(float v);
 template <> __device__ __forceinline__ bf16 to_out<bf16>(float v) { return __float2bfloat16(v); }
 template <> __device__ __forceinline__ float to_out<float>(float v) { return v; }
 
-// y[n][co][oy][ox] = b[co] + sum_{ci,u,v} w[co][ci][u][v] x[n][ci][oy s - p + u][ox s - p + v]
-template <typename TO>
-__global__ void __launch_bounds__(kCnnThreads) k_conv_fwd(const bf16* x, const float* prm, TO* y, Layer L) {
-  extern __shared__ float ws[];
-  const int co = blockIdx.y, n = blockIdx.z;
-  const int kk = L.k * L.k, per = L.cin * kk;
-  for (int i = threadIdx.x; i < per; i += blockDim.x) ws[i] = prm[L.woff + co * per + i];
-  __syncthreads();
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= L.hout * L.hout) return;
-  const int oy = o / L.hout, ox = o % L.hout;
-  float acc = prm[L.boff + co];
-  for (int ci = 0; ci < L.cin; ++ci) {
-    const bf16* xc = x + ((int64_t)n * L.cin + ci) * L.hin * L.hin;
-    for (int u = 0; u < L.k; ++u) {
-      const int iy = oy * L.s - L.p + u;
-      if (iy < 0 || iy >= L.hin) continue;
-      for (int v = 0; v < L.k; ++v) {
-        const int ix = ox * L.s - L.p + v;
-        if (ix < 0 || ix >= L.hin) continue;
-        acc = fmaf(ws[ci * kk + u * L.k + v], __bfloat162float(xc[iy * L.hin + ix]), acc);
-      }
+// Convolutions on the tensor cores (tcgen05), as implicit GEMMs:
+//   y[n][co][o] = b[co] + sum_k A[o][k] B[co][k],
+// o an output position, k = (u KS + v) CIN + ci a tap and an input channel,
+// A[o][k] = x[n][ci][oy s - p + u][ox s - p + v] (zero outside x) and
+// B[co][k] = w[co][ci][u][v] rounded to BF16.  A CTA takes 128 consecutive
+// output positions (tcgen05's M) and all output channels (N = 32; 16 for the
+// two-channel head, its rows 2..15 zero): its eight warps gather A from the
+// BF16 activations into shared memory, one thread issues the K / 16 MMAs into
+// an FP32 accumulator in tensor memory, and each warp reads back 16 channels
+// of 32 positions for the epilogue (bias, ReLU, store).  K is padded with
+// zeros to a multiple of 16.
+constexpr int kTcWaitLimit = 1 << 20;
+
+// B images of all four layers (BF16, the shared-memory layout of
+// cbp_tc.cuh), one layer per blockIdx.y; rows co >= cout and columns
+// k >= KS^2 CIN are zero.
+template <int CIN, int KS, int N>
+__device__ void conv_w_image(const float* prm, const Layer& L, uint8_t* img) {
+  using C = ConvTc<CIN, KS, N>;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N * C::kKpad; i += gridDim.x * blockDim.x) {
+    const int co = i / C::kKpad, k = i - co * C::kKpad;
+    float w = 0.f;
+    if (co < L.cout && k < C::kK) {
+      const int tap = k / CIN, ci = k - tap * CIN;
+      w = prm[L.woff + (co * CIN + ci) * KS * KS + tap];
     }
+    *(bf16*)(img + tc::kmajor_offset(N, co, k)) = __float2bfloat16(w);
   }
-  if (L.relu) acc = fmaxf(acc, 0.f);
-  y[(((int64_t)n * L.cout + co) * L.hout + oy) * L.hout + ox] = to_out<TO>(acc);
+}
+__global__ void k_conv_w_images(const float* prm, uint8_t* img) {
+  switch (blockIdx.y) {
+    case 0: conv_w_image<2, 3, 32>(prm, cnn_layer(0), img + tc_img_offset(0)); break;
+    case 1: conv_w_image<32, 3, 32>(prm, cnn_layer(1), img + tc_img_offset(1)); break;
+    case 2: conv_w_image<32, 3, 32>(prm, cnn_layer(2), img + tc_img_offset(2)); break;
+    default: conv_w_image<32, 2, 16>(prm, cnn_layer(3), img + tc_img_offset(3)); break;
+  }
 }
 
-// The same convolution for 32 output channels, all computed by each thread for
-// kConvPos output positions: an input value is read once per position and
-// serves 32 channels, a weight (shared memory, [ci][u][v][co] so that the 32
-// channels of one tap are one broadcast row) serves kConvPos positions.
-constexpr int kConvPos = 2;
-constexpr int kConvCo = 32;
-template <typename TO>
-__global__ void __launch_bounds__(kCnnThreads) k_conv_fwd32(const bf16* x, const float* prm, TO* y,
-                                                            Layer L) {
-  extern __shared__ float ws[];   // [cin * k * k][32]
-  const int n = blockIdx.z;
-  const int kk = L.k * L.k, per = L.cin * kk;
-  for (int i = threadIdx.x; i < per * kConvCo; i += blockDim.x) {
-    const int co = i / per, t = i - co * per;     // parameter order [co][ci][u][v]
-    ws[t * kConvCo + co] = prm[L.woff + i];
-  }
-  __syncthreads();
-  const int npos = L.hout * L.hout;
-  const int o0 = (blockIdx.x * blockDim.x + threadIdx.x) * kConvPos;
-  if (o0 >= npos) return;
-  int oy[kConvPos], ox[kConvPos];
-  bool ok[kConvPos];
+template <int CIN, int KS, int N, typename TO>
+__global__ void __launch_bounds__(kTcThreads) k_conv_tc(const bf16* __restrict__ x,
+                                                         const uint8_t* __restrict__ wimg,
+                                                         const float* __restrict__ prm, TO* __restrict__ y,
+                                                         Layer L, int* err) {
+  using C = ConvTc<CIN, KS, N>;
+  extern __shared__ __align__(128) uint8_t tsm[];
+  __shared__ uint64_t done;
+  __shared__ uint32_t tslot;
+  uint8_t* sB = tsm;
+  uint8_t* sA = tsm + C::kBBytes;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n = blockIdx.y, npos = L.hout * L.hout, m0 = blockIdx.x * kTcM;
+
+  if (warp == 0) tc::tmem_alloc(&tslot, kTcCols);
+  if (tid == 0) tc::bar_init(&done, 1);
+  for (int i = tid; i < C::kBBytes / 16; i += kTcThreads)
+    ((uint4*)sB)[i] = __ldg((const uint4*)wimg + i);
+  // A: thread-chunk (m, g) holds k = 8g .. 8g + 7 of position m0 + m; the
+  // warp's 32 chunks are 32 consecutive positions, stored as 512 contiguous bytes
+  const unsigned short* xs = reinterpret_cast<const unsigned short*>(x) + (int64_t)n * CIN * L.hin * L.hin;
+  const int64_t plane = (int64_t)L.hin * L.hin;
+#pragma unroll 2
+  for (int c = tid; c < kTcM * C::kGroups; c += kTcThreads) {
+    const int m = c & (kTcM - 1), g = c / kTcM;
+    const int o = m0 + m;
+    uint32_t q[4] = {0u, 0u, 0u, 0u};
+    if (o < npos) {
+      const int oy = o / L.hout, ox = o - oy * L.hout;
+      const int iy0 = oy * L.s - L.p, ix0 = ox * L.s - L.p;
+      if constexpr (CIN % 8 == 0) {   // the group is 8 channels of one tap
+        const int tap = g / (CIN / 8), ci0 = (g - tap * (CIN / 8)) * 8;
+        const int u = tap / KS, v = tap - u * KS;
+        const int iy = iy0 + u, ix = ix0 + v;
+        if (tap < KS * KS && iy >= 0 && iy < L.hin && ix >= 0 && ix < L.hin) {
+          const unsigned short* px = xs + ci0 * plane + (int64_t)iy * L.hin + ix;
 #pragma unroll
-  for (int q = 0; q < kConvPos; ++q) {
-    ok[q] = o0 + q < npos;
-    const int o = ok[q] ? o0 + q : o0;
-    oy[q] = o / L.hout;
-    ox[q] = o % L.hout;
-  }
-  float acc[kConvPos][kConvCo];
-#pragma unroll
-  for (int c = 0; c < kConvCo; ++c) {
-    const float b = prm[L.boff + c];
-#pragma unroll
-    for (int q = 0; q < kConvPos; ++q) acc[q][c] = b;
-  }
-  for (int ci = 0; ci < L.cin; ++ci) {
-    const bf16* xc = x + ((int64_t)n * L.cin + ci) * L.hin * L.hin;
-    for (int u = 0; u < L.k; ++u) {
-      for (int v = 0; v < L.k; ++v) {
-        float xv[kConvPos];
-#pragma unroll
-        for (int q = 0; q < kConvPos; ++q) {
-          const int iy = oy[q] * L.s - L.p + u, ix = ox[q] * L.s - L.p + v;
-          xv[q] = (iy >= 0 && iy < L.hin && ix >= 0 && ix < L.hin)
-                      ? __bfloat162float(xc[iy * L.hin + ix])
-                      : 0.f;
+          for (int e = 0; e < 8; ++e) q[e >> 1] |= (uint32_t)__ldg(px + e * plane) << (16 * (e & 1));
         }
-        const float4* wr = reinterpret_cast<const float4*>(ws + ((ci * L.k + u) * L.k + v) * kConvCo);
+      } else {
 #pragma unroll
-        for (int c4 = 0; c4 < kConvCo / 4; ++c4) {
-          const float4 w = wr[c4];
+        for (int e = 0; e < 8; ++e) {
+          const int k = g * 8 + e;
+          const int tap = k / CIN, ci = k - tap * CIN;
+          const int u = tap / KS, v = tap - u * KS;
+          const int iy = iy0 + u, ix = ix0 + v;
+          if (tap < KS * KS && iy >= 0 && iy < L.hin && ix >= 0 && ix < L.hin)
+            q[e >> 1] |= (uint32_t)__ldg(xs + ci * plane + (int64_t)iy * L.hin + ix) << (16 * (e & 1));
+        }
+      }
+    }
+    *(uint4*)(sA + tc::kmajor_offset(kTcM, m, 8 * g)) = make_uint4(q[0], q[1], q[2], q[3]);
+  }
+  tc::fence_smem_to_async();
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tslot;
+  if (tid == 0) {
+    const uint32_t a0 = tc::saddr(sA), b0 = tc::saddr(sB);
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(kTcM, N);
+#pragma unroll 1
+    for (int s = 0; s < C::kKpad / 16; ++s)
+      tc::mma_bf16(tmem, tc::sdesc(a0 + 2 * s * C::kAGroup, C::kAGroup, 128),
+                   tc::sdesc(b0 + 2 * s * C::kBGroup, C::kBGroup, 128), idesc, s > 0);
+    tc::mma_commit(&done);
+  }
+  const bool arrived = tc::bar_wait(&done, 0, kTcWaitLimit);
+  const bool late = __syncthreads_or(!arrived);
+  if (late) {
+    // the MMAs did not complete in time: report it, wait once more (bounded)
+    // and leave NaN outputs behind
+    if (tid == 0 && err) atomicOr(err, 1);
+    if (!arrived) tc::bar_wait(&done, 0, kTcWaitLimit);
+  }
+  tc::fence_after_sync();
+  const int quarter = warp & 3, half = warp >> 2;
+  if (half * 16 < N) {
+    float v[16];
+    if (!late) {
+      tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + half * 16, v);
+    } else {
 #pragma unroll
-          for (int q = 0; q < kConvPos; ++q) {
-            acc[q][4 * c4 + 0] = fmaf(w.x, xv[q], acc[q][4 * c4 + 0]);
-            acc[q][4 * c4 + 1] = fmaf(w.y, xv[q], acc[q][4 * c4 + 1]);
-            acc[q][4 * c4 + 2] = fmaf(w.z, xv[q], acc[q][4 * c4 + 2]);
-            acc[q][4 * c4 + 3] = fmaf(w.w, xv[q], acc[q][4 * c4 + 3]);
-          }
+      for (int j = 0; j < 16; ++j) v[j] = __int_as_float(0x7fc00000);
+    }
+    const int o = m0 + quarter * 32 + lane;
+    if (o < npos) {
+      TO* yo = y + (int64_t)n * L.cout * npos + o;
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const int co = half * 16 + j;
+        if (co < L.cout) {
+          float a = v[j] + __ldg(prm + L.boff + co);
+          if (L.relu) a = fmaxf(a, 0.f);
+          yo[(int64_t)co * npos] = to_out<TO>(a);
         }
       }
     }
   }
-#pragma unroll
-  for (int q = 0; q < kConvPos; ++q) {
-    if (!ok[q]) continue;
-#pragma unroll
-    for (int c = 0; c < kConvCo; ++c) {
-      float a = acc[q][c];
-      if (L.relu) a = fmaxf(a, 0.f);
-      y[(((int64_t)n * L.cout + c) * L.hout + oy[q]) * L.hout + ox[q]] = to_out<TO>(a);
-    }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_free(tmem, kTcCols);
   }
+}
+
+template <int CIN, int KS, int N, typename TO>
+void run_conv_tc(const bf16* x, const uint8_t* img, const float* prm, TO* y, int li, int n, int* err,
+                 cudaStream_t st) {
+  using C = ConvTc<CIN, KS, N>;
+  const Layer L = cnn_layer(li);
+  const int npos = L.hout * L.hout;
+  auto kfn = k_conv_tc<CIN, KS, N, TO>;
+  cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+  kfn<<<dim3((npos + kTcM - 1) / kTcM, n), kTcThreads, C::kSmem, st>>>(x, img + tc_img_offset(li), prm, y, L, err);
 }
 
 // Softmax of each (pair, head) over its 225 logits; with targets, the loss
@@ -445,20 +526,16 @@ __global__ void k_cnn_to_kd(const float* K, int n, double* kd) {
   kd[i] = (double)K[i];
 }
 
-void launch_conv_fwd(const bf16* x, const float* prm, void* y, int li, int n, cudaStream_t st) {
-  const Layer L = cnn_layer(li);
-  if (L.cout == kConvCo) {   // 32 output channels per thread
-    const int per_block = kCnnThreads * kConvPos;
-    dim3 g((L.hout * L.hout + per_block - 1) / per_block, 1, n);
-    const size_t sm = sizeof(float) * L.cin * L.k * L.k * kConvCo;
-    cudaFuncSetAttribute(k_conv_fwd32<bf16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_conv_fwd32<bf16><<<g, kCnnThreads, sm, st>>>(x, prm, (bf16*)y, L);
-    return;
+// Layer li of the network on the tensor cores; wimg holds the B images
+// written by k_conv_w_images for the same parameters.
+void launch_conv_fwd(const bf16* x, const uint8_t* wimg, const float* prm, void* y, int li, int n,
+                     int* err, cudaStream_t st) {
+  switch (li) {
+    case 0: run_conv_tc<2, 3, 32, bf16>(x, wimg, prm, (bf16*)y, 0, n, err, st); break;
+    case 1: run_conv_tc<32, 3, 32, bf16>(x, wimg, prm, (bf16*)y, 1, n, err, st); break;
+    case 2: run_conv_tc<32, 3, 32, bf16>(x, wimg, prm, (bf16*)y, 2, n, err, st); break;
+    default: run_conv_tc<32, 2, 16, float>(x, wimg, prm, (float*)y, 3, n, err, st); break;
   }
-  dim3 g((L.hout * L.hout + kCnnThreads - 1) / kCnnThreads, L.cout, n);
-  const size_t sm = sizeof(float) * L.cin * L.k * L.k;
-  if (li == 3) k_conv_fwd<float><<<g, kCnnThreads, sm, st>>>(x, prm, (float*)y, L);
-  else k_conv_fwd<bf16><<<g, kCnnThreads, sm, st>>>(x, prm, (bf16*)y, L);
 }
 
 void copy_f32(const bf16* a, float* b, int64_t n, cudaStream_t st) {
@@ -470,7 +547,7 @@ void copy_f32(const bf16* a, float* b, int64_t n, cudaStream_t st) {
 size_t cnn_workspace(int n, bool train) { return cnn_ws_layout(n, train).total; }
 
 void cnn_forward(const FrameDesc& b1, const FrameDesc& b2, int n, const float* prm, char* ws,
-                 cudaStream_t st, const cbp_cnn_trace* tr) {
+                 cudaStream_t st, const cbp_cnn_trace* tr, int* err) {
   const CnnWs L = cnn_ws_layout(n, false);
   bf16* x0 = (bf16*)(ws + L.x0);
   bf16* a[3] = {(bf16*)(ws + L.a1), (bf16*)(ws + L.a2), (bf16*)(ws + L.a3)};
@@ -478,10 +555,12 @@ void cnn_forward(const FrameDesc& b1, const FrameDesc& b2, int n, const float* p
     k_cnn_input_rows<<<dim3(kCnnSide, 2, n), kCnnThreads, 0, st>>>(b1, b2, x0);
   else
     k_cnn_input<<<dim3(kCnnSide * kCnnSide / kCnnThreads, 2, n), kCnnThreads, 0, st>>>(b1, b2, x0);
-  launch_conv_fwd(x0, prm, a[0], 0, n, st);
-  launch_conv_fwd(a[0], prm, a[1], 1, n, st);
-  launch_conv_fwd(a[1], prm, a[2], 2, n, st);
-  launch_conv_fwd(a[2], prm, ws + L.z4, 3, n, st);
+  uint8_t* wimg = (uint8_t*)(ws + L.wimg);
+  k_conv_w_images<<<dim3(8, 4), 256, 0, st>>>(prm, wimg);
+  launch_conv_fwd(x0, wimg, prm, a[0], 0, n, err, st);
+  launch_conv_fwd(a[0], wimg, prm, a[1], 1, n, err, st);
+  launch_conv_fwd(a[1], wimg, prm, a[2], 2, n, err, st);
+  launch_conv_fwd(a[2], wimg, prm, ws + L.z4, 3, n, err, st);
   k_softmax<<<(n * 2 * 32 + 127) / 128, 128, 0, st>>>((const float*)(ws + L.z4), (float*)(ws + L.k),
                                                       nullptr, nullptr, nullptr, n);
   if (tr) {

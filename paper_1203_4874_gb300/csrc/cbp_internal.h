@@ -166,7 +166,7 @@ void launch_residual_gate(const Plan& p, char* ws, cudaStream_t st);
 // learned proposal (cbp_cnn.cu)
 size_t cnn_workspace(int n, bool train);
 void cnn_forward(const FrameDesc& b1, const FrameDesc& b2, int n, const float* prm, char* ws,
-                 cudaStream_t st, const cbp_cnn_trace* tr = nullptr);
+                 cudaStream_t st, const cbp_cnn_trace* tr = nullptr, int* err = nullptr);
 const float* cnn_kernels(char* ws, int n);
 void cnn_to_kd(char* ws, int n, double* kd, cudaStream_t st);
 void cnn_train_step(const FrameDesc& b1, const FrameDesc& b2, int n, const float* kt, float* prm,

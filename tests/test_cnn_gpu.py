@@ -1,7 +1,11 @@
-"""Learned proposal kernels (BF16 activations, FP32 weights) against the FP64
-oracle: each layer from the GPU's own previous activation (only that layer's
-rounding differs), the whole forward pass, the loss gradient through the
-oracle's backward pass, the AdamW update, and determinism."""
+"""Learned proposal kernels against the FP64 oracle.  The forward
+convolutions run on the tensor cores with BF16 activations and the weights
+rounded to BF16 (FP32 accumulation); the oracle takes the same rounded
+weights (round to nearest even, by the CPU library's conversion), so each
+layer computed from the GPU's own previous activation differs from it only
+by that layer's accumulation order and output rounding.  Also: the whole
+forward pass, the loss gradient through the oracle's backward pass (FP32
+weights), the AdamW update, and determinism."""
 from __future__ import annotations
 
 import numpy as np
@@ -16,6 +20,13 @@ pytestmark = pytest.mark.gpu
 
 def _flat(params):
     return np.concatenate([np.concatenate([w.ravel(), b.ravel()]) for w, b in params])
+
+
+def _bf16(params):
+    """The weights as the tensor-core products see them: each float32 weight
+    rounded to BF16 (biases stay float32)."""
+    return [[torch.tensor(w, dtype=torch.float32).to(torch.bfloat16).double().numpy(), b.copy()]
+            for w, b in params]
 
 
 def _unflat(vec):
@@ -53,7 +64,7 @@ def test_layers_against_oracle(gpu_ctx, case):
     tr = cbp.cnn_trace_buffers(2, case["t1"].device)
     K = cbp.cbp_cnn_forward(gpu_ctx, case["t1"], case["t2"], case["w"], trace=tr)
     torch.cuda.synchronize()
-    P = case["params"]
+    P = _bf16(case["params"])
     for f in range(2):
         # network input: area-downsampled luma; bfloat16 storage (8 bits of mantissa)
         x_ref = cn.network_input(case["b1"][f], case["b2"][f], 256)
@@ -76,7 +87,8 @@ def test_layers_against_oracle(gpu_ctx, case):
         for c in range(2):
             want = cn.softmax(z[c].ravel()).reshape(15, 15)
             np.testing.assert_allclose(K[f, c].double().cpu().numpy(), want, rtol=1e-5, atol=1e-8)
-        # whole forward pass in FP64: BF16 storage of activations only
+        # whole forward pass in FP64 with the rounded weights: the GPU differs by
+        # its BF16 storage of activations
         K_ref, _ = cn.forward(P, x_ref)
         err = np.linalg.norm(K[f].double().cpu().numpy() - K_ref) / np.linalg.norm(K_ref)
         assert err < 2e-2, err
