@@ -16,6 +16,7 @@
 #include <cuda_bf16.h>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <vector>
 #include "cbp_common.cuh"
 #include "cbp_internal.h"
@@ -69,9 +70,43 @@ __host__ __device__ constexpr int tc_img_offset(int li) {
          (li > 3 ? Tc3::kBBytes : 0);
 }
 
+// Shapes of the input-gradient products (transposed weights, N = CIN).
+template <int CIN, int KS, int COUT>
+struct ConvTcT {
+  static constexpr int kK = KS * KS * COUT;
+  static constexpr int kKpad = (kK + 15) / 16 * 16;
+  static constexpr int kGroups = kKpad / 8;
+  static constexpr uint32_t kAGroup = kTcM * 16;
+  static constexpr uint32_t kBGroup = CIN * 16;
+  static constexpr int kBBytes = kKpad * CIN * 2;
+  static constexpr int kABytes = kKpad * kTcM * 2;
+  static constexpr int kSmem = kBBytes + kABytes;
+};
+using TcT1 = ConvTcT<32, 3, 32>;
+using TcT3 = ConvTcT<32, 2, 2>;
+// byte offsets of layers 1..3's transposed images
+__host__ __device__ constexpr int tct_img_offset(int li) {
+  return (li > 1 ? TcT1::kBBytes : 0) + (li > 2 ? TcT1::kBBytes : 0) + (li > 3 ? TcT3::kBBytes : 0);
+}
+constexpr int kTcWPos = 64;      // positions per step: four MMAs of K = 16
+constexpr int kTcWChunk = 1024;  // positions per CTA
+__host__ __device__ constexpr int tc_mtiles(int kw) { return (kw + kTcM - 1) / kTcM; }
+int64_t tc_wchunks(int n, const Layer& L) {
+  return ((int64_t)n * L.hout * L.hout + kTcWChunk - 1) / kTcWChunk;
+}
+// Floats of the partial-gradient buffer for n pairs (the largest layer's).
+size_t tc_wpart_floats(int n) {
+  size_t m = 0;
+  const int kw[4] = {18, 288, 288, 128}, nn[4] = {32, 32, 32, 16};
+  for (int li = 0; li < 4; ++li)
+    m = std::max(m, (size_t)tc_wchunks(n, cnn_layer(li)) * (tc_mtiles(kw[li]) * kTcM + 1) * nn[li]);
+  return m;
+}
+
+
 // Workspace layout (byte offsets) for n pairs.
 struct CnnWs {
-  size_t x0, a1, a2, a3, z4, k, wimg, dz4, dz3, dz2, dz1, grad, lossp, total;
+  size_t x0, a1, a2, a3, z4, k, wimg, dz4, dz3, dz2, dz1, grad, lossp, wtimg, wpart, total;
 };
 size_t al(size_t x) { return (x + 255) & ~size_t(255); }
 CnnWs cnn_ws_layout(int n, bool train) {
@@ -97,6 +132,8 @@ CnnWs cnn_ws_layout(int n, bool train) {
     L.dz1 = take(N * 32 * (kCnnSide / 2) * (kCnnSide / 2) * 4);
     L.grad = take((size_t)kCnnParams * 4);
     L.lossp = take(N * 2 * 4);
+    L.wtimg = take(tct_img_offset(4));
+    L.wpart = take(tc_wpart_floats(n) * 4);
   }
   L.total = o;
   return L;
@@ -412,89 +449,334 @@ __global__ void k_loss_sum(const float* lossp, int m, float denom, float* out) {
   }
 }
 
-// dx[n][ci][iy][ix] = sum_{co,u,v: iy = oy s - p + u, ix = ox s - p + v} w[co][ci][u][v] dy[n][co][oy][ox],
-// times the ReLU mask of the layer input (x > 0): the gradient of the
-// previous layer's pre-activation.
-__global__ void __launch_bounds__(kCnnThreads)
-k_conv_bwd_data(const float* dy, const float* prm, const bf16* xact, float* dx, Layer L) {
-  extern __shared__ float ws[];
-  const int ci = blockIdx.y, n = blockIdx.z;
-  const int kk = L.k * L.k;
-  for (int i = threadIdx.x; i < L.cout * kk; i += blockDim.x) {
-    const int co = i / kk, uv = i % kk;
-    ws[i] = prm[L.woff + (co * L.cin + ci) * kk + uv];
-  }
-  __syncthreads();
-  const int o = blockIdx.x * blockDim.x + threadIdx.x;
-  if (o >= L.hin * L.hin) return;
-  const int iy = o / L.hin, ix = o % L.hin;
-  const int64_t xi = ((int64_t)n * L.cin + ci) * L.hin * L.hin + o;
-  if (!(__bfloat162float(xact[xi]) > 0.f)) {
-    dx[xi] = 0.f;
-    return;
-  }
-  float acc = 0.f;
-  for (int u = 0; u < L.k; ++u) {
-    const int ty = iy + L.p - u;
-    if (ty < 0 || ty % L.s) continue;
-    const int oy = ty / L.s;
-    if (oy >= L.hout) continue;
-    for (int v = 0; v < L.k; ++v) {
-      const int tx = ix + L.p - v;
-      if (tx < 0 || tx % L.s) continue;
-      const int ox = tx / L.s;
-      if (ox >= L.hout) continue;
-      for (int co = 0; co < L.cout; ++co)
-        acc = fmaf(ws[co * kk + u * L.k + v],
-                   dy[(((int64_t)n * L.cout + co) * L.hout + oy) * L.hout + ox], acc);
-    }
-  }
-  dx[xi] = acc;
+__device__ __forceinline__ uint32_t bf16_bits(float v) {
+  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16(v));
 }
 
-// Weight and bias gradients of one (co, ci) pair: sum over pairs and output
-// positions, block-wide tree reduction in a fixed order.
-__global__ void __launch_bounds__(kCnnThreads)
-k_conv_bwd_w(const float* dy, const bf16* x, float* grad, Layer L, int n) {
-  __shared__ float red[10][kCnnThreads];
-  const int ci = blockIdx.x, co = blockIdx.y;
-  const int kk = L.k * L.k, hw = L.hout * L.hout;
-  float acc[10];
+// Input gradients on the tensor cores, an implicit GEMM over the layer's
+// input positions i (128 per CTA):
+//   dx[n][ci][i] = [x[n][ci][i] > 0] sum_k G[i][k] W^T[ci][k],
+// k = (u KS + v) COUT + co, G[i][k] = dy[n][co][oy][ox] where iy + p - u = oy s
+// and ix + p - v = ox s land on an output position (zero elsewhere: the
+// strided transpose of the forward product), rounded to BF16, and
+// W^T[ci][k] = w[co][ci][u][v] in BF16 (k_conv_wt_images).  The mask (the
+// ReLU of the layer's input) turns it into the previous layer's
+// pre-activation gradient.
+template <int CIN, int KS, int COUT>
+__device__ void conv_wt_image(const float* prm, const Layer& L, uint8_t* img) {
+  using C = ConvTcT<CIN, KS, COUT>;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < CIN * C::kKpad; i += gridDim.x * blockDim.x) {
+    const int ci = i / C::kKpad, k = i - ci * C::kKpad;
+    float w = 0.f;
+    if (k < C::kK) {
+      const int tap = k / COUT, co = k - tap * COUT;
+      w = prm[L.woff + (co * CIN + ci) * KS * KS + tap];
+    }
+    *(bf16*)(img + tc::kmajor_offset(CIN, ci, k)) = __float2bfloat16(w);
+  }
+}
+__global__ void k_conv_wt_images(const float* prm, uint8_t* img) {
+  switch (blockIdx.y) {
+    case 0: conv_wt_image<32, 3, 32>(prm, cnn_layer(1), img + tct_img_offset(1)); break;
+    case 1: conv_wt_image<32, 3, 32>(prm, cnn_layer(2), img + tct_img_offset(2)); break;
+    default: conv_wt_image<32, 2, 2>(prm, cnn_layer(3), img + tct_img_offset(3)); break;
+  }
+}
+
+template <int CIN, int KS, int COUT>
+__global__ void __launch_bounds__(kTcThreads) k_conv_bwd_data_tc(const float* __restrict__ dy,
+                                                                  const uint8_t* __restrict__ wtimg,
+                                                                  const bf16* __restrict__ xact,
+                                                                  float* __restrict__ dx, Layer L, int* err) {
+  using C = ConvTcT<CIN, KS, COUT>;
+  extern __shared__ __align__(128) uint8_t tsm[];
+  __shared__ uint64_t done;
+  __shared__ uint32_t tslot;
+  uint8_t* sB = tsm;
+  uint8_t* sA = tsm + C::kBBytes;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int n = blockIdx.y, nin = L.hin * L.hin, hw = L.hout * L.hout, m0 = blockIdx.x * kTcM;
+
+  if (warp == 0) tc::tmem_alloc(&tslot, kTcCols);
+  if (tid == 0) tc::bar_init(&done, 1);
+  for (int i = tid; i < C::kBBytes / 16; i += kTcThreads)
+    ((uint4*)sB)[i] = __ldg((const uint4*)wtimg + i);
+  const float* dyn = dy + (int64_t)n * COUT * hw;
+#pragma unroll 2
+  for (int c = tid; c < kTcM * C::kGroups; c += kTcThreads) {
+    const int m = c & (kTcM - 1), g = c / kTcM;
+    const int i = m0 + m;
+    uint32_t q[4] = {0u, 0u, 0u, 0u};
+    if (i < nin) {
+      const int iy = i / L.hin, ix = i - iy * L.hin;
+      if constexpr (COUT % 8 == 0) {   // the group is 8 channels of one tap
+        const int tap = g / (COUT / 8), co0 = (g - tap * (COUT / 8)) * 8;
+        const int u = tap / KS, v = tap - u * KS;
+        const int ty = iy + L.p - u, tx = ix + L.p - v;
+        if (tap < KS * KS && ty >= 0 && tx >= 0 && ty % L.s == 0 && tx % L.s == 0 &&
+            ty / L.s < L.hout && tx / L.s < L.hout) {
+          const float* pg = dyn + (int64_t)co0 * hw + (ty / L.s) * L.hout + tx / L.s;
 #pragma unroll
-  for (int j = 0; j < 10; ++j) acc[j] = 0.f;
-  for (int64_t q = threadIdx.x; q < (int64_t)n * hw; q += blockDim.x) {
-    const int nn = (int)(q / hw), o = (int)(q % hw);
-    const int oy = o / L.hout, ox = o % L.hout;
-    const float g = dy[((int64_t)nn * L.cout + co) * hw + o];
-    const bf16* xc = x + ((int64_t)nn * L.cin + ci) * L.hin * L.hin;
+          for (int e = 0; e < 8; ++e) q[e >> 1] |= bf16_bits(__ldg(pg + e * hw)) << (16 * (e & 1));
+        }
+      } else {
 #pragma unroll
-    for (int u = 0; u < 3; ++u) {
-      if (u >= L.k) break;
-      const int iy = oy * L.s - L.p + u;
-#pragma unroll
-      for (int v = 0; v < 3; ++v) {
-        if (v >= L.k) break;
-        const int ix = ox * L.s - L.p + v;
-        if (iy >= 0 && iy < L.hin && ix >= 0 && ix < L.hin)
-          acc[u * 3 + v] = fmaf(g, __bfloat162float(xc[iy * L.hin + ix]), acc[u * 3 + v]);
+        for (int e = 0; e < 8; ++e) {
+          const int k = g * 8 + e;
+          const int tap = k / COUT, co = k - tap * COUT;
+          const int u = tap / KS, v = tap - u * KS;
+          const int ty = iy + L.p - u, tx = ix + L.p - v;
+          if (tap < KS * KS && ty >= 0 && tx >= 0 && ty % L.s == 0 && tx % L.s == 0 &&
+              ty / L.s < L.hout && tx / L.s < L.hout)
+            q[e >> 1] |= bf16_bits(__ldg(dyn + (int64_t)co * hw + (ty / L.s) * L.hout + tx / L.s))
+                         << (16 * (e & 1));
+        }
       }
     }
-    acc[9] += g;
+    *(uint4*)(sA + tc::kmajor_offset(kTcM, m, 8 * g)) = make_uint4(q[0], q[1], q[2], q[3]);
   }
-#pragma unroll
-  for (int j = 0; j < 10; ++j) red[j][threadIdx.x] = acc[j];
+  tc::fence_smem_to_async();
+  tc::fence_before_sync();
   __syncthreads();
-  for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-    if (threadIdx.x < h)
+  tc::fence_after_sync();
+  const uint32_t tmem = tslot;
+  if (tid == 0) {
+    const uint32_t a0 = tc::saddr(sA), b0 = tc::saddr(sB);
+    constexpr uint32_t idesc = tc::idesc_bf16_f32(kTcM, CIN);
+#pragma unroll 1
+    for (int s = 0; s < C::kKpad / 16; ++s)
+      tc::mma_bf16(tmem, tc::sdesc(a0 + 2 * s * C::kAGroup, C::kAGroup, 128),
+                   tc::sdesc(b0 + 2 * s * C::kBGroup, C::kBGroup, 128), idesc, s > 0);
+    tc::mma_commit(&done);
+  }
+  const bool arrived = tc::bar_wait(&done, 0, kTcWaitLimit);
+  const bool late = __syncthreads_or(!arrived);
+  if (late) {
+    if (tid == 0 && err) atomicOr(err, 1);
+    if (!arrived) tc::bar_wait(&done, 0, kTcWaitLimit);
+  }
+  tc::fence_after_sync();
+  const int quarter = warp & 3, half = warp >> 2;
+  float v[16];
+  if (!late) {
+    tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + half * 16, v);
+  } else {
 #pragma unroll
-      for (int j = 0; j < 10; ++j) red[j][threadIdx.x] += red[j][threadIdx.x + h];
-    __syncthreads();
+    for (int j = 0; j < 16; ++j) v[j] = __int_as_float(0x7fc00000);
   }
-  if (threadIdx.x < kk) {
-    const int u = threadIdx.x / L.k, v = threadIdx.x % L.k;
-    grad[L.woff + (co * L.cin + ci) * kk + threadIdx.x] = red[u * 3 + v][0];
+  const int i = m0 + quarter * 32 + lane;
+  if (i < nin) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) {
+      const int64_t at = ((int64_t)n * CIN + half * 16 + j) * nin + i;
+      dx[at] = __bfloat162float(xact[at]) > 0.f ? v[j] : 0.f;
+    }
   }
-  if (ci == 0 && threadIdx.x == 0) grad[L.boff + co] = red[9][0];
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_free(tmem, kTcCols);
+  }
+  static_assert(CIN == 32, "one output channel per accumulator column, 16 per warp half");
+}
+
+// Weight gradients on the tensor cores, an implicit GEMM whose reduction runs
+// over the output positions o of all pairs:
+//   D[k][co] = sum_o X[k][o] dY[co][o],
+// k = (u KS + v) CIN + ci a weight's tap and input channel, X[k][o] = the layer
+// input x[n][ci][oy s - p + u][ox s - p + v] (zero outside), dY = dy rounded to
+// BF16.  A CTA takes 128 rows of k (M) and kTcWChunk positions, in steps of
+// kTcWPos positions through two shared-memory buffers: the MMAs of one step run
+// while the other buffer is filled, each buffer's MMAs completing on its own
+// mbarrier before it is refilled.  The bias gradients sum dy itself in FP32
+// (the CTAs of the first row tile, from the values they stage).  Each CTA
+// writes its partials; a second kernel sums them over the position chunks in
+// a fixed order (deterministic) into the gradient vector.
+template <int CIN, int KS, int N>
+__global__ void __launch_bounds__(kTcThreads) k_conv_bwd_w_tc(const float* __restrict__ dy,
+                                                               const bf16* __restrict__ x,
+                                                               float* __restrict__ part, Layer L,
+                                                               int npairs, int* err) {
+  constexpr int KW = KS * KS * CIN;
+  constexpr int kABytes = kTcM * kTcWPos * 2, kBBytes = N * kTcWPos * 2;
+  extern __shared__ __align__(128) uint8_t tsm[];
+  __shared__ uint64_t bars[2];
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int hw = L.hout * L.hout;
+  const int64_t P = (int64_t)npairs * hw;
+  const int kk0 = blockIdx.x * kTcM;
+  const int64_t pbeg = (int64_t)blockIdx.y * kTcWChunk, pend = min(P, pbeg + kTcWChunk);
+  const int steps = (int)((pend - pbeg + kTcWPos - 1) / kTcWPos);
+  const unsigned short* xs = reinterpret_cast<const unsigned short*>(x);
+
+  __shared__ float bred[8][N];
+  float bsum = 0.f;   // this thread's FP32 share of the bias gradient
+  if (warp == 0) tc::tmem_alloc(&tslot, kTcCols);
+  if (tid == 0) {
+    tc::bar_init(&bars[0], 1);
+    tc::bar_init(&bars[1], 1);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = tslot;
+  constexpr uint32_t idesc = tc::idesc_bf16_f32(kTcM, N);
+  bool ok = true, late = false;
+  int issued = 0;
+#pragma unroll 1
+  for (int t = 0; t < steps; ++t) {
+    const int b = t & 1;
+    uint8_t* sA = tsm + b * (kABytes + kBBytes);
+    uint8_t* sB = sA + kABytes;
+    // the MMAs of step t - 2 read this buffer
+    if (t >= 2) ok = tc::bar_wait(&bars[b], ((t - 2) >> 1) & 1, kTcWaitLimit) && ok;
+    const int64_t ob = pbeg + (int64_t)t * kTcWPos;
+    // X rows kk0 + r, positions ob + 8 g + e; a warp's lanes are 32 consecutive rows
+    for (int c = tid; c < kTcM * (kTcWPos / 8); c += kTcThreads) {
+      const int r = c & (kTcM - 1), g = c / kTcM, kk = kk0 + r;
+      uint32_t q[4] = {0u, 0u, 0u, 0u};
+      if (kk < KW) {
+        const int tap = kk / CIN, ci = kk - tap * CIN;
+        const int u = tap / KS, v = tap - u * KS;
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int64_t o = ob + 8 * g + e;
+          if (o >= pend) break;
+          const int pr = (int)(o / hw), loc = (int)(o - (int64_t)pr * hw);
+          const int oy = loc / L.hout, ox = loc - oy * L.hout;
+          const int iy = oy * L.s - L.p + u, ix = ox * L.s - L.p + v;
+          if (iy >= 0 && iy < L.hin && ix >= 0 && ix < L.hin)
+            q[e >> 1] |= (uint32_t)__ldg(xs + (((int64_t)pr * CIN + ci) * L.hin + iy) * L.hin + ix)
+                         << (16 * (e & 1));
+        }
+      }
+      *(uint4*)(sA + tc::kmajor_offset(kTcM, r, 8 * g)) = make_uint4(q[0], q[1], q[2], q[3]);
+    }
+    // dY rows co, the same positions
+    for (int c = tid; c < N * (kTcWPos / 8); c += kTcThreads) {
+      const int co = c % N, g = c / N;
+      uint32_t q[4] = {0u, 0u, 0u, 0u};
+      if (co < L.cout) {
+#pragma unroll
+        for (int e = 0; e < 8; ++e) {
+          const int64_t o = ob + 8 * g + e;
+          if (o >= pend) break;
+          const int pr = (int)(o / hw), loc = (int)(o - (int64_t)pr * hw);
+          const float d = __ldg(dy + ((int64_t)pr * L.cout + co) * hw + loc);
+          bsum += d;
+          q[e >> 1] |= bf16_bits(d) << (16 * (e & 1));
+        }
+      }
+      *(uint4*)(sB + tc::kmajor_offset(N, co, 8 * g)) = make_uint4(q[0], q[1], q[2], q[3]);
+    }
+    tc::fence_smem_to_async();
+    tc::fence_before_sync();
+    late = __syncthreads_or(!ok);
+    tc::fence_after_sync();
+    if (late) break;
+    if (tid == 0) {
+      const uint32_t a0 = tc::saddr(sA), b0 = tc::saddr(sB);
+#pragma unroll
+      for (int s = 0; s < kTcWPos / 16; ++s)
+        tc::mma_bf16(tmem, tc::sdesc(a0 + 2 * s * kTcM * 16, kTcM * 16, 128),
+                     tc::sdesc(b0 + 2 * s * N * 16, N * 16, 128), idesc, t > 0 || s > 0);
+      tc::mma_commit(&bars[b]);
+    }
+    ++issued;
+  }
+  // the bias partial of this chunk: the eight position groups in order
+  // (every thread c < 8 N staged one (co, g) in each step)
+  if (tid < 8 * N) bred[tid / N][tid % N] = bsum;
+  __syncthreads();
+  if (blockIdx.x == 0 && tid < N) {
+    float b = 0.f;
+#pragma unroll
+    for (int g = 0; g < 8; ++g) b += bred[g][tid];
+    part[(int64_t)gridDim.y * gridDim.x * kTcM * N + (int64_t)blockIdx.y * N + tid] = b;
+  }
+  // the last commit completes after every MMA issued before it
+  bool fin = true;
+  if (issued > 0) fin = tc::bar_wait(&bars[(issued - 1) & 1], ((issued - 1) >> 1) & 1, kTcWaitLimit);
+  const bool bad = __syncthreads_or(!fin) || late;
+  if (bad) {
+    // report, wait once more (bounded) for the MMAs in flight, leave NaN partials
+    if (tid == 0 && err) atomicOr(err, 1);
+    if (issued > 0 && !fin)
+      tc::bar_wait(&bars[(issued - 1) & 1], ((issued - 1) >> 1) & 1, kTcWaitLimit);
+  }
+  tc::fence_after_sync();
+  const int quarter = warp & 3, half = warp >> 2;
+  if (half * 16 < N) {
+    float v[16];
+    if (!bad) {
+      tc::tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + half * 16, v);
+    } else {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) v[j] = __int_as_float(0x7fc00000);
+    }
+    float4* o = (float4*)(part + (((int64_t)blockIdx.y * gridDim.x + blockIdx.x) * kTcM + quarter * 32 +
+                                  lane) * N + half * 16);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) {
+    tc::fence_after_sync();
+    tc::tmem_free(tmem, kTcCols);
+  }
+}
+
+// The gradient vector from the partials, summed over the position chunks in
+// order: weights [co][ci][u][v] from rows k < KS^2 CIN, then the biases.
+template <int CIN, int KS, int N>
+__global__ void k_conv_bwd_w_sum(const float* __restrict__ part, float* __restrict__ grad, Layer L,
+                                 int nchunks, int mtiles) {
+  constexpr int KW = KS * KS * CIN;
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (KW + 1) * L.cout) return;
+  const int kk = idx / L.cout, co = idx - kk * L.cout;
+  float s = 0.f;
+  if (kk < KW) {
+    for (int c = 0; c < nchunks; ++c)
+      s += part[(((int64_t)c * mtiles + kk / kTcM) * kTcM + kk % kTcM) * N + co];
+  } else {
+    const float* bp = part + (int64_t)nchunks * mtiles * kTcM * N;
+    for (int c = 0; c < nchunks; ++c) s += bp[(int64_t)c * N + co];
+  }
+  if (kk < KW) {
+    const int tap = kk / CIN, ci = kk - tap * CIN;
+    grad[L.woff + (co * CIN + ci) * KS * KS + tap] = s;
+  } else {
+    grad[L.boff + co] = s;
+  }
+}
+
+template <int CIN, int KS, int N>
+void run_bwd_w_tc(const float* dy, const bf16* x, float* part, float* grad, int li, int n, int* err,
+                  cudaStream_t st) {
+  const Layer L = cnn_layer(li);
+  constexpr int KW = KS * KS * CIN;
+  const int mt = tc_mtiles(KW);
+  const int nch = (int)tc_wchunks(n, L);
+  const int sm = 2 * (kTcM * kTcWPos * 2 + N * kTcWPos * 2);
+  auto kfn = k_conv_bwd_w_tc<CIN, KS, N>;
+  cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, sm);
+  kfn<<<dim3(mt, nch), kTcThreads, sm, st>>>(dy, x, part, L, n, err);
+  k_conv_bwd_w_sum<CIN, KS, N><<<((KW + 1) * L.cout + 255) / 256, 256, 0, st>>>(part, grad, L, nch, mt);
+}
+
+template <int CIN, int KS, int COUT>
+void run_bwd_data_tc(const float* dy, const uint8_t* wt, const bf16* xact, float* dx, int li, int n,
+                     int* err, cudaStream_t st) {
+  using C = ConvTcT<CIN, KS, COUT>;
+  const Layer L = cnn_layer(li);
+  auto kfn = k_conv_bwd_data_tc<CIN, KS, COUT>;
+  cudaFuncSetAttribute(kfn, cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+  kfn<<<dim3((L.hin * L.hin + kTcM - 1) / kTcM, n), kTcThreads, C::kSmem, st>>>(
+      dy, wt + tct_img_offset(li), xact, dx, L, err);
 }
 
 // AdamW (Loshchilov & Hutter): m, v moments, bias-corrected step, decoupled
@@ -592,16 +874,17 @@ void cnn_train_step(const FrameDesc& b1, const FrameDesc& b2, int n, const float
   float* grad = (float*)(ws + L.grad);
   k_softmax<<<(n * 2 * 32 + 127) / 128, 128, 0, st>>>((const float*)(ws + L.z4), (float*)(ws + L.k),
                                                       kt, dz[3], (float*)(ws + L.lossp), n);
-  for (int li = 3; li >= 0; --li) {
-    const Layer Ly = cnn_layer(li);
-    const bf16* xin = li ? a[li - 1] : x0;
-    k_conv_bwd_w<<<dim3(Ly.cin, Ly.cout), kCnnThreads, 0, st>>>(dz[li], xin, grad, Ly, n);
-    if (li > 0) {
-      dim3 g((Ly.hin * Ly.hin + kCnnThreads - 1) / kCnnThreads, Ly.cin, n);
-      k_conv_bwd_data<<<g, kCnnThreads, sizeof(float) * Ly.cout * Ly.k * Ly.k, st>>>(
-          dz[li], prm, a[li - 1], dz[li - 1], Ly);
-    }
-  }
+  uint8_t* wt = (uint8_t*)(ws + L.wtimg);
+  float* part = (float*)(ws + L.wpart);
+  k_conv_wt_images<<<dim3(8, 3), 256, 0, st>>>(prm, wt);
+  // layer by layer from the head: weight gradients, then the input gradient
+  run_bwd_w_tc<32, 2, 16>(dz[3], a[2], part, grad, 3, n, nullptr, st);
+  run_bwd_data_tc<32, 2, 2>(dz[3], wt, a[2], dz[2], 3, n, nullptr, st);
+  run_bwd_w_tc<32, 3, 32>(dz[2], a[1], part, grad, 2, n, nullptr, st);
+  run_bwd_data_tc<32, 3, 32>(dz[2], wt, a[1], dz[1], 2, n, nullptr, st);
+  run_bwd_w_tc<32, 3, 32>(dz[1], a[0], part, grad, 1, n, nullptr, st);
+  run_bwd_data_tc<32, 3, 32>(dz[1], wt, a[0], dz[0], 1, n, nullptr, st);
+  run_bwd_w_tc<2, 3, 32>(dz[0], x0, part, grad, 0, n, nullptr, st);
   if (tr && tr->grad)
     cudaMemcpyAsync(tr->grad, grad, (size_t)kCnnParams * 4, cudaMemcpyDeviceToDevice, st);
   if (loss) k_loss_sum<<<1, 32, 0, st>>>((const float*)(ws + L.lossp), n * 2, (float)(n * 2 * kT2), loss);
