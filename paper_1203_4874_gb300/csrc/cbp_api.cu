@@ -13,6 +13,7 @@
 #include <cstdio>
 #endif
 #include "cbp_serve.h"
+#include "cbp_nvtx.h"
 
 namespace cbp {
 
@@ -114,6 +115,15 @@ cbp_status Ctx::ensure_cnn_ws(size_t bytes, cudaStream_t st) {
   return CBP_OK;
 }
 
+// Range names of the stages (cbp_stage order).
+const char* stage_label(int stage) {
+  static const char* const names[CBP_NUM_STAGES] = {
+      "cbp.eval",     "cbp.sample_solve", "cbp.scale_solve", "cbp.kernel_spectra",
+      "cbp.row_fft",  "cbp.col_deconv",   "cbp.row_ifft",    "cbp.h2d",
+      "cbp.d2h",      "cbp.proposal",     "cbp.gate"};
+  return stage >= 0 && stage < CBP_NUM_STAGES ? names[stage] : "cbp.stage";
+}
+
 // Enqueue the whole path of one plan on `st` with workspace `wsp`.
 cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
                     const cbp_params* prm, void* k1, void* k2, void* latent, bool deblur,
@@ -122,11 +132,22 @@ cbp_status run_plan(const Plan& p, const cbp_frames* b1, const cbp_frames* b2,
                     cudaStream_t solve, cudaEvent_t fork, cudaEvent_t join, bool tw_ready) {
   cudaEvent_t ev = nullptr;
   cudaStream_t cur = st;   // the stream stages are timed on
+  // an NVTX range per stage; one still open at an error return is closed here
+  struct OpenRanges {
+    int n = 0;
+    ~OpenRanges() {
+      for (; n > 0; --n) nvtx_pop();
+    }
+  } ranges;
   auto begin = [&](int stage) {
+    nvtx_push(stage_label(stage));
+    ++ranges.n;
     if (prof) prof->begin(stage, cur, &ev);
   };
   auto end = [&](int stage, int nk) {
     if (prof) prof->end(stage, cur, ev, nk);
+    nvtx_pop();
+    --ranges.n;
   };
   const bool host_io = prm->flags & CBP_FLAG_HOST_IO;
   const bool kin = deblur && (prm->flags & CBP_FLAG_KERNELS_IN);
@@ -737,6 +758,7 @@ cbp_status cbp_workspace_size(const cbp_frames* b1, const cbp_frames* b2,
 cbp_status cbp_estimate_kernels(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
                                 const cbp_params* params, void* k1, void* k2, cbp_diag* diag,
                                 void* stream) {
+  cbp::NvtxScope range("cbp_estimate_kernels");
   try {
     return call_path(ctx, b1, b2, params, k1, k2, nullptr, diag, stream, false);
   } catch (...) {
@@ -747,6 +769,7 @@ cbp_status cbp_estimate_kernels(cbp_ctx* ctx, const cbp_frames* b1, const cbp_fr
 cbp_status cbp_estimate_kernels_stages(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
                                        const cbp_params* params, void* k1, void* k2,
                                        cbp_diag* diag, const cbp_stage_out* out, void* stream) {
+  cbp::NvtxScope range("cbp_estimate_kernels_stages");
   try {
     if (params && (params->flags & CBP_FLAG_HOST_IO)) return CBP_ERR_INVALID_ARG;
     return call_path(ctx, b1, b2, params, k1, k2, nullptr, diag, stream, false, out);
@@ -758,6 +781,7 @@ cbp_status cbp_estimate_kernels_stages(cbp_ctx* ctx, const cbp_frames* b1, const
 cbp_status cbp_deblur_pair(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
                            const cbp_params* params, void* k1, void* k2, void* latent,
                            cbp_diag* diag, void* stream) {
+  cbp::NvtxScope range("cbp_deblur_pair");
   try {
     return call_path(ctx, b1, b2, params, k1, k2, latent, diag, stream, true);
   } catch (...) {
@@ -837,6 +861,7 @@ cbp_status cbp_stage_times(cbp_ctx* ctx, double* ms, int64_t* launches) {
 cbp_status cbp_estimate_size(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
                              const cbp_size_params* params, int32_t* t1_out, int32_t* t2_out,
                              int32_t* found, double* ratios, int32_t* ncand_out, void* stream) {
+  cbp::NvtxScope range("cbp_estimate_size");
   return size_scan(ctx, b1, b2, params, t1_out, t2_out, found, ratios, ncand_out, stream);
 }
 
@@ -844,6 +869,7 @@ cbp_status cbp_encrypt(cbp_ctx* ctx, const void* latent, int32_t n, int32_t c, i
                        cbp_dtype dtype, const cbp_encrypt_params* params, double* k1, double* k2,
                        void* b1, void* b2, double* k3, double* k4, void* c1, void* c2,
                        int32_t* attempts, void* stream) {
+  cbp::NvtxScope range("cbp_encrypt");
   try {
     return encrypt_frames(ctx, latent, n, c, h, w, dtype, params, k1, k2, b1, b2, k3, k4, c1, c2,
                           attempts, stream);

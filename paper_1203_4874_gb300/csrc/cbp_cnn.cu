@@ -21,6 +21,7 @@
 #include "cbp_common.cuh"
 #include "cbp_internal.h"
 #include "cbp_serve.h"
+#include "cbp_nvtx.h"
 #include "cbp_tc.cuh"
 
 namespace cbp {
@@ -916,6 +917,7 @@ size_t cbp_cnn_param_count(void) { return (size_t)cbp::kCnnParams; }
 
 cbp_status cbp_cnn_forward(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
                            const float* weights, float* kernels, cbp_cnn_trace* trace, void* stream) {
+  cbp::NvtxScope range("cbp_cnn_forward");
   if (!ctx || !kernels) return CBP_ERR_INVALID_ARG;
   Ctx* c = reinterpret_cast<Ctx*>(ctx);
   cbp::FrameDesc d1, d2;
@@ -938,6 +940,7 @@ cbp_status cbp_cnn_forward(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames*
 cbp_status cbp_cnn_train_step(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
                               const float* k_true, float* weights, float* adam_m, float* adam_v,
                               const cbp_adamw* hp, float* loss, cbp_cnn_trace* trace, void* stream) {
+  cbp::NvtxScope range("cbp_cnn_train_step");
   if (!ctx || !k_true || !weights || !adam_m || !adam_v || !hp || hp->step < 1)
     return CBP_ERR_INVALID_ARG;
   Ctx* c = reinterpret_cast<Ctx*>(ctx);

@@ -27,6 +27,7 @@
 #include <deque>
 #include <thread>
 #include <unordered_map>
+#include "cbp_nvtx.h"
 #include "cbp_serve.h"
 
 namespace cbp {
@@ -250,6 +251,7 @@ struct ServeState {
   }
 
   void launch(Slot& s, Entry* e, std::vector<Request*>& batch) {
+    NvtxScope range("cbp.serve_batch");
     const int B = e->B;
     for (int i = 0; i < B; ++i) {
       const Request* r = batch[i];
@@ -454,6 +456,7 @@ extern "C" {
 cbp_status cbp_stream_submit(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
                              const cbp_params* params, void* k1, void* k2, void* latent,
                              uint64_t* ticket) {
+  cbp::NvtxScope range("cbp_stream_submit");
   if (!ctx || !b1 || !b2 || !params || !ticket || !k1 || !k2) return CBP_ERR_INVALID_ARG;
   if (b1->n != 1 || b2->n != 1 || !b1->data || !b2->data) return CBP_ERR_INVALID_ARG;
   if (params->flags & cbp::kServeRejectFlags) return CBP_ERR_INVALID_ARG;
