@@ -337,6 +337,17 @@ cbp_status cbp_encrypt(cbp_ctx* ctx, const void* latent, int32_t n, int32_t c, i
 cbp_status cbp_truncate_lsb(cbp_ctx* ctx, const void* in, cbp_dtype dtype, int64_t count,
                             int32_t bits, int32_t drop, void* out, void* stream);
 
+/* Bounds-checked builds (the library compiled with -DCBP_CHECKS: the
+ * diagnostic variant libcbp_checks.so; the paper has no counterpart).  The
+ * kernels check the indices of their main global stores and shared-memory
+ * staging; a failed check sets a bit in its source file's check word and
+ * skips the access instead of faulting.  Waits for the device, then writes n
+ * words (word i: one source file, bit b: one checked site, 0 = no failure)
+ * and clears them if reset != 0.  Host buffer.
+ * Errors: CBP_ERR_UNSUPPORTED (a normal build), CBP_ERR_INVALID_ARG,
+ * CBP_ERR_CUDA. */
+cbp_status cbp_check_words(uint32_t* words, int32_t n, int32_t reset);
+
 /* Verification of the solver's double-precision reciprocal and reciprocal
  * square root (the paper has no counterpart): the Newton-Raphson iteration
  * from a single-precision seed, two steps, used inside the eigen-solver for

@@ -1,8 +1,10 @@
 """Build libcbp.so (the CUDA library behind include/cbp.h) in-tree for sm_103a.
 
 Each .cu file under csrc/ compiles to an object in parallel; the objects link
-into ``paper_1203_4874_gb300/libcbp.so``.  Rebuilds only when a source or
-header is newer than the library.
+into ``paper_1203_4874_gb300/libcbp.so``.  The same sources compiled with
+-DCBP_CHECKS link into ``libcbp_checks.so``, the bounds-checked diagnostic
+build (cbp_check_words); both builds' objects compile in one parallel pool.
+Rebuilds only when a source or header is newer than the library.
 """
 from __future__ import annotations
 
@@ -18,6 +20,9 @@ CSRC = PKG / "csrc"
 INCLUDE = ROOT / "include"
 BUILD = PKG / "_build"
 LIB = PKG / "libcbp.so"
+# variant -> (object folder, library, extra flags)
+VARIANTS = {"release": (BUILD, LIB, []),
+            "checks": (PKG / "_build_checks", PKG / "libcbp_checks.so", ["-DCBP_CHECKS"])}
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
               "-Xptxas", "-O3"]
@@ -33,10 +38,10 @@ def _sources():
     return sorted(CSRC.glob("*.cu"))
 
 
-def _stale() -> bool:
-    if not LIB.exists():
+def _stale(lib: Path = LIB) -> bool:
+    if not lib.exists():
         return True
-    t = LIB.stat().st_mtime
+    t = lib.stat().st_mtime
     deps = list(CSRC.glob("*")) + list(INCLUDE.glob("*.h")) + [Path(__file__)]
     return any(d.stat().st_mtime > t for d in deps)
 
@@ -47,10 +52,11 @@ def _extra_flags() -> list:
     return os.environ.get("CBP_NVCC_FLAGS", "").split()
 
 
-def _compile(src: Path, verbose_ptxas: bool) -> Path:
-    obj = BUILD / (src.stem + ".o")
-    cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, *_extra_flags(), f"-I{INCLUDE}", f"-I{CSRC}", "-c", str(src),
-           "-o", str(obj)]
+def _compile(src: Path, verbose_ptxas: bool, variant: str = "release") -> Path:
+    folder, _, flags = VARIANTS[variant]
+    obj = folder / (src.stem + ".o")
+    cmd = [_nvcc(), *ARCH, *NVCC_FLAGS, *flags, *_extra_flags(), f"-I{INCLUDE}", f"-I{CSRC}", "-c",
+           str(src), "-o", str(obj)]
     if verbose_ptxas:
         cmd[1:1] = ["-Xptxas", "-v"]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -61,22 +67,31 @@ def _compile(src: Path, verbose_ptxas: bool) -> Path:
     return obj
 
 
-def build(force: bool = False, verbose_ptxas: bool = False) -> Path:
-    """Compile and link libcbp.so; returns its path."""
-    if not force and not _stale():
-        return LIB
-    BUILD.mkdir(exist_ok=True)
-    srcs = _sources()
-    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(srcs), os.cpu_count() or 4))) as ex:
-        objs = list(ex.map(lambda s: _compile(s, verbose_ptxas), srcs))
-    tmp = LIB.with_suffix(".so.tmp")
+def _link(objs, lib: Path) -> None:
+    tmp = lib.with_suffix(".so.tmp")
     cuda = os.environ.get("CUDA_HOME", "/usr/local/cuda")
     cmd = [_nvcc(), *ARCH, "-shared", "-cudart", "shared", "-o", str(tmp), *map(str, objs),
            "-Xlinker", f"-rpath={cuda}/lib64", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
+
+
+def build(force: bool = False, verbose_ptxas: bool = False, variants=("release", "checks")) -> Path:
+    """Compile and link the libraries of `variants` that are out of date
+    (all of them with force); returns the release library's path."""
+    todo = [v for v in variants if force or _stale(VARIANTS[v][1])]
+    if not todo:
+        return LIB
+    srcs = _sources()
+    jobs = [(v, src) for v in todo for src in srcs]
+    for v in todo:
+        VARIANTS[v][0].mkdir(exist_ok=True)
+    with cf.ThreadPoolExecutor(max_workers=max(1, min(len(jobs), os.cpu_count() or 4))) as ex:
+        objs = list(ex.map(lambda j: (j[0], _compile(j[1], verbose_ptxas, j[0])), jobs))
+    for v in todo:
+        _link([o for vv, o in objs if vv == v], VARIANTS[v][1])
     return LIB
 
 

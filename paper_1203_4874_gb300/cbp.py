@@ -3,16 +3,20 @@
 Argument marshalling only: tensors become ``cbp_frames`` descriptors and raw
 pointers, every step of the method runs in the CUDA library.  PyTorch supplies
 device memory and streams.  If ``libcbp.so`` is missing, loading raises.
+With CBP_LIBRARY=checks in the environment the bounds-checked build
+``libcbp_checks.so`` is loaded instead (see cbp_check_words).
 """
 from __future__ import annotations
 
 import ctypes
 from ctypes import POINTER, byref, c_double, c_int, c_int32, c_int64, c_uint32, c_uint64, c_void_p
+import os
 from pathlib import Path
 
 import torch
 
-LIB_PATH = Path(__file__).resolve().parent / "libcbp.so"
+LIB_PATH = Path(__file__).resolve().parent / (
+    "libcbp_checks.so" if os.environ.get("CBP_LIBRARY") == "checks" else "libcbp.so")
 
 CBP_OK, CBP_WARN_ILL_CONDITIONED = 0, 1
 CBP_ERR_INVALID_ARG, CBP_ERR_SIZE_MISMATCH, CBP_ERR_NOT_COPRIME = -1, -2, -3
@@ -31,7 +35,7 @@ EXPORTED = [
     "cbp_stream_submit", "cbp_stream_poll", "cbp_stream_stats", "cbp_profile", "cbp_stage_times",
     "cbp_estimate_kernels_stages", "cbp_estimate_kernels_noalloc", "cbp_cnn_param_count",
     "cbp_cnn_forward", "cbp_cnn_train_step", "cbp_learned_load", "cbp_estimate_size",
-    "cbp_truncate_lsb", "cbp_encrypt", "cbp_check_recip",
+    "cbp_truncate_lsb", "cbp_encrypt", "cbp_check_recip", "cbp_check_words",
 ]
 STAGES = ["eval", "sample_solve", "scale_solve", "kernel_spectra", "row_fft", "col_deconv",
           "row_ifft", "h2d", "d2h", "proposal", "gate"]
@@ -92,7 +96,7 @@ def lib() -> ctypes.CDLL:
     global _lib
     if _lib is None:
         if not LIB_PATH.exists():
-            raise RuntimeError(f"libcbp.so not built at {LIB_PATH}; run __graft_entry__.build()")
+            raise RuntimeError(f"{LIB_PATH.name} not built at {LIB_PATH}; run __graft_entry__.build()")
         L = ctypes.CDLL(str(LIB_PATH))
         fr, pr, dg = POINTER(cbp_frames), POINTER(cbp_params), POINTER(cbp_diag)
         sig = {
@@ -125,6 +129,7 @@ def lib() -> ctypes.CDLL:
             "cbp_truncate_lsb": ([c_void_p, c_void_p, c_int, c_int64, c_int32, c_int32, c_void_p,
                                   c_void_p], c_int),
             "cbp_check_recip": ([c_void_p, c_int64, c_void_p, c_void_p, c_void_p], c_int),
+            "cbp_check_words": ([POINTER(c_uint32), c_int32, c_int32], c_int),
             "cbp_encrypt": ([c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int,
                              POINTER(cbp_encrypt_params), c_void_p, c_void_p, c_void_p, c_void_p,
                              c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_int32), c_void_p], c_int),
@@ -546,3 +551,14 @@ def save_cnn_weights(path, weights) -> None:
 
 def cbp_learned_load(ctx, path) -> None:
     _check(lib().cbp_learned_load(ctx, str(path).encode()), "cbp_learned_load")
+
+
+CHECK_WORDS = 6   # source files with checked sites: fft, colpass, eval, solve, cnn, forward
+
+
+def cbp_check_words(reset: bool = False) -> list:
+    """The bounds-checked build's check words (all zero: no failed check);
+    raises CbpError(CBP_ERR_UNSUPPORTED) in a normal build."""
+    w = (c_uint32 * CHECK_WORDS)()
+    _check(lib().cbp_check_words(w, CHECK_WORDS, int(reset)), "cbp_check_words")
+    return list(w)

@@ -8,6 +8,7 @@
 #include <new>
 #include <vector>
 #include "cbp.h"
+#include "cbp_common.cuh"
 #include "cbp_internal.h"
 #if defined(CBP_DEBUG_ERRORS) || defined(CBP_TIMELINE)
 #include <cstdio>
@@ -113,6 +114,17 @@ cbp_status Ctx::ensure_cnn_ws(size_t bytes, cudaStream_t st) {
   cnn_ws = (char*)p;
   cnn_ws_size = bytes;
   return CBP_OK;
+}
+
+// Check-word readers of the source files (bounds-checked builds).
+namespace {
+unsigned (*&check_reader(int id))(bool) {
+  static unsigned (*readers[kChkWords])(bool) = {};
+  return readers[id];
+}
+}  // namespace
+void register_check_word(int id, unsigned (*read)(bool)) {
+  if (id >= 0 && id < kChkWords) check_reader(id) = read;
 }
 
 // Range names of the stages (cbp_stage order).
@@ -876,6 +888,23 @@ cbp_status cbp_encrypt(cbp_ctx* ctx, const void* latent, int32_t n, int32_t c, i
   } catch (...) {
     return CBP_ERR_OOM;
   }
+}
+
+cbp_status cbp_check_words(uint32_t* words, int32_t n, int32_t reset) {
+#ifdef CBP_CHECKS
+  if (!words || n < 0) return CBP_ERR_INVALID_ARG;
+  if (cudaDeviceSynchronize() != cudaSuccess) return CBP_ERR_CUDA;
+  for (int i = 0; i < n; ++i) {
+    auto rd = i < cbp::kChkWords ? cbp::check_reader(i) : nullptr;
+    words[i] = rd ? rd(reset != 0) : 0u;
+  }
+  return cudaGetLastError() == cudaSuccess ? CBP_OK : CBP_ERR_CUDA;
+#else
+  (void)words;
+  (void)n;
+  (void)reset;
+  return CBP_ERR_UNSUPPORTED;
+#endif
 }
 
 cbp_status cbp_check_recip(const double* x, int64_t n, double* rcp, double* rsqrt, void* stream) {

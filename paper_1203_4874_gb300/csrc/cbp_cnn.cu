@@ -26,6 +26,8 @@
 
 namespace cbp {
 
+CBP_CHECKS_TU(kChkCnn)
+
 namespace {
 
 using bf16 = __nv_bfloat16;
@@ -204,7 +206,7 @@ __device__ __forceinline__ void cnn_profile_cols(const In* base, const FrameDesc
 #pragma unroll
   for (int j = 0; j < kCnnColsPT; ++j) {
     const int c = threadIdx.x + j * kCnnThreads;
-    if (c < fr.w) prof[c] = col[j];
+    if (c < fr.w && CBP_CHECK(c < kCnnMaxW, 6)) prof[c] = col[j];
   }
 }
 
@@ -328,8 +330,9 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const bf16* __restrict__
         const int iy = iy0 + u, ix = ix0 + v;
         if (tap < KS * KS && iy >= 0 && iy < L.hin && ix >= 0 && ix < L.hin) {
           const unsigned short* px = xs + ci0 * plane + (int64_t)iy * L.hin + ix;
+          if (CBP_CHECK(ci0 + 7 < CIN && (int64_t)iy * L.hin + ix < plane, 0))
 #pragma unroll
-          for (int e = 0; e < 8; ++e) q[e >> 1] |= (uint32_t)__ldg(px + e * plane) << (16 * (e & 1));
+            for (int e = 0; e < 8; ++e) q[e >> 1] |= (uint32_t)__ldg(px + e * plane) << (16 * (e & 1));
         }
       } else {
 #pragma unroll
@@ -343,7 +346,8 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_tc(const bf16* __restrict__
         }
       }
     }
-    *(uint4*)(sA + tc::kmajor_offset(kTcM, m, 8 * g)) = make_uint4(q[0], q[1], q[2], q[3]);
+    if (CBP_CHECK(tc::kmajor_offset(kTcM, m, 8 * g) + 16 <= (uint32_t)C::kABytes, 1))
+      *(uint4*)(sA + tc::kmajor_offset(kTcM, m, 8 * g)) = make_uint4(q[0], q[1], q[2], q[3]);
   }
   tc::fence_smem_to_async();
   tc::fence_before_sync();
@@ -517,8 +521,9 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_bwd_data_tc(const float* __
         if (tap < KS * KS && ty >= 0 && tx >= 0 && ty % L.s == 0 && tx % L.s == 0 &&
             ty / L.s < L.hout && tx / L.s < L.hout) {
           const float* pg = dyn + (int64_t)co0 * hw + (ty / L.s) * L.hout + tx / L.s;
+          if (CBP_CHECK(co0 + 7 < COUT && (ty / L.s) * L.hout + tx / L.s < hw, 3))
 #pragma unroll
-          for (int e = 0; e < 8; ++e) q[e >> 1] |= bf16_bits(__ldg(pg + e * hw)) << (16 * (e & 1));
+            for (int e = 0; e < 8; ++e) q[e >> 1] |= bf16_bits(__ldg(pg + e * hw)) << (16 * (e & 1));
         }
       } else {
 #pragma unroll
@@ -534,7 +539,8 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_bwd_data_tc(const float* __
         }
       }
     }
-    *(uint4*)(sA + tc::kmajor_offset(kTcM, m, 8 * g)) = make_uint4(q[0], q[1], q[2], q[3]);
+    if (CBP_CHECK(tc::kmajor_offset(kTcM, m, 8 * g) + 16 <= (uint32_t)C::kABytes, 2))
+      *(uint4*)(sA + tc::kmajor_offset(kTcM, m, 8 * g)) = make_uint4(q[0], q[1], q[2], q[3]);
   }
   tc::fence_smem_to_async();
   tc::fence_before_sync();
@@ -653,7 +659,8 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_bwd_w_tc(const float* __res
                          << (16 * (e & 1));
         }
       }
-      *(uint4*)(sA + tc::kmajor_offset(kTcM, r, 8 * g)) = make_uint4(q[0], q[1], q[2], q[3]);
+      if (CBP_CHECK(tc::kmajor_offset(kTcM, r, 8 * g) + 16 <= (uint32_t)kABytes, 4))
+        *(uint4*)(sA + tc::kmajor_offset(kTcM, r, 8 * g)) = make_uint4(q[0], q[1], q[2], q[3]);
     }
     // dY rows co, the same positions
     for (int c = tid; c < N * (kTcWPos / 8); c += kTcThreads) {
@@ -670,7 +677,8 @@ __global__ void __launch_bounds__(kTcThreads) k_conv_bwd_w_tc(const float* __res
           q[e >> 1] |= bf16_bits(d) << (16 * (e & 1));
         }
       }
-      *(uint4*)(sB + tc::kmajor_offset(N, co, 8 * g)) = make_uint4(q[0], q[1], q[2], q[3]);
+      if (CBP_CHECK(tc::kmajor_offset(N, co, 8 * g) + 16 <= (uint32_t)kBBytes, 5))
+        *(uint4*)(sB + tc::kmajor_offset(N, co, 8 * g)) = make_uint4(q[0], q[1], q[2], q[3]);
     }
     tc::fence_smem_to_async();
     tc::fence_before_sync();

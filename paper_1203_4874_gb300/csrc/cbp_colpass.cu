@@ -41,6 +41,9 @@
 #endif
 
 namespace cbp {
+
+CBP_CHECKS_TU(kChkColpass)
+
 namespace {
 
 constexpr int kFcThreads = 160;
@@ -100,7 +103,8 @@ __device__ __forceinline__ void fc_stage(cf* buf, const cf* src, int Hk, int Pw2
     const int row = e >> 1, half = e & 1;
     const int valid = row < Hk ? max(0, min(2, nv - 2 * half)) * (int)sizeof(cf) : 0;
     const cf* g = valid ? src + (int64_t)row * Pw2p + 2 * half : src;
-    fc_cp_async16(buf + fc_phys<N1>(row) * kFcCols + 2 * half, g, valid);
+    if (CBP_CHECK(fc_phys<N1>(row) < Ph && 2 * half + 2 <= kFcCols, 0))
+      fc_cp_async16(buf + fc_phys<N1>(row) * kFcCols + 2 * half, g, valid);
   }
 }
 
@@ -133,7 +137,7 @@ __global__ void __launch_bounds__(kKrThreads) k_kernel_rows(const double* kd, co
       if (w >= Pw) w -= Pw;
     }
   }
-  krow[(((int64_t)f * 2 + k) * tm + p) * Pw2p + v] = acc;
+  if (CBP_CHECK(p < tm && v < Pw2p, 1)) krow[(((int64_t)f * 2 + k) * tm + p) * Pw2p + v] = acc;
 }
 
 // Inputs of an N1-point DFT giving a kernel's column spectrum K^(k2 + N2 k1):
@@ -202,7 +206,7 @@ k_col_deconv_fused(FusedColArgs a) {
     const cf* KR = a.krow + (int64_t)f * 2 * tm * a.Pw2p + v0;
     for (int e = tid; e < 2 * tm * 2; e += kFcThreads) {
       const int half = e & 1, kp = e >> 1, k = kp / tm, p = kp - k * tm;
-      if (p < (k ? a.t2 : a.t1))
+      if (p < (k ? a.t2 : a.t1) && CBP_CHECK(p < kFcMaxT && v0 + 4 <= a.Pw2p, 2))
         fc_cp_async16(rt + (k * kFcMaxT + p) * kFcCols + 2 * half,
                       KR + ((int64_t)k * tm + p) * a.Pw2p + 2 * half, 16);
     }
@@ -229,6 +233,7 @@ k_col_deconv_fused(FusedColArgs a) {
       float rn = 0.f, rd = 0.f;   // RESID: this task's residual sums
       if (tid < N2 * kFcCols) {
         const int k2 = tid / kFcCols, col = tid % kFcCols;
+        (void)CBP_CHECK((N1 * k2 + N1) * S <= B1, 3);   // this task's slots inside the strip
         cf* q[4];
         {
           cf* base = buf0 + (N1 * k2) * S + col;
@@ -376,7 +381,7 @@ k_col_deconv_fused(FusedColArgs a) {
         const int64_t step = (int64_t)N1 * a.Pw2p;
 #pragma unroll
         for (int n2 = 0; n2 < N2; ++n2) {
-          if (n1 + N1 * n2 < a.H) dst[n2 * step] = conj(x[reg_pos<N2>(n2)]);
+          if (n1 + N1 * n2 < a.H && CBP_CHECK(v0 + col < a.Pw2p, 4)) dst[n2 * step] = conj(x[reg_pos<N2>(n2)]);
         }
       }
     }

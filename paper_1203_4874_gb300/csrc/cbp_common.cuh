@@ -99,4 +99,37 @@ template <typename T> __device__ __forceinline__ T ld_frame(const void* p, int64
   return is_f64 ? (T)__ldg(((const double*)p) + i) : (T)__ldg(((const float*)p) + i);
 }
 
+// Bounds-checked builds (-DCBP_CHECKS).  CBP_CHECK(cond, site) guards one
+// access: in a normal build it is `true` and costs nothing; in a checked
+// build a failed condition sets bit `site` (0..31) of this source file's
+// check word and yields false, so the caller skips the access instead of
+// faulting.  CBP_CHECKS_TU(id) (once per source file) makes the file's word
+// readable through cbp_check_words() as word `id`.
+void register_check_word(int id, unsigned (*read)(bool reset));
+#ifdef CBP_CHECKS
+static __device__ unsigned cbp_check_word;
+__device__ __forceinline__ bool cbp_check(bool ok, int site) {
+  if (!ok) atomicOr(&cbp_check_word, 1u << (site & 31));
+  return ok;
+}
+#define CBP_CHECK(cond, site) (::cbp::cbp_check((cond), (site)))
+#define CBP_CHECKS_TU(id)                                                     \
+  static unsigned cbp_read_check_word(bool reset) {                         \
+    unsigned v = 0;                                                         \
+    cudaMemcpyFromSymbol(&v, cbp_check_word, sizeof v);                     \
+    if (reset) {                                                            \
+      const unsigned z = 0;                                                 \
+      cudaMemcpyToSymbol(cbp_check_word, &z, sizeof z);                     \
+    }                                                                       \
+    return v;                                                               \
+  }                                                                         \
+  static const bool cbp_check_word_registered =                             \
+      (::cbp::register_check_word((id), cbp_read_check_word), true);
+#else
+#define CBP_CHECK(cond, site) (true)
+#define CBP_CHECKS_TU(id)
+#endif
+// Check-word numbers of the source files.
+enum CheckTu { kChkFft = 0, kChkColpass, kChkEval, kChkSolve, kChkCnn, kChkForward, kChkWords };
+
 }  // namespace cbp

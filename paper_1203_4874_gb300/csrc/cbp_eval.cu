@@ -26,6 +26,9 @@
 #include "cbp_internal.h"
 
 namespace cbp {
+
+CBP_CHECKS_TU(kChkEval)
+
 namespace {
 
 constexpr int kDftThreads = 128;
@@ -58,6 +61,7 @@ __device__ __forceinline__ double bin_at(const void* b, int64_t i) {
 template <bool F32>
 __global__ void __launch_bounds__(kDftThreads) k_fold_dft(FoldDftArgs a) {
   if (a.accepted && a.accepted[blockIdx.y / a.C]) return;   // the proposal stands (whole block)
+  if (!CBP_CHECK(a.M <= kMaxM && a.ns <= a.M, 0)) return;    // the root tables' size (whole block)
   __shared__ double cs[kMaxM], sn[kMaxM];
   for (int k = threadIdx.x; k < a.M; k += blockDim.x) sincospi(2.0 * (double)k / (double)a.M, &sn[k], &cs[k]);
   __syncthreads();
@@ -87,6 +91,7 @@ __global__ void __launch_bounds__(kDftThreads) k_fold_dft(FoldDftArgs a) {
       if (m > h) break;
       k += s;
       if (k >= M) k -= M;
+      if (!CBP_CHECK(k >= 0 && k < M, 1)) k = 0;
       re = fma(ev[m - 1], cs[k], re);
       im = fma(-od[m - 1], sn[k], im);
     }
@@ -126,6 +131,7 @@ __device__ __forceinline__ F2 f2_norm(F2 a) {
 // ~1e-14 of the terms' magnitudes, like the bins themselves.
 __global__ void __launch_bounds__(kDftThreads, 4) k_fold_dft_ff(FoldDftArgs a) {
   if (a.accepted && a.accepted[blockIdx.y / a.C]) return;   // the proposal stands (whole block)
+  if (!CBP_CHECK(a.M <= kMaxM && a.ns <= a.M, 0)) return;    // the root tables' size (whole block)
   __shared__ F2 cs[kMaxM], sn[kMaxM];
   for (int k = threadIdx.x; k < a.M; k += blockDim.x) {
     double s, c;
@@ -164,6 +170,7 @@ __global__ void __launch_bounds__(kDftThreads, 4) k_fold_dft_ff(FoldDftArgs a) {
       if (m > h) break;
       k += s;
       if (k >= M) k -= M;
+      if (!CBP_CHECK(k >= 0 && k < M, 1)) k = 0;
       f2_mac(re, ev[m - 1], cs[k]);
       f2_mac(im, f2_neg(od[m - 1]), sn[k]);
     }

@@ -23,6 +23,9 @@
 #endif
 
 namespace cbp {
+
+CBP_CHECKS_TU(kChkFft)
+
 namespace {
 
 constexpr int kFftThreads = 256;
@@ -821,7 +824,7 @@ k_row_pass_ir(RowPassArgs a, const cf* tw_w) {
     // zero each row past W up to the transform length (and rows past nr)
     for (int e = tid; e < nr * (2 * N - W); e += kIrThreads) {
       const int i = e / (2 * N - W), c = W + e - i * (2 * N - W);
-      raw[i * rw + rph[i] + c] = 0.f;
+      if (CBP_CHECK(i < kIrRows && rph[i] + c < rw, 0)) raw[i * rw + rph[i] + c] = 0.f;
     }
     __syncthreads();
     if (FOLD) {
@@ -875,7 +878,8 @@ k_row_pass_ir(RowPassArgs a, const cf* tw_w) {
         const int i = t / M, m = t - i * M;
         TwoSum v = rb[(i * nseg) * M + m];
         for (int sg = 1; sg < nseg; ++sg) v.merge(rb[(i * nseg + sg) * M + m]);
-        v.store((char*)a.bins_r[blockIdx.z] + 8 * (((int64_t)fc * M + m) * fr.h + row_of(g, i)));
+        if (CBP_CHECK(row_of(g, i) < fr.h && (i * nseg + nseg) * M <= kIrThreads, 1))
+          v.store((char*)a.bins_r[blockIdx.z] + 8 * (((int64_t)fc * M + m) * fr.h + row_of(g, i)));
       }
     }
     if (fft) {
@@ -925,6 +929,7 @@ k_row_pass_ir(RowPassArgs a, const cf* tw_w) {
         constexpr unsigned kMask = (N2 == 32) ? 0xffffffffu : ((1u << N2) - 1u);
         const int src = k2 ? N2 - k2 : 0;
         cf* out = spec + (int64_t)row_of(g, i) * a.Pw2p;
+        (void)CBP_CHECK(N < a.Pw2p && row_of(g, i) < fr.h && rph[i] + 2 * N <= rw, 2);
         const cf* tw = tws + k2;
 #pragma unroll
         for (int k1 = 0; k1 < N1; ++k1) {
@@ -1547,6 +1552,7 @@ __global__ void __launch_bounds__(kIrThreads, 2) k_row_ifft_ir(IRowArgs a, const
     // ---- step A: one warp per row, lane k2
     const bool ta = warp < nr && lane < N2;
     const int k2 = lane;
+    (void)CBP_CHECK(N < a.Pw2p && nr <= kIrRows && kIrRows <= kIrThreads / 32, 3);
     cf x[N1];
     if (ta) {
       const cf* X_ = raw + warp * a.Pw2p;
@@ -1585,6 +1591,7 @@ __global__ void __launch_bounds__(kIrThreads, 2) k_row_ifft_ir(IRowArgs a, const
       for (int kk = 0; kk < N2; ++kk) y[kk] = q[(kk >> 2) & 3][N1 * kk];
       reg_dft<true, N2>(y);
       float* o = outp + (int64_t)row_of(g, i) * a.W;
+      (void)CBP_CHECK(row_of(g, i) < a.H, 4);
 #pragma unroll
       for (int n2 = 0; n2 < N2; ++n2) {
         const int c = 2 * (n1 + N1 * n2);

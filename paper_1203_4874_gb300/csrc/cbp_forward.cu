@@ -8,6 +8,9 @@
 #include "cbp_philox.cuh"
 
 namespace cbp {
+
+CBP_CHECKS_TU(kChkForward)
+
 namespace {
 
 // Uniform in (0, 1] from 32 bits.
@@ -118,6 +121,7 @@ k_forward_blur_rb(const float* lat, int c, int h, int w, const double* kern, dou
   for (int q = 0; q < T; ++q) {
     float v[kBlurRows + T - 1];
     const float* col = tile + (ty * kBlurRows) * TW + tx + T - 1 - q;
+    (void)CBP_CHECK((ty * kBlurRows + kBlurRows + T - 2) * TW + tx + T - 1 - q < TH * TW, 0);
 #pragma unroll
     for (int j = 0; j < kBlurRows + T - 1; ++j) v[j] = col[j * TW];
 #pragma unroll

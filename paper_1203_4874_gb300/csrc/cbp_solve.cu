@@ -34,6 +34,9 @@
 #endif
 
 namespace cbp {
+
+CBP_CHECKS_TU(kChkSolve)
+
 namespace {
 
 constexpr int kSolveThreads = 256;
@@ -423,7 +426,8 @@ struct SylvesterApply {
         for (int i = threadIdx.x; i < len0 + len1; i += nth) {
           const float2* src = i < len0 ? g0 + 2 * i : g1 + 2 * (i - len0);
           const unsigned dst = (unsigned)__cvta_generic_to_shared(s0 + i);
-          asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
+          if (CBP_CHECK(L + i < ys_cap, 0))
+            asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(src) : "memory");
         }
         asm volatile("cp.async.wait_all;\n" ::: "memory");
         pb[0] = s0;
@@ -597,6 +601,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_sample_gram(SampleArgs a) {
   __shared__ cdf tile[2 * kGramTile];
   const int f = blockIdx.x, ps = blockIdx.y, s = blockIdx.z;
   if (a.accepted && a.accepted[f]) return;   // the proposal stands; nothing to solve
+  if (!CBP_CHECK(a.t1 + a.t2 <= kMaxN && s < a.ns && ps < 2, 1)) return;   // rho's size (whole block)
   // Real samples (z = 1; z = -1 when M is even) have real Gram matrices.
   const bool real = s == 0 || 2 * s == a.M;
   const SamplePolys<double, double> P64 =
@@ -637,6 +642,8 @@ __global__ void k_sample_solve(SampleArgs a, int nreal) {
     s = 1 + c % ncs;
   }
   if (a.accepted && a.accepted[f]) return;   // the proposal stands; nothing to solve
+  // a real sample's whole CTA, or a complex sample's warp, leaves together
+  if (!CBP_CHECK(f < a.nfr && s < a.ns && n <= kMaxN, 2)) return;
   const int64_t o = ((int64_t)f * 2 + ps) * a.ns + s;
   const TriWs W = carve_tri(smem + (real ? 0 : (size_t)warp * tri_ws_bytes(n)), n);
   const cd* G = a.G + o * n * n;
@@ -1103,7 +1110,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
       l_re += acc.re * acc.re;
       l_im += acc.im * acc.im;
       if (pp >= t || q >= t) l_out += abs2(acc);
-      if (pp < t && q < t) {
+      if (pp < t && q < t && CBP_CHECK(pp < a.M && q < a.M, 3)) {
         kd[pp * t + q] = acc.re;
         void* out = k ? a.k2_out : a.k1_out;
         int64_t oi = (int64_t)f * t * t + pp * t + q;

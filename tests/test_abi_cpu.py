@@ -146,3 +146,17 @@ def test_size_and_encrypt_validation(built_lib):
     assert s == cbp.CBP_ERR_INVALID_ARG
     assert L.cbp_truncate_lsb(ctypes.c_void_p(1), ctypes.c_void_p(0x1000), cbp.CBP_F32, 10, 16, 16,
                               ctypes.c_void_p(0x1000), None) == cbp.CBP_ERR_INVALID_ARG
+
+
+def test_check_words_need_the_checked_build(built_lib):
+    """cbp_check_words answers CBP_ERR_UNSUPPORTED in the normal build (no
+    device call); both builds export every declared symbol."""
+    from paper_1203_4874_gb300 import cbp
+    import pytest as _pt
+    with _pt.raises(cbp.CbpError) as e:
+        cbp.cbp_check_words()
+    assert e.value.status == cbp.CBP_ERR_UNSUPPORTED
+    import ctypes
+    checked = ctypes.CDLL(str(cbp.LIB_PATH.with_name("libcbp_checks.so")))
+    for name in declared_functions():
+        assert hasattr(checked, name), name
