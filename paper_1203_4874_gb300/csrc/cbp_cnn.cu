@@ -178,10 +178,11 @@ __global__ void __launch_bounds__(kCnnThreads) k_cnn_input(FrameDesc f1, FrameDe
 }
 
 // The same resampling with one CTA per output row: the input rows of the row's
-// cells are read once, coalesced (a thread per input column), weighted by
-// their overlaps and summed over rows and channels into a shared column
-// profile; each output cell then sums its columns' profile with the column
-// overlaps.  Widths up to kCnnMaxW.
+// cells are read once, coalesced (a thread per input column, three channels'
+// loads in flight together), weighted by their overlaps and summed over rows
+// and channels into a shared column profile (dynamic shared memory, one float
+// per input column); each output cell then sums its columns' profile with the
+// column overlaps.  Widths up to kCnnMaxW.
 constexpr int kCnnMaxW = 8192;
 constexpr int kCnnColsPT = 8;
 template <typename In>
@@ -194,7 +195,24 @@ __device__ __forceinline__ void cnn_profile_cols(const In* base, const FrameDesc
     const int wy = min(yb, (r + 1) * kCnnSide) - max(ya, r * kCnnSide);
 #pragma unroll
     for (int j = 0; j < kCnnColsPT; ++j) v[j] = 0.f;
-    for (int ch = 0; ch < fr.c; ++ch) {
+    int ch = 0;
+    for (; ch + 3 <= fr.c; ch += 3) {
+      // three channels' loads in flight together; summed in channel order
+      const In* row = base + (int64_t)ch * fr.cs + (int64_t)r * fr.rs + threadIdx.x;
+      float a[3][kCnnColsPT];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < kCnnColsPT; ++j)
+          a[k][j] = ((int)threadIdx.x + j * kCnnThreads < fr.w)
+                        ? (float)__ldg(row + k * fr.cs + j * kCnnThreads)
+                        : 0.f;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < kCnnColsPT; ++j) v[j] += a[k][j];
+    }
+    for (; ch < fr.c; ++ch) {
       const In* row = base + (int64_t)ch * fr.cs + (int64_t)r * fr.rs + threadIdx.x;
 #pragma unroll
       for (int j = 0; j < kCnnColsPT; ++j)
@@ -210,8 +228,12 @@ __device__ __forceinline__ void cnn_profile_cols(const In* base, const FrameDesc
   }
 }
 
-__global__ void __launch_bounds__(kCnnThreads) k_cnn_input_rows(FrameDesc f1, FrameDesc f2, bf16* x0) {
-  __shared__ float prof[kCnnMaxW];
+#ifndef CBP_CNN_INPUT_BLOCKS
+#define CBP_CNN_INPUT_BLOCKS 4   // resident blocks per SM the register budget is set for
+#endif
+__global__ void __launch_bounds__(kCnnThreads, CBP_CNN_INPUT_BLOCKS)
+k_cnn_input_rows(FrameDesc f1, FrameDesc f2, bf16* x0) {
+  extern __shared__ float prof[];   // max(f1.w, f2.w) columns
   const int y = blockIdx.x, z = blockIdx.y, f = blockIdx.z;
   const FrameDesc& fr = z ? f2 : f1;
   const int r0 = (int)(((int64_t)y * fr.h) / kCnnSide);
@@ -843,7 +865,8 @@ void cnn_forward(const FrameDesc& b1, const FrameDesc& b2, int n, const float* p
   bf16* x0 = (bf16*)(ws + L.x0);
   bf16* a[3] = {(bf16*)(ws + L.a1), (bf16*)(ws + L.a2), (bf16*)(ws + L.a3)};
   if (b1.w <= kCnnMaxW && b2.w <= kCnnMaxW)
-    k_cnn_input_rows<<<dim3(kCnnSide, 2, n), kCnnThreads, 0, st>>>(b1, b2, x0);
+    k_cnn_input_rows<<<dim3(kCnnSide, 2, n), kCnnThreads, sizeof(float) * std::max(b1.w, b2.w), st>>>(
+        b1, b2, x0);
   else
     k_cnn_input<<<dim3(kCnnSide * kCnnSide / kCnnThreads, 2, n), kCnnThreads, 0, st>>>(b1, b2, x0);
   uint8_t* wimg = (uint8_t*)(ws + L.wimg);
