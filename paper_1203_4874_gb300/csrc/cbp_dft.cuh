@@ -5,8 +5,39 @@
 
 namespace cbp {
 
+// Butterfly arithmetic: complex add and subtract, and a real multiple of a
+// complex value, alone or added to another.  For float data on this GPU each
+// is one paired FP32 instruction on a (re, im) register pair, rounded exactly
+// like the two scalar operations it replaces (a - b as the fused b * -1 + a;
+// s a + c fused, as the scalar code contracts it).  -DCBP_F32X2=0 keeps them
+// scalar.
+#ifndef CBP_F32X2
+#define CBP_F32X2 1
+#endif
+template <typename T> __device__ __forceinline__ cpx<T> bf_add(cpx<T> a, cpx<T> b) { return a + b; }
+template <typename T> __device__ __forceinline__ cpx<T> bf_sub(cpx<T> a, cpx<T> b) { return a - b; }
+template <typename T> __device__ __forceinline__ cpx<T> bf_scale(T s, cpx<T> a) { return s * a; }
+template <typename T> __device__ __forceinline__ cpx<T> bf_fma(T s, cpx<T> a, cpx<T> c) {
+  return mk<T>(fma(s, a.re, c.re), fma(s, a.im, c.im));
+}
+#if CBP_F32X2 && defined(__CUDA_ARCH__) && (__CUDA_ARCH__ >= 1000)
+__device__ __forceinline__ float2 bf_f2(cf a) { return make_float2(a.re, a.im); }
+__device__ __forceinline__ cf bf_cf(float2 a) { return mk(a.x, a.y); }
+template <> __device__ __forceinline__ cf bf_add<float>(cf a, cf b) { return bf_cf(__fadd2_rn(bf_f2(a), bf_f2(b))); }
+template <> __device__ __forceinline__ cf bf_sub<float>(cf a, cf b) {
+  return bf_cf(__ffma2_rn(bf_f2(b), make_float2(-1.f, -1.f), bf_f2(a)));
+}
+template <> __device__ __forceinline__ cf bf_scale<float>(float s, cf a) {
+  return bf_cf(__fmul2_rn(make_float2(s, s), bf_f2(a)));
+}
+template <> __device__ __forceinline__ cf bf_fma<float>(float s, cf a, cf c) {
+  return bf_cf(__ffma2_rn(make_float2(s, s), bf_f2(a), bf_f2(c)));
+}
+#endif
+
 // In-register DFTs of size R (Inv: e^{+i...}, unnormalised), float constants
 // for float data.  Radix 8 = 2 x 4 and radix 9 = 3 x 3 with internal twiddles.
+// Products by +-i stay scalar (a swap and a sign, free in scalar adds).
 template <typename T, bool Inv>
 __device__ __forceinline__ cpx<T> mul_i(cpx<T> d) {     // (Inv ? +i : -i) * d
   return Inv ? mk<T>(-d.im, d.re) : mk<T>(d.im, -d.re);
@@ -14,28 +45,28 @@ __device__ __forceinline__ cpx<T> mul_i(cpx<T> d) {     // (Inv ? +i : -i) * d
 
 template <typename T, bool Inv>
 __device__ __forceinline__ void dft2(cpx<T>& a, cpx<T>& b) {
-  const cpx<T> t = a - b;
-  a = a + b;
+  const cpx<T> t = bf_sub(a, b);
+  a = bf_add(a, b);
   b = t;
 }
 
 template <typename T, bool Inv>
 __device__ __forceinline__ void dft3(cpx<T>& a, cpx<T>& b, cpx<T>& c) {
   const T h = (T)0.86602540378443864676;       // sin(2 pi / 3)
-  const cpx<T> sm = b + c, d = b - c;
-  const cpx<T> t1 = a - (T)0.5 * sm;
+  const cpx<T> sm = bf_add(b, c), d = bf_sub(b, c);
+  const cpx<T> t1 = bf_fma((T)-0.5, sm, a);
   const cpx<T> t2 = h * mul_i<T, Inv>(d);
-  a = a + sm;
-  b = t1 + t2;
-  c = t1 - t2;
+  a = bf_add(a, sm);
+  b = bf_add(t1, t2);
+  c = bf_sub(t1, t2);
 }
 
 template <typename T, bool Inv>
 __device__ __forceinline__ void dft4(cpx<T>& v0, cpx<T>& v1, cpx<T>& v2, cpx<T>& v3) {
-  const cpx<T> t0 = v0 + v2, t1 = v0 - v2, t2 = v1 + v3;
-  const cpx<T> t3 = mul_i<T, Inv>(v1 - v3);
-  v0 = t0 + t2;
-  v2 = t0 - t2;
+  const cpx<T> t0 = bf_add(v0, v2), t1 = bf_sub(v0, v2), t2 = bf_add(v1, v3);
+  const cpx<T> t3 = mul_i<T, Inv>(bf_sub(v1, v3));
+  v0 = bf_add(t0, t2);
+  v2 = bf_sub(t0, t2);
   v1 = t1 + t3;
   v3 = t1 - t3;
 }
@@ -47,13 +78,13 @@ __device__ __forceinline__ void dft_odd(cpx<T>* v, const T* C, const T* S) {
   cpx<T> a[H], b[H];
 #pragma unroll
   for (int m = 1; m <= H; ++m) {
-    a[m - 1] = v[m] + v[R - m];
-    b[m - 1] = v[m] - v[R - m];
+    a[m - 1] = bf_add(v[m], v[R - m]);
+    b[m - 1] = bf_sub(v[m], v[R - m]);
   }
   const cpx<T> x0 = v[0];
   cpx<T> s0 = x0;
 #pragma unroll
-  for (int m = 0; m < H; ++m) s0 = s0 + a[m];
+  for (int m = 0; m < H; ++m) s0 = bf_add(s0, a[m]);
   v[0] = s0;
 #pragma unroll
   for (int k = 1; k <= H; ++k) {
@@ -61,8 +92,8 @@ __device__ __forceinline__ void dft_odd(cpx<T>* v, const T* C, const T* S) {
 #pragma unroll
     for (int m = 1; m <= H; ++m) {
       const int j = (k * m) % R;
-      re = re + C[j] * a[m - 1];
-      im = im + S[j] * b[m - 1];
+      re = bf_fma(C[j], a[m - 1], re);
+      im = bf_fma(S[j], b[m - 1], im);
     }
     const cpx<T> si = mul_i<T, Inv>(im);   // forward: X[k] = re - i im, X[R-k] = re + i im
     v[k] = re + si;
@@ -97,18 +128,18 @@ __device__ __forceinline__ void small_dft(cpx<T>* v) {
     dft4<T, Inv>(v[0], v[2], v[4], v[6]);
     dft4<T, Inv>(v[1], v[3], v[5], v[7]);
     const T r = (T)0.70710678118654752440;
-    const cpx<T> o1 = r * (v[3] + mul_i<T, Inv>(v[3]));     // w8^1 = r (1 -/+ i)
-    const cpx<T> o2 = mul_i<T, Inv>(v[5]);                   // w8^2 = -/+ i
-    const cpx<T> o3 = r * (mul_i<T, Inv>(v[7]) - v[7]);     // w8^3 = r (-1 -/+ i)
+    const cpx<T> o1 = bf_scale(r, v[3] + mul_i<T, Inv>(v[3]));     // w8^1 = r (1 -/+ i)
+    const cpx<T> o2 = mul_i<T, Inv>(v[5]);                          // w8^2 = -/+ i
+    const cpx<T> o3 = bf_scale(r, mul_i<T, Inv>(v[7]) - v[7]);     // w8^3 = r (-1 -/+ i)
     const cpx<T> e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
-    v[0] = e0 + v[1];
-    v[4] = e0 - v[1];
-    v[1] = e1 + o1;
-    v[5] = e1 - o1;
+    v[0] = bf_add(e0, v[1]);
+    v[4] = bf_sub(e0, v[1]);
+    v[1] = bf_add(e1, o1);
+    v[5] = bf_sub(e1, o1);
     v[2] = e2 + o2;
     v[6] = e2 - o2;
-    v[3] = e3 + o3;
-    v[7] = e3 - o3;
+    v[3] = bf_add(e3, o3);
+    v[7] = bf_sub(e3, o3);
   } else {  // R == 9: 3 x 3
     dft3<T, Inv>(v[0], v[3], v[6]);
     dft3<T, Inv>(v[1], v[4], v[7]);
