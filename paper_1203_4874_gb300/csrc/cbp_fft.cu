@@ -1561,7 +1561,7 @@ __global__ void __launch_bounds__(kIrThreads, 2) k_row_ifft_ir(IRowArgs a, const
       for (int k1 = 0; k1 < N1; ++k1) {
         const int k = k2 + N2 * k1;                 // < N
         const cf xk = X_[k], xc = conj(X_[N - k]);
-        const cf e = 0.5f * (xk + xc), d = 0.5f * (xk - xc);
+        const cf e = bf_scale(0.5f, bf_add(xk, xc)), d = bf_scale(0.5f, bf_sub(xk, xc));
         const cf o = conj(ldg_cpx(tw + N2 * k1)) * d;   // w_Pw^-k d
         x[k1] = mk(e.re - o.im, e.im + o.re);       // E + i O
       }
