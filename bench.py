@@ -92,14 +92,23 @@ def fp32_peak_tflops(sm_mhz: float) -> float:
     return 152 * 128 * 2 * sm_mhz * 1e6 / 1e12
 
 
-STAGE_FILES = {"eval": "cbp_eval.cu", "sample_solve": "cbp_solve.cu", "scale_solve": "cbp_solve.cu",
-               "kernel_spectra": "cbp_fft.cu", "row_fft": "cbp_fft.cu", "col_deconv": "cbp_colpass.cu",
-               "row_ifft": "cbp_fft.cu"}
+# The sources each stage's kernels are compiled from (the file, then the
+# headers its kernels' code comes from).
+_COMMON = ["cbp_common.cuh", "cbp_internal.h"]
+STAGE_FILES = {"eval": ["cbp_eval.cu"] + _COMMON,
+               "sample_solve": ["cbp_solve.cu", "cbp_tri.cuh", "cbp_ff.cuh"] + _COMMON,
+               "scale_solve": ["cbp_solve.cu", "cbp_tri.cuh", "cbp_ff.cuh"] + _COMMON,
+               "kernel_spectra": ["cbp_fft.cu", "cbp_dft.cuh"] + _COMMON,
+               "row_fft": ["cbp_fft.cu", "cbp_dft.cuh"] + _COMMON,
+               "col_deconv": ["cbp_colpass.cu", "cbp_dft.cuh"] + _COMMON,
+               "row_ifft": ["cbp_fft.cu", "cbp_dft.cuh"] + _COMMON}
 
 
 def source_hash(stage: str) -> str:
-    f = ROOT / "paper_1203_4874_gb300" / "csrc" / STAGE_FILES[stage]
-    return hashlib.sha256(f.read_bytes()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in STAGE_FILES[stage]:
+        h.update((ROOT / "paper_1203_4874_gb300" / "csrc" / name).read_bytes())
+    return h.hexdigest()[:16]
 
 
 def measured_traffic(stage: str):

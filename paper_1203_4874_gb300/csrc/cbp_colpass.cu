@@ -161,10 +161,10 @@ __device__ __forceinline__ float fc_abs2(cf k) { return __fmaf_rn(k.re, k.re, __
 // I^ = (t1 + conj(K2) B2) / (d1 + |K2|^2 + eps), t1 = conj(K1) B1, d1 = |K1|^2
 __device__ __forceinline__ cf fc_formula(cf t1, float d1, cf k2, cf b2, float eps) {
   const cf t2 = fc_cmulc(k2, b2);
-  const cf num = mk(__fadd_rn(t1.re, t2.re), __fadd_rn(t1.im, t2.im));
+  const cf num = bf_add(t1, t2);                 // paired, rounded as two __fadd_rn
   const float den = __fadd_rn(__fadd_rn(d1, fc_abs2(k2)), eps);
   const float r = den != 0.f ? fc_rcp(den) : 0.f;
-  return mk(__fmul_rn(r, num.re), __fmul_rn(r, num.im));
+  return bf_scale(r, num);                       // paired, rounded as two __fmul_rn
 }
 
 // RESID (learned path): the same pass with the proposal's kernels, and besides
