@@ -348,6 +348,15 @@ cbp_status cbp_truncate_lsb(cbp_ctx* ctx, const void* in, cbp_dtype dtype, int64
  * CBP_ERR_CUDA. */
 cbp_status cbp_check_words(uint32_t* words, int32_t n, int32_t reset);
 
+/* Checked builds only: with on != 0 every bulk-copy barrier of the row passes
+ * expects 16 bytes more than its copies deliver, so the copies all land but no
+ * phase completes and each bounded wait runs out; a call then reports
+ * CBP_ERR_TIMEOUT in every pair's diagnostics, with no copy in flight and the
+ * context still usable.  For testing the timeout path; on = 0 restores normal
+ * operation.  Waits for the device first.
+ * Errors: CBP_ERR_UNSUPPORTED (a normal build), CBP_ERR_CUDA. */
+cbp_status cbp_check_expire_waits(int32_t on);
+
 /* Verification of the solver's double-precision reciprocal and reciprocal
  * square root (the paper has no counterpart): the Newton-Raphson iteration
  * from a single-precision seed, two steps, used inside the eigen-solver for

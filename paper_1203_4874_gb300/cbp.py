@@ -36,6 +36,7 @@ EXPORTED = [
     "cbp_estimate_kernels_stages", "cbp_estimate_kernels_noalloc", "cbp_cnn_param_count",
     "cbp_cnn_forward", "cbp_cnn_train_step", "cbp_learned_load", "cbp_estimate_size",
     "cbp_truncate_lsb", "cbp_encrypt", "cbp_check_recip", "cbp_check_words",
+    "cbp_check_expire_waits",
 ]
 STAGES = ["eval", "sample_solve", "scale_solve", "kernel_spectra", "row_fft", "col_deconv",
           "row_ifft", "h2d", "d2h", "proposal", "gate"]
@@ -130,6 +131,7 @@ def lib() -> ctypes.CDLL:
                                   c_void_p], c_int),
             "cbp_check_recip": ([c_void_p, c_int64, c_void_p, c_void_p, c_void_p], c_int),
             "cbp_check_words": ([POINTER(c_uint32), c_int32, c_int32], c_int),
+            "cbp_check_expire_waits": ([c_int32], c_int),
             "cbp_encrypt": ([c_void_p, c_void_p, c_int32, c_int32, c_int32, c_int32, c_int,
                              POINTER(cbp_encrypt_params), c_void_p, c_void_p, c_void_p, c_void_p,
                              c_void_p, c_void_p, c_void_p, c_void_p, POINTER(c_int32), c_void_p], c_int),
@@ -562,3 +564,9 @@ def cbp_check_words(reset: bool = False) -> list:
     w = (c_uint32 * CHECK_WORDS)()
     _check(lib().cbp_check_words(w, CHECK_WORDS, int(reset)), "cbp_check_words")
     return list(w)
+
+
+def cbp_check_expire_waits(on: bool) -> None:
+    """Checked build only: make the row passes' bulk-copy waits run out
+    (CBP_ERR_TIMEOUT) or restore them."""
+    _check(lib().cbp_check_expire_waits(int(on)), "cbp_check_expire_waits")

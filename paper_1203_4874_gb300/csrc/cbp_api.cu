@@ -907,6 +907,16 @@ cbp_status cbp_check_words(uint32_t* words, int32_t n, int32_t reset) {
 #endif
 }
 
+cbp_status cbp_check_expire_waits(int32_t on) {
+#ifdef CBP_CHECKS
+  if (cudaDeviceSynchronize() != cudaSuccess) return CBP_ERR_CUDA;
+  return cbp::set_tx_extra(on ? 16u : 0u) ? CBP_OK : CBP_ERR_CUDA;
+#else
+  (void)on;
+  return CBP_ERR_UNSUPPORTED;
+#endif
+}
+
 cbp_status cbp_check_recip(const double* x, int64_t n, double* rcp, double* rsqrt, void* stream) {
   if (!x || !rcp || !rsqrt || n < 0) return CBP_ERR_INVALID_ARG;
   if (n == 0) return CBP_OK;

@@ -26,6 +26,17 @@ namespace cbp {
 
 CBP_CHECKS_TU(kChkFft)
 
+// Checked builds only: bytes every bulk-copy barrier expects beyond its copies.
+// Nonzero (cbp_check_expire_waits), every copy still lands but no barrier
+// phase completes, so each bounded wait runs out with nothing in flight: the
+// timeout path, exercised without a fault.
+#ifdef CBP_CHECKS
+static __device__ uint32_t cbp_tx_extra;
+#define CBP_TX_EXTRA cbp_tx_extra
+#else
+#define CBP_TX_EXTRA 0u
+#endif
+
 namespace {
 
 constexpr int kFftThreads = 256;
@@ -271,6 +282,7 @@ __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  bytes += CBP_TX_EXTRA;
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
                : "memory");
 }
@@ -1889,6 +1901,15 @@ void launch_residual_gate(const Plan& p, char* ws, cudaStream_t st) {
   if (p.fft_f64) run_col_deconv<double, true>(p, ws, st);
   else run_col_deconv<float, true>(p, ws, st);
   launch_gate(p, ws, st, p.col_strips);
+}
+
+bool set_tx_extra(uint32_t bytes) {
+#ifdef CBP_CHECKS
+  return cudaMemcpyToSymbol(cbp_tx_extra, &bytes, sizeof bytes) == cudaSuccess;
+#else
+  (void)bytes;
+  return false;
+#endif
 }
 
 }  // namespace cbp

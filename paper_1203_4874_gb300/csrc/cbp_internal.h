@@ -163,6 +163,8 @@ void launch_row_ifft(const Plan& p, char* ws, void* latent, int out_f64, cudaStr
 // learned path: consistency residual of the kernels in kd (column pass in
 // residual mode, then the per-pair gate: rho, accepted)
 void launch_residual_gate(const Plan& p, char* ws, cudaStream_t st);
+// checked builds: bytes the bulk-copy barriers over-expect (false in a normal build)
+bool set_tx_extra(uint32_t bytes);
 // learned proposal (cbp_cnn.cu)
 size_t cnn_workspace(int n, bool train);
 void cnn_forward(const FrameDesc& b1, const FrameDesc& b2, int n, const float* prm, char* ws,

@@ -149,12 +149,16 @@ def test_size_and_encrypt_validation(built_lib):
 
 
 def test_check_words_need_the_checked_build(built_lib):
-    """cbp_check_words answers CBP_ERR_UNSUPPORTED in the normal build (no
-    device call); both builds export every declared symbol."""
+    """cbp_check_words and cbp_check_expire_waits answer CBP_ERR_UNSUPPORTED
+    in the normal build (no device call); both builds export every declared
+    symbol."""
     from paper_1203_4874_gb300 import cbp
     import pytest as _pt
     with _pt.raises(cbp.CbpError) as e:
         cbp.cbp_check_words()
+    assert e.value.status == cbp.CBP_ERR_UNSUPPORTED
+    with _pt.raises(cbp.CbpError) as e:
+        cbp.cbp_check_expire_waits(True)
     assert e.value.status == cbp.CBP_ERR_UNSUPPORTED
     import ctypes
     checked = ctypes.CDLL(str(cbp.LIB_PATH.with_name("libcbp_checks.so")))
