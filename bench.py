@@ -812,7 +812,8 @@ def main():
     lath = torch.empty((n, C, H, W), dtype=torch.float32).pin_memory()
     k1h = torch.empty((n, T1, T1), dtype=torch.float32).pin_memory()
     k2h = torch.empty((n, T2, T2), dtype=torch.float32).pin_memory()
-    prmh = cbp.params(T1, T2, path="mixed", eps=EPS, flags=cbp.CBP_FLAG_HOST_IO)
+    # consecutive steps overlap (one step's input copies beside the previous one's tail)
+    prmh = cbp.params(T1, T2, path="mixed", eps=EPS, flags=cbp.CBP_FLAG_HOST_IO | cbp.CBP_FLAG_OVERLAP_CALLS)
 
     def step_h():
         cbp.cbp_deblur_pair(ctx, b1h, b2h, prmh, k1=k1h, k2=k2h, latent=lath, diag=False, stream=stream)

@@ -97,6 +97,16 @@ typedef struct cbp_frames {
                                     q >= t_k; gamma_j is the null vector of those
                                     equations (the z1-first pass is not used).
                                     Needs m > max(t1, t2); excludes K1_ONLY        */
+#define CBP_FLAG_OVERLAP_CALLS 64u /* with CBP_FLAG_HOST_IO: the call's input copies
+                                    and kernels do not wait for earlier work on the
+                                    stream, only for this context's previous call
+                                    to be done with each chunk's buffers, so
+                                    consecutive calls overlap (one's input copies
+                                    beside another's tail).  The caller guarantees
+                                    that nothing on the stream still writes the
+                                    host input buffers.  Takes effect when the
+                                    previous call on the context had the same
+                                    chunk layout; results are unchanged          */
 
 typedef struct cbp_params {
   int32_t t1, t2;     /* kernel sizes (square kernels), 1 <= t_k, t1 + t2 <= 64  */

@@ -26,6 +26,7 @@ CBP_F32, CBP_F64 = 0, 1
 CBP_PATH_FP64, CBP_PATH_MIXED, CBP_PATH_LEARNED = 0, 1, 2
 CBP_FLAG_HOST_IO, CBP_FLAG_KERNELS_IN, CBP_FLAG_SINGLE_KERNEL, CBP_FLAG_KERNELS_F64 = 1, 2, 4, 8
 CBP_FLAG_K1_ONLY, CBP_FLAG_SCALE_SUPPORT = 16, 32
+CBP_FLAG_OVERLAP_CALLS = 64
 PATHS = {"fp64": CBP_PATH_FP64, "mixed": CBP_PATH_MIXED, "learned": CBP_PATH_LEARNED}
 
 # Every symbol include/cbp.h declares (checked by the CPU tests).

@@ -618,12 +618,22 @@ cbp_status call_path(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
   const bool kin = (prm->flags & CBP_FLAG_KERNELS_IN) != 0;
   // Host I/O: the chunks' inputs go over on one copy stream in chunk order, so
   // chunk i computes while the inputs of chunks > i are still in flight and
-  // its results go back while later chunks compute.
-  if (host_io && cudaStreamWaitEvent(c->io_st, c->chunk_ev[c->kMaxChunks], 0) != cudaSuccess)
+  // its results go back while later chunks compute.  With
+  // CBP_FLAG_OVERLAP_CALLS and the previous call's chunk layout (tw_ready:
+  // same workspace, same regions), the copies and kernels wait only for the
+  // previous call's chunk i to be done with region i (its chunk event; the
+  // chunk's kernels follow it on the same stream), not for all earlier work
+  // on the caller's stream.
+  const bool overlap = host_io && (prm->flags & CBP_FLAG_OVERLAP_CALLS) && tw_ready;
+  if (host_io && !overlap &&
+      cudaStreamWaitEvent(c->io_st, c->chunk_ev[c->kMaxChunks], 0) != cudaSuccess)
     return CBP_ERR_CUDA;
   for (int i = 0; i < nch; ++i) {
     cudaStream_t cs = c->chunk_st[i % Ctx::kChunkStreams];
-    if (cudaStreamWaitEvent(cs, c->chunk_ev[c->kMaxChunks], 0) != cudaSuccess) return CBP_ERR_CUDA;
+    if (!overlap && cudaStreamWaitEvent(cs, c->chunk_ev[c->kMaxChunks], 0) != cudaSuccess)
+      return CBP_ERR_CUDA;
+    if (overlap && cudaStreamWaitEvent(c->io_st, c->chunk_ev[i], 0) != cudaSuccess)
+      return CBP_ERR_CUDA;
     const size_t a = (size_t)start[i];
     void* ck1 = k1 ? (char*)k1 + a * p.t1 * p.t1 * kes : nullptr;
     void* ck2 = k2 ? (char*)k2 + a * p.t2 * p.t2 * kes : nullptr;
