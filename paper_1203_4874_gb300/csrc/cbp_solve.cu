@@ -1051,7 +1051,6 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
   __syncthreads();
   CBP_TICK(ph, 4);
   // inverse DFT, separable: T[i][q] = sum_j X[i][j] w^{-jq};  K[p][q] = sum_i w^{-ip} T[i][q] / M^2
-  __shared__ double acc_sq[4];  // re^2, im^2, outside-support, total  (per kernel, reused)
   for (int k = 0; k < 2; ++k) {
     if (k >= nk) {
       // k1-only: no kernel 2 (its internal copy zeroed, the caller's buffer untouched)
@@ -1087,8 +1086,6 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
       for (int j = 0; j < M; ++j) cfma(acc, Xk[i * M + j] * inv00, root(wt, j * q, M, 1.0));
       T[idx] = acc;
     }
-    __syncthreads();
-    if (threadIdx.x < 4) acc_sq[threadIdx.x] = 0.0;
     __syncthreads();
     const int t = k ? t2 : t1;
     double* kd = a.kd + (int64_t)f * (t1 * t1 + t2 * t2) + (k ? t1 * t1 : 0);
@@ -1131,8 +1128,6 @@ __global__ void __launch_bounds__(kSolveThreads) k_scale_solve(ScaleArgs a) {
     if (threadIdx.x == 0) {
       double ir = l_re > 0 ? sqrt(l_im / l_re) : 0.0;
       double sr = (l_re + l_im) > 0 ? l_out / (l_re + l_im) : 0.0;
-      acc_sq[0] = ir;
-      acc_sq[1] = sr;
       if (k == 0) {
         a.diag[f].imag_ratio = ir;
         a.diag[f].support_ratio = sr;
