@@ -367,7 +367,7 @@ cbp_status copy_stages(const Plan& p, const char* ws, const cbp_stage_out* o, cu
 // SMs and tails (the scale solve, for one, runs one block per pair).  Pairs
 // are independent, so the results do not depend on the split.
 #ifndef CBP_CHUNKS
-#define CBP_CHUNKS 3     // chunks of a device-resident call (measured: 2: 7.79, 3: 7.67, 4: 7.90, 6: 8.35 ms per 60-pair step)
+#define CBP_CHUNKS 2     // chunks of a device-resident call (measured with the current kernels: 2: 6.58, 3: 6.64, 4: 6.73 ms per 60-pair step)
 #endif
 constexpr int kChunks = CBP_CHUNKS;
 constexpr int kIoChunks = Ctx::kMaxChunks;
