@@ -467,16 +467,22 @@ typedef struct cbp_adamw {
 size_t cbp_cnn_param_count(void);
 
 /* Proposals for n pairs: kernels = device float32 [n][2][15][15] (K1, K2).
- * weights: device float32 vector, or NULL for the context's loaded weights.
+ * weights: device float32 vector, or NULL for the context's loaded weights;
+ * the convolutions run on the tensor cores with the weights rounded to
+ * bfloat16 and bfloat16 activations, accumulating in float32 (a tensor-core
+ * completion that does not arrive in time leaves NaN proposals).
  * Frames as for cbp_estimate_kernels (any size; both of one dtype).  Async. */
 cbp_status cbp_cnn_forward(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
                            const float* weights, float* kernels, cbp_cnn_trace* trace,
                            void* stream);
 
 /* One training step on n pairs: loss = mean over pairs and entries of
- * (K - k_true)^2, k_true device float32 [n][2][15][15]; backward pass, then
- * AdamW on the device float32 weights with moments adam_m, adam_v (same
- * length, zero before the first step).  loss: device float32 [1] or NULL. */
+ * (K - k_true)^2, k_true device float32 [n][2][15][15]; backward pass (its
+ * products on the tensor cores with bfloat16 operands and float32
+ * accumulation, the bias gradients summed in float32, every reduction in a
+ * fixed order), then AdamW on the device float32 weights with moments
+ * adam_m, adam_v (same length, zero before the first step).  loss: device
+ * float32 [1] or NULL. */
 cbp_status cbp_cnn_train_step(cbp_ctx* ctx, const cbp_frames* b1, const cbp_frames* b2,
                               const float* k_true, float* weights, float* adam_m, float* adam_v,
                               const cbp_adamw* hp, float* loss, cbp_cnn_trace* trace,
