@@ -442,7 +442,8 @@ cbp_status cbp_stream_stats(cbp_ctx* ctx, uint64_t* completed, double* p50_ms,
  * 256 x 256, then conv 3x3 stride 2 pad 1 (2 -> 32) + ReLU, conv 3x3 stride 2
  * pad 1 (32 -> 32) + ReLU, conv 3x3 stride 4 pad 1 (32 -> 32) + ReLU,
  * conv 2x2 (32 -> 2), softmax over each channel's 15 x 15 logits: K1, K2.
- * Activations bfloat16, weights and accumulation float32.  A weight vector is
+ * Activations bfloat16, weights kept in float32 (rounded to bfloat16 for the
+ * tensor-core products), accumulation float32.  A weight vector is
  * cbp_cnn_param_count() floats: w1 [32][2][3][3], b1 [32], w2 [32][32][3][3],
  * b2 [32], w3 [32][32][3][3], b3 [32], w4 [2][32][2][2], b4 [2].
  *
