@@ -103,6 +103,18 @@ def conv2d_backward(x, w, dy, stride, pad):
     return dxp[:, pad:pad + H, pad:pad + W], dw, db
 
 
+def bf16_round(x: np.ndarray) -> np.ndarray:
+    """The values rounded first to float32, then to bfloat16 (8 significant
+    bits, round to nearest, ties to even), returned as float64: the weights as
+    the tensor-core products see them.  On the float32 bit pattern: add
+    0x7FFF plus the lowest kept bit, clear the low 16 bits (finite inputs)."""
+    f = np.asarray(x, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    r = ((u + 0x7FFF + lsb) & 0xFFFF0000).astype(np.uint32)
+    return r.view(np.float32).astype(np.float64)
+
+
 def softmax(z: np.ndarray) -> np.ndarray:
     e = np.exp(z - z.max())
     return e / e.sum()

@@ -1,7 +1,7 @@
 """Learned proposal kernels against the FP64 oracle.  The forward
 convolutions run on the tensor cores with BF16 activations and the weights
 rounded to BF16 (FP32 accumulation); the oracle takes the same rounded
-weights (round to nearest even, by the CPU library's conversion), so each
+weights (round to nearest even, oracle.cnn_oracle.bf16_round), so each
 layer computed from the GPU's own previous activation differs from it only
 by that layer's accumulation order and output rounding.  Also: the whole
 forward pass, the loss gradient through the oracle's backward pass, the
@@ -26,9 +26,8 @@ def _flat(params):
 
 def _bf16(params):
     """The weights as the tensor-core products see them: each float32 weight
-    rounded to BF16 (biases stay float32)."""
-    return [[torch.tensor(w, dtype=torch.float32).to(torch.bfloat16).double().numpy(), b.copy()]
-            for w, b in params]
+    rounded to BF16 by the oracle's rounding (biases stay float32)."""
+    return [[cn.bf16_round(w), b.copy()] for w, b in params]
 
 
 def _unflat(vec):

@@ -144,3 +144,25 @@ def test_consistency_residual_eq4():
     k1p = k1.copy()
     k1p[1, 1] += 1e-3
     assert cn.consistency_residual(b1, b2, k1p, k2, grid) > 1e-5
+
+
+def test_bf16_round_pins():
+    """bfloat16 rounding: representable values unchanged, ties to even in both
+    directions, one ulp of 2^-7 at 1, signs and powers of two, and the CPU
+    library's float32 -> bfloat16 conversion on a million random values."""
+    import torch
+    one = 1.0
+    assert cn.bf16_round(np.array([one]))[0] == one
+    assert cn.bf16_round(np.array([one + 2.0 ** -7]))[0] == one + 2.0 ** -7       # representable
+    assert cn.bf16_round(np.array([one + 2.0 ** -8]))[0] == one                    # tie -> even (down)
+    assert cn.bf16_round(np.array([one + 3 * 2.0 ** -8]))[0] == one + 2.0 ** -6   # tie -> even (up)
+    assert cn.bf16_round(np.array([one + 2.0 ** -8 + 2.0 ** -20]))[0] == one + 2.0 ** -7   # above the tie
+    assert cn.bf16_round(np.array([-(one + 2.0 ** -8 + 2.0 ** -20)]))[0] == -(one + 2.0 ** -7)
+    for e in (-30, -1, 0, 5, 30):
+        assert cn.bf16_round(np.array([2.0 ** e]))[0] == 2.0 ** e
+    x = np.random.default_rng(5).normal(0, 1, 1_000_000) * np.exp(np.random.default_rng(6).uniform(-20, 20, 1_000_000))
+    ref = torch.tensor(x, dtype=torch.float32).to(torch.bfloat16).double().numpy()
+    assert np.array_equal(cn.bf16_round(x), ref)
+    # at most half an ulp (2^-8 relative) from the float32 value
+    f = x.astype(np.float32).astype(np.float64)
+    assert np.all(np.abs(cn.bf16_round(x) - f) <= 2.0 ** -8 * np.abs(f))
