@@ -42,6 +42,14 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
 }
 
+// The encodings, checked at compile time: the shapes of the library's MMAs
+// (M = 128; N = 32 and 16) and the operand layout's neighbours.
+static_assert(idesc_bf16_f32(128, 32) == 0x08080490u, "kind::f16 descriptor, BF16 x BF16 -> F32, 128 x 32");
+static_assert(idesc_bf16_f32(128, 16) == 0x08040490u, "kind::f16 descriptor, BF16 x BF16 -> F32, 128 x 16");
+static_assert(kmajor_offset(128, 1, 0) == 16 && kmajor_offset(128, 8, 0) == 128 &&
+                  kmajor_offset(128, 0, 1) == 2 && kmajor_offset(128, 0, 8) == 128 * 16,
+              "rows 16 bytes apart in a core matrix, 8-row groups 128 bytes apart, K-groups R * 16");
+
 // Tensor memory: `ncols` columns (a power of two, >= 32) for this CTA, by one
 // whole warp; the base address is written to *slot.
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
